@@ -1,0 +1,517 @@
+/*
+ * FP64 collision oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, brute-force C used by tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py to check the CUDA library.  Nothing in the
+ * library links, includes or calls this file.
+ *
+ * Contents (paper: "Efficient GPU Cloth Simulation with Non-distance
+ * Barriers and Subspace Reuse", arXiv 2403.19272):
+ *   - brute-force broad phase over all vertex-triangle (VT) and edge-edge
+ *     (EE) primitive pairs (Sec. 4: candidate pairs for CCD; Sec. 8
+ *     implementation details replace the paper's patch BVH by any exact
+ *     culling, here the O(n*m + e^2) definition itself);
+ *   - exact CCD: first time of impact in [0,1] under linear trajectories
+ *     (Sec. 4, Eq. intersect), found as the first root of the coplanarity
+ *     cubic at which the primitives touch;
+ *   - partial CCD: the sign test of the query function Q (Sec. 4.1,
+ *     Eq. collision_judge and Eq. query) at sample points;
+ *   - closest points between primitives and triangle-triangle intersection
+ *     (for the penetration-free invariant of Sec. 7).
+ *
+ * Every floating-point quantity is double; the FP32 box-overlap predicate of
+ * the broad phase is evaluated on float inputs with the single rounding the
+ * definition states (see bp_overlap).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct { double x, y, z; } v3;
+
+static inline v3 mk(double x, double y, double z) { v3 r = {x, y, z}; return r; }
+static inline v3 ld(const double *p) { return mk(p[0], p[1], p[2]); }
+static inline v3 add(v3 a, v3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static inline v3 sub(v3 a, v3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static inline v3 scl(v3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+static inline double dot(v3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static inline v3 crs(v3 a, v3 b) { return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+static inline double nrm(v3 a) { return sqrt(dot(a, a)); }
+static inline v3 lerp(v3 a, v3 b, double t) { return add(a, scl(sub(b, a), t)); }
+static inline double clamp01(double t) { return t < 0 ? 0 : (t > 1 ? 1 : t); }
+
+/* ------------------------------------------------------------------------
+ * Closest points.
+ * ------------------------------------------------------------------------ */
+
+/* Closest point of segment [a,b] to point p: parameter in [0,1]. */
+static double seg_point_param(v3 a, v3 b, v3 p) {
+    v3 ab = sub(b, a);
+    double den = dot(ab, ab);
+    if (den <= 0) return 0.0;
+    return clamp01(dot(sub(p, a), ab) / den);
+}
+
+/* Closest point on triangle (a,b,c) to p, as barycentric weights w[3] of
+ * (a,b,c).  Written as: project p to the plane; if the projection lies in
+ * the triangle (all barycentrics >= 0) take it, otherwise the nearest of the
+ * three edge closest points.  Degenerate (zero-area) triangles use the
+ * edges only. */
+static void closest_pt_tri(v3 p, v3 a, v3 b, v3 c, double w[3]) {
+    v3 ab = sub(b, a), ac = sub(c, a), ap = sub(p, a);
+    double d00 = dot(ab, ab), d01 = dot(ab, ac), d11 = dot(ac, ac);
+    double d20 = dot(ap, ab), d21 = dot(ap, ac);
+    double den = d00 * d11 - d01 * d01;
+    if (den > 1e-300 * (d00 * d11 + 1e-300)) {
+        double v = (d11 * d20 - d01 * d21) / den;
+        double u = (d00 * d21 - d01 * d20) / den;
+        if (v >= 0 && u >= 0 && v + u <= 1) {
+            w[0] = 1 - v - u; w[1] = v; w[2] = u;
+            return;
+        }
+    }
+    /* edges: (a,b), (b,c), (c,a) */
+    double best = INFINITY;
+    v3 P[3] = {a, b, c};
+    for (int e = 0; e < 3; ++e) {
+        v3 s0 = P[e], s1 = P[(e + 1) % 3];
+        double t = seg_point_param(s0, s1, p);
+        v3 q = lerp(s0, s1, t);
+        double d = dot(sub(p, q), sub(p, q));
+        if (d < best) {
+            best = d;
+            w[0] = w[1] = w[2] = 0;
+            w[e] = 1 - t;
+            w[(e + 1) % 3] = t;
+        }
+    }
+}
+
+/* Closest points between segments [p1,q1], [p2,q2]: parameters s,t in [0,1].
+ * Solved as a convex quadratic over the unit square: the unconstrained
+ * minimiser if it is interior, else the best of the four boundary problems
+ * (each a clamped 1-D projection). */
+static void closest_seg_seg(v3 p1, v3 q1, v3 p2, v3 q2, double *s_out, double *t_out) {
+    v3 d1 = sub(q1, p1), d2 = sub(q2, p2), r = sub(p1, p2);
+    double a = dot(d1, d1), e = dot(d2, d2), b = dot(d1, d2), c = dot(d1, r), f = dot(d2, r);
+    double den = a * e - b * b;
+    if (a > 0 && e > 0 && den > 1e-14 * a * e) {
+        double s = (b * f - c * e) / den, t = (a * f - b * c) / den;
+        if (s >= 0 && s <= 1 && t >= 0 && t <= 1) { *s_out = s; *t_out = t; return; }
+    }
+    double best = INFINITY, bs = 0, bt = 0;
+    /* boundaries s=0, s=1: t = clamp(projection) ; t=0, t=1: s = clamp */
+    for (int k = 0; k < 4; ++k) {
+        double s, t;
+        if (k < 2) { s = (double)k; v3 ps = lerp(p1, q1, s); t = seg_point_param(p2, q2, ps); }
+        else { t = (double)(k - 2); v3 pt = lerp(p2, q2, t); s = seg_point_param(p1, q1, pt); }
+        v3 dd = sub(lerp(p1, q1, s), lerp(p2, q2, t));
+        double d = dot(dd, dd);
+        if (d < best) { best = d; bs = s; bt = t; }
+    }
+    *s_out = bs; *t_out = bt;
+}
+
+static double dist_vt(v3 p, v3 a, v3 b, v3 c) {
+    double w[3];
+    closest_pt_tri(p, a, b, c, w);
+    v3 q = add(add(scl(a, w[0]), scl(b, w[1])), scl(c, w[2]));
+    return nrm(sub(p, q));
+}
+
+static double dist_ee(v3 a, v3 b, v3 c, v3 d) {
+    double s, t;
+    closest_seg_seg(a, b, c, d, &s, &t);
+    return nrm(sub(lerp(a, b, s), lerp(c, d, t)));
+}
+
+/* ------------------------------------------------------------------------
+ * Exact CCD (Sec. 4, Eq. intersect): four points moving linearly from x0 to
+ * x1 over t in [0,1].  Contact of a VT or EE pair needs the four points to
+ * be coplanar, i.e. f(t) = det[q1-q0, q2-q0, q3-q0] = 0, a cubic in t.  The
+ * time of impact is the first coplanarity time (a root of f, or a critical
+ * point of f, which also catches tangential grazing) at which the closest
+ * distance between the primitives is <= eta.  If the cubic vanishes
+ * identically (coplanar motion) the distance is checked on a uniform grid of
+ * 1025 times instead.  Returns 2.0 when there is no impact in [0,1].
+ * ------------------------------------------------------------------------ */
+
+static double det3(v3 a, v3 b, v3 c) { return dot(a, crs(b, c)); }
+
+static double cubic_eval(const double c[4], double t) { return ((c[3] * t + c[2]) * t + c[1]) * t + c[0]; }
+
+typedef double (*distfn)(const v3 *q);
+
+static double dvt(const v3 *q) { return dist_vt(q[0], q[1], q[2], q[3]); }
+static double dee(const v3 *q) { return dist_ee(q[0], q[1], q[2], q[3]); }
+
+static void pos_at(const v3 *q0, const v3 *q1, double t, v3 *q) {
+    for (int i = 0; i < 4; ++i) q[i] = lerp(q0[i], q1[i], t);
+}
+
+static int dcmp(const void *a, const void *b) {
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+static double ccd_generic(const v3 *q0, const v3 *q1, double eta, distfn dist) {
+    /* cubic coefficients of det[u(t), v(t), w(t)], u = q1-q0 etc. */
+    v3 u0 = sub(q0[1], q0[0]), v0 = sub(q0[2], q0[0]), w0 = sub(q0[3], q0[0]);
+    v3 du = sub(sub(q1[1], q1[0]), u0), dv = sub(sub(q1[2], q1[0]), v0), dw = sub(sub(q1[3], q1[0]), w0);
+    double c[4];
+    c[0] = det3(u0, v0, w0);
+    c[1] = det3(du, v0, w0) + det3(u0, dv, w0) + det3(u0, v0, dw);
+    c[2] = det3(du, dv, w0) + det3(du, v0, dw) + det3(u0, dv, dw);
+    c[3] = det3(du, dv, dw);
+    double scale = 0;
+    v3 vs[6] = {u0, v0, w0, du, dv, dw};
+    for (int i = 0; i < 6; ++i) { double m = nrm(vs[i]); if (m > scale) scale = m; }
+    double s3 = scale * scale * scale;
+    v3 q[4];
+    if (fabs(c[0]) <= 1e-14 * s3 && fabs(c[1]) <= 1e-14 * s3 && fabs(c[2]) <= 1e-14 * s3 &&
+        fabs(c[3]) <= 1e-14 * s3) {
+        for (int k = 0; k <= 1024; ++k) {
+            double t = k / 1024.0;
+            pos_at(q0, q1, t, q);
+            if (dist(q) <= eta) return t;
+        }
+        return 2.0;
+    }
+    /* candidate times: 0, critical points of f in (0,1), roots of f */
+    double cand[8];
+    int nc = 0;
+    cand[nc++] = 0.0;
+    double brk[4];
+    int nb = 0;
+    brk[nb++] = 0.0;
+    {
+        /* f'(t) = c1 + 2 c2 t + 3 c3 t^2 */
+        double A = 3 * c[3], B = 2 * c[2], C = c[1];
+        double r[2];
+        int nr = 0;
+        if (fabs(A) > 1e-300) {
+            double disc = B * B - 4 * A * C;
+            if (disc >= 0) {
+                double sq = sqrt(disc);
+                double qq = -0.5 * (B + (B >= 0 ? sq : -sq));
+                if (qq != 0) { r[nr++] = qq / A; r[nr++] = C / qq; }
+                else { r[nr++] = 0.0; }
+            }
+        } else if (fabs(B) > 1e-300) {
+            r[nr++] = -C / B;
+        }
+        if (nr == 2 && r[0] > r[1]) { double tmp = r[0]; r[0] = r[1]; r[1] = tmp; }
+        for (int i = 0; i < nr; ++i)
+            if (r[i] > 0 && r[i] < 1) { brk[nb++] = r[i]; cand[nc++] = r[i]; }
+    }
+    brk[nb++] = 1.0;
+    for (int i = 0; i + 1 < nb; ++i) {
+        double lo = brk[i], hi = brk[i + 1];
+        double flo = cubic_eval(c, lo), fhi = cubic_eval(c, hi);
+        if (flo == 0) { cand[nc++] = lo; continue; }
+        if (fhi == 0) { cand[nc++] = hi; continue; }
+        if ((flo < 0) == (fhi < 0)) continue;
+        for (int it = 0; it < 200 && hi - lo > 1e-17; ++it) {
+            double mid = 0.5 * (lo + hi);
+            double fm = cubic_eval(c, mid);
+            if (fm == 0) { lo = hi = mid; break; }
+            if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
+        }
+        cand[nc++] = lo;
+    }
+    qsort(cand, nc, sizeof(double), dcmp);
+    for (int i = 0; i < nc; ++i) {
+        pos_at(q0, q1, cand[i], q);
+        if (dist(q) <= eta) return cand[i];
+    }
+    return 2.0;
+}
+
+/* VT: q = {vertex, tri a, tri b, tri c}; EE: q = {e1 a, e1 b, e2 a, e2 b}. */
+double oc_ccd_vt(const double *x0, const double *x1, double eta) {
+    v3 q0[4], q1[4];
+    for (int i = 0; i < 4; ++i) { q0[i] = ld(x0 + 3 * i); q1[i] = ld(x1 + 3 * i); }
+    return ccd_generic(q0, q1, eta, dvt);
+}
+
+double oc_ccd_ee(const double *x0, const double *x1, double eta) {
+    v3 q0[4], q1[4];
+    for (int i = 0; i < 4; ++i) { q0[i] = ld(x0 + 3 * i); q1[i] = ld(x1 + 3 * i); }
+    return ccd_generic(q0, q1, eta, dee);
+}
+
+/* Batched exact CCD over a pair list.  X0, X1: [nvert,3] float positions
+ * (converted exactly to double).  pairs: [np,4] vertex ids in the order
+ * documented above; kind[i] = 0 (VT) or 1 (EE).  out_toi[i] in [0,1] or 2. */
+void oc_ccd_batch(const float *X0, const float *X1, int64_t np, const int32_t *pairs, const int32_t *kind,
+                  double eta, double *out_toi) {
+    for (int64_t i = 0; i < np; ++i) {
+        double a[12], b[12];
+        for (int k = 0; k < 4; ++k)
+            for (int d = 0; d < 3; ++d) {
+                a[3 * k + d] = (double)X0[3 * (int64_t)pairs[4 * i + k] + d];
+                b[3 * k + d] = (double)X1[3 * (int64_t)pairs[4 * i + k] + d];
+            }
+        out_toi[i] = kind[i] ? oc_ccd_ee(a, b, eta) : oc_ccd_vt(a, b, eta);
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Closest-point coefficients at t = 0 (used by partial CCD sample points and
+ * by the contact projection).  The gap vector p2 - p1 is sum_j c_j x_j:
+ *   VT (v; a,b,c): p1 = x_v, p2 = closest point on the triangle,
+ *                  c = (-1, w_a, w_b, w_c)
+ *   EE (a,b; c,d): p1 = a + s(b-a), p2 = c + t(d-c),
+ *                  c = (-(1-s), -s, 1-t, t)
+ * ------------------------------------------------------------------------ */
+void oc_closest_coef(const double *x, int kind, double *coef) {
+    v3 q[4];
+    for (int i = 0; i < 4; ++i) q[i] = ld(x + 3 * i);
+    if (kind == 0) {
+        double w[3];
+        closest_pt_tri(q[0], q[1], q[2], q[3], w);
+        coef[0] = -1; coef[1] = w[0]; coef[2] = w[1]; coef[3] = w[2];
+    } else {
+        double s, t;
+        closest_seg_seg(q[0], q[1], q[2], q[3], &s, &t);
+        coef[0] = -(1 - s); coef[1] = -s; coef[2] = 1 - t; coef[3] = t;
+    }
+}
+
+/* Partial CCD (Sec. 4.1): Q(lambda) = (p2^1 - p1^1) . (p2^0 - p1^0) at each
+ * sample lambda.  The pair is active when, at some sample,
+ * Q <= dhat * |p2^0 - p1^0| (the end separation measured along the start
+ * direction is below the gap dhat; with dhat = 0 this is exactly the
+ * necessary collision condition Q <= 0 of Eq. collision_judge).
+ * Samples: the closest point at t=0 plus a fixed pattern of nsamp points:
+ *   VT: nsamp 1 -> centroid; 3 -> (1/6,1/6),(2/3,1/6),(1/6,2/3) as weights of
+ *       (b, c) with a getting the remainder;
+ *   EE: nsamp 1 -> (1/2,1/2); 4 -> {1/4,3/4}^2 as (s, t).
+ * Also returns min over samples of Q - dhat*|d0| in *margin. */
+int oc_partial_ccd(const double *x0, const double *x1, int kind, int nsamp, double dhat, double *margin) {
+    double coef[4];
+    oc_closest_coef(x0, kind, coef);
+    double lam[5][2];
+    int ns = 0;
+    if (kind == 0) {
+        lam[ns][0] = coef[2]; lam[ns][1] = coef[3]; ns++;
+        if (nsamp == 1) { lam[ns][0] = 1.0 / 3; lam[ns][1] = 1.0 / 3; ns++; }
+        if (nsamp == 3) {
+            lam[ns][0] = 1.0 / 6; lam[ns][1] = 1.0 / 6; ns++;
+            lam[ns][0] = 2.0 / 3; lam[ns][1] = 1.0 / 6; ns++;
+            lam[ns][0] = 1.0 / 6; lam[ns][1] = 2.0 / 3; ns++;
+        }
+    } else {
+        lam[ns][0] = -coef[1]; lam[ns][1] = coef[3]; ns++;
+        if (nsamp == 1) { lam[ns][0] = 0.5; lam[ns][1] = 0.5; ns++; }
+        if (nsamp == 4) {
+            double v[2] = {0.25, 0.75};
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) { lam[ns][0] = v[i]; lam[ns][1] = v[j]; ns++; }
+        }
+    }
+    v3 a0[4], a1[4];
+    for (int i = 0; i < 4; ++i) { a0[i] = ld(x0 + 3 * i); a1[i] = ld(x1 + 3 * i); }
+    double best = INFINITY;
+    for (int s = 0; s < ns; ++s) {
+        double l1 = lam[s][0], l2 = lam[s][1];
+        v3 p10, p20, p11, p21;
+        if (kind == 0) {
+            p10 = a0[0]; p11 = a1[0];
+            p20 = add(a0[1], add(scl(sub(a0[2], a0[1]), l1), scl(sub(a0[3], a0[1]), l2)));
+            p21 = add(a1[1], add(scl(sub(a1[2], a1[1]), l1), scl(sub(a1[3], a1[1]), l2)));
+        } else {
+            p10 = lerp(a0[0], a0[1], l1); p11 = lerp(a1[0], a1[1], l1);
+            p20 = lerp(a0[2], a0[3], l2); p21 = lerp(a1[2], a1[3], l2);
+        }
+        v3 d0 = sub(p20, p10), d1 = sub(p21, p11);
+        double m = dot(d1, d0) - dhat * nrm(d0);
+        if (m < best) best = m;
+    }
+    *margin = best;
+    return best <= 0 ? 1 : 0;
+}
+
+void oc_partial_ccd_batch(const float *X0, const float *X1, int64_t np, const int32_t *pairs, const int32_t *kind,
+                          int nsamp_vt, int nsamp_ee, double dhat, int32_t *out_active, double *out_margin) {
+    for (int64_t i = 0; i < np; ++i) {
+        double a[12], b[12];
+        for (int k = 0; k < 4; ++k)
+            for (int d = 0; d < 3; ++d) {
+                a[3 * k + d] = (double)X0[3 * (int64_t)pairs[4 * i + k] + d];
+                b[3 * k + d] = (double)X1[3 * (int64_t)pairs[4 * i + k] + d];
+            }
+        out_active[i] = oc_partial_ccd(a, b, kind[i], kind[i] ? nsamp_ee : nsamp_vt, dhat, &out_margin[i]);
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Brute-force broad phase.  The swept box of a primitive is the per-axis
+ * min/max of its vertices' float coordinates at t=0 and t=1.  Boxes A and B
+ * are candidates when, on every axis,
+ *     lo_A <= fl32(hi_B + dhat)  and  lo_B <= fl32(hi_A + dhat),
+ * fl32 being round-to-nearest float addition (computed here as the exact
+ * double sum of two floats, then rounded to float).
+ * VT: every (vertex v, triangle t) with v not in t and not both kinematic.
+ * EE: every (edge e, edge f), e < f by edge index, sharing no vertex and not
+ * both kinematic.  Vertices with id >= n_dyn are kinematic (obstacles).
+ * Returns the pair count; writes at most cap pairs.
+ * ------------------------------------------------------------------------ */
+
+typedef struct { float lo[3], hi[3]; } box;
+
+static box box_of(const float *X0, const float *X1, const int32_t *ids, int k) {
+    box b;
+    for (int d = 0; d < 3; ++d) { b.lo[d] = INFINITY; b.hi[d] = -INFINITY; }
+    for (int i = 0; i < k; ++i)
+        for (int d = 0; d < 3; ++d) {
+            float u = X0[3 * (int64_t)ids[i] + d], v = X1[3 * (int64_t)ids[i] + d];
+            float mn = u < v ? u : v, mx = u < v ? v : u;
+            if (mn < b.lo[d]) b.lo[d] = mn;
+            if (mx > b.hi[d]) b.hi[d] = mx;
+        }
+    return b;
+}
+
+static inline float f32add(float a, float b) { return (float)((double)a + (double)b); }
+
+static int bp_overlap(const box *a, const box *b, float dhat) {
+    for (int d = 0; d < 3; ++d) {
+        if (!(a->lo[d] <= f32add(b->hi[d], dhat))) return 0;
+        if (!(b->lo[d] <= f32add(a->hi[d], dhat))) return 0;
+    }
+    return 1;
+}
+
+int64_t oc_broadphase_vt(const float *X0, const float *X1, int32_t nv, int32_t n_dyn, const int32_t *tris,
+                         int32_t nt, float dhat, int64_t cap, int32_t *out) {
+    box *tb = (box *)malloc(sizeof(box) * (size_t)(nt > 0 ? nt : 1));
+    for (int t = 0; t < nt; ++t) tb[t] = box_of(X0, X1, tris + 3 * t, 3);
+    int64_t n = 0;
+    for (int v = 0; v < nv; ++v) {
+        box vb = box_of(X0, X1, &v, 1);
+        for (int t = 0; t < nt; ++t) {
+            const int32_t *T = tris + 3 * t;
+            if (T[0] == v || T[1] == v || T[2] == v) continue;
+            if (v >= n_dyn && T[0] >= n_dyn && T[1] >= n_dyn && T[2] >= n_dyn) continue;
+            if (!bp_overlap(&vb, &tb[t], dhat)) continue;
+            if (n < cap) { out[2 * n] = v; out[2 * n + 1] = t; }
+            ++n;
+        }
+    }
+    free(tb);
+    return n;
+}
+
+int64_t oc_broadphase_ee(const float *X0, const float *X1, int32_t n_dyn, const int32_t *edges, int32_t ne,
+                         float dhat, int64_t cap, int32_t *out) {
+    box *eb = (box *)malloc(sizeof(box) * (size_t)(ne > 0 ? ne : 1));
+    for (int e = 0; e < ne; ++e) eb[e] = box_of(X0, X1, edges + 2 * e, 2);
+    int64_t n = 0;
+    for (int e = 0; e < ne; ++e) {
+        const int32_t *E = edges + 2 * e;
+        for (int f = e + 1; f < ne; ++f) {
+            const int32_t *F = edges + 2 * f;
+            if (E[0] == F[0] || E[0] == F[1] || E[1] == F[0] || E[1] == F[1]) continue;
+            if (E[0] >= n_dyn && E[1] >= n_dyn && F[0] >= n_dyn && F[1] >= n_dyn) continue;
+            if (!bp_overlap(&eb[e], &eb[f], dhat)) continue;
+            if (n < cap) { out[2 * n] = e; out[2 * n + 1] = f; }
+            ++n;
+        }
+    }
+    free(eb);
+    return n;
+}
+
+/* Brute-force candidates of ONE query primitive against all others (for
+ * sampled checks at sizes where the full O(n*m) sweep is too slow). */
+int64_t oc_broadphase_vt_one(const float *X0, const float *X1, int32_t v, int32_t n_dyn, const int32_t *tris,
+                             int32_t nt, float dhat, int64_t cap, int32_t *out_t) {
+    box vb = box_of(X0, X1, &v, 1);
+    int64_t n = 0;
+    for (int t = 0; t < nt; ++t) {
+        const int32_t *T = tris + 3 * t;
+        if (T[0] == v || T[1] == v || T[2] == v) continue;
+        if (v >= n_dyn && T[0] >= n_dyn && T[1] >= n_dyn && T[2] >= n_dyn) continue;
+        box tb = box_of(X0, X1, T, 3);
+        if (!bp_overlap(&vb, &tb, dhat)) continue;
+        if (n < cap) out_t[n] = t;
+        ++n;
+    }
+    return n;
+}
+
+int64_t oc_broadphase_ee_one(const float *X0, const float *X1, const int32_t *e2, int32_t n_dyn,
+                             const int32_t *edges, int32_t ne, float dhat, int64_t cap, int32_t *out_f) {
+    box qb = box_of(X0, X1, e2, 2);
+    int64_t n = 0;
+    for (int f = 0; f < ne; ++f) {
+        const int32_t *F = edges + 2 * f;
+        if (e2[0] == F[0] || e2[0] == F[1] || e2[1] == F[0] || e2[1] == F[1]) continue;
+        if (e2[0] >= n_dyn && e2[1] >= n_dyn && F[0] >= n_dyn && F[1] >= n_dyn) continue;
+        box fb = box_of(X0, X1, F, 2);
+        if (!bp_overlap(&qb, &fb, dhat)) continue;
+        if (n < cap) out_f[n] = f;
+        ++n;
+    }
+    return n;
+}
+
+/* ------------------------------------------------------------------------
+ * Triangle-triangle intersection (penetration-free invariant, Sec. 7).
+ * Two triangles intersect iff an edge of one crosses the other (closed
+ * segment-vs-triangle test, done with exact-sign-style orientation
+ * predicates in double).  Pairs sharing a vertex test only the edges that
+ * do not contain the shared vertex; pairs sharing an edge are skipped.
+ * ------------------------------------------------------------------------ */
+
+static double orient(v3 a, v3 b, v3 c, v3 d) { return det3(sub(b, a), sub(c, a), sub(d, a)); }
+
+/* does segment pq cross triangle abc (proper or touching)? */
+static int seg_tri(v3 p, v3 q, v3 a, v3 b, v3 c) {
+    double sp = orient(a, b, c, p), sq = orient(a, b, c, q);
+    if ((sp > 0 && sq > 0) || (sp < 0 && sq < 0)) return 0;
+    if (sp == 0 && sq == 0) return 0; /* coplanar: not counted as crossing */
+    double s1 = orient(p, q, a, b), s2 = orient(p, q, b, c), s3 = orient(p, q, c, a);
+    return ((s1 >= 0 && s2 >= 0 && s3 >= 0) || (s1 <= 0 && s2 <= 0 && s3 <= 0));
+}
+
+int64_t oc_count_tri_tri(const double *X, const int32_t *tris, int32_t nt, int64_t cap, int32_t *out) {
+    int64_t n = 0;
+    for (int i = 0; i < nt; ++i) {
+        const int32_t *A = tris + 3 * i;
+        v3 a[3] = {ld(X + 3 * A[0]), ld(X + 3 * A[1]), ld(X + 3 * A[2])};
+        double lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            double u = (&a[0].x)[d], v = (&a[1].x)[d], w = (&a[2].x)[d];
+            lo[d] = fmin(u, fmin(v, w)); hi[d] = fmax(u, fmax(v, w));
+        }
+        for (int j = i + 1; j < nt; ++j) {
+            const int32_t *B = tris + 3 * j;
+            int shared = 0, sa = -1, sb = -1;
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y)
+                    if (A[x] == B[y]) { shared++; sa = x; sb = y; }
+            if (shared >= 2) continue;
+            v3 b[3] = {ld(X + 3 * B[0]), ld(X + 3 * B[1]), ld(X + 3 * B[2])};
+            int skip = 0;
+            for (int d = 0; d < 3 && !skip; ++d) {
+                double u = (&b[0].x)[d], v = (&b[1].x)[d], w = (&b[2].x)[d];
+                if (fmax(u, fmax(v, w)) < lo[d] || fmin(u, fmin(v, w)) > hi[d]) skip = 1;
+            }
+            if (skip) continue;
+            int hit = 0;
+            for (int e = 0; e < 3 && !hit; ++e) {
+                int e0 = e, e1 = (e + 1) % 3;
+                if (!(shared == 1 && (e0 == sa || e1 == sa))) hit |= seg_tri(a[e0], a[e1], b[0], b[1], b[2]);
+                if (!(shared == 1 && (e0 == sb || e1 == sb))) hit |= seg_tri(b[e0], b[e1], a[0], a[1], a[2]);
+            }
+            if (hit) {
+                if (n < cap) { out[2 * n] = i; out[2 * n + 1] = j; }
+                ++n;
+            }
+        }
+    }
+    return n;
+}

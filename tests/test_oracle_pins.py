@@ -1,0 +1,416 @@
+"""Pins of the FP64 oracle against closed forms, invariants and brute force.
+
+Each test ties an oracle function to something other than itself: a closed
+form of the paper's equations, a geometric identity, a hand-built case with
+a known answer (tests/golden) or an exhaustive search.  CPU only.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import collide, pd, subspace
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rot(rng):
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] *= -1
+    return q
+
+
+# ----------------------------------------------------------------------------
+# rest model
+# ----------------------------------------------------------------------------
+
+def test_lumped_mass_total_is_density_times_area():
+    sc = wl.tiny_scene(side=9)
+    m = pd.Model(sc.verts, sc.tris, sc.pins, 0.1, 1e3, 1e-2, 0.005)
+    uv, _ = wl.grid_mesh(9, 9, 0.5, 0.5)
+    assert abs(m.mass.sum() - 0.1 * m.area.sum()) < 1e-15
+    assert abs(m.area.sum() - 0.25) < 5e-4  # jittered 0.5 x 0.5 sheet
+
+
+def test_H_rows_and_definiteness():
+    sc = wl.tiny_scene(side=7, curved=True)
+    m = pd.Model(sc.verts, sc.tris, sc.pins, 0.1, 1e3, 1e-2, 0.005)
+    H = m.H.toarray()
+    assert np.allclose(H, H.T, atol=1e-9)
+    # stiffness rows annihilate translations: H 1 = M / h^2  (Eq. (global))
+    assert np.allclose(H.sum(1), m.mass / m.h ** 2, rtol=1e-9, atol=1e-9 * np.abs(H).max())
+    ev = np.linalg.eigvalsh(H)
+    assert ev.min() > 0
+
+
+def test_deformation_gradient_is_isometry_at_rest_and_equivariant():
+    rng = np.random.default_rng(3)
+    sc = wl.tiny_scene(side=5, curved=True)
+    m = pd.Model(sc.verts, sc.tris, sc.pins, 0.1, 1e3, 1e-2, 0.005)
+    X = m.X
+    F = np.einsum("tjd,tjk->tdk", X[m.T], m.G)
+    FtF = np.einsum("tdk,tdl->tkl", F, F)
+    assert np.allclose(FtF, np.eye(2)[None], atol=1e-12)
+    Q = _rot(rng)
+    Y = X @ Q.T + rng.normal(size=3)
+    F2 = np.einsum("tjd,tjk->tdk", Y[m.T], m.G)
+    assert np.allclose(F2, np.einsum("de,tek->tdk", Q, F), atol=1e-12)
+
+
+def test_polar_projection_orthonormal_equivariant_minimal():
+    rng = np.random.default_rng(4)
+    sc = wl.tiny_scene(side=5)
+    m = pd.Model(sc.verts, sc.tris, sc.pins, 0.1, 1e3, 1e-2, 0.005)
+    x = m.X + 0.02 * rng.normal(size=m.X.shape)
+    R = m.stretch_targets(x)
+    assert np.allclose(np.einsum("tdk,tdl->tkl", R, R), np.eye(2)[None], atol=1e-12)
+    Q = _rot(rng)
+    R2 = m.stretch_targets(x @ Q.T)
+    assert np.allclose(R2, np.einsum("de,tek->tdk", Q, R), atol=1e-10)
+    F = np.einsum("tjd,tjk->tdk", x[m.T], m.G)
+    best = np.sum((F - R) ** 2, axis=(1, 2))
+    for _ in range(200):
+        Rr, _ = np.linalg.qr(rng.normal(size=(len(F), 3, 2)))
+        # compare with random frames nudged toward R: still not closer
+        Rn, _ = np.linalg.qr(R + 0.05 * rng.normal(size=R.shape))
+        for cand in (Rr, Rn):
+            assert np.all(np.sum((F - cand) ** 2, axis=(1, 2)) >= best - 1e-12)
+
+
+def test_bending_stencil_planar_nullspace_and_fold_identity():
+    """For a hinge the stencil sum_j K_j x_j vanishes on planar shapes and
+    has length 2|e| sin(theta/2) when the rest-flat hinge is folded
+    isometrically by dihedral angle theta (cotangent-weight identity)."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        P = rng.normal(size=(4, 3))
+        P[:, 2] = 0
+        e = P[1] - P[0]
+        nrm = np.array([-e[1], e[0], 0.0])
+        if np.dot(P[2] - P[0], nrm) * np.dot(P[3] - P[0], nrm) > 0:
+            P[3] -= 2 * np.dot(P[3] - P[0], nrm) / np.dot(nrm, nrm) * nrm
+        m = pd.Model(P, np.array([[0, 1, 2], [1, 0, 3]]), [], 1, 1, 1, 0.01)
+        assert m.hinges.tolist() == [[0, 1, 2, 3]]
+        K = m.Kh[0]
+        assert abs(K.sum()) < 1e-12
+        assert np.linalg.norm(K @ P) < 1e-12 * np.abs(K).max()
+        Q3 = _rot(rng)
+        Pp = P @ Q3.T + 1.0
+        assert np.linalg.norm(K @ Pp) < 1e-11 * np.abs(K).max()
+        a = e / np.linalg.norm(e)
+        for th in (0.05, 0.7, 2.0):
+            v = P[3] - P[0]
+            vr = v * np.cos(th) + np.cross(a, v) * np.sin(th) + a * np.dot(a, v) * (1 - np.cos(th))
+            Qp = P.copy()
+            Qp[3] = P[0] + vr
+            assert abs(np.linalg.norm(K @ Qp) - 2 * np.linalg.norm(e) * np.sin(th / 2)) < 1e-11 * np.abs(K).max()
+
+
+# ----------------------------------------------------------------------------
+# whole-step closed forms
+# ----------------------------------------------------------------------------
+
+def _params(**kw):
+    p = pd.Params(collisions=False, warm_iters=3, tol_inner=1e-14)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_free_fall_matches_closed_form_with_elasticity_on():
+    """Eq. (var) with a rigidly translating rest-shape cloth: every
+    projection is exact, so each step returns x = z of Eq. (z) and
+    x_n = x_0 + n h v_0 + h^2 g n (n+1) / 2,  v_n = v_0 + n h g."""
+    sc = wl.tiny_scene(side=6, curved=True, pinned=False)
+    v0 = np.array([0.3, -0.1, 0.2])
+    sc.v0 = np.tile(v0, (sc.n, 1)).astype(np.float32)
+    v0 = sc.v0[0].astype(np.float64)  # the state is stored in float32
+    p = _params()
+    o = pd.Oracle(sc, p)
+    x0 = sc.verts.astype(np.float64)
+    g = np.array(p.gravity)
+    h = p.dt
+    for n in range(1, 9):
+        x, v, _ = o.step()
+        xe = x0 + n * h * v0 + h * h * g * n * (n + 1) / 2
+        ve = v0 + n * h * g
+        assert np.max(np.abs(x - xe)) < 1e-12
+        assert np.max(np.abs(v - ve)) < 1e-9
+
+
+def test_rotated_rest_shape_is_stationary():
+    rng = np.random.default_rng(6)
+    sc = wl.tiny_scene(side=6, curved=True, pinned=False)
+    Q = _rot(rng)
+    sc.verts = sc.verts.astype(np.float64)
+    p = _params(gravity=(0.0, 0.0, 0.0))
+    o = pd.Oracle(sc, p)
+    xr = o.model.X @ Q.T + np.array([0.1, 0.2, 0.3])
+    x, v, _ = o.step(xr, np.zeros_like(xr), pin_next=np.zeros((0, 3)), obs_next=[])
+    assert np.max(np.abs(x - xr)) < 1e-12
+
+
+def test_rest_state_with_pins_and_no_gravity_is_fixed_point():
+    sc = wl.tiny_scene(side=7, curved=True)
+    p = _params(gravity=(0.0, 0.0, 0.0))
+    o = pd.Oracle(sc, p)
+    X = o.model.X.copy()
+    for _ in range(3):
+        x, v, _ = o.step()
+    assert np.max(np.abs(x - X)) < 1e-12
+
+
+def test_pd_energy_monotone_per_lg_iteration():
+    """Local step = exact minimisation over projections, global step = exact
+    minimisation over x (Eq. (global)): the PD energy never increases."""
+    rng = np.random.default_rng(7)
+    sc = wl.tiny_scene(side=8, curved=True)
+    m = pd.Model(sc.verts, sc.tris, sc.pins, sc.density, sc.k_stretch, sc.k_bend, 0.005)
+    z = m.X + 0.03 * rng.normal(size=m.X.shape)
+    x = m.X + 0.05 * rng.normal(size=m.X.shape)
+    x[~m.free] = m.X[~m.free]
+    z[~m.free] = m.X[~m.free]
+    E_prev = m.energy(x, z)
+    for _ in range(12):
+        b = m.rhs(x, z)
+        R, sh = m.stretch_targets(x), m.bend_targets(x)
+        xn = m.solve(b, x)
+        E_mid = m.energy(xn, z, R, sh)  # new x, old projections
+        E_new = m.energy(xn, z)  # new projections
+        assert E_mid <= E_prev * (1 + 1e-12)
+        assert E_new <= E_mid * (1 + 1e-12)
+        E_prev, x = E_new, xn
+
+
+def test_exact_global_solve_matches_dense():
+    rng = np.random.default_rng(8)
+    sc = wl.tiny_scene(side=6)
+    m = pd.Model(sc.verts, sc.tris, sc.pins, 0.1, 1e3, 1e-2, 0.005)
+    b = rng.normal(size=(m.n, 3))
+    cw = np.where(rng.random(m.n) < 0.3, 50.0, 0.0)
+    x = m.solve(b, m.X, cw)
+    A = m.H.toarray() + np.diag(cw)
+    f = m.free
+    xe = m.X.copy()
+    xe[f] = np.linalg.solve(A[np.ix_(f, f)], b[f] - A[np.ix_(f, ~f)] @ m.X[~f])
+    assert np.max(np.abs(x - xe)) < 1e-10 * np.max(np.abs(xe))
+
+
+# ----------------------------------------------------------------------------
+# CCD
+# ----------------------------------------------------------------------------
+
+def test_ccd_golden_cases():
+    cases = json.load(open(os.path.join(GOLDEN, "ccd_cases.json")))["cases"]
+    for c in cases:
+        t = collide.ccd_single(np.array(c["x0"], float), np.array(c["x1"], float), c["kind"], 1e-9)
+        if c["toi"] is None:
+            assert t > 1.0, c["name"]
+        else:
+            assert abs(t - c["toi"]) < 1e-12, (c["name"], t)
+
+
+def _vt_first_crossing(q0, q1, ts):
+    """First sample time at which the vertex has crossed the (moving)
+    triangle's plane at a point inside the triangle (vectorised over ts)."""
+    Q = q0[None] + ts[:, None, None] * (q1 - q0)[None]
+    n = np.cross(Q[:, 2] - Q[:, 1], Q[:, 3] - Q[:, 1])
+    s = np.einsum("ij,ij->i", Q[:, 0] - Q[:, 1], n)
+    flip = np.nonzero(np.signbit(s[1:]) != np.signbit(s[:-1]))[0] + 1
+    for k in flip:
+        q = Q[k]
+        # the crossing point at the interval's midpoint must be inside
+        qm = 0.5 * (Q[k - 1] + Q[k])
+        nm = np.cross(qm[2] - qm[1], qm[3] - qm[1])
+        p = qm[0] - np.dot(qm[0] - qm[1], nm) / np.dot(nm, nm) * nm
+        a, b, c = qm[1], qm[2], qm[3]
+        s1 = np.dot(np.cross(b - a, p - a), nm)
+        s2 = np.dot(np.cross(c - b, p - b), nm)
+        s3 = np.dot(np.cross(a - c, p - c), nm)
+        m = min(abs(s1), abs(s2), abs(s3)) / np.dot(nm, nm)
+        if ((s1 > 0 and s2 > 0 and s3 > 0) or (s1 < 0 and s2 < 0 and s3 < 0)) and m > 1e-3:
+            return ts[k]
+    return None
+
+
+def test_ccd_vt_against_dense_time_sampling():
+    """A vertex that crosses the triangle's plane well inside the triangle
+    between two sample times must get a TOI no later than that interval; a
+    reported TOI must put the vertex on the triangle's plane."""
+    rng = np.random.default_rng(9)
+    ts = np.linspace(0, 1, 4001)
+    hits = 0
+    for _ in range(400):
+        q0 = rng.normal(size=(4, 3))
+        q0[0] = q0[1:].mean(0) + rng.normal(size=3) * 0.7
+        q1 = q0 + rng.normal(size=(4, 3)) * 1.2
+        toi = collide.ccd_single(q0, q1, 0, 1e-9)
+        first = _vt_first_crossing(q0, q1, ts)
+        if first is not None:
+            hits += 1
+            assert toi <= first + 1e-12
+        if toi <= 1.0:
+            q = q0 + toi * (q1 - q0)
+            n = np.cross(q[2] - q[1], q[3] - q[1])
+            assert abs(np.dot(q[0] - q[1], n)) / np.linalg.norm(n) < 1e-8
+    assert hits > 20
+
+
+def test_ccd_ee_against_dense_time_sampling():
+    rng = np.random.default_rng(10)
+    ts = np.linspace(0, 1, 4001)
+    hits = 0
+    for _ in range(400):
+        q0 = rng.normal(size=(4, 3))
+        q1 = q0 + rng.normal(size=(4, 3)) * 1.5
+        toi = collide.ccd_single(q0, q1, 1, 1e-9)
+        Q = q0[None] + ts[:, None, None] * (q1 - q0)[None]
+        s = np.einsum("ij,ij->i", np.cross(Q[:, 1] - Q[:, 0], Q[:, 3] - Q[:, 2]), Q[:, 2] - Q[:, 0])
+        first = None
+        for k in np.nonzero(np.signbit(s[1:]) != np.signbit(s[:-1]))[0] + 1:
+            q = 0.5 * (Q[k - 1] + Q[k])
+            d1, d2, r = q[1] - q[0], q[3] - q[2], q[0] - q[2]
+            A = np.array([[d1 @ d1, -d1 @ d2], [-d1 @ d2, d2 @ d2]])
+            st = np.linalg.solve(A, [-d1 @ r, d2 @ r])
+            if 1e-3 < st[0] < 1 - 1e-3 and 1e-3 < st[1] < 1 - 1e-3:
+                first = ts[k]
+                break
+        if first is not None:
+            hits += 1
+            assert toi <= first + 1e-12
+    assert hits > 20
+
+
+def test_partial_ccd_query_identity_at_crossing():
+    """Eq. (collision_judge): at the contact point lambda* of a pair that
+    meets at t*, Q(lambda*) = (t*-1)/t* |p2^0 - p1^0|^2 <= 0."""
+    rng = np.random.default_rng(11)
+    checked = 0
+    for _ in range(400):
+        q0 = rng.normal(size=(4, 3))
+        q1 = q0 + rng.normal(size=(4, 3)) * 1.5
+        t = collide.ccd_single(q0, q1, 0, 1e-9)
+        if not (1e-3 < t <= 1.0):
+            continue
+        qt = q0 + t * (q1 - q0)
+        c = collide.closest_coef(qt, 0)  # contact point barycentrics at t*
+        d0 = c @ q0
+        d1 = c @ q1
+        Q = float(d1 @ d0)
+        assert abs(Q - (t - 1) / t * float(d0 @ d0)) < 1e-7 * max(1.0, float(d0 @ d0) / t)
+        assert Q <= 1e-9
+        checked += 1
+    assert checked > 20
+
+
+def test_partial_ccd_flags_crossing_and_not_separating():
+    # vertex crosses the triangle: active for every sample pattern
+    q0 = np.array([[0.2, 0.2, 1.0], [0, 0, 0], [1, 0, 0], [0, 1, 0]], float)
+    q1 = q0.copy()
+    q1[0, 2] = -1.0
+    for ns in (0, 1, 3):
+        act, mar = collide.partial_ccd(q0, q1, np.array([[0, 1, 2, 3]]), np.array([0]), ns, 4, 0.0)
+        assert act[0] and mar[0] < 0
+    # vertex moves away: inactive
+    q1 = q0.copy()
+    q1[0, 2] = 2.0
+    act, _ = collide.partial_ccd(q0, q1, np.array([[0, 1, 2, 3]]), np.array([0]), 3, 4, 0.0)
+    assert not act[0]
+    # within dhat and not separating: active (sufficiently close, Sec. 4)
+    q0[0, 2] = 5e-4
+    q1 = q0.copy()
+    act, _ = collide.partial_ccd(q0, q1, np.array([[0, 1, 2, 3]]), np.array([0]), 3, 4, 1e-3)
+    assert act[0]
+
+
+# ----------------------------------------------------------------------------
+# broad phase, non-penetration
+# ----------------------------------------------------------------------------
+
+def test_broadphase_contains_every_colliding_pair():
+    rng = np.random.default_rng(12)
+    sc = wl.tiny_scene(side=6)
+    m = pd.Model(sc.verts, sc.tris, sc.pins, 0.1, 1e3, 1e-2, 0.005)
+    X0 = m.X.astype(np.float32)
+    X1 = (m.X + 0.08 * rng.normal(size=m.X.shape)).astype(np.float32)
+    cm = pd.CollisionMesh(m, [])
+    quads, kinds, keys = cm.candidates(X0, X1, 1e-3)
+    cand = set(keys)
+    # every VT / EE pair of the mesh that collides must be a candidate
+    allq, allk, allkeys = [], [], []
+    for v in range(m.n):
+        for t, (a, b, c) in enumerate(m.T):
+            if v in (a, b, c):
+                continue
+            allq.append((v, a, b, c)); allk.append(0); allkeys.append(("vt", v, t))
+    E = cm.edges
+    for i in range(len(E)):
+        for j in range(i + 1, len(E)):
+            if set(E[i]) & set(E[j]):
+                continue
+            allq.append((*E[i], *E[j])); allk.append(1); allkeys.append(("ee", *E[i], *E[j]))
+    toi = collide.ccd(X0, X1, np.array(allq), np.array(allk), 1e-9)
+    hit = [allkeys[i] for i in np.nonzero(toi <= 1.0)[0]]
+    assert len(hit) > 0
+    assert all(h in cand for h in hit)
+
+
+def test_oracle_drape_is_penetration_free():
+    """Sec. 7: the exit CCD line search keeps every step intersection free
+    (cloth-cloth and cloth-sphere)."""
+    sc = wl.drape_sphere(side=12, sphere_subdiv=2)
+    p = pd.Params(max_outer=2, max_inner=6)
+    o = pd.Oracle(sc, p)
+    allT = o.cm.tris
+    for k in range(25):
+        x, v, st = o.step()
+        X = np.concatenate([x] + o.obs)
+        assert len(collide.intersecting_triangle_pairs(X, allT)) == 0
+    assert x[:, 2].min() < -0.04  # it did reach the sphere
+
+
+# ----------------------------------------------------------------------------
+# subspace reference
+# ----------------------------------------------------------------------------
+
+def test_subspace_correction_exact_for_in_span_solution():
+    rng = np.random.default_rng(13)
+    sc = wl.tiny_scene(side=7)
+    m = pd.Model(sc.verts, sc.tris, sc.pins, 0.1, 1e3, 1e-2, 0.005)
+    f = m.free
+    H = m.H.tocsr()
+    cw = np.where(rng.random(m.n) < 0.2, 30.0, 0.0) * f
+    A = m.H.toarray() + np.diag(cw)
+    # U has the exact solution direction in its span
+    sol = np.zeros((m.n, 3))
+    sol[f] = rng.normal(size=(f.sum(), 3))
+    r = A @ sol
+    r[~f] = 0
+    B = np.concatenate([sol, rng.normal(size=(m.n, 5))], axis=1)
+    B[~f] = 0
+    U, _ = np.linalg.qr(B)
+    delta, q = subspace.subspace_correction(U, H, cw, r)
+    assert np.max(np.abs(delta - sol)) < 1e-9 * np.max(np.abs(sol))
+    # Galerkin: q minimises 1/2 y^T A y - r^T y over y = U q
+    def J(qq):
+        y = U @ qq
+        return 0.5 * np.sum(y * (A @ y)) - np.sum(r * y)
+    for _ in range(20):
+        assert J(q) <= J(q + 1e-3 * rng.normal(size=q.shape)) + 1e-12
+
+
+def test_jacobi_reference_converges_to_exact_solve():
+    rng = np.random.default_rng(14)
+    sc = wl.tiny_scene(side=5)
+    m = pd.Model(sc.verts, sc.tris, sc.pins, 1.0, 1.0, 1e-4, 0.005)  # diagonally dominant
+    r = rng.normal(size=(m.n, 3))
+    r[~m.free] = 0
+    d = subspace.jacobi(m.H, None, r, np.zeros_like(r), 400, 1.0, m.free)
+    A = m.H.toarray()
+    f = m.free
+    ex = np.zeros_like(r)
+    ex[f] = np.linalg.solve(A[np.ix_(f, f)], r[f])
+    assert np.max(np.abs(d - ex)) < 1e-8 * np.max(np.abs(ex))
