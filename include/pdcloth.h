@@ -1,0 +1,240 @@
+/*
+ * pdcloth -- GB300 (sm_103a) projective-dynamics cloth stepper, C ABI.
+ *
+ * Implements the per-time-step solve of Lan et al., "Efficient GPU Cloth
+ * Simulation with Non-distance Barriers and Subspace Reuse" (arXiv
+ * 2403.19272): the implicit-Euler variational problem of Sec. 3
+ * (Eq. var_barrier) solved by local-global (LG) iterations (Eq. local /
+ * Eq. global), with
+ *   - non-distance barrier (NDB) collision weights w = k*K^a, Eq. (exp);
+ *   - partial CCD (Sec. 4.1, Eq. collision_judge / Eq. query) to update the
+ *     weights every LG iteration, exact CCD and the alpha*t_TOI line search
+ *     filter for the penetration-free guarantee (Alg. 1, Sec. 7);
+ *   - the subspace-reuse correction of Sec. 5 (Eq. subspace_global,
+ *     Eq. subspace_collision, Eq. uu) followed by Jacobi relaxation of the
+ *     high-frequency residual (Eq. high_frequency_residual);
+ *   - the two-subspace scheme of Sec. 7 (a basis of r_warm modes used
+ *     without collision springs, its first r_reuse columns with them).
+ *
+ * Conventions for every entry point
+ *   - Every call returns a pdc_status; details of the last failure are
+ *     returned by pdc_last_error(handle) (a static string for a NULL
+ *     handle).  No call aborts the process.
+ *   - The library owns all device memory it allocates (cudaMalloc on the
+ *     current device at pdc_create).  The caller owns every buffer it
+ *     passes in and out; arguments named on_device select whether a pointer
+ *     is a device pointer (1) or a host pointer (0).  Host buffers are only
+ *     read or written during the call.
+ *   - Positions and velocities are float32, row-major [count][3] (x, y, z
+ *     interleaved).  Index arrays are int32.
+ *   - Collision vertex ids: cloth vertices 0..nv-1 first, then each
+ *     obstacle's vertices in the order obstacles were added.  Collision
+ *     triangle ids likewise (cloth triangles first).
+ *   - pdc_step is ordered on the stream given to pdc_create (NULL = legacy
+ *     default stream) and returns after the step has finished on the GPU.
+ *   - Not thread safe per handle; different handles are independent.
+ */
+#ifndef PDCLOTH_H
+#define PDCLOTH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdc_ctx *pdc_handle;
+
+typedef enum {
+    PDC_OK = 0,
+    PDC_ERR_ARG = 1,        /* invalid argument (NULL, size, range, dt mismatch) */
+    PDC_ERR_CUDA = 2,       /* a CUDA runtime call failed                        */
+    PDC_ERR_NUMERIC = 3,    /* NaN/Inf or a failed factorisation; state rolled back */
+    PDC_ERR_TIMEOUT = 4,    /* a bounded device wait ran out                      */
+    PDC_ERR_DEGENERATE = 5, /* zero-area rest triangle or bad topology           */
+    PDC_ERR_STATE = 6,      /* call out of order (e.g. no mesh)                  */
+    PDC_ERR_CAPACITY = 7    /* a candidate / hash buffer could not be grown      */
+} pdc_status;
+
+/* Mesh given to pdc_create (copied; host pointers). */
+typedef struct {
+    const float *verts;   /* [nv][3] rest (= initial) positions              */
+    int32_t nv;
+    const int32_t *tris;  /* [nt][3] vertex ids, consistently oriented        */
+    int32_t nt;
+    const int32_t *pins;  /* [npins] vertex ids held by Dirichlet conditions  */
+    int32_t npins;
+} pdc_mesh_desc;
+
+/* Material (Tab. 1 columns rho_m and kappa).  Stretch energy per triangle
+ * k_stretch*A_t/2 |F - R|^2 with R the closest 3x2 matrix with orthonormal
+ * columns; bending per interior edge (3 k_bend/(A_1+A_2))/2 |sum_j K_j x_j -
+ * s_hat|^2 with cotangent weights K and s_hat keeping the rest magnitude. */
+typedef struct {
+    double density;   /* kg / m^2 */
+    double k_stretch;
+    double k_bend;
+} pdc_material;
+
+/* Solver settings.  Fill with pdc_default_params() and override. */
+typedef struct {
+    double dt;               /* time step h (s); the basis depends on it         */
+    double gravity[3];       /* f_ext = m g                                      */
+    double k_ndb_scale;      /* k of Eq. (exp) = k_ndb_scale * mean(diag H)      */
+    double K_ndb;            /* growth base K of Eq. (exp) (paper: 2)            */
+    int32_t a_max;           /* cap on the life-span counter a                   */
+    double alpha_ls;         /* line-search factor alpha (paper: 0.8)            */
+    double d_hat;            /* gap of the activity test and contact target (m); <= 0: automatic */
+    double eta_ccd;          /* exact-CCD contact distance (m)                   */
+    double tol_outer;        /* ||dx||_inf / bbox-diagonal between outer passes  */
+    double tol_inner;        /* ||dx||_inf / bbox-diagonal between inner iterations */
+    double tol_rel_residual; /* > 0: inner loop stops when the PD residual falls
+                                below this fraction of the residual at z        */
+    int32_t max_outer, max_inner, warm_iters;
+    int32_t jacobi_sweeps;   /* Jacobi sweeps per solve cycle                    */
+    double jacobi_omega;     /* Jacobi damping; <= 0: automatic                  */
+    int32_t solve_cycles;    /* subspace correction + sweeps per LG iteration    */
+    int32_t r_warm;          /* basis size used without collision springs (0: none) */
+    int32_t r_reuse;         /* leading columns used with collision springs      */
+    int32_t precision;       /* 0: plain FP32; 1: mixed (BF16 basis on tensor
+                                cores, FP64 reduced solves)                      */
+    int32_t samples_vt;      /* partial-CCD sample pattern: 0, 1 or 3            */
+    int32_t samples_ee;      /* partial-CCD sample pattern: 0, 1 or 4            */
+    int32_t collisions;      /* 0: no collision handling at all                  */
+    int32_t fixed_iters;     /* 1: run exactly warm/max_outer/max_inner iterations */
+    int32_t eig_iters;       /* filtered subspace iterations building the basis  */
+    uint64_t seed;           /* seed of the basis start block                    */
+} pdc_params;
+
+/* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
+typedef struct {
+    int32_t warm_iters, outer_iters, inner_iters;
+    int32_t contact_iters;       /* inner iterations that used collision springs */
+    int64_t n_candidates;        /* broad-phase pairs of the last full CCD       */
+    int64_t n_active;            /* active NDB constraints after the step        */
+    int64_t n_contact_vertices;  /* vertices with a collision spring (last iter) */
+    double t_toi;                /* exit time of impact (2 = none)               */
+    double s_line_search;        /* applied step fraction (1 or alpha*t_TOI)     */
+    double rho0;                 /* PD residual at z                              */
+    double rel_residual;         /* last measured residual / rho0                 */
+    double ms_step, ms_broad, ms_narrow, ms_lg; /* host wall time per phase (ms) */
+    int32_t overflow_retries;    /* buffer regrowths during this step            */
+} pdc_stats;
+
+/* Defaults: dt 1/200, g = (0,0,-9.8), K = 2, a_max 20, alpha 0.8, automatic
+ * d_hat, eta 1e-9, tolerances 1e-3 / 5e-2, 4 outer x 32 inner, 5 warm
+ * iterations, 4 sweeps, 1 cycle, no basis, FP32, samples 3/4, collisions on. */
+void pdc_default_params(pdc_params *p);
+
+/* Build the solver for one cloth mesh (Sec. 3; Eq. (global) rest matrix,
+ * lumped masses, rest operators; Sec. 7 basis precomputation of the r_warm
+ * lowest eigenvectors of the rest matrix).  Fails with PDC_ERR_DEGENERATE on
+ * zero-area triangles or edges shared by more than two triangles.
+ * stream: a cudaStream_t or NULL. */
+pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const pdc_params *params,
+                      void *stream, pdc_handle *out);
+
+/* Add a kinematic (infinite-mass) triangle obstacle; host arrays copied.
+ * Must be called before the first pdc_step.  Its current and target
+ * positions start at verts. */
+pdc_status pdc_add_obstacle(pdc_handle h, const float *verts, int32_t nv, const int32_t *tris, int32_t nt,
+                            int32_t *out_id);
+
+/* Target position of obstacle id at the end of the next step: m4x4 (row
+ * major, host) applied to the obstacle's verts as given at pdc_add_obstacle.
+ * Within a step the obstacle moves linearly from its current position. */
+pdc_status pdc_set_obstacle_transform(pdc_handle h, int32_t id, const float *m4x4);
+
+/* Pinned positions [npins][3] at the end of the next step (Dirichlet). */
+pdc_status pdc_set_pin_targets(pdc_handle h, const float *xyz, int32_t on_device);
+
+/* Overwrite / read the state x*, v* ([nv][3] each; v may be NULL on set to
+ * zero it).  The current positions must be free of intersections (Sec. 3:
+ * the barrier method starts from a feasible state). */
+pdc_status pdc_set_state(pdc_handle h, const float *x, const float *v, int32_t on_device);
+pdc_status pdc_get_state(pdc_handle h, float *x, float *v, int32_t on_device);
+
+/* Replace the library's basis by a caller-supplied one: U host [nv][r]
+ * float32 row-major (rows of pinned vertices are ignored and taken as 0),
+ * r >= r_reuse.  The reduced matrices U^T H U are recomputed from it
+ * (Eq. subspace_global with the basis actually used). */
+pdc_status pdc_set_basis(pdc_handle h, const float *U, int32_t r);
+
+/* Copy the basis in use (float32 [nv][r_warm]) and its reduced matrix
+ * U^T H U (float64 [r_warm][r_warm]) to host buffers (either may be NULL). */
+pdc_status pdc_get_basis(pdc_handle h, float *U, double *A0);
+
+/* Advance one time step (Alg. 1).  dt must equal params.dt (PDC_ERR_ARG
+ * otherwise: H and the basis depend on h).  On PDC_ERR_NUMERIC the state is
+ * left at x*, v*. */
+pdc_status pdc_step(pdc_handle h, double dt);
+
+/* Current cloth positions [nv][3]. */
+pdc_status pdc_get_positions(pdc_handle h, float *out, int32_t on_device);
+
+/* Statistics of the last step. */
+pdc_status pdc_get_stats(pdc_handle h, pdc_stats *out);
+
+/* Free everything owned by the handle (NULL is ignored). */
+void pdc_destroy(pdc_handle h);
+
+/* Last error message of the handle, or of the last failed pdc_create when
+ * h is NULL.  Never NULL. */
+const char *pdc_last_error(pdc_handle h);
+
+/* --------------------------------------------------------------------------
+ * Stage entry points.  Each runs exactly the kernels pdc_step uses for one
+ * stage, on caller data, so that every stage can be checked on its own.
+ * Collision positions cover all collision vertices (cloth, then obstacles).
+ * ------------------------------------------------------------------------ */
+
+/* Broad phase (the candidate set of the CCD of Sec. 4 / Alg. 1): all
+ * vertex-triangle pairs (v, t), v not in t, and edge-edge pairs sharing no
+ * vertex, not both kinematic, whose swept boxes over x0 -> x1 meet under
+ * lo_a <= fl32(hi_b + d_hat) and lo_b <= fl32(hi_a + d_hat) per axis.
+ * Output: vt [cap_vt][2] (v, t) sorted by (v, t); ee [cap_ee][4] vertex ids
+ * (a, b, c, d), a < b, c < d, sorted by edge ids.  Counts are returned even
+ * when they exceed the caps (then only cap entries are written).
+ * x0, x1: host [nvc][3], nvc = cloth + obstacle vertices. */
+pdc_status pdc_op_broadphase(pdc_handle h, const float *x0, const float *x1, int32_t *vt, int64_t cap_vt,
+                             int64_t *n_vt, int32_t *ee, int64_t cap_ee, int64_t *n_ee);
+
+/* Exact CCD (Sec. 4, Eq. intersect; Alg. 1 FullCCD) per pair: first t in
+ * [0,1] at which the primitives touch (distance <= eta_ccd at a root or
+ * critical point of the coplanarity cubic), 2 if none.  quads [np][4]
+ * vertex ids (VT: v,a,b,c; EE: a,b,c,d), kinds [np] 0 = VT, 1 = EE.  Host. */
+pdc_status pdc_op_ccd(pdc_handle h, const float *x0, const float *x1, const int32_t *quads,
+                      const int32_t *kinds, int64_t np, double *toi);
+
+/* Partial CCD (Sec. 4.1): active[i] = 1 when Q(lambda_s) <= d_hat*|p2^0 -
+ * p1^0| at some sample (the t=0 closest point plus the samples_vt /
+ * samples_ee pattern).  Host arrays as in pdc_op_ccd. */
+pdc_status pdc_op_partial_ccd(pdc_handle h, const float *x0, const float *x1, const int32_t *quads,
+                              const int32_t *kinds, int64_t np, int32_t *active);
+
+/* Collision springs (Sec. 5.1, A_i = B_i = Id) of the given active pairs
+ * with weights w [np]: per cloth vertex the weight sum cw [nv] and the
+ * force sum cf [nv][3] = sum_i w_i (y_ij - x_j), targets from the t=0
+ * closest points on x0 and the constraint (p2 - p1).n0 >= d_hat at x. */
+pdc_status pdc_op_contact(pdc_handle h, const float *x0, const float *x, const int32_t *quads,
+                          const int32_t *kinds, const float *w, int64_t np, float *cw, float *cf);
+
+/* PD residual r = b(x) - (H + diag(cw)) x of Eq. (global) with the local
+ * projections at x, over cloth vertices (0 on pinned rows); cw, cf as
+ * returned by pdc_op_contact (NULL = no contact).  Host arrays. */
+pdc_status pdc_op_residual(pdc_handle h, const float *x, const float *z, const float *cw, const float *cf,
+                           float *r);
+
+/* One global solve as run inside an LG iteration: residual at x, then
+ * `cycles` times {subspace correction in span(U[:, :r]) with the reduced
+ * matrix U^T (H + diag(cw)) U (Eq. subspace_collision / uu), `sweeps`
+ * Jacobi sweeps (Eq. high_frequency_residual)}; writes x_out = x + delta.
+ * r = 0 skips the correction.  Host arrays. */
+pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, const float *cw, const float *cf,
+                               int32_t r, int32_t cycles, int32_t sweeps, float *x_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDCLOTH_H */

@@ -89,14 +89,28 @@ static void closest_pt_tri(v3 p, v3 a, v3 b, v3 c, double w[3]) {
 }
 
 /* Closest points between segments [p1,q1], [p2,q2]: parameters s,t in [0,1].
- * Solved as a convex quadratic over the unit square: the unconstrained
- * minimiser if it is interior, else the best of the four boundary problems
- * (each a clamped 1-D projection). */
+ * Non-parallel segments: the unique minimiser of |p1(s) - p2(t)|^2 over the
+ * unit square, i.e. the unconstrained minimiser if it is interior, else the
+ * best of the four boundary problems (each a clamped 1-D projection).
+ * Parallel segments (a e - b^2 <= 1e-6 a e) have a whole set of closest
+ * pairs; the sample point is then taken at s = the midpoint of the clamped
+ * projections of p2 and q2 onto segment 1, t = the clamped projection of
+ * p1(s) onto segment 2 (a tie-break the paper does not fix).  Zero-length
+ * segments project the other segment's start. */
 static void closest_seg_seg(v3 p1, v3 q1, v3 p2, v3 q2, double *s_out, double *t_out) {
     v3 d1 = sub(q1, p1), d2 = sub(q2, p2), r = sub(p1, p2);
     double a = dot(d1, d1), e = dot(d2, d2), b = dot(d1, d2), c = dot(d1, r), f = dot(d2, r);
+    if (a <= 0 && e <= 0) { *s_out = 0; *t_out = 0; return; }
+    if (a <= 0) { *s_out = 0; *t_out = clamp01(f / e); return; }
+    if (e <= 0) { *t_out = 0; *s_out = clamp01(-c / a); return; }
     double den = a * e - b * b;
-    if (a > 0 && e > 0 && den > 1e-14 * a * e) {
+    if (den <= 1e-6 * a * e) {
+        double s = 0.5 * (clamp01(-c / a) + clamp01((b - c) / a));
+        *s_out = s;
+        *t_out = clamp01((b * s + f) / e);
+        return;
+    }
+    {
         double s = (b * f - c * e) / den, t = (a * f - b * c) / den;
         if (s >= 0 && s <= 1 && t >= 0 && t <= 1) { *s_out = s; *t_out = t; return; }
     }

@@ -519,8 +519,10 @@ class Oracle:
             tmin = float(tt.min()) if len(tt) else 2.0
             return qd, kd, ky, new_state, tmin
 
-        # the first inner loop uses the candidates of the initial full CCD;
-        # with no inner iteration x^+ = x^- and nothing can collide (t = 2)
+        # the first inner loop uses the candidates of the initial full CCD; the
+        # first outer pass always ends with a full CCD (pinned rows of x^+ sit
+        # at their targets even if no inner iteration ran); later passes
+        # without an inner iteration leave x^+ unchanged and reuse the result
         t_toi = 2.0
         x_outer_prev = xm.copy()
         for o in range(p.max_outer):
@@ -553,7 +555,7 @@ class Oracle:
                 x = xn
                 if not p.fixed_iters and p.tol_rel_residual <= 0 and dx <= p.tol_inner * L:
                     break
-            if inner_done > 0:
+            if inner_done > 0 or o == 0:
                 quads, kinds, keys, state, t_toi = full_ccd(x)
             dxo = np.max(np.abs(x - x_outer_prev))
             x_outer_prev = x.copy()

@@ -1,0 +1,1307 @@
+// C-ABI of the pdcloth library: context set-up (rest model of Sec. 3,
+// basis of Sec. 5/7) and the per-step pipeline of Alg. 1 / Sec. 7.
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <unordered_map>
+
+#include "pdc_collide.cuh"
+#include "pdc_subspace.cuh"
+
+namespace pdc {
+void set_chol_smem_limits();
+
+namespace {
+
+__global__ void k_f3_to_f4(int n, const float *__restrict__ a, float4 *__restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float4(a[3 * i], a[3 * i + 1], a[3 * i + 2], 0.f);
+}
+__global__ void k_f4_to_f3(int n, const float4 *__restrict__ a, float *__restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        float4 v = a[i];
+        b[3 * i] = v.x;
+        b[3 * i + 1] = v.y;
+        b[3 * i + 2] = v.z;
+    }
+}
+// x_i <- rest_i transformed by the 3x4 affine m (row major)
+__global__ void k_transform(int n, const float4 *__restrict__ rest, const float *__restrict__ m, float4 *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 p = rest[i];
+    out[i] = make_float4(m[0] * p.x + m[1] * p.y + m[2] * p.z + m[3], m[4] * p.x + m[5] * p.y + m[6] * p.z + m[7],
+                         m[8] * p.x + m[9] * p.y + m[10] * p.z + m[11], 0.f);
+}
+// s = alpha * t if an impact was found (t <= 1), else 1
+__global__ void k_step_fraction(const unsigned long long *toi_bits, double alpha, double *s_out, double *t_out) {
+    double t = __longlong_as_double((long long)*toi_bits);
+    *t_out = t;
+    *s_out = (t <= 1.0) ? alpha * t : 1.0;
+}
+// final state: x = xm + s (xp - xm) (or xp), v = (x - x*)/h for cloth vertices
+__global__ void k_finish(int nv, int n, const float4 *__restrict__ xm, const float4 *__restrict__ xp,
+                         const double *s_frac, int use_lerp, float inv_h, float4 *__restrict__ xs, float4 *__restrict__ vs) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    float3 xn;
+    if (use_lerp) {
+        float s = (float)*s_frac;
+        float3 a = f3(xm[i]), b = f3(xp[i]);
+        xn = a + s * (b - a);
+    } else {
+        xn = f3(xp[i]);
+    }
+    if (i < n) vs[i] = f4(inv_h * (xn - f3(xs[i])));
+    xs[i] = f4(xn);
+}
+__global__ void k_maxdiff(int n, const float4 *__restrict__ a, const float4 *__restrict__ b, unsigned int *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.f;
+    if (i < n) {
+        float4 p = a[i], q = b[i];
+        m = fmaxf(fabsf(p.x - q.x), fmaxf(fabsf(p.y - q.y), fabsf(p.z - q.z)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+__global__ void k_finite(int n, const float4 *__restrict__ a, int *bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        float4 p = a[i];
+        if (!isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z)) atomicOr(bad, 1);
+    }
+}
+
+inline int nb(long long n) { return (int)((n + 255) / 256); }
+inline float bits_to_float(unsigned int u) {
+    float f;
+    std::memcpy(&f, &u, sizeof(f));
+    return f;
+}
+
+struct Obstacle {
+    std::vector<float> V;  // rest verts
+    std::vector<int> T;
+    int off;               // first collision-vertex id
+};
+
+}  // namespace
+}  // namespace pdc
+
+using namespace pdc;
+
+struct pdc_ctx {
+    std::string err;
+    cudaStream_t s = nullptr;
+    pdc_params P;
+    pdc_material M;
+    int n = 0, m = 0, nh = 0, npins = 0;
+    std::vector<float> X;
+    std::vector<int> T, pins;
+    std::vector<unsigned char> freev;
+    double L = 1.0, k_ndb = 1.0, omega = 1.0;
+    float dhat = 1e-3f;
+    // rest model
+    DevBuf<int4> tri, hin;
+    DevBuf<float4> tri_g, hin_K, hin_srest;
+    DevBuf<float> tri_w, hin_w, hin_slen, mh2, hdiag, ell_val;
+    DevBuf<int> vt_off, vt_list, vh_off, vh_list, ell_col, pins_d;
+    DevBuf<unsigned char> is_free;
+    int ell_w = 0;
+    // pins
+    DevBuf<float4> pin_tgt;
+    // state (collision-vertex arrays: cloth first, obstacles after)
+    DevBuf<float4> Xs, Vs, Z, Xp, Xm, Xbak, Vbak, Xprev;
+    DevBuf<float4> R, RL, D0, D1, CF;
+    DevBuf<float> CW;
+    DevBuf<float> stage3;  // staging for float[3] transfers
+    // obstacles
+    std::vector<Obstacle> obs;
+    DevBuf<float4> obs_rest, obs_tgt;  // [nv_obs]
+    int nv_all = 0, nt_all = 0, ne_all = 0;
+    bool topo_dirty = true;
+    std::vector<int> ctri_h, cedge_h;
+    DevBuf<int4> ctri;
+    DevBuf<int2> cedge;
+    DevBuf<unsigned char> vfixed;
+    BroadPhase bp;
+    DevBuf<ActivePair> act;
+    int cap_act = 0;
+    DevBuf<int> contact_list;
+    // subspace
+    int r_warm = 0, r_reuse = 0;
+    DevBuf<float> U32, A0inv32, proj_partial, qbuf, dA;
+    DevBuf<__nv_bfloat16> U16;
+    DevBuf<double> A0, A0inv, gbuf;
+    DevBuf<int> sflag;
+    // scalars
+    DevBuf<Scalars> sc;
+    Scalars *hsc = nullptr;
+    DevBuf<double> sfrac, ttoi;
+    DevBuf<unsigned long long> toi_bits;
+    DevBuf<int> n_act_d, n_cv_d, bad_d;
+    DevBuf<unsigned int> umax_d;
+    pdc_stats st;
+    bool stepped = false;
+
+    ~pdc_ctx() {
+        if (hsc) cudaFreeHost(hsc);
+    }
+
+    ClothView cloth() const {
+        ClothView c;
+        c.n = n;
+        c.m = m;
+        c.nh = nh;
+        c.tri = tri;
+        c.tri_g = tri_g;
+        c.tri_w = tri_w;
+        c.hin = hin;
+        c.hin_K = hin_K;
+        c.hin_w = hin_w;
+        c.hin_slen = hin_slen;
+        c.hin_srest = hin_srest;
+        c.vt_off = vt_off;
+        c.vt_list = vt_list;
+        c.vh_off = vh_off;
+        c.vh_list = vh_list;
+        c.mh2 = mh2;
+        c.hdiag = hdiag;
+        c.is_free = is_free;
+        c.ell_w = ell_w;
+        c.ell_col = ell_col;
+        c.ell_val = ell_val;
+        return c;
+    }
+    CollView coll() const {
+        CollView v;
+        v.nv = nv_all;
+        v.nc = n;
+        v.nt = nt_all;
+        v.ne = ne_all;
+        v.tri = ctri;
+        v.edge = cedge;
+        v.vfixed = vfixed;
+        return v;
+    }
+    SubspaceView sub(int r_nc, int r_c) const {
+        SubspaceView S;
+        S.n = n;
+        S.ld = r_warm;
+        S.r_nc = r_nc;
+        S.r_c = r_c;
+        S.U32 = U32;
+        S.U16 = U16;
+        S.A0 = A0;
+        S.A0inv = A0inv;
+        S.A0inv32 = A0inv32;
+        S.precision = P.precision;
+        return S;
+    }
+    SubspaceWork work() {
+        SubspaceWork W;
+        W.partial = proj_partial;
+        W.g = gbuf;
+        W.q = qbuf;
+        W.dA = dA;
+        W.flag = sflag;
+        return W;
+    }
+    CollParams cparams() const {
+        CollParams C;
+        C.dhat = dhat;
+        C.eta = P.eta_ccd;
+        C.k_ndb = (float)k_ndb;
+        C.K_ndb = (float)P.K_ndb;
+        C.a_max = P.a_max;
+        C.samples_vt = P.samples_vt;
+        C.samples_ee = P.samples_ee;
+        return C;
+    }
+
+    void setup(const pdc_mesh_desc *mesh);
+    void setup_basis();
+    void install_basis(const std::vector<float> &U, int r);
+    void ensure_topology();
+    void read_scalars() {
+        sc.download(hsc, 1, s);
+        PDC_CK(cudaStreamSynchronize(s));
+    }
+    void lg_iteration(bool contacts, bool check_rel, double rho0, bool &converged, int r_nc, int r_c, int cycles,
+                      int sweeps);
+    void full_ccd(const float4 *x0, const float4 *x1, bool merge);
+    void step();
+};
+
+// ============================================================================ set-up
+void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
+    n = mesh->nv;
+    m = mesh->nt;
+    npins = mesh->npins;
+    X.assign(mesh->verts, mesh->verts + 3 * (size_t)n);
+    T.assign(mesh->tris, mesh->tris + 3 * (size_t)m);
+    pins.assign(mesh->pins, mesh->pins + npins);
+    freev.assign(n, 1);
+    for (int p : pins) {
+        if (p < 0 || p >= n) throw Error(PDC_ERR_ARG, "pin index out of range");
+        freev[p] = 0;
+    }
+    for (int t = 0; t < m; ++t)
+        for (int k = 0; k < 3; ++k)
+            if (T[3 * t + k] < 0 || T[3 * t + k] >= n) throw Error(PDC_ERR_ARG, "triangle index out of range");
+    const double h = P.dt;
+    auto Xd = [&](int i, int k) { return (double)X[3 * (size_t)i + k]; };
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], Xd(i, k));
+            hi[k] = std::max(hi[k], Xd(i, k));
+        }
+    L = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                  (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    if (!(L > 0)) L = 1.0;
+
+    // ---- triangles: rest frame, Dm^-1 rows, area, weight, lumped mass
+    std::vector<int4> tri_h(m);
+    std::vector<float4> trig_h(m);
+    std::vector<float> triw_h(m);
+    std::vector<double> area(m), mass(n, 0.0);
+    std::vector<std::array<double, 6>> G(m);  // g0, g1, g2 (2 each)
+    for (int t = 0; t < m; ++t) {
+        int a = T[3 * t], b = T[3 * t + 1], c = T[3 * t + 2];
+        double e1[3], e2[3];
+        for (int k = 0; k < 3; ++k) {
+            e1[k] = Xd(b, k) - Xd(a, k);
+            e2[k] = Xd(c, k) - Xd(a, k);
+        }
+        double nr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double nn = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+        double l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+        if (!(nn > 1e-14 * L * L) || !(l1 > 0)) throw Error(PDC_ERR_DEGENERATE, "zero-area rest triangle " + std::to_string(t));
+        area[t] = 0.5 * nn;
+        // orthonormal frame (t1 along e1, t2 = n x t1 / |..|) -> Dm = [[|e1|, e2.t1], [0, e2.t2]]
+        double t1[3] = {e1[0] / l1, e1[1] / l1, e1[2] / l1};
+        double e2t1 = e2[0] * t1[0] + e2[1] * t1[1] + e2[2] * t1[2];
+        double e2t2 = nn / l1;  // |e1 x e2| / |e1|
+        // Dm^-1 = [[1/l1, -e2t1/(l1 e2t2)], [0, 1/e2t2]]
+        double i00 = 1.0 / l1, i01 = -e2t1 / (l1 * e2t2), i10 = 0.0, i11 = 1.0 / e2t2;
+        // g1 = row 0, g2 = row 1, g0 = -g1 - g2
+        G[t] = {-(i00 + i10), -(i01 + i11), i00, i01, i10, i11};
+        tri_h[t] = make_int4(a, b, c, 0);
+        trig_h[t] = make_float4((float)i00, (float)i01, (float)i10, (float)i11);
+        triw_h[t] = (float)(M.k_stretch * area[t]);
+        for (int k = 0; k < 3; ++k) mass[T[3 * t + k]] += M.density * area[t] / 3.0;
+    }
+
+    // ---- edges -> hinges
+    std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> emap;  // edge -> (tri, opposite)
+    for (int t = 0; t < m; ++t)
+        for (int k = 0; k < 3; ++k) {
+            int u = T[3 * t + k], v = T[3 * t + (k + 1) % 3], o = T[3 * t + (k + 2) % 3];
+            emap[{std::min(u, v), std::max(u, v)}].push_back({t, o});
+        }
+    std::vector<int4> hin_h;
+    std::vector<float4> hK_h, hsr_h;
+    std::vector<float> hw_h, hsl_h;
+    std::vector<std::array<double, 4>> Kd;
+    std::vector<double> wd;
+    for (auto &kv : emap) {
+        if (kv.second.size() > 2) throw Error(PDC_ERR_DEGENERATE, "edge shared by more than two triangles");
+        if (kv.second.size() != 2) continue;
+        int x0 = kv.first.first, x1 = kv.first.second, x2 = kv.second[0].second, x3 = kv.second[1].second;
+        auto cotv = [&](int o, int p, int q) {  // cot of the angle at o between (p - o) and (q - o)
+            double u[3], w[3];
+            for (int k = 0; k < 3; ++k) {
+                u[k] = Xd(p, k) - Xd(o, k);
+                w[k] = Xd(q, k) - Xd(o, k);
+            }
+            double d = u[0] * w[0] + u[1] * w[1] + u[2] * w[2];
+            double cx = u[1] * w[2] - u[2] * w[1], cy = u[2] * w[0] - u[0] * w[2], cz = u[0] * w[1] - u[1] * w[0];
+            return d / std::sqrt(cx * cx + cy * cy + cz * cz);
+        };
+        double cA0 = cotv(x0, x1, x2), cA1 = cotv(x1, x0, x2), cB0 = cotv(x0, x1, x3), cB1 = cotv(x1, x0, x3);
+        std::array<double, 4> K = {cA1 + cB1, cA0 + cB0, -cA0 - cA1, -cB0 - cB1};
+        double w = 3.0 * M.k_bend / (area[kv.second[0].first] + area[kv.second[1].first]);
+        int ids[4] = {x0, x1, x2, x3};
+        double s[3] = {0, 0, 0};
+        for (int j = 0; j < 4; ++j)
+            for (int k = 0; k < 3; ++k) s[k] += K[j] * Xd(ids[j], k);
+        double sl = std::sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+        hin_h.push_back(make_int4(x0, x1, x2, x3));
+        hK_h.push_back(make_float4((float)K[0], (float)K[1], (float)K[2], (float)K[3]));
+        hw_h.push_back((float)w);
+        hsl_h.push_back((float)sl);
+        hsr_h.push_back(make_float4((float)s[0], (float)s[1], (float)s[2], 0.f));
+        Kd.push_back(K);
+        wd.push_back(w);
+    }
+    nh = (int)hin_h.size();
+
+    // ---- H = M/h^2 + sum_t w_t G G^T + sum_h w_h K K^T  (scalar, per vertex pair)
+    std::vector<std::unordered_map<int, double>> rows(n);
+    for (int i = 0; i < n; ++i) rows[i][i] += mass[i] / (h * h);
+    for (int t = 0; t < m; ++t) {
+        double w = M.k_stretch * area[t];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double v = w * (G[t][2 * a] * G[t][2 * b] + G[t][2 * a + 1] * G[t][2 * b + 1]);
+                rows[T[3 * t + a]][T[3 * t + b]] += v;
+            }
+    }
+    for (int hh = 0; hh < nh; ++hh) {
+        int ids[4] = {hin_h[hh].x, hin_h[hh].y, hin_h[hh].z, hin_h[hh].w};
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) rows[ids[a]][ids[b]] += wd[hh] * Kd[hh][a] * Kd[hh][b];
+    }
+    std::vector<float> hdiag_h(n), mh2_h(n);
+    ell_w = 0;
+    for (int i = 0; i < n; ++i) {
+        hdiag_h[i] = (float)rows[i][i];
+        mh2_h[i] = (float)(mass[i] / (h * h));
+        if (!freev[i]) continue;
+        int cnt = 0;
+        for (auto &kv : rows[i])
+            if (kv.first != i && freev[kv.first]) ++cnt;
+        ell_w = std::max(ell_w, cnt);
+    }
+    std::vector<int> ecol((size_t)ell_w * n);
+    std::vector<float> evalv((size_t)ell_w * n, 0.f);
+    for (int i = 0; i < n; ++i) {
+        std::vector<std::pair<int, double>> ent;
+        if (freev[i])
+            for (auto &kv : rows[i])
+                if (kv.first != i && freev[kv.first]) ent.push_back(kv);
+        std::sort(ent.begin(), ent.end());
+        for (int k = 0; k < ell_w; ++k) {
+            ecol[(size_t)k * n + i] = k < (int)ent.size() ? ent[k].first : i;
+            evalv[(size_t)k * n + i] = k < (int)ent.size() ? (float)ent[k].second : 0.f;
+        }
+    }
+    double dsum = 0;
+    int nf = 0;
+    for (int i = 0; i < n; ++i)
+        if (freev[i]) {
+            dsum += rows[i][i];
+            ++nf;
+        }
+    k_ndb = P.k_ndb_scale * (nf ? dsum / nf : 1.0);
+
+    // Jacobi damping: power iteration for the largest eigenvalue of D^-1 H
+    if (P.jacobi_omega > 0) {
+        omega = P.jacobi_omega;
+    } else {
+        std::vector<double> v(n), w(n);
+        for (int i = 0; i < n; ++i) v[i] = freev[i] ? 1.0 + 0.37 * std::sin(1.3 * i) : 0.0;
+        double lam = 1.0;
+        for (int it = 0; it < 60; ++it) {
+            double nrm = 0;
+            for (int i = 0; i < n; ++i) {
+                if (!freev[i]) {
+                    w[i] = 0;
+                    continue;
+                }
+                double acc = 0;
+                for (auto &kv : rows[i])
+                    if (freev[kv.first]) acc += kv.second * v[kv.first];
+                w[i] = acc / rows[i][i];
+                nrm += w[i] * w[i];
+            }
+            nrm = std::sqrt(nrm);
+            double vn = 0;
+            for (int i = 0; i < n; ++i) vn += v[i] * v[i];
+            lam = nrm / std::max(std::sqrt(vn), 1e-300);
+            for (int i = 0; i < n; ++i) v[i] = w[i] / std::max(nrm, 1e-300);
+        }
+        omega = std::min(1.0, 1.8 / (lam * 1.05));
+    }
+    // gap
+    if (P.d_hat > 0) {
+        dhat = (float)P.d_hat;
+    } else {
+        double es = 0;
+        for (auto &kv : emap) {
+            double d2 = 0;
+            for (int k = 0; k < 3; ++k) {
+                double dd = Xd(kv.first.first, k) - Xd(kv.first.second, k);
+                d2 += dd * dd;
+            }
+            es += std::sqrt(d2);
+        }
+        double me = emap.empty() ? 1.0 : es / emap.size();
+        dhat = (float)std::min(1e-3, 0.2 * me);
+    }
+
+    // ---- incidence lists
+    std::vector<int> vto(n + 1, 0), vho(n + 1, 0);
+    for (int t = 0; t < m; ++t)
+        for (int k = 0; k < 3; ++k) vto[T[3 * t + k] + 1]++;
+    for (int hh = 0; hh < nh; ++hh) {
+        vho[hin_h[hh].x + 1]++;
+        vho[hin_h[hh].y + 1]++;
+        vho[hin_h[hh].z + 1]++;
+        vho[hin_h[hh].w + 1]++;
+    }
+    for (int i = 0; i < n; ++i) {
+        vto[i + 1] += vto[i];
+        vho[i + 1] += vho[i];
+    }
+    std::vector<int> vtl(vto[n]), vhl(vho[n]), ft(vto.begin(), vto.end() - 1), fh(vho.begin(), vho.end() - 1);
+    for (int t = 0; t < m; ++t)
+        for (int k = 0; k < 3; ++k) vtl[ft[T[3 * t + k]]++] = (t << 2) | k;
+    for (int hh = 0; hh < nh; ++hh) {
+        int ids[4] = {hin_h[hh].x, hin_h[hh].y, hin_h[hh].z, hin_h[hh].w};
+        for (int k = 0; k < 4; ++k) vhl[fh[ids[k]]++] = (hh << 2) | k;
+    }
+
+    // ---- upload
+    tri.upload(tri_h, s);
+    tri_g.upload(trig_h, s);
+    tri_w.upload(triw_h, s);
+    hin.upload(hin_h, s);
+    hin_K.upload(hK_h, s);
+    hin_w.upload(hw_h, s);
+    hin_slen.upload(hsl_h, s);
+    hin_srest.upload(hsr_h, s);
+    vt_off.upload(vto, s);
+    vt_list.upload(vtl, s);
+    vh_off.upload(vho, s);
+    vh_list.upload(vhl, s);
+    mh2.upload(mh2_h, s);
+    hdiag.upload(hdiag_h, s);
+    is_free.upload(freev, s);
+    ell_col.upload(ecol, s);
+    ell_val.upload(evalv, s);
+    pins_d.upload(pins, s);
+    std::vector<float4> pt(npins);
+    for (int k = 0; k < npins; ++k) pt[k] = make_float4(X[3 * pins[k]], X[3 * pins[k] + 1], X[3 * pins[k] + 2], 0.f);
+    pin_tgt.upload(pt, s);
+    if (npins == 0) pin_tgt.alloc(1);
+
+    R.alloc(n);
+    RL.alloc(n);
+    D0.alloc(n);
+    D1.alloc(n);
+    CF.alloc(n);
+    CW.alloc(n);
+    Z.alloc(n);
+    Vs.alloc(n);
+    Vs.zero(s);
+    stage3.alloc(3 * (size_t)std::max(n, 1));
+    sc.alloc(1);
+    PDC_CK(cudaHostAlloc((void **)&hsc, sizeof(Scalars), cudaHostAllocDefault));
+    sfrac.alloc(1);
+    ttoi.alloc(1);
+    toi_bits.alloc(1);
+    n_act_d.alloc(1);
+    n_cv_d.alloc(1);
+    bad_d.alloc(1);
+    umax_d.alloc(1);
+    sflag.alloc(1);
+    n_cv_d.zero(s);
+    n_act_d.zero(s);
+    contact_list.alloc(std::max(n, 1));
+    // cloth-only collision arrays until obstacles are added
+    ensure_topology();
+    std::vector<float4> x4(n);
+    for (int i = 0; i < n; ++i) x4[i] = make_float4(X[3 * i], X[3 * i + 1], X[3 * i + 2], 0.f);
+    PDC_CK(cudaMemcpyAsync(Xs.p, x4.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s));
+    PDC_CK(cudaStreamSynchronize(s));
+}
+
+void pdc_ctx::install_basis(const std::vector<float> &U, int r) {
+    r_warm = r;
+    r_reuse = std::min(std::max(P.r_reuse, 0), r);
+    if (r_reuse > 128) throw Error(PDC_ERR_ARG, "r_reuse must be <= 128");
+    if (r > 1024) throw Error(PDC_ERR_ARG, "basis size must be <= 1024");
+    std::vector<float> Uz(U);
+    for (int i = 0; i < n; ++i)
+        if (!freev[i])
+            for (int j = 0; j < r; ++j) Uz[(size_t)i * r + j] = 0.f;
+    if (P.precision == 1) {
+        // round to BF16; the reduced matrix is formed from the rounded basis
+        std::vector<__nv_bfloat16> ub(Uz.size());
+        for (size_t k = 0; k < Uz.size(); ++k) {
+            ub[k] = __float2bfloat16_rn(Uz[k]);
+            Uz[k] = __bfloat162float(ub[k]);
+        }
+        U16.upload(ub, s);
+    }
+    U32.upload(Uz, s);
+    std::vector<double> A0h;
+    reduced_matrix(s, cloth(), U32, r, A0h);
+    std::vector<double> Ainv;
+    spd_inverse(A0h, r, Ainv);
+    A0.upload(A0h, s);
+    A0inv.upload(Ainv, s);
+    std::vector<float> Ainv32(Ainv.begin(), Ainv.end());
+    A0inv32.upload(Ainv32, s);
+    proj_partial.alloc((size_t)PROJ_BLOCKS * r * 3);
+    gbuf.alloc((size_t)r * 3);
+    qbuf.alloc((size_t)r * 3);
+    dA.alloc((size_t)std::max(r_reuse * r_reuse, 1));
+    PDC_CK(cudaStreamSynchronize(s));
+}
+
+void pdc_ctx::setup_basis() {
+    int r = std::min(P.r_warm, (int)std::count(freev.begin(), freev.end(), 1));
+    if (r <= 0) {
+        r_warm = r_reuse = 0;
+        return;
+    }
+    std::vector<float> U;
+    std::vector<double> ritz;
+    build_basis(s, cloth(), r, std::max(P.eig_iters, 0), P.seed, U, ritz);
+    install_basis(U, r);
+}
+
+void pdc_ctx::ensure_topology() {
+    if (!topo_dirty) return;
+    int nvo = 0, nto = 0;
+    for (auto &o : obs) {
+        nvo += (int)o.V.size() / 3;
+        nto += (int)o.T.size() / 3;
+    }
+    int nv_new = n + nvo;
+    // grow the collision-vertex state arrays, keeping the cloth part
+    auto grow = [&](DevBuf<float4> &b) {
+        DevBuf<float4> nbuf;
+        nbuf.alloc(nv_new);
+        nbuf.zero(s);
+        if (b.p) PDC_CK(cudaMemcpyAsync(nbuf.p, b.p, sizeof(float4) * std::min<size_t>(b.n, n), cudaMemcpyDeviceToDevice, s));
+        std::swap(b.p, nbuf.p);
+        std::swap(b.n, nbuf.n);
+    };
+    grow(Xs);
+    grow(Xp);
+    grow(Xm);
+    grow(Xbak);
+    grow(Xprev);
+    Vbak.alloc(n);
+    nv_all = nv_new;
+    // obstacle rest / current / target positions
+    std::vector<float4> orest;
+    for (auto &o : obs)
+        for (size_t k = 0; k < o.V.size() / 3; ++k) orest.push_back(make_float4(o.V[3 * k], o.V[3 * k + 1], o.V[3 * k + 2], 0.f));
+    if (!orest.empty()) {
+        obs_rest.upload(orest, s);
+        if (obs_tgt.n != orest.size()) obs_tgt.upload(orest, s);
+        PDC_CK(cudaMemcpyAsync(Xs.p + n, orest.data(), sizeof(float4) * nvo, cudaMemcpyHostToDevice, s));
+    }
+    // triangles and edges of the collision set
+    ctri_h.clear();
+    std::vector<int4> ct;
+    for (int t = 0; t < m; ++t) ct.push_back(make_int4(T[3 * t], T[3 * t + 1], T[3 * t + 2], 0));
+    for (auto &o : obs)
+        for (size_t t = 0; t < o.T.size() / 3; ++t)
+            ct.push_back(make_int4(o.T[3 * t] + o.off, o.T[3 * t + 1] + o.off, o.T[3 * t + 2] + o.off, 0));
+    nt_all = (int)ct.size();
+    std::vector<std::pair<int, int>> ed;
+    ed.reserve(ct.size() * 3);
+    for (auto &q : ct) {
+        int v[3] = {q.x, q.y, q.z};
+        for (int k = 0; k < 3; ++k) ed.push_back({std::min(v[k], v[(k + 1) % 3]), std::max(v[k], v[(k + 1) % 3])});
+    }
+    std::sort(ed.begin(), ed.end());
+    ed.erase(std::unique(ed.begin(), ed.end()), ed.end());
+    std::vector<int2> ce(ed.size());
+    for (size_t k = 0; k < ed.size(); ++k) ce[k] = make_int2(ed[k].first, ed[k].second);
+    ne_all = (int)ce.size();
+    ctri.upload(ct, s);
+    cedge.upload(ce, s);
+    std::vector<unsigned char> vf(nv_all, 1);
+    for (int i = 0; i < n; ++i) vf[i] = freev[i] ? 0 : 1;
+    vfixed.upload(vf, s);
+    long long cvt = std::max<long long>(1024, 16LL * nv_all), cee = std::max<long long>(1024, 24LL * ne_all);
+    long long cent = std::max<long long>(4096, 8LL * (nt_all + ne_all));
+    bp.reserve(coll(), cvt, cee, cent);
+    cap_act = (int)std::max<long long>(1024, 4LL * nv_all);
+    act.alloc(cap_act);
+    PDC_CK(cudaStreamSynchronize(s));
+    topo_dirty = false;
+}
+
+// ============================================================================ the step (Alg. 1)
+// One LG iteration: local projections + residual at the iterate Xp[0:n],
+// then `cycles` x {subspace correction, `sweeps` Jacobi sweeps}, Xp += delta,
+// then (with contacts) partial CCD on (Xm, Xp).
+void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &converged, int r_nc, int r_c, int cycles,
+                           int sweeps) {
+    ClothView c = cloth();
+    converged = false;
+    PDC_CK(cudaMemsetAsync(&sc.p->rsq, 0, sizeof(double), s));
+    PDC_CK(cudaMemsetAsync(&sc.p->dxmax, 0, sizeof(unsigned int), s));
+    const float *cw = nullptr;
+    const float4 *cf = nullptr;
+    if (contacts) {
+        CW.zero(s);
+        CF.zero(s);
+        launch_contact(s, coll(), act, n_act_d, cap_act, Xp, dhat, CW, CF);
+        launch_contact_list(s, n, CW, contact_list, n_cv_d);
+        cw = CW;
+        cf = CF;
+    } else {
+        n_cv_d.zero(s);
+    }
+    launch_residual(s, c, Xp, Z, cw, cf, R, sc, nullptr, 0);
+    if (check_rel) {
+        read_scalars();
+        double rho = std::sqrt(hsc->rsq);
+        st.rel_residual = rho / std::max(rho0, 1e-300);
+        if (rho <= P.tol_rel_residual * rho0) {
+            converged = true;
+            return;
+        }
+    }
+    SubspaceView S = sub(r_nc, r_c);
+    SubspaceWork W = work();
+    float4 *din = D0, *dout = D1;
+    bool have_delta = false;
+    for (int cyc = 0; cyc < cycles; ++cyc) {
+        const float4 *rl = R;
+        if (have_delta) {
+            launch_linear_residual(s, c, cw, R, din, RL);
+            rl = RL;
+        }
+        if (r_warm > 0 && (r_nc > 0 || r_c > 0)) {
+            launch_project(s, S, rl, n_cv_d, W);
+            if (contacts && r_c > 0) launch_syrk(s, S, contact_list, n_cv_d, cw, W);
+            launch_reduced_solve(s, S, n_cv_d, W);
+            launch_lift(s, S, n_cv_d, W, have_delta ? din : nullptr, dout);
+            std::swap(din, dout);
+            have_delta = true;
+        }
+        if (!have_delta) {
+            PDC_CK(cudaMemsetAsync(din, 0, sizeof(float4) * n, s));
+            have_delta = true;
+        }
+        for (int k = 0; k < sweeps; ++k) {
+            bool last = (cyc == cycles - 1) && (k == sweeps - 1);
+            launch_sweep(s, c, cw, R, din, dout, (float)omega, Xp, last ? Xp.p : nullptr, last ? sc.p : nullptr);
+            std::swap(din, dout);
+        }
+        if (sweeps == 0 && cyc == cycles - 1) {
+            // no sweep: apply the correction directly
+            launch_sweep(s, c, cw, R, din, dout, 0.f, Xp, Xp.p, sc.p);
+        }
+    }
+    if (contacts && P.collisions) {
+        launch_partial_ccd(s, coll(), bp, Xm, Xp, cparams(), act, cap_act, n_act_d, &sc.p->overflow);
+    }
+}
+
+void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {
+    bp.run(s, coll(), x0, x1, dhat, &sc.p->overflow);
+    unsigned long long inf = 0x7ff0000000000000ULL;  // +inf
+    PDC_CK(cudaMemcpyAsync(toi_bits.p, &inf, sizeof(inf), cudaMemcpyHostToDevice, s));
+    launch_full_ccd(s, coll(), bp, x0, x1, cparams(), merge, toi_bits);
+    k_step_fraction<<<1, 1, 0, s>>>(toi_bits, P.alpha_ls, sfrac, ttoi);
+    PDC_LAUNCH_CK();
+}
+
+void pdc_ctx::step() {
+    ensure_topology();
+    ClothView c = cloth();
+    const float h = (float)P.dt;
+    const bool fixed = P.fixed_iters != 0;
+    const bool relmode = P.tol_rel_residual > 0 && !fixed;
+    const int cycles = std::max(P.solve_cycles, 1), sweeps = std::max(P.jacobi_sweeps, 0);
+    st = pdc_stats();
+    st.t_toi = 2.0;
+    st.s_line_search = 1.0;
+    auto t0 = std::chrono::steady_clock::now();
+    PDC_CK(cudaMemcpyAsync(Xbak.p, Xs.p, sizeof(float4) * nv_all, cudaMemcpyDeviceToDevice, s));
+    PDC_CK(cudaMemcpyAsync(Vbak.p, Vs.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+    PDC_CK(cudaMemsetAsync(sc.p, 0, sizeof(Scalars), s));
+
+    // Eq. (z) and x <- z (Alg. 1); obstacles move to their targets in x^+
+    float3 g = make_float3((float)P.gravity[0], (float)P.gravity[1], (float)P.gravity[2]);
+    launch_prologue(s, n, Xs, Vs, pins_d, pin_tgt, npins, h, g, Z, Xp);
+    if (nv_all > n)
+        PDC_CK(cudaMemcpyAsync(Xp.p + n, obs_tgt.p, sizeof(float4) * (nv_all - n), cudaMemcpyDeviceToDevice, s));
+    // rho0 = residual at z (no collision springs)
+    PDC_CK(cudaMemsetAsync(&sc.p->rsq, 0, sizeof(double), s));
+    launch_residual(s, c, Xp, Z, nullptr, nullptr, R, sc, nullptr, 0);
+    read_scalars();
+    double rho0 = std::sqrt(hsc->rsq);
+    st.rho0 = rho0;
+    const double tolx_in = P.tol_inner * L, tolx_out = P.tol_outer * L;
+
+    // ---- warm start: LG iterations of I + Psi in span(U) + sweeps
+    for (int it = 0; it < P.warm_iters; ++it) {
+        bool conv = false;
+        lg_iteration(false, relmode, rho0, conv, r_warm, 0, cycles, sweeps);
+        if (conv) break;
+        st.warm_iters++;
+        if (!fixed && !relmode) {
+            read_scalars();
+            if (bits_to_float(hsc->dxmax) <= tolx_in) break;
+        }
+    }
+
+    bool use_lerp = false;
+    if (P.collisions) {
+        use_lerp = true;
+        // initial full CCD from x* to the warm start, filter -> x^- (Alg. 1)
+        full_ccd(Xs, Xp, false);
+        launch_lerp(s, nv_all, Xs, Xp, sfrac, Xm);
+        // the iterate restarts at x^- with pins at their targets
+        PDC_CK(cudaMemcpyAsync(Xp.p, Xm.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+        launch_set_pins(s, pins_d, npins, pin_tgt, Xp);
+        launch_collect_active(s, coll(), bp, Xm, cparams(), act, cap_act, n_act_d, &sc.p->overflow);
+        PDC_CK(cudaMemcpyAsync(Xprev.p, Xm.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+        unsigned long long none = 0x4000000000000000ULL;  // 2.0: no impact yet
+        PDC_CK(cudaMemcpyAsync(toi_bits.p, &none, sizeof(none), cudaMemcpyHostToDevice, s));
+        k_step_fraction<<<1, 1, 0, s>>>(toi_bits, P.alpha_ls, sfrac, ttoi);
+        PDC_LAUNCH_CK();
+        for (int o = 0; o < P.max_outer; ++o) {
+            st.outer_iters++;
+            int inner = 0;
+            for (int it = 0; it < P.max_inner; ++it) {
+                bool conv = false;
+                lg_iteration(true, relmode, rho0, conv, r_warm, r_reuse, cycles, sweeps);
+                if (conv) break;
+                ++inner;
+                st.inner_iters++;
+                if (!fixed && !relmode) {
+                    read_scalars();
+                    if (bits_to_float(hsc->dxmax) <= tolx_in) break;
+                }
+            }
+            if (inner > 0 || o == 0) {
+                full_ccd(Xm, Xp, true);
+                launch_collect_active(s, coll(), bp, Xm, cparams(), act, cap_act, n_act_d, &sc.p->overflow);
+            }
+            if (!fixed) {
+                umax_d.zero(s);
+                k_maxdiff<<<nb(n), 256, 0, s>>>(n, Xp, Xprev, umax_d);
+                PDC_LAUNCH_CK();
+                unsigned int um = 0;
+                umax_d.download(&um, 1, s);
+                PDC_CK(cudaStreamSynchronize(s));
+                PDC_CK(cudaMemcpyAsync(Xprev.p, Xp.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+                if (bits_to_float(um) <= tolx_out) break;
+            }
+        }
+    }
+    // exit line search and velocities (Alg. 1; v = (x - x*)/h)
+    k_finish<<<nb(nv_all), 256, 0, s>>>(nv_all, n, Xm, Xp, sfrac, use_lerp ? 1 : 0, 1.f / h, Xs, Vs);
+    PDC_LAUNCH_CK();
+    bad_d.zero(s);
+    k_finite<<<nb(n), 256, 0, s>>>(n, Xs, bad_d);
+    PDC_LAUNCH_CK();
+    int bad = 0, sflag_h = 0;
+    long long counts[2] = {0, 0};
+    int nact = 0, ncv = 0;
+    double tt = 2.0, sf = 1.0;
+    bad_d.download(&bad, 1, s);
+    sflag.download(&sflag_h, 1, s);
+    if (P.collisions) {
+        bp.cnt_vt_d[bp.cur].download(&counts[0], 1, s);
+        bp.cnt_ee_d[bp.cur].download(&counts[1], 1, s);
+    }
+    n_act_d.download(&nact, 1, s);
+    n_cv_d.download(&ncv, 1, s);
+    ttoi.download(&tt, 1, s);
+    sfrac.download(&sf, 1, s);
+    read_scalars();
+    st.n_candidates = counts[0] + counts[1];
+    st.n_active = nact;
+    st.n_contact_vertices = ncv;
+    if (P.collisions) {
+        st.t_toi = tt;
+        st.s_line_search = sf;
+    }
+    st.ms_step = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (hsc->overflow) {
+        // roll back; the caller (pdc_step) grows the buffers and retries
+        PDC_CK(cudaMemcpyAsync(Xs.p, Xbak.p, sizeof(float4) * nv_all, cudaMemcpyDeviceToDevice, s));
+        PDC_CK(cudaMemcpyAsync(Vs.p, Vbak.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+        PDC_CK(cudaStreamSynchronize(s));
+        throw Error(PDC_ERR_CAPACITY, "overflow:" + std::to_string(hsc->overflow));
+    }
+    if (bad) {
+        PDC_CK(cudaMemcpyAsync(Xs.p, Xbak.p, sizeof(float4) * nv_all, cudaMemcpyDeviceToDevice, s));
+        PDC_CK(cudaMemcpyAsync(Vs.p, Vbak.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+        PDC_CK(cudaStreamSynchronize(s));
+        throw Error(PDC_ERR_NUMERIC, "non-finite positions; state rolled back");
+    }
+    stepped = true;
+}
+
+// ============================================================================ C ABI
+static std::string g_create_error = "no error";
+
+#define API_BEGIN(h)                                                                                  \
+    if (!(h)) return PDC_ERR_ARG;                                                                      \
+    try {
+#define API_END(h)                                                                                    \
+    }                                                                                                  \
+    catch (const Error &e) {                                                                           \
+        (h)->err = e.what();                                                                           \
+        return e.code;                                                                                 \
+    }                                                                                                  \
+    catch (const std::exception &e) {                                                                  \
+        (h)->err = e.what();                                                                           \
+        return PDC_ERR_CUDA;                                                                           \
+    }                                                                                                  \
+    return PDC_OK;
+
+extern "C" {
+
+void pdc_default_params(pdc_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->dt = 1.0 / 200.0;
+    p->gravity[2] = -9.8;
+    p->k_ndb_scale = 1.0;
+    p->K_ndb = 2.0;
+    p->a_max = 20;
+    p->alpha_ls = 0.8;
+    p->d_hat = 0.0;
+    p->eta_ccd = 1e-9;
+    p->tol_outer = 1e-3;
+    p->tol_inner = 5e-2;
+    p->tol_rel_residual = 0.0;
+    p->max_outer = 4;
+    p->max_inner = 32;
+    p->warm_iters = 5;
+    p->jacobi_sweeps = 4;
+    p->jacobi_omega = 0.0;
+    p->solve_cycles = 1;
+    p->r_warm = 0;
+    p->r_reuse = 0;
+    p->precision = 0;
+    p->samples_vt = 3;
+    p->samples_ee = 4;
+    p->collisions = 1;
+    p->fixed_iters = 0;
+    p->eig_iters = 12;
+    p->seed = 12345;
+}
+
+pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const pdc_params *params, void *stream,
+                      pdc_handle *out) {
+    if (!out || !mesh || !mat || !params) {
+        g_create_error = "pdc_create: NULL argument";
+        return PDC_ERR_ARG;
+    }
+    *out = nullptr;
+    if (mesh->nv <= 0 || mesh->nt <= 0 || !mesh->verts || !mesh->tris || mesh->npins < 0 ||
+        (mesh->npins > 0 && !mesh->pins)) {
+        g_create_error = "pdc_create: empty or inconsistent mesh";
+        return PDC_ERR_ARG;
+    }
+    if (!(params->dt > 0) || params->precision < 0 || params->precision > 1 || params->r_warm < 0 ||
+        params->r_reuse < 0 || params->r_reuse > 128 || params->max_outer < 0 || params->max_inner < 0 ||
+        params->warm_iters < 0 || params->a_max < 0 || params->a_max > 127 ||
+        !(params->samples_vt == 0 || params->samples_vt == 1 || params->samples_vt == 3) ||
+        !(params->samples_ee == 0 || params->samples_ee == 1 || params->samples_ee == 4)) {
+        g_create_error = "pdc_create: invalid parameters";
+        return PDC_ERR_ARG;
+    }
+    std::unique_ptr<pdc_ctx> c(new pdc_ctx());
+    c->P = *params;
+    c->M = *mat;
+    c->s = (cudaStream_t)stream;
+    try {
+        set_chol_smem_limits();
+        c->setup(mesh);
+        c->setup_basis();
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.code;
+    } catch (const std::exception &e) {
+        g_create_error = e.what();
+        return PDC_ERR_CUDA;
+    }
+    *out = c.release();
+    return PDC_OK;
+}
+
+void pdc_destroy(pdc_handle h) {
+    if (!h) return;
+    if (h->s) cudaStreamSynchronize(h->s);
+    else cudaDeviceSynchronize();
+    delete h;
+}
+
+const char *pdc_last_error(pdc_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+pdc_status pdc_add_obstacle(pdc_handle h, const float *verts, int32_t nv, const int32_t *tris, int32_t nt,
+                            int32_t *out_id) {
+    API_BEGIN(h)
+    if (!verts || !tris || nv <= 0 || nt <= 0) throw Error(PDC_ERR_ARG, "pdc_add_obstacle: empty mesh");
+    if (h->stepped) throw Error(PDC_ERR_STATE, "pdc_add_obstacle: obstacles must be added before the first step");
+    for (int k = 0; k < 3 * nt; ++k)
+        if (tris[k] < 0 || tris[k] >= nv) throw Error(PDC_ERR_ARG, "pdc_add_obstacle: triangle index out of range");
+    Obstacle o;
+    o.V.assign(verts, verts + 3 * (size_t)nv);
+    o.T.assign(tris, tris + 3 * (size_t)nt);
+    o.off = h->nv_all;
+    for (auto &q : h->obs) (void)q;
+    int id = (int)h->obs.size();
+    h->obs.push_back(o);
+    h->topo_dirty = true;
+    h->obs_tgt.release();
+    h->ensure_topology();
+    if (out_id) *out_id = id;
+    API_END(h)
+}
+
+pdc_status pdc_set_obstacle_transform(pdc_handle h, int32_t id, const float *m4x4) {
+    API_BEGIN(h)
+    if (id < 0 || id >= (int)h->obs.size() || !m4x4) throw Error(PDC_ERR_ARG, "pdc_set_obstacle_transform: bad id");
+    h->ensure_topology();
+    const Obstacle &o = h->obs[id];
+    int base = o.off - h->n, cnt = (int)o.V.size() / 3;
+    DevBuf<float> md;
+    std::vector<float> m(m4x4, m4x4 + 12);
+    md.upload(m, h->s);
+    k_transform<<<nb(cnt), 256, 0, h->s>>>(cnt, h->obs_rest.p + base, md, h->obs_tgt.p + base);
+    PDC_LAUNCH_CK();
+    PDC_CK(cudaStreamSynchronize(h->s));
+    API_END(h)
+}
+
+pdc_status pdc_set_pin_targets(pdc_handle h, const float *xyz, int32_t on_device) {
+    API_BEGIN(h)
+    if (h->npins == 0) return PDC_OK;
+    if (!xyz) throw Error(PDC_ERR_ARG, "pdc_set_pin_targets: NULL");
+    if (on_device) {
+        k_f3_to_f4<<<nb(h->npins), 256, 0, h->s>>>(h->npins, xyz, h->pin_tgt);
+    } else {
+        PDC_CK(cudaMemcpyAsync(h->stage3.p, xyz, sizeof(float) * 3 * h->npins, cudaMemcpyHostToDevice, h->s));
+        k_f3_to_f4<<<nb(h->npins), 256, 0, h->s>>>(h->npins, h->stage3, h->pin_tgt);
+    }
+    PDC_LAUNCH_CK();
+    PDC_CK(cudaStreamSynchronize(h->s));
+    API_END(h)
+}
+
+pdc_status pdc_set_state(pdc_handle h, const float *x, const float *v, int32_t on_device) {
+    API_BEGIN(h)
+    if (!x) throw Error(PDC_ERR_ARG, "pdc_set_state: NULL positions");
+    int n = h->n;
+    const float *src = x;
+    if (!on_device) {
+        PDC_CK(cudaMemcpyAsync(h->stage3.p, x, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, h->s));
+        src = h->stage3;
+    }
+    k_f3_to_f4<<<nb(n), 256, 0, h->s>>>(n, src, h->Xs);
+    PDC_LAUNCH_CK();
+    if (v) {
+        const float *vs = v;
+        if (!on_device) {
+            PDC_CK(cudaMemcpyAsync(h->stage3.p, v, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, h->s));
+            vs = h->stage3;
+        }
+        k_f3_to_f4<<<nb(n), 256, 0, h->s>>>(n, vs, h->Vs);
+        PDC_LAUNCH_CK();
+    } else {
+        h->Vs.zero(h->s);
+    }
+    PDC_CK(cudaStreamSynchronize(h->s));
+    API_END(h)
+}
+
+static void get_f4(pdc_handle h, const float4 *src, float *out, int on_device) {
+    int n = h->n;
+    float *dst = on_device ? out : h->stage3.p;
+    k_f4_to_f3<<<nb(n), 256, 0, h->s>>>(n, src, dst);
+    PDC_LAUNCH_CK();
+    if (!on_device) PDC_CK(cudaMemcpyAsync(out, h->stage3.p, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->s));
+    PDC_CK(cudaStreamSynchronize(h->s));
+}
+
+pdc_status pdc_get_state(pdc_handle h, float *x, float *v, int32_t on_device) {
+    API_BEGIN(h)
+    if (x) get_f4(h, h->Xs, x, on_device);
+    if (v) get_f4(h, h->Vs, v, on_device);
+    API_END(h)
+}
+
+pdc_status pdc_get_positions(pdc_handle h, float *out, int32_t on_device) {
+    API_BEGIN(h)
+    if (!out) throw Error(PDC_ERR_ARG, "pdc_get_positions: NULL");
+    get_f4(h, h->Xs, out, on_device);
+    API_END(h)
+}
+
+pdc_status pdc_set_basis(pdc_handle h, const float *U, int32_t r) {
+    API_BEGIN(h)
+    if (!U || r <= 0) throw Error(PDC_ERR_ARG, "pdc_set_basis: empty basis");
+    std::vector<float> Uh(U, U + (size_t)h->n * r);
+    h->install_basis(Uh, r);
+    API_END(h)
+}
+
+pdc_status pdc_get_basis(pdc_handle h, float *U, double *A0) {
+    API_BEGIN(h)
+    if (h->r_warm == 0) throw Error(PDC_ERR_STATE, "pdc_get_basis: no basis");
+    if (U) h->U32.download(U, (size_t)h->n * h->r_warm, h->s);
+    if (A0) h->A0.download(A0, (size_t)h->r_warm * h->r_warm, h->s);
+    PDC_CK(cudaStreamSynchronize(h->s));
+    API_END(h)
+}
+
+pdc_status pdc_step(pdc_handle h, double dt) {
+    API_BEGIN(h)
+    if (std::fabs(dt - h->P.dt) > 1e-12 * h->P.dt) throw Error(PDC_ERR_ARG, "pdc_step: dt differs from params.dt");
+    int retries = 0;
+    for (;;) {
+        try {
+            h->step();
+            break;
+        } catch (const Error &e) {
+            if (e.code != PDC_ERR_CAPACITY || retries >= 6) throw;
+            int ovf = h->hsc->overflow;
+            ++retries;
+            BroadPhase &bp = h->bp;
+            CollView cv = h->coll();
+            long long cvt = bp.cap_vt, cee = bp.cap_ee, cent = bp.cap_ent;
+            if (ovf & OVF_VT) cvt *= 2;
+            if (ovf & OVF_EE) cee *= 2;
+            if (ovf & OVF_HASH) cent *= 2;
+            if (ovf & OVF_CELLS) bp.cell_scale *= 4.f;
+            if (ovf & (OVF_VT | OVF_EE | OVF_HASH)) bp.reserve(cv, cvt, cee, cent);
+            if (ovf & OVF_ACTIVE) {
+                h->cap_act *= 2;
+                h->act.alloc(h->cap_act);
+            }
+        }
+    }
+    h->st.overflow_retries = retries;
+    API_END(h)
+}
+
+pdc_status pdc_get_stats(pdc_handle h, pdc_stats *out) {
+    API_BEGIN(h)
+    if (!out) throw Error(PDC_ERR_ARG, "pdc_get_stats: NULL");
+    *out = h->st;
+    API_END(h)
+}
+
+// ----------------------------------------------------------------------------- stage entry points
+static void upload_f4(pdc_handle h, const float *x, int count, DevBuf<float4> &dst) {
+    DevBuf<float> tmp;
+    tmp.upload(x, 3 * (size_t)count, h->s);
+    dst.alloc(count);
+    k_f3_to_f4<<<nb(count), 256, 0, h->s>>>(count, tmp, dst);
+    PDC_LAUNCH_CK();
+    PDC_CK(cudaStreamSynchronize(h->s));
+}
+
+pdc_status pdc_op_broadphase(pdc_handle h, const float *x0, const float *x1, int32_t *vt, int64_t cap_vt,
+                             int64_t *n_vt, int32_t *ee, int64_t cap_ee, int64_t *n_ee) {
+    API_BEGIN(h)
+    if (!x0 || !x1) throw Error(PDC_ERR_ARG, "pdc_op_broadphase: NULL positions");
+    h->ensure_topology();
+    DevBuf<float4> a, b;
+    upload_f4(h, x0, h->nv_all, a);
+    upload_f4(h, x1, h->nv_all, b);
+    for (int tries = 0;; ++tries) {
+        PDC_CK(cudaMemsetAsync(h->sc.p, 0, sizeof(Scalars), h->s));
+        h->bp.run(h->s, h->coll(), a, b, h->dhat, &h->sc.p->overflow);
+        h->read_scalars();
+        int ovf = h->hsc->overflow;
+        if (!ovf) break;
+        if (tries > 6) throw Error(PDC_ERR_CAPACITY, "broad phase capacity");
+        BroadPhase &bp = h->bp;
+        long long cvt = bp.cap_vt * ((ovf & OVF_VT) ? 2 : 1), cee = bp.cap_ee * ((ovf & OVF_EE) ? 2 : 1),
+                  cent = bp.cap_ent * ((ovf & OVF_HASH) ? 2 : 1);
+        if (ovf & OVF_CELLS) bp.cell_scale *= 4.f;
+        bp.reserve(h->coll(), cvt, cee, cent);
+    }
+    BroadPhase &bp = h->bp;
+    long long nv_ = 0, ne_ = 0;
+    bp.cnt_vt_d[bp.cur].download(&nv_, 1, h->s);
+    bp.cnt_ee_d[bp.cur].download(&ne_, 1, h->s);
+    PDC_CK(cudaStreamSynchronize(h->s));
+    if (n_vt) *n_vt = nv_;
+    if (n_ee) *n_ee = ne_;
+    if (vt && cap_vt > 0) {
+        long long k = std::min<long long>(cap_vt, nv_);
+        if (k) PDC_CK(cudaMemcpyAsync(vt, bp.vt[bp.cur].p, sizeof(int2) * k, cudaMemcpyDeviceToHost, h->s));
+    }
+    if (ee && cap_ee > 0) {
+        long long k = std::min<long long>(cap_ee, ne_);
+        if (k) {
+            DevBuf<int4> q;
+            q.alloc(k);
+            launch_pairs_to_quads(h->s, h->coll(), bp.ee[bp.cur], k, q);
+            PDC_CK(cudaMemcpyAsync(ee, q.p, sizeof(int4) * k, cudaMemcpyDeviceToHost, h->s));
+        }
+    }
+    PDC_CK(cudaStreamSynchronize(h->s));
+    API_END(h)
+}
+
+static void upload_quads(pdc_handle h, const int32_t *quads, const int32_t *kinds, int64_t np, DevBuf<int4> &q,
+                         DevBuf<int> &k) {
+    std::vector<int4> qh(np);
+    for (int64_t i = 0; i < np; ++i) {
+        qh[i] = make_int4(quads[4 * i], quads[4 * i + 1], quads[4 * i + 2], quads[4 * i + 3]);
+        for (int j = 0; j < 4; ++j)
+            if (quads[4 * i + j] < 0 || quads[4 * i + j] >= h->nv_all) throw Error(PDC_ERR_ARG, "vertex id out of range");
+        if (kinds[i] != 0 && kinds[i] != 1) throw Error(PDC_ERR_ARG, "kind must be 0 or 1");
+    }
+    q.upload(qh, h->s);
+    k.upload(kinds, np, h->s);
+}
+
+pdc_status pdc_op_ccd(pdc_handle h, const float *x0, const float *x1, const int32_t *quads, const int32_t *kinds,
+                      int64_t np, double *toi) {
+    API_BEGIN(h)
+    if (np < 0 || (np > 0 && (!x0 || !x1 || !quads || !kinds || !toi))) throw Error(PDC_ERR_ARG, "pdc_op_ccd: NULL");
+    if (np == 0) return PDC_OK;
+    h->ensure_topology();
+    DevBuf<float4> a, b;
+    upload_f4(h, x0, h->nv_all, a);
+    upload_f4(h, x1, h->nv_all, b);
+    DevBuf<int4> q;
+    DevBuf<int> k;
+    upload_quads(h, quads, kinds, np, q, k);
+    DevBuf<double> t;
+    t.alloc(np);
+    launch_ccd_quads(h->s, q, k, np, a, b, h->P.eta_ccd, t);
+    t.download(toi, np, h->s);
+    PDC_CK(cudaStreamSynchronize(h->s));
+    API_END(h)
+}
+
+pdc_status pdc_op_partial_ccd(pdc_handle h, const float *x0, const float *x1, const int32_t *quads,
+                              const int32_t *kinds, int64_t np, int32_t *active) {
+    API_BEGIN(h)
+    if (np < 0 || (np > 0 && (!x0 || !x1 || !quads || !kinds || !active)))
+        throw Error(PDC_ERR_ARG, "pdc_op_partial_ccd: NULL");
+    if (np == 0) return PDC_OK;
+    h->ensure_topology();
+    DevBuf<float4> a, b;
+    upload_f4(h, x0, h->nv_all, a);
+    upload_f4(h, x1, h->nv_all, b);
+    DevBuf<int4> q;
+    DevBuf<int> k;
+    upload_quads(h, quads, kinds, np, q, k);
+    DevBuf<int> out;
+    out.alloc(np);
+    launch_partial_quads(h->s, q, k, np, a, b, h->cparams(), out);
+    out.download(active, np, h->s);
+    PDC_CK(cudaStreamSynchronize(h->s));
+    API_END(h)
+}
+
+pdc_status pdc_op_contact(pdc_handle h, const float *x0, const float *x, const int32_t *quads, const int32_t *kinds,
+                          const float *w, int64_t np, float *cw, float *cf) {
+    API_BEGIN(h)
+    if (!x0 || !x || !cw || !cf || np < 0 || (np > 0 && (!quads || !kinds || !w)))
+        throw Error(PDC_ERR_ARG, "pdc_op_contact: NULL");
+    h->ensure_topology();
+    DevBuf<float4> a, b;
+    upload_f4(h, x0, h->nv_all, a);
+    upload_f4(h, x, h->nv_all, b);
+    DevBuf<int4> q;
+    DevBuf<int> k;
+    DevBuf<float> wd;
+    DevBuf<ActivePair> ap;
+    DevBuf<int> na;
+    na.alloc(1);
+    ap.alloc(std::max<int64_t>(np, 1));
+    if (np > 0) {
+        upload_quads(h, quads, kinds, np, q, k);
+        wd.upload(w, np, h->s);
+    }
+    launch_activate_quads(h->s, q, k, wd, np, a, ap, na);
+    h->CW.zero(h->s);
+    h->CF.zero(h->s);
+    launch_contact(h->s, h->coll(), ap, na, (int)std::max<int64_t>(np, 1), b, h->dhat, h->CW, h->CF);
+    h->CW.download(cw, h->n, h->s);
+    get_f4(h, h->CF, cf, 0);
+    API_END(h)
+}
+
+static void upload_contact(pdc_handle h, const float *cw, const float *cf) {
+    if (cw) {
+        h->CW.upload(cw, h->n, h->s);
+    } else {
+        h->CW.zero(h->s);
+    }
+    if (cf) {
+        PDC_CK(cudaMemcpyAsync(h->stage3.p, cf, sizeof(float) * 3 * h->n, cudaMemcpyHostToDevice, h->s));
+        k_f3_to_f4<<<nb(h->n), 256, 0, h->s>>>(h->n, h->stage3, h->CF);
+        PDC_LAUNCH_CK();
+    } else {
+        h->CF.zero(h->s);
+    }
+}
+
+pdc_status pdc_op_residual(pdc_handle h, const float *x, const float *z, const float *cw, const float *cf, float *r) {
+    API_BEGIN(h)
+    if (!x || !z || !r) throw Error(PDC_ERR_ARG, "pdc_op_residual: NULL");
+    DevBuf<float4> a, b;
+    upload_f4(h, x, h->n, a);
+    upload_f4(h, z, h->n, b);
+    upload_contact(h, cw, cf);
+    launch_residual(h->s, h->cloth(), a, b, h->CW, h->CF, h->R, nullptr, nullptr, 0);
+    get_f4(h, h->R, r, 0);
+    API_END(h)
+}
+
+pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, const float *cw, const float *cf,
+                               int32_t r, int32_t cycles, int32_t sweeps, float *x_out) {
+    API_BEGIN(h)
+    if (!x || !z || !x_out || cycles < 1 || sweeps < 0) throw Error(PDC_ERR_ARG, "pdc_op_global_solve: bad arguments");
+    if (r < 0 || r > h->r_warm) throw Error(PDC_ERR_ARG, "pdc_op_global_solve: r exceeds the basis size");
+    if (r > 128) throw Error(PDC_ERR_ARG, "pdc_op_global_solve: r must be <= 128");
+    cudaStream_t s = h->s;
+    int n = h->n;
+    DevBuf<float4> xa, za;
+    upload_f4(h, x, n, xa);
+    upload_f4(h, z, n, za);
+    upload_contact(h, cw, cf);
+    ClothView c = h->cloth();
+    // the factorised path with the leading r columns: reduced matrix U^T (H + diag(cw)) U
+    SubspaceView S = h->sub(0, r);
+    SubspaceWork W = h->work();
+    DevBuf<int> one, ncv;
+    int o1 = 1;
+    one.upload(&o1, 1, s);
+    ncv.alloc(1);
+    launch_contact_list(s, n, h->CW, h->contact_list, ncv);
+    launch_residual(s, c, xa, za, h->CW, h->CF, h->R, nullptr, nullptr, 0);
+    float4 *din = h->D0, *dout = h->D1;
+    bool have = false;
+    for (int cyc = 0; cyc < cycles; ++cyc) {
+        const float4 *rl = h->R;
+        if (have) {
+            launch_linear_residual(s, c, h->CW, h->R, din, h->RL);
+            rl = h->RL;
+        }
+        if (r > 0) {
+            launch_project(s, S, rl, one, W);
+            PDC_CK(cudaMemsetAsync(W.dA, 0, sizeof(float) * r * r, s));
+            launch_syrk(s, S, h->contact_list, ncv, h->CW, W);
+            launch_reduced_solve(s, S, one, W);
+            launch_lift(s, S, one, W, have ? din : nullptr, dout);
+            std::swap(din, dout);
+            have = true;
+        }
+        if (!have) {
+            PDC_CK(cudaMemsetAsync(din, 0, sizeof(float4) * n, s));
+            have = true;
+        }
+        for (int k = 0; k < sweeps; ++k) {
+            launch_sweep(s, c, h->CW, h->R, din, dout, (float)h->omega, nullptr, nullptr, nullptr);
+            std::swap(din, dout);
+        }
+    }
+    launch_sweep(s, c, h->CW, h->R, din, dout, 0.f, xa, xa.p, nullptr);  // x_out = x + delta
+    get_f4(h, xa, x_out, 0);
+    API_END(h)
+}
+
+}  // extern "C"

@@ -1,0 +1,412 @@
+// Collision kernels: spatial-hash broad phase, exact CCD (FP32 distance
+// filter + FP64 root isolation), partial CCD with the non-distance barrier
+// life-span counters, and the collision springs of the global step.
+//
+// Primitive pairs (Sec. 4): vertex-triangle (VT) and edge-edge (EE).  The
+// candidate set is defined by an FP32 swept-box predicate; the hash only
+// culls, so the lists equal the brute-force definition.  Lists are built
+// with a count pass, a prefix sum and a write pass, and every primary's
+// segment is sorted by the secondary id: the pair lists come out sorted by
+// (primary, secondary) and deterministic, which lets the NDB counters of
+// one full CCD be carried to the next by binary search.
+#include "pdc_collide.cuh"
+#include "pdc_scan.cuh"
+
+namespace pdc {
+
+namespace {
+
+constexpr int CELL_BIAS = 1 << 20;
+constexpr int MAX_CELLS_PER_PRIM = 1 << 15;
+
+__device__ inline int cell1(float v, float inv) {
+    float c = floorf(v * inv);
+    c = fminf(fmaxf(c, (float)(-CELL_BIAS)), (float)(CELL_BIAS - 1));
+    return (int)c;
+}
+__device__ inline int3 cellv(float3 p, float inv) { return make_int3(cell1(p.x, inv), cell1(p.y, inv), cell1(p.z, inv)); }
+__device__ inline unsigned long long cell_key(int x, int y, int z) {
+    return ((unsigned long long)(x + CELL_BIAS) << 42) | ((unsigned long long)(y + CELL_BIAS) << 21) |
+           (unsigned long long)(z + CELL_BIAS);
+}
+__device__ inline unsigned int hash_key(unsigned long long k, unsigned int mask) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdULL;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ULL;
+    k ^= k >> 33;
+    return (unsigned int)k & mask;
+}
+
+__device__ inline float3 fmin3(float3 a, float3 b) { return make_float3(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z)); }
+__device__ inline float3 fmax3(float3 a, float3 b) { return make_float3(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z)); }
+
+// Candidate predicate: lo_a <= fl32(hi_b + dhat) and lo_b <= fl32(hi_a + dhat) on every axis.
+__device__ inline bool box_overlap(float3 alo, float3 ahi, float3 blo, float3 bhi, float d) {
+    return alo.x <= __fadd_rn(bhi.x, d) && blo.x <= __fadd_rn(ahi.x, d) && alo.y <= __fadd_rn(bhi.y, d) &&
+           blo.y <= __fadd_rn(ahi.y, d) && alo.z <= __fadd_rn(bhi.z, d) && blo.z <= __fadd_rn(ahi.z, d);
+}
+
+// Cell range of a box inflated by dhat on both sides.  If two boxes satisfy
+// the predicate, their inflated ranges share a cell (rounding is monotone).
+__device__ inline void cell_range(float3 lo, float3 hi, float d, float inv, int3 &clo, int3 &chi) {
+    float3 l = make_float3(__fsub_rn(lo.x, d), __fsub_rn(lo.y, d), __fsub_rn(lo.z, d));
+    float3 h = make_float3(__fadd_rn(hi.x, d), __fadd_rn(hi.y, d), __fadd_rn(hi.z, d));
+    clo = cellv(l, inv);
+    chi = cellv(h, inv);
+}
+
+__device__ inline void vbox(const float4 *x0, const float4 *x1, int v, float3 &lo, float3 &hi) {
+    float3 a = f3(x0[v]), b = f3(x1[v]);
+    lo = fmin3(a, b);
+    hi = fmax3(a, b);
+}
+
+template <int K> __device__ inline void prim_box(const float4 *x0, const float4 *x1, const int *ids, float3 &lo, float3 &hi) {
+    vbox(x0, x1, ids[0], lo, hi);
+    for (int k = 1; k < K; ++k) {
+        float3 l, h;
+        vbox(x0, x1, ids[k], l, h);
+        lo = fmin3(lo, l);
+        hi = fmax3(hi, h);
+    }
+}
+
+// ------------------------------------------------------------------ boxes
+__global__ void k_tri_boxes(CollView cv, const float4 *__restrict__ x0, const float4 *__restrict__ x1,
+                            float4 *__restrict__ blo, float4 *__restrict__ bhi, GridParams *gp) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    float ext = 0.f;
+    if (t < cv.nt) {
+        int4 T = cv.tri[t];
+        int ids[3] = {T.x, T.y, T.z};
+        float3 lo, hi;
+        prim_box<3>(x0, x1, ids, lo, hi);
+        blo[t] = f4(lo);
+        bhi[t] = f4(hi);
+        ext = fmaxf(hi.x - lo.x, fmaxf(hi.y - lo.y, hi.z - lo.z));
+    }
+    for (int o = 16; o > 0; o >>= 1) ext += __shfl_xor_sync(0xffffffffu, ext, o);
+    if ((threadIdx.x & 31) == 0 && ext > 0.f) atomicAdd(&gp->ext_sum, (double)ext);
+}
+
+__global__ void k_edge_boxes(CollView cv, const float4 *__restrict__ x0, const float4 *__restrict__ x1,
+                             float4 *__restrict__ blo, float4 *__restrict__ bhi) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cv.ne) return;
+    int2 E = cv.edge[e];
+    int ids[2] = {E.x, E.y};
+    float3 lo, hi;
+    prim_box<2>(x0, x1, ids, lo, hi);
+    blo[e] = f4(lo);
+    bhi[e] = f4(hi);
+}
+
+__global__ void k_grid_params(GridParams *gp, int nt, float dhat, float scale) {
+    double mean = nt > 0 ? gp->ext_sum / nt : 0.0;
+    float cell = fmaxf((float)mean, 2.f * dhat);
+    cell = fmaxf(cell, 1e-6f) * scale;
+    gp->cell = cell;
+    gp->inv_cell = 1.f / cell;
+}
+
+// ------------------------------------------------------------------ hash table
+// mode 0: count per bucket; mode 1: fill entries.
+__global__ void k_hash_insert(int np, const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
+                              const GridParams *gp, float dhat, unsigned int mask, int *__restrict__ bcnt,
+                              const int *__restrict__ bstart, int *__restrict__ bfill,
+                              unsigned long long *__restrict__ ekey, int *__restrict__ eprim, int mode,
+                              const long long *total, long long cap, int *overflow) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    if (mode == 1 && *total > cap) return;
+    float inv = gp->inv_cell;
+    int3 lo, hi;
+    cell_range(f3(blo[p]), f3(bhi[p]), dhat, inv, lo, hi);
+    long long ncell = (long long)(hi.x - lo.x + 1) * (hi.y - lo.y + 1) * (hi.z - lo.z + 1);
+    if (ncell > MAX_CELLS_PER_PRIM) {
+        if (mode == 0) atomicOr(overflow, OVF_CELLS);
+        return;
+    }
+    for (int z = lo.z; z <= hi.z; ++z)
+        for (int y = lo.y; y <= hi.y; ++y)
+            for (int x = lo.x; x <= hi.x; ++x) {
+                unsigned long long k = cell_key(x, y, z);
+                unsigned int b = hash_key(k, mask);
+                if (mode == 0) {
+                    atomicAdd(&bcnt[b], 1);
+                } else {
+                    int pos = bstart[b] + atomicAdd(&bfill[b], 1);
+                    ekey[pos] = k;
+                    eprim[pos] = p;
+                }
+            }
+}
+
+// ------------------------------------------------------------------ queries
+// VT: primary = vertex v (all collision vertices), secondary = triangle.
+__global__ void __launch_bounds__(128) k_query_vt(CollView cv, const float4 *__restrict__ x0,
+                                                  const float4 *__restrict__ x1, const float4 *__restrict__ tlo,
+                                                  const float4 *__restrict__ thi, const GridParams *gp, float dhat,
+                                                  unsigned int mask, const int *__restrict__ bcnt,
+                                                  const int *__restrict__ bstart,
+                                                  const unsigned long long *__restrict__ ekey,
+                                                  const int *__restrict__ eprim, int *__restrict__ cnt,
+                                                  const int *__restrict__ off, int2 *__restrict__ out,
+                                                  const long long *hash_total, long long cap_ent,
+                                                  const long long *total, long long cap, int *overflow) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= cv.nv) return;
+    bool write = out != nullptr;
+    if (*hash_total > cap_ent) {  // table not filled: produce nothing
+        if (!write) cnt[v] = 0;
+        return;
+    }
+    if (write && *total > cap) return;
+    float inv = gp->inv_cell;
+    float3 lo, hi;
+    vbox(x0, x1, v, lo, hi);
+    int3 clo, chi;
+    cell_range(lo, hi, dhat, inv, clo, chi);
+    if ((long long)(chi.x - clo.x + 1) * (chi.y - clo.y + 1) * (chi.z - clo.z + 1) > MAX_CELLS_PER_PRIM) {
+        if (!write) {
+            cnt[v] = 0;
+            atomicOr(overflow, OVF_CELLS);
+        }
+        return;
+    }
+    bool vfix = v >= cv.nc;
+    int base = write ? off[v] : 0;
+    int c = 0;
+    for (int z = clo.z; z <= chi.z; ++z)
+        for (int y = clo.y; y <= chi.y; ++y)
+            for (int x = clo.x; x <= chi.x; ++x) {
+                unsigned long long k = cell_key(x, y, z);
+                unsigned int b = hash_key(k, mask);
+                int e0 = bstart[b], e1 = e0 + bcnt[b];
+                for (int e = e0; e < e1; ++e) {
+                    if (ekey[e] != k) continue;
+                    int t = eprim[e];
+                    int4 T = cv.tri[t];
+                    if (T.x == v || T.y == v || T.z == v) continue;
+                    if (vfix && T.x >= cv.nc && T.y >= cv.nc && T.z >= cv.nc) continue;
+                    float3 bl = f3(tlo[t]), bh = f3(thi[t]);
+                    int3 tl, th;
+                    cell_range(bl, bh, dhat, inv, tl, th);
+                    if (x != max(clo.x, tl.x) || y != max(clo.y, tl.y) || z != max(clo.z, tl.z)) continue;
+                    if (!box_overlap(lo, hi, bl, bh, dhat)) continue;
+                    if (write) out[base + c] = make_int2(v, t);
+                    ++c;
+                }
+            }
+    if (!write) {
+        cnt[v] = c;
+    } else {
+        for (int i = 1; i < c; ++i) {  // insertion sort of the segment by triangle id
+            int2 key = out[base + i];
+            int j = i - 1;
+            while (j >= 0 && out[base + j].y > key.y) {
+                out[base + j + 1] = out[base + j];
+                --j;
+            }
+            out[base + j + 1] = key;
+        }
+    }
+}
+
+// EE: primary = edge e, secondary = edge f > e.
+__global__ void __launch_bounds__(128) k_query_ee(CollView cv, const float4 *__restrict__ elo,
+                                                  const float4 *__restrict__ ehi, const GridParams *gp, float dhat,
+                                                  unsigned int mask, const int *__restrict__ bcnt,
+                                                  const int *__restrict__ bstart,
+                                                  const unsigned long long *__restrict__ ekey,
+                                                  const int *__restrict__ eprim, int *__restrict__ cnt,
+                                                  const int *__restrict__ off, int2 *__restrict__ out,
+                                                  const long long *hash_total, long long cap_ent,
+                                                  const long long *total, long long cap, int *overflow) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cv.ne) return;
+    bool write = out != nullptr;
+    if (*hash_total > cap_ent) {
+        if (!write) cnt[e] = 0;
+        return;
+    }
+    if (write && *total > cap) return;
+    float inv = gp->inv_cell;
+    float3 lo = f3(elo[e]), hi = f3(ehi[e]);
+    int3 clo, chi;
+    cell_range(lo, hi, dhat, inv, clo, chi);
+    if ((long long)(chi.x - clo.x + 1) * (chi.y - clo.y + 1) * (chi.z - clo.z + 1) > MAX_CELLS_PER_PRIM) {
+        if (!write) {
+            cnt[e] = 0;
+            atomicOr(overflow, OVF_CELLS);
+        }
+        return;
+    }
+    int2 E = cv.edge[e];
+    bool efix = E.x >= cv.nc && E.y >= cv.nc;
+    int base = write ? off[e] : 0;
+    int c = 0;
+    for (int z = clo.z; z <= chi.z; ++z)
+        for (int y = clo.y; y <= chi.y; ++y)
+            for (int x = clo.x; x <= chi.x; ++x) {
+                unsigned long long k = cell_key(x, y, z);
+                unsigned int b = hash_key(k, mask);
+                int e0 = bstart[b], e1 = e0 + bcnt[b];
+                for (int q = e0; q < e1; ++q) {
+                    if (ekey[q] != k) continue;
+                    int f = eprim[q];
+                    if (f <= e) continue;
+                    int2 F = cv.edge[f];
+                    if (E.x == F.x || E.x == F.y || E.y == F.x || E.y == F.y) continue;
+                    if (efix && F.x >= cv.nc && F.y >= cv.nc) continue;
+                    float3 bl = f3(elo[f]), bh = f3(ehi[f]);
+                    int3 tl, th;
+                    cell_range(bl, bh, dhat, inv, tl, th);
+                    if (x != max(clo.x, tl.x) || y != max(clo.y, tl.y) || z != max(clo.z, tl.z)) continue;
+                    if (!box_overlap(lo, hi, bl, bh, dhat)) continue;
+                    if (write) out[base + c] = make_int2(e, f);
+                    ++c;
+                }
+            }
+    if (!write) {
+        cnt[e] = c;
+    } else {
+        for (int i = 1; i < c; ++i) {
+            int2 key = out[base + i];
+            int j = i - 1;
+            while (j >= 0 && out[base + j].y > key.y) {
+                out[base + j + 1] = out[base + j];
+                --j;
+            }
+            out[base + j + 1] = key;
+        }
+    }
+}
+
+__global__ void k_check_cap(const long long *total, long long cap, int flag, int *overflow, long long *count_out) {
+    long long t = *total;
+    *count_out = t;
+    if (t > cap) atomicOr(overflow, flag);
+}
+
+inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+// ====================================================================== broad phase driver
+void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee_, long long cap_ent_) {
+    nt = cv.nt;
+    ne = cv.ne;
+    nv = cv.nv;
+    auto pow2 = [](long long x) {
+        long long p = 1024;
+        while (p < x) p <<= 1;
+        return p;
+    };
+    T_vt = (int)pow2(2LL * cv.nt + 1024);
+    T_ee = (int)pow2(2LL * cv.ne + 1024);
+    for (int k = 0; k < 2; ++k) {
+        bcnt[k].alloc(k == 0 ? T_vt : T_ee);
+        bstart[k].alloc(k == 0 ? T_vt : T_ee);
+        bfill[k].alloc(k == 0 ? T_vt : T_ee);
+    }
+    cap_ent = cap_ent_;
+    for (int k = 0; k < 2; ++k) {
+        ekey[k].alloc(cap_ent);
+        eprim[k].alloc(cap_ent);
+    }
+    tlo.alloc(cv.nt);
+    thi.alloc(cv.nt);
+    elo.alloc(cv.ne);
+    ehi.alloc(cv.ne);
+    cnt_v.alloc(cv.nv);
+    off_v.alloc(cv.nv);
+    cnt_e.alloc(cv.ne);
+    off_e.alloc(cv.ne);
+    long long mx = std::max<long long>(std::max<long long>(T_vt, T_ee), std::max<long long>(cv.nv, cv.ne));
+    scratch.alloc(scan_scratch_ints((int)mx) + 16);
+    gp.alloc(1);
+    totals.alloc(8);
+    cap_vt = cap_vt_;
+    cap_ee = cap_ee_;
+    for (int k = 0; k < 2; ++k) {
+        vt[k].alloc(cap_vt);
+        ee[k].alloc(cap_ee);
+        st_vt[k].alloc(cap_vt);
+        st_ee[k].alloc(cap_ee);
+        cnt_vt_d[k].alloc(1);
+        cnt_ee_d[k].alloc(1);
+    }
+    cur = 0;
+    for (int k = 0; k < 2; ++k) {
+        cnt_vt_d[k].zero(0);
+        cnt_ee_d[k].zero(0);
+    }
+}
+
+// Builds the new candidate lists in buffer (cur ^ 1) and makes it current.
+void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat,
+                     int *overflow) {
+    int nw = cur ^ 1;
+    PDC_CK(cudaMemsetAsync(gp.p, 0, sizeof(GridParams), s));
+    if (cv.nt) k_tri_boxes<<<nblk(cv.nt, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, gp);
+    if (cv.ne) k_edge_boxes<<<nblk(cv.ne, 256), 256, 0, s>>>(cv, x0, x1, elo, ehi);
+    k_grid_params<<<1, 1, 0, s>>>(gp, cv.nt, dhat, cell_scale);
+    PDC_LAUNCH_CK();
+    long long *tot = totals.p;
+    // ---- tables: 0 = triangles (VT), 1 = edges (EE)
+    for (int k = 0; k < 2; ++k) {
+        int np = k == 0 ? cv.nt : cv.ne;
+        int T = k == 0 ? T_vt : T_ee;
+        const float4 *lo = k == 0 ? tlo.p : elo.p;
+        const float4 *hi = k == 0 ? thi.p : ehi.p;
+        bcnt[k].zero(s);
+        bfill[k].zero(s);
+        if (np) {
+            k_hash_insert<<<nblk(np, 256), 256, 0, s>>>(np, lo, hi, gp, dhat, (unsigned)(T - 1), bcnt[k], bstart[k],
+                                                        bfill[k], ekey[k], eprim[k], 0, tot + k, cap_ent, overflow);
+            PDC_LAUNCH_CK();
+        }
+        exclusive_scan(s, bcnt[k], bstart[k], T, scratch, tot + k);
+        k_check_cap<<<1, 1, 0, s>>>(tot + k, cap_ent, OVF_HASH, overflow, tot + 4 + k);
+        if (np) {
+            k_hash_insert<<<nblk(np, 256), 256, 0, s>>>(np, lo, hi, gp, dhat, (unsigned)(T - 1), bcnt[k], bstart[k],
+                                                        bfill[k], ekey[k], eprim[k], 1, tot + k, cap_ent, overflow);
+            PDC_LAUNCH_CK();
+        }
+    }
+    // ---- VT candidates
+    if (cv.nv) {
+        k_query_vt<<<nblk(cv.nv, 128), 128, 0, s>>>(cv, x0, x1, tlo, thi, gp, dhat, (unsigned)(T_vt - 1), bcnt[0],
+                                                    bstart[0], ekey[0], eprim[0], cnt_v, nullptr, nullptr, tot + 0,
+                                                    cap_ent, tot + 0, cap_ent, overflow);
+        PDC_LAUNCH_CK();
+    }
+    exclusive_scan(s, cnt_v, off_v, cv.nv, scratch, tot + 2);
+    k_check_cap<<<1, 1, 0, s>>>(tot + 2, cap_vt, OVF_VT, overflow, cnt_vt_d[nw]);
+    if (cv.nv) {
+        k_query_vt<<<nblk(cv.nv, 128), 128, 0, s>>>(cv, x0, x1, tlo, thi, gp, dhat, (unsigned)(T_vt - 1), bcnt[0],
+                                                    bstart[0], ekey[0], eprim[0], cnt_v, off_v, vt[nw], tot + 0,
+                                                    cap_ent, tot + 2, cap_vt, overflow);
+        PDC_LAUNCH_CK();
+    }
+    // ---- EE candidates
+    if (cv.ne) {
+        k_query_ee<<<nblk(cv.ne, 128), 128, 0, s>>>(cv, elo, ehi, gp, dhat, (unsigned)(T_ee - 1), bcnt[1], bstart[1],
+                                                    ekey[1], eprim[1], cnt_e, nullptr, nullptr, tot + 1, cap_ent,
+                                                    tot + 1, cap_ent, overflow);
+        PDC_LAUNCH_CK();
+    }
+    exclusive_scan(s, cnt_e, off_e, cv.ne, scratch, tot + 3);
+    k_check_cap<<<1, 1, 0, s>>>(tot + 3, cap_ee, OVF_EE, overflow, cnt_ee_d[nw]);
+    if (cv.ne) {
+        k_query_ee<<<nblk(cv.ne, 128), 128, 0, s>>>(cv, elo, ehi, gp, dhat, (unsigned)(T_ee - 1), bcnt[1], bstart[1],
+                                                    ekey[1], eprim[1], cnt_e, off_e, ee[nw], tot + 1, cap_ent,
+                                                    tot + 3, cap_ee, overflow);
+        PDC_LAUNCH_CK();
+    }
+    cur = nw;
+}
+
+}  // namespace pdc

@@ -1,0 +1,610 @@
+// Per-pair collision kernels: exact CCD, partial CCD + NDB counters,
+// active-constraint collection, collision springs.
+//
+// Closest points (used for the partial-CCD sample at the t = 0 projection
+// point, for the contact direction and for the CCD contact test):
+//   VT: the closest point of a triangle to a point, by the Voronoi region of
+//       the triangle that contains the point (vertex, edge or face region);
+//   EE: the minimiser of |p1(s) - p2(t)|^2 over [0,1]^2, found by clamping the
+//       unconstrained minimiser one parameter at a time; for parallel
+//       segments (a e - b^2 <= 1e-6 a e) the parameter s is the midpoint of
+//       the projections of segment 2's end points onto segment 1 (clamped),
+//       t the clamped projection of p1(s) onto segment 2.
+#include "pdc_collide.cuh"
+
+namespace pdc {
+
+namespace {
+
+template <class T> struct V {
+    T x, y, z;
+};
+// the float3 helpers of the enclosing namespace stay visible beside the V<T> ones
+using pdc::operator+;
+using pdc::operator-;
+using pdc::operator*;
+template <class T> __device__ inline V<T> mk(T x, T y, T z) { return V<T>{x, y, z}; }
+template <class T> __device__ inline V<T> operator+(V<T> a, V<T> b) { return mk<T>(a.x + b.x, a.y + b.y, a.z + b.z); }
+template <class T> __device__ inline V<T> operator-(V<T> a, V<T> b) { return mk<T>(a.x - b.x, a.y - b.y, a.z - b.z); }
+template <class T> __device__ inline V<T> operator*(T s, V<T> a) { return mk<T>(s * a.x, s * a.y, s * a.z); }
+template <class T> __device__ inline T dotv(V<T> a, V<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T> __device__ inline V<T> crossv(V<T> a, V<T> b) {
+    return mk<T>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+template <class T> __device__ inline V<T> ld(float4 a) { return mk<T>((T)a.x, (T)a.y, (T)a.z); }
+template <class T> __device__ inline T clamp01(T v) { return v < T(0) ? T(0) : (v > T(1) ? T(1) : v); }
+
+// Barycentric weights (wa, wb, wc) of the closest point of triangle abc to p.
+template <class T> __device__ void closest_tri(V<T> p, V<T> a, V<T> b, V<T> c, T w[3]) {
+    V<T> ab = b - a, ac = c - a, ap = p - a;
+    T d1 = dotv(ab, ap), d2 = dotv(ac, ap);
+    if (d1 <= T(0) && d2 <= T(0)) { w[0] = 1; w[1] = 0; w[2] = 0; return; }
+    V<T> bp = p - b;
+    T d3 = dotv(ab, bp), d4 = dotv(ac, bp);
+    if (d3 >= T(0) && d4 <= d3) { w[0] = 0; w[1] = 1; w[2] = 0; return; }
+    T vc = d1 * d4 - d3 * d2;
+    if (vc <= T(0) && d1 >= T(0) && d3 <= T(0)) {
+        T den = d1 - d3;
+        T v = den > T(0) ? d1 / den : T(0);
+        w[0] = 1 - v; w[1] = v; w[2] = 0;
+        return;
+    }
+    V<T> cp = p - c;
+    T d5 = dotv(ab, cp), d6 = dotv(ac, cp);
+    if (d6 >= T(0) && d5 <= d6) { w[0] = 0; w[1] = 0; w[2] = 1; return; }
+    T vb = d5 * d2 - d1 * d6;
+    if (vb <= T(0) && d2 >= T(0) && d6 <= T(0)) {
+        T den = d2 - d6;
+        T u = den > T(0) ? d2 / den : T(0);
+        w[0] = 1 - u; w[1] = 0; w[2] = u;
+        return;
+    }
+    T va = d3 * d6 - d5 * d4;
+    if (va <= T(0) && (d4 - d3) >= T(0) && (d5 - d6) >= T(0)) {
+        T den = (d4 - d3) + (d5 - d6);
+        T u = den > T(0) ? (d4 - d3) / den : T(0);
+        w[0] = 0; w[1] = 1 - u; w[2] = u;
+        return;
+    }
+    T sum = va + vb + vc;
+    if (!(sum > T(0))) {  // degenerate triangle: nearest vertex
+        T da = dotv(ap, ap), db = dotv(bp, bp), dc = dotv(cp, cp);
+        w[0] = w[1] = w[2] = 0;
+        if (da <= db && da <= dc) w[0] = 1; else if (db <= dc) w[1] = 1; else w[2] = 1;
+        return;
+    }
+    T inv = T(1) / sum;
+    T v = vb * inv, u = vc * inv;
+    w[0] = 1 - v - u; w[1] = v; w[2] = u;
+}
+
+template <class T> __device__ void closest_seg(V<T> p1, V<T> q1, V<T> p2, V<T> q2, T &s, T &t) {
+    V<T> d1 = q1 - p1, d2 = q2 - p2, r = p1 - p2;
+    T a = dotv(d1, d1), e = dotv(d2, d2), f = dotv(d2, r);
+    if (a <= T(0) && e <= T(0)) { s = 0; t = 0; return; }
+    if (a <= T(0)) { s = 0; t = clamp01(f / e); return; }
+    T c = dotv(d1, r);
+    if (e <= T(0)) { t = 0; s = clamp01(-c / a); return; }
+    T b = dotv(d1, d2);
+    T den = a * e - b * b;
+    if (den <= T(1e-6) * a * e) {
+        // parallel: midpoint of the projections of p2, q2 onto segment 1
+        T s0 = clamp01(-c / a), s1 = clamp01((b - c) / a);
+        s = T(0.5) * (s0 + s1);
+        t = clamp01((b * s + f) / e);
+        return;
+    }
+    s = clamp01((b * f - c * e) / den);
+    t = (b * s + f) / e;
+    if (t < T(0)) { t = 0; s = clamp01(-c / a); }
+    else if (t > T(1)) { t = 1; s = clamp01((b - c) / a); }
+}
+
+// Gap-vector coefficients c at the closest points of the 4 points q (kind 0:
+// v, a, b, c; kind 1: a, b, c, d): p2 - p1 = sum_j c_j q_j.
+template <class T> __device__ void closest_coef(int kind, const V<T> q[4], T c[4]) {
+    if (kind == 0) {
+        T w[3];
+        closest_tri(q[0], q[1], q[2], q[3], w);
+        c[0] = -1; c[1] = w[0]; c[2] = w[1]; c[3] = w[2];
+    } else {
+        T s, t;
+        closest_seg(q[0], q[1], q[2], q[3], s, t);
+        c[0] = -(1 - s); c[1] = -s; c[2] = 1 - t; c[3] = t;
+    }
+}
+
+template <class T> __device__ inline T gap_dist(int kind, const V<T> q[4]) {
+    T c[4];
+    closest_coef(kind, q, c);
+    V<T> d = c[0] * q[0] + c[1] * q[1] + c[2] * q[2] + c[3] * q[3];
+    return sqrt(dotv(d, d));
+}
+
+__device__ inline double det3(V<double> a, V<double> b, V<double> c) { return dotv(a, crossv(b, c)); }
+__device__ inline double cubic(const double c[4], double t) { return ((c[3] * t + c[2]) * t + c[1]) * t + c[0]; }
+
+// Exact CCD (Sec. 4, Eq. intersect) of one pair moving linearly q0 -> q1.
+// FP32 filter: the distance at t = 0 minus the largest relative displacement
+// bounds the distance over the whole interval from below; pairs that stay
+// apart are rejected.  Survivors: the four points must become coplanar for
+// contact, f(t) = det[q1-q0, q2-q0, q3-q0] = 0 (cubic); candidate times are
+// 0, the critical points of f and its roots (bisection on monotone pieces),
+// in increasing order; the first one at which the primitives are within eta
+// is the time of impact.  Coplanar motion (f == 0): 1025 uniform samples.
+__device__ double ccd_pair(int kind, const float4 a0[4], const float4 a1[4], double eta) {
+    {
+        V<float> q[4];
+        float cmax = 0.f;
+        V<float> dv[4];
+        for (int i = 0; i < 4; ++i) {
+            q[i] = ld<float>(a0[i]);
+            V<float> e = ld<float>(a1[i]);
+            dv[i] = e - q[i];
+            cmax = fmaxf(cmax, fmaxf(fabsf(q[i].x), fmaxf(fabsf(q[i].y), fabsf(q[i].z))));
+            cmax = fmaxf(cmax, fmaxf(fabsf(e.x), fmaxf(fabsf(e.y), fabsf(e.z))));
+        }
+        float maxrel = 0.f;
+        if (kind == 0) {
+            for (int j = 1; j < 4; ++j) { V<float> r = dv[j] - dv[0]; maxrel = fmaxf(maxrel, sqrtf(dotv(r, r))); }
+        } else {
+            for (int j = 0; j < 2; ++j)
+                for (int k = 2; k < 4; ++k) { V<float> r = dv[k] - dv[j]; maxrel = fmaxf(maxrel, sqrtf(dotv(r, r))); }
+        }
+        float d0 = gap_dist<float>(kind, q);
+        if (d0 > 1.001f * maxrel + (float)eta + 4e-6f * cmax) return 2.0;
+    }
+    V<double> q0[4], q1[4];
+    for (int i = 0; i < 4; ++i) { q0[i] = ld<double>(a0[i]); q1[i] = ld<double>(a1[i]); }
+    V<double> u0 = q0[1] - q0[0], v0 = q0[2] - q0[0], w0 = q0[3] - q0[0];
+    V<double> du = (q1[1] - q1[0]) - u0, dv = (q1[2] - q1[0]) - v0, dw = (q1[3] - q1[0]) - w0;
+    double c[4];
+    c[0] = det3(u0, v0, w0);
+    c[1] = det3(du, v0, w0) + det3(u0, dv, w0) + det3(u0, v0, dw);
+    c[2] = det3(du, dv, w0) + det3(du, v0, dw) + det3(u0, dv, dw);
+    c[3] = det3(du, dv, dw);
+    double sc = 0.0;
+    {
+        V<double> vs[6] = {u0, v0, w0, du, dv, dw};
+        for (int i = 0; i < 6; ++i) sc = fmax(sc, sqrt(dotv(vs[i], vs[i])));
+    }
+    double s3 = sc * sc * sc;
+    V<double> q[4];
+    auto at = [&](double t) {
+        for (int i = 0; i < 4; ++i) q[i] = q0[i] + t * (q1[i] - q0[i]);
+        return gap_dist<double>(kind, q);
+    };
+    double lim = 1e-14 * s3;
+    if (fabs(c[0]) <= lim && fabs(c[1]) <= lim && fabs(c[2]) <= lim && fabs(c[3]) <= lim) {
+        for (int k = 0; k <= 1024; ++k) {
+            double t = k / 1024.0;
+            if (at(t) <= eta) return t;
+        }
+        return 2.0;
+    }
+    double cand[8];
+    int nc = 0;
+    cand[nc++] = 0.0;
+    double brk[4];
+    int nb = 0;
+    brk[nb++] = 0.0;
+    {
+        double A = 3.0 * c[3], B = 2.0 * c[2], C = c[1];
+        double r0 = 2.0, r1 = 2.0;
+        if (fabs(A) > 1e-300) {
+            double disc = B * B - 4.0 * A * C;
+            if (disc >= 0.0) {
+                double sq = sqrt(disc);
+                double qq = -0.5 * (B + (B >= 0.0 ? sq : -sq));
+                if (qq != 0.0) { r0 = qq / A; r1 = C / qq; }
+                else { r0 = 0.0; }
+            }
+        } else if (fabs(B) > 1e-300) {
+            r0 = -C / B;
+        }
+        if (r0 > r1) { double tmp = r0; r0 = r1; r1 = tmp; }
+        if (r0 > 0.0 && r0 < 1.0) { brk[nb++] = r0; cand[nc++] = r0; }
+        if (r1 > 0.0 && r1 < 1.0 && r1 != r0) { brk[nb++] = r1; cand[nc++] = r1; }
+    }
+    brk[nb++] = 1.0;
+    for (int i = 0; i + 1 < nb; ++i) {
+        double lo = brk[i], hi = brk[i + 1];
+        double flo = cubic(c, lo), fhi = cubic(c, hi);
+        if (flo == 0.0) { cand[nc++] = lo; continue; }
+        if (fhi == 0.0) { cand[nc++] = hi; continue; }
+        if ((flo < 0.0) == (fhi < 0.0)) continue;
+        for (int it = 0; it < 200; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (!(mid > lo && mid < hi)) break;
+            double fm = cubic(c, mid);
+            if (fm == 0.0) { lo = hi = mid; break; }
+            if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+        }
+        cand[nc++] = lo;
+    }
+    // ascending order (at most 6 candidates)
+    for (int i = 1; i < nc; ++i) {
+        double v = cand[i];
+        int j = i - 1;
+        while (j >= 0 && cand[j] > v) { cand[j + 1] = cand[j]; --j; }
+        cand[j + 1] = v;
+    }
+    for (int i = 0; i < nc; ++i)
+        if (at(cand[i]) <= eta) return cand[i];
+    return 2.0;
+}
+
+// Partial CCD (Sec. 4.1): Q(lambda) = (p2^1 - p1^1).(p2^0 - p1^0) at the t=0
+// closest point and the fixed sample pattern; active when some sample has
+// Q <= dhat |p2^0 - p1^0|.  Returns the closest-point coefficients in c.
+__device__ bool partial_pair(int kind, const float4 a0[4], const float4 a1[4], float dhat, int ns, float c[4]) {
+    V<float> p[4], e[4];
+    for (int i = 0; i < 4; ++i) { p[i] = ld<float>(a0[i]); e[i] = ld<float>(a1[i]); }
+    closest_coef<float>(kind, p, c);
+    float lam[5][2];
+    int n = 0;
+    if (kind == 0) {
+        lam[n][0] = c[2]; lam[n][1] = c[3]; ++n;
+        if (ns == 1) { lam[n][0] = 1.f / 3.f; lam[n][1] = 1.f / 3.f; ++n; }
+        if (ns == 3) {
+            lam[n][0] = 1.f / 6.f; lam[n][1] = 1.f / 6.f; ++n;
+            lam[n][0] = 2.f / 3.f; lam[n][1] = 1.f / 6.f; ++n;
+            lam[n][0] = 1.f / 6.f; lam[n][1] = 2.f / 3.f; ++n;
+        }
+    } else {
+        lam[n][0] = -c[1]; lam[n][1] = c[3]; ++n;
+        if (ns == 1) { lam[n][0] = 0.5f; lam[n][1] = 0.5f; ++n; }
+        if (ns == 4) {
+            const float v[2] = {0.25f, 0.75f};
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) { lam[n][0] = v[i]; lam[n][1] = v[j]; ++n; }
+        }
+    }
+    for (int k = 0; k < n; ++k) {
+        float l1 = lam[k][0], l2 = lam[k][1];
+        V<float> p10, p20, p11, p21;
+        if (kind == 0) {
+            p10 = p[0]; p11 = e[0];
+            p20 = p[1] + (l1 * (p[2] - p[1]) + l2 * (p[3] - p[1]));
+            p21 = e[1] + (l1 * (e[2] - e[1]) + l2 * (e[3] - e[1]));
+        } else {
+            p10 = p[0] + l1 * (p[1] - p[0]); p11 = e[0] + l1 * (e[1] - e[0]);
+            p20 = p[2] + l2 * (p[3] - p[2]); p21 = e[2] + l2 * (e[3] - e[2]);
+        }
+        V<float> d0 = p20 - p10, d1 = p21 - p11;
+        if (dotv(d1, d0) - dhat * sqrtf(dotv(d0, d0)) <= 0.f) return true;
+    }
+    return false;
+}
+
+// Unit start direction of the gap vector; falls back to the triangle normal
+// (VT) or the edge cross product (EE) when the gap vanishes.
+__device__ float3 start_dir(int kind, const float4 a0[4], const float c[4]) {
+    float3 q[4];
+    for (int i = 0; i < 4; ++i) q[i] = f3(a0[i]);
+    float3 d = c[0] * q[0] + c[1] * q[1] + c[2] * q[2] + c[3] * q[3];
+    float l = sqrtf(dot3(d, d));
+    if (l > 1e-30f) return (1.f / l) * d;
+    float3 nn = kind == 0 ? cross3(q[2] - q[1], q[3] - q[1]) : cross3(q[1] - q[0], q[3] - q[2]);
+    l = sqrtf(dot3(nn, nn));
+    return l > 1e-30f ? (1.f / l) * nn : make_float3(0.f, 0.f, 1.f);
+}
+
+__device__ inline void pair_ids(const CollView &cv, const int2 *vt, const int2 *ee, long long nvt, long long idx,
+                                int ids[4], int &kind) {
+    if (idx < nvt) {
+        int2 p = vt[idx];
+        int4 T = cv.tri[p.y];
+        ids[0] = p.x; ids[1] = T.x; ids[2] = T.y; ids[3] = T.z;
+        kind = 0;
+    } else {
+        int2 p = ee[idx - nvt];
+        int2 E = cv.edge[p.x], F = cv.edge[p.y];
+        ids[0] = E.x; ids[1] = E.y; ids[2] = F.x; ids[3] = F.y;
+        kind = 1;
+    }
+}
+
+__device__ inline float ndb_weight(const CollParams &P, int a) {
+    float w = P.k_ndb;
+    for (int i = 0; i < a; ++i) w *= P.K_ndb;  // w = k K^a, Eq. (exp)
+    return w;
+}
+
+// Warp-aggregated append (all 32 lanes must call it together).
+__device__ inline void append_active(bool want, const ActivePair &ap, ActivePair *act, int cap, int *n_act,
+                                     int *overflow) {
+    unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(n_act, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) {
+        int slot = base + __popc(m & ((1u << lane) - 1u));
+        if (slot < cap) act[slot] = ap;
+        else atomicOr(overflow, OVF_ACTIVE);
+    }
+}
+
+__device__ inline long long find_pair(const int2 *list, long long n, int2 key) {
+    long long lo = 0, hi = n;
+    while (lo < hi) {
+        long long mid = (lo + hi) >> 1;
+        int2 v = list[mid];
+        if (v.x < key.x || (v.x == key.x && v.y < key.y)) lo = mid + 1; else hi = mid;
+    }
+    if (lo < n) {
+        int2 v = list[lo];
+        if (v.x == key.x && v.y == key.y) return lo;
+    }
+    return -1;
+}
+
+constexpr int PAIR_BLOCKS = 152 * 8;
+constexpr int PAIR_THREADS = 256;
+
+__global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const int2 *__restrict__ vt,
+                                                           const int2 *__restrict__ ee, const long long *nvt_p,
+                                                           const long long *nee_p, unsigned char *__restrict__ st_vt,
+                                                           unsigned char *__restrict__ st_ee,
+                                                           const int2 *__restrict__ ovt, const int2 *__restrict__ oee,
+                                                           const long long *onvt_p, const long long *onee_p,
+                                                           const unsigned char *__restrict__ ost_vt,
+                                                           const unsigned char *__restrict__ ost_ee,
+                                                           const float4 *__restrict__ x0, const float4 *__restrict__ x1,
+                                                           double eta, unsigned long long *toi_min) {
+    long long nvt = *nvt_p, n = nvt + *nee_p;
+    long long onvt = ovt ? *onvt_p : 0, onee = oee ? *onee_p : 0;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int ids[4], kind;
+        pair_ids(cv, vt, ee, nvt, idx, ids, kind);
+        unsigned char st = 0;
+        if (ovt) {
+            long long j;
+            if (kind == 0) {
+                j = find_pair(ovt, onvt, vt[idx]);
+                if (j >= 0) st = ost_vt[j];
+            } else {
+                j = find_pair(oee, onee, ee[idx - nvt]);
+                if (j >= 0) st = ost_ee[j];
+            }
+            if (!(st & ST_ACTIVE)) st = 0;
+        }
+        float4 a0[4], a1[4];
+        for (int i = 0; i < 4; ++i) { a0[i] = x0[ids[i]]; a1[i] = x1[ids[i]]; }
+        double t = ccd_pair(kind, a0, a1, eta);
+        if (t <= 1.0) {
+            st |= ST_ACTIVE;
+            atomicMin(toi_min, (unsigned long long)__double_as_longlong(t));
+        }
+        if (kind == 0) st_vt[idx] = st; else st_ee[idx - nvt] = st;
+    }
+}
+
+// mode 0: collect active states; mode 1: partial CCD update then collect.
+__global__ void __launch_bounds__(PAIR_THREADS) k_pairs_update(CollView cv, const int2 *__restrict__ vt,
+                                                               const int2 *__restrict__ ee, const long long *nvt_p,
+                                                               const long long *nee_p, unsigned char *st_vt,
+                                                               unsigned char *st_ee, const float4 *__restrict__ xm,
+                                                               const float4 *__restrict__ xp, CollParams P, int mode,
+                                                               ActivePair *act, int cap, int *n_act, int *overflow) {
+    long long nvt = *nvt_p, n = nvt + *nee_p;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    long long start = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    for (long long base = start; base < n; base += stride) {  // warp-uniform trip count
+        long long idx = base + (threadIdx.x & 31);
+        bool want = false;
+        ActivePair ap;
+        if (idx < n) {
+            int ids[4], kind;
+            pair_ids(cv, vt, ee, nvt, idx, ids, kind);
+            unsigned char *stp = kind == 0 ? st_vt + idx : st_ee + (idx - nvt);
+            unsigned char st = *stp;
+            float4 a0[4];
+            for (int i = 0; i < 4; ++i) a0[i] = xm[ids[i]];
+            float c[4];
+            if (mode == 1) {
+                float4 a1[4];
+                for (int i = 0; i < 4; ++i) a1[i] = xp[ids[i]];
+                bool flag = partial_pair(kind, a0, a1, P.dhat, kind == 0 ? P.samples_vt : P.samples_ee, c);
+                if (flag) {
+                    int a = (st & ST_ACTIVE) ? min((int)(st & 0x7f) + 1, P.a_max) : 0;
+                    st = ST_ACTIVE | (unsigned char)a;
+                } else {
+                    st = 0;
+                }
+                *stp = st;
+            } else if (st & ST_ACTIVE) {
+                V<float> q[4];
+                for (int i = 0; i < 4; ++i) q[i] = ld<float>(a0[i]);
+                closest_coef<float>(kind, q, c);
+            }
+            if (st & ST_ACTIVE) {
+                want = true;
+                float3 n0 = start_dir(kind, a0, c);
+                ap.ids = make_int4(ids[0], ids[1], ids[2], ids[3]);
+                ap.c = make_float4(c[0], c[1], c[2], c[3]);
+                ap.n0w = make_float4(n0.x, n0.y, n0.z, ndb_weight(P, st & 0x7f));
+            }
+        }
+        append_active(want, ap, act, cap, n_act, overflow);
+    }
+}
+
+// Collision springs (Sec. 5.1, A_i = B_i = Id): constraint C(x) = d(x).n0 - dhat
+// with d = sum_j c_j x_j; the least-norm displacement restoring C = 0 moves
+// movable vertex j by -min(C,0) c_j n0 / sum_k c_k^2; every movable vertex
+// with c_j != 0 gets weight w toward its target.
+__global__ void k_contact(CollView cv, const ActivePair *__restrict__ act, const int *n_act_p, int cap,
+                          const float4 *__restrict__ x, float dhat, float *__restrict__ cw, float4 *__restrict__ cf) {
+    int n = min(*n_act_p, cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        ActivePair ap = act[i];
+        int ids[4] = {ap.ids.x, ap.ids.y, ap.ids.z, ap.ids.w};
+        float c[4] = {ap.c.x, ap.c.y, ap.c.z, ap.c.w};
+        float3 n0 = make_float3(ap.n0w.x, ap.n0w.y, ap.n0w.z);
+        float w = ap.n0w.w;
+        float3 d = make_float3(0.f, 0.f, 0.f);
+        float S = 0.f;
+        bool mv[4];
+        for (int j = 0; j < 4; ++j) {
+            d = d + c[j] * f3(x[ids[j]]);
+            mv[j] = c[j] != 0.f && !cv.vfixed[ids[j]];
+            if (mv[j]) S += c[j] * c[j];
+        }
+        if (!(S > 0.f)) continue;
+        float C = dot3(d, n0) - dhat;
+        float k = -fminf(C, 0.f) / S;
+        for (int j = 0; j < 4; ++j) {
+            if (!mv[j]) continue;
+            int v = ids[j];
+            atomicAdd(&cw[v], w);
+            float s = w * k * c[j];
+            if (s != 0.f) {
+                atomicAdd(&cf[v].x, s * n0.x);
+                atomicAdd(&cf[v].y, s * n0.y);
+                atomicAdd(&cf[v].z, s * n0.z);
+            }
+        }
+    }
+}
+
+__global__ void k_contact_list(int n, const float *__restrict__ cw, int *__restrict__ list, int *count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool want = i < n && cw[i] > 0.f;
+    unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) list[base + __popc(m & ((1u << lane) - 1u))] = i;
+}
+
+// ----------------------------------------------------------------- stage helpers
+__global__ void k_ccd_quads(const int4 *q, const int *kinds, long long np, const float4 *x0, const float4 *x1,
+                            double eta, double *toi) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (long long)gridDim.x * blockDim.x) {
+        int4 Q = q[i];
+        int ids[4] = {Q.x, Q.y, Q.z, Q.w};
+        float4 a0[4], a1[4];
+        for (int k = 0; k < 4; ++k) { a0[k] = x0[ids[k]]; a1[k] = x1[ids[k]]; }
+        toi[i] = ccd_pair(kinds[i], a0, a1, eta);
+    }
+}
+
+__global__ void k_partial_quads(const int4 *q, const int *kinds, long long np, const float4 *x0, const float4 *x1,
+                                CollParams P, int *active) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (long long)gridDim.x * blockDim.x) {
+        int4 Q = q[i];
+        int ids[4] = {Q.x, Q.y, Q.z, Q.w};
+        float4 a0[4], a1[4];
+        for (int k = 0; k < 4; ++k) { a0[k] = x0[ids[k]]; a1[k] = x1[ids[k]]; }
+        float c[4];
+        int kind = kinds[i];
+        active[i] = partial_pair(kind, a0, a1, P.dhat, kind == 0 ? P.samples_vt : P.samples_ee, c) ? 1 : 0;
+    }
+}
+
+__global__ void k_activate_quads(const int4 *q, const int *kinds, const float *w, long long np, const float4 *xm,
+                                 ActivePair *act, int *n_act) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (long long)gridDim.x * blockDim.x) {
+        int4 Q = q[i];
+        int ids[4] = {Q.x, Q.y, Q.z, Q.w};
+        float4 a0[4];
+        V<float> p[4];
+        for (int k = 0; k < 4; ++k) { a0[k] = xm[ids[k]]; p[k] = ld<float>(a0[k]); }
+        float c[4];
+        int kind = kinds[i];
+        closest_coef<float>(kind, p, c);
+        float3 n0 = start_dir(kind, a0, c);
+        ActivePair ap;
+        ap.ids = Q;
+        ap.c = make_float4(c[0], c[1], c[2], c[3]);
+        ap.n0w = make_float4(n0.x, n0.y, n0.z, w[i]);
+        act[i] = ap;
+        if (i == 0) *n_act = (int)np;
+    }
+}
+
+__global__ void k_pairs_to_quads(CollView cv, const int2 *ee, long long nee, int4 *out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nee; i += (long long)gridDim.x * blockDim.x) {
+        int2 p = ee[i];
+        int2 E = cv.edge[p.x], F = cv.edge[p.y];
+        out[i] = make_int4(E.x, E.y, F.x, F.y);
+    }
+}
+
+inline int nblk(long long n, int b) { return (int)std::min<long long>((n + b - 1) / b, 152LL * 16); }
+
+}  // namespace
+
+void launch_full_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *x0, const float4 *x1,
+                     const CollParams &P, bool merge, unsigned long long *toi_min) {
+    int c = bp.cur, o = c ^ 1;
+    k_full_ccd<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(
+        cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c], bp.st_vt[c], bp.st_ee[c], merge ? bp.vt[o].p : nullptr,
+        merge ? bp.ee[o].p : nullptr, bp.cnt_vt_d[o], bp.cnt_ee_d[o], bp.st_vt[o], bp.st_ee[o], x0, x1, P.eta, toi_min);
+    PDC_LAUNCH_CK();
+}
+
+void launch_collect_active(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm,
+                           const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow) {
+    int c = bp.cur;
+    PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
+    k_pairs_update<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
+                                                        bp.st_vt[c], bp.st_ee[c], xm, xm, P, 0, act, cap_act, n_act,
+                                                        overflow);
+    PDC_LAUNCH_CK();
+}
+
+void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm, const float4 *xp,
+                        const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow) {
+    int c = bp.cur;
+    PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
+    k_pairs_update<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
+                                                        bp.st_vt[c], bp.st_ee[c], xm, xp, P, 1, act, cap_act, n_act,
+                                                        overflow);
+    PDC_LAUNCH_CK();
+}
+
+void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, const int *n_act, int cap_act,
+                    const float4 *x, float dhat, float *cw, float4 *cf) {
+    k_contact<<<152 * 4, 256, 0, s>>>(cv, act, n_act, cap_act, x, dhat, cw, cf);
+    PDC_LAUNCH_CK();
+}
+
+void launch_contact_list(cudaStream_t s, int n, const float *cw, int *list, int *count) {
+    PDC_CK(cudaMemsetAsync(count, 0, sizeof(int), s));
+    if (n > 0) k_contact_list<<<(n + 255) / 256, 256, 0, s>>>(n, cw, list, count);
+    PDC_LAUNCH_CK();
+}
+
+void launch_ccd_quads(cudaStream_t s, const int4 *quads, const int *kinds, long long np, const float4 *x0,
+                      const float4 *x1, double eta, double *toi) {
+    if (np > 0) k_ccd_quads<<<nblk(np, 128), 128, 0, s>>>(quads, kinds, np, x0, x1, eta, toi);
+    PDC_LAUNCH_CK();
+}
+
+void launch_partial_quads(cudaStream_t s, const int4 *quads, const int *kinds, long long np, const float4 *x0,
+                          const float4 *x1, const CollParams &P, int *active) {
+    if (np > 0) k_partial_quads<<<nblk(np, 128), 128, 0, s>>>(quads, kinds, np, x0, x1, P, active);
+    PDC_LAUNCH_CK();
+}
+
+void launch_activate_quads(cudaStream_t s, const int4 *quads, const int *kinds, const float *w, long long np,
+                           const float4 *xm, ActivePair *act, int *n_act) {
+    PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
+    if (np > 0) k_activate_quads<<<nblk(np, 128), 128, 0, s>>>(quads, kinds, w, np, xm, act, n_act);
+    PDC_LAUNCH_CK();
+}
+
+void launch_pairs_to_quads(cudaStream_t s, const CollView &cv, const int2 *ee, long long nee, int4 *out) {
+    if (nee > 0) k_pairs_to_quads<<<nblk(nee, 256), 256, 0, s>>>(cv, ee, nee, out);
+    PDC_LAUNCH_CK();
+}
+
+}  // namespace pdc

@@ -1,0 +1,248 @@
+// Projective-dynamics kernels: inertial target, local projections fused with
+// the residual of the global system, Jacobi sweeps, line search.
+//
+// All vertex streams are float4 (16 B); one thread per vertex.  The
+// residual is formed in "force form": instead of assembling b and
+// subtracting H x (two large, nearly cancelling vectors), every element adds
+// its force w (target - current) directly, which is the same vector
+// r = b - (H + dH) x of Eq. (global) without the cancellation error.
+#include "pdc_internal.cuh"
+
+namespace pdc {
+
+namespace {
+
+__device__ inline float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline float warp_max(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum of one float, added (one atomic per block) into a double.
+__device__ inline void block_add(float v, double *dst) {
+    __shared__ float part[32];
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        float t = lane < nw ? part[lane] : 0.f;
+        t = warp_sum(t);
+        if (lane == 0 && t != 0.f) atomicAdd(dst, (double)t);
+    }
+}
+
+__device__ inline void block_max(float v, unsigned int *dst) {
+    __shared__ float part[32];
+    v = warp_max(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        float t = lane < nw ? part[lane] : 0.f;
+        t = warp_max(t);
+        if (lane == 0 && t > 0.f) atomicMax(dst, __float_as_uint(t));
+    }
+}
+
+// Closest 3x2 matrix with orthonormal columns to F = [f1 f2] (polar factor).
+// C = F^T F = [[a, b], [b, d]];  with s = sqrt(det C) and t = sqrt(tr C + 2s)
+// the inverse square root is C^{-1/2} = [[d + s, -b], [-b, a + s]] / (s t),
+// and R = F C^{-1/2}.  Nearly rank-deficient F: Gram-Schmidt of its columns.
+__device__ inline void polar32(float3 f1, float3 f2, float3 &r1, float3 &r2) {
+    float a = dot3(f1, f1), b = dot3(f1, f2), d = dot3(f2, f2);
+    float det = fmaf(a, d, -b * b);
+    float tr = a + d;
+    if (det > 1e-10f * tr * tr) {
+        float s = sqrtf(det);
+        float t = sqrtf(tr + 2.f * s);
+        float k = 1.f / (s * t);
+        float m00 = (d + s) * k, m01 = -b * k, m11 = (a + s) * k;
+        r1 = m00 * f1 + m01 * f2;
+        r2 = m01 * f1 + m11 * f2;
+        return;
+    }
+    float n1 = sqrtf(a);
+    float3 c1 = n1 > 1e-30f ? (1.f / n1) * f1 : make_float3(1.f, 0.f, 0.f);
+    float3 c2 = f2 - dot3(f2, c1) * c1;
+    float n2 = sqrtf(dot3(c2, c2));
+    if (n2 <= 1e-6f * fmaxf(n1, 1e-30f)) {
+        float ax = fabsf(c1.x), ay = fabsf(c1.y), az = fabsf(c1.z);
+        float3 e = (ax <= ay && ax <= az) ? make_float3(1, 0, 0) : (ay <= az ? make_float3(0, 1, 0) : make_float3(0, 0, 1));
+        c2 = e - dot3(e, c1) * c1;
+        n2 = sqrtf(dot3(c2, c2));
+    }
+    r1 = c1;
+    r2 = (1.f / n2) * c2;
+}
+
+__global__ void k_prologue(int n, const float4 *__restrict__ xs, const float4 *__restrict__ vs, float h, float3 g,
+                           float4 *__restrict__ z, float4 *__restrict__ x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float3 p = f3(xs[i]), v = f3(vs[i]);
+    float3 zz = p + h * v + (h * h) * g;   // Eq. (z), f_ext = m g
+    float4 o = f4(zz);
+    z[i] = o;
+    x[i] = o;
+}
+
+__global__ void k_set_pins(const int *__restrict__ pins, int np, const float4 *__restrict__ tgt, float4 *__restrict__ x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < np) x[pins[i]] = tgt[i];
+}
+
+// r_i = m_i/h^2 (z_i - x_i) + sum_t w_t (R_t - F_t) g_{t,i} + sum_h w_h K_{h,i} (s_hat_h - s_h) + cf_i
+__global__ void __launch_bounds__(256) k_residual(const ClothView c, const float4 *__restrict__ x,
+                                                  const float4 *__restrict__ z, const float *__restrict__ cw,
+                                                  const float4 *__restrict__ cf, float4 *__restrict__ r,
+                                                  Scalars *sc, float *__restrict__ r_soa, int soa_ld) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float sq = 0.f;
+    if (i < c.n) {
+        float3 f = make_float3(0.f, 0.f, 0.f);
+        if (c.is_free[i]) {
+            float3 xi = f3(x[i]);
+            f = c.mh2[i] * (f3(z[i]) - xi);
+            for (int e = c.vt_off[i]; e < c.vt_off[i + 1]; ++e) {
+                int ent = c.vt_list[e];
+                int t = ent >> 2, corner = ent & 3;
+                int4 T = c.tri[t];
+                float4 g = c.tri_g[t];
+                float w = c.tri_w[t];
+                float3 x0 = f3(x[T.x]);
+                float3 e1 = f3(x[T.y]) - x0, e2 = f3(x[T.z]) - x0;
+                float3 F1 = g.x * e1 + g.z * e2;   // column 1 of F = [e1 e2] Dm^-1
+                float3 F2 = g.y * e1 + g.w * e2;   // column 2
+                float3 R1, R2;
+                polar32(F1, F2, R1, R2);
+                float gx = corner == 0 ? -(g.x + g.z) : (corner == 1 ? g.x : g.z);
+                float gy = corner == 0 ? -(g.y + g.w) : (corner == 1 ? g.y : g.w);
+                f = f + w * (gx * (R1 - F1) + gy * (R2 - F2));
+            }
+            for (int e = c.vh_off[i]; e < c.vh_off[i + 1]; ++e) {
+                int ent = c.vh_list[e];
+                int hh = ent >> 2, slot = ent & 3;
+                int4 Hh = c.hin[hh];
+                float4 K = c.hin_K[hh];
+                float3 p0 = f3(x[Hh.x]);
+                float3 s = K.y * (f3(x[Hh.y]) - p0) + K.z * (f3(x[Hh.z]) - p0) + K.w * (f3(x[Hh.w]) - p0);
+                float sl = c.hin_slen[hh];
+                float3 sh;
+                float ns = sqrtf(dot3(s, s));
+                if (sl == 0.f) sh = make_float3(0.f, 0.f, 0.f);
+                else if (ns > 1e-30f) sh = (sl / ns) * s;
+                else sh = f3(c.hin_srest[hh]);
+                float ks = slot == 0 ? K.x : (slot == 1 ? K.y : (slot == 2 ? K.z : K.w));
+                f = f + (c.hin_w[hh] * ks) * (sh - s);
+            }
+            if (cf) f = f + f3(cf[i]);
+            sq = dot3(f, f);
+        }
+        r[i] = f4(f);
+        if (r_soa) {
+            r_soa[i] = f.x;
+            r_soa[soa_ld + i] = f.y;
+            r_soa[2 * soa_ld + i] = f.z;
+        }
+    }
+    if (sc) block_add(sq, &sc->rsq);
+}
+
+// One damped Jacobi sweep on (H + diag(cw)) delta = r:
+//   delta'_i = (1 - omega) delta_i + omega (r_i - sum_{j != i} H_ij delta_j) / (H_ii + cw_i)
+// If xout is given, also writes x + delta' and reduces max |delta'|.
+__global__ void __launch_bounds__(256) k_sweep(const ClothView c, const float *__restrict__ cw,
+                                               const float4 *__restrict__ r, const float4 *__restrict__ din,
+                                               float4 *__restrict__ dout, float omega,
+                                               const float4 *__restrict__ x, float4 *__restrict__ xout,
+                                               Scalars *sc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float mx = 0.f;
+    if (i < c.n) {
+        float3 dn = make_float3(0.f, 0.f, 0.f);
+        if (c.is_free[i]) {
+            float3 acc = f3(r[i]);
+            const int *col = c.ell_col + i;
+            const float *val = c.ell_val + i;
+            for (int k = 0; k < c.ell_w; ++k) {
+                float v = val[(size_t)k * c.n];
+                int j = col[(size_t)k * c.n];
+                acc = acc - v * f3(din[j]);
+            }
+            float D = c.hdiag[i] + (cw ? cw[i] : 0.f);
+            float3 di = f3(din[i]);
+            dn = (1.f - omega) * di + (omega / D) * acc;
+            mx = fmaxf(fabsf(dn.x), fmaxf(fabsf(dn.y), fabsf(dn.z)));
+        }
+        dout[i] = f4(dn);
+        if (xout) xout[i] = f4(f3(x[i]) + dn);
+    }
+    if (xout && sc) block_max(mx, &sc->dxmax);
+}
+
+__global__ void k_lerp(int nv, const float4 *__restrict__ a, const float4 *__restrict__ b, const double *s_frac,
+                       float4 *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    float s = (float)(*s_frac);
+    float3 p = f3(a[i]), q = f3(b[i]);
+    out[i] = f4(p + s * (q - p));
+}
+
+__global__ void k_velocity(int n, const float4 *__restrict__ xn, const float4 *__restrict__ xs, float inv_h,
+                           float4 *__restrict__ v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    v[i] = f4(inv_h * (f3(xn[i]) - f3(xs[i])));
+}
+
+inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+void launch_prologue(cudaStream_t s, int n, const float4 *xs, const float4 *vs, const int *pins, const float4 *pin_tgt,
+                     int npins, float h, float3 g, float4 *z, float4 *x) {
+    if (n > 0) k_prologue<<<nblk(n, 256), 256, 0, s>>>(n, xs, vs, h, g, z, x);
+    PDC_LAUNCH_CK();
+    if (npins > 0) {
+        k_set_pins<<<nblk(npins, 256), 256, 0, s>>>(pins, npins, pin_tgt, z);
+        k_set_pins<<<nblk(npins, 256), 256, 0, s>>>(pins, npins, pin_tgt, x);
+        PDC_LAUNCH_CK();
+    }
+}
+
+void launch_set_pins(cudaStream_t s, const int *pins, int npins, const float4 *tgt, float4 *x) {
+    if (npins > 0) k_set_pins<<<nblk(npins, 256), 256, 0, s>>>(pins, npins, tgt, x);
+    PDC_LAUNCH_CK();
+}
+
+void launch_residual(cudaStream_t s, const ClothView &c, const float4 *x, const float4 *z, const float *cw,
+                     const float4 *cf, float4 *r, Scalars *sc, float *r_soa, int soa_ld) {
+    (void)cw;
+    if (c.n > 0) k_residual<<<nblk(c.n, 256), 256, 0, s>>>(c, x, z, cw, cf, r, sc, r_soa, soa_ld);
+    PDC_LAUNCH_CK();
+}
+
+void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
+                  float4 *dout, float omega, const float4 *x, float4 *xout, Scalars *sc) {
+    if (c.n > 0) k_sweep<<<nblk(c.n, 256), 256, 0, s>>>(c, cw, r, din, dout, omega, x, xout, sc);
+    PDC_LAUNCH_CK();
+}
+
+void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out) {
+    if (nv > 0) k_lerp<<<nblk(nv, 256), 256, 0, s>>>(nv, a, b, s_frac, out);
+    PDC_LAUNCH_CK();
+}
+
+void launch_velocity(cudaStream_t s, int n, const float4 *xnew, const float4 *xs, float inv_h, float4 *v) {
+    if (n > 0) k_velocity<<<nblk(n, 256), 256, 0, s>>>(n, xnew, xs, inv_h, v);
+    PDC_LAUNCH_CK();
+}
+
+}  // namespace pdc

@@ -1,0 +1,344 @@
+// Subspace-reuse kernels (Sec. 5): projection g = U^T r, the collision
+// update of the reduced matrix (Eq. uu), the reduced solve and the lift
+// delta = U q (Eq. subspace_collision), plus the linear residual used when a
+// global solve runs several correction cycles.
+//
+// Reduced solves: without collision springs the reduced matrix U^T H U is
+// fixed and its inverse is precomputed (the explicit-inverse idea of the
+// paper's implementation section), so the solve is a matrix-vector product;
+// with springs the leading r_c x r_c block plus the SYRK update is factored
+// by Cholesky in one CTA.  Mixed form: FP64 inverse / factorisation; plain
+// form: FP32.
+#include "pdc_subspace.cuh"
+
+namespace pdc {
+
+namespace {
+
+__device__ inline int active_r(const SubspaceView &S, const int *n_cv) {
+    return (n_cv && *n_cv > 0) ? S.r_c : S.r_nc;
+}
+
+template <class TU> __device__ inline float tofloat(TU v);
+template <> __device__ inline float tofloat<float>(float v) { return v; }
+template <> __device__ inline float tofloat<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+constexpr int PROJ_T = 256;
+constexpr int PROJ_TILE = 256;
+constexpr int MAXC = 4;  // columns per thread (r <= 1024)
+
+// Partial projection of the block's row chunk: partial[b][j][c] = sum_i U[i][j] rl_i[c].
+template <class TU>
+__global__ void __launch_bounds__(PROJ_T) k_project(SubspaceView S, const TU *__restrict__ U,
+                                                    const float4 *__restrict__ rl, const int *n_cv,
+                                                    float *__restrict__ partial) {
+    __shared__ float4 s_r[PROJ_TILE];
+    __shared__ float s_red[PROJ_T * 3];
+    int r = active_r(S, n_cv);
+    if (r == 0) return;
+    int ncol = min(((r + 31) / 32) * 32, PROJ_T);
+    int nph = PROJ_T / ncol;
+    int tc = threadIdx.x % ncol, ph = threadIdx.x / ncol;
+    long long chunk = (S.n + gridDim.x - 1) / gridDim.x;
+    long long row0 = (long long)blockIdx.x * chunk, row1 = min(row0 + chunk, (long long)S.n);
+    float acc[MAXC][3];
+    for (int a = 0; a < MAXC; ++a) acc[a][0] = acc[a][1] = acc[a][2] = 0.f;
+    for (long long t0 = row0; t0 < row1; t0 += PROJ_TILE) {
+        int cnt = (int)min((long long)PROJ_TILE, row1 - t0);
+        __syncthreads();
+        if (threadIdx.x < cnt) s_r[threadIdx.x] = rl[t0 + threadIdx.x];
+        __syncthreads();
+        if (ph < nph) {
+            for (int k = ph; k < cnt; k += nph) {
+                float4 rv = s_r[k];
+                const TU *urow = U + (t0 + k) * (long long)S.ld;
+#pragma unroll
+                for (int a = 0; a < MAXC; ++a) {
+                    int j = tc + a * ncol;
+                    if (j < r) {
+                        float u = tofloat<TU>(urow[j]);
+                        acc[a][0] = fmaf(u, rv.x, acc[a][0]);
+                        acc[a][1] = fmaf(u, rv.y, acc[a][1]);
+                        acc[a][2] = fmaf(u, rv.z, acc[a][2]);
+                    }
+                }
+            }
+        }
+    }
+    // reduce over row phases
+    for (int a = 0; a < MAXC; ++a) {
+        int j = tc + a * ncol;
+        __syncthreads();
+        s_red[threadIdx.x * 3 + 0] = acc[a][0];
+        s_red[threadIdx.x * 3 + 1] = acc[a][1];
+        s_red[threadIdx.x * 3 + 2] = acc[a][2];
+        __syncthreads();
+        if (ph == 0 && j < r) {
+            float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+            for (int p = 0; p < nph; ++p) {
+                int t = p * ncol + tc;
+                v0 += s_red[t * 3 + 0];
+                v1 += s_red[t * 3 + 1];
+                v2 += s_red[t * 3 + 2];
+            }
+            float *o = partial + ((long long)blockIdx.x * S.ld + j) * 3;
+            o[0] = v0;
+            o[1] = v1;
+            o[2] = v2;
+        }
+    }
+}
+
+__global__ void k_project_reduce(SubspaceView S, const int *n_cv, int nblocks, const float *__restrict__ partial,
+                                 double *__restrict__ g) {
+    int r = active_r(S, n_cv);
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= r * 3) return;
+    int j = e / 3, c = e % 3;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += (double)partial[((long long)b * S.ld + j) * 3 + c];
+    g[j * 3 + c] = s;
+}
+
+// q = A0^-1 g without collision springs (one warp per row of the inverse).
+template <class T>
+__global__ void k_apply_inverse(SubspaceView S, const int *n_cv, const T *__restrict__ Ainv, const double *__restrict__ g,
+                                float *__restrict__ q) {
+    if (n_cv && *n_cv > 0) return;
+    int r = S.r_nc;
+    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= r) return;
+    T a0 = 0, a1 = 0, a2 = 0;
+    for (int k = lane; k < r; k += 32) {
+        T m = Ainv[(long long)w * r + k];
+        a0 += m * (T)g[k * 3 + 0];
+        a1 += m * (T)g[k * 3 + 1];
+        a2 += m * (T)g[k * 3 + 2];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (lane == 0) {
+        q[w * 3 + 0] = (float)a0;
+        q[w * 3 + 1] = (float)a1;
+        q[w * 3 + 2] = (float)a2;
+    }
+}
+
+// dA = sum_v cw_v U_v U_v^T over the contact list (leading r_c columns).
+constexpr int SYRK_T = 256;
+constexpr int SYRK_MAXE = 64;  // entries per thread: r_c^2 <= 256*64 -> r_c <= 128
+template <class TU>
+__global__ void __launch_bounds__(SYRK_T) k_syrk(SubspaceView S, const TU *__restrict__ U, const int *__restrict__ list,
+                                                 const int *n_cv, const float *__restrict__ cw, float *__restrict__ dA) {
+    __shared__ float s_u[128];
+    __shared__ float s_w;
+    int nc = n_cv ? *n_cv : 0;
+    int r = S.r_c;
+    if (nc == 0 || r == 0) return;
+    int ne = r * r;
+    float acc[SYRK_MAXE];
+#pragma unroll
+    for (int p = 0; p < SYRK_MAXE; ++p) acc[p] = 0.f;
+    for (int c = blockIdx.x; c < nc; c += gridDim.x) {
+        int v = list[c];
+        __syncthreads();
+        if (threadIdx.x < r) s_u[threadIdx.x] = tofloat<TU>(U[(long long)v * S.ld + threadIdx.x]);
+        if (threadIdx.x == 0) s_w = cw[v];
+        __syncthreads();
+        float w = s_w;
+#pragma unroll
+        for (int p = 0; p < SYRK_MAXE; ++p) {
+            int e = threadIdx.x + p * SYRK_T;
+            if (e < ne) {
+                int i = e / r, j = e % r;
+                acc[p] = fmaf(w * s_u[i], s_u[j], acc[p]);
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < SYRK_MAXE; ++p) {
+        int e = threadIdx.x + p * SYRK_T;
+        if (e < ne && acc[p] != 0.f) atomicAdd(&dA[e], acc[p]);
+    }
+}
+
+// Cholesky factorisation and solve of (A0[:r,:r] + dA) q = g in one CTA.
+template <class T>
+__global__ void __launch_bounds__(256) k_chol_solve(SubspaceView S, const int *n_cv, const float *__restrict__ dA,
+                                                    const double *__restrict__ g, float *__restrict__ q, int *flag) {
+    extern __shared__ unsigned char smem_raw[];
+    if (!(n_cv && *n_cv > 0)) return;
+    int r = S.r_c;
+    if (r == 0) return;
+    T *A = reinterpret_cast<T *>(smem_raw);  // [r][r]
+    T *b = A + r * r;                         // [r][3]
+    int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < r * r; e += nt) {
+        int i = e / r, j = e % r;
+        A[e] = (T)S.A0[(long long)i * S.ld + j] + (T)dA[e];
+    }
+    for (int e = tid; e < r * 3; e += nt) b[e] = (T)g[e];
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        if (tid == 0) {
+            T d = A[k * r + k];
+            if (!(d > (T)0)) {
+                atomicOr(flag, 1);
+                d = (T)1e-30;
+            }
+            A[k * r + k] = sqrt(d);
+        }
+        __syncthreads();
+        T dk = A[k * r + k];
+        for (int i = k + 1 + tid; i < r; i += nt) A[i * r + k] /= dk;
+        __syncthreads();
+        for (int i = k + 1 + tid; i < r; i += nt) {
+            T lik = A[i * r + k];
+            for (int j = k + 1; j <= i; ++j) A[i * r + j] -= lik * A[j * r + k];
+        }
+        __syncthreads();
+    }
+    // forward: L y = b
+    for (int k = 0; k < r; ++k) {
+        if (tid < 3) b[k * 3 + tid] /= A[k * r + k];
+        __syncthreads();
+        for (int e = tid; e < (r - k - 1) * 3; e += nt) {
+            int i = k + 1 + e / 3, c = e % 3;
+            b[i * 3 + c] -= A[i * r + k] * b[k * 3 + c];
+        }
+        __syncthreads();
+    }
+    // backward: L^T q = y
+    for (int k = r - 1; k >= 0; --k) {
+        if (tid < 3) b[k * 3 + tid] /= A[k * r + k];
+        __syncthreads();
+        for (int e = tid; e < k * 3; e += nt) {
+            int i = e / 3, c = e % 3;
+            b[i * 3 + c] -= A[k * r + i] * b[k * 3 + c];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < r * 3; e += nt) q[e] = (float)b[e];
+}
+
+// dout_i = din_i + sum_j U[i][j] q_j   (one warp per row)
+template <class TU>
+__global__ void __launch_bounds__(256) k_lift(SubspaceView S, const TU *__restrict__ U, const int *n_cv,
+                                              const float *__restrict__ q, const float4 *__restrict__ din,
+                                              float4 *__restrict__ dout) {
+    __shared__ float s_q[1024 * 3];
+    int r = active_r(S, n_cv);
+    for (int e = threadIdx.x; e < r * 3; e += blockDim.x) s_q[e] = q[e];
+    __syncthreads();
+    int lane = threadIdx.x & 31;
+    int wpb = blockDim.x >> 5;
+    for (long long i = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); i < S.n; i += (long long)gridDim.x * wpb) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        const TU *urow = U + i * S.ld;
+        for (int j = lane; j < r; j += 32) {
+            float u = tofloat<TU>(urow[j]);
+            a0 = fmaf(u, s_q[j * 3 + 0], a0);
+            a1 = fmaf(u, s_q[j * 3 + 1], a1);
+            a2 = fmaf(u, s_q[j * 3 + 2], a2);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (lane == 0) {
+            float4 d = din ? din[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            dout[i] = make_float4(d.x + a0, d.y + a1, d.z + a2, 0.f);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_linear_residual(ClothView c, const float *__restrict__ cw,
+                                                         const float4 *__restrict__ r, const float4 *__restrict__ d,
+                                                         float4 *__restrict__ rl) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.n) return;
+    float3 acc = make_float3(0.f, 0.f, 0.f);
+    if (c.is_free[i]) {
+        acc = f3(r[i]);
+        for (int k = 0; k < c.ell_w; ++k) {
+            float v = c.ell_val[(size_t)k * c.n + i];
+            int j = c.ell_col[(size_t)k * c.n + i];
+            acc = acc - v * f3(d[j]);
+        }
+        float D = c.hdiag[i] + (cw ? cw[i] : 0.f);
+        acc = acc - D * f3(d[i]);
+    }
+    rl[i] = f4(acc);
+}
+
+}  // namespace
+
+void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W) {
+    if (S.precision == 1)
+        k_project<__nv_bfloat16><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, S.U16, rl, n_cv, W.partial);
+    else
+        k_project<float><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, S.U32, rl, n_cv, W.partial);
+    int mx = S.ld * 3;
+    k_project_reduce<<<(mx + 127) / 128, 128, 0, s>>>(S, n_cv, PROJ_BLOCKS, W.partial, W.g);
+    PDC_LAUNCH_CK();
+}
+
+void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const int *n_cv, const float *cw,
+                 SubspaceWork &W) {
+    if (S.r_c == 0) return;
+    PDC_CK(cudaMemsetAsync(W.dA, 0, sizeof(float) * S.r_c * S.r_c, s));
+    if (S.precision == 1)
+        k_syrk<__nv_bfloat16><<<152, SYRK_T, 0, s>>>(S, S.U16, list, n_cv, cw, W.dA);
+    else
+        k_syrk<float><<<152, SYRK_T, 0, s>>>(S, S.U32, list, n_cv, cw, W.dA);
+    PDC_LAUNCH_CK();
+}
+
+void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv, SubspaceWork &W) {
+    if (S.r_nc > 0) {
+        int thr = S.r_nc * 32;
+        if (S.precision == 1)
+            k_apply_inverse<double><<<(thr + 255) / 256, 256, 0, s>>>(S, n_cv, S.A0inv, W.g, W.q);
+        else
+            k_apply_inverse<float><<<(thr + 255) / 256, 256, 0, s>>>(S, n_cv, S.A0inv32, W.g, W.q);
+    }
+    if (S.r_c > 0) {
+        if (S.precision == 1) {
+            size_t sm = sizeof(double) * (S.r_c * S.r_c + S.r_c * 3);
+            k_chol_solve<double><<<1, 256, sm, s>>>(S, n_cv, W.dA, W.g, W.q, W.flag);
+        } else {
+            size_t sm = sizeof(float) * (S.r_c * S.r_c + S.r_c * 3);
+            k_chol_solve<float><<<1, 256, sm, s>>>(S, n_cv, W.dA, W.g, W.q, W.flag);
+        }
+    }
+    PDC_LAUNCH_CK();
+}
+
+void launch_lift(cudaStream_t s, const SubspaceView &S, const int *n_cv, const SubspaceWork &W, const float4 *din,
+                 float4 *dout) {
+    int blocks = std::min((S.n + 7) / 8, 152 * 16);
+    if (blocks < 1) return;
+    if (S.precision == 1)
+        k_lift<__nv_bfloat16><<<blocks, 256, 0, s>>>(S, S.U16, n_cv, W.q, din, dout);
+    else
+        k_lift<float><<<blocks, 256, 0, s>>>(S, S.U32, n_cv, W.q, din, dout);
+    PDC_LAUNCH_CK();
+}
+
+void launch_linear_residual(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r,
+                            const float4 *delta, float4 *rl) {
+    if (c.n > 0) k_linear_residual<<<(c.n + 255) / 256, 256, 0, s>>>(c, cw, r, delta, rl);
+    PDC_LAUNCH_CK();
+}
+
+void set_chol_smem_limits() {
+    size_t mx = sizeof(double) * (128 * 128 + 128 * 3);
+    PDC_CK(cudaFuncSetAttribute(k_chol_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+    PDC_CK(cudaFuncSetAttribute(k_chol_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+}
+
+}  // namespace pdc

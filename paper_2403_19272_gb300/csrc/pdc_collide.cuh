@@ -1,0 +1,88 @@
+// Collision data structures and kernel entry points.
+#pragma once
+#include <algorithm>
+
+#include "pdc_internal.cuh"
+
+namespace pdc {
+
+enum OverflowBits { OVF_HASH = 1, OVF_VT = 2, OVF_EE = 4, OVF_ACTIVE = 8, OVF_CELLS = 16 };
+
+struct GridParams {
+    double ext_sum;  // sum over triangles of the largest swept-box extent
+    float cell, inv_cell;
+};
+
+// Collision settings shared by the pair kernels.
+struct CollParams {
+    float dhat;       // activity gap / contact target gap
+    double eta;       // exact-CCD contact distance
+    float k_ndb;      // initial weight k of Eq. (exp)
+    float K_ndb;      // growth base K
+    int a_max;        // cap of the life-span counter
+    int samples_vt;   // 0, 1, 3
+    int samples_ee;   // 0, 1, 4
+};
+
+// An active collision constraint: 4 collision-vertex ids, the gap-vector
+// coefficients c (p2 - p1 = sum_j c_j x_j at the t = 0 closest points), the
+// unit start direction n0 and the NDB weight w.
+struct ActivePair {
+    int4 ids;
+    float4 c;
+    float4 n0w;
+};
+
+// Pair state byte: bit 7 = active, bits 0..6 = life-span counter a.
+constexpr unsigned char ST_ACTIVE = 0x80;
+
+struct BroadPhase {
+    int nt = 0, ne = 0, nv = 0;
+    int T_vt = 0, T_ee = 0;
+    long long cap_ent = 0, cap_vt = 0, cap_ee = 0;
+    float cell_scale = 1.f;
+    DevBuf<int> bcnt[2], bstart[2], bfill[2];
+    DevBuf<unsigned long long> ekey[2];
+    DevBuf<int> eprim[2];
+    DevBuf<float4> tlo, thi, elo, ehi;
+    DevBuf<int> cnt_v, off_v, cnt_e, off_e, scratch;
+    DevBuf<GridParams> gp;
+    DevBuf<long long> totals;
+    // double-buffered candidate lists and NDB pair states
+    DevBuf<int2> vt[2], ee[2];
+    DevBuf<unsigned char> st_vt[2], st_ee[2];
+    DevBuf<long long> cnt_vt_d[2], cnt_ee_d[2];
+    int cur = 0;
+
+    void reserve(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent);
+    void run(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat, int *overflow);
+};
+
+// Exact CCD over the current lists; if merge, NDB states are carried over
+// from the previous lists (binary search by pair key), else start inactive.
+// Pairs with an impact in [0,1] become active.  toi_min: atomic min (double bits).
+void launch_full_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *x0, const float4 *x1,
+                     const CollParams &P, bool merge, unsigned long long *toi_min);
+// Rebuild the active list from the current states (closest points on xm).
+void launch_collect_active(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm,
+                           const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow);
+// Partial CCD over (xm, xp) on the current lists: update states, rebuild the active list.
+void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm, const float4 *xp,
+                        const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow);
+// Collision springs of the active list at positions x: cw += w, cf += w (y - x).
+void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, const int *n_act, int cap_act,
+                    const float4 *x, float dhat, float *cw, float4 *cf);
+// Compact the cloth vertices with cw > 0.
+void launch_contact_list(cudaStream_t s, int n, const float *cw, int *list, int *count);
+
+// Stage helpers on explicit quads (kinds: 0 VT, 1 EE).
+void launch_ccd_quads(cudaStream_t s, const int4 *quads, const int *kinds, long long np, const float4 *x0,
+                      const float4 *x1, double eta, double *toi);
+void launch_partial_quads(cudaStream_t s, const int4 *quads, const int *kinds, long long np, const float4 *x0,
+                          const float4 *x1, const CollParams &P, int *active);
+void launch_activate_quads(cudaStream_t s, const int4 *quads, const int *kinds, const float *w, long long np,
+                           const float4 *xm, ActivePair *act, int *n_act);
+// Broad-phase lists as vertex quads for the stage entry point.
+void launch_pairs_to_quads(cudaStream_t s, const CollView &cv, const int2 *ee, long long nee, int4 *out);
+
+}  // namespace pdc

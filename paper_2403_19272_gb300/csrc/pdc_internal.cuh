@@ -1,0 +1,155 @@
+// Internal declarations of the pdcloth CUDA library (sm_103a).
+//
+// Layout in HBM (one cloth of n vertices, m triangles, nh hinges):
+//   vertex streams   float4 (x, y, z, 0), 16 B per vertex: x*, v*, z, x,
+//                    x^-, residual r, Jacobi increments, contact force
+//   per-triangle     int4 ids, float4 (g1, g2) rows of Dm^-1, float weight
+//   per-hinge        int4 ids, float4 cotangent stencil K, weight, rest |s|
+//   vertex incidence CSR of (element << 2 | corner) for the gather residual
+//   rest matrix H    diagonal + ELL off-diagonals (column-major, width W)
+//   basis U          row-major [n][r_warm] (FP32 or BF16) + column-major copy
+//   collision set    cloth vertices then obstacle vertices; triangles and
+//                    edges likewise; broad-phase hash and pair lists
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/pdcloth.h"
+
+namespace pdc {
+
+// ---------------------------------------------------------------- errors
+struct Error : std::runtime_error {
+    pdc_status code;
+    Error(pdc_status c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define PDC_CK(call)                                                                                   \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            throw ::pdc::Error(PDC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_) +       \
+                                                 " (" __FILE__ ":" + std::to_string(__LINE__) + ")");   \
+    } while (0)
+
+#define PDC_LAUNCH_CK() PDC_CK(cudaGetLastError())
+
+// ---------------------------------------------------------------- device buffer
+template <class T> struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count) {
+        if (count == n && p) return;
+        release();
+        if (count == 0) return;
+        PDC_CK(cudaMalloc((void **)&p, count * sizeof(T)));
+        n = count;
+    }
+    void zero(cudaStream_t s) {
+        if (p) PDC_CK(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+    }
+    void upload(const T *h, size_t count, cudaStream_t s) {
+        alloc(count);
+        if (count) PDC_CK(cudaMemcpyAsync(p, h, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    void upload(const std::vector<T> &h, cudaStream_t s) { upload(h.data(), h.size(), s); }
+    void download(T *h, size_t count, cudaStream_t s) const {
+        if (count) PDC_CK(cudaMemcpyAsync(h, p, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    }
+    operator T *() const { return p; }
+};
+
+// ---------------------------------------------------------------- small vector math
+__host__ __device__ inline float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__host__ __device__ inline float4 f4(float3 a) { return make_float4(a.x, a.y, a.z, 0.f); }
+__host__ __device__ inline float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__host__ __device__ inline float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__host__ __device__ inline float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__host__ __device__ inline float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__host__ __device__ inline float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// ---------------------------------------------------------------- device views
+// Rest model of the cloth (read-only in the step kernels).
+struct ClothView {
+    int n, m, nh;
+    const int4 *tri;       // [m] (i0, i1, i2, 0)
+    const float4 *tri_g;   // [m] (g1.x, g1.y, g2.x, g2.y); g0 = -g1 - g2
+    const float *tri_w;    // [m] k_stretch * area
+    const int4 *hin;       // [nh] (x0, x1 | x2, x3)
+    const float4 *hin_K;   // [nh] cotangent stencil
+    const float *hin_w;    // [nh] 3 k_bend / (A_A + A_B)
+    const float *hin_slen; // [nh] |sum_j K_j X_j| at rest
+    const float4 *hin_srest; // [nh] rest stencil vector (fallback direction)
+    const int *vt_off;     // [n+1] triangle incidence
+    const int *vt_list;    // (t << 2) | corner
+    const int *vh_off;     // [n+1] hinge incidence
+    const int *vh_list;    // (h << 2) | slot
+    const float *mh2;      // [n] m / h^2
+    const float *hdiag;    // [n] diag(H)
+    const unsigned char *is_free; // [n]
+    int ell_w;
+    const int *ell_col;    // [ell_w][n]
+    const float *ell_val;  // [ell_w][n]
+};
+
+// Collision-set topology (cloth + obstacles).
+struct CollView {
+    int nv, nc;            // all vertices, cloth vertices
+    int nt, ne;            // all triangles, all edges
+    const int4 *tri;       // [nt]
+    const int2 *edge;      // [ne] (a < b)
+    const unsigned char *vfixed; // [nv] 1: infinite mass (obstacle or pinned)
+};
+
+// Scalars written by reductions (device).
+struct Scalars {
+    double rsq;            // sum of squared residual entries
+    unsigned int dxmax;    // max |delta| (float bits)
+    unsigned int pad0;
+    unsigned long long toi_min; // min time of impact (double bits, >= 0)
+    int n_active;          // active pairs appended this pass
+    int n_contact_v;       // contact vertices
+    int overflow;          // buffer overflow flags (bit mask)
+    int pad1;
+    long long n_vt, n_ee;  // candidate counts
+    long long n_hash;      // hash insertions
+};
+
+// ---------------------------------------------------------------- kernels (k_pd.cu)
+void launch_prologue(cudaStream_t s, int n, const float4 *xs, const float4 *vs, const int *pins, const float4 *pin_tgt,
+                     int npins, float h, float3 g, float4 *z, float4 *x);
+void launch_residual(cudaStream_t s, const ClothView &c, const float4 *x, const float4 *z, const float *cw,
+                     const float4 *cf, float4 *r, Scalars *sc, float *r_soa, int soa_ld);
+void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
+                  float4 *dout, float omega, const float4 *x, float4 *xout, Scalars *sc);
+void launch_line_search(cudaStream_t s, int nv_all, const float4 *xm, const float4 *xp, const double *s_frac,
+                        float4 *xout);
+void launch_velocity(cudaStream_t s, int n, const float4 *xnew, const float4 *xs, float inv_h, float4 *v);
+void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out);
+void launch_set_pins(cudaStream_t s, const int *pins, int npins, const float4 *tgt, float4 *x);
+
+// ---------------------------------------------------------------- kernels (k_collide.cu)
+struct BroadPhase;
+void bp_run(cudaStream_t s, BroadPhase &bp, const CollView &cv, const float4 *x0, const float4 *x1, float dhat,
+            Scalars *sc);
+void launch_ccd(cudaStream_t s, const CollView &cv, const int2 *vt, long long nvt, const int2 *ee, long long nee,
+                const float4 *x0, const float4 *x1, double eta, unsigned long long *toi_min, float *toi_out);
+
+}  // namespace pdc
