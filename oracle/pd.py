@@ -364,8 +364,10 @@ def contact_terms(cm: CollisionMesh, Xall0, xall, active, quads, kinds, weights,
     the constraint is C(x) = d(x).n0 - dhat >= 0.  Its projection moves each
     non-fixed vertex j by -min(C,0) c_j n0 / sum_k c_k^2 (sum over non-fixed
     k): the least-norm displacement that satisfies C = 0.  Every non-fixed
-    vertex with c_j != 0 gets a spring of weight w_i to its target, so the
-    per-vertex sums are  dH_jj = sum_i w_i  and  (w y)_j = sum_i w_i y_ij.
+    vertex of the pair gets a spring of weight w_i to its target (A_i = B_i =
+    Id on the pair's vertices; a vertex with c_j = 0 is held at its current
+    position), so the per-vertex sums are  dH_jj = sum_i w_i  and
+    (w y)_j = sum_i w_i y_ij.
     Returns (contact_w [n], contact_wy [n,3]) over cloth vertices."""
     n = cm.nc
     cw = np.zeros(n)
@@ -378,7 +380,7 @@ def contact_terms(cm: CollisionMesh, Xall0, xall, active, quads, kinds, weights,
         n0 = contact_normal(q0, kind, coef)
         qx = xall[q]
         C = float(coef @ qx @ n0) - dhat
-        movable = [(j, coef[j]) for j in range(4) if coef[j] != 0.0 and not cm.fixed_v[q[j]]]
+        movable = [(j, coef[j]) for j in range(4) if not cm.fixed_v[q[j]]]
         S = sum(c * c for _, c in movable)
         if S <= 0:
             continue

@@ -556,7 +556,7 @@ void pdc_ctx::setup_basis() {
     std::vector<float> U;
     std::vector<double> ritz;
     build_basis(s, cloth(), r, std::max(P.eig_iters, 0), P.seed, U, ritz);
-    install_basis(U, r);
+    install_basis(U, (int)(U.size() / n));
 }
 
 void pdc_ctx::ensure_topology() {
@@ -1264,6 +1264,7 @@ pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, con
     upload_f4(h, z, n, za);
     upload_contact(h, cw, cf);
     ClothView c = h->cloth();
+    if (h->dA.n < (size_t)std::max(r * r, 1)) h->dA.alloc((size_t)r * r);
     // the factorised path with the leading r columns: reduced matrix U^T (H + diag(cw)) U
     SubspaceView S = h->sub(0, r);
     SubspaceWork W = h->work();

@@ -311,7 +311,13 @@ void reduced_matrix(cudaStream_t s, const ClothView &c, const float *U, int ld, 
 void build_basis(cudaStream_t s, const ClothView &c, int r, int iters, uint64_t seed, std::vector<float> &U,
                  std::vector<double> &ritz) {
     int n = c.n;
+    std::vector<unsigned char> fr0(n);
+    PDC_CK(cudaMemcpyAsync(fr0.data(), c.is_free, n, cudaMemcpyDeviceToHost, s));
+    PDC_CK(cudaStreamSynchronize(s));
+    int nfree = (int)std::count(fr0.begin(), fr0.end(), 1);
     int m = ((r + std::max(16, r / 4)) + 31) / 32 * 32;
+    m = std::min(m, nfree);
+    if (r > m) r = m;
     Ctx cx(s, c, m);
     DevBuf<float> X, Y, Z, HX;
     size_t nm = (size_t)n * m;

@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs_update(CollView cv, cons
 // Collision springs (Sec. 5.1, A_i = B_i = Id): constraint C(x) = d(x).n0 - dhat
 // with d = sum_j c_j x_j; the least-norm displacement restoring C = 0 moves
 // movable vertex j by -min(C,0) c_j n0 / sum_k c_k^2; every movable vertex
-// with c_j != 0 gets weight w toward its target.
+// of the pair gets weight w toward its target (held in place when c_j = 0).
 __global__ void k_contact(CollView cv, const ActivePair *__restrict__ act, const int *n_act_p, int cap,
                           const float4 *__restrict__ x, float dhat, float *__restrict__ cw, float4 *__restrict__ cf) {
     int n = min(*n_act_p, cap);
@@ -452,7 +452,7 @@ __global__ void k_contact(CollView cv, const ActivePair *__restrict__ act, const
         bool mv[4];
         for (int j = 0; j < 4; ++j) {
             d = d + c[j] * f3(x[ids[j]]);
-            mv[j] = c[j] != 0.f && !cv.vfixed[ids[j]];
+            mv[j] = !cv.vfixed[ids[j]];
             if (mv[j]) S += c[j] * c[j];
         }
         if (!(S > 0.f)) continue;
