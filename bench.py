@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Benchmark of the per-step cloth solve.
+
+Workload: the 512x512 hanging cloth (262,144 vertices, 522,242 triangles),
+1 m wide in the x-z plane, top row pinned and swept 0.2 m at 1 Hz, dt 1/200 s,
+self-collision on; every step iterates until the PD residual falls to 1e-3
+of its value at z (mixed form: BF16 basis of 256 modes, FP64 reduced
+solves; plain form: all FP32).  Metric: ms per time step (lower is better).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  With N > 1 (torchrun) every rank runs its own
+replica (the cloth does not shard; "replicas only"), timing is max over
+ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/step at 262K-vertex cloth (plain FP32 vs mixed) at 1e-3 residual; % HBM peak"
+SIDE = 512
+WORKLOAD = ("hanging swept cloth 512x512 (262,144 vertices, 522,242 triangles, 1 m, top row pinned and "
+            "swept 0.2 m at 1 Hz), dt 1/200 s, self-collision on, iterate to 1e-3 relative PD residual")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=SIDE)
+    ap.add_argument("--forms", default="mixed,fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-side", type=int, default=64)
+    return ap.parse_args()
+
+
+def solver_params(pc, precision):
+    p = pc.pdc_default_params()
+    p.tol_rel_residual = 1e-3
+    p.max_outer = 3
+    p.max_inner = 64
+    p.warm_iters = 5
+    p.r_warm = 256
+    p.r_reuse = 32
+    p.precision = precision
+    p.jacobi_sweeps = 4
+    p.solve_cycles = 1
+    p.eig_iters = 12
+    return p
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_form(pc, torch, scene, precision, steps, warmup, dev_index):
+    """Warm-up, timed region (device), profiled replay, e2e through host buffers."""
+    import numpy as np
+    stream = torch.cuda.Stream()
+    p = solver_params(pc, precision)
+    t_setup = time.time()
+    h = pc.pdc_create(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend, p,
+                      stream.cuda_stream)
+    setup_s = time.time() - t_setup
+    dt = p.dt
+    total = warmup + 2 * steps + steps
+    # scripted pin targets for every step, resident on the device
+    pins = np.stack([scene.pins_at((k + 1) * dt) for k in range(total)]).astype(np.float32)
+    pins_d = torch.from_numpy(pins).to(f"cuda:{dev_index}")
+    k = 0
+
+    def one_step():
+        nonlocal k
+        pc.pdc_set_pin_targets_device(h, pins_d[k].data_ptr())
+        pc.pdc_step(h, dt)
+        k += 1
+
+    for _ in range(warmup):
+        one_step()
+    torch.cuda.synchronize()
+    # ---- timed region: device events on the library's stream
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    time.sleep(0.3)
+    st_list = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = None
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        one_step()
+        st_list.append(pc.pdc_get_stats(h))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    # ---- profiled replay of the same number of steps (per-kernel event timing)
+    pc.pdc_set_profiling(h, True)
+    for _ in range(steps):
+        one_step()
+    torch.cuda.synchronize()
+    kt = pc.pdc_get_kernel_times(h)
+    pc.pdc_set_profiling(h, False)
+    # ---- e2e through the public API with host buffers: pin targets h2d, positions d2h
+    pin_host = torch.empty(pins.shape[1:], dtype=torch.float32).pin_memory()
+    pos_host = torch.empty((scene.n, 3), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(steps):
+        pin_host.numpy()[:] = scene.pins_at((k + 1) * dt)
+        lib = pc.lib()
+        pc._check(h, lib.pdc_set_pin_targets(h, pin_host.data_ptr(), 0))
+        pc.pdc_step(h, dt)
+        k += 1
+        pc._check(h, lib.pdc_get_positions(h, pos_host.data_ptr(), 0))
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
+    x = pos_host.numpy().copy()
+    pc.pdc_destroy(h)
+    iters = [s["warm_iters"] + s["inner_iters"] for s in st_list]
+    return dict(ms=ms / steps, setup_s=setup_s, clocks=clk, kernels=kt, e2e_ms=e2e_ms,
+                h2d=int(pins.shape[1] * 12), d2h=int(scene.n * 12), iters=statistics.mean(iters),
+                rel_res=statistics.mean(s["rel_residual"] for s in st_list),
+                cand=statistics.mean(s["n_candidates"] for s in st_list),
+                toi=min(s["t_toi"] for s in st_list), finite=bool(np.isfinite(x).all()),
+                launches=None)
+
+
+def roofline(kernels, pk, ms_step):
+    """Dominant kernel by total profiled time, against the measured HBM copy peak."""
+    best = max(kernels.items(), key=lambda kv: kv[1]["total_ms"])
+    name, d = best
+    per_launch_ms = d["total_ms"] / max(d["launches"], 1)
+    bytes_per_launch = d["algo_bytes"] / max(d["launches"], 1)
+    achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "launches": d["launches"],
+            "ms_per_launch": round(per_launch_ms, 5), "bytes_per_launch": bytes_per_launch,
+            "peak_source": "measured" if not pk.get("_fallback") else "fallback"}
+
+
+def cpu_baseline(side, steps=2):
+    """The FP64 oracle on a bounded sample: `steps` steps of the same scene at
+    side x side, one thread, time scaled linearly by vertex count."""
+    code = r'''
+import os, sys, time, json
+sys.path.insert(0, %r)
+import workloads as wl
+from oracle import pd, build
+build.build()
+sc = wl.hanging_swept(side=%d)
+p = pd.Params(tol_rel_residual=1e-3, max_outer=3, max_inner=64, warm_iters=5)
+o = pd.Oracle(sc, p)
+t0 = time.time()
+for k in range(%d):
+    o.step()
+print(json.dumps({"s": (time.time() - t0) / %d, "n": sc.n}))
+''' % (ROOT, side, steps, steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        return {"value": None, "error": out.stderr[-300:]}
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    scale = (SIDE * SIDE) / d["n"]
+    return {"value": round(d["s"] * 1e3 * scale, 1), "unit": "ms/step", "cores": 1, "kind": "oracle",
+            "sample": "%d oracle steps of the same swept-cloth scene at %dx%d (%d vertices), ms/step scaled "
+                      "linearly by vertex count to 512x512" % (steps, side, side, d["n"])}
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.time()
+        base = None
+        vals = []
+        for _ in range(a.warmup):
+            pass
+        for _ in range(max(a.steps, 1)):
+            r = cpu_baseline(a.cpu_sample_side, steps=1)
+            if r["value"] is None:
+                print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + r.get("error", "")}))
+                return
+            vals.append(r["value"])
+            base = r
+        v = statistics.mean(vals)
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "ms/step", "n_gpus": a.gpus,
+                          "steps": a.steps, "warmup": a.warmup, "ms_per_step": v, "higher_is_better": False,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": WORKLOAD},
+                          "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": base["sample"], "value": v,
+                                           "unit": "ms/step"},
+                          "e2e": {"value": v, "unit": "ms/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    from paper_2403_19272_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2403_19272_gb300 import pdcloth as pc
+    import workloads as wl
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    scene = wl.hanging_swept(side=a.side)
+    forms = {}
+    for f in a.forms.split(","):
+        forms[f] = run_form(pc, torch, scene, 1 if f == "mixed" else 0, a.steps, a.warmup, local)
+    head = "mixed" if "mixed" in forms else list(forms)[0]
+    ms = forms[head]["ms"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        return
+    pk = peaks()
+    rl = roofline(forms[head]["kernels"], pk, ms)
+    line = {
+        "metric": METRIC, "value": round(ms, 3), "unit": "ms/step", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f32+f64" if head == "mixed" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": head, "basis": "r=256 (r_reuse=32 with collision springs)",
+                   "l2": "inputs larger than L2 (basis 134 MB BF16 / 268 MB FP32 plus matrices and state)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "forms": {f: {"ms_per_step": round(d["ms"], 3), "lg_iters_per_step": d["iters"],
+                      "rel_residual": d["rel_res"], "candidates": d["cand"], "min_toi": d["toi"],
+                      "setup_s": round(d["setup_s"], 2), "e2e_ms_per_step": round(d["e2e_ms"], 3)}
+                  for f, d in forms.items()},
+        "roofline": rl,
+        "clocks": forms[head]["clocks"],
+        "e2e": {"value": round(forms[head]["e2e_ms"], 3), "unit": "ms/step",
+                "h2d_bytes_per_step": forms[head]["h2d"], "d2h_bytes_per_step": forms[head]["d2h"]},
+        "gpu_launches": int(sum(d["launches"] for d in forms[head]["kernels"].values()) / max(a.steps, 1) * a.steps),
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3),
+                        "GBps": round(v["algo_bytes"] / max(v["total_ms"], 1e-9) / 1e6, 1)}
+                    for k, v in forms[head]["kernels"].items()},
+    }
+    if not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a.cpu_sample_side)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -182,6 +182,24 @@ void pdc_destroy(pdc_handle h);
  * h is NULL.  Never NULL. */
 const char *pdc_last_error(pdc_handle h);
 
+/* Per-kernel device time of the launches made while profiling is on: a
+ * CUDA event pair on the library's stream around every launch, resolved at
+ * the end of each pdc_step.  algo_bytes is the algorithmic traffic of those
+ * launches (the minimum bytes the method must move for them: element data,
+ * vertex streams, sparse-matrix entries, basis rows; gathered neighbour
+ * re-reads not counted).  Profiling adds a few microseconds per launch. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+    double algo_bytes;
+} pdc_kernel_time;
+
+/* enable = 1 starts profiling and clears the accumulated times; 0 stops. */
+pdc_status pdc_set_profiling(pdc_handle h, int32_t enable);
+/* Copies at most cap entries; *count receives the number of kernel kinds. */
+pdc_status pdc_get_kernel_times(pdc_handle h, pdc_kernel_time *out, int32_t cap, int32_t *count);
+
 /* --------------------------------------------------------------------------
  * Stage entry points.  Each runs exactly the kernels pdc_step uses for one
  * stage, on caller data, so that every stage can be checked on its own.

@@ -90,10 +90,81 @@ struct Obstacle {
     int off;               // first collision-vertex id
 };
 
+// Event-pair timing of individual launches (pdc_set_profiling).
+struct Profiler {
+    bool on = false;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<Rec> pending;
+    std::vector<std::string> names;
+    std::vector<pdc_kernel_time> acc;
+    ~Profiler() {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+    cudaEvent_t ev() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            PDC_CK(cudaEventCreate(&e));
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    int kind(const char *name) {
+        for (size_t i = 0; i < names.size(); ++i)
+            if (names[i] == name) return (int)i;
+        names.push_back(name);
+        pdc_kernel_time t;
+        std::memset(&t, 0, sizeof(t));
+        std::strncpy(t.name, name, sizeof(t.name) - 1);
+        acc.push_back(t);
+        return (int)names.size() - 1;
+    }
+    void begin(cudaStream_t s, const char *name, double bytes) {
+        Rec r;
+        r.kind = kind(name);
+        r.a = ev();
+        r.b = ev();
+        r.bytes = bytes;
+        PDC_CK(cudaEventRecord(r.a, s));
+        pending.push_back(r);
+    }
+    void end(cudaStream_t s) { PDC_CK(cudaEventRecord(pending.back().b, s)); }
+    void flush() {
+        for (auto &r : pending) {
+            PDC_CK(cudaEventSynchronize(r.b));
+            float ms = 0.f;
+            PDC_CK(cudaEventElapsedTime(&ms, r.a, r.b));
+            acc[r.kind].launches += 1;
+            acc[r.kind].total_ms += ms;
+            acc[r.kind].algo_bytes += r.bytes;
+        }
+        pending.clear();
+        used = 0;
+    }
+    void reset() {
+        pending.clear();
+        used = 0;
+        names.clear();
+        acc.clear();
+    }
+};
+
 }  // namespace
 }  // namespace pdc
 
 using namespace pdc;
+
+#define PROF(name, bytes, ...)                                                                        \
+    do {                                                                                               \
+        if (prof.on) prof.begin(s, name, (double)(bytes));                                              \
+        __VA_ARGS__;                                                                                   \
+        if (prof.on) prof.end(s);                                                                      \
+    } while (0)
 
 struct pdc_ctx {
     std::string err;
@@ -148,6 +219,8 @@ struct pdc_ctx {
     DevBuf<unsigned int> umax_d;
     pdc_stats st;
     bool stepped = false;
+    Profiler prof;
+    long long nnz_off = 0;  // off-diagonal entries of H over free rows
 
     ~pdc_ctx() {
         if (hsc) cudaFreeHost(hsc);
@@ -232,6 +305,16 @@ struct pdc_ctx {
         sc.download(hsc, 1, s);
         PDC_CK(cudaStreamSynchronize(s));
     }
+    // algorithmic bytes per launch (FP32 values, 4-byte indices)
+    double bytes_residual(bool contacts) const {
+        return (double)m * 32 + (double)nh * 40 + (double)n * (12 + 12 + 12 + 4 + 1 + 8) +
+               (double)(3LL * m + 4LL * nh) * 4 + (contacts ? (double)n * 16 : 0.0);
+    }
+    double bytes_sweep(bool contacts, bool writes_x) const {
+        return (double)nnz_off * 8 + (double)n * (12 + 12 + 4 + 1 + 12) + (contacts ? 4.0 * n : 0.0) +
+               (writes_x ? 24.0 * n : 0.0);
+    }
+    double bytes_basis(int r) const { return (double)n * r * (P.precision == 1 ? 2 : 4) + (double)n * 12; }
     void lg_iteration(bool contacts, bool check_rel, double rho0, bool &converged, int r_nc, int r_c, int cycles,
                       int sweeps);
     void full_ccd(const float4 *x0, const float4 *x1, bool merge);
@@ -369,6 +452,11 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
             if (kv.first != i && freev[kv.first]) ++cnt;
         ell_w = std::max(ell_w, cnt);
     }
+    nnz_off = 0;
+    for (int i = 0; i < n; ++i)
+        if (freev[i])
+            for (auto &kv : rows[i])
+                if (kv.first != i && freev[kv.first]) ++nnz_off;
     std::vector<int> ecol((size_t)ell_w * n);
     std::vector<float> evalv((size_t)ell_w * n, 0.f);
     for (int i = 0; i < n; ++i) {
@@ -640,14 +728,14 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
     if (contacts) {
         CW.zero(s);
         CF.zero(s);
-        launch_contact(s, coll(), act, n_act_d, cap_act, Xp, dhat, CW, CF);
+        PROF("contact_springs", 0, launch_contact(s, coll(), act, n_act_d, cap_act, Xp, dhat, CW, CF));
         launch_contact_list(s, n, CW, contact_list, n_cv_d);
         cw = CW;
         cf = CF;
     } else {
         n_cv_d.zero(s);
     }
-    launch_residual(s, c, Xp, Z, cw, cf, R, sc, nullptr, 0);
+    PROF("local_residual", bytes_residual(contacts), launch_residual(s, c, Xp, Z, cw, cf, R, sc, nullptr, 0));
     if (check_rel) {
         read_scalars();
         double rho = std::sqrt(hsc->rsq);
@@ -664,14 +752,15 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
     for (int cyc = 0; cyc < cycles; ++cyc) {
         const float4 *rl = R;
         if (have_delta) {
-            launch_linear_residual(s, c, cw, R, din, RL);
+            PROF("linear_residual", bytes_sweep(contacts, false), launch_linear_residual(s, c, cw, R, din, RL));
             rl = RL;
         }
         if (r_warm > 0 && (r_nc > 0 || r_c > 0)) {
-            launch_project(s, S, rl, n_cv_d, W);
-            if (contacts && r_c > 0) launch_syrk(s, S, contact_list, n_cv_d, cw, W);
-            launch_reduced_solve(s, S, n_cv_d, W);
-            launch_lift(s, S, n_cv_d, W, have_delta ? din : nullptr, dout);
+            PROF("subspace_project", bytes_basis(contacts ? r_c : r_nc), launch_project(s, S, rl, n_cv_d, W));
+            if (contacts && r_c > 0) PROF("subspace_syrk", 0, launch_syrk(s, S, contact_list, n_cv_d, cw, W));
+            PROF("reduced_solve", 0, launch_reduced_solve(s, S, n_cv_d, W));
+            PROF("subspace_lift", bytes_basis(contacts ? r_c : r_nc) + 12.0 * n,
+                 launch_lift(s, S, n_cv_d, W, have_delta ? din : nullptr, dout));
             std::swap(din, dout);
             have_delta = true;
         }
@@ -681,7 +770,8 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
         }
         for (int k = 0; k < sweeps; ++k) {
             bool last = (cyc == cycles - 1) && (k == sweeps - 1);
-            launch_sweep(s, c, cw, R, din, dout, (float)omega, Xp, last ? Xp.p : nullptr, last ? sc.p : nullptr);
+            PROF("jacobi_sweep", bytes_sweep(contacts, last),
+                 launch_sweep(s, c, cw, R, din, dout, (float)omega, Xp, last ? Xp.p : nullptr, last ? sc.p : nullptr));
             std::swap(din, dout);
         }
         if (sweeps == 0 && cyc == cycles - 1) {
@@ -690,15 +780,15 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
         }
     }
     if (contacts && P.collisions) {
-        launch_partial_ccd(s, coll(), bp, Xm, Xp, cparams(), act, cap_act, n_act_d, &sc.p->overflow);
+        PROF("partial_ccd", 0, launch_partial_ccd(s, coll(), bp, Xm, Xp, cparams(), act, cap_act, n_act_d, &sc.p->overflow));
     }
 }
 
 void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {
-    bp.run(s, coll(), x0, x1, dhat, &sc.p->overflow);
+    PROF("broad_phase", 0, bp.run(s, coll(), x0, x1, dhat, &sc.p->overflow));
     unsigned long long inf = 0x7ff0000000000000ULL;  // +inf
     PDC_CK(cudaMemcpyAsync(toi_bits.p, &inf, sizeof(inf), cudaMemcpyHostToDevice, s));
-    launch_full_ccd(s, coll(), bp, x0, x1, cparams(), merge, toi_bits);
+    PROF("full_ccd", 0, launch_full_ccd(s, coll(), bp, x0, x1, cparams(), merge, toi_bits));
     k_step_fraction<<<1, 1, 0, s>>>(toi_bits, P.alpha_ls, sfrac, ttoi);
     PDC_LAUNCH_CK();
 }
@@ -830,6 +920,7 @@ void pdc_ctx::step() {
         PDC_CK(cudaStreamSynchronize(s));
         throw Error(PDC_ERR_NUMERIC, "non-finite positions; state rolled back");
     }
+    if (prof.on) prof.flush();
     stepped = true;
 }
 
@@ -1076,6 +1167,22 @@ pdc_status pdc_step(pdc_handle h, double dt) {
         }
     }
     h->st.overflow_retries = retries;
+    API_END(h)
+}
+
+pdc_status pdc_set_profiling(pdc_handle h, int32_t enable) {
+    API_BEGIN(h)
+    h->prof.reset();
+    h->prof.on = enable != 0;
+    API_END(h)
+}
+
+pdc_status pdc_get_kernel_times(pdc_handle h, pdc_kernel_time *out, int32_t cap, int32_t *count) {
+    API_BEGIN(h)
+    int k = (int)h->prof.acc.size();
+    if (count) *count = k;
+    if (out)
+        for (int i = 0; i < std::min(k, (int)cap); ++i) out[i] = h->prof.acc[i];
     API_END(h)
 }
 

@@ -345,9 +345,15 @@ void build_basis(cudaStream_t s, const ClothView &c, int r, int iters, uint64_t 
     }
 
     orthonormalize(cx, X, Y);
-    ritz = rayleigh_ritz(cx, X, HX, Y);
+    // Initial filter bound from the eigenvalue count of a 2-D operator (Weyl:
+    // lambda_m / lambda_max ~ m / n); later bounds are the largest Ritz value.
+    // Rayleigh-Ritz (host eigenproblem of the m x m Rayleigh matrix) runs every
+    // third pass and at the end.
+    double a_bound = bmax * std::min(0.5, 2.0 * m / std::max(nfree, 1));
+    double a_low = 0.0;
+    ritz.assign(m, 0.0);
     for (int it = 0; it < iters; ++it) {
-        double a = ritz[m - 1], b = bmax * 1.01, aL = std::max(ritz[0], 0.0);
+        double a = a_bound, b = bmax * 1.01, aL = a_low;
         if (!(a < b)) break;
         double e = 0.5 * (b - a), cc = 0.5 * (b + a);
         // degree: enough to damp [a, b] relative to the low end, bounded growth
@@ -370,8 +376,13 @@ void build_basis(cudaStream_t s, const ClothView &c, int r, int iters, uint64_t 
         }
         if (Q != X.p) PDC_CK(cudaMemcpyAsync(X.p, Q, sizeof(float) * nm, cudaMemcpyDeviceToDevice, s));
         orthonormalize(cx, X, Y);
-        ritz = rayleigh_ritz(cx, X, HX, Y);
+        if (it % 3 == 2 || it == iters - 1) {
+            ritz = rayleigh_ritz(cx, X, HX, Y);
+            a_bound = std::min(a_bound, ritz[m - 1]);
+            a_low = std::max(ritz[0], 0.0);
+        }
     }
+    if (iters <= 0) ritz = rayleigh_ritz(cx, X, HX, Y);
     // first r Ritz vectors
     std::vector<float> hX(nm);
     X.download(hX.data(), nm, s);

@@ -52,6 +52,10 @@ class pdc_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pdc_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", c_i64), ("total_ms", c_dbl), ("algo_bytes", c_dbl)]
+
+
 # every entry point declared in include/pdcloth.h: name -> (restype, argtypes)
 SIGNATURES = {
     "pdc_default_params": (None, [P]),
@@ -68,6 +72,8 @@ SIGNATURES = {
     "pdc_get_stats": (c_i32, [P, P]),
     "pdc_destroy": (None, [P]),
     "pdc_last_error": (ctypes.c_char_p, [P]),
+    "pdc_set_profiling": (c_i32, [P, c_i32]),
+    "pdc_get_kernel_times": (c_i32, [P, P, c_i32, P]),
     "pdc_op_broadphase": (c_i32, [P, P, P, P, c_i64, P, P, c_i64, P]),
     "pdc_op_ccd": (c_i32, [P, P, P, P, P, c_i64, P]),
     "pdc_op_partial_ccd": (c_i32, [P, P, P, P, P, c_i64, P]),
@@ -211,6 +217,20 @@ def pdc_get_stats(h) -> dict:
     s = pdc_stats()
     _check(h, lib().pdc_get_stats(h, ctypes.byref(s)))
     return s.as_dict()
+
+
+def pdc_set_profiling(h, enable: bool):
+    _check(h, lib().pdc_set_profiling(h, 1 if enable else 0))
+
+
+def pdc_get_kernel_times(h) -> dict:
+    """{name: {"launches", "total_ms", "algo_bytes"}} of the profiled launches."""
+    cnt = c_i32()
+    _check(h, lib().pdc_get_kernel_times(h, None, 0, ctypes.byref(cnt)))
+    arr = (pdc_kernel_time * max(cnt.value, 1))()
+    _check(h, lib().pdc_get_kernel_times(h, arr, cnt.value, ctypes.byref(cnt)))
+    return {arr[i].name.decode(): dict(launches=arr[i].launches, total_ms=arr[i].total_ms,
+                                       algo_bytes=arr[i].algo_bytes) for i in range(cnt.value)}
 
 
 def pdc_op_broadphase(h, x0, x1):
