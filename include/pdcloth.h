@@ -104,6 +104,10 @@ typedef struct {
     int32_t fixed_iters;     /* 1: run exactly warm/max_outer/max_inner iterations */
     int32_t eig_iters;       /* filtered subspace iterations building the basis  */
     uint64_t seed;           /* seed of the basis start block                    */
+    int32_t accel;           /* 1: Chebyshev semi-iterative acceleration of the LG
+                                iterates (ignored when fixed_iters = 1)           */
+    double accel_rho;        /* spectral radius for accel; <= 0: estimated from the
+                                residual decay of the first iterations of a pass */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */

@@ -3,6 +3,8 @@
 #include <array>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -88,6 +90,50 @@ struct Obstacle {
     std::vector<float> V;  // rest verts
     std::vector<int> T;
     int off;               // first collision-vertex id
+};
+
+// Chebyshev semi-iterative acceleration of the LG iterates (Wang 2015, a
+// Jacobi-type PD accelerator the paper cites): after S plain iterations of a
+// pass, x_{k+1} = w_{k+1} (x_hat_{k+1} - x_{k-1}) + x_{k-1} with
+// w = 2 / (2 - rho^2) first and w_{k+1} = 4 / (4 - rho^2 w_k) after; rho is
+// the spectral radius of the plain iteration, estimated from the decay of the
+// measured residual over the plain iterations.  A residual jump restarts it.
+struct Accel {
+    bool on = false;
+    double rho_fixed = 0.0, rho = 0.0, w = 1.0;
+    int k = 0;
+    std::vector<double> hist;
+    static constexpr int S = 5;
+    void reset() {
+        k = 0;
+        w = 1.0;
+        hist.clear();
+    }
+    double next(double meas) {
+        if (!on) return 1.0;
+        if (!hist.empty() && meas > 1.5 * hist.back()) reset();
+        hist.push_back(meas);
+        if (k < S) {
+            ++k;
+            w = 1.0;
+            return 1.0;
+        }
+        if (k == S) {
+            if (rho_fixed > 0) {
+                rho = rho_fixed;
+            } else {
+                size_t n = hist.size();
+                double ratio = hist[n - 1] / std::max(hist[n - 4], 1e-300);
+                rho = std::pow(std::max(ratio, 1e-12), 1.0 / 3.0);
+                rho = std::min(std::max(rho, 0.3), 0.995);
+            }
+            w = 2.0 / (2.0 - rho * rho);
+        } else {
+            w = 4.0 / (4.0 - rho * rho * w);
+        }
+        ++k;
+        return w;
+    }
 };
 
 // Event-pair timing of individual launches (pdc_set_profiling).
@@ -205,7 +251,7 @@ struct pdc_ctx {
     int cap_act = 0;
     DevBuf<int> contact_list;
     // subspace
-    int r_warm = 0, r_reuse = 0;
+    int r_warm = 0, r_reuse = 0, ld = 0;
     DevBuf<float> U32, A0inv32, proj_partial, qbuf, dA;
     DevBuf<__nv_bfloat16> U16;
     DevBuf<double> A0, A0inv, gbuf;
@@ -220,7 +266,11 @@ struct pdc_ctx {
     pdc_stats st;
     bool stepped = false;
     Profiler prof;
+    Accel accel;
+    float last_dx = 0.f;
+    DevBuf<float4> Xacc;  // previous iterate for the accelerated update
     long long nnz_off = 0;  // off-diagonal entries of H over free rows
+    bool log = std::getenv("PDC_LOG") != nullptr;  // per-iteration residuals to stderr
 
     ~pdc_ctx() {
         if (hsc) cudaFreeHost(hsc);
@@ -265,7 +315,7 @@ struct pdc_ctx {
     SubspaceView sub(int r_nc, int r_c) const {
         SubspaceView S;
         S.n = n;
-        S.ld = r_warm;
+        S.ld = ld;
         S.r_nc = r_nc;
         S.r_c = r_c;
         S.U32 = U32;
@@ -479,33 +529,22 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
         }
     k_ndb = P.k_ndb_scale * (nf ? dsum / nf : 1.0);
 
-    // Jacobi damping: power iteration for the largest eigenvalue of D^-1 H
+    // Jacobi damping: omega < 2 / lambda_max(D^-1 H) keeps the sweep
+    // convergent; the Gershgorin bound max_i sum_j |H_ij| / H_ii bounds
+    // lambda_max from above (bending makes H far from diagonally dominant:
+    // lambda_max(D^-1 H) is about 3.5 on a 512 x 512 sheet).
     if (P.jacobi_omega > 0) {
         omega = P.jacobi_omega;
     } else {
-        std::vector<double> v(n), w(n);
-        for (int i = 0; i < n; ++i) v[i] = freev[i] ? 1.0 + 0.37 * std::sin(1.3 * i) : 0.0;
-        double lam = 1.0;
-        for (int it = 0; it < 60; ++it) {
-            double nrm = 0;
-            for (int i = 0; i < n; ++i) {
-                if (!freev[i]) {
-                    w[i] = 0;
-                    continue;
-                }
-                double acc = 0;
-                for (auto &kv : rows[i])
-                    if (freev[kv.first]) acc += kv.second * v[kv.first];
-                w[i] = acc / rows[i][i];
-                nrm += w[i] * w[i];
-            }
-            nrm = std::sqrt(nrm);
-            double vn = 0;
-            for (int i = 0; i < n; ++i) vn += v[i] * v[i];
-            lam = nrm / std::max(std::sqrt(vn), 1e-300);
-            for (int i = 0; i < n; ++i) v[i] = w[i] / std::max(nrm, 1e-300);
+        double gmax = 1.0;
+        for (int i = 0; i < n; ++i) {
+            if (!freev[i]) continue;
+            double sum = 0;
+            for (auto &kv : rows[i])
+                if (freev[kv.first]) sum += std::fabs(kv.second);
+            gmax = std::max(gmax, sum / rows[i][i]);
         }
-        omega = std::min(1.0, 1.8 / (lam * 1.05));
+        omega = std::min(1.0, 1.8 / gmax);
     }
     // gap
     if (P.d_hat > 0) {
@@ -572,6 +611,7 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
 
     R.alloc(n);
     RL.alloc(n);
+    Xacc.alloc(n);
     D0.alloc(n);
     D1.alloc(n);
     CF.alloc(n);
@@ -606,10 +646,12 @@ void pdc_ctx::install_basis(const std::vector<float> &U, int r) {
     r_reuse = std::min(std::max(P.r_reuse, 0), r);
     if (r_reuse > 128) throw Error(PDC_ERR_ARG, "r_reuse must be <= 128");
     if (r > 1024) throw Error(PDC_ERR_ARG, "basis size must be <= 1024");
-    std::vector<float> Uz(U);
+    // rows padded to a multiple of 8 columns: 16-byte aligned vector loads
+    ld = (r + 7) / 8 * 8;
+    std::vector<float> Uz((size_t)n * ld, 0.f);
     for (int i = 0; i < n; ++i)
-        if (!freev[i])
-            for (int j = 0; j < r; ++j) Uz[(size_t)i * r + j] = 0.f;
+        if (freev[i])
+            for (int j = 0; j < r; ++j) Uz[(size_t)i * ld + j] = U[(size_t)i * r + j];
     if (P.precision == 1) {
         // round to BF16; the reduced matrix is formed from the rounded basis
         std::vector<__nv_bfloat16> ub(Uz.size());
@@ -620,17 +662,19 @@ void pdc_ctx::install_basis(const std::vector<float> &U, int r) {
         U16.upload(ub, s);
     }
     U32.upload(Uz, s);
-    std::vector<double> A0h;
-    reduced_matrix(s, cloth(), U32, r, A0h);
-    std::vector<double> Ainv;
-    spd_inverse(A0h, r, Ainv);
+    std::vector<double> A0h;  // [ld][ld], zero padding rows / columns
+    reduced_matrix(s, cloth(), U32, ld, A0h);
+    std::vector<double> A0r((size_t)r * r), Ainv;
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < r; ++j) A0r[(size_t)i * r + j] = A0h[(size_t)i * ld + j];
+    spd_inverse(A0r, r, Ainv);
     A0.upload(A0h, s);
     A0inv.upload(Ainv, s);
     std::vector<float> Ainv32(Ainv.begin(), Ainv.end());
     A0inv32.upload(Ainv32, s);
-    proj_partial.alloc((size_t)PROJ_BLOCKS * r * 3);
-    gbuf.alloc((size_t)r * 3);
-    qbuf.alloc((size_t)r * 3);
+    proj_partial.alloc((size_t)PROJ_BLOCKS * ld * 3);
+    gbuf.alloc((size_t)ld * 3);
+    qbuf.alloc((size_t)ld * 3);
     dA.alloc((size_t)std::max(r_reuse * r_reuse, 1));
     PDC_CK(cudaStreamSynchronize(s));
 }
@@ -736,8 +780,13 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
         n_cv_d.zero(s);
     }
     PROF("local_residual", bytes_residual(contacts), launch_residual(s, c, Xp, Z, cw, cf, R, sc, nullptr, 0));
-    if (check_rel) {
+    bool acc = accel.on && !(P.fixed_iters != 0);
+    if (check_rel || log || acc) {
         read_scalars();
+        double rho = std::sqrt(hsc->rsq);
+        if (log) std::fprintf(stderr, "[pdc] lg contacts=%d rho=%.6g rel=%.6g\n", (int)contacts, rho, rho / std::max(rho0, 1e-300));
+    }
+    if (check_rel) {
         double rho = std::sqrt(hsc->rsq);
         st.rel_residual = rho / std::max(rho0, 1e-300);
         if (rho <= P.tol_rel_residual * rho0) {
@@ -745,6 +794,8 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             return;
         }
     }
+    float w_acc = acc ? (float)accel.next(std::sqrt(hsc->rsq)) : 1.f;
+    float4 *xprev = acc ? Xacc.p : nullptr;
     SubspaceView S = sub(r_nc, r_c);
     SubspaceWork W = work();
     float4 *din = D0, *dout = D1;
@@ -771,12 +822,13 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
         for (int k = 0; k < sweeps; ++k) {
             bool last = (cyc == cycles - 1) && (k == sweeps - 1);
             PROF("jacobi_sweep", bytes_sweep(contacts, last),
-                 launch_sweep(s, c, cw, R, din, dout, (float)omega, Xp, last ? Xp.p : nullptr, last ? sc.p : nullptr));
+                 launch_sweep(s, c, cw, R, din, dout, (float)omega, Xp, last ? Xp.p : nullptr, last ? sc.p : nullptr,
+                              last ? xprev : nullptr, w_acc));
             std::swap(din, dout);
         }
         if (sweeps == 0 && cyc == cycles - 1) {
             // no sweep: apply the correction directly
-            launch_sweep(s, c, cw, R, din, dout, 0.f, Xp, Xp.p, sc.p);
+            launch_sweep(s, c, cw, R, din, dout, 0.f, Xp, Xp.p, sc.p, xprev, w_acc);
         }
     }
     if (contacts && P.collisions) {
@@ -819,9 +871,13 @@ void pdc_ctx::step() {
     read_scalars();
     double rho0 = std::sqrt(hsc->rsq);
     st.rho0 = rho0;
+    if (log) std::fprintf(stderr, "[pdc] step n=%d omega=%.4f rho0=%.6g dhat=%.3g k=%.4g\n", n, omega, rho0, dhat, k_ndb);
     const double tolx_in = P.tol_inner * L, tolx_out = P.tol_outer * L;
 
     // ---- warm start: LG iterations of I + Psi in span(U) + sweeps
+    accel.on = P.accel != 0 && !fixed;
+    accel.rho_fixed = P.accel_rho;
+    accel.reset();
     for (int it = 0; it < P.warm_iters; ++it) {
         bool conv = false;
         lg_iteration(false, relmode, rho0, conv, r_warm, 0, cycles, sweeps);
@@ -850,6 +906,7 @@ void pdc_ctx::step() {
         PDC_LAUNCH_CK();
         for (int o = 0; o < P.max_outer; ++o) {
             st.outer_iters++;
+            accel.reset();  // the constraint set changed (full CCD)
             int inner = 0;
             for (int it = 0; it < P.max_inner; ++it) {
                 bool conv = false;
@@ -903,7 +960,7 @@ void pdc_ctx::step() {
     st.n_active = nact;
     st.n_contact_vertices = ncv;
     if (P.collisions) {
-        st.t_toi = tt;
+        st.t_toi = tt <= 1.0 ? tt : 2.0;
         st.s_line_search = sf;
     }
     st.ms_step = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -973,6 +1030,8 @@ void pdc_default_params(pdc_params *p) {
     p->fixed_iters = 0;
     p->eig_iters = 12;
     p->seed = 12345;
+    p->accel = 0;
+    p->accel_rho = 0.0;
 }
 
 pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const pdc_params *params, void *stream,
@@ -1134,9 +1193,16 @@ pdc_status pdc_set_basis(pdc_handle h, const float *U, int32_t r) {
 pdc_status pdc_get_basis(pdc_handle h, float *U, double *A0) {
     API_BEGIN(h)
     if (h->r_warm == 0) throw Error(PDC_ERR_STATE, "pdc_get_basis: no basis");
-    if (U) h->U32.download(U, (size_t)h->n * h->r_warm, h->s);
-    if (A0) h->A0.download(A0, (size_t)h->r_warm * h->r_warm, h->s);
+    int r = h->r_warm, ld = h->ld;
+    std::vector<float> Uh((size_t)h->n * ld);
+    std::vector<double> Ah((size_t)ld * ld);
+    h->U32.download(Uh.data(), Uh.size(), h->s);
+    h->A0.download(Ah.data(), Ah.size(), h->s);
     PDC_CK(cudaStreamSynchronize(h->s));
+    for (int i = 0; i < h->n && U; ++i)
+        for (int j = 0; j < r; ++j) U[(size_t)i * r + j] = Uh[(size_t)i * ld + j];
+    for (int i = 0; i < r && A0; ++i)
+        for (int j = 0; j < r; ++j) A0[(size_t)i * r + j] = Ah[(size_t)i * ld + j];
     API_END(h)
 }
 

@@ -12,6 +12,8 @@
 // matrix (cyclic Jacobi rotations).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 #include "pdc_subspace.cuh"
 
@@ -380,6 +382,9 @@ void build_basis(cudaStream_t s, const ClothView &c, int r, int iters, uint64_t 
             ritz = rayleigh_ritz(cx, X, HX, Y);
             a_bound = std::min(a_bound, ritz[m - 1]);
             a_low = std::max(ritz[0], 0.0);
+            if (std::getenv("PDC_LOG"))
+                std::fprintf(stderr, "[pdc] basis pass %d deg %d ritz[0]=%.5g ritz[r-1]=%.5g ritz[m-1]=%.5g bmax=%.5g\n", it,
+                             deg, ritz[0], ritz[r - 1], ritz[m - 1], bmax);
         }
     }
     if (iters <= 0) ritz = rayleigh_ritz(cx, X, HX, Y);

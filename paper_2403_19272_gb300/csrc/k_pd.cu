@@ -156,11 +156,13 @@ __global__ void __launch_bounds__(256) k_residual(const ClothView c, const float
 
 // One damped Jacobi sweep on (H + diag(cw)) delta = r:
 //   delta'_i = (1 - omega) delta_i + omega (r_i - sum_{j != i} H_ij delta_j) / (H_ii + cw_i)
-// If xout is given, also writes x + delta' and reduces max |delta'|.
+// If xout is given, also writes the new iterate and reduces max |x_new - x|:
+//   x_new = x + delta'                                   (xprev == NULL), or
+//   x_new = w (x + delta' - xprev) + xprev, xprev <- x   (Chebyshev step, weight w)
 __global__ void __launch_bounds__(256) k_sweep(const ClothView c, const float *__restrict__ cw,
                                                const float4 *__restrict__ r, const float4 *__restrict__ din,
                                                float4 *__restrict__ dout, float omega,
-                                               const float4 *__restrict__ x, float4 *__restrict__ xout,
+                                               const float4 *x, float4 *xout, float4 *xprev, float w_acc,
                                                Scalars *sc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float mx = 0.f;
@@ -178,10 +180,22 @@ __global__ void __launch_bounds__(256) k_sweep(const ClothView c, const float *_
             float D = c.hdiag[i] + (cw ? cw[i] : 0.f);
             float3 di = f3(din[i]);
             dn = (1.f - omega) * di + (omega / D) * acc;
-            mx = fmaxf(fabsf(dn.x), fmaxf(fabsf(dn.y), fabsf(dn.z)));
         }
         dout[i] = f4(dn);
-        if (xout) xout[i] = f4(f3(x[i]) + dn);
+        if (xout) {
+            float3 xo = f3(x[i]);
+            float3 xn = xo + dn;
+            if (xprev) {
+                if (c.is_free[i]) {
+                    float3 xp = f3(xprev[i]);
+                    xn = xp + w_acc * (xn - xp);
+                }
+                xprev[i] = f4(xo);
+            }
+            xout[i] = f4(xn);
+            float3 d = xn - xo;
+            mx = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z)));
+        }
     }
     if (xout && sc) block_max(mx, &sc->dxmax);
 }
@@ -230,8 +244,9 @@ void launch_residual(cudaStream_t s, const ClothView &c, const float4 *x, const 
 }
 
 void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
-                  float4 *dout, float omega, const float4 *x, float4 *xout, Scalars *sc) {
-    if (c.n > 0) k_sweep<<<nblk(c.n, 256), 256, 0, s>>>(c, cw, r, din, dout, omega, x, xout, sc);
+                  float4 *dout, float omega, const float4 *x, float4 *xout, Scalars *sc, float4 *xprev,
+                  float w_acc) {
+    if (c.n > 0) k_sweep<<<nblk(c.n, 256), 256, 0, s>>>(c, cw, r, din, dout, omega, x, xout, xprev, w_acc, sc);
     PDC_LAUNCH_CK();
 }
 

@@ -9,6 +9,8 @@
 // with springs the leading r_c x r_c block plus the SYRK update is factored
 // by Cholesky in one CTA.  Mixed form: FP64 inverse / factorisation; plain
 // form: FP32.
+#include <algorithm>
+
 #include "pdc_subspace.cuh"
 
 namespace pdc {
@@ -24,67 +26,81 @@ template <> __device__ inline float tofloat<float>(float v) { return v; }
 template <> __device__ inline float tofloat<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 constexpr int PROJ_T = 256;
-constexpr int PROJ_TILE = 256;
-constexpr int MAXC = 4;  // columns per thread (r <= 1024)
+constexpr int PROJ_W = PROJ_T / 32;  // warps per block
 
-// Partial projection of the block's row chunk: partial[b][j][c] = sum_i U[i][j] rl_i[c].
-template <class TU>
+// 8 consecutive basis entries of one row as floats (one 16-byte load for
+// BF16, two for FP32).  Requires 16-byte aligned rows (ld % 8 == 0).
+__device__ inline void load8(const __nv_bfloat16 *p, float u[8]) {
+    uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float2 f = __bfloat1622float2(h[k]);
+        u[2 * k] = f.x;
+        u[2 * k + 1] = f.y;
+    }
+}
+__device__ inline void load8(const float *p, float u[8]) {
+    float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
+    u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
+}
+
+// Partial projection partial[b][j][c] = sum_{rows i of block b} U[i][j] rl_i[c].
+// One warp per row, lane l owns columns 8l..8l+7 of each 256-column chunk;
+// NCH chunks cover r <= 256*NCH.  The warps of a block reduce in shared memory.
+template <class TU, int NCH>
 __global__ void __launch_bounds__(PROJ_T) k_project(SubspaceView S, const TU *__restrict__ U,
                                                     const float4 *__restrict__ rl, const int *n_cv,
                                                     float *__restrict__ partial) {
-    __shared__ float4 s_r[PROJ_TILE];
-    __shared__ float s_red[PROJ_T * 3];
+    __shared__ float s_acc[PROJ_W][256 * 3];
     int r = active_r(S, n_cv);
     if (r == 0) return;
-    int ncol = min(((r + 31) / 32) * 32, PROJ_T);
-    int nph = PROJ_T / ncol;
-    int tc = threadIdx.x % ncol, ph = threadIdx.x / ncol;
-    long long chunk = (S.n + gridDim.x - 1) / gridDim.x;
-    long long row0 = (long long)blockIdx.x * chunk, row1 = min(row0 + chunk, (long long)S.n);
-    float acc[MAXC][3];
-    for (int a = 0; a < MAXC; ++a) acc[a][0] = acc[a][1] = acc[a][2] = 0.f;
-    for (long long t0 = row0; t0 < row1; t0 += PROJ_TILE) {
-        int cnt = (int)min((long long)PROJ_TILE, row1 - t0);
-        __syncthreads();
-        if (threadIdx.x < cnt) s_r[threadIdx.x] = rl[t0 + threadIdx.x];
-        __syncthreads();
-        if (ph < nph) {
-            for (int k = ph; k < cnt; k += nph) {
-                float4 rv = s_r[k];
-                const TU *urow = U + (t0 + k) * (long long)S.ld;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float acc[NCH][8][3];
 #pragma unroll
-                for (int a = 0; a < MAXC; ++a) {
-                    int j = tc + a * ncol;
-                    if (j < r) {
-                        float u = tofloat<TU>(urow[j]);
-                        acc[a][0] = fmaf(u, rv.x, acc[a][0]);
-                        acc[a][1] = fmaf(u, rv.y, acc[a][1]);
-                        acc[a][2] = fmaf(u, rv.z, acc[a][2]);
-                    }
+    for (int c = 0; c < NCH; ++c)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[c][k][0] = acc[c][k][1] = acc[c][k][2] = 0.f;
+    long long gw = (long long)blockIdx.x * PROJ_W + w, nw = (long long)gridDim.x * PROJ_W;
+    for (long long i = gw; i < S.n; i += nw) {
+        float4 rv = __ldg(rl + i);
+        const TU *row = U + i * S.ld;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            int j0 = c * 256 + lane * 8;
+            if (j0 < r) {
+                float u[8];
+                load8(row + j0, u);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    acc[c][k][0] = fmaf(u[k], rv.x, acc[c][k][0]);
+                    acc[c][k][1] = fmaf(u[k], rv.y, acc[c][k][1]);
+                    acc[c][k][2] = fmaf(u[k], rv.z, acc[c][k][2]);
                 }
             }
         }
     }
-    // reduce over row phases
-    for (int a = 0; a < MAXC; ++a) {
-        int j = tc + a * ncol;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
         __syncthreads();
-        s_red[threadIdx.x * 3 + 0] = acc[a][0];
-        s_red[threadIdx.x * 3 + 1] = acc[a][1];
-        s_red[threadIdx.x * 3 + 2] = acc[a][2];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int j = lane * 8 + k;
+            s_acc[w][j * 3 + 0] = acc[c][k][0];
+            s_acc[w][j * 3 + 1] = acc[c][k][1];
+            s_acc[w][j * 3 + 2] = acc[c][k][2];
+        }
         __syncthreads();
-        if (ph == 0 && j < r) {
-            float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-            for (int p = 0; p < nph; ++p) {
-                int t = p * ncol + tc;
-                v0 += s_red[t * 3 + 0];
-                v1 += s_red[t * 3 + 1];
-                v2 += s_red[t * 3 + 2];
+        for (int e = threadIdx.x; e < 256 * 3; e += PROJ_T) {
+            int j = c * 256 + e / 3;
+            if (j < r) {
+                float v = 0.f;
+#pragma unroll
+                for (int q = 0; q < PROJ_W; ++q) v += s_acc[q][e];
+                partial[((long long)blockIdx.x * S.ld + j) * 3 + e % 3] = v;
             }
-            float *o = partial + ((long long)blockIdx.x * S.ld + j) * 3;
-            o[0] = v0;
-            o[1] = v1;
-            o[2] = v2;
         }
     }
 }
@@ -224,25 +240,35 @@ __global__ void __launch_bounds__(256) k_chol_solve(SubspaceView S, const int *n
     for (int e = tid; e < r * 3; e += nt) q[e] = (float)b[e];
 }
 
-// dout_i = din_i + sum_j U[i][j] q_j   (one warp per row)
-template <class TU>
+// dout_i = din_i + sum_j U[i][j] q_j: one warp per row, lane l owns columns
+// 8l..8l+7 of each 256-column chunk, warp-shuffle reduction of the 3 sums.
+template <class TU, int NCH>
 __global__ void __launch_bounds__(256) k_lift(SubspaceView S, const TU *__restrict__ U, const int *n_cv,
                                               const float *__restrict__ q, const float4 *__restrict__ din,
                                               float4 *__restrict__ dout) {
-    __shared__ float s_q[1024 * 3];
+    __shared__ float s_q[256 * NCH * 3];
     int r = active_r(S, n_cv);
-    for (int e = threadIdx.x; e < r * 3; e += blockDim.x) s_q[e] = q[e];
+    for (int e = threadIdx.x; e < 256 * NCH * 3; e += blockDim.x) s_q[e] = e < r * 3 ? q[e] : 0.f;
     __syncthreads();
     int lane = threadIdx.x & 31;
     int wpb = blockDim.x >> 5;
     for (long long i = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); i < S.n; i += (long long)gridDim.x * wpb) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        const TU *urow = U + i * S.ld;
-        for (int j = lane; j < r; j += 32) {
-            float u = tofloat<TU>(urow[j]);
-            a0 = fmaf(u, s_q[j * 3 + 0], a0);
-            a1 = fmaf(u, s_q[j * 3 + 1], a1);
-            a2 = fmaf(u, s_q[j * 3 + 2], a2);
+        const TU *row = U + i * S.ld;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            int j0 = c * 256 + lane * 8;
+            if (j0 < r) {
+                float u[8];
+                load8(row + j0, u);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float *qq = s_q + (j0 + k) * 3;
+                    a0 = fmaf(u[k], qq[0], a0);
+                    a1 = fmaf(u[k], qq[1], a1);
+                    a2 = fmaf(u[k], qq[2], a2);
+                }
+            }
         }
         for (int o = 16; o > 0; o >>= 1) {
             a0 += __shfl_xor_sync(0xffffffffu, a0, o);
@@ -277,11 +303,19 @@ __global__ void __launch_bounds__(256) k_linear_residual(ClothView c, const floa
 
 }  // namespace
 
+template <class TU> static void project_t(cudaStream_t s, const SubspaceView &S, const TU *U, const float4 *rl,
+                                          const int *n_cv, float *partial) {
+    int rmax = std::max(S.r_nc, S.r_c);
+    if (rmax <= 256) k_project<TU, 1><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, U, rl, n_cv, partial);
+    else if (rmax <= 512) k_project<TU, 2><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, U, rl, n_cv, partial);
+    else k_project<TU, 4><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, U, rl, n_cv, partial);
+}
+
 void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W) {
     if (S.precision == 1)
-        k_project<__nv_bfloat16><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, S.U16, rl, n_cv, W.partial);
+        project_t<__nv_bfloat16>(s, S, S.U16, rl, n_cv, W.partial);
     else
-        k_project<float><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, S.U32, rl, n_cv, W.partial);
+        project_t<float>(s, S, S.U32, rl, n_cv, W.partial);
     int mx = S.ld * 3;
     k_project_reduce<<<(mx + 127) / 128, 128, 0, s>>>(S, n_cv, PROJ_BLOCKS, W.partial, W.g);
     PDC_LAUNCH_CK();
@@ -322,10 +356,16 @@ void launch_lift(cudaStream_t s, const SubspaceView &S, const int *n_cv, const S
                  float4 *dout) {
     int blocks = std::min((S.n + 7) / 8, 152 * 16);
     if (blocks < 1) return;
-    if (S.precision == 1)
-        k_lift<__nv_bfloat16><<<blocks, 256, 0, s>>>(S, S.U16, n_cv, W.q, din, dout);
-    else
-        k_lift<float><<<blocks, 256, 0, s>>>(S, S.U32, n_cv, W.q, din, dout);
+    int rmax = std::max(S.r_nc, S.r_c);
+    if (S.precision == 1) {
+        if (rmax <= 256) k_lift<__nv_bfloat16, 1><<<blocks, 256, 0, s>>>(S, S.U16, n_cv, W.q, din, dout);
+        else if (rmax <= 512) k_lift<__nv_bfloat16, 2><<<blocks, 256, 0, s>>>(S, S.U16, n_cv, W.q, din, dout);
+        else k_lift<__nv_bfloat16, 4><<<blocks, 256, 0, s>>>(S, S.U16, n_cv, W.q, din, dout);
+    } else {
+        if (rmax <= 256) k_lift<float, 1><<<blocks, 256, 0, s>>>(S, S.U32, n_cv, W.q, din, dout);
+        else if (rmax <= 512) k_lift<float, 2><<<blocks, 256, 0, s>>>(S, S.U32, n_cv, W.q, din, dout);
+        else k_lift<float, 4><<<blocks, 256, 0, s>>>(S, S.U32, n_cv, W.q, din, dout);
+    }
     PDC_LAUNCH_CK();
 }
 
