@@ -11,6 +11,7 @@
 #include <unordered_map>
 
 #include "pdc_collide.cuh"
+#include "pdc_prof.cuh"
 #include "pdc_subspace.cuh"
 
 namespace pdc {
@@ -109,9 +110,10 @@ struct Accel {
         w = 1.0;
         hist.clear();
     }
+    double rho_carry = 0.0;  // estimate carried from earlier passes
     double next(double meas) {
         if (!on) return 1.0;
-        if (!hist.empty() && meas > 1.5 * hist.back()) reset();
+        if (!hist.empty() && meas > 2.0 * *std::min_element(hist.begin(), hist.end())) reset();
         hist.push_back(meas);
         if (k < S) {
             ++k;
@@ -125,7 +127,11 @@ struct Accel {
                 size_t n = hist.size();
                 double ratio = hist[n - 1] / std::max(hist[n - 4], 1e-300);
                 rho = std::pow(std::max(ratio, 1e-12), 1.0 / 3.0);
-                rho = std::min(std::max(rho, 0.3), 0.995);
+                // the first iterations of a pass decay faster than the asymptotic
+                // rate: keep the largest estimate seen so far
+                rho = std::max(rho, rho_carry);
+                rho = std::min(std::max(rho, 0.3), 0.99);
+                rho_carry = rho;
             }
             w = 2.0 / (2.0 - rho * rho);
         } else {
@@ -133,70 +139,6 @@ struct Accel {
         }
         ++k;
         return w;
-    }
-};
-
-// Event-pair timing of individual launches (pdc_set_profiling).
-struct Profiler {
-    bool on = false;
-    struct Rec {
-        int kind;
-        cudaEvent_t a, b;
-        double bytes;
-    };
-    std::vector<cudaEvent_t> pool;
-    size_t used = 0;
-    std::vector<Rec> pending;
-    std::vector<std::string> names;
-    std::vector<pdc_kernel_time> acc;
-    ~Profiler() {
-        for (auto e : pool) cudaEventDestroy(e);
-    }
-    cudaEvent_t ev() {
-        if (used == pool.size()) {
-            cudaEvent_t e;
-            PDC_CK(cudaEventCreate(&e));
-            pool.push_back(e);
-        }
-        return pool[used++];
-    }
-    int kind(const char *name) {
-        for (size_t i = 0; i < names.size(); ++i)
-            if (names[i] == name) return (int)i;
-        names.push_back(name);
-        pdc_kernel_time t;
-        std::memset(&t, 0, sizeof(t));
-        std::strncpy(t.name, name, sizeof(t.name) - 1);
-        acc.push_back(t);
-        return (int)names.size() - 1;
-    }
-    void begin(cudaStream_t s, const char *name, double bytes) {
-        Rec r;
-        r.kind = kind(name);
-        r.a = ev();
-        r.b = ev();
-        r.bytes = bytes;
-        PDC_CK(cudaEventRecord(r.a, s));
-        pending.push_back(r);
-    }
-    void end(cudaStream_t s) { PDC_CK(cudaEventRecord(pending.back().b, s)); }
-    void flush() {
-        for (auto &r : pending) {
-            PDC_CK(cudaEventSynchronize(r.b));
-            float ms = 0.f;
-            PDC_CK(cudaEventElapsedTime(&ms, r.a, r.b));
-            acc[r.kind].launches += 1;
-            acc[r.kind].total_ms += ms;
-            acc[r.kind].algo_bytes += r.bytes;
-        }
-        pending.clear();
-        used = 0;
-    }
-    void reset() {
-        pending.clear();
-        used = 0;
-        names.clear();
-        acc.clear();
     }
 };
 
@@ -269,6 +211,7 @@ struct pdc_ctx {
     Accel accel;
     float last_dx = 0.f;
     DevBuf<float4> Xacc;  // previous iterate for the accelerated update
+    DevBuf<float> disp;   // |x^+ - x^-| per collision vertex
     long long nnz_off = 0;  // off-diagonal entries of H over free rows
     bool log = std::getenv("PDC_LOG") != nullptr;  // per-iteration residuals to stderr
 
@@ -752,6 +695,7 @@ void pdc_ctx::ensure_topology() {
     long long cent = std::max<long long>(4096, 8LL * (nt_all + ne_all));
     bp.reserve(coll(), cvt, cee, cent);
     cap_act = (int)std::max<long long>(1024, 4LL * nv_all);
+    disp.alloc(nv_all);
     act.alloc(cap_act);
     PDC_CK(cudaStreamSynchronize(s));
     topo_dirty = false;
@@ -784,7 +728,14 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
     if (check_rel || log || acc) {
         read_scalars();
         double rho = std::sqrt(hsc->rsq);
-        if (log) std::fprintf(stderr, "[pdc] lg contacts=%d rho=%.6g rel=%.6g\n", (int)contacts, rho, rho / std::max(rho0, 1e-300));
+        if (log) {
+            int na = 0, ncv = 0;
+            n_act_d.download(&na, 1, s);
+            n_cv_d.download(&ncv, 1, s);
+            PDC_CK(cudaStreamSynchronize(s));
+            std::fprintf(stderr, "[pdc] lg contacts=%d rho=%.6g rel=%.6g active=%d contact_v=%d\n", (int)contacts, rho,
+                         rho / std::max(rho0, 1e-300), na, ncv);
+        }
     }
     if (check_rel) {
         double rho = std::sqrt(hsc->rsq);
@@ -795,6 +746,7 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
         }
     }
     float w_acc = acc ? (float)accel.next(std::sqrt(hsc->rsq)) : 1.f;
+    if (log && acc) std::fprintf(stderr, "[pdc]    accel k=%d w=%.4f rho=%.4f\n", accel.k, w_acc, accel.rho);
     float4 *xprev = acc ? Xacc.p : nullptr;
     SubspaceView S = sub(r_nc, r_c);
     SubspaceWork W = work();
@@ -832,11 +784,13 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
         }
     }
     if (contacts && P.collisions) {
-        PROF("partial_ccd", 0, launch_partial_ccd(s, coll(), bp, Xm, Xp, cparams(), act, cap_act, n_act_d, &sc.p->overflow));
+        PROF("partial_ccd", 0,
+             launch_partial_ccd(s, coll(), bp, Xm, Xp, cparams(), act, cap_act, n_act_d, &sc.p->overflow, disp));
     }
 }
 
 void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {
+    bp.prof = prof.on ? &prof : nullptr;
     PROF("broad_phase", 0, bp.run(s, coll(), x0, x1, dhat, &sc.p->overflow));
     unsigned long long inf = 0x7ff0000000000000ULL;  // +inf
     PDC_CK(cudaMemcpyAsync(toi_bits.p, &inf, sizeof(inf), cudaMemcpyHostToDevice, s));

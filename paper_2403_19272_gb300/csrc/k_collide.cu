@@ -337,6 +337,8 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
         ee[k].alloc(cap_ee);
         st_vt[k].alloc(cap_vt);
         st_ee[k].alloc(cap_ee);
+        d0_vt[k].alloc(cap_vt);
+        d0_ee[k].alloc(cap_ee);
         cnt_vt_d[k].alloc(1);
         cnt_ee_d[k].alloc(1);
     }
@@ -348,13 +350,20 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
 }
 
 // Builds the new candidate lists in buffer (cur ^ 1) and makes it current.
+#define BP_PROF(name, ...)                                                                            \
+    do {                                                                                               \
+        if (prof) prof->begin(s, name, 0.0);                                                           \
+        __VA_ARGS__;                                                                                   \
+        if (prof) prof->end(s);                                                                        \
+    } while (0)
+
 void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat,
                      int *overflow) {
     int nw = cur ^ 1;
     PDC_CK(cudaMemsetAsync(gp.p, 0, sizeof(GridParams), s));
-    if (cv.nt) k_tri_boxes<<<nblk(cv.nt, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, gp);
-    if (cv.ne) k_edge_boxes<<<nblk(cv.ne, 256), 256, 0, s>>>(cv, x0, x1, elo, ehi);
-    k_grid_params<<<1, 1, 0, s>>>(gp, cv.nt, dhat, cell_scale);
+    BP_PROF("bp_boxes", if (cv.nt) k_tri_boxes<<<nblk(cv.nt, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, gp);
+            if (cv.ne) k_edge_boxes<<<nblk(cv.ne, 256), 256, 0, s>>>(cv, x0, x1, elo, ehi);
+            k_grid_params<<<1, 1, 0, s>>>(gp, cv.nt, dhat, cell_scale));
     PDC_LAUNCH_CK();
     long long *tot = totals.p;
     // ---- tables: 0 = triangles (VT), 1 = edges (EE)
@@ -363,8 +372,7 @@ void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const
         int T = k == 0 ? T_vt : T_ee;
         const float4 *lo = k == 0 ? tlo.p : elo.p;
         const float4 *hi = k == 0 ? thi.p : ehi.p;
-        bcnt[k].zero(s);
-        bfill[k].zero(s);
+        BP_PROF("bp_hash_build", bcnt[k].zero(s); bfill[k].zero(s);
         if (np) {
             k_hash_insert<<<nblk(np, 256), 256, 0, s>>>(np, lo, hi, gp, dhat, (unsigned)(T - 1), bcnt[k], bstart[k],
                                                         bfill[k], ekey[k], eprim[k], 0, tot + k, cap_ent, overflow);
@@ -376,9 +384,10 @@ void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const
             k_hash_insert<<<nblk(np, 256), 256, 0, s>>>(np, lo, hi, gp, dhat, (unsigned)(T - 1), bcnt[k], bstart[k],
                                                         bfill[k], ekey[k], eprim[k], 1, tot + k, cap_ent, overflow);
             PDC_LAUNCH_CK();
-        }
+        });
     }
     // ---- VT candidates
+    if (prof) prof->begin(s, "bp_query_vt", 0.0);
     if (cv.nv) {
         k_query_vt<<<nblk(cv.nv, 128), 128, 0, s>>>(cv, x0, x1, tlo, thi, gp, dhat, (unsigned)(T_vt - 1), bcnt[0],
                                                     bstart[0], ekey[0], eprim[0], cnt_v, nullptr, nullptr, tot + 0,
@@ -393,7 +402,9 @@ void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const
                                                     cap_ent, tot + 2, cap_vt, overflow);
         PDC_LAUNCH_CK();
     }
+    if (prof) prof->end(s);
     // ---- EE candidates
+    if (prof) prof->begin(s, "bp_query_ee", 0.0);
     if (cv.ne) {
         k_query_ee<<<nblk(cv.ne, 128), 128, 0, s>>>(cv, elo, ehi, gp, dhat, (unsigned)(T_ee - 1), bcnt[1], bstart[1],
                                                     ekey[1], eprim[1], cnt_e, nullptr, nullptr, tot + 1, cap_ent,
@@ -408,6 +419,7 @@ void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const
                                                     tot + 3, cap_ee, overflow);
         PDC_LAUNCH_CK();
     }
+    if (prof) prof->end(s);
     cur = nw;
 }
 

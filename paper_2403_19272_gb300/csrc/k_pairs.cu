@@ -384,11 +384,19 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const in
     }
 }
 
-// mode 0: collect active states; mode 1: partial CCD update then collect.
+// mode 0: store each pair's closest distance on xm and collect the active
+//         states into the active list;
+// mode 1: partial CCD update then collect.  A pair whose closest distance on
+//         xm exceeds dhat + (largest displacement on side 1) + (largest on
+//         side 2) cannot satisfy Q <= dhat |d0| at any sample (|d1 - d0| is
+//         bounded by those displacements), so it is set inactive without
+//         evaluating the samples.
 __global__ void __launch_bounds__(PAIR_THREADS) k_pairs_update(CollView cv, const int2 *__restrict__ vt,
                                                                const int2 *__restrict__ ee, const long long *nvt_p,
                                                                const long long *nee_p, unsigned char *st_vt,
-                                                               unsigned char *st_ee, const float4 *__restrict__ xm,
+                                                               unsigned char *st_ee, float *d0_vt, float *d0_ee,
+                                                               const float *__restrict__ disp,
+                                                               const float4 *__restrict__ xm,
                                                                const float4 *__restrict__ xp, CollParams P, int mode,
                                                                ActivePair *act, int cap, int *n_act, int *overflow) {
     long long nvt = *nvt_p, n = nvt + *nee_p;
@@ -402,14 +410,26 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs_update(CollView cv, cons
             int ids[4], kind;
             pair_ids(cv, vt, ee, nvt, idx, ids, kind);
             unsigned char *stp = kind == 0 ? st_vt + idx : st_ee + (idx - nvt);
+            float *d0p = kind == 0 ? d0_vt + idx : d0_ee + (idx - nvt);
             unsigned char st = *stp;
-            float4 a0[4];
-            for (int i = 0; i < 4; ++i) a0[i] = xm[ids[i]];
             float c[4];
+            bool near = true;
             if (mode == 1) {
-                float4 a1[4];
-                for (int i = 0; i < 4; ++i) a1[i] = xp[ids[i]];
-                bool flag = partial_pair(kind, a0, a1, P.dhat, kind == 0 ? P.samples_vt : P.samples_ee, c);
+                float m1 = kind == 0 ? disp[ids[0]] : fmaxf(disp[ids[0]], disp[ids[1]]);
+                float m2 = kind == 0 ? fmaxf(disp[ids[1]], fmaxf(disp[ids[2]], disp[ids[3]]))
+                                     : fmaxf(disp[ids[2]], disp[ids[3]]);
+                near = *d0p <= (P.dhat + m1 + m2) * 1.001f + 1e-7f;
+            }
+            float4 a0[4];
+            if (near)
+                for (int i = 0; i < 4; ++i) a0[i] = xm[ids[i]];
+            if (mode == 1) {
+                bool flag = false;
+                if (near) {
+                    float4 a1[4];
+                    for (int i = 0; i < 4; ++i) a1[i] = xp[ids[i]];
+                    flag = partial_pair(kind, a0, a1, P.dhat, kind == 0 ? P.samples_vt : P.samples_ee, c);
+                }
                 if (flag) {
                     int a = (st & ST_ACTIVE) ? min((int)(st & 0x7f) + 1, P.a_max) : 0;
                     st = ST_ACTIVE | (unsigned char)a;
@@ -417,10 +437,12 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs_update(CollView cv, cons
                     st = 0;
                 }
                 *stp = st;
-            } else if (st & ST_ACTIVE) {
+            } else {
                 V<float> q[4];
                 for (int i = 0; i < 4; ++i) q[i] = ld<float>(a0[i]);
                 closest_coef<float>(kind, q, c);
+                V<float> d = c[0] * q[0] + c[1] * q[1] + c[2] * q[2] + c[3] * q[3];
+                *d0p = sqrtf(dotv(d, d));
             }
             if (st & ST_ACTIVE) {
                 want = true;
@@ -432,6 +454,13 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs_update(CollView cv, cons
         }
         append_active(want, ap, act, cap, n_act, overflow);
     }
+}
+
+__global__ void k_disp(int nv, const float4 *__restrict__ a, const float4 *__restrict__ b, float *__restrict__ d) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    float3 e = f3(b[i]) - f3(a[i]);
+    d[i] = sqrtf(dot3(e, e));
 }
 
 // Collision springs (Sec. 5.1, A_i = B_i = Id): constraint C(x) = d(x).n0 - dhat
@@ -556,18 +585,19 @@ void launch_collect_active(cudaStream_t s, const CollView &cv, BroadPhase &bp, c
     int c = bp.cur;
     PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
     k_pairs_update<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
-                                                        bp.st_vt[c], bp.st_ee[c], xm, xm, P, 0, act, cap_act, n_act,
-                                                        overflow);
+                                                        bp.st_vt[c], bp.st_ee[c], bp.d0_vt[c], bp.d0_ee[c], nullptr,
+                                                        xm, xm, P, 0, act, cap_act, n_act, overflow);
     PDC_LAUNCH_CK();
 }
 
 void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm, const float4 *xp,
-                        const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow) {
+                        const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow, float *disp) {
     int c = bp.cur;
     PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
+    if (cv.nv > 0) k_disp<<<(cv.nv + 255) / 256, 256, 0, s>>>(cv.nv, xm, xp, disp);
     k_pairs_update<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
-                                                        bp.st_vt[c], bp.st_ee[c], xm, xp, P, 1, act, cap_act, n_act,
-                                                        overflow);
+                                                        bp.st_vt[c], bp.st_ee[c], bp.d0_vt[c], bp.d0_ee[c], disp, xm,
+                                                        xp, P, 1, act, cap_act, n_act, overflow);
     PDC_LAUNCH_CK();
 }
 

@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "pdc_internal.cuh"
+#include "pdc_prof.cuh"
 
 namespace pdc {
 
@@ -51,8 +52,10 @@ struct BroadPhase {
     // double-buffered candidate lists and NDB pair states
     DevBuf<int2> vt[2], ee[2];
     DevBuf<unsigned char> st_vt[2], st_ee[2];
+    DevBuf<float> d0_vt[2], d0_ee[2];  // per pair: closest distance on x^- (partial-CCD prefilter)
     DevBuf<long long> cnt_vt_d[2], cnt_ee_d[2];
     int cur = 0;
+    Profiler *prof = nullptr;  // optional sub-kernel timing
 
     void reserve(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent);
     void run(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat, int *overflow);
@@ -67,8 +70,9 @@ void launch_full_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const f
 void launch_collect_active(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm,
                            const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow);
 // Partial CCD over (xm, xp) on the current lists: update states, rebuild the active list.
+// disp (scratch, nv floats) receives |xp - xm| per collision vertex.
 void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm, const float4 *xp,
-                        const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow);
+                        const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow, float *disp);
 // Collision springs of the active list at positions x: cw += w, cf += w (y - x).
 void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, const int *n_act, int cap_act,
                     const float4 *x, float dhat, float *cw, float4 *cf);
