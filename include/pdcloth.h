@@ -108,6 +108,10 @@ typedef struct {
                                 iterates (ignored when fixed_iters = 1)           */
     double accel_rho;        /* spectral radius for accel; <= 0: estimated from the
                                 residual decay of the first iterations of a pass */
+    int32_t sweep_kind;      /* 0: damped Jacobi sweeps; 1: Jacobi-preconditioned
+                                Chebyshev iteration of jacobi_sweeps steps over the
+                                spectrum interval [b / cheb_ratio, b] of D^-1 A   */
+    double cheb_ratio;       /* interval ratio for sweep_kind 1 (> 1)            */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */

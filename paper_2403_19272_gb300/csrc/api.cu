@@ -129,6 +129,7 @@ struct Accel {
                 rho = std::pow(std::max(ratio, 1e-12), 1.0 / 3.0);
                 // the first iterations of a pass decay faster than the asymptotic
                 // rate: keep the largest estimate seen so far
+                if (!std::isfinite(rho)) rho = 0.3;
                 rho = std::max(rho, rho_carry);
                 rho = std::min(std::max(rho, 0.3), 0.99);
                 rho_carry = rho;
@@ -212,6 +213,8 @@ struct pdc_ctx {
     float last_dx = 0.f;
     DevBuf<float4> Xacc;  // previous iterate for the accelerated update
     DevBuf<float> disp;   // |x^+ - x^-| per collision vertex
+    DevBuf<float4> CD0, CD1;  // Chebyshev directions
+    double gersh = 1.0;       // Gershgorin bound of D^-1 H
     long long nnz_off = 0;  // off-diagonal entries of H over free rows
     bool log = std::getenv("PDC_LOG") != nullptr;  // per-iteration residuals to stderr
 
@@ -489,6 +492,17 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
         }
         omega = std::min(1.0, 1.8 / gmax);
     }
+    {
+        double gmax = 1.0;
+        for (int i = 0; i < n; ++i) {
+            if (!freev[i]) continue;
+            double sum = 0;
+            for (auto &kv : rows[i])
+                if (freev[kv.first]) sum += std::fabs(kv.second);
+            gmax = std::max(gmax, sum / rows[i][i]);
+        }
+        gersh = gmax;
+    }
     // gap
     if (P.d_hat > 0) {
         dhat = (float)P.d_hat;
@@ -555,6 +569,10 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
     R.alloc(n);
     RL.alloc(n);
     Xacc.alloc(n);
+    if (P.sweep_kind == 1) {
+        CD0.alloc(n);
+        CD1.alloc(n);
+    }
     D0.alloc(n);
     D1.alloc(n);
     CF.alloc(n);
@@ -771,12 +789,38 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             PDC_CK(cudaMemsetAsync(din, 0, sizeof(float4) * n, s));
             have_delta = true;
         }
-        for (int k = 0; k < sweeps; ++k) {
-            bool last = (cyc == cycles - 1) && (k == sweeps - 1);
-            PROF("jacobi_sweep", bytes_sweep(contacts, last),
-                 launch_sweep(s, c, cw, R, din, dout, (float)omega, Xp, last ? Xp.p : nullptr, last ? sc.p : nullptr,
-                              last ? xprev : nullptr, w_acc));
-            std::swap(din, dout);
+        if (P.sweep_kind == 1) {
+            // Chebyshev iteration on the interval [b / ratio, b] of the spectrum of D^-1 A
+            double b = std::max(gersh, 1.0) * 1.02, a = b / std::max(P.cheb_ratio, 1.0001);
+            double theta = 0.5 * (b + a), dl = 0.5 * (b - a), sig = theta / dl;
+            double rho_prev = 1.0 / sig;
+            float4 *dp = CD0, *dq = CD1;
+            for (int k = 0; k < sweeps; ++k) {
+                bool last = (cyc == cycles - 1) && (k == sweeps - 1);
+                double alpha, beta;
+                if (k == 0) {
+                    alpha = 0.0;
+                    beta = 1.0 / theta;
+                } else {
+                    double rk = 1.0 / (2.0 * sig - rho_prev);
+                    alpha = rk * rho_prev;
+                    beta = 2.0 * rk / dl;
+                    rho_prev = rk;
+                }
+                PROF("cheb_sweep", bytes_sweep(contacts, last) + 24.0 * n,
+                     launch_cheb_step(s, c, cw, R, din, dp, dout, dq, (float)alpha, (float)beta, Xp,
+                                      last ? Xp.p : nullptr, last ? sc.p : nullptr, last ? xprev : nullptr, w_acc));
+                std::swap(din, dout);
+                std::swap(dp, dq);
+            }
+        } else {
+            for (int k = 0; k < sweeps; ++k) {
+                bool last = (cyc == cycles - 1) && (k == sweeps - 1);
+                PROF("jacobi_sweep", bytes_sweep(contacts, last),
+                     launch_sweep(s, c, cw, R, din, dout, (float)omega, Xp, last ? Xp.p : nullptr,
+                                  last ? sc.p : nullptr, last ? xprev : nullptr, w_acc));
+                std::swap(din, dout);
+            }
         }
         if (sweeps == 0 && cyc == cycles - 1) {
             // no sweep: apply the correction directly
@@ -986,6 +1030,8 @@ void pdc_default_params(pdc_params *p) {
     p->seed = 12345;
     p->accel = 0;
     p->accel_rho = 0.0;
+    p->sweep_kind = 0;
+    p->cheb_ratio = 100.0;
 }
 
 pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const pdc_params *params, void *stream,
@@ -1004,7 +1050,8 @@ pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const 
         params->r_reuse < 0 || params->r_reuse > 128 || params->max_outer < 0 || params->max_inner < 0 ||
         params->warm_iters < 0 || params->a_max < 0 || params->a_max > 127 ||
         !(params->samples_vt == 0 || params->samples_vt == 1 || params->samples_vt == 3) ||
-        !(params->samples_ee == 0 || params->samples_ee == 1 || params->samples_ee == 4)) {
+        !(params->samples_ee == 0 || params->samples_ee == 1 || params->samples_ee == 4) ||
+        params->sweep_kind < 0 || params->sweep_kind > 1 || (params->sweep_kind == 1 && !(params->cheb_ratio > 1.0))) {
         g_create_error = "pdc_create: invalid parameters";
         return PDC_ERR_ARG;
     }
@@ -1184,6 +1231,8 @@ pdc_status pdc_step(pdc_handle h, double dt) {
                 h->cap_act *= 2;
                 h->act.alloc(h->cap_act);
             }
+            h->accel.rho_carry = 0.0;
+            if (h->log) std::fprintf(stderr, "[pdc] step retried after overflow 0x%x\n", ovf);
         }
     }
     h->st.overflow_retries = retries;

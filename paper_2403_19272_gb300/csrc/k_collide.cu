@@ -284,11 +284,12 @@ __global__ void __launch_bounds__(128) k_query_ee(CollView cv, const float4 *__r
     }
 }
 
-// Stores min(total, cap) as the list length seen by every later kernel and
-// flags an overflow (the step is then redone with larger buffers).
+// Stores the list length seen by every later kernel.  On overflow the write
+// pass is skipped, so the buffer holds no valid entries: the length is set to
+// 0 and the overflow flagged (the step is then redone with larger buffers).
 __global__ void k_check_cap(const long long *total, long long cap, int flag, int *overflow, long long *count_out) {
     long long t = *total;
-    *count_out = t < cap ? t : cap;
+    *count_out = t <= cap ? t : 0;
     if (t > cap) atomicOr(overflow, flag);
 }
 

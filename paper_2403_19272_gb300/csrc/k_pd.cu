@@ -186,7 +186,59 @@ __global__ void __launch_bounds__(256) k_sweep(const ClothView c, const float *_
             float3 xo = f3(x[i]);
             float3 xn = xo + dn;
             if (xprev) {
-                if (c.is_free[i]) {
+                if (c.is_free[i] && w_acc != 1.f) {
+                    float3 xp = f3(xprev[i]);
+                    xn = xp + w_acc * (xn - xp);
+                }
+                xprev[i] = f4(xo);
+            }
+            xout[i] = f4(xn);
+            float3 d = xn - xo;
+            mx = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z)));
+        }
+    }
+    if (xout && sc) block_max(mx, &sc->dxmax);
+}
+
+// One step of the Jacobi-preconditioned Chebyshev iteration on
+// (H + diag(cw)) delta = r:
+//   d'     = alpha d + beta D^-1 (r - (H + diag(cw)) delta)
+//   delta' = delta + d'
+// (alpha, beta from the Chebyshev recurrence for the interval [a, b] of the
+// spectrum of D^-1 (H + diag cw)).  The last step also writes the iterate as
+// k_sweep does.
+__global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const float *__restrict__ cw,
+                                                   const float4 *__restrict__ r, const float4 *__restrict__ din,
+                                                   const float4 *__restrict__ dprev, float4 *__restrict__ dout,
+                                                   float4 *__restrict__ dnew, float alpha, float beta,
+                                                   const float4 *x, float4 *xout, float4 *xprev, float w_acc,
+                                                   Scalars *sc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float mx = 0.f;
+    if (i < c.n) {
+        float3 dn = make_float3(0.f, 0.f, 0.f), dd = make_float3(0.f, 0.f, 0.f);
+        if (c.is_free[i]) {
+            float3 di = f3(din[i]);
+            float D = c.hdiag[i] + (cw ? cw[i] : 0.f);
+            float3 acc = f3(r[i]) - D * di;
+            const int *col = c.ell_col + i;
+            const float *val = c.ell_val + i;
+            for (int k = 0; k < c.ell_w; ++k) {
+                float v = val[(size_t)k * c.n];
+                int j = col[(size_t)k * c.n];
+                acc = acc - v * f3(din[j]);
+            }
+            dd = (beta / D) * acc;
+            if (alpha != 0.f) dd = dd + alpha * f3(dprev[i]);
+            dn = di + dd;
+        }
+        dout[i] = f4(dn);
+        dnew[i] = f4(dd);
+        if (xout) {
+            float3 xo = f3(x[i]);
+            float3 xn = xo + dn;
+            if (xprev) {
+                if (c.is_free[i] && w_acc != 1.f) {
                     float3 xp = f3(xprev[i]);
                     xn = xp + w_acc * (xn - xp);
                 }
@@ -247,6 +299,15 @@ void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const flo
                   float4 *dout, float omega, const float4 *x, float4 *xout, Scalars *sc, float4 *xprev,
                   float w_acc) {
     if (c.n > 0) k_sweep<<<nblk(c.n, 256), 256, 0, s>>>(c, cw, r, din, dout, omega, x, xout, xprev, w_acc, sc);
+    PDC_LAUNCH_CK();
+}
+
+void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
+                      const float4 *dprev, float4 *dout, float4 *dnew, float alpha, float beta, const float4 *x,
+                      float4 *xout, Scalars *sc, float4 *xprev, float w_acc) {
+    if (c.n > 0)
+        k_cheb_step<<<nblk(c.n, 256), 256, 0, s>>>(c, cw, r, din, dprev, dout, dnew, alpha, beta, x, xout, xprev,
+                                                     w_acc, sc);
     PDC_LAUNCH_CK();
 }
 

@@ -140,6 +140,9 @@ void launch_residual(cudaStream_t s, const ClothView &c, const float4 *x, const 
 void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                   float4 *dout, float omega, const float4 *x, float4 *xout, Scalars *sc, float4 *xprev = nullptr,
                   float w_acc = 1.f);
+void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
+                      const float4 *dprev, float4 *dout, float4 *dnew, float alpha, float beta, const float4 *x,
+                      float4 *xout, Scalars *sc, float4 *xprev, float w_acc);
 void launch_line_search(cudaStream_t s, int nv_all, const float4 *xm, const float4 *xp, const double *s_frac,
                         float4 *xout);
 void launch_velocity(cudaStream_t s, int n, const float4 *xnew, const float4 *xs, float inv_h, float4 *v);

@@ -39,7 +39,8 @@ class pdc_params(ctypes.Structure):
                 ("warm_iters", c_i32), ("jacobi_sweeps", c_i32), ("jacobi_omega", c_dbl), ("solve_cycles", c_i32),
                 ("r_warm", c_i32), ("r_reuse", c_i32), ("precision", c_i32), ("samples_vt", c_i32),
                 ("samples_ee", c_i32), ("collisions", c_i32), ("fixed_iters", c_i32), ("eig_iters", c_i32),
-                ("seed", c_u64), ("accel", c_i32), ("accel_rho", c_dbl)]
+                ("seed", c_u64), ("accel", c_i32), ("accel_rho", c_dbl), ("sweep_kind", c_i32),
+                ("cheb_ratio", c_dbl)]
 
 
 class pdc_stats(ctypes.Structure):
