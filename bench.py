@@ -47,13 +47,16 @@ def parse():
 def solver_params(pc, precision):
     p = pc.pdc_default_params()
     p.tol_rel_residual = 1e-3
-    p.max_outer = 3
-    p.max_inner = 64
+    p.max_outer = 2
+    p.max_inner = 400
     p.warm_iters = 5
     p.r_warm = 256
     p.r_reuse = 32
     p.precision = precision
-    p.jacobi_sweeps = 4
+    p.sweep_kind = 1        # Chebyshev-iteration sweeps
+    p.jacobi_sweeps = 16
+    p.cheb_ratio = 1000.0
+    p.accel = 1             # Chebyshev acceleration of the LG iterates
     p.solve_cycles = 1
     p.eig_iters = 12
     return p
