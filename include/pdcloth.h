@@ -104,14 +104,17 @@ typedef struct {
     int32_t fixed_iters;     /* 1: run exactly warm/max_outer/max_inner iterations */
     int32_t eig_iters;       /* filtered subspace iterations building the basis  */
     uint64_t seed;           /* seed of the basis start block                    */
-    int32_t accel;           /* 1: Chebyshev semi-iterative acceleration of the LG
-                                iterates (ignored when fixed_iters = 1)           */
+    int32_t accel;           /* acceleration of the LG iterates (ignored when
+                                fixed_iters = 1): 0 none; 1 Chebyshev
+                                semi-iteration; 2 Anderson mixing of depth
+                                aa_depth                                          */
     double accel_rho;        /* spectral radius for accel; <= 0: estimated from the
                                 residual decay of the first iterations of a pass */
     int32_t sweep_kind;      /* 0: damped Jacobi sweeps; 1: Jacobi-preconditioned
                                 Chebyshev iteration of jacobi_sweeps steps over the
                                 spectrum interval [b / cheb_ratio, b] of D^-1 A   */
     double cheb_ratio;       /* interval ratio for sweep_kind 1 (> 1)            */
+    int32_t aa_depth;        /* history length for accel = 2 (1..8)              */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */

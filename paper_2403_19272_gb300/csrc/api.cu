@@ -109,8 +109,26 @@ struct Accel {
         k = 0;
         w = 1.0;
         hist.clear();
+        aa_reset();
     }
     double rho_carry = 0.0;  // estimate carried from earlier passes
+    // Anderson mixing history (accel = 2)
+    int aa_count = 0, aa_widx = 0;
+    bool aa_have_prev = false;
+    void aa_reset() {
+        aa_count = 0;
+        aa_widx = 0;
+        aa_have_prev = false;
+    }
+    // Anderson: restart the history when the residual jumps above twice the
+    // smallest residual of the current history
+    void aa_observe(double meas) {
+        if (!hist.empty() && meas > 2.0 * *std::min_element(hist.begin(), hist.end())) {
+            hist.clear();
+            aa_reset();
+        }
+        hist.push_back(meas);
+    }
     double next(double meas) {
         if (!on) return 1.0;
         if (!hist.empty() && meas > 2.0 * *std::min_element(hist.begin(), hist.end())) reset();
@@ -214,6 +232,9 @@ struct pdc_ctx {
     DevBuf<float4> Xacc;  // previous iterate for the accelerated update
     DevBuf<float> disp;   // |x^+ - x^-| per collision vertex
     DevBuf<float4> CD0, CD1;  // Chebyshev directions
+    DevBuf<float4> aa_dF, aa_dG, aa_f, aa_g;  // Anderson history
+    DevBuf<double> aa_Gb;
+    DevBuf<float> aa_theta;
     double gersh = 1.0;       // Gershgorin bound of D^-1 H
     long long nnz_off = 0;  // off-diagonal entries of H over free rows
     bool log = std::getenv("PDC_LOG") != nullptr;  // per-iteration residuals to stderr
@@ -573,6 +594,15 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
         CD0.alloc(n);
         CD1.alloc(n);
     }
+    if (P.accel == 2) {
+        int m = std::min(std::max(P.aa_depth, 1), 8);
+        aa_dF.alloc((size_t)m * n);
+        aa_dG.alloc((size_t)m * n);
+        aa_f.alloc(n);
+        aa_g.alloc(n);
+        aa_Gb.alloc(64);
+        aa_theta.alloc(8);
+    }
     D0.alloc(n);
     D1.alloc(n);
     CF.alloc(n);
@@ -743,6 +773,7 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
     }
     PROF("local_residual", bytes_residual(contacts), launch_residual(s, c, Xp, Z, cw, cf, R, sc, nullptr, 0));
     bool acc = accel.on && !(P.fixed_iters != 0);
+    bool aa = acc && P.accel == 2;
     if (check_rel || log || acc) {
         read_scalars();
         double rho = std::sqrt(hsc->rsq);
@@ -763,9 +794,11 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             return;
         }
     }
-    float w_acc = acc ? (float)accel.next(std::sqrt(hsc->rsq)) : 1.f;
-    if (log && acc) std::fprintf(stderr, "[pdc]    accel k=%d w=%.4f rho=%.4f\n", accel.k, w_acc, accel.rho);
-    float4 *xprev = acc ? Xacc.p : nullptr;
+    float w_acc = 1.f;
+    if (aa) accel.aa_observe(std::sqrt(hsc->rsq));
+    else if (acc) w_acc = (float)accel.next(std::sqrt(hsc->rsq));
+    if (log && acc && !aa) std::fprintf(stderr, "[pdc]    accel k=%d w=%.4f rho=%.4f\n", accel.k, w_acc, accel.rho);
+    float4 *xprev = (acc && !aa) ? Xacc.p : nullptr;
     SubspaceView S = sub(r_nc, r_c);
     SubspaceWork W = work();
     float4 *din = D0, *dout = D1;
@@ -826,6 +859,19 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             // no sweep: apply the correction directly
             launch_sweep(s, c, cw, R, din, dout, 0.f, Xp, Xp.p, sc.p, xprev, w_acc);
         }
+    }
+    if (aa) {
+        int m = std::min(std::max(P.aa_depth, 1), 8);
+        int slot = 0;
+        if (accel.aa_have_prev) {
+            slot = accel.aa_widx % m;
+            accel.aa_widx++;
+            accel.aa_count = std::min(accel.aa_count + 1, m);
+        }
+        PROF("anderson_mix", 0,
+             launch_aa(s, n, is_free, din, Xp, aa_f, aa_g, aa_dF, aa_dG, slot, accel.aa_have_prev ? 1 : 0,
+                       accel.aa_count, aa_Gb, aa_theta));
+        accel.aa_have_prev = true;
     }
     if (contacts && P.collisions) {
         PROF("partial_ccd", 0,
@@ -1032,6 +1078,7 @@ void pdc_default_params(pdc_params *p) {
     p->accel_rho = 0.0;
     p->sweep_kind = 0;
     p->cheb_ratio = 100.0;
+    p->aa_depth = 6;
 }
 
 pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const pdc_params *params, void *stream,
@@ -1051,7 +1098,8 @@ pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const 
         params->warm_iters < 0 || params->a_max < 0 || params->a_max > 127 ||
         !(params->samples_vt == 0 || params->samples_vt == 1 || params->samples_vt == 3) ||
         !(params->samples_ee == 0 || params->samples_ee == 1 || params->samples_ee == 4) ||
-        params->sweep_kind < 0 || params->sweep_kind > 1 || (params->sweep_kind == 1 && !(params->cheb_ratio > 1.0))) {
+        params->sweep_kind < 0 || params->sweep_kind > 1 || (params->sweep_kind == 1 && !(params->cheb_ratio > 1.0)) ||
+        params->accel < 0 || params->accel > 2 || (params->accel == 2 && (params->aa_depth < 1 || params->aa_depth > 8))) {
         g_create_error = "pdc_create: invalid parameters";
         return PDC_ERR_ARG;
     }

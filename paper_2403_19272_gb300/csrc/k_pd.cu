@@ -252,6 +252,121 @@ __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const floa
     if (xout && sc) block_max(mx, &sc->dxmax);
 }
 
+// Anderson mixing of the LG fixed-point map x -> G(x) = x + delta(x)
+// (history of depth m): with f_k = delta_k, g_k = x_k + delta_k and the
+// differences dF_j, dG_j of consecutive f and g, theta minimises
+// |f_k - dF theta| and x_{k+1} = g_k - dG theta.
+constexpr int AA_MAX = 8;
+
+// Inserts the newest differences (if a previous iterate exists) into slot
+// `slot`, stores f_k, g_k, and accumulates the normal equations
+// G_jl = dF_j . dF_l, b_j = dF_j . f_k over the ncol valid columns.
+__global__ void __launch_bounds__(256) k_aa_gram(int n, const unsigned char *__restrict__ is_free,
+                                                 const float4 *__restrict__ delta, const float4 *__restrict__ xhat,
+                                                 float4 *__restrict__ fprev, float4 *__restrict__ gprev,
+                                                 float4 *__restrict__ dF, float4 *__restrict__ dG, int slot,
+                                                 int have_prev, int ncol, double *__restrict__ Gb) {
+    __shared__ float red[AA_MAX * (AA_MAX + 3) / 2 + AA_MAX][8];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float3 col[AA_MAX];
+    float3 fk = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < AA_MAX; ++j) col[j] = make_float3(0.f, 0.f, 0.f);
+    if (i < n && is_free[i]) {
+        fk = f3(delta[i]);
+        float3 gk = f3(xhat[i]);
+        float3 df = make_float3(0.f, 0.f, 0.f);
+        if (have_prev) {
+            df = fk - f3(fprev[i]);
+            float3 dg = gk - f3(gprev[i]);
+            dF[(size_t)slot * n + i] = f4(df);
+            dG[(size_t)slot * n + i] = f4(dg);
+        }
+        fprev[i] = f4(fk);
+        gprev[i] = f4(gk);
+#pragma unroll
+        for (int j = 0; j < AA_MAX; ++j)
+            if (j < ncol) col[j] = (have_prev && j == slot) ? df : f3(dF[(size_t)j * n + i]);
+    } else if (i < n) {
+        fprev[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        gprev[i] = xhat[i];
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int e = 0;
+    for (int j = 0; j < ncol; ++j) {
+        for (int l = j; l < ncol; ++l) {
+            float v = dot3(col[j], col[l]);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[e][w] = v;
+            ++e;
+        }
+        float v = dot3(col[j], fk);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[e][w] = v;
+        ++e;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < e; q += blockDim.x) {
+        float t = 0.f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[q][k];
+        if (t != 0.f) atomicAdd(&Gb[q], (double)t);
+    }
+}
+
+// Solves the regularised normal equations (one thread, FP64) into theta.
+__global__ void k_aa_solve(int ncol, const double *__restrict__ Gb, float *__restrict__ theta) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double A[AA_MAX][AA_MAX], b[AA_MAX];
+    int e = 0;
+    double tr = 0.0;
+    for (int j = 0; j < ncol; ++j) {
+        for (int l = j; l < ncol; ++l) {
+            A[j][l] = A[l][j] = Gb[e++];
+        }
+        b[j] = Gb[e++];
+        tr += A[j][j];
+    }
+    for (int j = 0; j < ncol; ++j) A[j][j] += 1e-10 * tr + 1e-300;
+    // Cholesky
+    bool ok = tr > 0.0;
+    for (int j = 0; j < ncol && ok; ++j) {
+        double d = A[j][j];
+        for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+        if (!(d > 0.0)) { ok = false; break; }
+        d = sqrt(d);
+        A[j][j] = d;
+        for (int q = j + 1; q < ncol; ++q) {
+            double v = A[q][j];
+            for (int k = 0; k < j; ++k) v -= A[q][k] * A[j][k];
+            A[q][j] = v / d;
+        }
+    }
+    double y[AA_MAX], x[AA_MAX];
+    for (int j = 0; j < ncol; ++j) {
+        double v = b[j];
+        for (int k = 0; k < j; ++k) v -= A[j][k] * y[k];
+        y[j] = ok ? v / A[j][j] : 0.0;
+    }
+    for (int j = ncol - 1; j >= 0; --j) {
+        double v = y[j];
+        for (int k = j + 1; k < ncol; ++k) v -= A[k][j] * x[k];
+        x[j] = ok ? v / A[j][j] : 0.0;
+    }
+    for (int j = 0; j < AA_MAX; ++j) theta[j] = (j < ncol && ok && isfinite(x[j])) ? (float)x[j] : 0.f;
+}
+
+// x_{k+1} = g_k - sum_j theta_j dG_j on free vertices.
+__global__ void __launch_bounds__(256) k_aa_mix(int n, const unsigned char *__restrict__ is_free,
+                                                const float4 *__restrict__ xhat, const float4 *__restrict__ dG,
+                                                int ncol, const float *__restrict__ theta, float4 *__restrict__ xout) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float3 x = f3(xhat[i]);
+    if (is_free[i])
+        for (int j = 0; j < ncol; ++j) x = x - theta[j] * f3(dG[(size_t)j * n + i]);
+    xout[i] = f4(x);
+}
+
 __global__ void k_lerp(int nv, const float4 *__restrict__ a, const float4 *__restrict__ b, const double *s_frac,
                        float4 *__restrict__ out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -308,6 +423,18 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
     if (c.n > 0)
         k_cheb_step<<<nblk(c.n, 256), 256, 0, s>>>(c, cw, r, din, dprev, dout, dnew, alpha, beta, x, xout, xprev,
                                                      w_acc, sc);
+    PDC_LAUNCH_CK();
+}
+
+void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x, float4 *fprev,
+               float4 *gprev, float4 *dF, float4 *dG, int slot, int have_prev, int ncol, double *Gb, float *theta) {
+    if (n <= 0) return;
+    PDC_CK(cudaMemsetAsync(Gb, 0, sizeof(double) * (AA_MAX * (AA_MAX + 3) / 2 + AA_MAX), s));
+    k_aa_gram<<<nblk(n, 256), 256, 0, s>>>(n, is_free, delta, x, fprev, gprev, dF, dG, slot, have_prev, ncol, Gb);
+    if (ncol > 0) {
+        k_aa_solve<<<1, 32, 0, s>>>(ncol, Gb, theta);
+        k_aa_mix<<<nblk(n, 256), 256, 0, s>>>(n, is_free, x, dG, ncol, theta, x);
+    }
     PDC_LAUNCH_CK();
 }
 

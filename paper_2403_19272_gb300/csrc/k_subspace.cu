@@ -64,23 +64,35 @@ __global__ void __launch_bounds__(PROJ_T) k_project(SubspaceView S, const TU *__
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[c][k][0] = acc[c][k][1] = acc[c][k][2] = 0.f;
     long long gw = (long long)blockIdx.x * PROJ_W + w, nw = (long long)gridDim.x * PROJ_W;
-    for (long long i = gw; i < S.n; i += nw) {
-        float4 rv = __ldg(rl + i);
-        const TU *row = U + i * S.ld;
+    constexpr int UR = NCH == 1 ? 4 : 2;  // rows in flight per warp
+    for (long long i0 = gw; i0 < S.n; i0 += nw * UR) {
+        float4 rv[UR];
+        float u[UR][NCH][8];
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            int j0 = c * 256 + lane * 8;
-            if (j0 < r) {
-                float u[8];
-                load8(row + j0, u);
+        for (int q = 0; q < UR; ++q) {
+            long long i = i0 + q * nw;
+            bool ok = i < S.n;
+            rv[q] = ok ? __ldg(rl + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const TU *row = U + (ok ? i : 0) * S.ld;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    acc[c][k][0] = fmaf(u[k], rv.x, acc[c][k][0]);
-                    acc[c][k][1] = fmaf(u[k], rv.y, acc[c][k][1]);
-                    acc[c][k][2] = fmaf(u[k], rv.z, acc[c][k][2]);
-                }
+            for (int c = 0; c < NCH; ++c) {
+                int j0 = c * 256 + lane * 8;
+                if (ok && j0 < r) load8(row + j0, u[q][c]);
+                else
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) u[q][c][k] = 0.f;
             }
         }
+#pragma unroll
+        for (int q = 0; q < UR; ++q)
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    acc[c][k][0] = fmaf(u[q][c][k], rv[q].x, acc[c][k][0]);
+                    acc[c][k][1] = fmaf(u[q][c][k], rv[q].y, acc[c][k][1]);
+                    acc[c][k][2] = fmaf(u[q][c][k], rv[q].z, acc[c][k][2]);
+                }
     }
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
@@ -252,32 +264,53 @@ __global__ void __launch_bounds__(256) k_lift(SubspaceView S, const TU *__restri
     __syncthreads();
     int lane = threadIdx.x & 31;
     int wpb = blockDim.x >> 5;
-    for (long long i = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); i < S.n; i += (long long)gridDim.x * wpb) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        const TU *row = U + i * S.ld;
+    // this lane's q entries stay in registers
+    float ql[NCH][8][3];
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            int j0 = c * 256 + lane * 8;
-            if (j0 < r) {
-                float u[8];
-                load8(row + j0, u);
+    for (int c = 0; c < NCH; ++c)
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const float *qq = s_q + (j0 + k) * 3;
-                    a0 = fmaf(u[k], qq[0], a0);
-                    a1 = fmaf(u[k], qq[1], a1);
-                    a2 = fmaf(u[k], qq[2], a2);
-                }
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) ql[c][k][d] = s_q[(c * 256 + lane * 8 + k) * 3 + d];
+    constexpr int UR = NCH == 1 ? 4 : 2;  // rows in flight per warp
+    long long nwarp = (long long)gridDim.x * wpb;
+    for (long long i0 = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); i0 < S.n; i0 += nwarp * UR) {
+        float u[UR][NCH][8];
+#pragma unroll
+        for (int q = 0; q < UR; ++q) {
+            long long i = i0 + q * nwarp;
+            bool ok = i < S.n;
+            const TU *row = U + (ok ? i : 0) * S.ld;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                int j0 = c * 256 + lane * 8;
+                if (ok && j0 < r) load8(row + j0, u[q][c]);
+                else
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) u[q][c][k] = 0.f;
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-        }
-        if (lane == 0) {
-            float4 d = din ? din[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-            dout[i] = make_float4(d.x + a0, d.y + a1, d.z + a2, 0.f);
+#pragma unroll
+        for (int q = 0; q < UR; ++q) {
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    a0 = fmaf(u[q][c][k], ql[c][k][0], a0);
+                    a1 = fmaf(u[q][c][k], ql[c][k][1], a1);
+                    a2 = fmaf(u[q][c][k], ql[c][k][2], a2);
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            }
+            long long i = i0 + q * nwarp;
+            if (lane == 0 && i < S.n) {
+                float4 d = din ? din[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                dout[i] = make_float4(d.x + a0, d.y + a1, d.z + a2, 0.f);
+            }
         }
     }
 }

@@ -143,6 +143,9 @@ void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const flo
 void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                       const float4 *dprev, float4 *dout, float4 *dnew, float alpha, float beta, const float4 *x,
                       float4 *xout, Scalars *sc, float4 *xprev, float w_acc);
+// Anderson mixing step on the iterate x (= x_k + delta_k on entry, x_{k+1} on exit).
+void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x, float4 *fprev,
+               float4 *gprev, float4 *dF, float4 *dG, int slot, int have_prev, int ncol, double *Gb, float *theta);
 void launch_line_search(cudaStream_t s, int nv_all, const float4 *xm, const float4 *xp, const double *s_frac,
                         float4 *xout);
 void launch_velocity(cudaStream_t s, int n, const float4 *xnew, const float4 *xs, float inv_h, float4 *v);

@@ -28,7 +28,7 @@ struct SubspaceWork {
     int *flag;         // factorisation status
 };
 
-constexpr int PROJ_BLOCKS = 304;
+constexpr int PROJ_BLOCKS = 608;
 
 // g = U[:, :r]^T rl  (r = r_c if *n_cv > 0 else r_nc).
 void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W);

@@ -40,7 +40,7 @@ class pdc_params(ctypes.Structure):
                 ("r_warm", c_i32), ("r_reuse", c_i32), ("precision", c_i32), ("samples_vt", c_i32),
                 ("samples_ee", c_i32), ("collisions", c_i32), ("fixed_iters", c_i32), ("eig_iters", c_i32),
                 ("seed", c_u64), ("accel", c_i32), ("accel_rho", c_dbl), ("sweep_kind", c_i32),
-                ("cheb_ratio", c_dbl)]
+                ("cheb_ratio", c_dbl), ("aa_depth", c_i32)]
 
 
 class pdc_stats(ctypes.Structure):
