@@ -477,6 +477,18 @@ class Oracle:
                 break
 
         if not p.collisions:
+            # without collision handling the inner LG loop of Alg. 1 still runs,
+            # with no springs, partial CCD or full CCD
+            for it in range(p.max_inner):
+                if p.tol_rel_residual > 0 and not p.fixed_iters:
+                    if self.rel_residual(x, z) <= p.tol_rel_residual * rho0:
+                        break
+                xn = self._lg(x, z, pin_next)
+                st.inner_iters += 1
+                dx = np.max(np.abs(xn - x)) if len(x) else 0.0
+                x = xn
+                if not p.fixed_iters and p.tol_rel_residual <= 0 and dx <= p.tol_inner * L:
+                    break
             x_new = x
             st.rel_residual = self.rel_residual(x_new, z) / max(rho0, 1e-300)
             v_new = (x_new - x_star) / h

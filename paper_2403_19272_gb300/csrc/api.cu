@@ -46,21 +46,30 @@ __global__ void k_step_fraction(const unsigned long long *toi_bits, double alpha
     *t_out = t;
     *s_out = (t <= 1.0) ? alpha * t : 1.0;
 }
-// final state: x = xm + s (xp - xm) (or xp), v = (x - x*)/h for cloth vertices
-__global__ void k_finish(int nv, int n, const float4 *__restrict__ xm, const float4 *__restrict__ xp,
-                         const double *s_frac, int use_lerp, float inv_h, float4 *__restrict__ xs, float4 *__restrict__ vs) {
+// final state (exit line search of Alg. 1): cloth u = um + s (up - um) (or up),
+// x = x* + u, v = u / h; obstacle vertices lerp between their absolute x^- and x^+.
+__global__ void k_finish(int nv, int n, const float4 *__restrict__ um, const float4 *__restrict__ up,
+                         const float4 *__restrict__ xm, const float4 *__restrict__ xp, const double *s_frac,
+                         int use_lerp, float inv_h, float4 *__restrict__ xs, float4 *__restrict__ vs) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
-    float3 xn;
-    if (use_lerp) {
-        float s = (float)*s_frac;
-        float3 a = f3(xm[i]), b = f3(xp[i]);
-        xn = a + s * (b - a);
+    float s = use_lerp ? (float)*s_frac : 1.f;
+    if (i < n) {
+        float3 d = f3(up[i]);
+        if (use_lerp) {
+            float3 a = f3(um[i]);
+            d = a + s * (d - a);
+        }
+        vs[i] = f4(inv_h * d);
+        xs[i] = f4(f3(xs[i]) + d);
     } else {
-        xn = f3(xp[i]);
+        float3 b = f3(xp[i]);
+        if (use_lerp) {
+            float3 a = f3(xm[i]);
+            b = a + s * (b - a);
+        }
+        xs[i] = f4(b);
     }
-    if (i < n) vs[i] = f4(inv_h * (xn - f3(xs[i])));
-    xs[i] = f4(xn);
 }
 __global__ void k_maxdiff(int n, const float4 *__restrict__ a, const float4 *__restrict__ b, unsigned int *out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -196,6 +205,7 @@ struct pdc_ctx {
     // state (collision-vertex arrays: cloth first, obstacles after)
     DevBuf<float4> Xs, Vs, Z, Xp, Xm, Xbak, Vbak, Xprev;
     DevBuf<float4> R, RL, D0, D1, CF;
+    DevBuf<float4> Ucur, Um;  // iterate and x^- as displacements from x* (cloth vertices)
     DevBuf<float> CW;
     DevBuf<float> stage3;  // staging for float[3] transfers
     // obstacles
@@ -590,6 +600,8 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
     R.alloc(n);
     RL.alloc(n);
     Xacc.alloc(n);
+    Ucur.alloc(n);
+    Um.alloc(n);
     if (P.sweep_kind == 1) {
         CD0.alloc(n);
         CD1.alloc(n);
@@ -771,7 +783,7 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
     } else {
         n_cv_d.zero(s);
     }
-    PROF("local_residual", bytes_residual(contacts), launch_residual(s, c, Xp, Z, cw, cf, R, sc, nullptr, 0));
+    PROF("local_residual", bytes_residual(contacts), launch_residual(s, c, Xs, Ucur, Z, cw, cf, R, sc, nullptr, 0));
     bool acc = accel.on && !(P.fixed_iters != 0);
     bool aa = acc && P.accel == 2;
     if (check_rel || log || acc) {
@@ -841,8 +853,9 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
                     rho_prev = rk;
                 }
                 PROF("cheb_sweep", bytes_sweep(contacts, last) + 24.0 * n,
-                     launch_cheb_step(s, c, cw, R, din, dp, dout, dq, (float)alpha, (float)beta, Xp,
-                                      last ? Xp.p : nullptr, last ? sc.p : nullptr, last ? xprev : nullptr, w_acc));
+                     launch_cheb_step(s, c, cw, R, din, dp, dout, dq, (float)alpha, (float)beta, Ucur,
+                                      last ? Ucur.p : nullptr, last ? sc.p : nullptr, last ? xprev : nullptr, w_acc,
+                                      Xs, last ? Xp.p : nullptr));
                 std::swap(din, dout);
                 std::swap(dp, dq);
             }
@@ -850,14 +863,14 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             for (int k = 0; k < sweeps; ++k) {
                 bool last = (cyc == cycles - 1) && (k == sweeps - 1);
                 PROF("jacobi_sweep", bytes_sweep(contacts, last),
-                     launch_sweep(s, c, cw, R, din, dout, (float)omega, Xp, last ? Xp.p : nullptr,
-                                  last ? sc.p : nullptr, last ? xprev : nullptr, w_acc));
+                     launch_sweep(s, c, cw, R, din, dout, (float)omega, Ucur, last ? Ucur.p : nullptr,
+                                  last ? sc.p : nullptr, last ? xprev : nullptr, w_acc, Xs, last ? Xp.p : nullptr));
                 std::swap(din, dout);
             }
         }
         if (sweeps == 0 && cyc == cycles - 1) {
             // no sweep: apply the correction directly
-            launch_sweep(s, c, cw, R, din, dout, 0.f, Xp, Xp.p, sc.p, xprev, w_acc);
+            launch_sweep(s, c, cw, R, din, dout, 0.f, Ucur, Ucur.p, sc.p, xprev, w_acc, Xs, Xp.p);
         }
     }
     if (aa) {
@@ -869,8 +882,8 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             accel.aa_count = std::min(accel.aa_count + 1, m);
         }
         PROF("anderson_mix", 0,
-             launch_aa(s, n, is_free, din, Xp, aa_f, aa_g, aa_dF, aa_dG, slot, accel.aa_have_prev ? 1 : 0,
-                       accel.aa_count, aa_Gb, aa_theta));
+             launch_aa(s, n, is_free, din, Ucur, aa_f, aa_g, aa_dF, aa_dG, slot, accel.aa_have_prev ? 1 : 0,
+                       accel.aa_count, aa_Gb, aa_theta, Xs, Xp));
         accel.aa_have_prev = true;
     }
     if (contacts && P.collisions) {
@@ -906,12 +919,12 @@ void pdc_ctx::step() {
 
     // Eq. (z) and x <- z (Alg. 1); obstacles move to their targets in x^+
     float3 g = make_float3((float)P.gravity[0], (float)P.gravity[1], (float)P.gravity[2]);
-    launch_prologue(s, n, Xs, Vs, pins_d, pin_tgt, npins, h, g, Z, Xp);
+    launch_prologue(s, n, Xs, Vs, pins_d, pin_tgt, npins, h, g, Z, Ucur, Xp);
     if (nv_all > n)
         PDC_CK(cudaMemcpyAsync(Xp.p + n, obs_tgt.p, sizeof(float4) * (nv_all - n), cudaMemcpyDeviceToDevice, s));
     // rho0 = residual at z (no collision springs)
     PDC_CK(cudaMemsetAsync(&sc.p->rsq, 0, sizeof(double), s));
-    launch_residual(s, c, Xp, Z, nullptr, nullptr, R, sc, nullptr, 0);
+    launch_residual(s, c, Xs, Ucur, Z, nullptr, nullptr, R, sc, nullptr, 0);
     read_scalars();
     double rho0 = std::sqrt(hsc->rsq);
     st.rho0 = rho0;
@@ -934,16 +947,37 @@ void pdc_ctx::step() {
     }
 
     bool use_lerp = false;
-    if (P.collisions) {
+    if (!P.collisions) {
+        // no collision handling: the inner LG loop without springs or CCD
+        accel.reset();
+        for (int it = 0; it < P.max_inner; ++it) {
+            bool conv = false;
+            lg_iteration(false, relmode, rho0, conv, r_warm, 0, cycles, sweeps);
+            if (conv) break;
+            st.inner_iters++;
+            if (!fixed && !relmode) {
+                read_scalars();
+                if (bits_to_float(hsc->dxmax) <= tolx_in) break;
+            }
+        }
+    } else {
         use_lerp = true;
         // initial full CCD from x* to the warm start, filter -> x^- (Alg. 1)
         full_ccd(Xs, Xp, false);
-        launch_lerp(s, nv_all, Xs, Xp, sfrac, Xm);
+        if (log) {
+            double t0v = 0, s0v = 0;
+            ttoi.download(&t0v, 1, s);
+            sfrac.download(&s0v, 1, s);
+            PDC_CK(cudaStreamSynchronize(s));
+            std::fprintf(stderr, "[pdc] initial full CCD: t_toi=%.6g s=%.6g\n", t0v, s0v);
+        }
+        launch_lerp(s, nv_all, Xs, Xp, sfrac, Xm);                // obstacles (and cloth, overwritten next)
+        launch_scale_disp(s, n, Xs, Ucur, sfrac, Um, Xm);         // cloth x^- = x* + s u
         // the iterate restarts at x^- with pins at their targets
-        PDC_CK(cudaMemcpyAsync(Xp.p, Xm.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
-        launch_set_pins(s, pins_d, npins, pin_tgt, Xp);
+        launch_restart(s, n, Xs, Um, Ucur, Xp);
+        launch_set_pins(s, pins_d, npins, pin_tgt, Xs, Ucur, Xp);
         launch_collect_active(s, coll(), bp, Xm, cparams(), act, cap_act, n_act_d, &sc.p->overflow);
-        PDC_CK(cudaMemcpyAsync(Xprev.p, Xm.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+        PDC_CK(cudaMemcpyAsync(Xprev.p, Um.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
         unsigned long long none = 0x4000000000000000ULL;  // 2.0: no impact yet
         PDC_CK(cudaMemcpyAsync(toi_bits.p, &none, sizeof(none), cudaMemcpyHostToDevice, s));
         k_step_fraction<<<1, 1, 0, s>>>(toi_bits, P.alpha_ls, sfrac, ttoi);
@@ -969,18 +1003,18 @@ void pdc_ctx::step() {
             }
             if (!fixed) {
                 umax_d.zero(s);
-                k_maxdiff<<<nb(n), 256, 0, s>>>(n, Xp, Xprev, umax_d);
+                k_maxdiff<<<nb(n), 256, 0, s>>>(n, Ucur, Xprev, umax_d);
                 PDC_LAUNCH_CK();
                 unsigned int um = 0;
                 umax_d.download(&um, 1, s);
                 PDC_CK(cudaStreamSynchronize(s));
-                PDC_CK(cudaMemcpyAsync(Xprev.p, Xp.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+                PDC_CK(cudaMemcpyAsync(Xprev.p, Ucur.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
                 if (bits_to_float(um) <= tolx_out) break;
             }
         }
     }
     // exit line search and velocities (Alg. 1; v = (x - x*)/h)
-    k_finish<<<nb(nv_all), 256, 0, s>>>(nv_all, n, Xm, Xp, sfrac, use_lerp ? 1 : 0, 1.f / h, Xs, Vs);
+    k_finish<<<nb(nv_all), 256, 0, s>>>(nv_all, n, Um, Ucur, Xm, Xp, sfrac, use_lerp ? 1 : 0, 1.f / h, Xs, Vs);
     PDC_LAUNCH_CK();
     bad_d.zero(s);
     k_finite<<<nb(n), 256, 0, s>>>(n, Xs, bad_d);
@@ -1466,11 +1500,16 @@ static void upload_contact(pdc_handle h, const float *cw, const float *cf) {
 pdc_status pdc_op_residual(pdc_handle h, const float *x, const float *z, const float *cw, const float *cf, float *r) {
     API_BEGIN(h)
     if (!x || !z || !r) throw Error(PDC_ERR_ARG, "pdc_op_residual: NULL");
-    DevBuf<float4> a, b;
+    // reference x* = x, displacement u = 0, z - x* = z - x (differences in double)
+    DevBuf<float4> a, u0, zr;
     upload_f4(h, x, h->n, a);
-    upload_f4(h, z, h->n, b);
+    std::vector<float> d(3 * (size_t)h->n);
+    for (size_t k = 0; k < d.size(); ++k) d[k] = (float)((double)z[k] - (double)x[k]);
+    upload_f4(h, d.data(), h->n, zr);
+    u0.alloc(h->n);
+    u0.zero(h->s);
     upload_contact(h, cw, cf);
-    launch_residual(h->s, h->cloth(), a, b, h->CW, h->CF, h->R, nullptr, nullptr, 0);
+    launch_residual(h->s, h->cloth(), a, u0, zr, h->CW, h->CF, h->R, nullptr, nullptr, 0);
     get_f4(h, h->R, r, 0);
     API_END(h)
 }
@@ -1483,9 +1522,14 @@ pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, con
     if (r > 128) throw Error(PDC_ERR_ARG, "pdc_op_global_solve: r must be <= 128");
     cudaStream_t s = h->s;
     int n = h->n;
-    DevBuf<float4> xa, za;
+    DevBuf<float4> xa, za, ua, xo;
     upload_f4(h, x, n, xa);
-    upload_f4(h, z, n, za);
+    std::vector<float> dz(3 * (size_t)n);
+    for (size_t k = 0; k < dz.size(); ++k) dz[k] = (float)((double)z[k] - (double)x[k]);
+    upload_f4(h, dz.data(), n, za);
+    ua.alloc(n);
+    ua.zero(s);
+    xo.alloc(n);
     upload_contact(h, cw, cf);
     ClothView c = h->cloth();
     if (h->dA.n < (size_t)std::max(r * r, 1)) h->dA.alloc((size_t)r * r);
@@ -1497,7 +1541,7 @@ pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, con
     one.upload(&o1, 1, s);
     ncv.alloc(1);
     launch_contact_list(s, n, h->CW, h->contact_list, ncv);
-    launch_residual(s, c, xa, za, h->CW, h->CF, h->R, nullptr, nullptr, 0);
+    launch_residual(s, c, xa, ua, za, h->CW, h->CF, h->R, nullptr, nullptr, 0);
     float4 *din = h->D0, *dout = h->D1;
     bool have = false;
     for (int cyc = 0; cyc < cycles; ++cyc) {
@@ -1524,8 +1568,8 @@ pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, con
             std::swap(din, dout);
         }
     }
-    launch_sweep(s, c, h->CW, h->R, din, dout, 0.f, xa, xa.p, nullptr);  // x_out = x + delta
-    get_f4(h, xa, x_out, 0);
+    launch_sweep(s, c, h->CW, h->R, din, dout, 0.f, ua, ua.p, nullptr, nullptr, 1.f, xa, xo.p);  // x + delta
+    get_f4(h, xo, x_out, 0);
     API_END(h)
 }
 

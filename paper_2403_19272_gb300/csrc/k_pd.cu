@@ -81,42 +81,81 @@ __device__ inline void polar32(float3 f1, float3 f2, float3 &r1, float3 &r2) {
     r2 = (1.f / n2) * c2;
 }
 
+// Positions inside a step are carried as x = x* + u: x* (the step's start
+// state, FP32) stays fixed and u is a small FP32 displacement.  Differences
+// of neighbouring x* entries are exact in FP32, so element quantities keep
+// the precision of u instead of the ulp of the absolute coordinates.
+
+// Eq. (z): z - x* = h v* + h^2 g (f_ext = m g); the iterate starts at u = z - x*.
 __global__ void k_prologue(int n, const float4 *__restrict__ xs, const float4 *__restrict__ vs, float h, float3 g,
-                           float4 *__restrict__ z, float4 *__restrict__ x) {
+                           float4 *__restrict__ zrel, float4 *__restrict__ u, float4 *__restrict__ xabs) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float3 p = f3(xs[i]), v = f3(vs[i]);
-    float3 zz = p + h * v + (h * h) * g;   // Eq. (z), f_ext = m g
-    float4 o = f4(zz);
-    z[i] = o;
-    x[i] = o;
+    float3 v = f3(vs[i]);
+    float3 d = h * v + (h * h) * g;
+    float4 o = f4(d);
+    zrel[i] = o;
+    u[i] = o;
+    xabs[i] = f4(f3(xs[i]) + d);
 }
 
-__global__ void k_set_pins(const int *__restrict__ pins, int np, const float4 *__restrict__ tgt, float4 *__restrict__ x) {
+// pinned rows: u = target - x*, absolute position = target (zrel too if given)
+__global__ void k_set_pins(const int *__restrict__ pins, int np, const float4 *__restrict__ tgt,
+                           const float4 *__restrict__ xs, float4 *__restrict__ zrel, float4 *__restrict__ u,
+                           float4 *__restrict__ xabs) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < np) x[pins[i]] = tgt[i];
+    if (i >= np) return;
+    int p = pins[i];
+    float4 d = f4(f3(tgt[i]) - f3(xs[p]));
+    if (zrel) zrel[p] = d;
+    u[p] = d;
+    xabs[p] = tgt[i];
+}
+
+// u = um (the displacement of x^-), xabs = x* + um
+__global__ void k_restart(int n, const float4 *__restrict__ xs, const float4 *__restrict__ um, float4 *__restrict__ u,
+                          float4 *__restrict__ xabs) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 d = um[i];
+    u[i] = d;
+    xabs[i] = f4(f3(xs[i]) + f3(d));
+}
+
+// um = s u (cloth part of the filtered x^-), xm = x* + um
+__global__ void k_scale_disp(int n, const float4 *__restrict__ xs, const float4 *__restrict__ u, const double *s_frac,
+                             float4 *__restrict__ um, float4 *__restrict__ xm) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = (float)*s_frac;
+    float3 d = s * f3(u[i]);
+    um[i] = f4(d);
+    xm[i] = f4(f3(xs[i]) + d);
 }
 
 // r_i = m_i/h^2 (z_i - x_i) + sum_t w_t (R_t - F_t) g_{t,i} + sum_h w_h K_{h,i} (s_hat_h - s_h) + cf_i
-__global__ void __launch_bounds__(256) k_residual(const ClothView c, const float4 *__restrict__ x,
-                                                  const float4 *__restrict__ z, const float *__restrict__ cw,
-                                                  const float4 *__restrict__ cf, float4 *__restrict__ r,
-                                                  Scalars *sc, float *__restrict__ r_soa, int soa_ld) {
+__device__ inline float3 dpos(const float4 *__restrict__ xs, const float4 *__restrict__ u, int a, int b) {
+    return (f3(xs[a]) - f3(xs[b])) + (f3(u[a]) - f3(u[b]));  // (x*_a - x*_b) + (u_a - u_b)
+}
+
+__global__ void __launch_bounds__(256) k_residual(const ClothView c, const float4 *__restrict__ xs,
+                                                  const float4 *__restrict__ u, const float4 *__restrict__ zrel,
+                                                  const float *__restrict__ cw, const float4 *__restrict__ cf,
+                                                  float4 *__restrict__ r, Scalars *sc, float *__restrict__ r_soa,
+                                                  int soa_ld) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float sq = 0.f;
     if (i < c.n) {
         float3 f = make_float3(0.f, 0.f, 0.f);
         if (c.is_free[i]) {
-            float3 xi = f3(x[i]);
-            f = c.mh2[i] * (f3(z[i]) - xi);
+            f = c.mh2[i] * (f3(zrel[i]) - f3(u[i]));
             for (int e = c.vt_off[i]; e < c.vt_off[i + 1]; ++e) {
                 int ent = c.vt_list[e];
                 int t = ent >> 2, corner = ent & 3;
                 int4 T = c.tri[t];
                 float4 g = c.tri_g[t];
                 float w = c.tri_w[t];
-                float3 x0 = f3(x[T.x]);
-                float3 e1 = f3(x[T.y]) - x0, e2 = f3(x[T.z]) - x0;
+                float3 e1 = dpos(xs, u, T.y, T.x), e2 = dpos(xs, u, T.z, T.x);
                 float3 F1 = g.x * e1 + g.z * e2;   // column 1 of F = [e1 e2] Dm^-1
                 float3 F2 = g.y * e1 + g.w * e2;   // column 2
                 float3 R1, R2;
@@ -130,8 +169,8 @@ __global__ void __launch_bounds__(256) k_residual(const ClothView c, const float
                 int hh = ent >> 2, slot = ent & 3;
                 int4 Hh = c.hin[hh];
                 float4 K = c.hin_K[hh];
-                float3 p0 = f3(x[Hh.x]);
-                float3 s = K.y * (f3(x[Hh.y]) - p0) + K.z * (f3(x[Hh.z]) - p0) + K.w * (f3(x[Hh.w]) - p0);
+                float3 s = K.y * dpos(xs, u, Hh.y, Hh.x) + K.z * dpos(xs, u, Hh.z, Hh.x) +
+                           K.w * dpos(xs, u, Hh.w, Hh.x);
                 float sl = c.hin_slen[hh];
                 float3 sh;
                 float ns = sqrtf(dot3(s, s));
@@ -163,6 +202,7 @@ __global__ void __launch_bounds__(256) k_sweep(const ClothView c, const float *_
                                                const float4 *__restrict__ r, const float4 *__restrict__ din,
                                                float4 *__restrict__ dout, float omega,
                                                const float4 *x, float4 *xout, float4 *xprev, float w_acc,
+                                               const float4 *__restrict__ xs, float4 *__restrict__ xabs,
                                                Scalars *sc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float mx = 0.f;
@@ -193,6 +233,7 @@ __global__ void __launch_bounds__(256) k_sweep(const ClothView c, const float *_
                 xprev[i] = f4(xo);
             }
             xout[i] = f4(xn);
+            if (xabs) xabs[i] = f4(f3(xs[i]) + xn);
             float3 d = xn - xo;
             mx = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z)));
         }
@@ -212,6 +253,7 @@ __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const floa
                                                    const float4 *__restrict__ dprev, float4 *__restrict__ dout,
                                                    float4 *__restrict__ dnew, float alpha, float beta,
                                                    const float4 *x, float4 *xout, float4 *xprev, float w_acc,
+                                                   const float4 *__restrict__ xs, float4 *__restrict__ xabs,
                                                    Scalars *sc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float mx = 0.f;
@@ -245,6 +287,7 @@ __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const floa
                 xprev[i] = f4(xo);
             }
             xout[i] = f4(xn);
+            if (xabs) xabs[i] = f4(f3(xs[i]) + xn);
             float3 d = xn - xo;
             mx = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z)));
         }
@@ -358,13 +401,15 @@ __global__ void k_aa_solve(int ncol, const double *__restrict__ Gb, float *__res
 // x_{k+1} = g_k - sum_j theta_j dG_j on free vertices.
 __global__ void __launch_bounds__(256) k_aa_mix(int n, const unsigned char *__restrict__ is_free,
                                                 const float4 *__restrict__ xhat, const float4 *__restrict__ dG,
-                                                int ncol, const float *__restrict__ theta, float4 *__restrict__ xout) {
+                                                int ncol, const float *__restrict__ theta, float4 *__restrict__ xout,
+                                                const float4 *__restrict__ xs, float4 *__restrict__ xabs) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float3 x = f3(xhat[i]);
     if (is_free[i])
         for (int j = 0; j < ncol; ++j) x = x - theta[j] * f3(dG[(size_t)j * n + i]);
     xout[i] = f4(x);
+    if (xabs) xabs[i] = f4(f3(xs[i]) + x);
 }
 
 __global__ void k_lerp(int nv, const float4 *__restrict__ a, const float4 *__restrict__ b, const double *s_frac,
@@ -388,52 +433,64 @@ inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 }  // namespace
 
 void launch_prologue(cudaStream_t s, int n, const float4 *xs, const float4 *vs, const int *pins, const float4 *pin_tgt,
-                     int npins, float h, float3 g, float4 *z, float4 *x) {
-    if (n > 0) k_prologue<<<nblk(n, 256), 256, 0, s>>>(n, xs, vs, h, g, z, x);
+                     int npins, float h, float3 g, float4 *zrel, float4 *u, float4 *xabs) {
+    if (n > 0) k_prologue<<<nblk(n, 256), 256, 0, s>>>(n, xs, vs, h, g, zrel, u, xabs);
     PDC_LAUNCH_CK();
     if (npins > 0) {
-        k_set_pins<<<nblk(npins, 256), 256, 0, s>>>(pins, npins, pin_tgt, z);
-        k_set_pins<<<nblk(npins, 256), 256, 0, s>>>(pins, npins, pin_tgt, x);
+        k_set_pins<<<nblk(npins, 256), 256, 0, s>>>(pins, npins, pin_tgt, xs, zrel, u, xabs);
         PDC_LAUNCH_CK();
     }
 }
 
-void launch_set_pins(cudaStream_t s, const int *pins, int npins, const float4 *tgt, float4 *x) {
-    if (npins > 0) k_set_pins<<<nblk(npins, 256), 256, 0, s>>>(pins, npins, tgt, x);
+void launch_set_pins(cudaStream_t s, const int *pins, int npins, const float4 *tgt, const float4 *xs, float4 *u,
+                     float4 *xabs) {
+    if (npins > 0) k_set_pins<<<nblk(npins, 256), 256, 0, s>>>(pins, npins, tgt, xs, nullptr, u, xabs);
     PDC_LAUNCH_CK();
 }
 
-void launch_residual(cudaStream_t s, const ClothView &c, const float4 *x, const float4 *z, const float *cw,
-                     const float4 *cf, float4 *r, Scalars *sc, float *r_soa, int soa_ld) {
-    (void)cw;
-    if (c.n > 0) k_residual<<<nblk(c.n, 256), 256, 0, s>>>(c, x, z, cw, cf, r, sc, r_soa, soa_ld);
+void launch_restart(cudaStream_t s, int n, const float4 *xs, const float4 *um, float4 *u, float4 *xabs) {
+    if (n > 0) k_restart<<<nblk(n, 256), 256, 0, s>>>(n, xs, um, u, xabs);
+    PDC_LAUNCH_CK();
+}
+
+void launch_scale_disp(cudaStream_t s, int n, const float4 *xs, const float4 *u, const double *s_frac, float4 *um,
+                       float4 *xm) {
+    if (n > 0) k_scale_disp<<<nblk(n, 256), 256, 0, s>>>(n, xs, u, s_frac, um, xm);
+    PDC_LAUNCH_CK();
+}
+
+void launch_residual(cudaStream_t s, const ClothView &c, const float4 *xs, const float4 *u, const float4 *zrel,
+                     const float *cw, const float4 *cf, float4 *r, Scalars *sc, float *r_soa, int soa_ld) {
+    if (c.n > 0) k_residual<<<nblk(c.n, 256), 256, 0, s>>>(c, xs, u, zrel, cw, cf, r, sc, r_soa, soa_ld);
     PDC_LAUNCH_CK();
 }
 
 void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                   float4 *dout, float omega, const float4 *x, float4 *xout, Scalars *sc, float4 *xprev,
-                  float w_acc) {
-    if (c.n > 0) k_sweep<<<nblk(c.n, 256), 256, 0, s>>>(c, cw, r, din, dout, omega, x, xout, xprev, w_acc, sc);
+                  float w_acc, const float4 *xs, float4 *xabs) {
+    if (c.n > 0)
+        k_sweep<<<nblk(c.n, 256), 256, 0, s>>>(c, cw, r, din, dout, omega, x, xout, xprev, w_acc, xs, xabs, sc);
     PDC_LAUNCH_CK();
 }
 
 void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                       const float4 *dprev, float4 *dout, float4 *dnew, float alpha, float beta, const float4 *x,
-                      float4 *xout, Scalars *sc, float4 *xprev, float w_acc) {
+                      float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs) {
     if (c.n > 0)
         k_cheb_step<<<nblk(c.n, 256), 256, 0, s>>>(c, cw, r, din, dprev, dout, dnew, alpha, beta, x, xout, xprev,
-                                                     w_acc, sc);
+                                                     w_acc, xs, xabs, sc);
     PDC_LAUNCH_CK();
 }
 
 void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x, float4 *fprev,
-               float4 *gprev, float4 *dF, float4 *dG, int slot, int have_prev, int ncol, double *Gb, float *theta) {
+               float4 *gprev, float4 *dF, float4 *dG, int slot, int have_prev, int ncol, double *Gb, float *theta,
+               const float4 *xs, float4 *xabs) {
     if (n <= 0) return;
     PDC_CK(cudaMemsetAsync(Gb, 0, sizeof(double) * (AA_MAX * (AA_MAX + 3) / 2 + AA_MAX), s));
     k_aa_gram<<<nblk(n, 256), 256, 0, s>>>(n, is_free, delta, x, fprev, gprev, dF, dG, slot, have_prev, ncol, Gb);
     if (ncol > 0) {
         k_aa_solve<<<1, 32, 0, s>>>(ncol, Gb, theta);
-        k_aa_mix<<<nblk(n, 256), 256, 0, s>>>(n, is_free, x, dG, ncol, theta, x);
+        k_aa_mix<<<nblk(n, 256), 256, 0, s>>>(n, is_free, x, dG, ncol, theta, x, xs, xabs);
     }
     PDC_LAUNCH_CK();
 }

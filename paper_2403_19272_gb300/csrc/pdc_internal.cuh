@@ -133,24 +133,30 @@ struct Scalars {
 };
 
 // ---------------------------------------------------------------- kernels (k_pd.cu)
+// Inside a step positions are x = x* + u (x* = xs fixed, u a small FP32
+// displacement); zrel = z - x*; xabs receives absolute positions for the
+// collision kernels.
 void launch_prologue(cudaStream_t s, int n, const float4 *xs, const float4 *vs, const int *pins, const float4 *pin_tgt,
-                     int npins, float h, float3 g, float4 *z, float4 *x);
-void launch_residual(cudaStream_t s, const ClothView &c, const float4 *x, const float4 *z, const float *cw,
-                     const float4 *cf, float4 *r, Scalars *sc, float *r_soa, int soa_ld);
+                     int npins, float h, float3 g, float4 *zrel, float4 *u, float4 *xabs);
+void launch_residual(cudaStream_t s, const ClothView &c, const float4 *xs, const float4 *u, const float4 *zrel,
+                     const float *cw, const float4 *cf, float4 *r, Scalars *sc, float *r_soa, int soa_ld);
 void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                   float4 *dout, float omega, const float4 *x, float4 *xout, Scalars *sc, float4 *xprev = nullptr,
-                  float w_acc = 1.f);
+                  float w_acc = 1.f, const float4 *xs = nullptr, float4 *xabs = nullptr);
 void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                       const float4 *dprev, float4 *dout, float4 *dnew, float alpha, float beta, const float4 *x,
-                      float4 *xout, Scalars *sc, float4 *xprev, float w_acc);
-// Anderson mixing step on the iterate x (= x_k + delta_k on entry, x_{k+1} on exit).
+                      float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs);
+// Anderson mixing step on the iterate u (= u_k + delta_k on entry, u_{k+1} on exit).
 void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x, float4 *fprev,
-               float4 *gprev, float4 *dF, float4 *dG, int slot, int have_prev, int ncol, double *Gb, float *theta);
-void launch_line_search(cudaStream_t s, int nv_all, const float4 *xm, const float4 *xp, const double *s_frac,
-                        float4 *xout);
-void launch_velocity(cudaStream_t s, int n, const float4 *xnew, const float4 *xs, float inv_h, float4 *v);
+               float4 *gprev, float4 *dF, float4 *dG, int slot, int have_prev, int ncol, double *Gb, float *theta,
+               const float4 *xs, float4 *xabs);
 void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out);
-void launch_set_pins(cudaStream_t s, const int *pins, int npins, const float4 *tgt, float4 *x);
+void launch_set_pins(cudaStream_t s, const int *pins, int npins, const float4 *tgt, const float4 *xs, float4 *u,
+                     float4 *xabs);
+void launch_restart(cudaStream_t s, int n, const float4 *xs, const float4 *um, float4 *u, float4 *xabs);
+void launch_scale_disp(cudaStream_t s, int n, const float4 *xs, const float4 *u, const double *s_frac, float4 *um,
+                       float4 *xm);
+void launch_velocity(cudaStream_t s, int n, const float4 *xnew, const float4 *xs, float inv_h, float4 *v);
 
 // ---------------------------------------------------------------- kernels (k_collide.cu)
 struct BroadPhase;
