@@ -232,7 +232,7 @@ struct pdc_ctx {
     Scalars *hsc = nullptr;
     DevBuf<double> sfrac, ttoi;
     DevBuf<unsigned long long> toi_bits;
-    DevBuf<int> n_act_d, n_cv_d, bad_d;
+    DevBuf<int> n_act_d, n_cv_d, bad_d, bp_ovf;
     DevBuf<unsigned int> umax_d;
     pdc_stats st;
     bool stepped = false;
@@ -629,6 +629,7 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
     ttoi.alloc(1);
     toi_bits.alloc(1);
     n_act_d.alloc(1);
+    bp_ovf.alloc(1);
     n_cv_d.alloc(1);
     bad_d.alloc(1);
     umax_d.alloc(1);
@@ -894,7 +895,26 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
 
 void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {
     bp.prof = prof.on ? &prof : nullptr;
-    PROF("broad_phase", 0, bp.run(s, coll(), x0, x1, dhat, &sc.p->overflow));
+    // broad phase; a list or table that overflows is regrown and rebuilt here
+    // (candidate sets spike while the iterate is far from converged), so the
+    // step itself need not be redone
+    for (int tries = 0;; ++tries) {
+        int cur0 = bp.cur;
+        bp_ovf.zero(s);
+        PROF("broad_phase", 0, bp.run(s, coll(), x0, x1, dhat, bp_ovf));
+        int ovf = 0;
+        bp_ovf.download(&ovf, 1, s);
+        PDC_CK(cudaStreamSynchronize(s));
+        if (!ovf) break;
+        if (tries >= 6) throw Error(PDC_ERR_CAPACITY, "broad phase buffers could not be grown enough");
+        bp.cur = cur0;  // the previous lists stay the merge source of the rebuilt ones
+        long long cvt = bp.cap_vt * ((ovf & OVF_VT) ? 2 : 1), cee = bp.cap_ee * ((ovf & OVF_EE) ? 2 : 1),
+                  cent = bp.cap_ent * ((ovf & OVF_HASH) ? 2 : 1);
+        if (ovf & OVF_CELLS) bp.cell_scale *= 4.f;
+        bp.grow(coll(), cvt, cee, cent, s);  // keeps the current lists (NDB states merge from them)
+        st.overflow_retries++;
+        if (log) std::fprintf(stderr, "[pdc] broad phase regrown after overflow 0x%x\n", ovf);
+    }
     unsigned long long inf = 0x7ff0000000000000ULL;  // +inf
     PDC_CK(cudaMemcpyAsync(toi_bits.p, &inf, sizeof(inf), cudaMemcpyHostToDevice, s));
     PROF("full_ccd", 0, launch_full_ccd(s, coll(), bp, x0, x1, cparams(), merge, toi_bits));

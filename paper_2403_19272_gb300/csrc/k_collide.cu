@@ -350,6 +350,43 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
     }
 }
 
+template <class T> static void grow_keep(DevBuf<T> &b, long long cap, cudaStream_t s) {
+    if ((long long)b.n >= cap) return;
+    DevBuf<T> nb;
+    nb.alloc(cap);
+    if (b.p && b.n) PDC_CK(cudaMemcpyAsync(nb.p, b.p, sizeof(T) * b.n, cudaMemcpyDeviceToDevice, s));
+    PDC_CK(cudaStreamSynchronize(s));
+    std::swap(b.p, nb.p);
+    std::swap(b.n, nb.n);
+}
+
+void BroadPhase::grow(const CollView &cv, long long cvt, long long cee, long long cent, cudaStream_t s) {
+    (void)cv;
+    if (cent > cap_ent) {
+        cap_ent = cent;
+        for (int k = 0; k < 2; ++k) {
+            ekey[k].alloc(cap_ent);
+            eprim[k].alloc(cap_ent);
+        }
+    }
+    if (cvt > cap_vt) {
+        cap_vt = cvt;
+        for (int k = 0; k < 2; ++k) {
+            grow_keep(vt[k], cap_vt, s);
+            grow_keep(st_vt[k], cap_vt, s);
+            grow_keep(d0_vt[k], cap_vt, s);
+        }
+    }
+    if (cee > cap_ee) {
+        cap_ee = cee;
+        for (int k = 0; k < 2; ++k) {
+            grow_keep(ee[k], cap_ee, s);
+            grow_keep(st_ee[k], cap_ee, s);
+            grow_keep(d0_ee[k], cap_ee, s);
+        }
+    }
+}
+
 // Builds the new candidate lists in buffer (cur ^ 1) and makes it current.
 #define BP_PROF(name, ...)                                                                            \
     do {                                                                                               \

@@ -58,6 +58,8 @@ struct BroadPhase {
     Profiler *prof = nullptr;  // optional sub-kernel timing
 
     void reserve(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent);
+    // larger capacities keeping the current candidate lists, states and counts
+    void grow(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent, cudaStream_t s);
     void run(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat, int *overflow);
 };
 
