@@ -240,7 +240,7 @@ struct pdc_ctx {
     Accel accel;
     float last_dx = 0.f;
     DevBuf<float4> Xacc;  // previous iterate for the accelerated update
-    DevBuf<float> disp;   // |x^+ - x^-| per collision vertex
+    DevBuf<float4> disp;  // x^+ - x^- per collision vertex
     DevBuf<float4> CD0, CD1;  // Chebyshev directions
     DevBuf<float4> aa_dF, aa_dG, aa_f, aa_g;  // Anderson history
     DevBuf<double> aa_Gb;

@@ -391,11 +391,11 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const in
 //         side 2) cannot satisfy Q <= dhat |d0| at any sample (|d1 - d0| is
 //         bounded by those displacements), so it is set inactive without
 //         evaluating the samples.
-__global__ void __launch_bounds__(PAIR_THREADS) k_pairs_update(CollView cv, const int2 *__restrict__ vt,
+__global__ void __launch_bounds__(PAIR_THREADS, 4) k_pairs_update(CollView cv, const int2 *__restrict__ vt,
                                                                const int2 *__restrict__ ee, const long long *nvt_p,
                                                                const long long *nee_p, unsigned char *st_vt,
                                                                unsigned char *st_ee, float *d0_vt, float *d0_ee,
-                                                               const float *__restrict__ disp,
+                                                               const float4 *__restrict__ disp4,
                                                                const float4 *__restrict__ xm,
                                                                const float4 *__restrict__ xp, CollParams P, int mode,
                                                                ActivePair *act, int cap, int *n_act, int *overflow) {
@@ -415,10 +415,18 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs_update(CollView cv, cons
             float c[4];
             bool near = true;
             if (mode == 1) {
-                float m1 = kind == 0 ? disp[ids[0]] : fmaxf(disp[ids[0]], disp[ids[1]]);
-                float m2 = kind == 0 ? fmaxf(disp[ids[1]], fmaxf(disp[ids[2]], disp[ids[3]]))
-                                     : fmaxf(disp[ids[2]], disp[ids[3]]);
-                near = *d0p <= (P.dhat + m1 + m2) * 1.001f + 1e-7f;
+                // |d1 - d0| at any sample is at most the largest relative
+                // displacement between a vertex of side 1 and one of side 2
+                float4 D[4];
+                for (int q = 0; q < 4; ++q) D[q] = disp4[ids[q]];
+                float rel = 0.f;
+                int n1 = kind == 0 ? 1 : 2;
+                for (int a = 0; a < n1; ++a)
+                    for (int b = n1; b < 4; ++b) {
+                        float3 dd = make_float3(D[b].x - D[a].x, D[b].y - D[a].y, D[b].z - D[a].z);
+                        rel = fmaxf(rel, dot3(dd, dd));
+                    }
+                near = *d0p <= (P.dhat + sqrtf(rel)) * 1.001f + 1e-7f;
             }
             float4 a0[4];
             if (near)
@@ -456,11 +464,10 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs_update(CollView cv, cons
     }
 }
 
-__global__ void k_disp(int nv, const float4 *__restrict__ a, const float4 *__restrict__ b, float *__restrict__ d) {
+__global__ void k_disp(int nv, const float4 *__restrict__ a, const float4 *__restrict__ b, float4 *__restrict__ d) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
-    float3 e = f3(b[i]) - f3(a[i]);
-    d[i] = sqrtf(dot3(e, e));
+    d[i] = f4(f3(b[i]) - f3(a[i]));
 }
 
 // Collision springs (Sec. 5.1, A_i = B_i = Id): constraint C(x) = d(x).n0 - dhat
@@ -591,7 +598,7 @@ void launch_collect_active(cudaStream_t s, const CollView &cv, BroadPhase &bp, c
 }
 
 void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm, const float4 *xp,
-                        const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow, float *disp) {
+                        const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow, float4 *disp) {
     int c = bp.cur;
     PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
     if (cv.nv > 0) k_disp<<<(cv.nv + 255) / 256, 256, 0, s>>>(cv.nv, xm, xp, disp);

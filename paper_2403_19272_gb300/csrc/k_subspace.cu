@@ -117,15 +117,17 @@ __global__ void __launch_bounds__(PROJ_T) k_project(SubspaceView S, const TU *__
     }
 }
 
+// g[e] = sum over blocks of partial[b][e] (e = 3 j + c): one warp per output,
+// lanes stride over the blocks, shuffle reduction in double.
 __global__ void k_project_reduce(SubspaceView S, const int *n_cv, int nblocks, const float *__restrict__ partial,
                                  double *__restrict__ g) {
     int r = active_r(S, n_cv);
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= r * 3) return;
-    int j = e / 3, c = e % 3;
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += (double)partial[((long long)b * S.ld + j) * 3 + c];
-    g[j * 3 + c] = s;
+    for (int b = lane; b < nblocks; b += 32) s += (double)partial[(long long)b * S.ld * 3 + e];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) g[e] = s;
 }
 
 // q = A0^-1 g without collision springs (one warp per row of the inverse).
@@ -349,8 +351,8 @@ void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, con
         project_t<__nv_bfloat16>(s, S, S.U16, rl, n_cv, W.partial);
     else
         project_t<float>(s, S, S.U32, rl, n_cv, W.partial);
-    int mx = S.ld * 3;
-    k_project_reduce<<<(mx + 127) / 128, 128, 0, s>>>(S, n_cv, PROJ_BLOCKS, W.partial, W.g);
+    int mx = S.ld * 3 * 32;
+    k_project_reduce<<<(mx + 255) / 256, 256, 0, s>>>(S, n_cv, PROJ_BLOCKS, W.partial, W.g);
     PDC_LAUNCH_CK();
 }
 

@@ -72,9 +72,9 @@ void launch_full_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const f
 void launch_collect_active(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm,
                            const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow);
 // Partial CCD over (xm, xp) on the current lists: update states, rebuild the active list.
-// disp (scratch, nv floats) receives |xp - xm| per collision vertex.
+// disp (scratch, nv float4) receives xp - xm per collision vertex.
 void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm, const float4 *xp,
-                        const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow, float *disp);
+                        const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow, float4 *disp);
 // Collision springs of the active list at positions x: cw += w, cf += w (y - x).
 void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, const int *n_act, int cap_act,
                     const float4 *x, float dhat, float *cw, float4 *cf);
