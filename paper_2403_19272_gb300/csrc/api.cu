@@ -911,6 +911,7 @@ void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {
         long long cvt = bp.cap_vt * ((ovf & OVF_VT) ? 2 : 1), cee = bp.cap_ee * ((ovf & OVF_EE) ? 2 : 1),
                   cent = bp.cap_ent * ((ovf & OVF_HASH) ? 2 : 1);
         if (ovf & OVF_CELLS) bp.cell_scale *= 4.f;
+        if (ovf & OVF_SLOTS) bp.grow_slots(coll(), true, true);
         bp.grow(coll(), cvt, cee, cent, s);  // keeps the current lists (NDB states merge from them)
         st.overflow_retries++;
         if (log) std::fprintf(stderr, "[pdc] broad phase regrown after overflow 0x%x\n", ovf);
@@ -1328,6 +1329,7 @@ pdc_status pdc_step(pdc_handle h, double dt) {
             if (ovf & OVF_EE) cee *= 2;
             if (ovf & OVF_HASH) cent *= 2;
             if (ovf & OVF_CELLS) bp.cell_scale *= 4.f;
+            if (ovf & OVF_SLOTS) bp.grow_slots(cv, true, true);
             if (ovf & (OVF_VT | OVF_EE | OVF_HASH)) bp.reserve(cv, cvt, cee, cent);
             if (ovf & OVF_ACTIVE) {
                 h->cap_act *= 2;
@@ -1393,6 +1395,7 @@ pdc_status pdc_op_broadphase(pdc_handle h, const float *x0, const float *x1, int
         long long cvt = bp.cap_vt * ((ovf & OVF_VT) ? 2 : 1), cee = bp.cap_ee * ((ovf & OVF_EE) ? 2 : 1),
                   cent = bp.cap_ent * ((ovf & OVF_HASH) ? 2 : 1);
         if (ovf & OVF_CELLS) bp.cell_scale *= 4.f;
+        if (ovf & OVF_SLOTS) bp.grow_slots(h->coll(), true, true);
         bp.reserve(h->coll(), cvt, cee, cent);
     }
     BroadPhase &bp = h->bp;

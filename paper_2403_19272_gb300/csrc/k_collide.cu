@@ -144,39 +144,48 @@ __global__ void k_hash_insert(int np, const float4 *__restrict__ blo, const floa
 }
 
 // ------------------------------------------------------------------ queries
+// Single-pass queries.  Each primary keeps its candidates sorted by
+// secondary id in a fixed-width row of a slot buffer (insertion as found);
+// the count is always exact, and a primary with more candidates than the row
+// width flags OVF_SLOTS (the pass is then rerun with wider rows).
+__device__ inline void slot_insert(int *row, int width, int c, int q) {
+    if (c >= width) return;
+    int j = c - 1;
+    while (j >= 0 && row[j] > q) {
+        row[j + 1] = row[j];
+        --j;
+    }
+    row[j + 1] = q;
+}
+
 // VT: primary = vertex v (all collision vertices), secondary = triangle.
 __global__ void __launch_bounds__(128) k_query_vt(CollView cv, const float4 *__restrict__ x0,
                                                   const float4 *__restrict__ x1, const float4 *__restrict__ tlo,
-                                                  const float4 *__restrict__ thi, const GridParams *gp, float dhat,
-                                                  unsigned int mask, const int *__restrict__ bcnt,
-                                                  const int *__restrict__ bstart,
+                                                  const float4 *__restrict__ thi, const int4 *__restrict__ tcell,
+                                                  const GridParams *gp, float dhat, unsigned int mask,
+                                                  const int *__restrict__ bcnt, const int *__restrict__ bstart,
                                                   const unsigned long long *__restrict__ ekey,
                                                   const int *__restrict__ eprim, int *__restrict__ cnt,
-                                                  const int *__restrict__ off, int2 *__restrict__ out,
-                                                  const long long *hash_total, long long cap_ent,
-                                                  const long long *total, long long cap, int *overflow) {
+                                                  int *__restrict__ slots, int width,
+                                                  const long long *hash_total, long long cap_ent, int *overflow) {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= cv.nv) return;
-    bool write = out != nullptr;
     if (*hash_total > cap_ent) {  // table not filled: produce nothing
-        if (!write) cnt[v] = 0;
+        cnt[v] = 0;
         return;
     }
-    if (write && *total > cap) return;
     float inv = gp->inv_cell;
     float3 lo, hi;
     vbox(x0, x1, v, lo, hi);
     int3 clo, chi;
     cell_range(lo, hi, dhat, inv, clo, chi);
     if ((long long)(chi.x - clo.x + 1) * (chi.y - clo.y + 1) * (chi.z - clo.z + 1) > MAX_CELLS_PER_PRIM) {
-        if (!write) {
-            cnt[v] = 0;
-            atomicOr(overflow, OVF_CELLS);
-        }
+        cnt[v] = 0;
+        atomicOr(overflow, OVF_CELLS);
         return;
     }
     bool vfix = v >= cv.nc;
-    int base = write ? off[v] : 0;
+    int *row = slots + (size_t)v * width;
     int c = 0;
     for (int z = clo.z; z <= chi.z; ++z)
         for (int y = clo.y; y <= chi.y; ++y)
@@ -187,65 +196,47 @@ __global__ void __launch_bounds__(128) k_query_vt(CollView cv, const float4 *__r
                 for (int e = e0; e < e1; ++e) {
                     if (ekey[e] != k) continue;
                     int t = eprim[e];
+                    int4 tl = tcell[t];
+                    if (x != max(clo.x, tl.x) || y != max(clo.y, tl.y) || z != max(clo.z, tl.z)) continue;
                     int4 T = cv.tri[t];
                     if (T.x == v || T.y == v || T.z == v) continue;
                     if (vfix && T.x >= cv.nc && T.y >= cv.nc && T.z >= cv.nc) continue;
-                    float3 bl = f3(tlo[t]), bh = f3(thi[t]);
-                    int3 tl, th;
-                    cell_range(bl, bh, dhat, inv, tl, th);
-                    if (x != max(clo.x, tl.x) || y != max(clo.y, tl.y) || z != max(clo.z, tl.z)) continue;
-                    if (!box_overlap(lo, hi, bl, bh, dhat)) continue;
-                    if (write) out[base + c] = make_int2(v, t);
+                    if (!box_overlap(lo, hi, f3(tlo[t]), f3(thi[t]), dhat)) continue;
+                    slot_insert(row, width, c, t);
                     ++c;
                 }
             }
-    if (!write) {
-        cnt[v] = c;
-    } else {
-        for (int i = 1; i < c; ++i) {  // insertion sort of the segment by triangle id
-            int2 key = out[base + i];
-            int j = i - 1;
-            while (j >= 0 && out[base + j].y > key.y) {
-                out[base + j + 1] = out[base + j];
-                --j;
-            }
-            out[base + j + 1] = key;
-        }
-    }
+    cnt[v] = c;
+    if (c > width) atomicOr(overflow, OVF_SLOTS);
 }
 
 // EE: primary = edge e, secondary = edge f > e.
 __global__ void __launch_bounds__(128) k_query_ee(CollView cv, const float4 *__restrict__ elo,
-                                                  const float4 *__restrict__ ehi, const GridParams *gp, float dhat,
-                                                  unsigned int mask, const int *__restrict__ bcnt,
-                                                  const int *__restrict__ bstart,
+                                                  const float4 *__restrict__ ehi, const int4 *__restrict__ ecell,
+                                                  const GridParams *gp, float dhat, unsigned int mask,
+                                                  const int *__restrict__ bcnt, const int *__restrict__ bstart,
                                                   const unsigned long long *__restrict__ ekey,
                                                   const int *__restrict__ eprim, int *__restrict__ cnt,
-                                                  const int *__restrict__ off, int2 *__restrict__ out,
-                                                  const long long *hash_total, long long cap_ent,
-                                                  const long long *total, long long cap, int *overflow) {
+                                                  int *__restrict__ slots, int width,
+                                                  const long long *hash_total, long long cap_ent, int *overflow) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= cv.ne) return;
-    bool write = out != nullptr;
     if (*hash_total > cap_ent) {
-        if (!write) cnt[e] = 0;
+        cnt[e] = 0;
         return;
     }
-    if (write && *total > cap) return;
     float inv = gp->inv_cell;
     float3 lo = f3(elo[e]), hi = f3(ehi[e]);
     int3 clo, chi;
     cell_range(lo, hi, dhat, inv, clo, chi);
     if ((long long)(chi.x - clo.x + 1) * (chi.y - clo.y + 1) * (chi.z - clo.z + 1) > MAX_CELLS_PER_PRIM) {
-        if (!write) {
-            cnt[e] = 0;
-            atomicOr(overflow, OVF_CELLS);
-        }
+        cnt[e] = 0;
+        atomicOr(overflow, OVF_CELLS);
         return;
     }
     int2 E = cv.edge[e];
     bool efix = E.x >= cv.nc && E.y >= cv.nc;
-    int base = write ? off[e] : 0;
+    int *row = slots + (size_t)e * width;
     int c = 0;
     for (int z = clo.z; z <= chi.z; ++z)
         for (int y = clo.y; y <= chi.y; ++y)
@@ -257,39 +248,45 @@ __global__ void __launch_bounds__(128) k_query_ee(CollView cv, const float4 *__r
                     if (ekey[q] != k) continue;
                     int f = eprim[q];
                     if (f <= e) continue;
+                    int4 tl = ecell[f];
+                    if (x != max(clo.x, tl.x) || y != max(clo.y, tl.y) || z != max(clo.z, tl.z)) continue;
                     int2 F = cv.edge[f];
                     if (E.x == F.x || E.x == F.y || E.y == F.x || E.y == F.y) continue;
                     if (efix && F.x >= cv.nc && F.y >= cv.nc) continue;
-                    float3 bl = f3(elo[f]), bh = f3(ehi[f]);
-                    int3 tl, th;
-                    cell_range(bl, bh, dhat, inv, tl, th);
-                    if (x != max(clo.x, tl.x) || y != max(clo.y, tl.y) || z != max(clo.z, tl.z)) continue;
-                    if (!box_overlap(lo, hi, bl, bh, dhat)) continue;
-                    if (write) out[base + c] = make_int2(e, f);
+                    if (!box_overlap(lo, hi, f3(elo[f]), f3(ehi[f]), dhat)) continue;
+                    slot_insert(row, width, c, f);
                     ++c;
                 }
             }
-    if (!write) {
-        cnt[e] = c;
-    } else {
-        for (int i = 1; i < c; ++i) {
-            int2 key = out[base + i];
-            int j = i - 1;
-            while (j >= 0 && out[base + j].y > key.y) {
-                out[base + j + 1] = out[base + j];
-                --j;
-            }
-            out[base + j + 1] = key;
-        }
-    }
+    cnt[e] = c;
+    if (c > width) atomicOr(overflow, OVF_SLOTS);
 }
 
-// Stores the list length seen by every later kernel.  On overflow the write
-// pass is skipped, so the buffer holds no valid entries: the length is set to
-// 0 and the overflow flagged (the step is then redone with larger buffers).
+// out[off[p] + k] = (p, slots[p][k]) for k < cnt[p]
+__global__ void k_compact_slots(int np, const int *__restrict__ cnt, const int *__restrict__ off,
+                                const int *__restrict__ slots, int width, const long long *total, long long cap,
+                                int2 *__restrict__ out) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np || *total > cap) return;
+    int c = min(cnt[p], width), o = off[p];
+    const int *row = slots + (size_t)p * width;
+    for (int k = 0; k < c; ++k) out[o + k] = make_int2(p, row[k]);
+}
+
+// lower cell corner of every primitive's inflated box (shared by insert and query)
+__global__ void k_prim_cells(int np, const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
+                             const GridParams *gp, float dhat, int4 *__restrict__ cell) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    int3 lo, hi;
+    cell_range(f3(blo[p]), f3(bhi[p]), dhat, gp->inv_cell, lo, hi);
+    cell[p] = make_int4(lo.x, lo.y, lo.z, 0);
+}
+
 __global__ void k_check_cap(const long long *total, long long cap, int flag, int *overflow, long long *count_out) {
     long long t = *total;
-    *count_out = t <= cap ? t : 0;
+    bool bad = t > cap || (*overflow & (OVF_SLOTS | OVF_CELLS | OVF_HASH)) != 0;
+    *count_out = bad ? 0 : t;
     if (t > cap) atomicOr(overflow, flag);
 }
 
@@ -327,6 +324,10 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
     off_v.alloc(cv.nv);
     cnt_e.alloc(cv.ne);
     off_e.alloc(cv.ne);
+    tcell.alloc(cv.nt);
+    ecell.alloc(cv.ne);
+    slots_vt.alloc((size_t)cv.nv * w_vt);
+    slots_ee.alloc((size_t)cv.ne * w_ee);
     long long mx = std::max<long long>(std::max<long long>(T_vt, T_ee), std::max<long long>(cv.nv, cv.ne));
     scratch.alloc(scan_scratch_ints((int)mx) + 16);
     gp.alloc(1);
@@ -358,6 +359,17 @@ template <class T> static void grow_keep(DevBuf<T> &b, long long cap, cudaStream
     PDC_CK(cudaStreamSynchronize(s));
     std::swap(b.p, nb.p);
     std::swap(b.n, nb.n);
+}
+
+void BroadPhase::grow_slots(const CollView &cv, bool vt_, bool ee_) {
+    if (vt_) {
+        w_vt *= 2;
+        slots_vt.alloc((size_t)cv.nv * w_vt);
+    }
+    if (ee_) {
+        w_ee *= 2;
+        slots_ee.alloc((size_t)cv.ne * w_ee);
+    }
 }
 
 void BroadPhase::grow(const CollView &cv, long long cvt, long long cee, long long cent, cudaStream_t s) {
@@ -424,37 +436,37 @@ void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const
             PDC_LAUNCH_CK();
         });
     }
+    // ---- per-primitive lower cells
+    if (cv.nt) k_prim_cells<<<nblk(cv.nt, 256), 256, 0, s>>>(cv.nt, tlo, thi, gp, dhat, tcell);
+    if (cv.ne) k_prim_cells<<<nblk(cv.ne, 256), 256, 0, s>>>(cv.ne, elo, ehi, gp, dhat, ecell);
+    PDC_LAUNCH_CK();
     // ---- VT candidates
     if (prof) prof->begin(s, "bp_query_vt", 0.0);
     if (cv.nv) {
-        k_query_vt<<<nblk(cv.nv, 128), 128, 0, s>>>(cv, x0, x1, tlo, thi, gp, dhat, (unsigned)(T_vt - 1), bcnt[0],
-                                                    bstart[0], ekey[0], eprim[0], cnt_v, nullptr, nullptr, tot + 0,
-                                                    cap_ent, tot + 0, cap_ent, overflow);
+        k_query_vt<<<nblk(cv.nv, 128), 128, 0, s>>>(cv, x0, x1, tlo, thi, tcell, gp, dhat, (unsigned)(T_vt - 1),
+                                                    bcnt[0], bstart[0], ekey[0], eprim[0], cnt_v, slots_vt, w_vt,
+                                                    tot + 0, cap_ent, overflow);
         PDC_LAUNCH_CK();
     }
     exclusive_scan(s, cnt_v, off_v, cv.nv, scratch, tot + 2);
     k_check_cap<<<1, 1, 0, s>>>(tot + 2, cap_vt, OVF_VT, overflow, cnt_vt_d[nw]);
     if (cv.nv) {
-        k_query_vt<<<nblk(cv.nv, 128), 128, 0, s>>>(cv, x0, x1, tlo, thi, gp, dhat, (unsigned)(T_vt - 1), bcnt[0],
-                                                    bstart[0], ekey[0], eprim[0], cnt_v, off_v, vt[nw], tot + 0,
-                                                    cap_ent, tot + 2, cap_vt, overflow);
+        k_compact_slots<<<nblk(cv.nv, 256), 256, 0, s>>>(cv.nv, cnt_v, off_v, slots_vt, w_vt, tot + 2, cap_vt, vt[nw]);
         PDC_LAUNCH_CK();
     }
     if (prof) prof->end(s);
     // ---- EE candidates
     if (prof) prof->begin(s, "bp_query_ee", 0.0);
     if (cv.ne) {
-        k_query_ee<<<nblk(cv.ne, 128), 128, 0, s>>>(cv, elo, ehi, gp, dhat, (unsigned)(T_ee - 1), bcnt[1], bstart[1],
-                                                    ekey[1], eprim[1], cnt_e, nullptr, nullptr, tot + 1, cap_ent,
-                                                    tot + 1, cap_ent, overflow);
+        k_query_ee<<<nblk(cv.ne, 128), 128, 0, s>>>(cv, elo, ehi, ecell, gp, dhat, (unsigned)(T_ee - 1), bcnt[1],
+                                                    bstart[1], ekey[1], eprim[1], cnt_e, slots_ee, w_ee, tot + 1,
+                                                    cap_ent, overflow);
         PDC_LAUNCH_CK();
     }
     exclusive_scan(s, cnt_e, off_e, cv.ne, scratch, tot + 3);
     k_check_cap<<<1, 1, 0, s>>>(tot + 3, cap_ee, OVF_EE, overflow, cnt_ee_d[nw]);
     if (cv.ne) {
-        k_query_ee<<<nblk(cv.ne, 128), 128, 0, s>>>(cv, elo, ehi, gp, dhat, (unsigned)(T_ee - 1), bcnt[1], bstart[1],
-                                                    ekey[1], eprim[1], cnt_e, off_e, ee[nw], tot + 1, cap_ent,
-                                                    tot + 3, cap_ee, overflow);
+        k_compact_slots<<<nblk(cv.ne, 256), 256, 0, s>>>(cv.ne, cnt_e, off_e, slots_ee, w_ee, tot + 3, cap_ee, ee[nw]);
         PDC_LAUNCH_CK();
     }
     if (prof) prof->end(s);

@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const in
 //         side 2) cannot satisfy Q <= dhat |d0| at any sample (|d1 - d0| is
 //         bounded by those displacements), so it is set inactive without
 //         evaluating the samples.
-__global__ void __launch_bounds__(PAIR_THREADS, 4) k_pairs_update(CollView cv, const int2 *__restrict__ vt,
+__global__ void __launch_bounds__(PAIR_THREADS, 3) k_pairs_update(CollView cv, const int2 *__restrict__ vt,
                                                                const int2 *__restrict__ ee, const long long *nvt_p,
                                                                const long long *nee_p, unsigned char *st_vt,
                                                                unsigned char *st_ee, float *d0_vt, float *d0_ee,

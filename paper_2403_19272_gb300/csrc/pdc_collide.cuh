@@ -7,7 +7,7 @@
 
 namespace pdc {
 
-enum OverflowBits { OVF_HASH = 1, OVF_VT = 2, OVF_EE = 4, OVF_ACTIVE = 8, OVF_CELLS = 16 };
+enum OverflowBits { OVF_HASH = 1, OVF_VT = 2, OVF_EE = 4, OVF_ACTIVE = 8, OVF_CELLS = 16, OVF_SLOTS = 32 };
 
 struct GridParams {
     double ext_sum;  // sum over triangles of the largest swept-box extent
@@ -47,6 +47,9 @@ struct BroadPhase {
     DevBuf<int> eprim[2];
     DevBuf<float4> tlo, thi, elo, ehi;
     DevBuf<int> cnt_v, off_v, cnt_e, off_e, scratch;
+    DevBuf<int4> tcell, ecell;       // lower cell of each primitive's inflated box
+    DevBuf<int> slots_vt, slots_ee;  // per-primary sorted candidate rows
+    int w_vt = 16, w_ee = 32;        // row widths (doubled on OVF_SLOTS)
     DevBuf<GridParams> gp;
     DevBuf<long long> totals;
     // double-buffered candidate lists and NDB pair states
@@ -60,6 +63,7 @@ struct BroadPhase {
     void reserve(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent);
     // larger capacities keeping the current candidate lists, states and counts
     void grow(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent, cudaStream_t s);
+    void grow_slots(const CollView &cv, bool vt, bool ee);
     void run(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat, int *overflow);
 };
 
