@@ -888,6 +888,7 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
         accel.aa_have_prev = true;
     }
     if (contacts && P.collisions) {
+        bp.prof = prof.on ? &prof : nullptr;
         PROF("partial_ccd", 0,
              launch_partial_ccd(s, coll(), bp, Xm, Xp, cparams(), act, cap_act, n_act_d, &sc.p->overflow, disp));
     }

@@ -600,12 +600,16 @@ void launch_collect_active(cudaStream_t s, const CollView &cv, BroadPhase &bp, c
 void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm, const float4 *xp,
                         const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow, float4 *disp) {
     int c = bp.cur;
+    if (bp.prof) bp.prof->begin(s, "pccd_prep", 0.0);
     PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
     if (cv.nv > 0) k_disp<<<(cv.nv + 255) / 256, 256, 0, s>>>(cv.nv, xm, xp, disp);
+    if (bp.prof) bp.prof->end(s);
+    if (bp.prof) bp.prof->begin(s, "pccd_pairs", 0.0);
     k_pairs_update<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
                                                         bp.st_vt[c], bp.st_ee[c], bp.d0_vt[c], bp.d0_ee[c], disp, xm,
                                                         xp, P, 1, act, cap_act, n_act, overflow);
     PDC_LAUNCH_CK();
+    if (bp.prof) bp.prof->end(s);
 }
 
 void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, const int *n_act, int cap_act,
