@@ -262,6 +262,57 @@ pdc_status pdc_op_residual(pdc_handle h, const float *x, const float *z, const f
 pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, const float *cw, const float *cf,
                                int32_t r, int32_t cycles, int32_t sweeps, float *x_out);
 
+/* Size of the one statically allocated device array (per device) that
+ * pdc_op_contact_noalloc uses for its temporaries. */
+#define PDC_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* Allocation-free variant of pdc_op_contact.  The paper has no counterpart:
+ * this is a library-integration entry point, not part of the method.
+ *
+ * It computes exactly what pdc_op_contact computes (the collision springs of
+ * Sec. 5.1 with A_i = B_i = Id for the given pairs and weights) but
+ * allocates no device memory: no cudaMalloc / cudaFree and no allocating
+ * library routine.  It is meant for callers that cannot let a library
+ * allocate inside a call -- a process whose caching allocator already holds
+ * nearly all free device memory (a cudaMalloc there fails, or forces the
+ * allocator to give memory back), or a latency-bound loop, since cudaFree
+ * synchronises the whole device and stalls every other stream.
+ *
+ * All pointers are DEVICE pointers on the current device:
+ *   x0, x   [nv_all][3] float32 collision-vertex positions (cloth, then
+ *           obstacles), t = 0 of the pairs and the evaluation positions;
+ *   quads   [np][4] int32 vertex ids, 16-byte aligned; kinds [np] int32
+ *           (0 = VT, 1 = EE); w [np] float32 weights;
+ *   cw      [nv] float32 out: per cloth vertex the weight sum (nv = cloth
+ *           vertices);
+ *   cf      [nv][3] float32 out: per cloth vertex sum_i w_i (y_ij - x_j).
+ * stream: a cudaStream_t on the current device (NULL = the handle's stream).
+ *
+ * Scratch: the temporaries (float4 copies of x0 and x, the force
+ * accumulator, the active-pair list and two counters) live in one file-scope
+ * device array of PDC_NOALLOC_SCRATCH_BYTES.  They need
+ *   32*nv_all + 16*nv + 48*max(np,1) bytes (+ alignment, each part rounded
+ *   up to 256 B, + 256 B of counters);
+ * larger inputs are rejected with PDC_ERR_CAPACITY before any work is
+ * enqueued (use pdc_op_contact for them).  Nothing has to start at zero:
+ * the call zeroes its counters, its accumulator and both outputs itself, and
+ * cw and cf are overwritten in full.
+ *
+ * The first call on a device looks the scratch address up with
+ * cudaGetSymbolAddress, which can load the library's device code; make that
+ * first call before any stream capture on the device.  Every call on one
+ * device shares the same scratch, so calls that overlap in time (other
+ * threads, other streams, other handles) race and corrupt each other's
+ * results: order them on one stream or on the host.
+ *
+ * Ids and kinds are checked on the device before use (one stream
+ * synchronisation): PDC_ERR_ARG if any is out of range.  The remaining work
+ * is enqueued on `stream`; cw and cf are valid once it has completed.
+ * PDC_ERR_STATE if obstacle topology has not been built. */
+pdc_status pdc_op_contact_noalloc(pdc_handle h, const float *x0, const float *x, const int32_t *quads,
+                                  const int32_t *kinds, const float *w, int64_t np, float *cw, float *cf,
+                                  void *stream);
+
 #ifdef __cplusplus
 }
 #endif

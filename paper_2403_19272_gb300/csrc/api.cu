@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <unordered_map>
 
 #include "pdc_collide.cuh"
@@ -1598,3 +1599,116 @@ pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, con
 }
 
 }  // extern "C"
+
+// ============================================================================ allocation-free contact springs
+// Library-integration entry point with no counterpart in the paper: the
+// collision springs of pdc_op_contact computed without allocating device
+// memory.  Callers that need it: a process whose caching allocator already
+// holds nearly all free device memory (a cudaMalloc inside the call would
+// fail or force the allocator to release memory), and latency-bound loops,
+// because cudaFree synchronises the whole device and stalls other streams.
+// All temporaries live in this one statically sized device array; calls that
+// overlap in time on one device share it and therefore race.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PDC_NOALLOC_SCRATCH_BYTES];
+
+namespace pdc {
+namespace {
+
+// bad += number of quads with a vertex id outside [0, nv) or a kind not 0/1
+__global__ void k_check_quads(long long np, const int4 *__restrict__ q, const int *__restrict__ kinds, int nv,
+                              int *bad) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np;
+         i += (long long)gridDim.x * blockDim.x) {
+        int4 v = q[i];
+        int k = kinds[i];
+        bool ok = v.x >= 0 && v.x < nv && v.y >= 0 && v.y < nv && v.z >= 0 && v.z < nv && v.w >= 0 && v.w < nv &&
+                  (k == 0 || k == 1);
+        if (!ok) atomicAdd(bad, 1);
+    }
+}
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_base[NOALLOC_MAX_DEVICES];
+
+// Device address of the static scratch on the current device, looked up
+// once per device (the lookup can load the module, so it must not happen
+// for the first time inside a stream capture).
+unsigned char *noalloc_scratch() {
+    int dev = -1;
+    PDC_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) throw Error(PDC_ERR_CUDA, "noalloc scratch: device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            throw Error(PDC_ERR_CUDA, std::string("cudaGetSymbolAddress(noalloc scratch): ") + cudaGetErrorString(e));
+        g_noalloc_base[dev] = p;
+    }
+    return (unsigned char *)g_noalloc_base[dev];
+}
+
+inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace pdc
+
+extern "C" pdc_status pdc_op_contact_noalloc(pdc_handle h, const float *x0, const float *x, const int32_t *quads,
+                                             const int32_t *kinds, const float *w, int64_t np, float *cw, float *cf,
+                                             void *stream) {
+    API_BEGIN(h)
+    if (!x0 || !x || !cw || !cf || np < 0 || (np > 0 && (!quads || !kinds || !w)))
+        throw Error(PDC_ERR_ARG, "pdc_op_contact_noalloc: NULL pointer or negative np");
+    if (((uintptr_t)quads & 15) != 0) throw Error(PDC_ERR_ARG, "pdc_op_contact_noalloc: quads must be 16-byte aligned");
+    if (h->topo_dirty) throw Error(PDC_ERR_STATE, "pdc_op_contact_noalloc: collision topology not built");
+    const size_t nv = (size_t)h->nv_all, n = (size_t)h->n;
+    // scratch layout: X0 | X1 | CF | active pairs | counters (n_act, bad)
+    const size_t off_x1 = round256(sizeof(float4) * nv);
+    const size_t off_cf = off_x1 + round256(sizeof(float4) * nv);
+    const size_t off_act = off_cf + round256(sizeof(float4) * n);
+    // room for the pair list: what is left after the counters, in whole
+    // 256-byte units so that the rounded-up list still fits; np is compared
+    // against it before a byte count is formed from it
+    const size_t act_room =
+        PDC_NOALLOC_SCRATCH_BYTES > off_act + 256 ? ((PDC_NOALLOC_SCRATCH_BYTES - off_act - 256) & ~(size_t)255) : 0;
+    const size_t np_max = act_room / sizeof(ActivePair);
+    if (act_room < 256 || (uint64_t)np > np_max)
+        throw Error(PDC_ERR_CAPACITY,
+                    "pdc_op_contact_noalloc: np=" + std::to_string(np) + " pairs with " + std::to_string(nv) +
+                        " collision vertices exceed the static scratch of " +
+                        std::to_string((size_t)PDC_NOALLOC_SCRATCH_BYTES) + " bytes (at most " +
+                        std::to_string(np_max) + " pairs here); use pdc_op_contact");
+    const size_t off_cnt = off_act + round256(sizeof(ActivePair) * (size_t)std::max<int64_t>(np, 1));
+    unsigned char *base = noalloc_scratch();
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->s;
+    float4 *X0 = (float4 *)base, *X1 = (float4 *)(base + off_x1), *CFa = (float4 *)(base + off_cf);
+    ActivePair *AP = (ActivePair *)(base + off_act);
+    int *n_act = (int *)(base + off_cnt), *bad = n_act + 1;
+    const int4 *q = (const int4 *)quads;
+    if (np > 0) {
+        PDC_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        k_check_quads<<<(int)std::min<long long>((np + 255) / 256, 152LL * 8), 256, 0, s>>>(np, q, kinds, (int)nv, bad);
+        PDC_LAUNCH_CK();
+        int nbad = 0;
+        PDC_CK(cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PDC_CK(cudaStreamSynchronize(s));
+        if (nbad)
+            throw Error(PDC_ERR_ARG, "pdc_op_contact_noalloc: " + std::to_string(nbad) +
+                                         " pairs with a vertex id out of range or a kind other than 0/1");
+    }
+    if (nv) {
+        k_f3_to_f4<<<nb((long long)nv), 256, 0, s>>>((int)nv, x0, X0);
+        k_f3_to_f4<<<nb((long long)nv), 256, 0, s>>>((int)nv, x, X1);
+        PDC_LAUNCH_CK();
+    }
+    launch_activate_quads(s, q, kinds, w, np, X0, AP, n_act);
+    PDC_CK(cudaMemsetAsync(cw, 0, sizeof(float) * n, s));
+    PDC_CK(cudaMemsetAsync(CFa, 0, sizeof(float4) * n, s));
+    launch_contact(s, h->coll(), AP, n_act, (int)std::max<int64_t>(np, 1), X1, h->dhat, cw, CFa);
+    if (n) {
+        k_f4_to_f3<<<nb((long long)n), 256, 0, s>>>((int)n, CFa, cf);
+        PDC_LAUNCH_CK();
+    }
+    API_END(h)
+}

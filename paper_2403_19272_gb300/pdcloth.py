@@ -81,6 +81,7 @@ SIGNATURES = {
     "pdc_op_contact": (c_i32, [P, P, P, P, P, P, c_i64, P, P]),
     "pdc_op_residual": (c_i32, [P, P, P, P, P, P]),
     "pdc_op_global_solve": (c_i32, [P, P, P, P, P, c_i32, c_i32, c_i32, P]),
+    "pdc_op_contact_noalloc": (c_i32, [P, P, P, P, P, P, c_i64, P, P, P]),
 }
 
 _lib = None
@@ -286,6 +287,16 @@ def pdc_op_global_solve(h, x, z, cw, cf, r, cycles, sweeps):
     _check(h, lib().pdc_op_global_solve(h, _ptr(x), _ptr(z), _ptr(cw), _ptr(cf), int(r), int(cycles), int(sweeps),
                                         _ptr(out)))
     return out
+
+
+def pdc_op_contact_noalloc(h, x0, x, quads, kinds, w, np_, cw, cf, stream=0):
+    """Allocation-free pdc_op_contact: every array argument is an integer
+    device pointer (x0, x [nv_all][3] f32; quads [np][4] i32, 16-byte
+    aligned; kinds [np] i32; w [np] f32; outputs cw [nv] f32, cf [nv][3]
+    f32); stream is a cudaStream_t as an integer (0 = the handle's stream).
+    Results are valid once the stream has completed the enqueued work."""
+    _check(h, lib().pdc_op_contact_noalloc(h, P(x0), P(x), P(quads) if quads else None, P(kinds) if kinds else None,
+                                           P(w) if w else None, int(np_), P(cw), P(cf), P(stream) if stream else None))
 
 
 # ----------------------------------------------------------------------------- convenience
