@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--forms", default="mixed,fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-side", type=int, default=64)
+    ap.add_argument("--no-launch-count", action="store_true",
+                    help="skip the CUDA activity trace (e.g. when running under ncu)")
     return ap.parse_args()
 
 
@@ -53,10 +55,11 @@ def solver_params(pc, precision):
     p.r_warm = 256
     p.r_reuse = 32
     p.precision = precision
-    p.sweep_kind = 1        # Chebyshev-iteration sweeps
-    p.jacobi_sweeps = 16
+    p.sweep_kind = 1        # Jacobi-preconditioned Chebyshev iteration for the sweeps
+    p.jacobi_sweeps = 32
     p.cheb_ratio = 1000.0
-    p.accel = 1             # Chebyshev acceleration of the LG iterates
+    p.accel = 2             # Anderson mixing of the LG iterates
+    p.aa_depth = 6
     p.solve_cycles = 1
     p.eig_iters = 12
     return p
@@ -114,7 +117,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def run_form(pc, torch, scene, precision, steps, warmup, dev_index):
+def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True):
     """Warm-up, timed region (device), profiled replay, e2e through host buffers."""
     import numpy as np
     stream = torch.cuda.Stream()
@@ -162,6 +165,9 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index):
     torch.cuda.synchronize()
     kt = pc.pdc_get_kernel_times(h)
     pc.pdc_set_profiling(h, False)
+    # ---- kernel launches of the library per step, counted by the CUDA
+    # activity profiler over a replay of the same number of steps
+    launches = count_launches(torch, one_step, steps) if launch_count else None
     # ---- e2e through the public API with host buffers: pin targets h2d, positions d2h
     pin_host = torch.empty(pins.shape[1:], dtype=torch.float32).pin_memory()
     pos_host = torch.empty((scene.n, 3), dtype=torch.float32).pin_memory()
@@ -184,12 +190,40 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index):
                 rel_res=statistics.mean(s["rel_residual"] for s in st_list),
                 cand=statistics.mean(s["n_candidates"] for s in st_list),
                 toi=min(s["t_toi"] for s in st_list), finite=bool(np.isfinite(x).all()),
-                launches=None)
+                launches=launches)
+
+
+def count_launches(torch, one_step, steps):
+    """Kernels launched by the library (names beginning with k_) during
+    `steps` steps, from torch.profiler's CUDA activity trace; None if the
+    trace is unavailable."""
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            for _ in range(steps):
+                one_step()
+            torch.cuda.synchronize()
+        import re
+        pat = re.compile(r"(?:^|[\s:])k_\w+")
+        n = 0
+        for ev in prof.events():
+            if str(getattr(ev, "device_type", "")).endswith("CUDA") and pat.search(ev.name or ""):
+                n += 1
+        return n
+    except Exception:
+        return None
+
+
+# profiled regions that enclose other profiled regions (not kernels themselves)
+PARENTS = {"broad_phase", "partial_ccd"}
 
 
 def roofline(kernels, pk, ms_step):
-    """Dominant kernel by total profiled time, against the measured HBM copy peak."""
-    best = max(kernels.items(), key=lambda kv: kv[1]["total_ms"])
+    """Dominant kernel (largest total time among the profiled leaf regions),
+    achieved algorithmic bytes per launch / event time against the measured
+    HBM copy peak."""
+    leaves = {k: v for k, v in kernels.items() if k not in PARENTS}
+    best = max(leaves.items(), key=lambda kv: kv[1]["total_ms"])
     name, d = best
     per_launch_ms = d["total_ms"] / max(d["launches"], 1)
     bytes_per_launch = d["algo_bytes"] / max(d["launches"], 1)
@@ -201,9 +235,10 @@ def roofline(kernels, pk, ms_step):
             "peak_source": "measured" if not pk.get("_fallback") else "fallback"}
 
 
-def cpu_baseline(side, steps=2):
-    """The FP64 oracle on a bounded sample: `steps` steps of the same scene at
-    side x side, one thread, time scaled linearly by vertex count."""
+def cpu_baseline(side, steps=2, warmup=0):
+    """The FP64 oracle on a bounded sample: `warmup` untimed then `steps`
+    timed steps of the same scene at side x side in one process, one thread;
+    ms/step scaled linearly by vertex count to the full workload."""
     code = r'''
 import os, sys, time, json
 sys.path.insert(0, %r)
@@ -213,20 +248,26 @@ build.build()
 sc = wl.hanging_swept(side=%d)
 p = pd.Params(tol_rel_residual=1e-3, max_outer=3, max_inner=64, warm_iters=5)
 o = pd.Oracle(sc, p)
-t0 = time.time()
 for k in range(%d):
     o.step()
-print(json.dumps({"s": (time.time() - t0) / %d, "n": sc.n}))
-''' % (ROOT, side, steps, steps)
+ts = []
+for k in range(%d):
+    t0 = time.time()
+    o.step()
+    ts.append(time.time() - t0)
+print(json.dumps({"s": ts, "n": sc.n}))
+''' % (ROOT, side, warmup, steps)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         return {"value": None, "error": out.stderr[-300:]}
     d = json.loads(out.stdout.strip().splitlines()[-1])
     scale = (SIDE * SIDE) / d["n"]
-    return {"value": round(d["s"] * 1e3 * scale, 1), "unit": "ms/step", "cores": 1, "kind": "oracle",
-            "sample": "%d oracle steps of the same swept-cloth scene at %dx%d (%d vertices), ms/step scaled "
-                      "linearly by vertex count to 512x512" % (steps, side, side, d["n"])}
+    per = [t * 1e3 * scale for t in d["s"]]
+    return {"value": round(statistics.mean(per), 1), "unit": "ms/step", "cores": 1, "kind": "oracle",
+            "per_step": per,
+            "sample": "%d oracle steps (after %d untimed) of the same swept-cloth scene at %dx%d (%d vertices), "
+                      "ms/step scaled linearly by vertex count to 512x512" % (steps, warmup, side, side, d["n"])}
 
 
 def main():
@@ -237,18 +278,12 @@ def main():
     if a.impl == "reference":
         if rank != 0:
             return
-        t0 = time.time()
-        base = None
-        vals = []
-        for _ in range(a.warmup):
-            pass
-        for _ in range(max(a.steps, 1)):
-            r = cpu_baseline(a.cpu_sample_side, steps=1)
-            if r["value"] is None:
-                print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + r.get("error", "")}))
-                return
-            vals.append(r["value"])
-            base = r
+        r = cpu_baseline(a.cpu_sample_side, steps=max(a.steps, 1), warmup=a.warmup)
+        if r["value"] is None:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + r.get("error", "")}))
+            return
+        base = r
+        vals = r["per_step"]
         v = statistics.mean(vals)
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "ms/step", "n_gpus": a.gpus,
                           "steps": a.steps, "warmup": a.warmup, "ms_per_step": v, "higher_is_better": False,
@@ -271,7 +306,8 @@ def main():
     scene = wl.hanging_swept(side=a.side)
     forms = {}
     for f in a.forms.split(","):
-        forms[f] = run_form(pc, torch, scene, 1 if f == "mixed" else 0, a.steps, a.warmup, local)
+        forms[f] = run_form(pc, torch, scene, 1 if f == "mixed" else 0, a.steps, a.warmup, local,
+                            not a.no_launch_count)
     head = "mixed" if "mixed" in forms else list(forms)[0]
     ms = forms[head]["ms"]
     if world > 1:
@@ -291,6 +327,8 @@ def main():
                    "l2": "inputs larger than L2 (basis 134 MB BF16 / 268 MB FP32 plus matrices and state)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "forms": {f: {"ms_per_step": round(d["ms"], 3), "lg_iters_per_step": d["iters"],
+                      "vertex_iters_per_s": round(scene.n * d["iters"] / (d["ms"] * 1e-3), 1),
+                      "gpu_launches": d["launches"],
                       "rel_residual": d["rel_res"], "candidates": d["cand"], "min_toi": d["toi"],
                       "setup_s": round(d["setup_s"], 2), "e2e_ms_per_step": round(d["e2e_ms"], 3)}
                   for f, d in forms.items()},
@@ -298,7 +336,7 @@ def main():
         "clocks": forms[head]["clocks"],
         "e2e": {"value": round(forms[head]["e2e_ms"], 3), "unit": "ms/step",
                 "h2d_bytes_per_step": forms[head]["h2d"], "d2h_bytes_per_step": forms[head]["d2h"]},
-        "gpu_launches": int(sum(d["launches"] for d in forms[head]["kernels"].values()) / max(a.steps, 1) * a.steps),
+        "gpu_launches": forms[head]["launches"],
         "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3),
                         "GBps": round(v["algo_bytes"] / max(v["total_ms"], 1e-9) / 1e6, 1)}
                     for k, v in forms[head]["kernels"].items()},

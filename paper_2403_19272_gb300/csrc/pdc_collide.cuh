@@ -23,6 +23,7 @@ struct CollParams {
     int a_max;        // cap of the life-span counter
     int samples_vt;   // 0, 1, 3
     int samples_ee;   // 0, 1, 4
+    int *near_count = nullptr;  // optional: pairs passing the partial-CCD displacement prefilter
 };
 
 // An active collision constraint: 4 collision-vertex ids, the gap-vector
@@ -59,6 +60,7 @@ struct BroadPhase {
     DevBuf<long long> cnt_vt_d[2], cnt_ee_d[2];
     int cur = 0;
     Profiler *prof = nullptr;  // optional sub-kernel timing
+    long long h_pairs = 0;     // host copy of the current list size (kept while profiling)
 
     void reserve(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent);
     // larger capacities keeping the current candidate lists, states and counts
