@@ -127,7 +127,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
                       stream.cuda_stream)
     setup_s = time.time() - t_setup
     dt = p.dt
-    total = warmup + 2 * steps + steps
+    total = warmup + steps
     # scripted pin targets for every step, resident on the device
     pins = np.stack([scene.pins_at((k + 1) * dt) for k in range(total)]).astype(np.float32)
     pins_d = torch.from_numpy(pins).to(f"cuda:{dev_index}")
@@ -142,6 +142,17 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
     for _ in range(warmup):
         one_step()
     torch.cuda.synchronize()
+    # checkpoint: the profiled replay, the launch count and the end-to-end
+    # run repeat the timed steps from the same positions and velocities
+    x_ck, v_ck = pc.pdc_get_state(h, scene.n)
+    k_ck = k
+
+    def restore():
+        nonlocal k
+        pc.pdc_set_state(h, x_ck, v_ck)
+        k = k_ck
+        torch.cuda.synchronize()
+
     # ---- timed region: device events on the library's stream
     clocks = ClockSampler(dev_index)
     clocks.start()
@@ -158,7 +169,8 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    # ---- profiled replay of the same number of steps (per-kernel event timing)
+    # ---- profiled replay of the same steps (per-kernel event timing)
+    restore()
     pc.pdc_set_profiling(h, True)
     for _ in range(steps):
         one_step()
@@ -167,7 +179,9 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
     pc.pdc_set_profiling(h, False)
     # ---- kernel launches of the library per step, counted by the CUDA
     # activity profiler over a replay of the same number of steps
+    restore()
     launches = count_launches(torch, one_step, steps) if launch_count else None
+    restore()
     # ---- e2e through the public API with host buffers: pin targets h2d, positions d2h
     pin_host = torch.empty(pins.shape[1:], dtype=torch.float32).pin_memory()
     pos_host = torch.empty((scene.n, 3), dtype=torch.float32).pin_memory()

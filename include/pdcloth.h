@@ -115,6 +115,10 @@ typedef struct {
                                 spectrum interval [b / cheb_ratio, b] of D^-1 A   */
     double cheb_ratio;       /* interval ratio for sweep_kind 1 (> 1)            */
     int32_t aa_depth;        /* history length for accel = 2 (1..8)              */
+    int32_t tensor_cores;    /* mixed form: 1 runs the full-basis projection and
+                                lift on the tcgen05 tensor cores (BF16 basis, FP32
+                                operand split into two BF16 parts, FP32
+                                accumulation); 0 uses the CUDA-core kernels      */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
@@ -261,6 +265,19 @@ pdc_status pdc_op_residual(pdc_handle h, const float *x, const float *z, const f
  * r = 0 skips the correction.  Host arrays. */
 pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, const float *cw, const float *cf,
                                int32_t r, int32_t cycles, int32_t sweeps, float *x_out);
+
+/* Subspace projection g = U[:, :r]^T v (the U^T r of Eq. subspace_global)
+ * with the handle's basis, as run in the LG iterations without collision
+ * springs: on the tcgen05 tensor cores when params.precision = 1,
+ * params.tensor_cores = 1 and the basis row stride is a multiple of 128
+ * (<= 256), else on the CUDA cores.  v: host [nv][3] float32 (pinned rows
+ * ignored through U's zero rows); g: host [r][3] float64; 0 < r <= r_warm. */
+pdc_status pdc_op_project(pdc_handle h, const float *v, int32_t r, double *g);
+
+/* Lift out = U[:, :r] q (the U q of Eq. subspace_collision), same path
+ * selection as pdc_op_project.  q: host [r][3] float64 (used as float32);
+ * out: host [nv][3] float32. */
+pdc_status pdc_op_lift(pdc_handle h, const double *q, int32_t r, float *out);
 
 /* Size of the one statically allocated device array (per device) that
  * pdc_op_contact_noalloc uses for its temporaries. */

@@ -14,6 +14,7 @@
 #include "pdc_collide.cuh"
 #include "pdc_prof.cuh"
 #include "pdc_subspace.cuh"
+#include "pdc_umma.cuh"
 
 namespace pdc {
 void set_chol_smem_limits();
@@ -226,6 +227,13 @@ struct pdc_ctx {
     int r_warm = 0, r_reuse = 0, ld = 0;
     DevBuf<float> U32, A0inv32, proj_partial, qbuf, dA;
     DevBuf<__nv_bfloat16> U16;
+    DevBuf<__nv_bfloat16> Ut16;  // transposed BF16 basis [ld][n_pad] (tensor-core projection)
+    int n_pad = 0;
+    UmmaMaps umma;
+    DevBuf<float> umma_partial;
+    int ldc = 0;                 // width of the compact copy of the leading r_reuse columns
+    DevBuf<float> Uc32;
+    DevBuf<__nv_bfloat16> Uc16;
     DevBuf<double> A0, A0inv, gbuf;
     DevBuf<int> sflag;
     // scalars
@@ -249,6 +257,7 @@ struct pdc_ctx {
     double gersh = 1.0;       // Gershgorin bound of D^-1 H
     long long nnz_off = 0;  // off-diagonal entries of H over free rows
     bool log = std::getenv("PDC_LOG") != nullptr;  // per-iteration residuals to stderr
+    DevBuf<int> near_cnt;                            // logging only
 
     ~pdc_ctx() {
         if (hsc) cudaFreeHost(hsc);
@@ -302,6 +311,12 @@ struct pdc_ctx {
         S.A0inv = A0inv;
         S.A0inv32 = A0inv32;
         S.precision = P.precision;
+        S.ldc = ldc;
+        S.Uc32 = Uc32;
+        S.Uc16 = Uc16;
+        S.umma = (umma.ok && P.precision == 1 && P.tensor_cores) ? &umma : nullptr;
+        S.umma_partial = umma_partial;
+        S.dev_err = sflag;
         return S;
     }
     SubspaceWork work() {
@@ -665,8 +680,40 @@ void pdc_ctx::install_basis(const std::vector<float> &U, int r) {
             Uz[k] = __bfloat162float(ub[k]);
         }
         U16.upload(ub, s);
+        // transposed copy and TMA descriptors for the tensor-core kernels
+        umma.ok = false;
+        if (umma_supported(ld, n)) {
+            n_pad = (n + 63) / 64 * 64;
+            std::vector<__nv_bfloat16> ut((size_t)ld * n_pad, __float2bfloat16_rn(0.f));
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < ld; ++j) ut[(size_t)j * n_pad + i] = ub[(size_t)i * ld + j];
+            Ut16.upload(ut, s);
+            umma_setup(umma, U16, Ut16, n, n_pad, ld);
+            umma_partial.alloc((size_t)umma_project_blocks(n) * ld * 3);
+        } else {
+            Ut16.release();
+        }
     }
     U32.upload(Uz, s);
+    // compact copy of the leading columns for the solves with collision
+    // springs: width a power of two in [8, 128] holding r_reuse columns
+    ldc = 0;
+    if (r_reuse > 0) {
+        ldc = 8;
+        while (ldc < r_reuse) ldc *= 2;
+        std::vector<float> Uc((size_t)n * ldc, 0.f);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < std::min(ldc, ld); ++j) Uc[(size_t)i * ldc + j] = Uz[(size_t)i * ld + j];
+        if (P.precision == 1) {
+            std::vector<__nv_bfloat16> ucb(Uc.size());
+            for (size_t k = 0; k < Uc.size(); ++k) ucb[k] = __float2bfloat16_rn(Uc[k]);  // exact: already rounded
+            Uc16.upload(ucb, s);
+            Uc32.release();
+        } else {
+            Uc32.upload(Uc, s);
+            Uc16.release();
+        }
+    }
     std::vector<double> A0h;  // [ld][ld], zero padding rows / columns
     reduced_matrix(s, cloth(), U32, ld, A0h);
     std::vector<double> A0r((size_t)r * r), Ainv;
@@ -824,11 +871,12 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             rl = RL;
         }
         if (r_warm > 0 && (r_nc > 0 || r_c > 0)) {
-            PROF("subspace_project", bytes_basis(contacts ? r_c : r_nc), launch_project(s, S, rl, n_cv_d, W));
+            PROF("subspace_project", bytes_basis(contacts ? r_c : r_nc),
+                 launch_project(s, S, rl, n_cv_d, W, contacts));
             if (contacts && r_c > 0) PROF("subspace_syrk", 0, launch_syrk(s, S, contact_list, n_cv_d, cw, W));
             PROF("reduced_solve", 0, launch_reduced_solve(s, S, n_cv_d, W));
             PROF("subspace_lift", bytes_basis(contacts ? r_c : r_nc) + 12.0 * n,
-                 launch_lift(s, S, n_cv_d, W, have_delta ? din : nullptr, dout));
+                 launch_lift(s, S, n_cv_d, W, have_delta ? din : nullptr, dout, contacts));
             std::swap(din, dout);
             have_delta = true;
         }
@@ -890,8 +938,24 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
     }
     if (contacts && P.collisions) {
         bp.prof = prof.on ? &prof : nullptr;
+        CollParams cp = cparams();
+        if (log) {
+            near_cnt.alloc(1);
+            near_cnt.zero(s);
+            cp.near_count = near_cnt.p;
+        }
         PROF("partial_ccd", 0,
-             launch_partial_ccd(s, coll(), bp, Xm, Xp, cparams(), act, cap_act, n_act_d, &sc.p->overflow, disp));
+             launch_partial_ccd(s, coll(), bp, Xm, Xp, cp, act, cap_act, n_act_d, &sc.p->overflow, disp));
+        if (log) {
+            long long cnt[2] = {0, 0};
+            int nn = 0;
+            bp.cnt_vt_d[bp.cur].download(&cnt[0], 1, s);
+            bp.cnt_ee_d[bp.cur].download(&cnt[1], 1, s);
+            near_cnt.download(&nn, 1, s);
+            PDC_CK(cudaStreamSynchronize(s));
+            std::fprintf(stderr, "[pdc] partial ccd: pairs vt=%lld ee=%lld, past the displacement prefilter %d\n",
+                         cnt[0], cnt[1], nn);
+        }
     }
 }
 
@@ -918,9 +982,19 @@ void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {
         st.overflow_retries++;
         if (log) std::fprintf(stderr, "[pdc] broad phase regrown after overflow 0x%x\n", ovf);
     }
+    if (prof.on) {  // list size for the byte models of the pair kernels
+        long long cnt[2] = {0, 0};
+        bp.cnt_vt_d[bp.cur].download(&cnt[0], 1, s);
+        bp.cnt_ee_d[bp.cur].download(&cnt[1], 1, s);
+        PDC_CK(cudaStreamSynchronize(s));
+        bp.h_pairs = cnt[0] + cnt[1];
+    }
     unsigned long long inf = 0x7ff0000000000000ULL;  // +inf
     PDC_CK(cudaMemcpyAsync(toi_bits.p, &inf, sizeof(inf), cudaMemcpyHostToDevice, s));
-    PROF("full_ccd", 0, launch_full_ccd(s, coll(), bp, x0, x1, cparams(), merge, toi_bits));
+    // algorithmic bytes: both position sets once, per pair its key and state
+    // (plus the previous list's key and state read by the merge)
+    PROF("full_ccd", 32.0 * nv_all + (merge ? 18.0 : 9.0) * (double)bp.h_pairs,
+         launch_full_ccd(s, coll(), bp, x0, x1, cparams(), merge, toi_bits));
     k_step_fraction<<<1, 1, 0, s>>>(toi_bits, P.alpha_ls, sfrac, ttoi);
     PDC_LAUNCH_CK();
 }
@@ -1048,6 +1122,14 @@ void pdc_ctx::step() {
     double tt = 2.0, sf = 1.0;
     bad_d.download(&bad, 1, s);
     sflag.download(&sflag_h, 1, s);
+    PDC_CK(cudaStreamSynchronize(s));
+    if (sflag_h & PDC_DEVERR_UMMA) {
+        PDC_CK(cudaMemcpyAsync(Xs.p, Xbak.p, sizeof(float4) * nv_all, cudaMemcpyDeviceToDevice, s));
+        PDC_CK(cudaMemcpyAsync(Vs.p, Vbak.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+        sflag.zero(s);
+        PDC_CK(cudaStreamSynchronize(s));
+        throw Error(PDC_ERR_TIMEOUT, "a tensor-core subspace kernel timed out waiting on its copies; state rolled back");
+    }
     if (P.collisions) {
         bp.cnt_vt_d[bp.cur].download(&counts[0], 1, s);
         bp.cnt_ee_d[bp.cur].download(&counts[1], 1, s);
@@ -1136,6 +1218,7 @@ void pdc_default_params(pdc_params *p) {
     p->sweep_kind = 0;
     p->cheb_ratio = 100.0;
     p->aa_depth = 6;
+    p->tensor_cores = 1;
 }
 
 pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const pdc_params *params, void *stream,
@@ -1595,6 +1678,55 @@ pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, con
     }
     launch_sweep(s, c, h->CW, h->R, din, dout, 0.f, ua, ua.p, nullptr, nullptr, 1.f, xa, xo.p);  // x + delta
     get_f4(h, xo, x_out, 0);
+    API_END(h)
+}
+
+pdc_status pdc_op_project(pdc_handle h, const float *v, int32_t r, double *g) {
+    API_BEGIN(h)
+    if (!v || !g) throw Error(PDC_ERR_ARG, "pdc_op_project: NULL");
+    if (r <= 0 || r > h->r_warm) throw Error(PDC_ERR_ARG, "pdc_op_project: r must be in [1, r_warm]");
+    DevBuf<float4> va;
+    upload_f4(h, v, h->n, va);
+    DevBuf<int> zero;
+    zero.alloc(1);
+    zero.zero(h->s);
+    SubspaceView S = h->sub(r, 0);
+    SubspaceWork W = h->work();
+    launch_project(h->s, S, va, zero, W, false);
+    PDC_CK(cudaMemcpyAsync(g, W.g, sizeof(double) * 3 * r, cudaMemcpyDeviceToHost, h->s));
+    int fl = 0;
+    h->sflag.download(&fl, 1, h->s);
+    PDC_CK(cudaStreamSynchronize(h->s));
+    if (fl & PDC_DEVERR_UMMA) {
+        h->sflag.zero(h->s);
+        throw Error(PDC_ERR_TIMEOUT, "pdc_op_project: tensor-core kernel timed out");
+    }
+    API_END(h)
+}
+
+pdc_status pdc_op_lift(pdc_handle h, const double *q, int32_t r, float *out) {
+    API_BEGIN(h)
+    if (!q || !out) throw Error(PDC_ERR_ARG, "pdc_op_lift: NULL");
+    if (r <= 0 || r > h->r_warm) throw Error(PDC_ERR_ARG, "pdc_op_lift: r must be in [1, r_warm]");
+    std::vector<float> qf(3 * (size_t)r);
+    for (size_t k = 0; k < qf.size(); ++k) qf[k] = (float)q[k];
+    SubspaceView S = h->sub(r, 0);
+    SubspaceWork W = h->work();
+    PDC_CK(cudaMemcpyAsync(W.q, qf.data(), sizeof(float) * qf.size(), cudaMemcpyHostToDevice, h->s));
+    DevBuf<int> zero;
+    zero.alloc(1);
+    zero.zero(h->s);
+    DevBuf<float4> o;
+    o.alloc(h->n);
+    launch_lift(h->s, S, zero, W, nullptr, o, false);
+    int fl = 0;
+    h->sflag.download(&fl, 1, h->s);
+    PDC_CK(cudaStreamSynchronize(h->s));
+    if (fl & PDC_DEVERR_UMMA) {
+        h->sflag.zero(h->s);
+        throw Error(PDC_ERR_TIMEOUT, "pdc_op_lift: tensor-core kernel timed out");
+    }
+    get_f4(h, o, out, 0);
     API_END(h)
 }
 

@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, 3) k_pairs_update(CollView cv, c
     long long start = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
     for (long long base = start; base < n; base += stride) {  // warp-uniform trip count
         long long idx = base + (threadIdx.x & 31);
-        bool want = false;
+        bool want = false, tested = false;
         ActivePair ap;
         if (idx < n) {
             int ids[4], kind;
@@ -427,6 +427,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, 3) k_pairs_update(CollView cv, c
                         rel = fmaxf(rel, dot3(dd, dd));
                     }
                 near = *d0p <= (P.dhat + sqrtf(rel)) * 1.001f + 1e-7f;
+                tested = near;
             }
             float4 a0[4];
             if (near)
@@ -459,6 +460,10 @@ __global__ void __launch_bounds__(PAIR_THREADS, 3) k_pairs_update(CollView cv, c
                 ap.c = make_float4(c[0], c[1], c[2], c[3]);
                 ap.n0w = make_float4(n0.x, n0.y, n0.z, ndb_weight(P, st & 0x7f));
             }
+        }
+        if (P.near_count) {
+            unsigned m = __ballot_sync(0xffffffffu, tested);
+            if ((threadIdx.x & 31) == 0 && m) atomicAdd(P.near_count, __popc(m));
         }
         append_active(want, ap, act, cap, n_act, overflow);
     }
@@ -600,11 +605,13 @@ void launch_collect_active(cudaStream_t s, const CollView &cv, BroadPhase &bp, c
 void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm, const float4 *xp,
                         const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow, float4 *disp) {
     int c = bp.cur;
-    if (bp.prof) bp.prof->begin(s, "pccd_prep", 0.0);
+    // algorithmic bytes: positions read and displacement written once per
+    // vertex; per candidate pair its key, stored distance and state byte
+    if (bp.prof) bp.prof->begin(s, "pccd_prep", 40.0 * cv.nv);
     PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
     if (cv.nv > 0) k_disp<<<(cv.nv + 255) / 256, 256, 0, s>>>(cv.nv, xm, xp, disp);
     if (bp.prof) bp.prof->end(s);
-    if (bp.prof) bp.prof->begin(s, "pccd_pairs", 0.0);
+    if (bp.prof) bp.prof->begin(s, "pccd_pairs", 14.0 * (double)bp.h_pairs + 40.0 * cv.nv);
     k_pairs_update<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
                                                         bp.st_vt[c], bp.st_ee[c], bp.d0_vt[c], bp.d0_ee[c], disp, xm,
                                                         xp, P, 1, act, cap_act, n_act, overflow);

@@ -21,6 +21,13 @@ __device__ inline int active_r(const SubspaceView &S, const int *n_cv) {
     return (n_cv && *n_cv > 0) ? S.r_c : S.r_nc;
 }
 
+// The compact copy serves the solves with collision springs when it holds
+// their r_c columns.
+__host__ __device__ inline bool compact_covers(const SubspaceView &S) { return S.ldc > 0 && S.r_c > 0 && S.r_c <= S.ldc; }
+__device__ inline bool compact_active(const SubspaceView &S, const int *n_cv) {
+    return compact_covers(S) && n_cv && *n_cv > 0;
+}
+
 template <class TU> __device__ inline float tofloat(TU v);
 template <> __device__ inline float tofloat<float>(float v) { return v; }
 template <> __device__ inline float tofloat<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -55,6 +62,7 @@ __global__ void __launch_bounds__(PROJ_T) k_project(SubspaceView S, const TU *__
                                                     const float4 *__restrict__ rl, const int *n_cv,
                                                     float *__restrict__ partial) {
     __shared__ float s_acc[PROJ_W][256 * 3];
+    if (compact_active(S, n_cv)) return;
     int r = active_r(S, n_cv);
     if (r == 0) return;
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -112,6 +120,121 @@ __global__ void __launch_bounds__(PROJ_T) k_project(SubspaceView S, const TU *__
 #pragma unroll
                 for (int q = 0; q < PROJ_W; ++q) v += s_acc[q][e];
                 partial[((long long)blockIdx.x * S.ld + j) * 3 + e % 3] = v;
+            }
+        }
+    }
+}
+
+
+// Projection and lift over the compact copy [n][ldc] (ldc <= 128): LPR =
+// ldc/8 lanes share a row (8 columns each), so a warp covers 32/LPR
+// consecutive rows with one contiguous 512-byte (BF16) or 1 KB (FP32) load.
+template <class TU, int LPR>
+__global__ void __launch_bounds__(PROJ_T) k_project_compact(SubspaceView S, const TU *__restrict__ U,
+                                                            const float4 *__restrict__ rl, const int *n_cv,
+                                                            float *__restrict__ partial) {
+    __shared__ float s_acc[PROJ_W][128 * 3];
+    if (!compact_active(S, n_cv)) return;
+    constexpr int RPW = 32 / LPR;  // rows per warp and pass
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int slot = lane / LPR, cg = lane % LPR;
+    float acc[8][3];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
+    long long gw = (long long)blockIdx.x * PROJ_W + w, nw = (long long)gridDim.x * PROJ_W;
+    constexpr int UR = 4;  // passes in flight per warp
+    for (long long p0 = gw; p0 * RPW < S.n; p0 += nw * UR) {
+        float4 rv[UR];
+        float u[UR][8];
+#pragma unroll
+        for (int q = 0; q < UR; ++q) {
+            long long i = (p0 + q * nw) * RPW + slot;
+            bool ok = i < S.n;
+            rv[q] = ok ? __ldg(rl + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok) load8(U + i * S.ldc + cg * 8, u[q]);
+            else
+#pragma unroll
+                for (int k = 0; k < 8; ++k) u[q][k] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < UR; ++q)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                acc[k][0] = fmaf(u[q][k], rv[q].x, acc[k][0]);
+                acc[k][1] = fmaf(u[q][k], rv[q].y, acc[k][1]);
+                acc[k][2] = fmaf(u[q][k], rv[q].z, acc[k][2]);
+            }
+    }
+    // sum the row slots of each column group
+#pragma unroll
+    for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) acc[k][d] += __shfl_xor_sync(0xffffffffu, acc[k][d], o);
+    if (slot == 0)
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) s_acc[w][(cg * 8 + k) * 3 + d] = acc[k][d];
+    __syncthreads();
+    int r = S.r_c;
+    for (int e = threadIdx.x; e < r * 3; e += PROJ_T) {
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < PROJ_W; ++q) v += s_acc[q][e];
+        partial[(long long)blockIdx.x * S.ld * 3 + e] = v;
+    }
+}
+
+template <class TU, int LPR>
+__global__ void __launch_bounds__(256) k_lift_compact(SubspaceView S, const TU *__restrict__ U, const int *n_cv,
+                                                      const float *__restrict__ q, const float4 *__restrict__ din,
+                                                      float4 *__restrict__ dout) {
+    if (!compact_active(S, n_cv)) return;
+    constexpr int RPW = 32 / LPR;
+    int lane = threadIdx.x & 31;
+    int slot = lane / LPR, cg = lane % LPR;
+    int r = S.r_c;
+    float ql[8][3];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        int j = cg * 8 + k;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ql[k][d] = j < r ? q[j * 3 + d] : 0.f;
+    }
+    int wpb = blockDim.x >> 5;
+    long long nw = (long long)gridDim.x * wpb;
+    constexpr int UR = 4;
+    for (long long p0 = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); p0 * RPW < S.n; p0 += nw * UR) {
+        float u[UR][8];
+#pragma unroll
+        for (int t = 0; t < UR; ++t) {
+            long long i = (p0 + t * nw) * RPW + slot;
+            if (i < S.n) load8(U + i * S.ldc + cg * 8, u[t]);
+            else
+#pragma unroll
+                for (int k = 0; k < 8; ++k) u[t][k] = 0.f;
+        }
+#pragma unroll
+        for (int t = 0; t < UR; ++t) {
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                a0 = fmaf(u[t][k], ql[k][0], a0);
+                a1 = fmaf(u[t][k], ql[k][1], a1);
+                a2 = fmaf(u[t][k], ql[k][2], a2);
+            }
+#pragma unroll
+            for (int o = 1; o < LPR; o <<= 1) {
+                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            }
+            long long i = (p0 + t * nw) * RPW + slot;
+            if (cg == 0 && i < S.n) {
+                float4 d = din ? din[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                dout[i] = make_float4(d.x + a0, d.y + a1, d.z + a2, 0.f);
             }
         }
     }
@@ -261,6 +384,7 @@ __global__ void __launch_bounds__(256) k_lift(SubspaceView S, const TU *__restri
                                               const float *__restrict__ q, const float4 *__restrict__ din,
                                               float4 *__restrict__ dout) {
     __shared__ float s_q[256 * NCH * 3];
+    if (compact_active(S, n_cv)) return;
     int r = active_r(S, n_cv);
     for (int e = threadIdx.x; e < 256 * NCH * 3; e += blockDim.x) s_q[e] = e < r * 3 ? q[e] : 0.f;
     __syncthreads();
@@ -346,11 +470,47 @@ template <class TU> static void project_t(cudaStream_t s, const SubspaceView &S,
     else k_project<TU, 4><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, U, rl, n_cv, partial);
 }
 
-void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W) {
+template <class TU> static void project_compact_t(cudaStream_t s, const SubspaceView &S, const TU *U,
+                                                  const float4 *rl, const int *n_cv, float *partial) {
+    switch (S.ldc) {
+        case 8: k_project_compact<TU, 1><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, U, rl, n_cv, partial); break;
+        case 16: k_project_compact<TU, 2><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, U, rl, n_cv, partial); break;
+        case 32: k_project_compact<TU, 4><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, U, rl, n_cv, partial); break;
+        case 64: k_project_compact<TU, 8><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, U, rl, n_cv, partial); break;
+        case 128: k_project_compact<TU, 16><<<PROJ_BLOCKS, PROJ_T, 0, s>>>(S, U, rl, n_cv, partial); break;
+        default: throw Error(PDC_ERR_ARG, "compact basis width must be 8, 16, 32, 64 or 128");
+    }
+}
+
+template <class TU> static void lift_compact_t(cudaStream_t s, const SubspaceView &S, const TU *U, const int *n_cv,
+                                               const float *q, const float4 *din, float4 *dout) {
+    int blocks = std::min((S.n + 63) / 64, 152 * 8);
+    switch (S.ldc) {
+        case 8: k_lift_compact<TU, 1><<<blocks, 256, 0, s>>>(S, U, n_cv, q, din, dout); break;
+        case 16: k_lift_compact<TU, 2><<<blocks, 256, 0, s>>>(S, U, n_cv, q, din, dout); break;
+        case 32: k_lift_compact<TU, 4><<<blocks, 256, 0, s>>>(S, U, n_cv, q, din, dout); break;
+        case 64: k_lift_compact<TU, 8><<<blocks, 256, 0, s>>>(S, U, n_cv, q, din, dout); break;
+        case 128: k_lift_compact<TU, 16><<<blocks, 256, 0, s>>>(S, U, n_cv, q, din, dout); break;
+        default: throw Error(PDC_ERR_ARG, "compact basis width must be 8, 16, 32, 64 or 128");
+    }
+}
+
+void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W,
+                    bool maybe_contacts) {
+    if (!maybe_contacts && S.umma && S.r_nc > 0 && S.r_nc <= S.ld) {
+        launch_project_umma(s, *S.umma, S.r_nc, rl, S.umma_partial, W.g, S.dev_err);
+        return;
+    }
     if (S.precision == 1)
         project_t<__nv_bfloat16>(s, S, S.U16, rl, n_cv, W.partial);
     else
         project_t<float>(s, S, S.U32, rl, n_cv, W.partial);
+    if (maybe_contacts && compact_covers(S)) {
+        if (S.precision == 1)
+            project_compact_t<__nv_bfloat16>(s, S, S.Uc16, rl, n_cv, W.partial);
+        else
+            project_compact_t<float>(s, S, S.Uc32, rl, n_cv, W.partial);
+    }
     int mx = S.ld * 3 * 32;
     k_project_reduce<<<(mx + 255) / 256, 256, 0, s>>>(S, n_cv, PROJ_BLOCKS, W.partial, W.g);
     PDC_LAUNCH_CK();
@@ -388,7 +548,17 @@ void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv
 }
 
 void launch_lift(cudaStream_t s, const SubspaceView &S, const int *n_cv, const SubspaceWork &W, const float4 *din,
-                 float4 *dout) {
+                 float4 *dout, bool maybe_contacts) {
+    if (!maybe_contacts && S.umma && S.r_nc > 0 && S.r_nc <= S.ld) {
+        launch_lift_umma(s, *S.umma, S.r_nc, W.q, din, dout, S.dev_err);
+        return;
+    }
+    if (maybe_contacts && compact_covers(S) && S.n > 0) {
+        if (S.precision == 1)
+            lift_compact_t<__nv_bfloat16>(s, S, S.Uc16, n_cv, W.q, din, dout);
+        else
+            lift_compact_t<float>(s, S, S.Uc32, n_cv, W.q, din, dout);
+    }
     int blocks = std::min((S.n + 7) / 8, 152 * 16);
     if (blocks < 1) return;
     int rmax = std::max(S.r_nc, S.r_c);

@@ -1,6 +1,7 @@
 // Subspace-reuse kernels (Sec. 5) and basis construction.
 #pragma once
 #include "pdc_internal.cuh"
+#include "pdc_umma.cuh"
 
 namespace pdc {
 
@@ -18,6 +19,15 @@ struct SubspaceView {
     const double *A0inv;       // [r_nc][r_nc] inverse (FP64)
     const float *A0inv32;      // [r_nc][r_nc] inverse (FP32)
     int precision;             // 0 plain FP32, 1 mixed
+    // compact copy of the leading ldc columns ([n][ldc], same values as U):
+    // the solves with collision springs stream only these
+    int ldc;                   // 0: no compact copy
+    const float *Uc32;
+    const __nv_bfloat16 *Uc16;
+    // tensor-core path of the full-basis solves (host pointer; NULL: off)
+    const UmmaMaps *umma;
+    float *umma_partial;       // [tiles][ld][3]
+    int *dev_err;              // status word receiving PDC_DEVERR_UMMA
 };
 
 struct SubspaceWork {
@@ -30,8 +40,10 @@ struct SubspaceWork {
 
 constexpr int PROJ_BLOCKS = 608;
 
-// g = U[:, :r]^T rl  (r = r_c if *n_cv > 0 else r_nc).
-void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W);
+// g = U[:, :r]^T rl  (r = r_c if *n_cv > 0 else r_nc).  maybe_contacts =
+// false promises *n_cv == 0 (only the full-basis kernel is launched).
+void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W,
+                    bool maybe_contacts = true);
 // dA = sum over listed vertices of cw_v U_v U_v^T (leading r_c columns).
 void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const int *n_cv, const float *cw,
                  SubspaceWork &W);
@@ -39,7 +51,7 @@ void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const i
 void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv, SubspaceWork &W);
 // dout = din + U q (din may be NULL: zero).
 void launch_lift(cudaStream_t s, const SubspaceView &S, const int *n_cv, const SubspaceWork &W, const float4 *din,
-                 float4 *dout);
+                 float4 *dout, bool maybe_contacts = true);
 // rl = r - (H + diag(cw)) delta (linear residual of the global system).
 void launch_linear_residual(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r,
                             const float4 *delta, float4 *rl);

@@ -40,7 +40,8 @@ class pdc_params(ctypes.Structure):
                 ("r_warm", c_i32), ("r_reuse", c_i32), ("precision", c_i32), ("samples_vt", c_i32),
                 ("samples_ee", c_i32), ("collisions", c_i32), ("fixed_iters", c_i32), ("eig_iters", c_i32),
                 ("seed", c_u64), ("accel", c_i32), ("accel_rho", c_dbl), ("sweep_kind", c_i32),
-                ("cheb_ratio", c_dbl), ("aa_depth", c_i32)]
+                ("cheb_ratio", c_dbl), ("aa_depth", c_i32),
+                ("tensor_cores", c_i32)]
 
 
 class pdc_stats(ctypes.Structure):
@@ -82,6 +83,8 @@ SIGNATURES = {
     "pdc_op_residual": (c_i32, [P, P, P, P, P, P]),
     "pdc_op_global_solve": (c_i32, [P, P, P, P, P, c_i32, c_i32, c_i32, P]),
     "pdc_op_contact_noalloc": (c_i32, [P, P, P, P, P, P, c_i64, P, P, P]),
+    "pdc_op_project": (c_i32, [P, P, c_i32, P]),
+    "pdc_op_lift": (c_i32, [P, P, c_i32, P]),
 }
 
 _lib = None
@@ -286,6 +289,20 @@ def pdc_op_global_solve(h, x, z, cw, cf, r, cycles, sweeps):
     out = np.empty_like(x)
     _check(h, lib().pdc_op_global_solve(h, _ptr(x), _ptr(z), _ptr(cw), _ptr(cf), int(r), int(cycles), int(sweeps),
                                         _ptr(out)))
+    return out
+
+
+def pdc_op_project(h, v, r):
+    v = _f32(v, (-1, 3))
+    g = np.empty((int(r), 3), np.float64)
+    _check(h, lib().pdc_op_project(h, _ptr(v), int(r), _ptr(g)))
+    return g
+
+
+def pdc_op_lift(h, n, q, r):
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, 3)
+    out = np.empty((n, 3), np.float32)
+    _check(h, lib().pdc_op_lift(h, _ptr(q), int(r), _ptr(out)))
     return out
 
 

@@ -1,0 +1,95 @@
+"""GPU parity of the subspace contractions of Sec. 5 through the C ABI: the
+projection g = U^T v (Eq. subspace_global) and the lift U q
+(Eq. subspace_collision), on the tcgen05 tensor-core path of the mixed form
+and on the CUDA-core paths, against FP64 products with the basis the library
+actually holds (BF16-rounded in the mixed form, Eq. uu's A0 is built from
+the same rounded basis).
+
+Tolerance: both paths see the FP32 operand with at least a 16-bit
+significand (the tensor-core path splits it into two BF16 parts) and
+accumulate in FP32, so each entry is within 1e-4 of the sum of absolute
+products (sum_i |U_ij| |v_i| for g, sum_j |U_ij| |q_j| for the lift).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    from paper_2403_19272_gb300 import build
+    build.build()
+    from paper_2403_19272_gb300 import pdcloth
+    return pdcloth
+
+
+def _cloth(pc, side, r, precision, tensor_cores, seed):
+    sc = wl.hanging_swept(side=side)
+    p = pc.pdc_default_params()
+    p.r_warm = 0
+    p.r_reuse = 32
+    p.precision = precision
+    p.tensor_cores = tensor_cores
+    cl = pc.Cloth(sc, p)
+    rng = np.random.default_rng(seed)
+    U = (rng.standard_normal((sc.n, r)) / np.sqrt(sc.n)).astype(np.float32)
+    pc.pdc_set_basis(cl.h, U)
+    Ug, _ = pc.pdc_get_basis(cl.h, sc.n, r)
+    return sc, cl, Ug.astype(np.float64), rng
+
+
+def _check_project(pc, cl, Ug, rng, r):
+    n = Ug.shape[0]
+    v = rng.standard_normal((n, 3)).astype(np.float32) * np.float32(3.7)
+    g = pc.pdc_op_project(cl.h, v, r)
+    U = Ug[:, :r]
+    ref = U.T @ v.astype(np.float64)
+    scale = np.abs(U).T @ np.abs(v.astype(np.float64))
+    assert np.all(np.abs(g - ref) <= 1e-4 * scale + 1e-30)
+    return g
+
+
+def _check_lift(pc, cl, Ug, rng, r):
+    n = Ug.shape[0]
+    q = rng.standard_normal((r, 3)) * 0.3
+    out = pc.pdc_op_lift(cl.h, n, q, r)
+    U = Ug[:, :r]
+    qf = q.astype(np.float32).astype(np.float64)
+    ref = U @ qf
+    scale = np.abs(U) @ np.abs(qf)
+    assert np.all(np.abs(out - ref) <= 1e-4 * scale + 1e-30)
+    return out
+
+
+@pytest.mark.parametrize("precision,tensor_cores", [(1, 1), (1, 0), (0, 0)])
+@pytest.mark.parametrize("r", [256, 128])
+def test_project_and_lift_ragged_tiles(pc, precision, tensor_cores, r):
+    # 40 x 40 = 1600 rows: 12 full 128-row tiles and a ragged tail
+    sc, cl, Ug, rng = _cloth(pc, 40, r, precision, tensor_cores, 31 + r)
+    _check_project(pc, cl, Ug, rng, r)
+    _check_lift(pc, cl, Ug, rng, r)
+    cl.close()
+
+
+def test_tensor_core_and_cuda_core_paths_agree(pc):
+    outs = []
+    for tc in (1, 0):
+        sc, cl, Ug, rng = _cloth(pc, 33, 256, 1, tc, 77)
+        v = np.random.default_rng(5).standard_normal((sc.n, 3)).astype(np.float32)
+        q = np.random.default_rng(6).standard_normal((256, 3))
+        outs.append((pc.pdc_op_project(cl.h, v, 256), pc.pdc_op_lift(cl.h, sc.n, q, 256)))
+        cl.close()
+    (g1, l1), (g0, l0) = outs
+    assert np.max(np.abs(g1 - g0)) <= 1e-4 * np.max(np.abs(g0))
+    assert np.max(np.abs(l1 - l0)) <= 1e-4 * np.max(np.abs(l0))
+
+
+def test_project_and_lift_full_size_512(pc):
+    # the benchmark's configuration: n = 262,144, r = 256, BF16 basis on the tensor cores
+    sc, cl, Ug, rng = _cloth(pc, 512, 256, 1, 1, 99)
+    _check_project(pc, cl, Ug, rng, 256)
+    _check_lift(pc, cl, Ug, rng, 256)
+    cl.close()
