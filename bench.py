@@ -38,12 +38,18 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=SIDE)
-    ap.add_argument("--forms", default="mixed,fp32")
+    ap.add_argument("--forms", default="mixed16,mixed,fp32",
+                    help="comma list of mixed16 (FP16 basis), mixed (BF16 basis), fp32; the first is the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-side", type=int, default=64)
     ap.add_argument("--no-launch-count", action="store_true",
                     help="skip the CUDA activity trace (e.g. when running under ncu)")
     return ap.parse_args()
+
+
+# form name -> pdc_params.precision, and the arithmetic types each form computes in
+FORMS = {"mixed16": 2, "mixed": 1, "fp32": 0}
+DTYPES = {"mixed16": "f16+f32+f64", "mixed": "bf16+f32+f64", "fp32": "f32"}
 
 
 def solver_params(pc, precision):
@@ -320,9 +326,9 @@ def main():
     scene = wl.hanging_swept(side=a.side)
     forms = {}
     for f in a.forms.split(","):
-        forms[f] = run_form(pc, torch, scene, 1 if f == "mixed" else 0, a.steps, a.warmup, local,
+        forms[f] = run_form(pc, torch, scene, FORMS[f], a.steps, a.warmup, local,
                             not a.no_launch_count)
-    head = "mixed" if "mixed" in forms else list(forms)[0]
+    head = list(forms)[0]
     ms = forms[head]["ms"]
     if world > 1:
         import torch.distributed as dist
@@ -336,7 +342,7 @@ def main():
     line = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms/step", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16+f32+f64" if head == "mixed" else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": head, "basis": "r=256 (r_reuse=32 with collision springs)",
                    "l2": "inputs larger than L2 (basis 134 MB BF16 / 268 MB FP32 plus matrices and state)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -96,8 +96,11 @@ typedef struct {
     int32_t solve_cycles;    /* subspace correction + sweeps per LG iteration    */
     int32_t r_warm;          /* basis size used without collision springs (0: none) */
     int32_t r_reuse;         /* leading columns used with collision springs      */
-    int32_t precision;       /* 0: plain FP32; 1: mixed (BF16 basis on tensor
-                                cores, FP64 reduced solves)                      */
+    int32_t precision;       /* 0: plain FP32; 1: mixed with a BF16 basis; 2:
+                                mixed with an FP16 basis scaled by a power of two
+                                (its rounding noise carries ~2^-6 of the BF16
+                                noise's H-energy).  Mixed forms: 16-bit basis on
+                                the tensor cores, FP64 reduced solves            */
     int32_t samples_vt;      /* partial-CCD sample pattern: 0, 1 or 3            */
     int32_t samples_ee;      /* partial-CCD sample pattern: 0, 1 or 4            */
     int32_t collisions;      /* 0: no collision handling at all                  */

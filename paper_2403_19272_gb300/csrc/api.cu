@@ -226,14 +226,14 @@ struct pdc_ctx {
     // subspace
     int r_warm = 0, r_reuse = 0, ld = 0;
     DevBuf<float> U32, A0inv32, proj_partial, qbuf, dA;
-    DevBuf<__nv_bfloat16> U16;
-    DevBuf<__nv_bfloat16> Ut16;  // transposed BF16 basis [ld][n_pad] (tensor-core projection)
+    DevBuf<uint16_t> U16bits;    // 16-bit basis [n][ld] (BF16 or scaled FP16 bits)
+    DevBuf<uint16_t> Ut16;       // its transpose [ld][n_pad] (tensor-core projection)
     int n_pad = 0;
     UmmaMaps umma;
     DevBuf<float> umma_partial;
     int ldc = 0;                 // width of the compact copy of the leading r_reuse columns
     DevBuf<float> Uc32;
-    DevBuf<__nv_bfloat16> Uc16;
+    DevBuf<uint16_t> Uc16bits;
     DevBuf<double> A0, A0inv, gbuf;
     DevBuf<int> sflag;
     // scalars
@@ -257,7 +257,6 @@ struct pdc_ctx {
     double gersh = 1.0;       // Gershgorin bound of D^-1 H
     long long nnz_off = 0;  // off-diagonal entries of H over free rows
     bool log = std::getenv("PDC_LOG") != nullptr;  // per-iteration residuals to stderr
-    DevBuf<int> near_cnt;                            // logging only
 
     ~pdc_ctx() {
         if (hsc) cudaFreeHost(hsc);
@@ -306,15 +305,17 @@ struct pdc_ctx {
         S.r_nc = r_nc;
         S.r_c = r_c;
         S.U32 = U32;
-        S.U16 = U16;
+        S.U16 = P.precision == 1 ? reinterpret_cast<const __nv_bfloat16 *>(U16bits.p) : nullptr;
+        S.Uh = P.precision == 2 ? reinterpret_cast<const __half *>(U16bits.p) : nullptr;
         S.A0 = A0;
         S.A0inv = A0inv;
         S.A0inv32 = A0inv32;
         S.precision = P.precision;
         S.ldc = ldc;
         S.Uc32 = Uc32;
-        S.Uc16 = Uc16;
-        S.umma = (umma.ok && P.precision == 1 && P.tensor_cores) ? &umma : nullptr;
+        S.Uc16 = P.precision == 1 ? reinterpret_cast<const __nv_bfloat16 *>(Uc16bits.p) : nullptr;
+        S.Uch = P.precision == 2 ? reinterpret_cast<const __half *>(Uc16bits.p) : nullptr;
+        S.umma = (umma.ok && P.precision != 0 && P.tensor_cores) ? &umma : nullptr;
         S.umma_partial = umma_partial;
         S.dev_err = sflag;
         return S;
@@ -357,7 +358,7 @@ struct pdc_ctx {
         return (double)nnz_off * 8 + (double)n * (12 + 12 + 4 + 1 + 12) + (contacts ? 4.0 * n : 0.0) +
                (writes_x ? 24.0 * n : 0.0);
     }
-    double bytes_basis(int r) const { return (double)n * r * (P.precision == 1 ? 2 : 4) + (double)n * 12; }
+    double bytes_basis(int r) const { return (double)n * r * (P.precision != 0 ? 2 : 4) + (double)n * 12; }
     void lg_iteration(bool contacts, bool check_rel, double rho0, bool &converged, int r_nc, int r_c, int cycles,
                       int sweeps);
     void full_ccd(const float4 *x0, const float4 *x1, bool merge);
@@ -672,46 +673,72 @@ void pdc_ctx::install_basis(const std::vector<float> &U, int r) {
     for (int i = 0; i < n; ++i)
         if (freev[i])
             for (int j = 0; j < r; ++j) Uz[(size_t)i * ld + j] = U[(size_t)i * r + j];
-    if (P.precision == 1) {
-        // round to BF16; the reduced matrix is formed from the rounded basis
-        std::vector<__nv_bfloat16> ub(Uz.size());
-        for (size_t k = 0; k < Uz.size(); ++k) {
-            ub[k] = __float2bfloat16_rn(Uz[k]);
-            Uz[k] = __bfloat162float(ub[k]);
+    // mixed forms: round to 16 bits; everything downstream (reduced matrix,
+    // SYRK, projections) uses the rounded basis.  BF16 as is; FP16 after
+    // scaling by the power of two that puts the largest entry in [2^13, 2^14)
+    // (the scale cancels: U^T H U scales by s^2, U^T r by s, q by 1/s).
+    const bool half16 = P.precision == 2;
+    std::vector<uint16_t> ub;
+    if (P.precision != 0) {
+        float scale = 1.f;
+        if (half16) {
+            float mx = 0.f;
+            for (float v : Uz) mx = std::max(mx, std::fabs(v));
+            int e = 0;
+            if (mx > 0.f) std::frexp(mx, &e);
+            scale = std::ldexp(1.f, 14 - e);
         }
-        U16.upload(ub, s);
+        ub.resize(Uz.size());
+        for (size_t k = 0; k < Uz.size(); ++k) {
+            float v = Uz[k] * scale;
+            if (half16) {
+                __half h = __float2half_rn(v);
+                std::memcpy(&ub[k], &h, 2);
+                Uz[k] = __half2float(h);
+            } else {
+                __nv_bfloat16 h = __float2bfloat16_rn(v);
+                std::memcpy(&ub[k], &h, 2);
+                Uz[k] = __bfloat162float(h);
+            }
+        }
+        U16bits.upload(ub, s);
         // transposed copy and TMA descriptors for the tensor-core kernels
         umma.ok = false;
         if (umma_supported(ld, n)) {
             n_pad = (n + 63) / 64 * 64;
-            std::vector<__nv_bfloat16> ut((size_t)ld * n_pad, __float2bfloat16_rn(0.f));
+            std::vector<uint16_t> ut((size_t)ld * n_pad, 0);
             for (int i = 0; i < n; ++i)
                 for (int j = 0; j < ld; ++j) ut[(size_t)j * n_pad + i] = ub[(size_t)i * ld + j];
             Ut16.upload(ut, s);
-            umma_setup(umma, U16, Ut16, n, n_pad, ld);
+            umma_setup(umma, U16bits, Ut16, half16, n, n_pad, ld);
             umma_partial.alloc((size_t)umma_project_blocks(n) * ld * 3);
         } else {
             Ut16.release();
         }
+    } else {
+        U16bits.release();
+        Ut16.release();
+        umma.ok = false;
     }
     U32.upload(Uz, s);
     // compact copy of the leading columns for the solves with collision
     // springs: width a power of two in [8, 128] holding r_reuse columns
     ldc = 0;
+    Uc32.release();
+    Uc16bits.release();
     if (r_reuse > 0) {
         ldc = 8;
         while (ldc < r_reuse) ldc *= 2;
-        std::vector<float> Uc((size_t)n * ldc, 0.f);
-        for (int i = 0; i < n; ++i)
-            for (int j = 0; j < std::min(ldc, ld); ++j) Uc[(size_t)i * ldc + j] = Uz[(size_t)i * ld + j];
-        if (P.precision == 1) {
-            std::vector<__nv_bfloat16> ucb(Uc.size());
-            for (size_t k = 0; k < Uc.size(); ++k) ucb[k] = __float2bfloat16_rn(Uc[k]);  // exact: already rounded
-            Uc16.upload(ucb, s);
-            Uc32.release();
+        if (P.precision != 0) {
+            std::vector<uint16_t> uc((size_t)n * ldc, 0);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < std::min(ldc, ld); ++j) uc[(size_t)i * ldc + j] = ub[(size_t)i * ld + j];
+            Uc16bits.upload(uc, s);
         } else {
+            std::vector<float> Uc((size_t)n * ldc, 0.f);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < std::min(ldc, ld); ++j) Uc[(size_t)i * ldc + j] = Uz[(size_t)i * ld + j];
             Uc32.upload(Uc, s);
-            Uc16.release();
         }
     }
     std::vector<double> A0h;  // [ld][ld], zero padding rows / columns
@@ -938,23 +965,17 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
     }
     if (contacts && P.collisions) {
         bp.prof = prof.on ? &prof : nullptr;
-        CollParams cp = cparams();
-        if (log) {
-            near_cnt.alloc(1);
-            near_cnt.zero(s);
-            cp.near_count = near_cnt.p;
-        }
         PROF("partial_ccd", 0,
-             launch_partial_ccd(s, coll(), bp, Xm, Xp, cp, act, cap_act, n_act_d, &sc.p->overflow, disp));
+             launch_partial_ccd(s, coll(), bp, Xm, Xp, cparams(), act, cap_act, n_act_d, &sc.p->overflow, disp));
         if (log) {
             long long cnt[2] = {0, 0};
-            int nn = 0;
+            PccdState ps;
             bp.cnt_vt_d[bp.cur].download(&cnt[0], 1, s);
             bp.cnt_ee_d[bp.cur].download(&cnt[1], 1, s);
-            near_cnt.download(&nn, 1, s);
+            bp.pccd.download(&ps, 1, s);
             PDC_CK(cudaStreamSynchronize(s));
-            std::fprintf(stderr, "[pdc] partial ccd: pairs vt=%lld ee=%lld, past the displacement prefilter %d\n",
-                         cnt[0], cnt[1], nn);
+            std::fprintf(stderr, "[pdc] partial ccd: pairs vt=%lld ee=%lld, %s pass, watch %d, near %d\n", cnt[0],
+                         cnt[1], ps.pass_full ? "full" : "watch-list", ps.n_watch, ps.n_near);
         }
     }
 }
@@ -1233,7 +1254,7 @@ pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const 
         g_create_error = "pdc_create: empty or inconsistent mesh";
         return PDC_ERR_ARG;
     }
-    if (!(params->dt > 0) || params->precision < 0 || params->precision > 1 || params->r_warm < 0 ||
+    if (!(params->dt > 0) || params->precision < 0 || params->precision > 2 || params->r_warm < 0 ||
         params->r_reuse < 0 || params->r_reuse > 128 || params->max_outer < 0 || params->max_inner < 0 ||
         params->warm_iters < 0 || params->a_max < 0 || params->a_max > 127 ||
         !(params->samples_vt == 0 || params->samples_vt == 1 || params->samples_vt == 3) ||

@@ -9,6 +9,8 @@
 // segment is sorted by the secondary id: the pair lists come out sorted by
 // (primary, secondary) and deterministic, which lets the NDB counters of
 // one full CCD be carried to the next by binary search.
+#include <cstring>
+
 #include "pdc_collide.cuh"
 #include "pdc_scan.cuh"
 
@@ -295,6 +297,10 @@ inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 }  // namespace
 
 // ====================================================================== broad phase driver
+namespace {
+__global__ void k_pccd_force(PccdState *ps) { ps->force_full = 1; }
+}  // namespace
+
 void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee_, long long cap_ent_) {
     nt = cv.nt;
     ne = cv.ne;
@@ -349,6 +355,21 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
         cnt_vt_d[k].zero(0);
         cnt_ee_d[k].zero(0);
     }
+    reserve_pccd(cv);
+}
+
+void BroadPhase::reserve_pccd(const CollView &cv) {
+    cap_pairs = cap_vt + cap_ee;
+    near.alloc(cap_pairs);
+    watch[0].alloc(cap_pairs);
+    watch[1].alloc(cap_pairs);
+    disp0.alloc(std::max(cv.nv, 1));
+    disp0.zero(0);
+    pccd.alloc(1);
+    PccdState p0;
+    memset(&p0, 0, sizeof(p0));
+    p0.force_full = 1;
+    PDC_CK(cudaMemcpy(pccd.p, &p0, sizeof(p0), cudaMemcpyHostToDevice));
 }
 
 template <class T> static void grow_keep(DevBuf<T> &b, long long cap, cudaStream_t s) {
@@ -373,7 +394,7 @@ void BroadPhase::grow_slots(const CollView &cv, bool vt_, bool ee_) {
 }
 
 void BroadPhase::grow(const CollView &cv, long long cvt, long long cee, long long cent, cudaStream_t s) {
-    (void)cv;
+    
     if (cent > cap_ent) {
         cap_ent = cent;
         for (int k = 0; k < 2; ++k) {
@@ -396,6 +417,10 @@ void BroadPhase::grow(const CollView &cv, long long cvt, long long cee, long lon
             grow_keep(st_ee[k], cap_ee, s);
             grow_keep(d0_ee[k], cap_ee, s);
         }
+    }
+    if (cap_vt + cap_ee > cap_pairs) {
+        PDC_CK(cudaStreamSynchronize(s));
+        reserve_pccd(cv);
     }
 }
 
@@ -471,6 +496,8 @@ void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const
     }
     if (prof) prof->end(s);
     cur = nw;
+    k_pccd_force<<<1, 1, 0, s>>>(pccd);  // new lists: the next partial-CCD pass scans them all
+    PDC_LAUNCH_CK();
 }
 
 }  // namespace pdc

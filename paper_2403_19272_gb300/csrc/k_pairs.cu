@@ -391,68 +391,38 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const in
 //         side 2) cannot satisfy Q <= dhat |d0| at any sample (|d1 - d0| is
 //         bounded by those displacements), so it is set inactive without
 //         evaluating the samples.
-__global__ void __launch_bounds__(PAIR_THREADS, 3) k_pairs_update(CollView cv, const int2 *__restrict__ vt,
+// After a full CCD: store each pair's closest distance on x^- (the partial-CCD
+// filter's d0; x^- is fixed for the step) and rebuild the active list from
+// the pair states, with closest points and start directions on x^-.
+__global__ void __launch_bounds__(PAIR_THREADS) k_pairs_collect(CollView cv, const int2 *__restrict__ vt,
                                                                const int2 *__restrict__ ee, const long long *nvt_p,
-                                                               const long long *nee_p, unsigned char *st_vt,
-                                                               unsigned char *st_ee, float *d0_vt, float *d0_ee,
-                                                               const float4 *__restrict__ disp4,
-                                                               const float4 *__restrict__ xm,
-                                                               const float4 *__restrict__ xp, CollParams P, int mode,
+                                                               const long long *nee_p,
+                                                               const unsigned char *__restrict__ st_vt,
+                                                               const unsigned char *__restrict__ st_ee,
+                                                               float *d0_vt, float *d0_ee,
+                                                               const float4 *__restrict__ xm, CollParams P,
                                                                ActivePair *act, int cap, int *n_act, int *overflow) {
     long long nvt = *nvt_p, n = nvt + *nee_p;
     long long stride = (long long)gridDim.x * blockDim.x;
     long long start = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
     for (long long base = start; base < n; base += stride) {  // warp-uniform trip count
         long long idx = base + (threadIdx.x & 31);
-        bool want = false, tested = false;
+        bool want = false;
         ActivePair ap;
         if (idx < n) {
             int ids[4], kind;
             pair_ids(cv, vt, ee, nvt, idx, ids, kind);
-            unsigned char *stp = kind == 0 ? st_vt + idx : st_ee + (idx - nvt);
-            float *d0p = kind == 0 ? d0_vt + idx : d0_ee + (idx - nvt);
-            unsigned char st = *stp;
-            float c[4];
-            bool near = true;
-            if (mode == 1) {
-                // |d1 - d0| at any sample is at most the largest relative
-                // displacement between a vertex of side 1 and one of side 2
-                float4 D[4];
-                for (int q = 0; q < 4; ++q) D[q] = disp4[ids[q]];
-                float rel = 0.f;
-                int n1 = kind == 0 ? 1 : 2;
-                for (int a = 0; a < n1; ++a)
-                    for (int b = n1; b < 4; ++b) {
-                        float3 dd = make_float3(D[b].x - D[a].x, D[b].y - D[a].y, D[b].z - D[a].z);
-                        rel = fmaxf(rel, dot3(dd, dd));
-                    }
-                near = *d0p <= (P.dhat + sqrtf(rel)) * 1.001f + 1e-7f;
-                tested = near;
-            }
+            unsigned char st = kind == 0 ? st_vt[idx] : st_ee[idx - nvt];
             float4 a0[4];
-            if (near)
-                for (int i = 0; i < 4; ++i) a0[i] = xm[ids[i]];
-            if (mode == 1) {
-                bool flag = false;
-                if (near) {
-                    float4 a1[4];
-                    for (int i = 0; i < 4; ++i) a1[i] = xp[ids[i]];
-                    flag = partial_pair(kind, a0, a1, P.dhat, kind == 0 ? P.samples_vt : P.samples_ee, c);
-                }
-                if (flag) {
-                    int a = (st & ST_ACTIVE) ? min((int)(st & 0x7f) + 1, P.a_max) : 0;
-                    st = ST_ACTIVE | (unsigned char)a;
-                } else {
-                    st = 0;
-                }
-                *stp = st;
-            } else {
-                V<float> q[4];
-                for (int i = 0; i < 4; ++i) q[i] = ld<float>(a0[i]);
-                closest_coef<float>(kind, q, c);
-                V<float> d = c[0] * q[0] + c[1] * q[1] + c[2] * q[2] + c[3] * q[3];
-                *d0p = sqrtf(dotv(d, d));
-            }
+            for (int i = 0; i < 4; ++i) a0[i] = xm[ids[i]];
+            V<float> q[4];
+            for (int i = 0; i < 4; ++i) q[i] = ld<float>(a0[i]);
+            float c[4];
+            closest_coef<float>(kind, q, c);
+            V<float> d = c[0] * q[0] + c[1] * q[1] + c[2] * q[2] + c[3] * q[3];
+            float dist = sqrtf(dotv(d, d));
+            if (kind == 0) d0_vt[idx] = dist;
+            else d0_ee[idx - nvt] = dist;
             if (st & ST_ACTIVE) {
                 want = true;
                 float3 n0 = start_dir(kind, a0, c);
@@ -461,18 +431,177 @@ __global__ void __launch_bounds__(PAIR_THREADS, 3) k_pairs_update(CollView cv, c
                 ap.n0w = make_float4(n0.x, n0.y, n0.z, ndb_weight(P, st & 0x7f));
             }
         }
-        if (P.near_count) {
-            unsigned m = __ballot_sync(0xffffffffu, tested);
-            if ((threadIdx.x & 31) == 0 && m) atomicAdd(P.near_count, __popc(m));
-        }
         append_active(want, ap, act, cap, n_act, overflow);
     }
 }
 
-__global__ void k_disp(int nv, const float4 *__restrict__ a, const float4 *__restrict__ b, float4 *__restrict__ d) {
+
+// ------------------------------------------------------------------ partial-CCD filter
+// Pass structure (one partial CCD, Sec. 4.1): k_pccd_disp -> k_pccd_decide
+// -> k_pccd_filter -> k_pccd_test.  The filter applies the displacement
+// bound to every pair (full pass) or only to the watch list; the test runs
+// the sampled activity test of Eq. (query) on the near pairs only.  Pairs the
+// filter proves non-near are inactive, exactly as the test would find them.
+
+__device__ inline void warp_max_atomic(float v, unsigned int *dst) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(dst, __float_as_uint(v));
+}
+
+// disp = xp - xm; amax = max |disp - disp0| (disp0 := the previous disp when
+// the previous pass was full, i.e. the reference moves to that pass).
+__global__ void k_pccd_disp(int nv, const float4 *__restrict__ xm, const float4 *__restrict__ xp,
+                            float4 *__restrict__ disp, float4 *__restrict__ disp0, PccdState *ps) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nv) return;
-    d[i] = f4(f3(b[i]) - f3(a[i]));
+    bool moved_ref = ps->pass_full != 0;
+    float m = 0.f;
+    if (i < nv) {
+        float3 ref;
+        if (moved_ref) {
+            float4 old = disp[i];
+            disp0[i] = old;
+            ref = f3(old);
+        } else {
+            ref = f3(disp0[i]);
+        }
+        float3 d = f3(xp[i]) - f3(xm[i]);
+        disp[i] = f4(d);
+        float3 e = d - ref;
+        m = sqrtf(dot3(e, e));
+    }
+    warp_max_atomic(m, &ps->amax_bits);
+}
+
+// Finishes the previous pass (a full pass installs its watch list) and
+// decides this one; resets the per-pass counters.
+__global__ void k_pccd_decide(PccdState *ps, float tau, long long cap) {
+    PccdState p = *ps;
+    if (p.pass_full) {
+        p.cur ^= 1;
+        p.n_watch = p.n_watch_new;
+        p.watch_ok = p.n_watch_new <= cap;
+    }
+    float amax = __uint_as_float(p.amax_bits);
+    // 1% slack over the bound 2 amax < tau keeps FP32 rounding on the safe side
+    p.pass_full = (p.force_full || !p.watch_ok || !(2.f * amax < 0.99f * tau)) ? 1 : 0;
+    p.force_full = 0;
+    p.amax_bits = 0;
+    p.n_near = 0;
+    p.n_watch_new = 0;
+    *ps = p;
+}
+
+__device__ inline void warp_append_idx(bool want, int idx, int *list, int *count, long long cap, int *flag,
+                                       int flag_bit) {
+    unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) {
+        long long slot = (long long)base + __popc(m & ((1u << lane) - 1u));
+        if (slot < cap) list[slot] = idx;
+        else if (flag) atomicOr(flag, flag_bit);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pccd_filter(CollView cv, const int2 *__restrict__ vt,
+                                                     const int2 *__restrict__ ee, const long long *nvt_p,
+                                                     const long long *nee_p, unsigned char *st_vt,
+                                                     unsigned char *st_ee, const float *__restrict__ d0_vt,
+                                                     const float *__restrict__ d0_ee,
+                                                     const float4 *__restrict__ disp4, float dhat, float tau,
+                                                     PccdState *ps, int *watch0, int *watch1, int *near,
+                                                     long long cap) {
+    const bool full = ps->pass_full != 0;
+    const int cur = ps->cur;
+    const int *watch = cur ? watch1 : watch0;
+    int *watch_new = cur ? watch0 : watch1;
+    long long nvt = *nvt_p;
+    long long n = full ? nvt + *nee_p : (long long)ps->n_watch;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    long long start = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    for (long long base = start; base < n; base += stride) {  // warp-uniform trip count
+        long long t = base + (threadIdx.x & 31);
+        bool is_near = false, keep = false;
+        int idx = 0;
+        if (t < n) {
+            idx = full ? (int)t : watch[t];
+            int ids[4], kind;
+            pair_ids(cv, vt, ee, nvt, idx, ids, kind);
+            float d0 = kind == 0 ? d0_vt[idx] : d0_ee[idx - nvt];
+            // |d1 - d0| at any sample is at most the largest relative
+            // displacement between a vertex of side 1 and one of side 2
+            float4 D[4];
+            for (int q = 0; q < 4; ++q) D[q] = disp4[ids[q]];
+            float rel = 0.f;
+            int n1 = kind == 0 ? 1 : 2;
+            for (int a = 0; a < n1; ++a)
+                for (int b = n1; b < 4; ++b) {
+                    float3 dd = make_float3(D[b].x - D[a].x, D[b].y - D[a].y, D[b].z - D[a].z);
+                    rel = fmaxf(rel, dot3(dd, dd));
+                }
+            float srel = sqrtf(rel);
+            is_near = d0 <= (dhat + srel) * 1.001f + 1e-7f;
+            if (!is_near) {
+                unsigned char *stp = kind == 0 ? st_vt + idx : st_ee + (idx - nvt);
+                if (*stp) *stp = 0;
+            }
+            if (full) keep = is_near || (d0 - 1e-7f) / 1.001f - dhat - srel < tau;
+        }
+        warp_append_idx(is_near, idx, near, &ps->n_near, cap, nullptr, 0);
+        if (full) warp_append_idx(keep, idx, watch_new, &ps->n_watch_new, cap, nullptr, 0);
+    }
+}
+
+// Sampled activity test on the near pairs: state update (a + 1 while active,
+// reset when not) and the active list.
+__global__ void __launch_bounds__(256) k_pccd_test(CollView cv, const int2 *__restrict__ vt,
+                                                   const int2 *__restrict__ ee, const long long *nvt_p,
+                                                   unsigned char *st_vt, unsigned char *st_ee,
+                                                   const float4 *__restrict__ xm, const float4 *__restrict__ xp,
+                                                   CollParams P, const int *__restrict__ near,
+                                                   const PccdState *ps, long long cap, ActivePair *act,
+                                                   int cap_act, int *n_act, int *overflow) {
+    long long nvt = *nvt_p;
+    long long n = min((long long)ps->n_near, cap);
+    long long stride = (long long)gridDim.x * blockDim.x;
+    long long start = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    for (long long base = start; base < n; base += stride) {
+        long long t = base + (threadIdx.x & 31);
+        bool want = false;
+        ActivePair ap;
+        if (t < n) {
+            int idx = near[t];
+            int ids[4], kind;
+            pair_ids(cv, vt, ee, nvt, idx, ids, kind);
+            unsigned char *stp = kind == 0 ? st_vt + idx : st_ee + (idx - nvt);
+            unsigned char st = *stp;
+            float4 a0[4], a1[4];
+            for (int i = 0; i < 4; ++i) {
+                a0[i] = xm[ids[i]];
+                a1[i] = xp[ids[i]];
+            }
+            float c[4];
+            bool flag = partial_pair(kind, a0, a1, P.dhat, kind == 0 ? P.samples_vt : P.samples_ee, c);
+            if (flag) {
+                int a = (st & ST_ACTIVE) ? min((int)(st & 0x7f) + 1, P.a_max) : 0;
+                st = ST_ACTIVE | (unsigned char)a;
+            } else {
+                st = 0;
+            }
+            *stp = st;
+            if (flag) {
+                want = true;
+                float3 n0 = start_dir(kind, a0, c);
+                ap.ids = make_int4(ids[0], ids[1], ids[2], ids[3]);
+                ap.c = make_float4(c[0], c[1], c[2], c[3]);
+                ap.n0w = make_float4(n0.x, n0.y, n0.z, ndb_weight(P, st & 0x7f));
+            }
+        }
+        append_active(want, ap, act, cap_act, n_act, overflow);
+    }
 }
 
 // Collision springs (Sec. 5.1, A_i = B_i = Id): constraint C(x) = d(x).n0 - dhat
@@ -596,25 +725,35 @@ void launch_collect_active(cudaStream_t s, const CollView &cv, BroadPhase &bp, c
                            const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow) {
     int c = bp.cur;
     PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
-    k_pairs_update<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
-                                                        bp.st_vt[c], bp.st_ee[c], bp.d0_vt[c], bp.d0_ee[c], nullptr,
-                                                        xm, xm, P, 0, act, cap_act, n_act, overflow);
+    k_pairs_collect<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
+                                                         bp.st_vt[c], bp.st_ee[c], bp.d0_vt[c], bp.d0_ee[c], xm, P,
+                                                         act, cap_act, n_act, overflow);
     PDC_LAUNCH_CK();
 }
 
 void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm, const float4 *xp,
                         const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow, float4 *disp) {
     int c = bp.cur;
-    // algorithmic bytes: positions read and displacement written once per
-    // vertex; per candidate pair its key, stored distance and state byte
+    // watch gap: pairs within 2 d_hat of the near bound are re-tested every pass
+    const float tau = 2.f * P.dhat;
     if (bp.prof) bp.prof->begin(s, "pccd_prep", 40.0 * cv.nv);
     PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
-    if (cv.nv > 0) k_disp<<<(cv.nv + 255) / 256, 256, 0, s>>>(cv.nv, xm, xp, disp);
+    if (cv.nv > 0) k_pccd_disp<<<(cv.nv + 255) / 256, 256, 0, s>>>(cv.nv, xm, xp, disp, bp.disp0, bp.pccd);
+    k_pccd_decide<<<1, 1, 0, s>>>(bp.pccd, tau, bp.cap_pairs);
+    PDC_LAUNCH_CK();
     if (bp.prof) bp.prof->end(s);
-    if (bp.prof) bp.prof->begin(s, "pccd_pairs", 14.0 * (double)bp.h_pairs + 40.0 * cv.nv);
-    k_pairs_update<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
-                                                        bp.st_vt[c], bp.st_ee[c], bp.d0_vt[c], bp.d0_ee[c], disp, xm,
-                                                        xp, P, 1, act, cap_act, n_act, overflow);
+    // (full or watch-list pass is decided on the device: no byte model here)
+    if (bp.prof) bp.prof->begin(s, "pccd_filter", 0.0);
+    k_pccd_filter<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
+                                                       bp.st_vt[c], bp.st_ee[c], bp.d0_vt[c], bp.d0_ee[c], disp,
+                                                       P.dhat, tau, bp.pccd, bp.watch[0], bp.watch[1], bp.near,
+                                                       bp.cap_pairs);
+    PDC_LAUNCH_CK();
+    if (bp.prof) bp.prof->end(s);
+    if (bp.prof) bp.prof->begin(s, "pccd_test", 0.0);
+    k_pccd_test<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.st_vt[c],
+                                                     bp.st_ee[c], xm, xp, P, bp.near, bp.pccd, bp.cap_pairs, act,
+                                                     cap_act, n_act, overflow);
     PDC_LAUNCH_CK();
     if (bp.prof) bp.prof->end(s);
 }

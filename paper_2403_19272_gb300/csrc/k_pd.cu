@@ -134,10 +134,6 @@ __global__ void k_scale_disp(int n, const float4 *__restrict__ xs, const float4 
 }
 
 // r_i = m_i/h^2 (z_i - x_i) + sum_t w_t (R_t - F_t) g_{t,i} + sum_h w_h K_{h,i} (s_hat_h - s_h) + cf_i
-__device__ inline float3 dpos(const float4 *__restrict__ xs, const float4 *__restrict__ u, int a, int b) {
-    return (f3(xs[a]) - f3(xs[b])) + (f3(u[a]) - f3(u[b]));  // (x*_a - x*_b) + (u_a - u_b)
-}
-
 __global__ void __launch_bounds__(256) k_residual(const ClothView c, const float4 *__restrict__ xs,
                                                   const float4 *__restrict__ u, const float4 *__restrict__ zrel,
                                                   const float *__restrict__ cw, const float4 *__restrict__ cf,
@@ -149,36 +145,85 @@ __global__ void __launch_bounds__(256) k_residual(const ClothView c, const float
         float3 f = make_float3(0.f, 0.f, 0.f);
         if (c.is_free[i]) {
             f = c.mh2[i] * (f3(zrel[i]) - f3(u[i]));
-            for (int e = c.vt_off[i]; e < c.vt_off[i + 1]; ++e) {
-                int ent = c.vt_list[e];
-                int t = ent >> 2, corner = ent & 3;
-                int4 T = c.tri[t];
-                float4 g = c.tri_g[t];
-                float w = c.tri_w[t];
-                float3 e1 = dpos(xs, u, T.y, T.x), e2 = dpos(xs, u, T.z, T.x);
-                float3 F1 = g.x * e1 + g.z * e2;   // column 1 of F = [e1 e2] Dm^-1
-                float3 F2 = g.y * e1 + g.w * e2;   // column 2
-                float3 R1, R2;
-                polar32(F1, F2, R1, R2);
-                float gx = corner == 0 ? -(g.x + g.z) : (corner == 1 ? g.x : g.z);
-                float gy = corner == 0 ? -(g.y + g.w) : (corner == 1 ? g.y : g.w);
-                f = f + w * (gx * (R1 - F1) + gy * (R2 - F2));
+            // Incident elements are processed in groups whose loads are all
+            // issued before any result is used (three memory latencies per
+            // group: incidence entries, element data, vertex positions).
+            constexpr int GT = 2, GH = 2;
+            const int tb = c.vt_off[i], te = c.vt_off[i + 1];
+            for (int e0 = tb; e0 < te; e0 += GT) {
+                int ent[GT];
+#pragma unroll
+                for (int q = 0; q < GT; ++q) ent[q] = e0 + q < te ? __ldg(c.vt_list + e0 + q) : -1;
+                int4 T[GT];
+                float4 g[GT];
+                float w[GT];
+#pragma unroll
+                for (int q = 0; q < GT; ++q) {
+                    int t = ent[q] >= 0 ? ent[q] >> 2 : 0;
+                    T[q] = c.tri[t];
+                    g[q] = c.tri_g[t];
+                    w[q] = ent[q] >= 0 ? c.tri_w[t] : 0.f;
+                }
+                float4 P[GT][3], Q[GT][3];
+#pragma unroll
+                for (int q = 0; q < GT; ++q) {
+                    P[q][0] = xs[T[q].x]; P[q][1] = xs[T[q].y]; P[q][2] = xs[T[q].z];
+                    Q[q][0] = u[T[q].x]; Q[q][1] = u[T[q].y]; Q[q][2] = u[T[q].z];
+                }
+#pragma unroll
+                for (int q = 0; q < GT; ++q) {
+                    if (ent[q] < 0) continue;
+                    int corner = ent[q] & 3;
+                    // (x*_a - x*_b) + (u_a - u_b): exact differences of the rest part
+                    float3 e1 = (f3(P[q][1]) - f3(P[q][0])) + (f3(Q[q][1]) - f3(Q[q][0]));
+                    float3 e2 = (f3(P[q][2]) - f3(P[q][0])) + (f3(Q[q][2]) - f3(Q[q][0]));
+                    float3 F1 = g[q].x * e1 + g[q].z * e2;  // column 1 of F = [e1 e2] Dm^-1
+                    float3 F2 = g[q].y * e1 + g[q].w * e2;  // column 2
+                    float3 R1, R2;
+                    polar32(F1, F2, R1, R2);
+                    float gx = corner == 0 ? -(g[q].x + g[q].z) : (corner == 1 ? g[q].x : g[q].z);
+                    float gy = corner == 0 ? -(g[q].y + g[q].w) : (corner == 1 ? g[q].y : g[q].w);
+                    f = f + w[q] * (gx * (R1 - F1) + gy * (R2 - F2));
+                }
             }
-            for (int e = c.vh_off[i]; e < c.vh_off[i + 1]; ++e) {
-                int ent = c.vh_list[e];
-                int hh = ent >> 2, slot = ent & 3;
-                int4 Hh = c.hin[hh];
-                float4 K = c.hin_K[hh];
-                float3 s = K.y * dpos(xs, u, Hh.y, Hh.x) + K.z * dpos(xs, u, Hh.z, Hh.x) +
-                           K.w * dpos(xs, u, Hh.w, Hh.x);
-                float sl = c.hin_slen[hh];
-                float3 sh;
-                float ns = sqrtf(dot3(s, s));
-                if (sl == 0.f) sh = make_float3(0.f, 0.f, 0.f);
-                else if (ns > 1e-30f) sh = (sl / ns) * s;
-                else sh = f3(c.hin_srest[hh]);
-                float ks = slot == 0 ? K.x : (slot == 1 ? K.y : (slot == 2 ? K.z : K.w));
-                f = f + (c.hin_w[hh] * ks) * (sh - s);
+            const int hb = c.vh_off[i], he = c.vh_off[i + 1];
+            for (int e0 = hb; e0 < he; e0 += GH) {
+                int ent[GH];
+#pragma unroll
+                for (int q = 0; q < GH; ++q) ent[q] = e0 + q < he ? __ldg(c.vh_list + e0 + q) : -1;
+                int4 Hh[GH];
+                float4 K[GH];
+                float sl[GH], hw[GH];
+#pragma unroll
+                for (int q = 0; q < GH; ++q) {
+                    int hh = ent[q] >= 0 ? ent[q] >> 2 : 0;
+                    Hh[q] = c.hin[hh];
+                    K[q] = c.hin_K[hh];
+                    sl[q] = c.hin_slen[hh];
+                    hw[q] = ent[q] >= 0 ? c.hin_w[hh] : 0.f;
+                }
+                float4 P[GH][4], Q[GH][4];
+#pragma unroll
+                for (int q = 0; q < GH; ++q) {
+                    P[q][0] = xs[Hh[q].x]; P[q][1] = xs[Hh[q].y]; P[q][2] = xs[Hh[q].z]; P[q][3] = xs[Hh[q].w];
+                    Q[q][0] = u[Hh[q].x]; Q[q][1] = u[Hh[q].y]; Q[q][2] = u[Hh[q].z]; Q[q][3] = u[Hh[q].w];
+                }
+#pragma unroll
+                for (int q = 0; q < GH; ++q) {
+                    if (ent[q] < 0) continue;
+                    int slot = ent[q] & 3;
+                    float3 d1 = (f3(P[q][1]) - f3(P[q][0])) + (f3(Q[q][1]) - f3(Q[q][0]));
+                    float3 d2 = (f3(P[q][2]) - f3(P[q][0])) + (f3(Q[q][2]) - f3(Q[q][0]));
+                    float3 d3 = (f3(P[q][3]) - f3(P[q][0])) + (f3(Q[q][3]) - f3(Q[q][0]));
+                    float3 sv = K[q].y * d1 + K[q].z * d2 + K[q].w * d3;
+                    float3 sh;
+                    float ns = sqrtf(dot3(sv, sv));
+                    if (sl[q] == 0.f) sh = make_float3(0.f, 0.f, 0.f);
+                    else if (ns > 1e-30f) sh = (sl[q] / ns) * sv;
+                    else sh = f3(c.hin_srest[ent[q] >> 2]);
+                    float ks = slot == 0 ? K[q].x : (slot == 1 ? K[q].y : (slot == 2 ? K[q].z : K[q].w));
+                    f = f + (hw[q] * ks) * (sh - sv);
+                }
             }
             if (cf) f = f + f3(cf[i]);
             sq = dot3(f, f);
@@ -193,11 +238,40 @@ __global__ void __launch_bounds__(256) k_residual(const ClothView c, const float
     if (sc) block_add(sq, &sc->rsq);
 }
 
+// sum_k H_ik delta_k over the ELL off-diagonals of row i.  With WMAX > 0
+// (a bound on the row width known at compile time) all column indices and
+// values are loaded first and then all neighbour gathers are issued, so a
+// row costs two memory latencies instead of one per entry.
+template <int WMAX>
+__device__ inline float3 ell_apply(const ClothView &c, int i, const float4 *__restrict__ v) {
+    float3 acc = make_float3(0.f, 0.f, 0.f);
+    const int *col = c.ell_col + i;
+    const float *val = c.ell_val + i;
+    if constexpr (WMAX > 0) {
+        int cj[WMAX];
+        float vj[WMAX];
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) {
+            cj[k] = k < c.ell_w ? __ldg(col + (size_t)k * c.n) : i;
+            vj[k] = k < c.ell_w ? __ldg(val + (size_t)k * c.n) : 0.f;
+        }
+        float4 dj[WMAX];
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) dj[k] = v[cj[k]];
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) acc = acc + vj[k] * f3(dj[k]);
+    } else {
+        for (int k = 0; k < c.ell_w; ++k) acc = acc + val[(size_t)k * c.n] * f3(v[col[(size_t)k * c.n]]);
+    }
+    return acc;
+}
+
 // One damped Jacobi sweep on (H + diag(cw)) delta = r:
 //   delta'_i = (1 - omega) delta_i + omega (r_i - sum_{j != i} H_ij delta_j) / (H_ii + cw_i)
 // If xout is given, also writes the new iterate and reduces max |x_new - x|:
 //   x_new = x + delta'                                   (xprev == NULL), or
 //   x_new = w (x + delta' - xprev) + xprev, xprev <- x   (Chebyshev step, weight w)
+template <int WMAX>
 __global__ void __launch_bounds__(256) k_sweep(const ClothView c, const float *__restrict__ cw,
                                                const float4 *__restrict__ r, const float4 *__restrict__ din,
                                                float4 *__restrict__ dout, float omega,
@@ -209,14 +283,7 @@ __global__ void __launch_bounds__(256) k_sweep(const ClothView c, const float *_
     if (i < c.n) {
         float3 dn = make_float3(0.f, 0.f, 0.f);
         if (c.is_free[i]) {
-            float3 acc = f3(r[i]);
-            const int *col = c.ell_col + i;
-            const float *val = c.ell_val + i;
-            for (int k = 0; k < c.ell_w; ++k) {
-                float v = val[(size_t)k * c.n];
-                int j = col[(size_t)k * c.n];
-                acc = acc - v * f3(din[j]);
-            }
+            float3 acc = f3(r[i]) - ell_apply<WMAX>(c, i, din);
             float D = c.hdiag[i] + (cw ? cw[i] : 0.f);
             float3 di = f3(din[i]);
             dn = (1.f - omega) * di + (omega / D) * acc;
@@ -248,6 +315,7 @@ __global__ void __launch_bounds__(256) k_sweep(const ClothView c, const float *_
 // (alpha, beta from the Chebyshev recurrence for the interval [a, b] of the
 // spectrum of D^-1 (H + diag cw)).  The last step also writes the iterate as
 // k_sweep does.
+template <int WMAX>
 __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const float *__restrict__ cw,
                                                    const float4 *__restrict__ r, const float4 *__restrict__ din,
                                                    const float4 *__restrict__ dprev, float4 *__restrict__ dout,
@@ -262,14 +330,7 @@ __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const floa
         if (c.is_free[i]) {
             float3 di = f3(din[i]);
             float D = c.hdiag[i] + (cw ? cw[i] : 0.f);
-            float3 acc = f3(r[i]) - D * di;
-            const int *col = c.ell_col + i;
-            const float *val = c.ell_val + i;
-            for (int k = 0; k < c.ell_w; ++k) {
-                float v = val[(size_t)k * c.n];
-                int j = col[(size_t)k * c.n];
-                acc = acc - v * f3(din[j]);
-            }
+            float3 acc = f3(r[i]) - D * di - ell_apply<WMAX>(c, i, din);
             dd = (beta / D) * acc;
             if (alpha != 0.f) dd = dd + alpha * f3(dprev[i]);
             dn = di + dd;
@@ -468,17 +529,31 @@ void launch_residual(cudaStream_t s, const ClothView &c, const float4 *xs, const
 void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                   float4 *dout, float omega, const float4 *x, float4 *xout, Scalars *sc, float4 *xprev,
                   float w_acc, const float4 *xs, float4 *xabs) {
-    if (c.n > 0)
-        k_sweep<<<nblk(c.n, 256), 256, 0, s>>>(c, cw, r, din, dout, omega, x, xout, xprev, w_acc, xs, xabs, sc);
+    if (c.n > 0) {
+        int b = nblk(c.n, 256);
+        if (c.ell_w <= 8) k_sweep<8><<<b, 256, 0, s>>>(c, cw, r, din, dout, omega, x, xout, xprev, w_acc, xs, xabs, sc);
+        else if (c.ell_w <= 12)
+            k_sweep<12><<<b, 256, 0, s>>>(c, cw, r, din, dout, omega, x, xout, xprev, w_acc, xs, xabs, sc);
+        else if (c.ell_w <= 16)
+            k_sweep<16><<<b, 256, 0, s>>>(c, cw, r, din, dout, omega, x, xout, xprev, w_acc, xs, xabs, sc);
+        else k_sweep<0><<<b, 256, 0, s>>>(c, cw, r, din, dout, omega, x, xout, xprev, w_acc, xs, xabs, sc);
+    }
     PDC_LAUNCH_CK();
 }
 
 void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                       const float4 *dprev, float4 *dout, float4 *dnew, float alpha, float beta, const float4 *x,
                       float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs) {
-    if (c.n > 0)
-        k_cheb_step<<<nblk(c.n, 256), 256, 0, s>>>(c, cw, r, din, dprev, dout, dnew, alpha, beta, x, xout, xprev,
-                                                     w_acc, xs, xabs, sc);
+    if (c.n > 0) {
+        int b = nblk(c.n, 256);
+#define PDC_CHEB(W)                                                                                   \
+    k_cheb_step<W><<<b, 256, 0, s>>>(c, cw, r, din, dprev, dout, dnew, alpha, beta, x, xout, xprev, w_acc, xs, xabs, sc)
+        if (c.ell_w <= 8) PDC_CHEB(8);
+        else if (c.ell_w <= 12) PDC_CHEB(12);
+        else if (c.ell_w <= 16) PDC_CHEB(16);
+        else PDC_CHEB(0);
+#undef PDC_CHEB
+    }
     PDC_LAUNCH_CK();
 }
 

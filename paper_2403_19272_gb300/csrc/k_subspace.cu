@@ -10,6 +10,7 @@
 // by Cholesky in one CTA.  Mixed form: FP64 inverse / factorisation; plain
 // form: FP32.
 #include <algorithm>
+#include <type_traits>
 
 #include "pdc_subspace.cuh"
 
@@ -31,6 +32,7 @@ __device__ inline bool compact_active(const SubspaceView &S, const int *n_cv) {
 template <class TU> __device__ inline float tofloat(TU v);
 template <> __device__ inline float tofloat<float>(float v) { return v; }
 template <> __device__ inline float tofloat<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ inline float tofloat<__half>(__half v) { return __half2float(v); }
 
 constexpr int PROJ_T = 256;
 constexpr int PROJ_W = PROJ_T / 32;  // warps per block
@@ -43,6 +45,16 @@ __device__ inline void load8(const __nv_bfloat16 *p, float u[8]) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         float2 f = __bfloat1622float2(h[k]);
+        u[2 * k] = f.x;
+        u[2 * k + 1] = f.y;
+    }
+}
+__device__ inline void load8(const __half *p, float u[8]) {
+    uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+    const __half2 *h = reinterpret_cast<const __half2 *>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float2 f = __half22float2(h[k]);
         u[2 * k] = f.x;
         u[2 * k + 1] = f.y;
     }
@@ -495,22 +507,22 @@ template <class TU> static void lift_compact_t(cudaStream_t s, const SubspaceVie
     }
 }
 
+// Calls f with the basis of the view's element type (full or compact copy).
+template <class F> static void with_basis(const SubspaceView &S, bool compact, F f) {
+    if (S.precision == 1) f(compact ? S.Uc16 : S.U16);
+    else if (S.precision == 2) f(compact ? S.Uch : S.Uh);
+    else f(compact ? S.Uc32 : S.U32);
+}
+
 void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W,
                     bool maybe_contacts) {
     if (!maybe_contacts && S.umma && S.r_nc > 0 && S.r_nc <= S.ld) {
         launch_project_umma(s, *S.umma, S.r_nc, rl, S.umma_partial, W.g, S.dev_err);
         return;
     }
-    if (S.precision == 1)
-        project_t<__nv_bfloat16>(s, S, S.U16, rl, n_cv, W.partial);
-    else
-        project_t<float>(s, S, S.U32, rl, n_cv, W.partial);
-    if (maybe_contacts && compact_covers(S)) {
-        if (S.precision == 1)
-            project_compact_t<__nv_bfloat16>(s, S, S.Uc16, rl, n_cv, W.partial);
-        else
-            project_compact_t<float>(s, S, S.Uc32, rl, n_cv, W.partial);
-    }
+    with_basis(S, false, [&](auto *U) { project_t(s, S, U, rl, n_cv, W.partial); });
+    if (maybe_contacts && compact_covers(S))
+        with_basis(S, true, [&](auto *U) { project_compact_t(s, S, U, rl, n_cv, W.partial); });
     int mx = S.ld * 3 * 32;
     k_project_reduce<<<(mx + 255) / 256, 256, 0, s>>>(S, n_cv, PROJ_BLOCKS, W.partial, W.g);
     PDC_LAUNCH_CK();
@@ -520,23 +532,24 @@ void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const i
                  SubspaceWork &W) {
     if (S.r_c == 0) return;
     PDC_CK(cudaMemsetAsync(W.dA, 0, sizeof(float) * S.r_c * S.r_c, s));
-    if (S.precision == 1)
-        k_syrk<__nv_bfloat16><<<152, SYRK_T, 0, s>>>(S, S.U16, list, n_cv, cw, W.dA);
-    else
-        k_syrk<float><<<152, SYRK_T, 0, s>>>(S, S.U32, list, n_cv, cw, W.dA);
+    with_basis(S, false, [&](auto *U) {
+        using TU = std::remove_const_t<std::remove_pointer_t<decltype(U)>>;
+        k_syrk<TU><<<152, SYRK_T, 0, s>>>(S, U, list, n_cv, cw, W.dA);
+    });
     PDC_LAUNCH_CK();
 }
 
 void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv, SubspaceWork &W) {
+    const bool mixed = S.precision != 0;  // mixed forms: FP64 reduced solves
     if (S.r_nc > 0) {
         int thr = S.r_nc * 32;
-        if (S.precision == 1)
+        if (mixed)
             k_apply_inverse<double><<<(thr + 255) / 256, 256, 0, s>>>(S, n_cv, S.A0inv, W.g, W.q);
         else
             k_apply_inverse<float><<<(thr + 255) / 256, 256, 0, s>>>(S, n_cv, S.A0inv32, W.g, W.q);
     }
     if (S.r_c > 0) {
-        if (S.precision == 1) {
+        if (mixed) {
             size_t sm = sizeof(double) * (S.r_c * S.r_c + S.r_c * 3);
             k_chol_solve<double><<<1, 256, sm, s>>>(S, n_cv, W.dA, W.g, W.q, W.flag);
         } else {
@@ -547,30 +560,25 @@ void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv
     PDC_LAUNCH_CK();
 }
 
+template <class TU> static void lift_t(cudaStream_t s, const SubspaceView &S, const TU *U, const int *n_cv,
+                                       const float *q, const float4 *din, float4 *dout) {
+    int blocks = std::min((S.n + 7) / 8, 152 * 16);
+    if (blocks < 1) return;
+    int rmax = std::max(S.r_nc, S.r_c);
+    if (rmax <= 256) k_lift<TU, 1><<<blocks, 256, 0, s>>>(S, U, n_cv, q, din, dout);
+    else if (rmax <= 512) k_lift<TU, 2><<<blocks, 256, 0, s>>>(S, U, n_cv, q, din, dout);
+    else k_lift<TU, 4><<<blocks, 256, 0, s>>>(S, U, n_cv, q, din, dout);
+}
+
 void launch_lift(cudaStream_t s, const SubspaceView &S, const int *n_cv, const SubspaceWork &W, const float4 *din,
                  float4 *dout, bool maybe_contacts) {
     if (!maybe_contacts && S.umma && S.r_nc > 0 && S.r_nc <= S.ld) {
         launch_lift_umma(s, *S.umma, S.r_nc, W.q, din, dout, S.dev_err);
         return;
     }
-    if (maybe_contacts && compact_covers(S) && S.n > 0) {
-        if (S.precision == 1)
-            lift_compact_t<__nv_bfloat16>(s, S, S.Uc16, n_cv, W.q, din, dout);
-        else
-            lift_compact_t<float>(s, S, S.Uc32, n_cv, W.q, din, dout);
-    }
-    int blocks = std::min((S.n + 7) / 8, 152 * 16);
-    if (blocks < 1) return;
-    int rmax = std::max(S.r_nc, S.r_c);
-    if (S.precision == 1) {
-        if (rmax <= 256) k_lift<__nv_bfloat16, 1><<<blocks, 256, 0, s>>>(S, S.U16, n_cv, W.q, din, dout);
-        else if (rmax <= 512) k_lift<__nv_bfloat16, 2><<<blocks, 256, 0, s>>>(S, S.U16, n_cv, W.q, din, dout);
-        else k_lift<__nv_bfloat16, 4><<<blocks, 256, 0, s>>>(S, S.U16, n_cv, W.q, din, dout);
-    } else {
-        if (rmax <= 256) k_lift<float, 1><<<blocks, 256, 0, s>>>(S, S.U32, n_cv, W.q, din, dout);
-        else if (rmax <= 512) k_lift<float, 2><<<blocks, 256, 0, s>>>(S, S.U32, n_cv, W.q, din, dout);
-        else k_lift<float, 4><<<blocks, 256, 0, s>>>(S, S.U32, n_cv, W.q, din, dout);
-    }
+    if (maybe_contacts && compact_covers(S) && S.n > 0)
+        with_basis(S, true, [&](auto *U) { lift_compact_t(s, S, U, n_cv, W.q, din, dout); });
+    with_basis(S, false, [&](auto *U) { lift_t(s, S, U, n_cv, W.q, din, dout); });
     PDC_LAUNCH_CK();
 }
 

@@ -23,7 +23,6 @@ struct CollParams {
     int a_max;        // cap of the life-span counter
     int samples_vt;   // 0, 1, 3
     int samples_ee;   // 0, 1, 4
-    int *near_count = nullptr;  // optional: pairs passing the partial-CCD displacement prefilter
 };
 
 // An active collision constraint: 4 collision-vertex ids, the gap-vector
@@ -37,6 +36,24 @@ struct ActivePair {
 
 // Pair state byte: bit 7 = active, bits 0..6 = life-span counter a.
 constexpr unsigned char ST_ACTIVE = 0x80;
+
+// Bookkeeping of the partial-CCD filter (device).  A pair can pass the
+// activity test only if its start distance d0 is within d_hat plus the
+// largest relative displacement of its vertices since x^- ("near").  A full
+// pass over the list measures each pair's margin to that bound; pairs whose
+// margin exceeds the watch gap tau stay non-near until some vertex has moved
+// by more than tau/2 since that pass, so until then only the watch list
+// (margin < tau) is scanned.
+struct PccdState {
+    unsigned int amax_bits;  // max_v |disp_v - disp0_v| since the last full pass (float bits)
+    int n_near;              // near pairs found by this pass
+    int n_watch_new;         // watch list being written by this (full) pass
+    int pass_full;           // this pass scans every pair
+    int force_full;          // the lists changed: the next pass must be full
+    int watch_ok;            // the current watch list is complete
+    int n_watch;             // current watch list length
+    int cur;                 // which watch buffer is current
+};
 
 struct BroadPhase {
     int nt = 0, ne = 0, nv = 0;
@@ -61,6 +78,13 @@ struct BroadPhase {
     int cur = 0;
     Profiler *prof = nullptr;  // optional sub-kernel timing
     long long h_pairs = 0;     // host copy of the current list size (kept while profiling)
+    // partial-CCD filter: near list, double-buffered watch list, reference
+    // displacement of the last full pass, bookkeeping
+    long long cap_pairs = 0;
+    DevBuf<int> near, watch[2];
+    DevBuf<float4> disp0;
+    DevBuf<PccdState> pccd;
+    void reserve_pccd(const CollView &cv);
 
     void reserve(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent);
     // larger capacities keeping the current candidate lists, states and counts

@@ -14,16 +14,18 @@ struct SubspaceView {
     int ld;                    // row stride of U (r_warm)
     int r_nc, r_c;             // columns used without / with collision springs
     const float *U32;          // [n][ld] FP32 basis (plain form)
-    const __nv_bfloat16 *U16;  // [n][ld] BF16 basis (mixed form)
+    const __nv_bfloat16 *U16;  // [n][ld] BF16 basis (mixed form, precision 1)
+    const __half *Uh;          // [n][ld] FP16 basis, power-of-two scaled (mixed form, precision 2)
     const double *A0;          // [ld][ld] U^T H U of the stored basis
     const double *A0inv;       // [r_nc][r_nc] inverse (FP64)
     const float *A0inv32;      // [r_nc][r_nc] inverse (FP32)
-    int precision;             // 0 plain FP32, 1 mixed
+    int precision;             // 0 plain FP32, 1 mixed BF16, 2 mixed FP16
     // compact copy of the leading ldc columns ([n][ldc], same values as U):
     // the solves with collision springs stream only these
     int ldc;                   // 0: no compact copy
     const float *Uc32;
     const __nv_bfloat16 *Uc16;
+    const __half *Uch;
     // tensor-core path of the full-basis solves (host pointer; NULL: off)
     const UmmaMaps *umma;
     float *umma_partial;       // [tiles][ld][3]

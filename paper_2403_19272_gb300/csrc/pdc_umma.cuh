@@ -14,17 +14,20 @@ constexpr int UMMA_MAX_LD = 256;
 // of a tensor-core kernel ran out.
 constexpr int PDC_DEVERR_UMMA = 2;
 
-// TMA descriptors of the BF16 basis U [n][ld] and of its transpose
-// Ut [ld][n_pad].
+// TMA descriptors of the 16-bit basis U [n][ld] (BF16 or FP16) and of its
+// transpose Ut [ld][n_pad].
 struct UmmaMaps {
     CUtensorMap mapU;
     CUtensorMap mapUt;
     int n = 0, ld = 0;
+    bool f16 = false;  // FP16 (scaled) basis instead of BF16
+    bool persistent = true;  // one pipelined CTA per SM (else one CTA per tile)
+    int sms = 1;
     bool ok = false;
 };
 
 bool umma_supported(int ld, int n);
-void umma_setup(UmmaMaps &M, const __nv_bfloat16 *U, const __nv_bfloat16 *Ut, int n, int n_pad, int ld);
+void umma_setup(UmmaMaps &M, const void *U, const void *Ut, bool f16, int n, int n_pad, int ld);
 int umma_project_blocks(int n);
 // g = U[:, :r]^T rl via per-tile partial sums [blocks][ld][3] and an FP64 reduction.
 void launch_project_umma(cudaStream_t s, const UmmaMaps &M, int r, const float4 *rl, float *partial, double *g,

@@ -64,7 +64,7 @@ def _check_lift(pc, cl, Ug, rng, r):
     return out
 
 
-@pytest.mark.parametrize("precision,tensor_cores", [(1, 1), (1, 0), (0, 0)])
+@pytest.mark.parametrize("precision,tensor_cores", [(1, 1), (1, 0), (2, 1), (2, 0), (0, 0)])
 @pytest.mark.parametrize("r", [256, 128])
 def test_project_and_lift_ragged_tiles(pc, precision, tensor_cores, r):
     # 40 x 40 = 1600 rows: 12 full 128-row tiles and a ragged tail
@@ -74,10 +74,11 @@ def test_project_and_lift_ragged_tiles(pc, precision, tensor_cores, r):
     cl.close()
 
 
-def test_tensor_core_and_cuda_core_paths_agree(pc):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_tensor_core_and_cuda_core_paths_agree(pc, precision):
     outs = []
     for tc in (1, 0):
-        sc, cl, Ug, rng = _cloth(pc, 33, 256, 1, tc, 77)
+        sc, cl, Ug, rng = _cloth(pc, 33, 256, precision, tc, 77)
         v = np.random.default_rng(5).standard_normal((sc.n, 3)).astype(np.float32)
         q = np.random.default_rng(6).standard_normal((256, 3))
         outs.append((pc.pdc_op_project(cl.h, v, 256), pc.pdc_op_lift(cl.h, sc.n, q, 256)))
@@ -87,9 +88,10 @@ def test_tensor_core_and_cuda_core_paths_agree(pc):
     assert np.max(np.abs(l1 - l0)) <= 1e-4 * np.max(np.abs(l0))
 
 
-def test_project_and_lift_full_size_512(pc):
-    # the benchmark's configuration: n = 262,144, r = 256, BF16 basis on the tensor cores
-    sc, cl, Ug, rng = _cloth(pc, 512, 256, 1, 1, 99)
+@pytest.mark.parametrize("precision", [1, 2])
+def test_project_and_lift_full_size_512(pc, precision):
+    # the benchmark's configuration: n = 262,144, r = 256, 16-bit basis on the tensor cores
+    sc, cl, Ug, rng = _cloth(pc, 512, 256, precision, 1, 99)
     _check_project(pc, cl, Ug, rng, 256)
     _check_lift(pc, cl, Ug, rng, 256)
     cl.close()
