@@ -42,6 +42,8 @@ def parse():
                     help="comma list of mixed16 (FP16 basis), mixed (BF16 basis), fp32; the first is the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-side", type=int, default=64)
+    ap.add_argument("--sweeps", type=int, default=32, help="Chebyshev steps per LG iteration")
+    ap.add_argument("--cheb-ratio", type=float, default=1000.0, help="Chebyshev interval ratio b/a")
     ap.add_argument("--no-launch-count", action="store_true",
                     help="skip the CUDA activity trace (e.g. when running under ncu)")
     return ap.parse_args()
@@ -52,7 +54,7 @@ FORMS = {"mixed16": 2, "mixed": 1, "fp32": 0}
 DTYPES = {"mixed16": "f16+f32+f64", "mixed": "bf16+f32+f64", "fp32": "f32"}
 
 
-def solver_params(pc, precision):
+def solver_params(pc, precision, sweeps=32, cheb_ratio=1000.0):
     p = pc.pdc_default_params()
     p.tol_rel_residual = 1e-3
     p.max_outer = 2
@@ -62,13 +64,31 @@ def solver_params(pc, precision):
     p.r_reuse = 32
     p.precision = precision
     p.sweep_kind = 1        # Jacobi-preconditioned Chebyshev iteration for the sweeps
-    p.jacobi_sweeps = 32
-    p.cheb_ratio = 1000.0
+    p.jacobi_sweeps = sweeps
+    p.cheb_ratio = cheb_ratio
     p.accel = 2             # Anderson mixing of the LG iterates
     p.aa_depth = 6
     p.solve_cycles = 1
     p.eig_iters = 12
     return p
+
+
+def max_over_ranks(value, device=None):
+    """Largest value over the ranks of the default process group (the value
+    itself on one rank); the timing of a multi-rank run is the slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
 
 
 def peaks():
@@ -123,11 +143,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True):
+def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True, sweeps=32, cheb_ratio=1000.0):
     """Warm-up, timed region (device), profiled replay, e2e through host buffers."""
     import numpy as np
     stream = torch.cuda.Stream()
-    p = solver_params(pc, precision)
+    p = solver_params(pc, precision, sweeps, cheb_ratio)
     t_setup = time.time()
     h = pc.pdc_create(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend, p,
                       stream.cuda_stream)
@@ -165,7 +185,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
     time.sleep(0.3)
     st_list = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches0 = None
+    barrier()
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(steps):
@@ -173,6 +193,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
         st_list.append(pc.pdc_get_stats(h))
     e1.record(stream)
     torch.cuda.synchronize()
+    barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     # ---- profiled replay of the same steps (per-kernel event timing)
@@ -327,14 +348,10 @@ def main():
     forms = {}
     for f in a.forms.split(","):
         forms[f] = run_form(pc, torch, scene, FORMS[f], a.steps, a.warmup, local,
-                            not a.no_launch_count)
+                            not a.no_launch_count, a.sweeps, a.cheb_ratio)
     head = list(forms)[0]
     ms = forms[head]["ms"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, f"cuda:{local}")
     if rank != 0:
         return
     pk = peaks()

@@ -238,28 +238,18 @@ __global__ void __launch_bounds__(256) k_residual(const ClothView c, const float
     if (sc) block_add(sq, &sc->rsq);
 }
 
-// sum_k H_ik delta_k over the ELL off-diagonals of row i.  With WMAX > 0
-// (a bound on the row width known at compile time) all column indices and
-// values are loaded first and then all neighbour gathers are issued, so a
-// row costs two memory latencies instead of one per entry.
+// sum_k H_ik delta_k over the ELL off-diagonals of row i; with WMAX > 0 (a
+// compile-time bound on the row width) the loop is unrolled so that the
+// loads of all entries are in flight together.
 template <int WMAX>
 __device__ inline float3 ell_apply(const ClothView &c, int i, const float4 *__restrict__ v) {
     float3 acc = make_float3(0.f, 0.f, 0.f);
     const int *col = c.ell_col + i;
     const float *val = c.ell_val + i;
     if constexpr (WMAX > 0) {
-        int cj[WMAX];
-        float vj[WMAX];
 #pragma unroll
-        for (int k = 0; k < WMAX; ++k) {
-            cj[k] = k < c.ell_w ? __ldg(col + (size_t)k * c.n) : i;
-            vj[k] = k < c.ell_w ? __ldg(val + (size_t)k * c.n) : 0.f;
-        }
-        float4 dj[WMAX];
-#pragma unroll
-        for (int k = 0; k < WMAX; ++k) dj[k] = v[cj[k]];
-#pragma unroll
-        for (int k = 0; k < WMAX; ++k) acc = acc + vj[k] * f3(dj[k]);
+        for (int k = 0; k < WMAX; ++k)
+            if (k < c.ell_w) acc = acc + __ldg(val + (size_t)k * c.n) * f3(v[__ldg(col + (size_t)k * c.n)]);
     } else {
         for (int k = 0; k < c.ell_w; ++k) acc = acc + val[(size_t)k * c.n] * f3(v[col[(size_t)k * c.n]]);
     }

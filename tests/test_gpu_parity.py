@@ -198,6 +198,24 @@ def test_residual_parity_force_form(pc):
     cl.close()
 
 
+def test_residual_parity_full_size_512(pc):
+    # the benchmark's cloth (262,144 vertices, 522,242 triangles, 782,341
+    # hinges) in the launch configuration of the step; every entry compared
+    rng = np.random.default_rng(28)
+    sc = wl.hanging_swept(side=512)
+    cl = pc.Cloth(sc, params(pc, r_warm=0))
+    m = pd.Model(sc.verts, sc.tris, sc.pins, sc.density, sc.k_stretch, sc.k_bend, 0.005)
+    x = (m.X + rng.normal(size=m.X.shape) * 5e-4).astype(np.float32)
+    z = (m.X + rng.normal(size=m.X.shape) * 2e-4).astype(np.float32)
+    rg = pc.pdc_op_residual(cl.h, x, z)
+    ro = -m.residual(x.astype(np.float64), z.astype(np.float64))
+    full = np.zeros((m.n, 3))
+    full[m.free] = ro
+    scale = np.max(np.abs(full))
+    assert np.max(np.abs(rg - full)) <= 1e-4 * scale
+    cl.close()
+
+
 def test_contact_springs_parity(pc):
     rng = np.random.default_rng(26)
     sc = wl.drape_sphere(side=16, sphere_subdiv=2)
