@@ -122,6 +122,12 @@ typedef struct {
                                 lift on the tcgen05 tensor cores (BF16 basis, FP32
                                 operand split into two BF16 parts, FP32
                                 accumulation); 0 uses the CUDA-core kernels      */
+    double bp_reuse;         /* > 0: the first broad phase of a step runs with the
+                                gap d_hat + 2 mu, mu = bp_reuse * d_hat, and later
+                                full CCDs of the step filter its candidate list
+                                (same pairs, same order as a fresh pass) while
+                                every vertex stays within 0.9 mu of its swept box;
+                                0 (default): a hash pass for every full CCD     */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
@@ -137,6 +143,8 @@ typedef struct {
     double rel_residual;         /* last measured residual / rho0                 */
     double ms_step, ms_broad, ms_narrow, ms_lg; /* host wall time per phase (ms) */
     int32_t overflow_retries;    /* buffer regrowths during this step            */
+    int32_t bp_reused;           /* full CCDs whose candidates were filtered from
+                                    the step's first broad phase (bp_reuse)      */
 } pdc_stats;
 
 /* Defaults: dt 1/200, g = (0,0,-9.8), K = 2, a_max 20, alpha 0.8, automatic
@@ -151,6 +159,21 @@ void pdc_default_params(pdc_params *p);
  * stream: a cudaStream_t or NULL. */
 pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const pdc_params *params,
                       void *stream, pdc_handle *out);
+
+/* Batched form: `count` independent cloths (meshes[k] with materials[k];
+ * host arrays, copied) advanced together as one system, so that every kernel
+ * of a step is one launch over all instances, whatever their sizes.  The
+ * union's vertices are numbered instance after instance (instance k starts
+ * at the sum of the vertex counts of instances 0..k-1); positions, pins,
+ * states and obstacles use that numbering, and every other call applies to
+ * the union unchanged.  Readings of the batched form: the iteration stops
+ * when the union meets the convergence test, the line search takes one step
+ * fraction for all instances (an impact in one shortens every instance's
+ * step), and the basis is built for the union's block-diagonal matrix.
+ * Place instances apart: a collision pair spanning two instances is handled
+ * like any other.  Errors as pdc_create. */
+pdc_status pdc_create_batch(int32_t count, const pdc_mesh_desc *meshes, const pdc_material *materials,
+                            const pdc_params *params, void *stream, pdc_handle *out);
 
 /* Add a kinematic (infinite-mass) triangle obstacle; host arrays copied.
  * Must be called before the first pdc_step.  Its current and target

@@ -189,6 +189,11 @@ struct pdc_ctx {
     cudaStream_t s = nullptr;
     pdc_params P;
     pdc_material M;
+    // batched form: material of each instance and the instance of each triangle
+    // (empty: one cloth with material M)
+    std::vector<pdc_material> mats;
+    std::vector<int> tri_inst;
+    const pdc_material &mat(int t) const { return tri_inst.empty() ? M : mats[tri_inst[t]]; }
     int n = 0, m = 0, nh = 0, npins = 0;
     std::vector<float> X;
     std::vector<int> T, pins;
@@ -250,7 +255,8 @@ struct pdc_ctx {
     float last_dx = 0.f;
     DevBuf<float4> Xacc;  // previous iterate for the accelerated update
     DevBuf<float4> disp;  // x^+ - x^- per collision vertex
-    DevBuf<float4> CD0, CD1;  // Chebyshev directions
+    DevBuf<float4> CD0;  // third Chebyshev iterate (delta_{k-1})
+    DevBuf<float4> corner;  // per-element corner forces of the residual [3m + 4nh]
     DevBuf<float4> aa_dF, aa_dG, aa_f, aa_g;  // Anderson history
     DevBuf<double> aa_Gb;
     DevBuf<float> aa_theta;
@@ -285,6 +291,7 @@ struct pdc_ctx {
         c.ell_w = ell_w;
         c.ell_col = ell_col;
         c.ell_val = ell_val;
+        c.corner = corner;
         return c;
     }
     CollView coll() const {
@@ -362,6 +369,7 @@ struct pdc_ctx {
     void lg_iteration(bool contacts, bool check_rel, double rho0, bool &converged, int r_nc, int r_c, int cycles,
                       int sweeps);
     void full_ccd(const float4 *x0, const float4 *x1, bool merge);
+    void broad_phase_pass(const float4 *x0, const float4 *x1, bool super);
     void step();
 };
 
@@ -421,8 +429,8 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
         G[t] = {-(i00 + i10), -(i01 + i11), i00, i01, i10, i11};
         tri_h[t] = make_int4(a, b, c, 0);
         trig_h[t] = make_float4((float)i00, (float)i01, (float)i10, (float)i11);
-        triw_h[t] = (float)(M.k_stretch * area[t]);
-        for (int k = 0; k < 3; ++k) mass[T[3 * t + k]] += M.density * area[t] / 3.0;
+        triw_h[t] = (float)(mat(t).k_stretch * area[t]);
+        for (int k = 0; k < 3; ++k) mass[T[3 * t + k]] += mat(t).density * area[t] / 3.0;
     }
 
     // ---- edges -> hinges
@@ -453,7 +461,7 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
         };
         double cA0 = cotv(x0, x1, x2), cA1 = cotv(x1, x0, x2), cB0 = cotv(x0, x1, x3), cB1 = cotv(x1, x0, x3);
         std::array<double, 4> K = {cA1 + cB1, cA0 + cB0, -cA0 - cA1, -cB0 - cB1};
-        double w = 3.0 * M.k_bend / (area[kv.second[0].first] + area[kv.second[1].first]);
+        double w = 3.0 * mat(kv.second[0].first).k_bend / (area[kv.second[0].first] + area[kv.second[1].first]);
         int ids[4] = {x0, x1, x2, x3};
         double s[3] = {0, 0, 0};
         for (int j = 0; j < 4; ++j)
@@ -468,12 +476,13 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
         wd.push_back(w);
     }
     nh = (int)hin_h.size();
+    corner.alloc(std::max<size_t>(3 * (size_t)m + 4 * (size_t)nh, 1));
 
     // ---- H = M/h^2 + sum_t w_t G G^T + sum_h w_h K K^T  (scalar, per vertex pair)
     std::vector<std::unordered_map<int, double>> rows(n);
     for (int i = 0; i < n; ++i) rows[i][i] += mass[i] / (h * h);
     for (int t = 0; t < m; ++t) {
-        double w = M.k_stretch * area[t];
+        double w = mat(t).k_stretch * area[t];
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) {
                 double v = w * (G[t][2 * a] * G[t][2 * b] + G[t][2 * a + 1] * G[t][2 * b + 1]);
@@ -621,7 +630,7 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
     Um.alloc(n);
     if (P.sweep_kind == 1) {
         CD0.alloc(n);
-        CD1.alloc(n);
+
     }
     if (P.accel == 2) {
         int m = std::min(std::max(P.aa_depth, 1), 8);
@@ -916,7 +925,7 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             double b = std::max(gersh, 1.0) * 1.02, a = b / std::max(P.cheb_ratio, 1.0001);
             double theta = 0.5 * (b + a), dl = 0.5 * (b - a), sig = theta / dl;
             double rho_prev = 1.0 / sig;
-            float4 *dp = CD0, *dq = CD1;
+            float4 *dp = CD0;  // delta_{k-1}; din = delta_k, dout = delta_{k+1}
             for (int k = 0; k < sweeps; ++k) {
                 bool last = (cyc == cycles - 1) && (k == sweeps - 1);
                 double alpha, beta;
@@ -929,12 +938,14 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
                     beta = 2.0 * rk / dl;
                     rho_prev = rk;
                 }
-                PROF("cheb_sweep", bytes_sweep(contacts, last) + 24.0 * n,
-                     launch_cheb_step(s, c, cw, R, din, dp, dout, dq, (float)alpha, (float)beta, Ucur,
+                PROF("cheb_sweep", bytes_sweep(contacts, last) + 12.0 * n,
+                     launch_cheb_step(s, c, cw, R, din, dp, dout, (float)alpha, (float)beta, Ucur,
                                       last ? Ucur.p : nullptr, last ? sc.p : nullptr, last ? xprev : nullptr, w_acc,
                                       Xs, last ? Xp.p : nullptr));
-                std::swap(din, dout);
-                std::swap(dp, dq);
+                float4 *t = dp;  // rotate: delta_{k-1} <- delta_k <- delta_{k+1}
+                dp = din;
+                din = dout;
+                dout = t;
             }
         } else {
             for (int k = 0; k < sweeps; ++k) {
@@ -982,27 +993,12 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
 
 void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {
     bp.prof = prof.on ? &prof : nullptr;
-    // broad phase; a list or table that overflows is regrown and rebuilt here
-    // (candidate sets spike while the iterate is far from converged), so the
-    // step itself need not be redone
-    for (int tries = 0;; ++tries) {
-        int cur0 = bp.cur;
-        bp_ovf.zero(s);
-        PROF("broad_phase", 0, bp.run(s, coll(), x0, x1, dhat, bp_ovf));
-        int ovf = 0;
-        bp_ovf.download(&ovf, 1, s);
-        PDC_CK(cudaStreamSynchronize(s));
-        if (!ovf) break;
-        if (tries >= 6) throw Error(PDC_ERR_CAPACITY, "broad phase buffers could not be grown enough");
-        bp.cur = cur0;  // the previous lists stay the merge source of the rebuilt ones
-        long long cvt = bp.cap_vt * ((ovf & OVF_VT) ? 2 : 1), cee = bp.cap_ee * ((ovf & OVF_EE) ? 2 : 1),
-                  cent = bp.cap_ent * ((ovf & OVF_HASH) ? 2 : 1);
-        if (ovf & OVF_CELLS) bp.cell_scale *= 4.f;
-        if (ovf & OVF_SLOTS) bp.grow_slots(coll(), true, true);
-        bp.grow(coll(), cvt, cee, cent, s);  // keeps the current lists (NDB states merge from them)
-        st.overflow_retries++;
-        if (log) std::fprintf(stderr, "[pdc] broad phase regrown after overflow 0x%x\n", ovf);
-    }
+    const bool reuse = P.bp_reuse > 0;
+    if (reuse && merge && bp.can_reuse(s, coll(), x0, x1)) {
+        PROF("broad_phase", 0, bp.filter(s, coll(), x0, x1, dhat));
+        st.bp_reused++;
+    } else
+        broad_phase_pass(x0, x1, reuse);
     if (prof.on) {  // list size for the byte models of the pair kernels
         long long cnt[2] = {0, 0};
         bp.cnt_vt_d[bp.cur].download(&cnt[0], 1, s);
@@ -1018,6 +1014,33 @@ void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {
          launch_full_ccd(s, coll(), bp, x0, x1, cparams(), merge, toi_bits));
     k_step_fraction<<<1, 1, 0, s>>>(toi_bits, P.alpha_ls, sfrac, ttoi);
     PDC_LAUNCH_CK();
+}
+
+void pdc_ctx::broad_phase_pass(const float4 *x0, const float4 *x1, bool super) {
+    // broad phase; a list or table that overflows is regrown and rebuilt here
+    // (candidate sets spike while the iterate is far from converged), so the
+    // step itself need not be redone
+    for (int tries = 0;; ++tries) {
+        int cur0 = bp.cur;
+        bp_ovf.zero(s);
+        if (super)
+            PROF("broad_phase", 0, bp.run_super(s, coll(), x0, x1, dhat, (float)(P.bp_reuse * dhat), bp_ovf));
+        else
+            PROF("broad_phase", 0, bp.run(s, coll(), x0, x1, dhat, bp_ovf));
+        int ovf = 0;
+        bp_ovf.download(&ovf, 1, s);
+        PDC_CK(cudaStreamSynchronize(s));
+        if (!ovf) break;
+        if (tries >= 6) throw Error(PDC_ERR_CAPACITY, "broad phase buffers could not be grown enough");
+        bp.cur = cur0;  // the previous lists stay the merge source of the rebuilt ones
+        long long cvt = bp.cap_vt * ((ovf & OVF_VT) ? 2 : 1), cee = bp.cap_ee * ((ovf & OVF_EE) ? 2 : 1),
+                  cent = bp.cap_ent * ((ovf & OVF_HASH) ? 2 : 1);
+        if (ovf & OVF_CELLS) bp.cell_scale *= 4.f;
+        if (ovf & OVF_SLOTS) bp.grow_slots(coll(), true, true);
+        bp.grow(coll(), cvt, cee, cent, s);  // keeps the current lists (NDB states merge from them)
+        st.overflow_retries++;
+        if (log) std::fprintf(stderr, "[pdc] broad phase regrown after overflow 0x%x\n", ovf);
+    }
 }
 
 void pdc_ctx::step() {
@@ -1240,33 +1263,28 @@ void pdc_default_params(pdc_params *p) {
     p->cheb_ratio = 100.0;
     p->aa_depth = 6;
     p->tensor_cores = 1;
+    p->bp_reuse = 0.0;
 }
 
-pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const pdc_params *params, void *stream,
-                      pdc_handle *out) {
-    if (!out || !mesh || !mat || !params) {
-        g_create_error = "pdc_create: NULL argument";
-        return PDC_ERR_ARG;
-    }
-    *out = nullptr;
-    if (mesh->nv <= 0 || mesh->nt <= 0 || !mesh->verts || !mesh->tris || mesh->npins < 0 ||
-        (mesh->npins > 0 && !mesh->pins)) {
-        g_create_error = "pdc_create: empty or inconsistent mesh";
-        return PDC_ERR_ARG;
-    }
-    if (!(params->dt > 0) || params->precision < 0 || params->precision > 2 || params->r_warm < 0 ||
-        params->r_reuse < 0 || params->r_reuse > 128 || params->max_outer < 0 || params->max_inner < 0 ||
-        params->warm_iters < 0 || params->a_max < 0 || params->a_max > 127 ||
-        !(params->samples_vt == 0 || params->samples_vt == 1 || params->samples_vt == 3) ||
-        !(params->samples_ee == 0 || params->samples_ee == 1 || params->samples_ee == 4) ||
-        params->sweep_kind < 0 || params->sweep_kind > 1 || (params->sweep_kind == 1 && !(params->cheb_ratio > 1.0)) ||
-        params->accel < 0 || params->accel > 2 || (params->accel == 2 && (params->aa_depth < 1 || params->aa_depth > 8))) {
-        g_create_error = "pdc_create: invalid parameters";
-        return PDC_ERR_ARG;
-    }
-    std::unique_ptr<pdc_ctx> c(new pdc_ctx());
+static bool params_valid(const pdc_params *params) {
+    return params->dt > 0 && params->precision >= 0 && params->precision <= 2 && params->r_warm >= 0 &&
+           params->r_reuse >= 0 && params->r_reuse <= 128 && params->max_outer >= 0 && params->max_inner >= 0 &&
+           params->warm_iters >= 0 && params->a_max >= 0 && params->a_max <= 127 &&
+           (params->samples_vt == 0 || params->samples_vt == 1 || params->samples_vt == 3) &&
+           (params->samples_ee == 0 || params->samples_ee == 1 || params->samples_ee == 4) &&
+           params->sweep_kind >= 0 && params->sweep_kind <= 1 && (params->sweep_kind != 1 || params->cheb_ratio > 1.0) &&
+           params->accel >= 0 && params->accel <= 2 && (params->accel != 2 || (params->aa_depth >= 1 && params->aa_depth <= 8));
+}
+
+static bool mesh_valid(const pdc_mesh_desc *mesh) {
+    return mesh->nv > 0 && mesh->nt > 0 && mesh->verts && mesh->tris && mesh->npins >= 0 &&
+           (mesh->npins == 0 || mesh->pins);
+}
+
+// Builds the context for one mesh; batch material tables are filled by the caller.
+static pdc_status create_ctx(std::unique_ptr<pdc_ctx> &c, const pdc_mesh_desc *mesh, const pdc_params *params,
+                             void *stream, pdc_handle *out) {
     c->P = *params;
-    c->M = *mat;
     c->s = (cudaStream_t)stream;
     try {
         set_chol_smem_limits();
@@ -1281,6 +1299,83 @@ pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const 
     }
     *out = c.release();
     return PDC_OK;
+}
+
+pdc_status pdc_create(const pdc_mesh_desc *mesh, const pdc_material *mat, const pdc_params *params, void *stream,
+                      pdc_handle *out) {
+    if (!out || !mesh || !mat || !params) {
+        g_create_error = "pdc_create: NULL argument";
+        return PDC_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!mesh_valid(mesh)) {
+        g_create_error = "pdc_create: empty or inconsistent mesh";
+        return PDC_ERR_ARG;
+    }
+    if (!params_valid(params)) {
+        g_create_error = "pdc_create: invalid parameters";
+        return PDC_ERR_ARG;
+    }
+    std::unique_ptr<pdc_ctx> c(new pdc_ctx());
+    c->M = *mat;
+    return create_ctx(c, mesh, params, stream, out);
+}
+
+pdc_status pdc_create_batch(int32_t count, const pdc_mesh_desc *meshes, const pdc_material *materials,
+                            const pdc_params *params, void *stream, pdc_handle *out) {
+    if (!out || !meshes || !materials || !params || count <= 0) {
+        g_create_error = "pdc_create_batch: NULL argument or empty batch";
+        return PDC_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!params_valid(params)) {
+        g_create_error = "pdc_create_batch: invalid parameters";
+        return PDC_ERR_ARG;
+    }
+    // the union mesh: instance k's vertices, triangles and pins follow those of
+    // instances 0..k-1, its ids shifted by their vertex count
+    std::vector<float> V;
+    std::vector<int32_t> Tr, Pn;
+    std::unique_ptr<pdc_ctx> c(new pdc_ctx());
+    long long nv = 0;
+    for (int k = 0; k < count; ++k) {
+        const pdc_mesh_desc &m = meshes[k];
+        if (!mesh_valid(&m)) {
+            g_create_error = "pdc_create_batch: empty or inconsistent mesh " + std::to_string(k);
+            return PDC_ERR_ARG;
+        }
+        if (nv + m.nv > (1LL << 30)) {
+            g_create_error = "pdc_create_batch: too many vertices";
+            return PDC_ERR_ARG;
+        }
+        V.insert(V.end(), m.verts, m.verts + 3 * (size_t)m.nv);
+        for (int t = 0; t < 3 * m.nt; ++t) {
+            if (m.tris[t] < 0 || m.tris[t] >= m.nv) {
+                g_create_error = "pdc_create_batch: triangle index out of range in mesh " + std::to_string(k);
+                return PDC_ERR_ARG;
+            }
+            Tr.push_back((int32_t)(m.tris[t] + nv));
+        }
+        for (int p = 0; p < m.npins; ++p) {
+            if (m.pins[p] < 0 || m.pins[p] >= m.nv) {
+                g_create_error = "pdc_create_batch: pin index out of range in mesh " + std::to_string(k);
+                return PDC_ERR_ARG;
+            }
+            Pn.push_back((int32_t)(m.pins[p] + nv));
+        }
+        c->mats.push_back(materials[k]);
+        c->tri_inst.insert(c->tri_inst.end(), (size_t)m.nt, k);
+        nv += m.nv;
+    }
+    c->M = materials[0];
+    pdc_mesh_desc u;
+    u.verts = V.data();
+    u.nv = (int32_t)nv;
+    u.tris = Tr.data();
+    u.nt = (int32_t)(Tr.size() / 3);
+    u.pins = Pn.empty() ? nullptr : Pn.data();
+    u.npins = (int32_t)Pn.size();
+    return create_ctx(c, &u, params, stream, out);
 }
 
 void pdc_destroy(pdc_handle h) {

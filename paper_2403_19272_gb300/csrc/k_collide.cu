@@ -299,6 +299,49 @@ inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 // ====================================================================== broad phase driver
 namespace {
 __global__ void k_pccd_force(PccdState *ps) { ps->force_full = 1; }
+
+// bad |= some coordinate of x0_v or x1_v leaves [min(r0,r1) - m, max(r0,r1) + m]
+__global__ void k_containment(int nv, const float4 *__restrict__ x0, const float4 *__restrict__ x1,
+                              const float4 *__restrict__ r0, const float4 *__restrict__ r1, float m, int *bad) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    float3 a = f3(r0[v]), b = f3(r1[v]);
+    float3 lo = make_float3(fminf(a.x, b.x) - m, fminf(a.y, b.y) - m, fminf(a.z, b.z) - m);
+    float3 hi = make_float3(fmaxf(a.x, b.x) + m, fmaxf(a.y, b.y) + m, fmaxf(a.z, b.z) + m);
+    float3 p = f3(x0[v]), q = f3(x1[v]);
+    bool in = p.x >= lo.x && p.y >= lo.y && p.z >= lo.z && p.x <= hi.x && p.y <= hi.y && p.z <= hi.z &&
+              q.x >= lo.x && q.y >= lo.y && q.z >= lo.z && q.x <= hi.x && q.y <= hi.y && q.z <= hi.z;
+    if (!in) atomicOr(bad, 1);
+}
+
+// flag[i] = pair i of a superset list passes the broad-phase predicate on the
+// current boxes (kind 0: (v, t) with the vertex's swept box; 1: (e, f))
+__global__ void k_pair_flags(int kind, int n, const int2 *__restrict__ list, const float4 *__restrict__ x0,
+                             const float4 *__restrict__ x1, const float4 *__restrict__ tlo,
+                             const float4 *__restrict__ thi, const float4 *__restrict__ elo,
+                             const float4 *__restrict__ ehi, float dhat, int *__restrict__ flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int2 p = list[i];
+    float3 alo, ahi, blo, bhi;
+    if (kind == 0) {
+        vbox(x0, x1, p.x, alo, ahi);
+        blo = f3(tlo[p.y]);
+        bhi = f3(thi[p.y]);
+    } else {
+        alo = f3(elo[p.x]);
+        ahi = f3(ehi[p.x]);
+        blo = f3(elo[p.y]);
+        bhi = f3(ehi[p.y]);
+    }
+    flag[i] = box_overlap(alo, ahi, blo, bhi, dhat) ? 1 : 0;
+}
+
+__global__ void k_pair_scatter(int n, const int2 *__restrict__ list, const int *__restrict__ flag,
+                               const int *__restrict__ pos, int2 *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[pos[i]] = list[i];
+}
 }  // namespace
 
 void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee_, long long cap_ent_) {
@@ -351,6 +394,7 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
         cnt_ee_d[k].alloc(1);
     }
     cur = 0;
+    sup_ok = false;
     for (int k = 0; k < 2; ++k) {
         cnt_vt_d[k].zero(0);
         cnt_ee_d[k].zero(0);
@@ -435,6 +479,15 @@ void BroadPhase::grow(const CollView &cv, long long cvt, long long cee, long lon
 void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat,
                      int *overflow) {
     int nw = cur ^ 1;
+    hash_pass(s, cv, x0, x1, dhat, overflow, vt[nw], ee[nw], cnt_vt_d[nw], cnt_ee_d[nw]);
+    cur = nw;
+    sup_ok = false;
+    k_pccd_force<<<1, 1, 0, s>>>(pccd);  // new lists: the next partial-CCD pass scans them all
+    PDC_LAUNCH_CK();
+}
+
+void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat,
+                           int *overflow, int2 *out_vt, int2 *out_ee, long long *out_nvt, long long *out_nee) {
     PDC_CK(cudaMemsetAsync(gp.p, 0, sizeof(GridParams), s));
     BP_PROF("bp_boxes", if (cv.nt) k_tri_boxes<<<nblk(cv.nt, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, gp);
             if (cv.ne) k_edge_boxes<<<nblk(cv.ne, 256), 256, 0, s>>>(cv, x0, x1, elo, ehi);
@@ -474,9 +527,9 @@ void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const
         PDC_LAUNCH_CK();
     }
     exclusive_scan(s, cnt_v, off_v, cv.nv, scratch, tot + 2);
-    k_check_cap<<<1, 1, 0, s>>>(tot + 2, cap_vt, OVF_VT, overflow, cnt_vt_d[nw]);
+    k_check_cap<<<1, 1, 0, s>>>(tot + 2, cap_vt, OVF_VT, overflow, out_nvt);
     if (cv.nv) {
-        k_compact_slots<<<nblk(cv.nv, 256), 256, 0, s>>>(cv.nv, cnt_v, off_v, slots_vt, w_vt, tot + 2, cap_vt, vt[nw]);
+        k_compact_slots<<<nblk(cv.nv, 256), 256, 0, s>>>(cv.nv, cnt_v, off_v, slots_vt, w_vt, tot + 2, cap_vt, out_vt);
         PDC_LAUNCH_CK();
     }
     if (prof) prof->end(s);
@@ -489,10 +542,86 @@ void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const
         PDC_LAUNCH_CK();
     }
     exclusive_scan(s, cnt_e, off_e, cv.ne, scratch, tot + 3);
-    k_check_cap<<<1, 1, 0, s>>>(tot + 3, cap_ee, OVF_EE, overflow, cnt_ee_d[nw]);
+    k_check_cap<<<1, 1, 0, s>>>(tot + 3, cap_ee, OVF_EE, overflow, out_nee);
     if (cv.ne) {
-        k_compact_slots<<<nblk(cv.ne, 256), 256, 0, s>>>(cv.ne, cnt_e, off_e, slots_ee, w_ee, tot + 3, cap_ee, ee[nw]);
+        k_compact_slots<<<nblk(cv.ne, 256), 256, 0, s>>>(cv.ne, cnt_e, off_e, slots_ee, w_ee, tot + 3, cap_ee, out_ee);
         PDC_LAUNCH_CK();
+    }
+    if (prof) prof->end(s);
+}
+
+void BroadPhase::run_super(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat,
+                           float mu, int *overflow) {
+    if (sup_vt.n < (size_t)cap_vt) sup_vt.alloc(cap_vt);
+    if (sup_ee.n < (size_t)cap_ee) sup_ee.alloc(cap_ee);
+    sup_cnt.alloc(2);
+    // gap of the superset: every pair within d_hat of each other on a swept
+    // box grown by mu' per side is within d_hat + 2 mu on the reference boxes
+    float gap = dhat + 2.f * mu;
+    hash_pass(s, cv, x0, x1, gap, overflow, sup_vt, sup_ee, sup_cnt.p, sup_cnt.p + 1);
+    long long cnt[2] = {0, 0};
+    sup_cnt.download(cnt, 2, s);
+    PDC_CK(cudaStreamSynchronize(s));
+    if (std::max(cnt[0], cnt[1]) > scan_capacity()) {  // too long to filter: plain pass
+        run(s, cv, x0, x1, dhat, overflow);
+        return;
+    }
+    ref0.alloc(std::max(cv.nv, 1));
+    ref1.alloc(std::max(cv.nv, 1));
+    if (cv.nv) {
+        PDC_CK(cudaMemcpyAsync(ref0.p, x0, sizeof(float4) * cv.nv, cudaMemcpyDeviceToDevice, s));
+        PDC_CK(cudaMemcpyAsync(ref1.p, x1, sizeof(float4) * cv.nv, cudaMemcpyDeviceToDevice, s));
+    }
+    sup_mu = mu;
+    filter(s, cv, x0, x1, dhat);
+    sup_ok = true;
+}
+
+bool BroadPhase::can_reuse(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1) {
+    if (!sup_ok || cv.nv != nv) return false;
+    reuse_bad.alloc(1);
+    reuse_bad.zero(s);
+    if (cv.nv) k_containment<<<nblk(cv.nv, 256), 256, 0, s>>>(cv.nv, x0, x1, ref0, ref1, 0.9f * sup_mu, reuse_bad);
+    PDC_LAUNCH_CK();
+    int bad = 1;
+    reuse_bad.download(&bad, 1, s);
+    PDC_CK(cudaStreamSynchronize(s));
+    return bad == 0;
+}
+
+void BroadPhase::filter(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat) {
+    int nw = cur ^ 1;
+    long long cnt[2] = {0, 0};
+    sup_cnt.download(cnt, 2, s);
+    PDC_CK(cudaStreamSynchronize(s));
+    long long mx = std::max<long long>(std::max(cnt[0], cnt[1]), 1);
+    if (mx > scan_capacity()) throw Error(PDC_ERR_CAPACITY, "superset list too long to filter");
+    if ((long long)flags.n < mx) {
+        flags.alloc(mx);
+        fpos.alloc(mx);
+        fscratch.alloc(scan_scratch_ints((int)mx) + 16);
+    }
+    if (prof) prof->begin(s, "bp_filter", 0.0);
+    // boxes over the new interval, with the same arithmetic as the hash pass
+    if (cv.nt) k_tri_boxes<<<nblk(cv.nt, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, gp);
+    if (cv.ne) k_edge_boxes<<<nblk(cv.ne, 256), 256, 0, s>>>(cv, x0, x1, elo, ehi);
+    PDC_LAUNCH_CK();
+    long long *tot = totals.p;
+    for (int k = 0; k < 2; ++k) {
+        int n = (int)cnt[k];
+        const int2 *in = k == 0 ? sup_vt.p : sup_ee.p;
+        int2 *out = k == 0 ? vt[nw].p : ee[nw].p;
+        long long *nout = k == 0 ? cnt_vt_d[nw].p : cnt_ee_d[nw].p;
+        if (n > 0) {
+            k_pair_flags<<<nblk(n, 256), 256, 0, s>>>(k, n, in, x0, x1, tlo, thi, elo, ehi, dhat, flags);
+            PDC_LAUNCH_CK();
+        }
+        exclusive_scan(s, flags, fpos, n, fscratch, tot + 6 + k);
+        if (n > 0) {
+            k_pair_scatter<<<nblk(n, 256), 256, 0, s>>>(n, in, flags, fpos, out);
+            PDC_LAUNCH_CK();
+        }
+        PDC_CK(cudaMemcpyAsync(nout, tot + 6 + k, sizeof(long long), cudaMemcpyDeviceToDevice, s));
     }
     if (prof) prof->end(s);
     cur = nw;

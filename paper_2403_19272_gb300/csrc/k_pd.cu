@@ -134,96 +134,78 @@ __global__ void k_scale_disp(int n, const float4 *__restrict__ xs, const float4 
 }
 
 // r_i = m_i/h^2 (z_i - x_i) + sum_t w_t (R_t - F_t) g_{t,i} + sum_h w_h K_{h,i} (s_hat_h - s_h) + cf_i
-__global__ void __launch_bounds__(256) k_residual(const ClothView c, const float4 *__restrict__ xs,
-                                                  const float4 *__restrict__ u, const float4 *__restrict__ zrel,
-                                                  const float *__restrict__ cw, const float4 *__restrict__ cf,
-                                                  float4 *__restrict__ r, Scalars *sc, float *__restrict__ r_soa,
-                                                  int soa_ld) {
+// The residual in two stages.  Each element computes its projection once and
+// writes its force on each of its vertices (stretch: w_t (g_k^T)(R - F) with F
+// from exact differences of the rest part and of the displacements; bend:
+// w_h K_j (s_hat - s)); each vertex then sums the forces of its incident
+// elements in incidence order, adds inertia and contact, and reduces |r|^2.
+__global__ void __launch_bounds__(256) k_tri_corner(const ClothView c, const float4 *__restrict__ xs,
+                                                    const float4 *__restrict__ u, float4 *__restrict__ ct) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= c.m) return;
+    int4 T = c.tri[t];
+    float4 g = c.tri_g[t];
+    float w = c.tri_w[t];
+    float3 p0 = f3(xs[T.x]), p1 = f3(xs[T.y]), p2 = f3(xs[T.z]);
+    float3 q0 = f3(u[T.x]), q1 = f3(u[T.y]), q2 = f3(u[T.z]);
+    float3 e1 = (p1 - p0) + (q1 - q0), e2 = (p2 - p0) + (q2 - q0);  // (x*_a - x*_b) + (u_a - u_b)
+    float3 F1 = g.x * e1 + g.z * e2;  // column 1 of F = [e1 e2] Dm^-1
+    float3 F2 = g.y * e1 + g.w * e2;  // column 2
+    float3 R1, R2;
+    polar32(F1, F2, R1, R2);
+    float3 d1 = R1 - F1, d2 = R2 - F2;
+    ct[3 * (size_t)t + 0] = f4(w * (-(g.x + g.z) * d1 + -(g.y + g.w) * d2));
+    ct[3 * (size_t)t + 1] = f4(w * (g.x * d1 + g.y * d2));
+    ct[3 * (size_t)t + 2] = f4(w * (g.z * d1 + g.w * d2));
+}
+
+__global__ void __launch_bounds__(256) k_hinge_corner(const ClothView c, const float4 *__restrict__ xs,
+                                                      const float4 *__restrict__ u, float4 *__restrict__ ch) {
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= c.nh) return;
+    int4 H = c.hin[h];
+    float4 K = c.hin_K[h];
+    float sl = c.hin_slen[h], hw = c.hin_w[h];
+    float3 p0 = f3(xs[H.x]), q0 = f3(u[H.x]);
+    float3 d1 = (f3(xs[H.y]) - p0) + (f3(u[H.y]) - q0);
+    float3 d2 = (f3(xs[H.z]) - p0) + (f3(u[H.z]) - q0);
+    float3 d3 = (f3(xs[H.w]) - p0) + (f3(u[H.w]) - q0);
+    float3 sv = K.y * d1 + K.z * d2 + K.w * d3;
+    float3 sh;
+    float ns = sqrtf(dot3(sv, sv));
+    if (sl == 0.f) sh = make_float3(0.f, 0.f, 0.f);
+    else if (ns > 1e-30f) sh = (sl / ns) * sv;
+    else sh = f3(c.hin_srest[h]);
+    float3 d = sh - sv;
+    float4 *o = ch + 4 * (size_t)h;
+    o[0] = f4((hw * K.x) * d);
+    o[1] = f4((hw * K.y) * d);
+    o[2] = f4((hw * K.z) * d);
+    o[3] = f4((hw * K.w) * d);
+}
+
+__global__ void __launch_bounds__(256) k_residual(const ClothView c, const float4 *__restrict__ u,
+                                                  const float4 *__restrict__ zrel, const float *__restrict__ cw,
+                                                  const float4 *__restrict__ cf, const float4 *__restrict__ ct,
+                                                  const float4 *__restrict__ ch, float4 *__restrict__ r, Scalars *sc,
+                                                  float *__restrict__ r_soa, int soa_ld) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float sq = 0.f;
     if (i < c.n) {
         float3 f = make_float3(0.f, 0.f, 0.f);
         if (c.is_free[i]) {
             f = c.mh2[i] * (f3(zrel[i]) - f3(u[i]));
-            // Incident elements are processed in groups whose loads are all
-            // issued before any result is used (three memory latencies per
-            // group: incidence entries, element data, vertex positions).
-            constexpr int GT = 2, GH = 2;
             const int tb = c.vt_off[i], te = c.vt_off[i + 1];
-            for (int e0 = tb; e0 < te; e0 += GT) {
-                int ent[GT];
-#pragma unroll
-                for (int q = 0; q < GT; ++q) ent[q] = e0 + q < te ? __ldg(c.vt_list + e0 + q) : -1;
-                int4 T[GT];
-                float4 g[GT];
-                float w[GT];
-#pragma unroll
-                for (int q = 0; q < GT; ++q) {
-                    int t = ent[q] >= 0 ? ent[q] >> 2 : 0;
-                    T[q] = c.tri[t];
-                    g[q] = c.tri_g[t];
-                    w[q] = ent[q] >= 0 ? c.tri_w[t] : 0.f;
-                }
-                float4 P[GT][3], Q[GT][3];
-#pragma unroll
-                for (int q = 0; q < GT; ++q) {
-                    P[q][0] = xs[T[q].x]; P[q][1] = xs[T[q].y]; P[q][2] = xs[T[q].z];
-                    Q[q][0] = u[T[q].x]; Q[q][1] = u[T[q].y]; Q[q][2] = u[T[q].z];
-                }
-#pragma unroll
-                for (int q = 0; q < GT; ++q) {
-                    if (ent[q] < 0) continue;
-                    int corner = ent[q] & 3;
-                    // (x*_a - x*_b) + (u_a - u_b): exact differences of the rest part
-                    float3 e1 = (f3(P[q][1]) - f3(P[q][0])) + (f3(Q[q][1]) - f3(Q[q][0]));
-                    float3 e2 = (f3(P[q][2]) - f3(P[q][0])) + (f3(Q[q][2]) - f3(Q[q][0]));
-                    float3 F1 = g[q].x * e1 + g[q].z * e2;  // column 1 of F = [e1 e2] Dm^-1
-                    float3 F2 = g[q].y * e1 + g[q].w * e2;  // column 2
-                    float3 R1, R2;
-                    polar32(F1, F2, R1, R2);
-                    float gx = corner == 0 ? -(g[q].x + g[q].z) : (corner == 1 ? g[q].x : g[q].z);
-                    float gy = corner == 0 ? -(g[q].y + g[q].w) : (corner == 1 ? g[q].y : g[q].w);
-                    f = f + w[q] * (gx * (R1 - F1) + gy * (R2 - F2));
-                }
+#pragma unroll 4
+            for (int e = tb; e < te; ++e) {
+                int ent = __ldg(c.vt_list + e);
+                f = f + f3(ct[3 * (size_t)(ent >> 2) + (ent & 3)]);
             }
             const int hb = c.vh_off[i], he = c.vh_off[i + 1];
-            for (int e0 = hb; e0 < he; e0 += GH) {
-                int ent[GH];
-#pragma unroll
-                for (int q = 0; q < GH; ++q) ent[q] = e0 + q < he ? __ldg(c.vh_list + e0 + q) : -1;
-                int4 Hh[GH];
-                float4 K[GH];
-                float sl[GH], hw[GH];
-#pragma unroll
-                for (int q = 0; q < GH; ++q) {
-                    int hh = ent[q] >= 0 ? ent[q] >> 2 : 0;
-                    Hh[q] = c.hin[hh];
-                    K[q] = c.hin_K[hh];
-                    sl[q] = c.hin_slen[hh];
-                    hw[q] = ent[q] >= 0 ? c.hin_w[hh] : 0.f;
-                }
-                float4 P[GH][4], Q[GH][4];
-#pragma unroll
-                for (int q = 0; q < GH; ++q) {
-                    P[q][0] = xs[Hh[q].x]; P[q][1] = xs[Hh[q].y]; P[q][2] = xs[Hh[q].z]; P[q][3] = xs[Hh[q].w];
-                    Q[q][0] = u[Hh[q].x]; Q[q][1] = u[Hh[q].y]; Q[q][2] = u[Hh[q].z]; Q[q][3] = u[Hh[q].w];
-                }
-#pragma unroll
-                for (int q = 0; q < GH; ++q) {
-                    if (ent[q] < 0) continue;
-                    int slot = ent[q] & 3;
-                    float3 d1 = (f3(P[q][1]) - f3(P[q][0])) + (f3(Q[q][1]) - f3(Q[q][0]));
-                    float3 d2 = (f3(P[q][2]) - f3(P[q][0])) + (f3(Q[q][2]) - f3(Q[q][0]));
-                    float3 d3 = (f3(P[q][3]) - f3(P[q][0])) + (f3(Q[q][3]) - f3(Q[q][0]));
-                    float3 sv = K[q].y * d1 + K[q].z * d2 + K[q].w * d3;
-                    float3 sh;
-                    float ns = sqrtf(dot3(sv, sv));
-                    if (sl[q] == 0.f) sh = make_float3(0.f, 0.f, 0.f);
-                    else if (ns > 1e-30f) sh = (sl[q] / ns) * sv;
-                    else sh = f3(c.hin_srest[ent[q] >> 2]);
-                    float ks = slot == 0 ? K[q].x : (slot == 1 ? K[q].y : (slot == 2 ? K[q].z : K[q].w));
-                    f = f + (hw[q] * ks) * (sh - sv);
-                }
+#pragma unroll 4
+            for (int e = hb; e < he; ++e) {
+                int ent = __ldg(c.vh_list + e);
+                f = f + f3(ch[4 * (size_t)(ent >> 2) + (ent & 3)]);
             }
             if (cf) f = f + f3(cf[i]);
             sq = dot3(f, f);
@@ -309,24 +291,23 @@ template <int WMAX>
 __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const float *__restrict__ cw,
                                                    const float4 *__restrict__ r, const float4 *__restrict__ din,
                                                    const float4 *__restrict__ dprev, float4 *__restrict__ dout,
-                                                   float4 *__restrict__ dnew, float alpha, float beta,
+                                                   float alpha, float beta,
                                                    const float4 *x, float4 *xout, float4 *xprev, float w_acc,
                                                    const float4 *__restrict__ xs, float4 *__restrict__ xabs,
                                                    Scalars *sc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float mx = 0.f;
     if (i < c.n) {
-        float3 dn = make_float3(0.f, 0.f, 0.f), dd = make_float3(0.f, 0.f, 0.f);
+        float3 dn = make_float3(0.f, 0.f, 0.f);
         if (c.is_free[i]) {
             float3 di = f3(din[i]);
             float D = c.hdiag[i] + (cw ? cw[i] : 0.f);
             float3 acc = f3(r[i]) - D * di - ell_apply<WMAX>(c, i, din);
-            dd = (beta / D) * acc;
-            if (alpha != 0.f) dd = dd + alpha * f3(dprev[i]);
+            float3 dd = (beta / D) * acc;
+            if (alpha != 0.f) dd = dd + alpha * (di - f3(dprev[i]));  // alpha (delta_k - delta_k-1)
             dn = di + dd;
         }
         dout[i] = f4(dn);
-        dnew[i] = f4(dd);
         if (xout) {
             float3 xo = f3(x[i]);
             float3 xn = xo + dn;
@@ -512,7 +493,10 @@ void launch_scale_disp(cudaStream_t s, int n, const float4 *xs, const float4 *u,
 
 void launch_residual(cudaStream_t s, const ClothView &c, const float4 *xs, const float4 *u, const float4 *zrel,
                      const float *cw, const float4 *cf, float4 *r, Scalars *sc, float *r_soa, int soa_ld) {
-    if (c.n > 0) k_residual<<<nblk(c.n, 256), 256, 0, s>>>(c, xs, u, zrel, cw, cf, r, sc, r_soa, soa_ld);
+    float4 *ct = c.corner, *ch = c.corner + 3 * (size_t)c.m;
+    if (c.m > 0) k_tri_corner<<<nblk(c.m, 256), 256, 0, s>>>(c, xs, u, ct);
+    if (c.nh > 0) k_hinge_corner<<<nblk(c.nh, 256), 256, 0, s>>>(c, xs, u, ch);
+    if (c.n > 0) k_residual<<<nblk(c.n, 256), 256, 0, s>>>(c, u, zrel, cw, cf, ct, ch, r, sc, r_soa, soa_ld);
     PDC_LAUNCH_CK();
 }
 
@@ -532,12 +516,12 @@ void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const flo
 }
 
 void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
-                      const float4 *dprev, float4 *dout, float4 *dnew, float alpha, float beta, const float4 *x,
+                      const float4 *dprev, float4 *dout, float alpha, float beta, const float4 *x,
                       float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs) {
     if (c.n > 0) {
         int b = nblk(c.n, 256);
 #define PDC_CHEB(W)                                                                                   \
-    k_cheb_step<W><<<b, 256, 0, s>>>(c, cw, r, din, dprev, dout, dnew, alpha, beta, x, xout, xprev, w_acc, xs, xabs, sc)
+    k_cheb_step<W><<<b, 256, 0, s>>>(c, cw, r, din, dprev, dout, alpha, beta, x, xout, xprev, w_acc, xs, xabs, sc)
         if (c.ell_w <= 8) PDC_CHEB(8);
         else if (c.ell_w <= 12) PDC_CHEB(12);
         else if (c.ell_w <= 16) PDC_CHEB(16);

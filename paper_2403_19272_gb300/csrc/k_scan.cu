@@ -85,6 +85,7 @@ __global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__
 }  // namespace
 
 size_t scan_scratch_ints(int n) { return (size_t)((n + SCAN_B - 1) / SCAN_B) + 1; }
+long long scan_capacity() { return (long long)SCAN_B * SCAN_B; }
 
 void exclusive_scan(cudaStream_t s, const int *in, int *out, int n, int *scratch, long long *total) {
     if (n <= 0) {

@@ -86,11 +86,32 @@ struct BroadPhase {
     DevBuf<PccdState> pccd;
     void reserve_pccd(const CollView &cv);
 
+    // superset lists of a hash pass with gap d_hat + 2 mu at positions (ref0,
+    // ref1); while every vertex stays within mu' = 0.9 mu of that swept box,
+    // the exact lists are a subsequence of them (see filter)
+    DevBuf<int2> sup_vt, sup_ee;
+    DevBuf<long long> sup_cnt;  // [2]
+    DevBuf<float4> ref0, ref1;
+    DevBuf<int> flags, fpos, fscratch;
+    DevBuf<int> reuse_bad;
+    float sup_mu = 0.f;
+    bool sup_ok = false;
+
     void reserve(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent);
     // larger capacities keeping the current candidate lists, states and counts
     void grow(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent, cudaStream_t s);
     void grow_slots(const CollView &cv, bool vt, bool ee);
     void run(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat, int *overflow);
+    // hash pass into the superset lists (gap dhat + 2 mu), then filter
+    void run_super(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat, float mu,
+                   int *overflow);
+    // true when every vertex of (x0, x1) lies in the reference swept box +- 0.9 mu (host sync)
+    bool can_reuse(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1);
+    // exact lists for (x0, x1) with gap dhat from the superset; makes them current
+    void filter(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat);
+    // the hash pipeline writing into the given lists
+    void hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat, int *overflow,
+                   int2 *out_vt, int2 *out_ee, long long *out_nvt, long long *out_nee);
 };
 
 // Exact CCD over the current lists; if merge, NDB states are carried over

@@ -108,6 +108,7 @@ struct ClothView {
     int ell_w;
     const int *ell_col;    // [ell_w][n]
     const float *ell_val;  // [ell_w][n]
+    float4 *corner;        // scratch [3m + 4nh]: per-element corner forces of the residual
 };
 
 // Collision-set topology (cloth + obstacles).
@@ -144,8 +145,10 @@ void launch_residual(cudaStream_t s, const ClothView &c, const float4 *xs, const
 void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                   float4 *dout, float omega, const float4 *x, float4 *xout, Scalars *sc, float4 *xprev = nullptr,
                   float w_acc = 1.f, const float4 *xs = nullptr, float4 *xabs = nullptr);
+// One Chebyshev step in three-term form: dout = din + alpha (din - dprev)
+// + beta D^-1 (r - (H + diag cw) din) (dprev unused when alpha = 0).
 void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
-                      const float4 *dprev, float4 *dout, float4 *dnew, float alpha, float beta, const float4 *x,
+                      const float4 *dprev, float4 *dout, float alpha, float beta, const float4 *x,
                       float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs);
 // Anderson mixing step on the iterate u (= u_k + delta_k on entry, u_{k+1} on exit).
 void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x, float4 *fprev,

@@ -41,14 +41,15 @@ class pdc_params(ctypes.Structure):
                 ("samples_ee", c_i32), ("collisions", c_i32), ("fixed_iters", c_i32), ("eig_iters", c_i32),
                 ("seed", c_u64), ("accel", c_i32), ("accel_rho", c_dbl), ("sweep_kind", c_i32),
                 ("cheb_ratio", c_dbl), ("aa_depth", c_i32),
-                ("tensor_cores", c_i32)]
+                ("tensor_cores", c_i32), ("bp_reuse", c_dbl)]
 
 
 class pdc_stats(ctypes.Structure):
     _fields_ = [("warm_iters", c_i32), ("outer_iters", c_i32), ("inner_iters", c_i32), ("contact_iters", c_i32),
                 ("n_candidates", c_i64), ("n_active", c_i64), ("n_contact_vertices", c_i64), ("t_toi", c_dbl),
                 ("s_line_search", c_dbl), ("rho0", c_dbl), ("rel_residual", c_dbl), ("ms_step", c_dbl),
-                ("ms_broad", c_dbl), ("ms_narrow", c_dbl), ("ms_lg", c_dbl), ("overflow_retries", c_i32)]
+                ("ms_broad", c_dbl), ("ms_narrow", c_dbl), ("ms_lg", c_dbl), ("overflow_retries", c_i32),
+                ("bp_reused", c_i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -62,6 +63,7 @@ class pdc_kernel_time(ctypes.Structure):
 SIGNATURES = {
     "pdc_default_params": (None, [P]),
     "pdc_create": (c_i32, [P, P, P, P, P]),
+    "pdc_create_batch": (c_i32, [c_i32, P, P, P, P, P]),
     "pdc_add_obstacle": (c_i32, [P, P, c_i32, P, c_i32, P]),
     "pdc_set_obstacle_transform": (c_i32, [P, c_i32, P]),
     "pdc_set_pin_targets": (c_i32, [P, P, c_i32]),
@@ -148,6 +150,28 @@ def pdc_create(verts, tris, pins, density, k_stretch, k_bend, params: pdc_params
     if st != PDC_OK:
         raise PdcError(st, lib().pdc_last_error(None).decode())
     return h
+
+
+def pdc_create_batch(instances, params: pdc_params, stream=None):
+    """instances: sequence of (verts, tris, pins, density, k_stretch, k_bend).
+    Returns (handle, vertex offsets of the instances in the union)."""
+    keep, meshes, mats, offs = [], [], [], []
+    nv = 0
+    for verts, tris, pins, density, k_stretch, k_bend in instances:
+        verts, tris, pins = _f32(verts, (-1, 3)), _i32(tris).reshape(-1, 3), _i32(pins).reshape(-1)
+        keep += [verts, tris, pins]
+        meshes.append(pdc_mesh_desc(_ptr(verts), len(verts), _ptr(tris), len(tris), _ptr(pins) if len(pins) else None,
+                                    len(pins)))
+        mats.append(pdc_material(density, k_stretch, k_bend))
+        offs.append(nv)
+        nv += len(verts)
+    marr = (pdc_mesh_desc * len(meshes))(*meshes)
+    tarr = (pdc_material * len(mats))(*mats)
+    h = P()
+    st = lib().pdc_create_batch(len(meshes), marr, tarr, ctypes.byref(params), stream, ctypes.byref(h))
+    if st != PDC_OK:
+        raise PdcError(st, lib().pdc_last_error(None).decode())
+    return h, np.array(offs + [nv], dtype=np.int64)
 
 
 def pdc_destroy(h):

@@ -356,6 +356,30 @@ def test_one_step_parity_config0_with_collision_pipeline(pc):
     cl.close()
 
 
+def test_broadphase_reuse_leaves_steps_unchanged(pc):
+    # the candidate lists filtered from a wider first pass are the lists of a
+    # fresh pass: from identical states both runs take the same step (up to
+    # the order of float atomics in the contact sums)
+    sc = wl.drape_sphere(side=16, sphere_subdiv=2)
+    base = dict(fixed_iters=1, warm_iters=2, max_outer=3, max_inner=3, solve_cycles=40, jacobi_sweeps=8, r_warm=32,
+                r_reuse=32, d_hat=1e-3)
+    a = pc.Cloth(sc, params(pc, bp_reuse=0.0, **base))
+    b = pc.Cloth(sc, params(pc, bp_reuse=4.0, **base))
+    L = float(np.linalg.norm(sc.verts.max(0) - sc.verts.min(0)))
+    reused = 0
+    for k in range(8):
+        a.step()
+        b.step()
+        reused += b.stats()["bp_reused"]
+        xa, va = a.state()
+        xb, vb = b.state()
+        assert np.max(np.abs(xa - xb)) <= 1e-6 * L, k
+        pc.pdc_set_state(b.h, xa, va)
+    assert reused > 0
+    a.close()
+    b.close()
+
+
 def test_drape_run_stays_penetration_free(pc):
     sc = wl.drape_sphere(side=16, sphere_subdiv=2)
     cl = pc.Cloth(sc, params(pc, r_warm=32, r_reuse=32, d_hat=1e-3, max_inner=12))
