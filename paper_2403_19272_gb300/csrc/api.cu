@@ -121,6 +121,23 @@ struct Accel {
         w = 1.0;
         hist.clear();
         aa_reset();
+        stag_best = 0.0;
+        stag_count = 0;
+    }
+    // residual-stagnation stop of the relative-residual mode: without
+    // collision springs, STAG_N iterations that do not lower the best
+    // residual of the pass by 1% end the inner loop (the FP32 floor of a
+    // nearly unstrained cloth, e.g. in free fall, lies above small targets)
+    static constexpr int STAG_N = 16;
+    double stag_best = 0.0;
+    int stag_count = 0;
+    bool stagnated(double rho, bool springs) {
+        if (springs || stag_best == 0.0 || rho < 0.99 * stag_best) {
+            stag_best = (springs || stag_best == 0.0) ? rho : std::min(stag_best, rho);
+            stag_count = 0;
+            return false;
+        }
+        return ++stag_count >= STAG_N;
     }
     double rho_carry = 0.0;  // estimate carried from earlier passes
     // Anderson mixing history (accel = 2)
@@ -182,6 +199,7 @@ using namespace pdc;
         if (prof.on) prof.begin(s, name, (double)(bytes));                                              \
         __VA_ARGS__;                                                                                   \
         if (prof.on) prof.end(s);                                                                      \
+        if (sync_check) check_region(name);                                                            \
     } while (0)
 
 struct pdc_ctx {
@@ -205,6 +223,10 @@ struct pdc_ctx {
     DevBuf<float4> tri_g, hin_K, hin_srest;
     DevBuf<float> tri_w, hin_w, hin_slen, mh2, hdiag, ell_val;
     DevBuf<int> vt_off, vt_list, vh_off, vh_list, ell_col, pins_d;
+    DevBuf<short> ell_dcol;
+    DevBuf<int> halo_off, halo_rows;
+    DevBuf<unsigned short> ell_lcol;
+    int halo_max = 0;
     DevBuf<unsigned char> is_free;
     int ell_w = 0;
     // pins
@@ -230,7 +252,8 @@ struct pdc_ctx {
     DevBuf<int> contact_list;
     // subspace
     int r_warm = 0, r_reuse = 0, ld = 0;
-    DevBuf<float> U32, A0inv32, proj_partial, qbuf, dA;
+    DevBuf<float> U32, A0inv32, proj_partial, qbuf;
+    DevBuf<double> dA;
     DevBuf<uint16_t> U16bits;    // 16-bit basis [n][ld] (BF16 or scaled FP16 bits)
     DevBuf<uint16_t> Ut16;       // its transpose [ld][n_pad] (tensor-core projection)
     int n_pad = 0;
@@ -263,6 +286,16 @@ struct pdc_ctx {
     double gersh = 1.0;       // Gershgorin bound of D^-1 H
     long long nnz_off = 0;  // off-diagonal entries of H over free rows
     bool log = std::getenv("PDC_LOG") != nullptr;  // per-iteration residuals to stderr
+    // diagnostics: synchronise after every profiled region and name the
+    // region in the error of a failed kernel
+    bool sync_check = std::getenv("PDC_SYNC_CHECK") != nullptr;
+    bool last_springs = false;  // the last LG iteration had collision springs
+    void check_region(const char *name) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess)
+            throw Error(PDC_ERR_CUDA, std::string("after ") + name + ": " + cudaGetErrorString(e));
+    }
 
     ~pdc_ctx() {
         if (hsc) cudaFreeHost(hsc);
@@ -290,6 +323,11 @@ struct pdc_ctx {
         c.is_free = is_free;
         c.ell_w = ell_w;
         c.ell_col = ell_col;
+        c.ell_dcol = ell_dcol.p;
+        c.halo_off = halo_off.p;
+        c.halo_rows = halo_rows.p;
+        c.ell_lcol = ell_lcol.p;
+        c.halo_max = halo_max;
         c.ell_val = ell_val;
         c.corner = corner;
         return c;
@@ -362,7 +400,7 @@ struct pdc_ctx {
                (double)(3LL * m + 4LL * nh) * 4 + (contacts ? (double)n * 16 : 0.0);
     }
     double bytes_sweep(bool contacts, bool writes_x) const {
-        return (double)nnz_off * 8 + (double)n * (12 + 12 + 4 + 1 + 12) + (contacts ? 4.0 * n : 0.0) +
+        return (double)nnz_off * (ell_dcol.p ? 6 : 8) + (double)n * (12 + 12 + 4 + 1 + 12) + (contacts ? 4.0 * n : 0.0) +
                (writes_x ? 24.0 * n : 0.0);
     }
     double bytes_basis(int r) const { return (double)n * r * (P.precision != 0 ? 2 : 4) + (double)n * 12; }
@@ -616,6 +654,61 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
     hdiag.upload(hdiag_h, s);
     is_free.upload(freev, s);
     ell_col.upload(ecol, s);
+    {  // 16-bit column offsets for the sweeps when the matrix bandwidth allows
+        std::vector<short> dcol(ecol.size());
+        bool fits = true;
+        for (size_t k = 0; k < ecol.size() && fits; ++k) {
+            long long d = (long long)ecol[k] - (long long)(k % (size_t)n);
+            fits = d >= -32768 && d <= 32767;
+            dcol[k] = (short)d;
+        }
+        if (fits && !dcol.empty()) ell_dcol.upload(dcol, s);
+        else ell_dcol.release();
+    }
+    {  // halo staging for the sweeps: per block of rows, the distinct
+       // referenced rows outside the block and each entry's staged slot
+        int nb = (n + STAGE_ROWS - 1) / STAGE_ROWS;
+        std::vector<int> hoff(nb + 1, 0), hrows;
+        std::vector<unsigned short> lcol((size_t)ell_w * n, 0);
+        bool ok = ell_w > 0;
+        halo_max = 0;
+        for (int b = 0; b < nb && ok; ++b) {
+            int a = b * STAGE_ROWS, e = std::min(n, a + STAGE_ROWS);
+            std::vector<int> hs;
+            for (int i = a; i < e; ++i)
+                for (int k = 0; k < ell_w; ++k) {
+                    int j = ecol[(size_t)k * n + i];
+                    if (j < a || j >= e) hs.push_back(j);
+                }
+            std::sort(hs.begin(), hs.end());
+            hs.erase(std::unique(hs.begin(), hs.end()), hs.end());
+            if (STAGE_ROWS + (int)hs.size() > STAGE_MAX_SLOTS) {
+                ok = false;
+                break;
+            }
+            halo_max = std::max(halo_max, (int)hs.size());
+            for (int i = a; i < e; ++i)
+                for (int k = 0; k < ell_w; ++k) {
+                    int j = ecol[(size_t)k * n + i];
+                    int slot = (j >= a && j < e) ? j - a
+                                                 : STAGE_ROWS + (int)(std::lower_bound(hs.begin(), hs.end(), j) - hs.begin());
+                    lcol[(size_t)k * n + i] = (unsigned short)slot;
+                }
+            hrows.insert(hrows.end(), hs.begin(), hs.end());
+            hoff[b + 1] = (int)hrows.size();
+        }
+        if (ok) {
+            halo_off.upload(hoff, s);
+            if (hrows.empty()) hrows.push_back(0);
+            halo_rows.upload(hrows, s);
+            ell_lcol.upload(lcol, s);
+        } else {
+            halo_off.release();
+            halo_rows.release();
+            ell_lcol.release();
+            halo_max = 0;
+        }
+    }
     ell_val.upload(evalv, s);
     pins_d.upload(pins, s);
     std::vector<float4> pt(npins);
@@ -871,8 +964,15 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
     PROF("local_residual", bytes_residual(contacts), launch_residual(s, c, Xs, Ucur, Z, cw, cf, R, sc, nullptr, 0));
     bool acc = accel.on && !(P.fixed_iters != 0);
     bool aa = acc && P.accel == 2;
+    // whether collision springs exist this iteration (device count); known on
+    // the host when the residual is read back anyway
+    bool springs = contacts;
+    last_springs = contacts;
     if (check_rel || log || acc) {
+        if (contacts) PDC_CK(cudaMemcpyAsync(&sc.p->n_contact_v, n_cv_d.p, sizeof(int), cudaMemcpyDeviceToDevice, s));
         read_scalars();
+        if (contacts) springs = hsc->n_contact_v > 0;
+        last_springs = springs;
         double rho = std::sqrt(hsc->rsq);
         if (log) {
             int na = 0, ncv = 0;
@@ -886,7 +986,7 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
     if (check_rel) {
         double rho = std::sqrt(hsc->rsq);
         st.rel_residual = rho / std::max(rho0, 1e-300);
-        if (rho <= P.tol_rel_residual * rho0) {
+        if (rho <= P.tol_rel_residual * rho0 || accel.stagnated(rho, springs)) {
             converged = true;
             return;
         }
@@ -907,12 +1007,12 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             rl = RL;
         }
         if (r_warm > 0 && (r_nc > 0 || r_c > 0)) {
-            PROF("subspace_project", bytes_basis(contacts ? r_c : r_nc),
-                 launch_project(s, S, rl, n_cv_d, W, contacts));
-            if (contacts && r_c > 0) PROF("subspace_syrk", 0, launch_syrk(s, S, contact_list, n_cv_d, cw, W));
+            PROF("subspace_project", bytes_basis(springs ? r_c : r_nc),
+                 launch_project(s, S, rl, n_cv_d, W, springs));
+            if (springs && r_c > 0) PROF("subspace_syrk", 0, launch_syrk(s, S, contact_list, n_cv_d, cw, W));
             PROF("reduced_solve", 0, launch_reduced_solve(s, S, n_cv_d, W));
-            PROF("subspace_lift", bytes_basis(contacts ? r_c : r_nc) + 12.0 * n,
-                 launch_lift(s, S, n_cv_d, W, have_delta ? din : nullptr, dout, contacts));
+            PROF("subspace_lift", bytes_basis(springs ? r_c : r_nc) + 12.0 * n,
+                 launch_lift(s, S, n_cv_d, W, have_delta ? din : nullptr, dout, springs));
             std::swap(din, dout);
             have_delta = true;
         }
@@ -925,7 +1025,8 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             double b = std::max(gersh, 1.0) * 1.02, a = b / std::max(P.cheb_ratio, 1.0001);
             double theta = 0.5 * (b + a), dl = 0.5 * (b - a), sig = theta / dl;
             double rho_prev = 1.0 / sig;
-            float4 *dp = CD0;  // delta_{k-1}; din = delta_k, dout = delta_{k+1}
+            // delta_{k-1}: the one of the three buffers that is neither din nor dout
+            float4 *dp = (CD0.p != din && CD0.p != dout) ? CD0.p : (D0.p != din && D0.p != dout) ? D0.p : D1.p;
             for (int k = 0; k < sweeps; ++k) {
                 bool last = (cyc == cycles - 1) && (k == sweeps - 1);
                 double alpha, beta;
@@ -1136,6 +1237,13 @@ void pdc_ctx::step() {
                 if (!fixed && !relmode) {
                     read_scalars();
                     if (bits_to_float(hsc->dxmax) <= tolx_in) break;
+                } else if (relmode && last_springs) {
+                    // with collision springs the residual carries barrier
+                    // terms whose weights change every iteration: the inner
+                    // loop also ends once the iterate has settled to the
+                    // outer tolerance
+                    read_scalars();
+                    if (bits_to_float(hsc->dxmax) <= tolx_out) break;
                 }
             }
             if (inner > 0 || o == 0) {
@@ -1203,6 +1311,13 @@ void pdc_ctx::step() {
         PDC_CK(cudaMemcpyAsync(Vs.p, Vbak.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
         PDC_CK(cudaStreamSynchronize(s));
         throw Error(PDC_ERR_NUMERIC, "non-finite positions; state rolled back");
+    }
+    if (unsigned int guard = P.collisions ? pair_guard_take(s) : 0u) {
+        PDC_CK(cudaMemcpyAsync(Xs.p, Xbak.p, sizeof(float4) * nv_all, cudaMemcpyDeviceToDevice, s));
+        PDC_CK(cudaMemcpyAsync(Vs.p, Vbak.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+        PDC_CK(cudaStreamSynchronize(s));
+        throw Error(PDC_ERR_STATE, "collision list index outside the topology (guard 0x" + std::to_string(guard) +
+                                       "); state rolled back");
     }
     if (prof.on) prof.flush();
     stepped = true;
@@ -1776,7 +1891,7 @@ pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, con
         }
         if (r > 0) {
             launch_project(s, S, rl, one, W);
-            PDC_CK(cudaMemsetAsync(W.dA, 0, sizeof(float) * r * r, s));
+            PDC_CK(cudaMemsetAsync(W.dA, 0, sizeof(double) * r * r, s));
             launch_syrk(s, S, h->contact_list, ncv, h->CW, W);
             launch_reduced_solve(s, S, one, W);
             launch_lift(s, S, one, W, have ? din : nullptr, dout);

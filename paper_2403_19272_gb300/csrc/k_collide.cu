@@ -9,12 +9,14 @@
 // segment is sorted by the secondary id: the pair lists come out sorted by
 // (primary, secondary) and deterministic, which lets the NDB counters of
 // one full CCD be carried to the next by binary search.
+#include <cooperative_groups.h>
 #include <cstring>
 
 #include "pdc_collide.cuh"
 #include "pdc_scan.cuh"
 
 namespace pdc {
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -146,10 +148,16 @@ __global__ void k_hash_insert(int np, const float4 *__restrict__ blo, const floa
 }
 
 // ------------------------------------------------------------------ queries
-// Single-pass queries.  Each primary keeps its candidates sorted by
-// secondary id in a fixed-width row of a slot buffer (insertion as found);
-// the count is always exact, and a primary with more candidates than the row
-// width flags OVF_SLOTS (the pass is then rerun with wider rows).
+// Queries.  Each primary collects its candidates, sorted by secondary id,
+// in a fixed-width row of a slot buffer; the count is always exact, and a
+// primary with more candidates than the row width flags OVF_SLOTS (the pass
+// is then rerun with wider rows).  In the VT query QG_VT lanes share one
+// vertex and stride over the entries of each bucket of its cell range
+// together (the lanes of a group run the same trip count), append through a
+// group ballot and sort the row once at the end.
+constexpr int QUERY_T = 128;
+constexpr int QG_VT = 8;  // lanes per vertex in the VT query
+
 __device__ inline void slot_insert(int *row, int width, int c, int q) {
     if (c >= width) return;
     int j = c - 1;
@@ -160,20 +168,34 @@ __device__ inline void slot_insert(int *row, int width, int c, int q) {
     row[j + 1] = q;
 }
 
+__device__ inline void sort_row(int *row, int c) {
+    for (int i = 1; i < c; ++i) {
+        int q = row[i], j = i - 1;
+        while (j >= 0 && row[j] > q) {
+            row[j + 1] = row[j];
+            --j;
+        }
+        row[j + 1] = q;
+    }
+}
+
 // VT: primary = vertex v (all collision vertices), secondary = triangle.
-__global__ void __launch_bounds__(128) k_query_vt(CollView cv, const float4 *__restrict__ x0,
-                                                  const float4 *__restrict__ x1, const float4 *__restrict__ tlo,
-                                                  const float4 *__restrict__ thi, const int4 *__restrict__ tcell,
-                                                  const GridParams *gp, float dhat, unsigned int mask,
-                                                  const int *__restrict__ bcnt, const int *__restrict__ bstart,
-                                                  const unsigned long long *__restrict__ ekey,
-                                                  const int *__restrict__ eprim, int *__restrict__ cnt,
-                                                  int *__restrict__ slots, int width,
-                                                  const long long *hash_total, long long cap_ent, int *overflow) {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= cv.nv) return;
+template <int QG>
+__global__ void __launch_bounds__(QUERY_T) k_query_vt(CollView cv, const float4 *__restrict__ x0,
+                                                      const float4 *__restrict__ x1, const float4 *__restrict__ tlo,
+                                                      const float4 *__restrict__ thi, const int4 *__restrict__ tcell,
+                                                      const GridParams *gp, float dhat, unsigned int mask,
+                                                      const int *__restrict__ bcnt, const int *__restrict__ bstart,
+                                                      const unsigned long long *__restrict__ ekey,
+                                                      const int *__restrict__ eprim, int *__restrict__ cnt,
+                                                      int *__restrict__ slots, int width,
+                                                      const long long *hash_total, long long cap_ent, int *overflow) {
+    auto grp = cg::tiled_partition<QG>(cg::this_thread_block());
+    const int gl = (int)grp.thread_rank();
+    const int v = (blockIdx.x * blockDim.x + threadIdx.x) / QG;
+    if (v >= cv.nv) return;  // uniform per group
     if (*hash_total > cap_ent) {  // table not filled: produce nothing
-        cnt[v] = 0;
+        if (gl == 0) cnt[v] = 0;
         return;
     }
     float inv = gp->inv_cell;
@@ -182,38 +204,55 @@ __global__ void __launch_bounds__(128) k_query_vt(CollView cv, const float4 *__r
     int3 clo, chi;
     cell_range(lo, hi, dhat, inv, clo, chi);
     if ((long long)(chi.x - clo.x + 1) * (chi.y - clo.y + 1) * (chi.z - clo.z + 1) > MAX_CELLS_PER_PRIM) {
-        cnt[v] = 0;
-        atomicOr(overflow, OVF_CELLS);
+        if (gl == 0) {
+            cnt[v] = 0;
+            atomicOr(overflow, OVF_CELLS);
+        }
         return;
     }
-    bool vfix = v >= cv.nc;
+    const bool vfix = v >= cv.nc;
     int *row = slots + (size_t)v * width;
     int c = 0;
     for (int z = clo.z; z <= chi.z; ++z)
         for (int y = clo.y; y <= chi.y; ++y)
             for (int x = clo.x; x <= chi.x; ++x) {
-                unsigned long long k = cell_key(x, y, z);
-                unsigned int b = hash_key(k, mask);
-                int e0 = bstart[b], e1 = e0 + bcnt[b];
-                for (int e = e0; e < e1; ++e) {
-                    if (ekey[e] != k) continue;
-                    int t = eprim[e];
-                    int4 tl = tcell[t];
-                    if (x != max(clo.x, tl.x) || y != max(clo.y, tl.y) || z != max(clo.z, tl.z)) continue;
-                    int4 T = cv.tri[t];
-                    if (T.x == v || T.y == v || T.z == v) continue;
-                    if (vfix && T.x >= cv.nc && T.y >= cv.nc && T.z >= cv.nc) continue;
-                    if (!box_overlap(lo, hi, f3(tlo[t]), f3(thi[t]), dhat)) continue;
-                    slot_insert(row, width, c, t);
-                    ++c;
+                const unsigned long long k = cell_key(x, y, z);
+                const unsigned int b = hash_key(k, mask);
+                const int e0 = bstart[b], e1 = e0 + bcnt[b];
+                for (int eb = e0; eb < e1; eb += QG) {
+                    const int e = eb + gl;
+                    bool cand = false;
+                    int t = 0;
+                    if (e < e1 && ekey[e] == k) {
+                        t = eprim[e];
+                        int4 tl = tcell[t];
+                        if (x == max(clo.x, tl.x) && y == max(clo.y, tl.y) && z == max(clo.z, tl.z)) {
+                            int4 T = cv.tri[t];
+                            cand = T.x != v && T.y != v && T.z != v &&
+                                   !(vfix && T.x >= cv.nc && T.y >= cv.nc && T.z >= cv.nc) &&
+                                   box_overlap(lo, hi, f3(tlo[t]), f3(thi[t]), dhat);
+                        }
+                    }
+                    const unsigned m = grp.ballot(cand);
+                    if (cand) {
+                        int slot = c + __popc(m & ((1u << gl) - 1u));
+                        if (slot < width) row[slot] = t;
+                    }
+                    c += __popc(m);
                 }
             }
-    cnt[v] = c;
-    if (c > width) atomicOr(overflow, OVF_SLOTS);
+    grp.sync();
+    if (gl == 0) {
+        sort_row(row, min(c, width));
+        cnt[v] = c;
+        if (c > width) atomicOr(overflow, OVF_SLOTS);
+    }
 }
 
-// EE: primary = edge e, secondary = edge f > e.
-__global__ void __launch_bounds__(128) k_query_ee(CollView cv, const float4 *__restrict__ elo,
+// EE: primary = edge e, secondary = edge f > e; one thread per edge (the
+// edge buckets are short and half their entries fail f > e at once, so the
+// grouped scan of the VT query does not pay here: measured slower).
+__global__ void __launch_bounds__(QUERY_T) k_query_ee(CollView cv, const float4 *__restrict__ elo,
                                                   const float4 *__restrict__ ehi, const int4 *__restrict__ ecell,
                                                   const GridParams *gp, float dhat, unsigned int mask,
                                                   const int *__restrict__ bcnt, const int *__restrict__ bstart,
@@ -521,9 +560,9 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
     // ---- VT candidates
     if (prof) prof->begin(s, "bp_query_vt", 0.0);
     if (cv.nv) {
-        k_query_vt<<<nblk(cv.nv, 128), 128, 0, s>>>(cv, x0, x1, tlo, thi, tcell, gp, dhat, (unsigned)(T_vt - 1),
-                                                    bcnt[0], bstart[0], ekey[0], eprim[0], cnt_v, slots_vt, w_vt,
-                                                    tot + 0, cap_ent, overflow);
+        k_query_vt<QG_VT><<<nblk((long long)cv.nv * QG_VT, QUERY_T), QUERY_T, 0, s>>>(
+            cv, x0, x1, tlo, thi, tcell, gp, dhat, (unsigned)(T_vt - 1), bcnt[0], bstart[0], ekey[0], eprim[0], cnt_v,
+            slots_vt, w_vt, tot + 0, cap_ent, overflow);
         PDC_LAUNCH_CK();
     }
     exclusive_scan(s, cnt_v, off_v, cv.nv, scratch, tot + 2);
@@ -536,9 +575,9 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
     // ---- EE candidates
     if (prof) prof->begin(s, "bp_query_ee", 0.0);
     if (cv.ne) {
-        k_query_ee<<<nblk(cv.ne, 128), 128, 0, s>>>(cv, elo, ehi, ecell, gp, dhat, (unsigned)(T_ee - 1), bcnt[1],
-                                                    bstart[1], ekey[1], eprim[1], cnt_e, slots_ee, w_ee, tot + 1,
-                                                    cap_ent, overflow);
+        k_query_ee<<<nblk(cv.ne, QUERY_T), QUERY_T, 0, s>>>(
+            cv, elo, ehi, ecell, gp, dhat, (unsigned)(T_ee - 1), bcnt[1], bstart[1], ekey[1], eprim[1], cnt_e,
+            slots_ee, w_ee, tot + 1, cap_ent, overflow);
         PDC_LAUNCH_CK();
     }
     exclusive_scan(s, cnt_e, off_e, cv.ne, scratch, tot + 3);

@@ -290,19 +290,35 @@ __device__ float3 start_dir(int kind, const float4 a0[4], const float c[4]) {
     return l > 1e-30f ? (1.f / l) * nn : make_float3(0.f, 0.f, 1.f);
 }
 
-__device__ inline void pair_ids(const CollView &cv, const int2 *vt, const int2 *ee, long long nvt, long long idx,
+// Index guard: an entry of a device-built list that lies outside the current
+// topology sets a bit here and is skipped (no access through it); the host
+// reads the word after each step and fails the step.
+__device__ unsigned int g_pair_guard;
+enum GuardBits { GUARD_PAIR = 1, GUARD_WATCH = 2, GUARD_NEAR = 4, GUARD_ACTIVE = 8 };
+
+__device__ inline bool pair_ids(const CollView &cv, const int2 *vt, const int2 *ee, long long nvt, long long idx,
                                 int ids[4], int &kind) {
+    ids[0] = ids[1] = ids[2] = ids[3] = 0;
     if (idx < nvt) {
         int2 p = vt[idx];
+        kind = 0;
+        if (p.x < 0 || p.x >= cv.nv || p.y < 0 || p.y >= cv.nt) {
+            atomicOr(&g_pair_guard, GUARD_PAIR);
+            return false;
+        }
         int4 T = cv.tri[p.y];
         ids[0] = p.x; ids[1] = T.x; ids[2] = T.y; ids[3] = T.z;
-        kind = 0;
     } else {
         int2 p = ee[idx - nvt];
+        kind = 1;
+        if (p.x < 0 || p.x >= cv.ne || p.y < 0 || p.y >= cv.ne) {
+            atomicOr(&g_pair_guard, GUARD_PAIR);
+            return false;
+        }
         int2 E = cv.edge[p.x], F = cv.edge[p.y];
         ids[0] = E.x; ids[1] = E.y; ids[2] = F.x; ids[3] = F.y;
-        kind = 1;
     }
+    return true;
 }
 
 __device__ inline float ndb_weight(const CollParams &P, int a) {
@@ -360,7 +376,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const in
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
         int ids[4], kind;
-        pair_ids(cv, vt, ee, nvt, idx, ids, kind);
+        if (!pair_ids(cv, vt, ee, nvt, idx, ids, kind)) continue;
         unsigned char st = 0;
         if (ovt) {
             long long j;
@@ -384,13 +400,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const in
     }
 }
 
-// mode 0: store each pair's closest distance on xm and collect the active
-//         states into the active list;
-// mode 1: partial CCD update then collect.  A pair whose closest distance on
-//         xm exceeds dhat + (largest displacement on side 1) + (largest on
-//         side 2) cannot satisfy Q <= dhat |d0| at any sample (|d1 - d0| is
-//         bounded by those displacements), so it is set inactive without
-//         evaluating the samples.
 // After a full CCD: store each pair's closest distance on x^- (the partial-CCD
 // filter's d0; x^- is fixed for the step) and rebuild the active list from
 // the pair states, with closest points and start directions on x^-.
@@ -409,9 +418,8 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs_collect(CollView cv, con
         long long idx = base + (threadIdx.x & 31);
         bool want = false;
         ActivePair ap;
-        if (idx < n) {
-            int ids[4], kind;
-            pair_ids(cv, vt, ee, nvt, idx, ids, kind);
+        int ids[4], kind;
+        if (idx < n && pair_ids(cv, vt, ee, nvt, idx, ids, kind)) {
             unsigned char st = kind == 0 ? st_vt[idx] : st_ee[idx - nvt];
             float4 a0[4];
             for (int i = 0; i < 4; ++i) a0[i] = xm[ids[i]];
@@ -526,10 +534,11 @@ __global__ void __launch_bounds__(256) k_pccd_filter(CollView cv, const int2 *__
         long long t = base + (threadIdx.x & 31);
         bool is_near = false, keep = false;
         int idx = 0;
-        if (t < n) {
-            idx = full ? (int)t : watch[t];
-            int ids[4], kind;
-            pair_ids(cv, vt, ee, nvt, idx, ids, kind);
+        int ids[4], kind;
+        if (t < n) idx = full ? (int)t : watch[t];
+        bool valid = t < n && idx >= 0 && idx < nvt + *nee_p;
+        if (t < n && !valid) atomicOr(&g_pair_guard, GUARD_WATCH);
+        if (valid && pair_ids(cv, vt, ee, nvt, idx, ids, kind)) {
             float d0 = kind == 0 ? d0_vt[idx] : d0_ee[idx - nvt];
             // |d1 - d0| at any sample is at most the largest relative
             // displacement between a vertex of side 1 and one of side 2
@@ -559,6 +568,7 @@ __global__ void __launch_bounds__(256) k_pccd_filter(CollView cv, const int2 *__
 // reset when not) and the active list.
 __global__ void __launch_bounds__(256) k_pccd_test(CollView cv, const int2 *__restrict__ vt,
                                                    const int2 *__restrict__ ee, const long long *nvt_p,
+                                                   const long long *nee_p,
                                                    unsigned char *st_vt, unsigned char *st_ee,
                                                    const float4 *__restrict__ xm, const float4 *__restrict__ xp,
                                                    CollParams P, const int *__restrict__ near,
@@ -572,10 +582,11 @@ __global__ void __launch_bounds__(256) k_pccd_test(CollView cv, const int2 *__re
         long long t = base + (threadIdx.x & 31);
         bool want = false;
         ActivePair ap;
-        if (t < n) {
-            int idx = near[t];
-            int ids[4], kind;
-            pair_ids(cv, vt, ee, nvt, idx, ids, kind);
+        int ids[4], kind;
+        int idx = t < n ? near[t] : -1;
+        bool valid = idx >= 0 && idx < nvt + *nee_p;
+        if (t < n && !valid) atomicOr(&g_pair_guard, GUARD_NEAR);
+        if (valid && pair_ids(cv, vt, ee, nvt, idx, ids, kind)) {
             unsigned char *stp = kind == 0 ? st_vt + idx : st_ee + (idx - nvt);
             unsigned char st = *stp;
             float4 a0[4], a1[4];
@@ -614,6 +625,10 @@ __global__ void k_contact(CollView cv, const ActivePair *__restrict__ act, const
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         ActivePair ap = act[i];
         int ids[4] = {ap.ids.x, ap.ids.y, ap.ids.z, ap.ids.w};
+        if (min(min(ids[0], ids[1]), min(ids[2], ids[3])) < 0 || max(max(ids[0], ids[1]), max(ids[2], ids[3])) >= cv.nv) {
+            atomicOr(&g_pair_guard, GUARD_ACTIVE);
+            continue;
+        }
         float c[4] = {ap.c.x, ap.c.y, ap.c.z, ap.c.w};
         float3 n0 = make_float3(ap.n0w.x, ap.n0w.y, ap.n0w.z);
         float w = ap.n0w.w;
@@ -712,6 +727,14 @@ inline int nblk(long long n, int b) { return (int)std::min<long long>((n + b - 1
 
 }  // namespace
 
+unsigned int pair_guard_take(cudaStream_t s) {
+    unsigned int v = 0, zero = 0;
+    PDC_CK(cudaMemcpyFromSymbolAsync(&v, g_pair_guard, sizeof(v), 0, cudaMemcpyDeviceToHost, s));
+    PDC_CK(cudaStreamSynchronize(s));
+    if (v) PDC_CK(cudaMemcpyToSymbol(g_pair_guard, &zero, sizeof(zero)));
+    return v;
+}
+
 void launch_full_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *x0, const float4 *x1,
                      const CollParams &P, bool merge, unsigned long long *toi_min) {
     int c = bp.cur, o = c ^ 1;
@@ -751,7 +774,7 @@ void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, cons
     PDC_LAUNCH_CK();
     if (bp.prof) bp.prof->end(s);
     if (bp.prof) bp.prof->begin(s, "pccd_test", 0.0);
-    k_pccd_test<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.st_vt[c],
+    k_pccd_test<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c], bp.st_vt[c],
                                                      bp.st_ee[c], xm, xp, P, bp.near, bp.pccd, bp.cap_pairs, act,
                                                      cap_act, n_act, overflow);
     PDC_LAUNCH_CK();

@@ -229,9 +229,16 @@ __device__ inline float3 ell_apply(const ClothView &c, int i, const float4 *__re
     const int *col = c.ell_col + i;
     const float *val = c.ell_val + i;
     if constexpr (WMAX > 0) {
+        if (c.ell_dcol) {  // 16-bit offsets: 6 instead of 8 bytes per entry
+            const short *dc = c.ell_dcol + i;
 #pragma unroll
-        for (int k = 0; k < WMAX; ++k)
-            if (k < c.ell_w) acc = acc + __ldg(val + (size_t)k * c.n) * f3(v[__ldg(col + (size_t)k * c.n)]);
+            for (int k = 0; k < WMAX; ++k)
+                if (k < c.ell_w) acc = acc + __ldg(val + (size_t)k * c.n) * f3(v[i + (int)__ldg(dc + (size_t)k * c.n)]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < WMAX; ++k)
+                if (k < c.ell_w) acc = acc + __ldg(val + (size_t)k * c.n) * f3(v[__ldg(col + (size_t)k * c.n)]);
+        }
     } else {
         for (int k = 0; k < c.ell_w; ++k) acc = acc + val[(size_t)k * c.n] * f3(v[col[(size_t)k * c.n]]);
     }
@@ -327,6 +334,58 @@ __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const floa
     if (xout && sc) block_max(mx, &sc->dxmax);
 }
 
+// The Chebyshev step with halo staging: the block's own rows of delta_k and
+// the distinct rows its ELL entries reach outside the block are loaded into
+// shared memory once (all loads independent), and every neighbour gather of
+// the row update then reads shared memory through the entry's staged slot.
+template <int WMAX>
+__global__ void __launch_bounds__(STAGE_ROWS) k_cheb_step_staged(
+    const ClothView c, const float *__restrict__ cw, const float4 *__restrict__ r, const float4 *__restrict__ din,
+    const float4 *__restrict__ dprev, float4 *__restrict__ dout, float alpha, float beta, const float4 *x,
+    float4 *xout, float4 *xprev, float w_acc, const float4 *__restrict__ xs, float4 *__restrict__ xabs, Scalars *sc) {
+    extern __shared__ float4 sd[];
+    const int a = blockIdx.x * STAGE_ROWS;
+    const int i = a + threadIdx.x;
+    sd[threadIdx.x] = i < c.n ? din[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int h0 = c.halo_off[blockIdx.x], nh = c.halo_off[blockIdx.x + 1] - h0;
+    for (int q = threadIdx.x; q < nh; q += STAGE_ROWS) sd[STAGE_ROWS + q] = din[__ldg(c.halo_rows + h0 + q)];
+    __syncthreads();
+    float mx = 0.f;
+    if (i < c.n) {
+        float3 dn = make_float3(0.f, 0.f, 0.f);
+        if (c.is_free[i]) {
+            float3 di = f3(sd[threadIdx.x]);
+            float D = c.hdiag[i] + (cw ? cw[i] : 0.f);
+            float3 acc = f3(r[i]) - D * di;
+            const float *val = c.ell_val + i;
+            const unsigned short *lc = c.ell_lcol + i;
+#pragma unroll
+            for (int k = 0; k < WMAX; ++k)
+                if (k < c.ell_w) acc = acc - __ldg(val + (size_t)k * c.n) * f3(sd[__ldg(lc + (size_t)k * c.n)]);
+            float3 dd = (beta / D) * acc;
+            if (alpha != 0.f) dd = dd + alpha * (di - f3(dprev[i]));
+            dn = di + dd;
+        }
+        dout[i] = f4(dn);
+        if (xout) {
+            float3 xo = f3(x[i]);
+            float3 xn = xo + dn;
+            if (xprev) {
+                if (c.is_free[i] && w_acc != 1.f) {
+                    float3 xp = f3(xprev[i]);
+                    xn = xp + w_acc * (xn - xp);
+                }
+                xprev[i] = f4(xo);
+            }
+            xout[i] = f4(xn);
+            if (xabs) xabs[i] = f4(f3(xs[i]) + xn);
+            float3 d = xn - xo;
+            mx = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z)));
+        }
+    }
+    if (xout && sc) block_max(mx, &sc->dxmax);
+}
+
 // Anderson mixing of the LG fixed-point map x -> G(x) = x + delta(x)
 // (history of depth m): with f_k = delta_k, g_k = x_k + delta_k and the
 // differences dF_j, dG_j of consecutive f and g, theta minimises
@@ -389,45 +448,60 @@ __global__ void __launch_bounds__(256) k_aa_gram(int n, const unsigned char *__r
 }
 
 // Solves the regularised normal equations (one thread, FP64) into theta.
-__global__ void k_aa_solve(int ncol, const double *__restrict__ Gb, float *__restrict__ theta) {
+// theta solving the (regularised) normal equations of the mixing
+// least-squares problem by Cholesky; M (= the column count) is a template
+// parameter so the tiny system lives in registers.
+template <int M>
+__global__ void k_aa_solve(const double *__restrict__ Gb, float *__restrict__ theta) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double A[AA_MAX][AA_MAX], b[AA_MAX];
+    double A[M][M], b[M];
     int e = 0;
     double tr = 0.0;
-    for (int j = 0; j < ncol; ++j) {
-        for (int l = j; l < ncol; ++l) {
-            A[j][l] = A[l][j] = Gb[e++];
-        }
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+#pragma unroll
+        for (int l = j; l < M; ++l) A[j][l] = A[l][j] = Gb[e + l - j];
+        e += M - j;
         b[j] = Gb[e++];
         tr += A[j][j];
     }
-    for (int j = 0; j < ncol; ++j) A[j][j] += 1e-10 * tr + 1e-300;
-    // Cholesky
+#pragma unroll
+    for (int j = 0; j < M; ++j) A[j][j] += 1e-10 * tr + 1e-300;
     bool ok = tr > 0.0;
-    for (int j = 0; j < ncol && ok; ++j) {
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
         double d = A[j][j];
+#pragma unroll
         for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
-        if (!(d > 0.0)) { ok = false; break; }
-        d = sqrt(d);
+        ok = ok && d > 0.0;
+        d = sqrt(fmax(d, 1e-300));
         A[j][j] = d;
-        for (int q = j + 1; q < ncol; ++q) {
+        double inv = 1.0 / d;
+#pragma unroll
+        for (int q = j + 1; q < M; ++q) {
             double v = A[q][j];
+#pragma unroll
             for (int k = 0; k < j; ++k) v -= A[q][k] * A[j][k];
-            A[q][j] = v / d;
+            A[q][j] = v * inv;
         }
     }
-    double y[AA_MAX], x[AA_MAX];
-    for (int j = 0; j < ncol; ++j) {
+    double y[M], x[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
         double v = b[j];
+#pragma unroll
         for (int k = 0; k < j; ++k) v -= A[j][k] * y[k];
-        y[j] = ok ? v / A[j][j] : 0.0;
+        y[j] = v / A[j][j];
     }
-    for (int j = ncol - 1; j >= 0; --j) {
+#pragma unroll
+    for (int j = M - 1; j >= 0; --j) {
         double v = y[j];
-        for (int k = j + 1; k < ncol; ++k) v -= A[k][j] * x[k];
-        x[j] = ok ? v / A[j][j] : 0.0;
+#pragma unroll
+        for (int k = j + 1; k < M; ++k) v -= A[k][j] * x[k];
+        x[j] = v / A[j][j];
     }
-    for (int j = 0; j < AA_MAX; ++j) theta[j] = (j < ncol && ok && isfinite(x[j])) ? (float)x[j] : 0.f;
+#pragma unroll
+    for (int j = 0; j < AA_MAX; ++j) theta[j] = (j < M && ok && isfinite(x[j < M ? j : 0])) ? (float)x[j < M ? j : 0] : 0.f;
 }
 
 // x_{k+1} = g_k - sum_j theta_j dG_j on free vertices.
@@ -522,7 +596,17 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
         int b = nblk(c.n, 256);
 #define PDC_CHEB(W)                                                                                   \
     k_cheb_step<W><<<b, 256, 0, s>>>(c, cw, r, din, dprev, dout, alpha, beta, x, xout, xprev, w_acc, xs, xabs, sc)
-        if (c.ell_w <= 8) PDC_CHEB(8);
+        if (c.ell_lcol && c.ell_w <= 16) {
+            size_t sm = sizeof(float4) * (STAGE_ROWS + (size_t)c.halo_max);
+            int bs = (c.n + STAGE_ROWS - 1) / STAGE_ROWS;
+#define PDC_CHEB_ST(W)                                                                                \
+    k_cheb_step_staged<W><<<bs, STAGE_ROWS, sm, s>>>(c, cw, r, din, dprev, dout, alpha, beta, x, xout, xprev, w_acc, \
+                                                     xs, xabs, sc)
+            if (c.ell_w <= 8) PDC_CHEB_ST(8);
+            else if (c.ell_w <= 12) PDC_CHEB_ST(12);
+            else PDC_CHEB_ST(16);
+#undef PDC_CHEB_ST
+        } else if (c.ell_w <= 8) PDC_CHEB(8);
         else if (c.ell_w <= 12) PDC_CHEB(12);
         else if (c.ell_w <= 16) PDC_CHEB(16);
         else PDC_CHEB(0);
@@ -538,7 +622,16 @@ void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4
     PDC_CK(cudaMemsetAsync(Gb, 0, sizeof(double) * (AA_MAX * (AA_MAX + 3) / 2 + AA_MAX), s));
     k_aa_gram<<<nblk(n, 256), 256, 0, s>>>(n, is_free, delta, x, fprev, gprev, dF, dG, slot, have_prev, ncol, Gb);
     if (ncol > 0) {
-        k_aa_solve<<<1, 32, 0, s>>>(ncol, Gb, theta);
+        switch (ncol) {
+            case 1: k_aa_solve<1><<<1, 32, 0, s>>>(Gb, theta); break;
+            case 2: k_aa_solve<2><<<1, 32, 0, s>>>(Gb, theta); break;
+            case 3: k_aa_solve<3><<<1, 32, 0, s>>>(Gb, theta); break;
+            case 4: k_aa_solve<4><<<1, 32, 0, s>>>(Gb, theta); break;
+            case 5: k_aa_solve<5><<<1, 32, 0, s>>>(Gb, theta); break;
+            case 6: k_aa_solve<6><<<1, 32, 0, s>>>(Gb, theta); break;
+            case 7: k_aa_solve<7><<<1, 32, 0, s>>>(Gb, theta); break;
+            default: k_aa_solve<8><<<1, 32, 0, s>>>(Gb, theta); break;
+        }
         k_aa_mix<<<nblk(n, 256), 256, 0, s>>>(n, is_free, x, dG, ncol, theta, x, xs, xabs);
     }
     PDC_LAUNCH_CK();

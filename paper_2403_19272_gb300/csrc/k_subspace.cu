@@ -292,76 +292,80 @@ __global__ void k_apply_inverse(SubspaceView S, const int *n_cv, const T *__rest
     }
 }
 
-// dA = sum_v cw_v U_v U_v^T over the contact list (leading r_c columns).
+// dA = sum_v cw_v U_v U_v^T over the contact list (leading r_c columns), in
+// FP64: NDB weights reach 2^a_max k, and single-precision sums of those terms
+// would bury the elastic part A0 of the reduced matrix in rounding noise.
 constexpr int SYRK_T = 256;
-constexpr int SYRK_MAXE = 64;  // entries per thread: r_c^2 <= 256*64 -> r_c <= 128
-template <class TU>
+template <class TU, int E>  // E entries per thread: r_c^2 <= 256 E
 __global__ void __launch_bounds__(SYRK_T) k_syrk(SubspaceView S, const TU *__restrict__ U, const int *__restrict__ list,
-                                                 const int *n_cv, const float *__restrict__ cw, float *__restrict__ dA) {
-    __shared__ float s_u[128];
-    __shared__ float s_w;
+                                                 const int *n_cv, const float *__restrict__ cw, double *__restrict__ dA) {
+    __shared__ double s_u[128];
+    __shared__ double s_w;
     int nc = n_cv ? *n_cv : 0;
     int r = S.r_c;
     if (nc == 0 || r == 0) return;
     int ne = r * r;
-    float acc[SYRK_MAXE];
+    double acc[E];
 #pragma unroll
-    for (int p = 0; p < SYRK_MAXE; ++p) acc[p] = 0.f;
+    for (int p = 0; p < E; ++p) acc[p] = 0.0;
     for (int c = blockIdx.x; c < nc; c += gridDim.x) {
         int v = list[c];
         __syncthreads();
-        if (threadIdx.x < r) s_u[threadIdx.x] = tofloat<TU>(U[(long long)v * S.ld + threadIdx.x]);
-        if (threadIdx.x == 0) s_w = cw[v];
+        if (threadIdx.x < r) s_u[threadIdx.x] = (double)tofloat<TU>(U[(long long)v * S.ld + threadIdx.x]);
+        if (threadIdx.x == 0) s_w = (double)cw[v];
         __syncthreads();
-        float w = s_w;
+        double w = s_w;
 #pragma unroll
-        for (int p = 0; p < SYRK_MAXE; ++p) {
+        for (int p = 0; p < E; ++p) {
             int e = threadIdx.x + p * SYRK_T;
             if (e < ne) {
                 int i = e / r, j = e % r;
-                acc[p] = fmaf(w * s_u[i], s_u[j], acc[p]);
+                acc[p] = fma(w * s_u[i], s_u[j], acc[p]);
             }
         }
     }
 #pragma unroll
-    for (int p = 0; p < SYRK_MAXE; ++p) {
+    for (int p = 0; p < E; ++p) {
         int e = threadIdx.x + p * SYRK_T;
-        if (e < ne && acc[p] != 0.f) atomicAdd(&dA[e], acc[p]);
+        if (e < ne && acc[p] != 0.0) atomicAdd(&dA[e], acc[p]);
     }
 }
 
-// Cholesky factorisation and solve of (A0[:r,:r] + dA) q = g in one CTA.
-template <class T>
-__global__ void __launch_bounds__(256) k_chol_solve(SubspaceView S, const int *n_cv, const float *__restrict__ dA,
+// Cholesky factorisation and solve of (A0[:r,:r] + dA) q = g in one CTA, in
+// FP64.  A non-positive pivot sets the flag and the correction is dropped
+// (q = 0: the sweeps still run) instead of dividing by a tiny pivot.
+__global__ void __launch_bounds__(256) k_chol_solve(SubspaceView S, const int *n_cv, const double *__restrict__ dA,
                                                     const double *__restrict__ g, float *__restrict__ q, int *flag) {
     extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_bad;
     if (!(n_cv && *n_cv > 0)) return;
     int r = S.r_c;
     if (r == 0) return;
-    T *A = reinterpret_cast<T *>(smem_raw);  // [r][r]
-    T *b = A + r * r;                         // [r][3]
+    double *A = reinterpret_cast<double *>(smem_raw);  // [r][r]
+    double *b = A + r * r;                              // [r][3]
     int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) s_bad = 0;
     for (int e = tid; e < r * r; e += nt) {
         int i = e / r, j = e % r;
-        A[e] = (T)S.A0[(long long)i * S.ld + j] + (T)dA[e];
+        A[e] = S.A0[(long long)i * S.ld + j] + dA[e];
     }
-    for (int e = tid; e < r * 3; e += nt) b[e] = (T)g[e];
+    for (int e = tid; e < r * 3; e += nt) b[e] = g[e];
     __syncthreads();
     for (int k = 0; k < r; ++k) {
         if (tid == 0) {
-            T d = A[k * r + k];
-            if (!(d > (T)0)) {
-                atomicOr(flag, 1);
-                d = (T)1e-30;
+            double d = A[k * r + k];
+            if (!(d > 0.0) || !isfinite(d)) {
+                s_bad = 1;
+                d = 1.0;
             }
             A[k * r + k] = sqrt(d);
         }
         __syncthreads();
-        T dk = A[k * r + k];
+        double dk = A[k * r + k];
         for (int i = k + 1 + tid; i < r; i += nt) A[i * r + k] /= dk;
         __syncthreads();
         for (int i = k + 1 + tid; i < r; i += nt) {
-            T lik = A[i * r + k];
+            double lik = A[i * r + k];
             for (int j = k + 1; j <= i; ++j) A[i * r + j] -= lik * A[j * r + k];
         }
         __syncthreads();
@@ -386,7 +390,8 @@ __global__ void __launch_bounds__(256) k_chol_solve(SubspaceView S, const int *n
         }
         __syncthreads();
     }
-    for (int e = tid; e < r * 3; e += nt) q[e] = (float)b[e];
+    if (s_bad && tid == 0) atomicOr(flag, 1);
+    for (int e = tid; e < r * 3; e += nt) q[e] = s_bad ? 0.f : (float)b[e];
 }
 
 // dout_i = din_i + sum_j U[i][j] q_j: one warp per row, lane l owns columns
@@ -531,10 +536,13 @@ void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, con
 void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const int *n_cv, const float *cw,
                  SubspaceWork &W) {
     if (S.r_c == 0) return;
-    PDC_CK(cudaMemsetAsync(W.dA, 0, sizeof(float) * S.r_c * S.r_c, s));
+    PDC_CK(cudaMemsetAsync(W.dA, 0, sizeof(double) * S.r_c * S.r_c, s));
     with_basis(S, false, [&](auto *U) {
         using TU = std::remove_const_t<std::remove_pointer_t<decltype(U)>>;
-        k_syrk<TU><<<152, SYRK_T, 0, s>>>(S, U, list, n_cv, cw, W.dA);
+        int ne = S.r_c * S.r_c;
+        if (ne <= 4 * SYRK_T) k_syrk<TU, 4><<<152, SYRK_T, 0, s>>>(S, U, list, n_cv, cw, W.dA);
+        else if (ne <= 16 * SYRK_T) k_syrk<TU, 16><<<152, SYRK_T, 0, s>>>(S, U, list, n_cv, cw, W.dA);
+        else k_syrk<TU, 64><<<152, SYRK_T, 0, s>>>(S, U, list, n_cv, cw, W.dA);
     });
     PDC_LAUNCH_CK();
 }
@@ -548,14 +556,9 @@ void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv
         else
             k_apply_inverse<float><<<(thr + 255) / 256, 256, 0, s>>>(S, n_cv, S.A0inv32, W.g, W.q);
     }
-    if (S.r_c > 0) {
-        if (mixed) {
-            size_t sm = sizeof(double) * (S.r_c * S.r_c + S.r_c * 3);
-            k_chol_solve<double><<<1, 256, sm, s>>>(S, n_cv, W.dA, W.g, W.q, W.flag);
-        } else {
-            size_t sm = sizeof(float) * (S.r_c * S.r_c + S.r_c * 3);
-            k_chol_solve<float><<<1, 256, sm, s>>>(S, n_cv, W.dA, W.g, W.q, W.flag);
-        }
+    if (S.r_c > 0) {  // FP64 in both forms (see k_syrk)
+        size_t sm = sizeof(double) * (S.r_c * S.r_c + S.r_c * 3);
+        k_chol_solve<<<1, 256, sm, s>>>(S, n_cv, W.dA, W.g, W.q, W.flag);
     }
     PDC_LAUNCH_CK();
 }
@@ -590,8 +593,7 @@ void launch_linear_residual(cudaStream_t s, const ClothView &c, const float *cw,
 
 void set_chol_smem_limits() {
     size_t mx = sizeof(double) * (128 * 128 + 128 * 3);
-    PDC_CK(cudaFuncSetAttribute(k_chol_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
-    PDC_CK(cudaFuncSetAttribute(k_chol_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+    PDC_CK(cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
 }
 
 }  // namespace pdc

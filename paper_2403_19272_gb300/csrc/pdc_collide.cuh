@@ -129,6 +129,9 @@ void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, cons
 // Collision springs of the active list at positions x: cw += w, cf += w (y - x).
 void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, const int *n_act, int cap_act,
                     const float4 *x, float dhat, float *cw, float4 *cf);
+// Reads and clears the index-guard word of the pair kernels (0: no entry of a
+// pair, watch, near or active list pointed outside the topology).
+unsigned int pair_guard_take(cudaStream_t s);
 // Compact the cloth vertices with cw > 0.
 void launch_contact_list(cudaStream_t s, int n, const float *cw, int *list, int *count);
 

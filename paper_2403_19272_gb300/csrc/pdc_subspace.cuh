@@ -36,7 +36,7 @@ struct SubspaceWork {
     float *partial;    // [blocks][ld][3]
     double *g;         // [ld][3]
     float *q;          // [ld][3]
-    float *dA;         // [r_c][r_c] collision update of the reduced matrix
+    double *dA;        // [r_c][r_c] collision update of the reduced matrix (FP64)
     int *flag;         // factorisation status
 };
 

@@ -342,6 +342,25 @@ def test_one_step_parity_without_collisions(pc):
     cl.close()
 
 
+def test_one_step_parity_with_chebyshev_sweeps(pc):
+    # the benchmark's smoother (Jacobi-preconditioned Chebyshev steps, with
+    # the halo-staged kernel) converged per LG iteration gives the oracle's
+    # exact global solves
+    sc = wl.drape_sphere(side=40, with_sphere=False)
+    gp = params(pc, fixed_iters=1, warm_iters=2, max_outer=1, max_inner=3, solve_cycles=40, jacobi_sweeps=32,
+                sweep_kind=1, cheb_ratio=300.0, r_warm=64, r_reuse=64, d_hat=1e-3, collisions=0)
+    cl = pc.Cloth(sc, gp)
+    orc = pd.Oracle(sc, pd.Params(fixed_iters=True, warm_iters=2, max_outer=1, max_inner=3, dhat=1e-3,
+                                  collisions=False))
+    for k in range(3):
+        cl.step()
+        xo, vo, _ = orc.step()
+        xg, vg = cl.state()
+        assert np.max(np.abs(xg - xo)) <= 1e-5 * orc.model.L, k
+        orc.x, orc.v = xg.astype(np.float64), vg.astype(np.float64)
+    cl.close()
+
+
 def test_one_step_parity_config0_with_collision_pipeline(pc):
     """32x32 drape over the sphere with self-collision on: the whole step
     (warm start, full CCD, filter, partial CCD, line search)."""
