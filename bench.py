@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--cpu-sample-side", type=int, default=64)
     ap.add_argument("--sweeps", type=int, default=32, help="Chebyshev steps per LG iteration")
     ap.add_argument("--cheb-ratio", type=float, default=300.0, help="Chebyshev interval ratio b/a")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form comparison")
     ap.add_argument("--no-launch-count", action="store_true",
                     help="skip the CUDA activity trace (e.g. when running under ncu)")
     return ap.parse_args()
@@ -234,6 +235,73 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
                 launches=launches)
 
 
+def run_batched(pc, torch, steps=5, warmup=2, dev_index=0):
+    """Batched form (64 drapes of sides 16..192 over their own spheres, about
+    0.9 M vertices, FP32, 32 LG iterations per step): one batched handle
+    against the same 64 cloths stepped one after another on 64 handles.
+    Instances are placed 2 m apart so that none touches another."""
+    import numpy as np
+    import workloads as wl
+    scenes = wl.batched_drape()
+    p = pc.pdc_default_params()
+    for k, v in dict(fixed_iters=1, warm_iters=5, max_outer=1, max_inner=27, sweep_kind=1, jacobi_sweeps=16,
+                     cheb_ratio=300.0, r_warm=32, r_reuse=32, eig_iters=4, precision=0).items():
+        setattr(p, k, v)
+    shifted = []
+    for k, sc in enumerate(scenes):
+        d = np.array([2.0 * (k % 8), 2.0 * (k // 8), 0.0], np.float32)
+        obs = [(o.verts + d).astype(np.float32) for o in sc.obstacles]
+        shifted.append(((sc.verts + d).astype(np.float32), sc.tris, sc.pins, sc.density, sc.k_stretch, sc.k_bend,
+                        obs, [o.tris for o in sc.obstacles]))
+    stream = torch.cuda.Stream()
+    # one batched handle
+    t0 = time.time()
+    h, off = pc.pdc_create_batch([s[:6] for s in shifted], p, stream.cuda_stream)
+    for s in shifted:
+        for ov, ot in zip(s[6], s[7]):
+            pc.pdc_add_obstacle(h, ov, ot)
+    setup_b = time.time() - t0
+    for _ in range(warmup):
+        pc.pdc_step(h, p.dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        pc.pdc_step(h, p.dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / steps
+    pc.pdc_destroy(h)
+    # the same cloths on separate handles, stepped in turn on one stream
+    t0 = time.time()
+    hs = []
+    for s in shifted:
+        hh = pc.pdc_create(s[0], s[1], s[2], s[3], s[4], s[5], p, stream.cuda_stream)
+        for ov, ot in zip(s[6], s[7]):
+            pc.pdc_add_obstacle(hh, ov, ot)
+        hs.append(hh)
+    setup_s = time.time() - t0
+    for _ in range(warmup):
+        for hh in hs:
+            pc.pdc_step(hh, p.dt)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        for hh in hs:
+            pc.pdc_step(hh, p.dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1) / steps
+    for hh in hs:
+        pc.pdc_destroy(hh)
+    return {"workload": "64 drapes over their own spheres, sides 16..192 (%d vertices), FP32, 32 LG iterations "
+                        "per step, Chebyshev 16 steps per iteration, basis r=32" % int(off[-1]),
+            "instances": len(shifted), "vertices": int(off[-1]), "steps": steps,
+            "ms_per_step_batched": round(ms_b, 3), "ms_per_step_separate_handles": round(ms_s, 3),
+            "speedup": round(ms_s / ms_b, 2), "setup_s_batched": round(setup_b, 1),
+            "setup_s_separate": round(setup_s, 1)}
+
+
 def count_launches(torch, one_step, steps):
     """Kernels launched by the library (names beginning with k_) during
     `steps` steps, from torch.profiler's CUDA activity trace; None if the
@@ -384,6 +452,11 @@ def main():
                         "GBps": round(v["algo_bytes"] / max(v["total_ms"], 1e-9) / 1e6, 1)}
                     for k, v in forms[head]["kernels"].items()},
     }
+    if not a.no_batched and world == 1:
+        try:
+            line["batched"] = run_batched(pc, torch, dev_index=local)
+        except Exception as e:  # reported, not fatal for the headline
+            line["batched"] = {"error": str(e)[:200]}
     if not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a.cpu_sample_side)
     print(json.dumps(line))

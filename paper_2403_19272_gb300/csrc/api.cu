@@ -128,7 +128,7 @@ struct Accel {
     // collision springs, STAG_N iterations that do not lower the best
     // residual of the pass by 1% end the inner loop (the FP32 floor of a
     // nearly unstrained cloth, e.g. in free fall, lies above small targets)
-    static constexpr int STAG_N = 16;
+    static constexpr int STAG_N = 32;
     double stag_best = 0.0;
     int stag_count = 0;
     bool stagnated(double rho, bool springs) {
@@ -224,9 +224,6 @@ struct pdc_ctx {
     DevBuf<float> tri_w, hin_w, hin_slen, mh2, hdiag, ell_val;
     DevBuf<int> vt_off, vt_list, vh_off, vh_list, ell_col, pins_d;
     DevBuf<short> ell_dcol;
-    DevBuf<int> halo_off, halo_rows;
-    DevBuf<unsigned short> ell_lcol;
-    int halo_max = 0;
     DevBuf<unsigned char> is_free;
     int ell_w = 0;
     // pins
@@ -324,10 +321,6 @@ struct pdc_ctx {
         c.ell_w = ell_w;
         c.ell_col = ell_col;
         c.ell_dcol = ell_dcol.p;
-        c.halo_off = halo_off.p;
-        c.halo_rows = halo_rows.p;
-        c.ell_lcol = ell_lcol.p;
-        c.halo_max = halo_max;
         c.ell_val = ell_val;
         c.corner = corner;
         return c;
@@ -665,50 +658,6 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
         if (fits && !dcol.empty()) ell_dcol.upload(dcol, s);
         else ell_dcol.release();
     }
-    {  // halo staging for the sweeps: per block of rows, the distinct
-       // referenced rows outside the block and each entry's staged slot
-        int nb = (n + STAGE_ROWS - 1) / STAGE_ROWS;
-        std::vector<int> hoff(nb + 1, 0), hrows;
-        std::vector<unsigned short> lcol((size_t)ell_w * n, 0);
-        bool ok = ell_w > 0;
-        halo_max = 0;
-        for (int b = 0; b < nb && ok; ++b) {
-            int a = b * STAGE_ROWS, e = std::min(n, a + STAGE_ROWS);
-            std::vector<int> hs;
-            for (int i = a; i < e; ++i)
-                for (int k = 0; k < ell_w; ++k) {
-                    int j = ecol[(size_t)k * n + i];
-                    if (j < a || j >= e) hs.push_back(j);
-                }
-            std::sort(hs.begin(), hs.end());
-            hs.erase(std::unique(hs.begin(), hs.end()), hs.end());
-            if (STAGE_ROWS + (int)hs.size() > STAGE_MAX_SLOTS) {
-                ok = false;
-                break;
-            }
-            halo_max = std::max(halo_max, (int)hs.size());
-            for (int i = a; i < e; ++i)
-                for (int k = 0; k < ell_w; ++k) {
-                    int j = ecol[(size_t)k * n + i];
-                    int slot = (j >= a && j < e) ? j - a
-                                                 : STAGE_ROWS + (int)(std::lower_bound(hs.begin(), hs.end(), j) - hs.begin());
-                    lcol[(size_t)k * n + i] = (unsigned short)slot;
-                }
-            hrows.insert(hrows.end(), hs.begin(), hs.end());
-            hoff[b + 1] = (int)hrows.size();
-        }
-        if (ok) {
-            halo_off.upload(hoff, s);
-            if (hrows.empty()) hrows.push_back(0);
-            halo_rows.upload(hrows, s);
-            ell_lcol.upload(lcol, s);
-        } else {
-            halo_off.release();
-            halo_rows.release();
-            ell_lcol.release();
-            halo_max = 0;
-        }
-    }
     ell_val.upload(evalv, s);
     pins_d.upload(pins, s);
     std::vector<float4> pt(npins);
@@ -753,6 +702,7 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
     bad_d.alloc(1);
     umax_d.alloc(1);
     sflag.alloc(1);
+    sflag.zero(s);
     n_cv_d.zero(s);
     n_act_d.zero(s);
     contact_list.alloc(std::max(n, 1));
@@ -1152,6 +1102,7 @@ void pdc_ctx::step() {
     const bool relmode = P.tol_rel_residual > 0 && !fixed;
     const int cycles = std::max(P.solve_cycles, 1), sweeps = std::max(P.jacobi_sweeps, 0);
     st = pdc_stats();
+    sflag.zero(s);  // status bits of this step (factorisation, tensor-core waits)
     st.t_toi = 2.0;
     st.s_line_search = 1.0;
     auto t0 = std::chrono::steady_clock::now();

@@ -334,58 +334,6 @@ __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const floa
     if (xout && sc) block_max(mx, &sc->dxmax);
 }
 
-// The Chebyshev step with halo staging: the block's own rows of delta_k and
-// the distinct rows its ELL entries reach outside the block are loaded into
-// shared memory once (all loads independent), and every neighbour gather of
-// the row update then reads shared memory through the entry's staged slot.
-template <int WMAX>
-__global__ void __launch_bounds__(STAGE_ROWS) k_cheb_step_staged(
-    const ClothView c, const float *__restrict__ cw, const float4 *__restrict__ r, const float4 *__restrict__ din,
-    const float4 *__restrict__ dprev, float4 *__restrict__ dout, float alpha, float beta, const float4 *x,
-    float4 *xout, float4 *xprev, float w_acc, const float4 *__restrict__ xs, float4 *__restrict__ xabs, Scalars *sc) {
-    extern __shared__ float4 sd[];
-    const int a = blockIdx.x * STAGE_ROWS;
-    const int i = a + threadIdx.x;
-    sd[threadIdx.x] = i < c.n ? din[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int h0 = c.halo_off[blockIdx.x], nh = c.halo_off[blockIdx.x + 1] - h0;
-    for (int q = threadIdx.x; q < nh; q += STAGE_ROWS) sd[STAGE_ROWS + q] = din[__ldg(c.halo_rows + h0 + q)];
-    __syncthreads();
-    float mx = 0.f;
-    if (i < c.n) {
-        float3 dn = make_float3(0.f, 0.f, 0.f);
-        if (c.is_free[i]) {
-            float3 di = f3(sd[threadIdx.x]);
-            float D = c.hdiag[i] + (cw ? cw[i] : 0.f);
-            float3 acc = f3(r[i]) - D * di;
-            const float *val = c.ell_val + i;
-            const unsigned short *lc = c.ell_lcol + i;
-#pragma unroll
-            for (int k = 0; k < WMAX; ++k)
-                if (k < c.ell_w) acc = acc - __ldg(val + (size_t)k * c.n) * f3(sd[__ldg(lc + (size_t)k * c.n)]);
-            float3 dd = (beta / D) * acc;
-            if (alpha != 0.f) dd = dd + alpha * (di - f3(dprev[i]));
-            dn = di + dd;
-        }
-        dout[i] = f4(dn);
-        if (xout) {
-            float3 xo = f3(x[i]);
-            float3 xn = xo + dn;
-            if (xprev) {
-                if (c.is_free[i] && w_acc != 1.f) {
-                    float3 xp = f3(xprev[i]);
-                    xn = xp + w_acc * (xn - xp);
-                }
-                xprev[i] = f4(xo);
-            }
-            xout[i] = f4(xn);
-            if (xabs) xabs[i] = f4(f3(xs[i]) + xn);
-            float3 d = xn - xo;
-            mx = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z)));
-        }
-    }
-    if (xout && sc) block_max(mx, &sc->dxmax);
-}
-
 // Anderson mixing of the LG fixed-point map x -> G(x) = x + delta(x)
 // (history of depth m): with f_k = delta_k, g_k = x_k + delta_k and the
 // differences dF_j, dG_j of consecutive f and g, theta minimises
@@ -596,17 +544,7 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
         int b = nblk(c.n, 256);
 #define PDC_CHEB(W)                                                                                   \
     k_cheb_step<W><<<b, 256, 0, s>>>(c, cw, r, din, dprev, dout, alpha, beta, x, xout, xprev, w_acc, xs, xabs, sc)
-        if (c.ell_lcol && c.ell_w <= 16) {
-            size_t sm = sizeof(float4) * (STAGE_ROWS + (size_t)c.halo_max);
-            int bs = (c.n + STAGE_ROWS - 1) / STAGE_ROWS;
-#define PDC_CHEB_ST(W)                                                                                \
-    k_cheb_step_staged<W><<<bs, STAGE_ROWS, sm, s>>>(c, cw, r, din, dprev, dout, alpha, beta, x, xout, xprev, w_acc, \
-                                                     xs, xabs, sc)
-            if (c.ell_w <= 8) PDC_CHEB_ST(8);
-            else if (c.ell_w <= 12) PDC_CHEB_ST(12);
-            else PDC_CHEB_ST(16);
-#undef PDC_CHEB_ST
-        } else if (c.ell_w <= 8) PDC_CHEB(8);
+        if (c.ell_w <= 8) PDC_CHEB(8);
         else if (c.ell_w <= 12) PDC_CHEB(12);
         else if (c.ell_w <= 16) PDC_CHEB(16);
         else PDC_CHEB(0);

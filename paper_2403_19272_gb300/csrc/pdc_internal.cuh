@@ -108,15 +108,6 @@ struct ClothView {
     int ell_w;
     const int *ell_col;    // [ell_w][n]
     const short *ell_dcol; // [ell_w][n] column minus row when every offset fits 16 bits (else NULL)
-    // halo staging of the sweeps (NULL when off): rows are taken in blocks
-    // of STAGE_ROWS; block b's neighbour rows outside the block are
-    // halo_rows[halo_off[b] .. halo_off[b+1]); ell_lcol [ell_w][n] gives each
-    // entry's slot in the block's staged vector (own rows 0..STAGE_ROWS-1,
-    // then the halo)
-    const int *halo_off;
-    const int *halo_rows;
-    const unsigned short *ell_lcol;
-    int halo_max;          // largest halo of a block
     const float *ell_val;  // [ell_w][n]
     float4 *corner;        // scratch [3m + 4nh]: per-element corner forces of the residual
 };
@@ -129,9 +120,6 @@ struct CollView {
     const int2 *edge;      // [ne] (a < b)
     const unsigned char *vfixed; // [nv] 1: infinite mass (obstacle or pinned)
 };
-
-constexpr int STAGE_ROWS = 256;      // rows per staged block (= threads per block)
-constexpr int STAGE_MAX_SLOTS = 3072;  // staged vector limit (48 KB of float4)
 
 // Scalars written by reductions (device).
 struct Scalars {

@@ -343,9 +343,9 @@ def test_one_step_parity_without_collisions(pc):
 
 
 def test_one_step_parity_with_chebyshev_sweeps(pc):
-    # the benchmark's smoother (Jacobi-preconditioned Chebyshev steps, with
-    # the halo-staged kernel) converged per LG iteration gives the oracle's
-    # exact global solves
+    # the benchmark's smoother (Jacobi-preconditioned Chebyshev steps in
+    # three-term form, several solve cycles) converged per LG iteration gives
+    # the oracle's exact global solves
     sc = wl.drape_sphere(side=40, with_sphere=False)
     gp = params(pc, fixed_iters=1, warm_iters=2, max_outer=1, max_inner=3, solve_cycles=40, jacobi_sweeps=32,
                 sweep_kind=1, cheb_ratio=300.0, r_warm=64, r_reuse=64, d_hat=1e-3, collisions=0)
