@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=32, help="Chebyshev steps per LG iteration")
     ap.add_argument("--cheb-ratio", type=float, default=300.0, help="Chebyshev interval ratio b/a")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form comparison")
+    ap.add_argument("--launch-overlap", type=int, default=1, choices=[0, 1],
+                    help="1: Chebyshev steps launched as programmatic dependents (default)")
     ap.add_argument("--no-launch-count", action="store_true",
                     help="skip the CUDA activity trace (e.g. when running under ncu)")
     return ap.parse_args()
@@ -55,8 +57,9 @@ FORMS = {"mixed16": 2, "mixed": 1, "fp32": 0}
 DTYPES = {"mixed16": "f16+f32+f64", "mixed": "bf16+f32+f64", "fp32": "f32"}
 
 
-def solver_params(pc, precision, sweeps=32, cheb_ratio=300.0):
+def solver_params(pc, precision, sweeps=32, cheb_ratio=300.0, overlap=1):
     p = pc.pdc_default_params()
+    p.launch_overlap = overlap  # Chebyshev steps as programmatic dependent launches
     p.tol_rel_residual = 1e-3
     p.max_outer = 2
     p.max_inner = 400
@@ -144,11 +147,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True, sweeps=32, cheb_ratio=300.0):
+def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True, sweeps=32, cheb_ratio=300.0,
+             overlap=1):
     """Warm-up, timed region (device), profiled replay, e2e through host buffers."""
     import numpy as np
     stream = torch.cuda.Stream()
-    p = solver_params(pc, precision, sweeps, cheb_ratio)
+    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap)
     t_setup = time.time()
     h = pc.pdc_create(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend, p,
                       stream.cuda_stream)
@@ -422,7 +426,7 @@ def main():
     forms = {}
     for f in a.forms.split(","):
         forms[f] = run_form(pc, torch, scene, FORMS[f], a.steps, a.warmup, local,
-                            not a.no_launch_count, a.sweeps, a.cheb_ratio)
+                            not a.no_launch_count, a.sweeps, a.cheb_ratio, a.launch_overlap)
     head = list(forms)[0]
     ms = forms[head]["ms"]
     ms = max_over_ranks(ms, f"cuda:{local}")

@@ -128,6 +128,13 @@ typedef struct {
                                 (same pairs, same order as a fresh pass) while
                                 every vertex stays within 0.9 mu of its swept box;
                                 0 (default): a hash pass for every full CCD     */
+    int32_t launch_overlap;  /* 1 (default): the Chebyshev steps of a global solve
+                                are launched as programmatic dependents of the
+                                kernel before them, so each step's launch and
+                                block scheduling overlap the previous kernel's
+                                tail (the step waits for its predecessor's
+                                results before reading them); 0: plain stream
+                                order.  Results are identical either way.      */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
@@ -224,11 +231,13 @@ void pdc_destroy(pdc_handle h);
 const char *pdc_last_error(pdc_handle h);
 
 /* Per-kernel device time of the launches made while profiling is on: a
- * CUDA event pair on the library's stream around every launch, resolved at
- * the end of each pdc_step.  algo_bytes is the algorithmic traffic of those
- * launches (the minimum bytes the method must move for them: element data,
- * vertex streams, sparse-matrix entries, basis rows; gathered neighbour
- * re-reads not counted).  Profiling adds a few microseconds per launch. */
+ * CUDA event pair on the library's stream around every launch (around each
+ * run of back-to-back Chebyshev steps of one global solve, which counts as
+ * that many launches), resolved at the end of each pdc_step.  algo_bytes is
+ * the algorithmic traffic of those launches (the minimum bytes the method
+ * must move for them: element data, vertex streams, sparse-matrix entries,
+ * basis rows; gathered neighbour re-reads not counted).  Profiling adds a
+ * few microseconds per event pair. */
 typedef struct {
     char name[32];
     int64_t launches;

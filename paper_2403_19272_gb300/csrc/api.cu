@@ -977,6 +977,13 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             double rho_prev = 1.0 / sig;
             // delta_{k-1}: the one of the three buffers that is neither din nor dout
             float4 *dp = (CD0.p != din && CD0.p != dout) ? CD0.p : (D0.p != din && D0.p != dout) ? D0.p : D1.p;
+            // the steps run back to back (each a programmatic dependent of the
+            // one before) and are timed as one run between two events
+            if (prof.on && sweeps > 0)
+                prof.begin(s, "cheb_sweep",
+                           (sweeps - 1) * bytes_sweep(contacts, false) + bytes_sweep(contacts, cyc == cycles - 1) +
+                               12.0 * n * sweeps,
+                           sweeps);
             for (int k = 0; k < sweeps; ++k) {
                 bool last = (cyc == cycles - 1) && (k == sweeps - 1);
                 double alpha, beta;
@@ -989,15 +996,16 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
                     beta = 2.0 * rk / dl;
                     rho_prev = rk;
                 }
-                PROF("cheb_sweep", bytes_sweep(contacts, last) + 12.0 * n,
-                     launch_cheb_step(s, c, cw, R, din, dp, dout, (float)alpha, (float)beta, Ucur,
-                                      last ? Ucur.p : nullptr, last ? sc.p : nullptr, last ? xprev : nullptr, w_acc,
-                                      Xs, last ? Xp.p : nullptr));
+                launch_cheb_step(s, c, cw, R, din, dp, dout, (float)alpha, (float)beta, Ucur, last ? Ucur.p : nullptr,
+                                 last ? sc.p : nullptr, last ? xprev : nullptr, w_acc, Xs, last ? Xp.p : nullptr,
+                                 P.launch_overlap != 0);
                 float4 *t = dp;  // rotate: delta_{k-1} <- delta_k <- delta_{k+1}
                 dp = din;
                 din = dout;
                 dout = t;
             }
+            if (prof.on && sweeps > 0) prof.end(s);
+            if (sync_check && sweeps > 0) check_region("cheb_sweep");
         } else {
             for (int k = 0; k < sweeps; ++k) {
                 bool last = (cyc == cycles - 1) && (k == sweeps - 1);
@@ -1330,6 +1338,7 @@ void pdc_default_params(pdc_params *p) {
     p->aa_depth = 6;
     p->tensor_cores = 1;
     p->bp_reuse = 0.0;
+    p->launch_overlap = 1;
 }
 
 static bool params_valid(const pdc_params *params) {

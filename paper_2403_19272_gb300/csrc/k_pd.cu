@@ -294,6 +294,11 @@ __global__ void __launch_bounds__(256) k_sweep(const ClothView c, const float *_
 // (alpha, beta from the Chebyshev recurrence for the interval [a, b] of the
 // spectrum of D^-1 (H + diag cw)).  The last step also writes the iterate as
 // k_sweep does.
+//
+// Launched as a programmatic dependent (launch_overlap), a block may start
+// while the previous kernel is still running: it waits for that kernel's
+// completion (and memory) before its first load or store, then releases the
+// next launch.  Launched plainly, the wait returns at once.
 template <int WMAX>
 __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const float *__restrict__ cw,
                                                    const float4 *__restrict__ r, const float4 *__restrict__ din,
@@ -302,6 +307,8 @@ __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const floa
                                                    const float4 *x, float4 *xout, float4 *xprev, float w_acc,
                                                    const float4 *__restrict__ xs, float4 *__restrict__ xabs,
                                                    Scalars *sc) {
+    grid_dep_wait();
+    grid_dep_release();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float mx = 0.f;
     if (i < c.n) {
@@ -539,11 +546,13 @@ void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const flo
 
 void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                       const float4 *dprev, float4 *dout, float alpha, float beta, const float4 *x,
-                      float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs) {
+                      float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs,
+                      bool overlap) {
     if (c.n > 0) {
         int b = nblk(c.n, 256);
-#define PDC_CHEB(W)                                                                                   \
-    k_cheb_step<W><<<b, 256, 0, s>>>(c, cw, r, din, dprev, dout, alpha, beta, x, xout, xprev, w_acc, xs, xabs, sc)
+#define PDC_CHEB(W)                                                                                         \
+    launch_dependent(overlap, k_cheb_step<W>, b, 256, s, c, cw, r, din, dprev, dout, alpha, beta, x, xout, xprev, \
+                     w_acc, xs, xabs, sc)
         if (c.ell_w <= 8) PDC_CHEB(8);
         else if (c.ell_w <= 12) PDC_CHEB(12);
         else if (c.ell_w <= 16) PDC_CHEB(16);

@@ -19,6 +19,7 @@
 
 #include <stdexcept>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/pdcloth.h"
@@ -86,6 +87,33 @@ __host__ __device__ inline float3 cross3(float3 a, float3 b) {
     return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
+// ---------------------------------------------------------------- dependent launches
+// A kernel launched by launch_dependent(true, ...) may begin while the kernel
+// before it in the stream is still running.  It must call grid_dep_wait()
+// before touching any memory that an earlier kernel writes or reads (the wait
+// returns once the previous grid has completed and its writes are visible;
+// with a plain launch it returns at once), and every thread calls it before
+// exiting, so that this grid's completion implies its predecessor's.
+// grid_dep_release() lets the next dependent launch begin.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_dependent(bool overlap, void (*kernel)(KArgs...), int grid, int block, cudaStream_t s,
+                             Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = overlap ? 1 : 0;
+    PDC_CK(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
 // ---------------------------------------------------------------- device views
 // Rest model of the cloth (read-only in the step kernels).
 struct ClothView {
@@ -150,7 +178,8 @@ void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const flo
 // + beta D^-1 (r - (H + diag cw) din) (dprev unused when alpha = 0).
 void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                       const float4 *dprev, float4 *dout, float alpha, float beta, const float4 *x,
-                      float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs);
+                      float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs,
+                      bool overlap = false);
 // Anderson mixing step on the iterate u (= u_k + delta_k on entry, u_{k+1} on exit).
 void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x, float4 *fprev,
                float4 *gprev, float4 *dF, float4 *dG, int slot, int have_prev, int ncol, double *Gb, float *theta,

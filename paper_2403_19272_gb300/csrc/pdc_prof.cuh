@@ -8,13 +8,15 @@
 
 namespace pdc {
 
-// Event-pair timing of individual launches (pdc_set_profiling).
+// Event-pair timing of individual launches, or of a run of back-to-back
+// launches of one kernel between a single pair of events (pdc_set_profiling).
 struct Profiler {
     bool on = false;
     struct Rec {
         int kind;
         cudaEvent_t a, b;
         double bytes;
+        int launches;  // kernel launches between the two events
     };
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
@@ -43,12 +45,13 @@ struct Profiler {
         return (int)names.size() - 1;
     }
     std::vector<size_t> open;  // nested begin/end pairs
-    void begin(cudaStream_t s, const char *name, double bytes) {
+    void begin(cudaStream_t s, const char *name, double bytes, int launches = 1) {
         Rec r;
         r.kind = kind(name);
         r.a = ev();
         r.b = ev();
         r.bytes = bytes;
+        r.launches = launches;
         PDC_CK(cudaEventRecord(r.a, s));
         open.push_back(pending.size());
         pending.push_back(r);
@@ -62,7 +65,7 @@ struct Profiler {
             PDC_CK(cudaEventSynchronize(r.b));
             float ms = 0.f;
             PDC_CK(cudaEventElapsedTime(&ms, r.a, r.b));
-            acc[r.kind].launches += 1;
+            acc[r.kind].launches += r.launches;
             acc[r.kind].total_ms += ms;
             acc[r.kind].algo_bytes += r.bytes;
         }

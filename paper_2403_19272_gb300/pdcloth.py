@@ -41,7 +41,7 @@ class pdc_params(ctypes.Structure):
                 ("samples_ee", c_i32), ("collisions", c_i32), ("fixed_iters", c_i32), ("eig_iters", c_i32),
                 ("seed", c_u64), ("accel", c_i32), ("accel_rho", c_dbl), ("sweep_kind", c_i32),
                 ("cheb_ratio", c_dbl), ("aa_depth", c_i32),
-                ("tensor_cores", c_i32), ("bp_reuse", c_dbl)]
+                ("tensor_cores", c_i32), ("bp_reuse", c_dbl), ("launch_overlap", c_i32)]
 
 
 class pdc_stats(ctypes.Structure):

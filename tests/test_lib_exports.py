@@ -52,3 +52,34 @@ def test_struct_layouts_match_header(libpath):
     assert p.gravity[2] == -9.8
     assert p.samples_vt == 3 and p.samples_ee == 4
     assert p.a_max == 20 and p.collisions == 1 and p.seed == 12345
+
+
+def test_binding_structs_have_the_header_layout(tmp_path):
+    """Every field of the ctypes structures sits at the offset (and every
+    structure has the size) that a C compiler gives the header's struct."""
+    import ctypes
+    from paper_2403_19272_gb300 import pdcloth
+    structs = [pdcloth.pdc_mesh_desc, pdcloth.pdc_material, pdcloth.pdc_params, pdcloth.pdc_stats,
+               pdcloth.pdc_kernel_time]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pdcloth.h"', "int main(void) {"]
+    for S in structs:
+        t = S.__name__
+        lines.append(f'printf("{t} %zu\\n", sizeof({t}));')
+        for f, _ in S._fields_:
+            lines.append(f'printf("{t}.{f} %zu\\n", offsetof({t}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    try:
+        subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       check=True, capture_output=True, text=True)
+    except FileNotFoundError:
+        pytest.skip("no C compiler")
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for S in structs:
+        t = S.__name__
+        assert int(got[t]) == ctypes.sizeof(S), t
+        for f, _ in S._fields_:
+            assert int(got[f"{t}.{f}"]) == getattr(S, f).offset, (t, f)
