@@ -224,6 +224,8 @@ struct pdc_ctx {
     DevBuf<float> tri_w, hin_w, hin_slen, mh2, hdiag, ell_val;
     DevBuf<int> vt_off, vt_list, vh_off, vh_list, ell_col, pins_d;
     DevBuf<short> ell_dcol;
+    DevBuf<unsigned char> ell_tile;
+    int ell_tw = 0;
     DevBuf<unsigned char> is_free;
     int ell_w = 0;
     // pins
@@ -322,6 +324,8 @@ struct pdc_ctx {
         c.ell_col = ell_col;
         c.ell_dcol = ell_dcol.p;
         c.ell_val = ell_val;
+        c.ell_tile = ell_tile.p;
+        c.ell_tw = ell_tw;
         c.corner = corner;
         return c;
     }
@@ -657,6 +661,26 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
         }
         if (fits && !dcol.empty()) ell_dcol.upload(dcol, s);
         else ell_dcol.release();
+        // per-block tiles of the same entries for the Chebyshev steps
+        ell_tw = ell_w <= 8 ? 8 : ell_w <= 12 ? 12 : 16;
+        if (fits && ell_w > 0 && ell_w <= 16) {
+            const size_t nb = ((size_t)n + ELL_TILE_ROWS - 1) / ELL_TILE_ROWS, tb = ell_tile_bytes(ell_tw);
+            std::vector<unsigned char> tiles(nb * tb, 0);
+            for (size_t b = 0; b < nb; ++b) {
+                float *tv = reinterpret_cast<float *>(tiles.data() + b * tb);
+                short *td = reinterpret_cast<short *>(tiles.data() + b * tb + (size_t)ell_tw * ELL_TILE_ROWS * 4);
+                for (int k = 0; k < ell_w; ++k)
+                    for (int t = 0; t < ELL_TILE_ROWS; ++t) {
+                        size_t i = b * ELL_TILE_ROWS + t;
+                        if (i >= (size_t)n) break;
+                        tv[k * ELL_TILE_ROWS + t] = evalv[(size_t)k * n + i];
+                        td[k * ELL_TILE_ROWS + t] = dcol[(size_t)k * n + i];
+                    }
+            }
+            ell_tile.upload(tiles, s);
+        } else {
+            ell_tile.release();
+        }
     }
     ell_val.upload(evalv, s);
     pins_d.upload(pins, s);
@@ -998,7 +1022,7 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
                 }
                 launch_cheb_step(s, c, cw, R, din, dp, dout, (float)alpha, (float)beta, Ucur, last ? Ucur.p : nullptr,
                                  last ? sc.p : nullptr, last ? xprev : nullptr, w_acc, Xs, last ? Xp.p : nullptr,
-                                 P.launch_overlap != 0);
+                                 P.launch_overlap != 0, sflag.p);
                 float4 *t = dp;  // rotate: delta_{k-1} <- delta_k <- delta_{k+1}
                 dp = din;
                 din = dout;
@@ -1234,12 +1258,14 @@ void pdc_ctx::step() {
     bad_d.download(&bad, 1, s);
     sflag.download(&sflag_h, 1, s);
     PDC_CK(cudaStreamSynchronize(s));
-    if (sflag_h & PDC_DEVERR_UMMA) {
+    if (sflag_h & (PDC_DEVERR_UMMA | PDC_DEVERR_COPY)) {
         PDC_CK(cudaMemcpyAsync(Xs.p, Xbak.p, sizeof(float4) * nv_all, cudaMemcpyDeviceToDevice, s));
         PDC_CK(cudaMemcpyAsync(Vs.p, Vbak.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
         sflag.zero(s);
         PDC_CK(cudaStreamSynchronize(s));
-        throw Error(PDC_ERR_TIMEOUT, "a tensor-core subspace kernel timed out waiting on its copies; state rolled back");
+        throw Error(PDC_ERR_TIMEOUT, (sflag_h & PDC_DEVERR_UMMA)
+                                         ? "a tensor-core subspace kernel timed out waiting on its copies; state rolled back"
+                                         : "a Chebyshev step timed out waiting on its matrix tile; state rolled back");
     }
     if (P.collisions) {
         bp.cnt_vt_d[bp.cur].download(&counts[0], 1, s);

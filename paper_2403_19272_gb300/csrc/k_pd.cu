@@ -6,7 +6,10 @@
 // subtracting H x (two large, nearly cancelling vectors), every element adds
 // its force w (target - current) directly, which is the same vector
 // r = b - (H + dH) x of Eq. (global) without the cancellation error.
+#include <algorithm>
+
 #include "pdc_internal.cuh"
+#include "pdc_async.cuh"
 
 namespace pdc {
 
@@ -341,6 +344,86 @@ __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const floa
     if (xout && sc) block_max(mx, &sc->dxmax);
 }
 
+// The Chebyshev step with the row's off-diagonals taken from its block's
+// ELL tile, which one thread brings into shared memory with a bulk copy
+// before the block waits on the previous kernel: the matrix never changes
+// during a step, so its fetch overlaps the previous kernel's tail, and only
+// the vertex streams are read after the wait.  Same arithmetic, in the same
+// order, as k_cheb_step.
+template <int W>
+__global__ void __launch_bounds__(ELL_TILE_ROWS, 8) k_cheb_step_tile(
+    const ClothView c, const float *__restrict__ cw, const float4 *__restrict__ r, const float4 *__restrict__ din,
+    const float4 *__restrict__ dprev, float4 *__restrict__ dout, float alpha, float beta, const float4 *x,
+    float4 *xout, float4 *xprev, float w_acc, const float4 *__restrict__ xs, float4 *__restrict__ xabs, Scalars *sc,
+    int *err) {
+    constexpr uint32_t BYTES = (uint32_t)W * ELL_TILE_ROWS * 6;
+    __shared__ __align__(128) unsigned char tile[BYTES];
+    __shared__ __align__(8) uint64_t bar;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (t == 0) {
+        mbar_expect_tx(&bar, BYTES);
+        bulk_load(tile, c.ell_tile + (size_t)blockIdx.x * BYTES, BYTES, &bar);
+    }
+    grid_dep_wait();
+    grid_dep_release();
+    const int i = blockIdx.x * ELL_TILE_ROWS + t;
+    float mx = 0.f;
+    const bool live = i < c.n;
+    const bool fr = live && c.is_free[i];
+    float3 di = make_float3(0.f, 0.f, 0.f), ri = di, pi = di;
+    float D = 1.f;
+    if (fr) {
+        di = f3(din[i]);
+        ri = f3(r[i]);
+        if (alpha != 0.f) pi = f3(dprev[i]);
+        D = c.hdiag[i] + (cw ? cw[i] : 0.f);
+    }
+    if (!__syncthreads_and(mbar_wait(&bar, 0))) {  // block-uniform: the reduction below syncs
+        if (t == 0) {
+            atomicOr(err, PDC_DEVERR_COPY);
+            mbar_wait(&bar, 0);  // let the copy land before the block's shared memory is released
+        }
+        return;
+    }
+    if (live) {
+        float3 dn = make_float3(0.f, 0.f, 0.f);
+        if (fr) {
+            const float *sv = reinterpret_cast<const float *>(tile);
+            const short *sd = reinterpret_cast<const short *>(tile + (size_t)W * ELL_TILE_ROWS * 4);
+            float3 e = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                if (k < c.ell_w) e = e + sv[k * ELL_TILE_ROWS + t] * f3(din[i + (int)sd[k * ELL_TILE_ROWS + t]]);
+            float3 acc = ri - D * di - e;
+            float3 dd = (beta / D) * acc;
+            if (alpha != 0.f) dd = dd + alpha * (di - pi);
+            dn = di + dd;
+        }
+        dout[i] = f4(dn);
+        if (xout) {
+            float3 xo = f3(x[i]);
+            float3 xn = xo + dn;
+            if (xprev) {
+                if (fr && w_acc != 1.f) {
+                    float3 xp = f3(xprev[i]);
+                    xn = xp + w_acc * (xn - xp);
+                }
+                xprev[i] = f4(xo);
+            }
+            xout[i] = f4(xn);
+            if (xabs) xabs[i] = f4(f3(xs[i]) + xn);
+            float3 d = xn - xo;
+            mx = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z)));
+        }
+    }
+    if (xout && sc) block_max(mx, &sc->dxmax);
+}
+
 // Anderson mixing of the LG fixed-point map x -> G(x) = x + delta(x)
 // (history of depth m): with f_k = delta_k, g_k = x_k + delta_k and the
 // differences dF_j, dG_j of consecutive f and g, theta minimises
@@ -547,7 +630,32 @@ void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const flo
 void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                       const float4 *dprev, float4 *dout, float alpha, float beta, const float4 *x,
                       float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs,
-                      bool overlap) {
+                      bool overlap, int *err) {
+    if (c.n > 0 && c.ell_tile && err) {
+        int b = nblk(c.n, ELL_TILE_ROWS);
+        // shared-memory carveout for 8 resident blocks (the register limit)
+        static unsigned long long carve[3] = {0, 0, 0};  // per-device bits
+        int ci = c.ell_tw == 8 ? 0 : c.ell_tw == 12 ? 1 : 2, dev = 0;
+        PDC_CK(cudaGetDevice(&dev));
+        if (!(carve[ci] >> (dev & 63) & 1ull)) {
+            size_t need = 8 * (ell_tile_bytes(c.ell_tw) + 2048);
+            int pct = (int)std::min<size_t>(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024));
+            cudaError_t e = ci == 0 ? cudaFuncSetAttribute(k_cheb_step_tile<8>, cudaFuncAttributePreferredSharedMemoryCarveout, pct)
+                          : ci == 1 ? cudaFuncSetAttribute(k_cheb_step_tile<12>, cudaFuncAttributePreferredSharedMemoryCarveout, pct)
+                                    : cudaFuncSetAttribute(k_cheb_step_tile<16>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            PDC_CK(e);
+            carve[ci] |= 1ull << (dev & 63);
+        }
+#define PDC_CHEB_T(W)                                                                                       \
+    launch_dependent(overlap, k_cheb_step_tile<W>, b, ELL_TILE_ROWS, s, c, cw, r, din, dprev, dout, alpha, beta, x, \
+                     xout, xprev, w_acc, xs, xabs, sc, err)
+        if (c.ell_tw == 8) PDC_CHEB_T(8);
+        else if (c.ell_tw == 12) PDC_CHEB_T(12);
+        else PDC_CHEB_T(16);
+#undef PDC_CHEB_T
+        PDC_LAUNCH_CK();
+        return;
+    }
     if (c.n > 0) {
         int b = nblk(c.n, 256);
 #define PDC_CHEB(W)                                                                                         \

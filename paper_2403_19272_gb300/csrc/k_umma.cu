@@ -30,6 +30,7 @@
 
 #include "pdc_subspace.cuh"
 #include "pdc_umma.cuh"
+#include "pdc_async.cuh"
 
 namespace pdc {
 
@@ -40,47 +41,6 @@ constexpr int KBOX = 64;             // BF16 elements per 128-byte swizzle row
 constexpr int ABOX_BYTES = TILE * 128;  // one [128][64] BF16 box
 constexpr int BBOX_BYTES = 16 * 128;    // one [16][64] BF16 box
 constexpr uint32_t NCOLS = 32;       // TMEM columns per CTA
-constexpr unsigned long long WAIT_NS = 1000000000ull;  // 1 s
-
-__device__ inline uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ inline unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ inline void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ inline void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ inline void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ inline void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ inline bool mbar_test(uint64_t *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-// Wait for phase `parity` of the barrier, giving up after WAIT_NS.
-__device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    if (mbar_test(bar, parity)) return true;
-    unsigned long long t0 = global_ns();
-    while (!mbar_test(bar, parity)) {
-        if (global_ns() - t0 > WAIT_NS) return false;
-        __nanosleep(64);
-    }
-    return true;
-}
 
 __device__ inline void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
     asm volatile(

@@ -137,8 +137,21 @@ struct ClothView {
     const int *ell_col;    // [ell_w][n]
     const short *ell_dcol; // [ell_w][n] column minus row when every offset fits 16 bits (else NULL)
     const float *ell_val;  // [ell_w][n]
+    // the same off-diagonals in blocks of ELL_TILE_ROWS rows, one contiguous
+    // tile per block: [ell_tw][ELL_TILE_ROWS] float values, then
+    // [ell_tw][ELL_TILE_ROWS] 16-bit offsets, zero-padded (NULL when the
+    // offsets do not fit 16 bits or the width exceeds 16)
+    const unsigned char *ell_tile;
+    int ell_tw;            // tile width: 8, 12 or 16 (>= ell_w)
     float4 *corner;        // scratch [3m + 4nh]: per-element corner forces of the residual
 };
+
+constexpr int ELL_TILE_ROWS = 256;
+inline size_t ell_tile_bytes(int tw) { return (size_t)tw * ELL_TILE_ROWS * 6; }
+
+// Device error bit set in the status word when a bounded wait for a bulk
+// copy into shared memory ran out.
+constexpr int PDC_DEVERR_COPY = 4;
 
 // Collision-set topology (cloth + obstacles).
 struct CollView {
@@ -179,7 +192,7 @@ void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const flo
 void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
                       const float4 *dprev, float4 *dout, float alpha, float beta, const float4 *x,
                       float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs,
-                      bool overlap = false);
+                      bool overlap = false, int *err = nullptr);
 // Anderson mixing step on the iterate u (= u_k + delta_k on entry, u_{k+1} on exit).
 void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x, float4 *fprev,
                float4 *gprev, float4 *dF, float4 *dG, int slot, int have_prev, int ncol, double *Gb, float *theta,
