@@ -51,13 +51,38 @@ __device__ inline bool box_overlap(float3 alo, float3 ahi, float3 blo, float3 bh
            blo.y <= __fadd_rn(ahi.y, d) && alo.z <= __fadd_rn(bhi.z, d) && blo.z <= __fadd_rn(ahi.z, d);
 }
 
-// Cell range of a box inflated by dhat on both sides.  If two boxes satisfy
-// the predicate, their inflated ranges share a cell (rounding is monotone).
-__device__ inline void cell_range(float3 lo, float3 hi, float d, float inv, int3 &clo, int3 &chi) {
-    float3 l = make_float3(__fsub_rn(lo.x, d), __fsub_rn(lo.y, d), __fsub_rn(lo.z, d));
+// Cells of the table side: the primitive's own box, not inflated.
+__device__ inline void cell_range_raw(float3 lo, float3 hi, float inv, int3 &clo, int3 &chi) {
+    clo = cellv(lo, inv);
+    chi = cellv(hi, inv);
+}
+
+// Cells searched by a query box b: if a table box a satisfies the predicate
+// with b, then a_lo <= fl32(b_hi + d) and a_hi >= b_lo - d - |a_hi + d| 2^-24
+// (from b_lo <= fl32(a_hi + d)); the search range covers both bounds (the
+// low end is lowered by a margin of 2^-20 (|b_lo| + d) that exceeds the
+// rounding of fl32(a_hi + d) and of its own computation), and floor(v / cell)
+// is monotone, so the raw cell range of a meets it.  Only the query side is
+// inflated: the gap is counted once.
+__device__ inline float low_search(float lo, float d) {
+    float m = (fabsf(lo) + d) * 9.5367431640625e-07f;  // 2^-20
+    return __fsub_rn(__fsub_rn(lo, d), m);
+}
+__device__ inline void cell_range_query(float3 lo, float3 hi, float d, float inv, int3 &clo, int3 &chi) {
+    float3 l = make_float3(low_search(lo.x, d), low_search(lo.y, d), low_search(lo.z, d));
     float3 h = make_float3(__fadd_rn(hi.x, d), __fadd_rn(hi.y, d), __fadd_rn(hi.z, d));
     clo = cellv(l, inv);
     chi = cellv(h, inv);
+}
+
+// A table entry stores (primitive << 3) | lowx | lowy << 1 | lowz << 2,
+// where low* says that the entry's cell is the lowest cell of the
+// primitive's raw range along that axis.  A pair is reported only in the
+// lowest cell common to the query range and the table range, max(q_lo,
+// t_lo) per axis; at a cell c of the query range this holds iff, per axis,
+// low* is set or c equals the query's lowest cell.
+__device__ inline bool owner_cell(int flags, int x, int y, int z, int3 qlo) {
+    return ((flags & 1) || x == qlo.x) && ((flags & 2) || y == qlo.y) && ((flags & 4) || z == qlo.z);
 }
 
 __device__ inline void vbox(const float4 *x0, const float4 *x1, int v, float3 &lo, float3 &hi) {
@@ -126,7 +151,7 @@ __global__ void k_hash_insert(int np, const float4 *__restrict__ blo, const floa
     if (mode == 1 && *total > cap) return;
     float inv = gp->inv_cell;
     int3 lo, hi;
-    cell_range(f3(blo[p]), f3(bhi[p]), dhat, inv, lo, hi);
+    cell_range_raw(f3(blo[p]), f3(bhi[p]), inv, lo, hi);
     long long ncell = (long long)(hi.x - lo.x + 1) * (hi.y - lo.y + 1) * (hi.z - lo.z + 1);
     if (ncell > MAX_CELLS_PER_PRIM) {
         if (mode == 0) atomicOr(overflow, OVF_CELLS);
@@ -142,7 +167,7 @@ __global__ void k_hash_insert(int np, const float4 *__restrict__ blo, const floa
                 } else {
                     int pos = bstart[b] + atomicAdd(&bfill[b], 1);
                     ekey[pos] = k;
-                    eprim[pos] = p;
+                    eprim[pos] = (p << 3) | (x == lo.x ? 1 : 0) | (y == lo.y ? 2 : 0) | (z == lo.z ? 4 : 0);
                 }
             }
 }
@@ -183,8 +208,7 @@ __device__ inline void sort_row(int *row, int c) {
 template <int QG>
 __global__ void __launch_bounds__(QUERY_T) k_query_vt(CollView cv, const float4 *__restrict__ x0,
                                                       const float4 *__restrict__ x1, const float4 *__restrict__ tlo,
-                                                      const float4 *__restrict__ thi, const int4 *__restrict__ tcell,
-                                                      const GridParams *gp, float dhat, unsigned int mask,
+                                                      const float4 *__restrict__ thi, const GridParams *gp, float dhat, unsigned int mask,
                                                       const int *__restrict__ bcnt, const int *__restrict__ bstart,
                                                       const unsigned long long *__restrict__ ekey,
                                                       const int *__restrict__ eprim, int *__restrict__ cnt,
@@ -202,7 +226,7 @@ __global__ void __launch_bounds__(QUERY_T) k_query_vt(CollView cv, const float4 
     float3 lo, hi;
     vbox(x0, x1, v, lo, hi);
     int3 clo, chi;
-    cell_range(lo, hi, dhat, inv, clo, chi);
+    cell_range_query(lo, hi, dhat, inv, clo, chi);
     if ((long long)(chi.x - clo.x + 1) * (chi.y - clo.y + 1) * (chi.z - clo.z + 1) > MAX_CELLS_PER_PRIM) {
         if (gl == 0) {
             cnt[v] = 0;
@@ -224,9 +248,9 @@ __global__ void __launch_bounds__(QUERY_T) k_query_vt(CollView cv, const float4 
                     bool cand = false;
                     int t = 0;
                     if (e < e1 && ekey[e] == k) {
-                        t = eprim[e];
-                        int4 tl = tcell[t];
-                        if (x == max(clo.x, tl.x) && y == max(clo.y, tl.y) && z == max(clo.z, tl.z)) {
+                        const int pk = eprim[e];
+                        t = pk >> 3;
+                        if (owner_cell(pk, x, y, z, clo)) {
                             int4 T = cv.tri[t];
                             cand = T.x != v && T.y != v && T.z != v &&
                                    !(vfix && T.x >= cv.nc && T.y >= cv.nc && T.z >= cv.nc) &&
@@ -253,8 +277,7 @@ __global__ void __launch_bounds__(QUERY_T) k_query_vt(CollView cv, const float4 
 // edge buckets are short and half their entries fail f > e at once, so the
 // grouped scan of the VT query does not pay here: measured slower).
 __global__ void __launch_bounds__(QUERY_T) k_query_ee(CollView cv, const float4 *__restrict__ elo,
-                                                  const float4 *__restrict__ ehi, const int4 *__restrict__ ecell,
-                                                  const GridParams *gp, float dhat, unsigned int mask,
+                                                  const float4 *__restrict__ ehi, const GridParams *gp, float dhat, unsigned int mask,
                                                   const int *__restrict__ bcnt, const int *__restrict__ bstart,
                                                   const unsigned long long *__restrict__ ekey,
                                                   const int *__restrict__ eprim, int *__restrict__ cnt,
@@ -269,7 +292,7 @@ __global__ void __launch_bounds__(QUERY_T) k_query_ee(CollView cv, const float4 
     float inv = gp->inv_cell;
     float3 lo = f3(elo[e]), hi = f3(ehi[e]);
     int3 clo, chi;
-    cell_range(lo, hi, dhat, inv, clo, chi);
+    cell_range_query(lo, hi, dhat, inv, clo, chi);
     if ((long long)(chi.x - clo.x + 1) * (chi.y - clo.y + 1) * (chi.z - clo.z + 1) > MAX_CELLS_PER_PRIM) {
         cnt[e] = 0;
         atomicOr(overflow, OVF_CELLS);
@@ -287,10 +310,10 @@ __global__ void __launch_bounds__(QUERY_T) k_query_ee(CollView cv, const float4 
                 int e0 = bstart[b], e1 = e0 + bcnt[b];
                 for (int q = e0; q < e1; ++q) {
                     if (ekey[q] != k) continue;
-                    int f = eprim[q];
+                    const int pk = eprim[q];
+                    const int f = pk >> 3;
                     if (f <= e) continue;
-                    int4 tl = ecell[f];
-                    if (x != max(clo.x, tl.x) || y != max(clo.y, tl.y) || z != max(clo.z, tl.z)) continue;
+                    if (!owner_cell(pk, x, y, z, clo)) continue;
                     int2 F = cv.edge[f];
                     if (E.x == F.x || E.x == F.y || E.y == F.x || E.y == F.y) continue;
                     if (efix && F.x >= cv.nc && F.y >= cv.nc) continue;
@@ -312,16 +335,6 @@ __global__ void k_compact_slots(int np, const int *__restrict__ cnt, const int *
     int c = min(cnt[p], width), o = off[p];
     const int *row = slots + (size_t)p * width;
     for (int k = 0; k < c; ++k) out[o + k] = make_int2(p, row[k]);
-}
-
-// lower cell corner of every primitive's inflated box (shared by insert and query)
-__global__ void k_prim_cells(int np, const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
-                             const GridParams *gp, float dhat, int4 *__restrict__ cell) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    int3 lo, hi;
-    cell_range(f3(blo[p]), f3(bhi[p]), dhat, gp->inv_cell, lo, hi);
-    cell[p] = make_int4(lo.x, lo.y, lo.z, 0);
 }
 
 __global__ void k_check_cap(const long long *total, long long cap, int flag, int *overflow, long long *count_out) {
@@ -412,8 +425,8 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
     off_v.alloc(cv.nv);
     cnt_e.alloc(cv.ne);
     off_e.alloc(cv.ne);
-    tcell.alloc(cv.nt);
-    ecell.alloc(cv.ne);
+    if (cv.nt >= (1 << 28) || cv.ne >= (1 << 28))
+        throw Error(PDC_ERR_ARG, "broad phase: more than 2^28 triangles or edges");
     slots_vt.alloc((size_t)cv.nv * w_vt);
     slots_ee.alloc((size_t)cv.ne * w_ee);
     long long mx = std::max<long long>(std::max<long long>(T_vt, T_ee), std::max<long long>(cv.nv, cv.ne));
@@ -553,15 +566,11 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
             PDC_LAUNCH_CK();
         });
     }
-    // ---- per-primitive lower cells
-    if (cv.nt) k_prim_cells<<<nblk(cv.nt, 256), 256, 0, s>>>(cv.nt, tlo, thi, gp, dhat, tcell);
-    if (cv.ne) k_prim_cells<<<nblk(cv.ne, 256), 256, 0, s>>>(cv.ne, elo, ehi, gp, dhat, ecell);
-    PDC_LAUNCH_CK();
     // ---- VT candidates
     if (prof) prof->begin(s, "bp_query_vt", 0.0);
     if (cv.nv) {
         k_query_vt<QG_VT><<<nblk((long long)cv.nv * QG_VT, QUERY_T), QUERY_T, 0, s>>>(
-            cv, x0, x1, tlo, thi, tcell, gp, dhat, (unsigned)(T_vt - 1), bcnt[0], bstart[0], ekey[0], eprim[0], cnt_v,
+            cv, x0, x1, tlo, thi, gp, dhat, (unsigned)(T_vt - 1), bcnt[0], bstart[0], ekey[0], eprim[0], cnt_v,
             slots_vt, w_vt, tot + 0, cap_ent, overflow);
         PDC_LAUNCH_CK();
     }
@@ -576,7 +585,7 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
     if (prof) prof->begin(s, "bp_query_ee", 0.0);
     if (cv.ne) {
         k_query_ee<<<nblk(cv.ne, QUERY_T), QUERY_T, 0, s>>>(
-            cv, elo, ehi, ecell, gp, dhat, (unsigned)(T_ee - 1), bcnt[1], bstart[1], ekey[1], eprim[1], cnt_e,
+            cv, elo, ehi, gp, dhat, (unsigned)(T_ee - 1), bcnt[1], bstart[1], ekey[1], eprim[1], cnt_e,
             slots_ee, w_ee, tot + 1, cap_ent, overflow);
         PDC_LAUNCH_CK();
     }

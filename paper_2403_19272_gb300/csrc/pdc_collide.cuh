@@ -65,7 +65,6 @@ struct BroadPhase {
     DevBuf<int> eprim[2];
     DevBuf<float4> tlo, thi, elo, ehi;
     DevBuf<int> cnt_v, off_v, cnt_e, off_e, scratch;
-    DevBuf<int4> tcell, ecell;       // lower cell of each primitive's inflated box
     DevBuf<int> slots_vt, slots_ee;  // per-primary sorted candidate rows
     int w_vt = 16, w_ee = 32;        // row widths (doubled on OVF_SLOTS)
     DevBuf<GridParams> gp;

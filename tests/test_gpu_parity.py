@@ -85,6 +85,40 @@ def test_broadphase_static_and_empty(pc):
     pc.pdc_destroy(h)
 
 
+def test_broadphase_pairs_on_the_predicate_boundary(pc):
+    """Two parallel sheets whose gap is exactly fl32(z + d_hat): every facing
+    pair satisfies the FP32 predicate with equality on z, so a search range
+    that dropped a cell at either end would lose pairs."""
+    d = 1e-3
+    n1 = 12
+    g = np.linspace(0.0, 0.5, n1, dtype=np.float32)
+    xx, yy = np.meshgrid(g, g, indexing="ij")
+    za = np.float32(0.3)
+    zb = np.float32(za + np.float32(d))  # fl32(z_a + d_hat)
+    A = np.stack([xx.ravel(), yy.ravel(), np.full(n1 * n1, za, np.float32)], 1)
+    B = np.stack([xx.ravel() + np.float32(0.013), yy.ravel(), np.full(n1 * n1, zb, np.float32)], 1)
+    V = np.concatenate([A, B]).astype(np.float32)
+    T = []
+    for i in range(n1 - 1):
+        for j in range(n1 - 1):
+            a, b, c, e = i * n1 + j, (i + 1) * n1 + j, i * n1 + j + 1, (i + 1) * n1 + j + 1
+            T += [[a, b, c], [b, e, c]]
+    T = np.array(T, np.int32)
+    T = np.concatenate([T, T + n1 * n1]).astype(np.int32)
+    h = pc.pdc_create(V, T, np.zeros(0, np.int32), 0.1, 1e3, 1e-2, params(pc, d_hat=d))
+    vt_g, ee_g = pc.pdc_op_broadphase(h, V, V)
+    m = pd.Model(V, T, np.zeros(0, np.int32), 0.1, 1e3, 1e-2, 0.005)
+    cm = pd.CollisionMesh(m, [])
+    vt_o, ee_o = collide.broadphase(V, V, cm.nc, cm.tris, cm.edges, d)
+    cross = np.sum((vt_o[:, 0] < n1 * n1) != (cm.tris[vt_o[:, 1], 0] < n1 * n1))
+    assert cross > 100  # pairs across the gap exist
+    assert np.array_equal(vt_g, vt_o[np.lexsort((vt_o[:, 1], vt_o[:, 0]))])
+    q_o = np.concatenate([cm.edges[ee_o[:, 0]], cm.edges[ee_o[:, 1]]], axis=1)
+    key = lambda q: set(map(tuple, q.tolist()))
+    assert key(ee_g) == key(q_o) and len(ee_g) == len(q_o)
+    pc.pdc_destroy(h)
+
+
 def test_broadphase_sampled_at_65k_vertices(pc):
     sc = wl.fold_on_box(side=256, box_subdiv=16)
     cl = pc.Cloth(sc, params(pc, d_hat=1e-3))
