@@ -334,7 +334,7 @@ PARENTS = {"broad_phase", "partial_ccd"}
 # DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, one
 # capture at 512x512) of the kernels that can be the dominant one; the file
 # under profiles/ gives the command
-TRAFFIC = {"cheb_sweep": 38995200.0}
+TRAFFIC = {"cheb_sweep": 33799680.0}
 
 
 def roofline(kernels, pk, ms_step):

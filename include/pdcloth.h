@@ -140,7 +140,10 @@ typedef struct {
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
 typedef struct {
     int32_t warm_iters, outer_iters, inner_iters;
-    int32_t contact_iters;       /* inner iterations that used collision springs */
+    int32_t contact_iters;       /* LG iterations that ran the collision-spring
+                                    path of the global solve (when the residual
+                                    is read back: only those with at least one
+                                    contact vertex)                              */
     int64_t n_candidates;        /* broad-phase pairs of the last full CCD       */
     int64_t n_active;            /* active NDB constraints after the step        */
     int64_t n_contact_vertices;  /* vertices with a collision spring (last iter) */

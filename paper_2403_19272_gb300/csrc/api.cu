@@ -965,6 +965,7 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
             return;
         }
     }
+    if (springs) st.contact_iters++;
     float w_acc = 1.f;
     if (aa) accel.aa_observe(std::sqrt(hsc->rsq));
     else if (acc) w_acc = (float)accel.next(std::sqrt(hsc->rsq));

@@ -11,6 +11,8 @@ All calls go through the C ABI (ctypes binding).  Tolerances:
     relative 1e-4 of the largest entry;
   * one step from identical states: 1e-5 of the bounding-box diagonal.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -444,4 +446,27 @@ def test_drape_run_stays_penetration_free(pc):
             X = all_pos(sc, cl.positions()).astype(np.float64)
             assert len(collide.intersecting_triangle_pairs(X, cm.tris)) == 0, k
     assert cl.positions()[:, 2].min() < -0.04
+    cl.close()
+
+
+def test_contact_iterations_are_counted(pc):
+    """A drape thrown at the sphere: once contact vertices exist, the step
+    statistics count the LG iterations that ran with collision springs."""
+    import bench
+    sc = wl.drape_sphere(side=32, sphere_subdiv=3)
+    v0 = sc.v0.copy()
+    v0[:, 2] -= 2.5  # reaches the sphere within a few steps
+    sc = dataclasses.replace(sc, v0=v0.astype(np.float32))
+    p = bench.solver_params(pc, 0)
+    for k, v in dict(r_warm=32, r_reuse=32, eig_iters=6, d_hat=1e-3).items():
+        setattr(p, k, v)
+    cl = pc.Cloth(sc, p)
+    counted = 0
+    for k in range(10):
+        cl.step()
+        st = cl.stats()
+        assert st["contact_iters"] <= st["warm_iters"] + st["inner_iters"]
+        if st["n_contact_vertices"] > 0:
+            counted += st["contact_iters"]
+    assert counted > 0
     cl.close()
