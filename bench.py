@@ -42,7 +42,7 @@ def parse():
                     help="comma list of mixed16 (FP16 basis), mixed (BF16 basis), fp32; the first is the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-side", type=int, default=64)
-    ap.add_argument("--sweeps", type=int, default=32, help="Chebyshev steps per LG iteration")
+    ap.add_argument("--sweeps", type=int, default=28, help="Chebyshev steps per LG iteration")
     ap.add_argument("--cheb-ratio", type=float, default=300.0, help="Chebyshev interval ratio b/a")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form comparison")
     ap.add_argument("--launch-overlap", type=int, default=1, choices=[0, 1],
@@ -57,7 +57,7 @@ FORMS = {"mixed16": 2, "mixed": 1, "fp32": 0}
 DTYPES = {"mixed16": "f16+f32+f64", "mixed": "bf16+f32+f64", "fp32": "f32"}
 
 
-def solver_params(pc, precision, sweeps=32, cheb_ratio=300.0, overlap=1):
+def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1):
     p = pc.pdc_default_params()
     p.launch_overlap = overlap  # Chebyshev steps as programmatic dependent launches
     p.tol_rel_residual = 1e-3
@@ -147,7 +147,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True, sweeps=32, cheb_ratio=300.0,
+def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True, sweeps=28, cheb_ratio=300.0,
              overlap=1):
     """Warm-up, timed region (device), profiled replay, e2e through host buffers."""
     import numpy as np
