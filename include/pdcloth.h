@@ -128,13 +128,15 @@ typedef struct {
                                 (same pairs, same order as a fresh pass) while
                                 every vertex stays within 0.9 mu of its swept box;
                                 0 (default): a hash pass for every full CCD     */
-    int32_t launch_overlap;  /* 1 (default): the Chebyshev steps of a global solve
-                                are launched as programmatic dependents of the
-                                kernel before them, so each step's launch and
-                                block scheduling overlap the previous kernel's
-                                tail (the step waits for its predecessor's
-                                results before reading them); 0: plain stream
-                                order.  Results are identical either way.      */
+    int32_t launch_overlap;  /* 1 (default): the kernels of an LG iteration (element
+                                forces and residual, tensor-core projection,
+                                reduction and lift, Chebyshev steps, Anderson
+                                mixing) are launched as programmatic dependents
+                                of the kernel before them, so each launch and
+                                its block scheduling overlap the previous
+                                kernel's tail (a kernel waits for its
+                                predecessor's results before touching them); 0:
+                                plain stream order.  Results are identical.    */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */

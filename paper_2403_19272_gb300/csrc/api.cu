@@ -324,6 +324,7 @@ struct pdc_ctx {
         c.ell_col = ell_col;
         c.ell_dcol = ell_dcol.p;
         c.ell_val = ell_val;
+        c.overlap = P.launch_overlap != 0;
         c.ell_tile = ell_tile.p;
         c.ell_tw = ell_tw;
         c.corner = corner;
@@ -360,6 +361,7 @@ struct pdc_ctx {
         S.umma = (umma.ok && P.precision != 0 && P.tensor_cores) ? &umma : nullptr;
         S.umma_partial = umma_partial;
         S.dev_err = sflag;
+        S.overlap = P.launch_overlap != 0;
         return S;
     }
     SubspaceWork work() {
@@ -923,6 +925,7 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
     converged = false;
     PDC_CK(cudaMemsetAsync(&sc.p->rsq, 0, sizeof(double), s));
     PDC_CK(cudaMemsetAsync(&sc.p->dxmax, 0, sizeof(unsigned int), s));
+    if (accel.on && P.accel == 2 && P.fixed_iters == 0) aa_clear(s, aa_Gb);  // normal equations of this iteration
     const float *cw = nullptr;
     const float4 *cf = nullptr;
     if (contacts) {
@@ -1055,7 +1058,7 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
         }
         PROF("anderson_mix", 0,
              launch_aa(s, n, is_free, din, Ucur, aa_f, aa_g, aa_dF, aa_dG, slot, accel.aa_have_prev ? 1 : 0,
-                       accel.aa_count, aa_Gb, aa_theta, Xs, Xp));
+                       accel.aa_count, aa_Gb, aa_theta, Xs, Xp, P.launch_overlap != 0));
         accel.aa_have_prev = true;
     }
     if (contacts && P.collisions) {

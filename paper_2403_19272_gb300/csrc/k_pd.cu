@@ -142,10 +142,10 @@ __global__ void k_scale_disp(int n, const float4 *__restrict__ xs, const float4 
 // from exact differences of the rest part and of the displacements; bend:
 // w_h K_j (s_hat - s)); each vertex then sums the forces of its incident
 // elements in incidence order, adds inertia and contact, and reduces |r|^2.
-__global__ void __launch_bounds__(256) k_tri_corner(const ClothView c, const float4 *__restrict__ xs,
-                                                    const float4 *__restrict__ u, float4 *__restrict__ ct) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= c.m) return;
+// One launch for both element kinds: blocks [0, tri_blocks) take triangles,
+// the rest hinges.
+__device__ inline void tri_corner(const ClothView &c, int t, const float4 *__restrict__ xs,
+                                  const float4 *__restrict__ u, float4 *__restrict__ ct) {
     int4 T = c.tri[t];
     float4 g = c.tri_g[t];
     float w = c.tri_w[t];
@@ -162,10 +162,8 @@ __global__ void __launch_bounds__(256) k_tri_corner(const ClothView c, const flo
     ct[3 * (size_t)t + 2] = f4(w * (g.z * d1 + g.w * d2));
 }
 
-__global__ void __launch_bounds__(256) k_hinge_corner(const ClothView c, const float4 *__restrict__ xs,
-                                                      const float4 *__restrict__ u, float4 *__restrict__ ch) {
-    int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= c.nh) return;
+__device__ inline void hinge_corner(const ClothView &c, int h, const float4 *__restrict__ xs,
+                                    const float4 *__restrict__ u, float4 *__restrict__ ch) {
     int4 H = c.hin[h];
     float4 K = c.hin_K[h];
     float sl = c.hin_slen[h], hw = c.hin_w[h];
@@ -187,11 +185,27 @@ __global__ void __launch_bounds__(256) k_hinge_corner(const ClothView c, const f
     o[3] = f4((hw * K.w) * d);
 }
 
+__global__ void __launch_bounds__(256) k_elem_corner(const ClothView c, int tri_blocks, const float4 *__restrict__ xs,
+                                                     const float4 *__restrict__ u, float4 *__restrict__ ct,
+                                                     float4 *__restrict__ ch) {
+    grid_dep_wait();
+    grid_dep_release();
+    if ((int)blockIdx.x < tri_blocks) {
+        int t = blockIdx.x * blockDim.x + threadIdx.x;
+        if (t < c.m) tri_corner(c, t, xs, u, ct);
+    } else {
+        int h = (blockIdx.x - tri_blocks) * blockDim.x + threadIdx.x;
+        if (h < c.nh) hinge_corner(c, h, xs, u, ch);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_residual(const ClothView c, const float4 *__restrict__ u,
                                                   const float4 *__restrict__ zrel, const float *__restrict__ cw,
                                                   const float4 *__restrict__ cf, const float4 *__restrict__ ct,
                                                   const float4 *__restrict__ ch, float4 *__restrict__ r, Scalars *sc,
                                                   float *__restrict__ r_soa, int soa_ld) {
+    grid_dep_wait();
+    grid_dep_release();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float sq = 0.f;
     if (i < c.n) {
@@ -439,6 +453,8 @@ __global__ void __launch_bounds__(256) k_aa_gram(int n, const unsigned char *__r
                                                  float4 *__restrict__ dF, float4 *__restrict__ dG, int slot,
                                                  int have_prev, int ncol, double *__restrict__ Gb) {
     __shared__ float red[AA_MAX * (AA_MAX + 3) / 2 + AA_MAX][8];
+    grid_dep_wait();
+    grid_dep_release();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float3 col[AA_MAX];
     float3 fk = make_float3(0.f, 0.f, 0.f);
@@ -485,13 +501,11 @@ __global__ void __launch_bounds__(256) k_aa_gram(int n, const unsigned char *__r
     }
 }
 
-// Solves the regularised normal equations (one thread, FP64) into theta.
 // theta solving the (regularised) normal equations of the mixing
-// least-squares problem by Cholesky; M (= the column count) is a template
-// parameter so the tiny system lives in registers.
+// least-squares problem by Cholesky (one thread, FP64); M (= the column
+// count) is a template parameter so the tiny system lives in registers.
 template <int M>
-__global__ void k_aa_solve(const double *__restrict__ Gb, float *__restrict__ theta) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ inline void aa_solve(const double *__restrict__ Gb, float *__restrict__ theta) {
     double A[M][M], b[M];
     int e = 0;
     double tr = 0.0;
@@ -542,16 +556,28 @@ __global__ void k_aa_solve(const double *__restrict__ Gb, float *__restrict__ th
     for (int j = 0; j < AA_MAX; ++j) theta[j] = (j < M && ok && isfinite(x[j < M ? j : 0])) ? (float)x[j < M ? j : 0] : 0.f;
 }
 
+// One thread solves the M x M system (a kernel of its own: inside the mixing
+// kernel its FP64 registers would cut that kernel's occupancy).
+template <int M> __global__ void k_aa_solve(const double *__restrict__ Gb, float *__restrict__ theta) {
+    grid_dep_wait();
+    grid_dep_release();
+    if (threadIdx.x == 0 && blockIdx.x == 0) aa_solve<M>(Gb, theta);
+}
+
 // x_{k+1} = g_k - sum_j theta_j dG_j on free vertices.
+template <int M>
 __global__ void __launch_bounds__(256) k_aa_mix(int n, const unsigned char *__restrict__ is_free,
                                                 const float4 *__restrict__ xhat, const float4 *__restrict__ dG,
-                                                int ncol, const float *__restrict__ theta, float4 *__restrict__ xout,
+                                                const float *__restrict__ theta, float4 *__restrict__ xout,
                                                 const float4 *__restrict__ xs, float4 *__restrict__ xabs) {
+    grid_dep_wait();
+    grid_dep_release();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float3 x = f3(xhat[i]);
     if (is_free[i])
-        for (int j = 0; j < ncol; ++j) x = x - theta[j] * f3(dG[(size_t)j * n + i]);
+#pragma unroll
+        for (int j = 0; j < M; ++j) x = x - theta[j] * f3(dG[(size_t)j * n + i]);
     xout[i] = f4(x);
     if (xabs) xabs[i] = f4(f3(xs[i]) + x);
 }
@@ -606,9 +632,11 @@ void launch_scale_disp(cudaStream_t s, int n, const float4 *xs, const float4 *u,
 void launch_residual(cudaStream_t s, const ClothView &c, const float4 *xs, const float4 *u, const float4 *zrel,
                      const float *cw, const float4 *cf, float4 *r, Scalars *sc, float *r_soa, int soa_ld) {
     float4 *ct = c.corner, *ch = c.corner + 3 * (size_t)c.m;
-    if (c.m > 0) k_tri_corner<<<nblk(c.m, 256), 256, 0, s>>>(c, xs, u, ct);
-    if (c.nh > 0) k_hinge_corner<<<nblk(c.nh, 256), 256, 0, s>>>(c, xs, u, ch);
-    if (c.n > 0) k_residual<<<nblk(c.n, 256), 256, 0, s>>>(c, u, zrel, cw, cf, ct, ch, r, sc, r_soa, soa_ld);
+    const int tb = nblk(c.m, 256), hb = nblk(c.nh, 256);
+    if (tb + hb > 0) launch_dependent(c.overlap != 0, k_elem_corner, tb + hb, 256, 0, s, c, tb, xs, u, ct, ch);
+    if (c.n > 0)
+        launch_dependent(c.overlap != 0, k_residual, nblk(c.n, 256), 256, 0, s, c, u, zrel, cw, cf, ct, ch, r, sc,
+                         r_soa, soa_ld);
     PDC_LAUNCH_CK();
 }
 
@@ -647,7 +675,7 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
             carve[ci] |= 1ull << (dev & 63);
         }
 #define PDC_CHEB_T(W)                                                                                       \
-    launch_dependent(overlap, k_cheb_step_tile<W>, b, ELL_TILE_ROWS, s, c, cw, r, din, dprev, dout, alpha, beta, x, \
+    launch_dependent(overlap, k_cheb_step_tile<W>, b, ELL_TILE_ROWS, 0, s, c, cw, r, din, dprev, dout, alpha, beta, x, \
                      xout, xprev, w_acc, xs, xabs, sc, err)
         if (c.ell_tw == 8) PDC_CHEB_T(8);
         else if (c.ell_tw == 12) PDC_CHEB_T(12);
@@ -659,7 +687,7 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
     if (c.n > 0) {
         int b = nblk(c.n, 256);
 #define PDC_CHEB(W)                                                                                         \
-    launch_dependent(overlap, k_cheb_step<W>, b, 256, s, c, cw, r, din, dprev, dout, alpha, beta, x, xout, xprev, \
+    launch_dependent(overlap, k_cheb_step<W>, b, 256, 0, s, c, cw, r, din, dprev, dout, alpha, beta, x, xout, xprev, \
                      w_acc, xs, xabs, sc)
         if (c.ell_w <= 8) PDC_CHEB(8);
         else if (c.ell_w <= 12) PDC_CHEB(12);
@@ -672,24 +700,35 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
 
 void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x, float4 *fprev,
                float4 *gprev, float4 *dF, float4 *dG, int slot, int have_prev, int ncol, double *Gb, float *theta,
-               const float4 *xs, float4 *xabs) {
+               const float4 *xs, float4 *xabs, bool overlap) {
     if (n <= 0) return;
-    PDC_CK(cudaMemsetAsync(Gb, 0, sizeof(double) * (AA_MAX * (AA_MAX + 3) / 2 + AA_MAX), s));
-    k_aa_gram<<<nblk(n, 256), 256, 0, s>>>(n, is_free, delta, x, fprev, gprev, dF, dG, slot, have_prev, ncol, Gb);
+    // Gb is zeroed by the caller (aa_clear) before the kernels of this LG
+    // iteration, so that the gram kernel can follow the last sweep directly
+    const int b = nblk(n, 256);
+    launch_dependent(overlap, k_aa_gram, b, 256, 0, s, n, is_free, delta, (const float4 *)x, fprev, gprev, dF, dG,
+                     slot, have_prev, ncol, Gb);
     if (ncol > 0) {
+#define PDC_AA(M)                                                                                             \
+    launch_dependent(overlap, k_aa_solve<M>, 1, 32, 0, s, (const double *)Gb, theta);                          \
+    launch_dependent(overlap, k_aa_mix<M>, b, 256, 0, s, n, is_free, (const float4 *)x, (const float4 *)dG,   \
+                     (const float *)theta, x, xs, xabs)
         switch (ncol) {
-            case 1: k_aa_solve<1><<<1, 32, 0, s>>>(Gb, theta); break;
-            case 2: k_aa_solve<2><<<1, 32, 0, s>>>(Gb, theta); break;
-            case 3: k_aa_solve<3><<<1, 32, 0, s>>>(Gb, theta); break;
-            case 4: k_aa_solve<4><<<1, 32, 0, s>>>(Gb, theta); break;
-            case 5: k_aa_solve<5><<<1, 32, 0, s>>>(Gb, theta); break;
-            case 6: k_aa_solve<6><<<1, 32, 0, s>>>(Gb, theta); break;
-            case 7: k_aa_solve<7><<<1, 32, 0, s>>>(Gb, theta); break;
-            default: k_aa_solve<8><<<1, 32, 0, s>>>(Gb, theta); break;
+            case 1: PDC_AA(1); break;
+            case 2: PDC_AA(2); break;
+            case 3: PDC_AA(3); break;
+            case 4: PDC_AA(4); break;
+            case 5: PDC_AA(5); break;
+            case 6: PDC_AA(6); break;
+            case 7: PDC_AA(7); break;
+            default: PDC_AA(8); break;
         }
-        k_aa_mix<<<nblk(n, 256), 256, 0, s>>>(n, is_free, x, dG, ncol, theta, x, xs, xabs);
+#undef PDC_AA
     }
     PDC_LAUNCH_CK();
+}
+
+void aa_clear(cudaStream_t s, double *Gb) {
+    PDC_CK(cudaMemsetAsync(Gb, 0, sizeof(double) * (AA_MAX * (AA_MAX + 3) / 2 + AA_MAX), s));
 }
 
 void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out) {

@@ -269,6 +269,8 @@ __global__ void k_project_reduce(SubspaceView S, const int *n_cv, int nblocks, c
 template <class T>
 __global__ void k_apply_inverse(SubspaceView S, const int *n_cv, const T *__restrict__ Ainv, const double *__restrict__ g,
                                 float *__restrict__ q) {
+    grid_dep_wait();
+    grid_dep_release();
     if (n_cv && *n_cv > 0) return;
     int r = S.r_nc;
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -522,7 +524,7 @@ template <class F> static void with_basis(const SubspaceView &S, bool compact, F
 void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W,
                     bool maybe_contacts) {
     if (!maybe_contacts && S.umma && S.r_nc > 0 && S.r_nc <= S.ld) {
-        launch_project_umma(s, *S.umma, S.r_nc, rl, S.umma_partial, W.g, S.dev_err);
+        launch_project_umma(s, *S.umma, S.r_nc, rl, S.umma_partial, W.g, S.dev_err, S.overlap != 0);
         return;
     }
     with_basis(S, false, [&](auto *U) { project_t(s, S, U, rl, n_cv, W.partial); });
@@ -552,7 +554,8 @@ void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv
     if (S.r_nc > 0) {
         int thr = S.r_nc * 32;
         if (mixed)
-            k_apply_inverse<double><<<(thr + 255) / 256, 256, 0, s>>>(S, n_cv, S.A0inv, W.g, W.q);
+            launch_dependent(S.overlap != 0, k_apply_inverse<double>, (thr + 255) / 256, 256, 0, s, S, n_cv,
+                             (const double *)S.A0inv, (const double *)W.g, W.q);
         else
             k_apply_inverse<float><<<(thr + 255) / 256, 256, 0, s>>>(S, n_cv, S.A0inv32, W.g, W.q);
     }
@@ -576,7 +579,7 @@ template <class TU> static void lift_t(cudaStream_t s, const SubspaceView &S, co
 void launch_lift(cudaStream_t s, const SubspaceView &S, const int *n_cv, const SubspaceWork &W, const float4 *din,
                  float4 *dout, bool maybe_contacts) {
     if (!maybe_contacts && S.umma && S.r_nc > 0 && S.r_nc <= S.ld) {
-        launch_lift_umma(s, *S.umma, S.r_nc, W.q, din, dout, S.dev_err);
+        launch_lift_umma(s, *S.umma, S.r_nc, W.q, din, dout, S.dev_err, S.overlap != 0);
         return;
     }
     if (maybe_contacts && compact_covers(S) && S.n > 0)

@@ -432,6 +432,10 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_lift_umma_p(const __grid_consta
         __syncwarp();
         tmem_alloc(&S.taddr);
     }
+    // launched as a programmatic dependent: everything above overlapped the
+    // previous kernel; q, din and dout are touched only after this wait
+    grid_dep_wait();
+    grid_dep_release();
     // B = q split into hi / lo parts, [16][ld], fixed for all tiles
     float qmax = 0.f;
     for (int e = tid; e < 3 * r; e += blockDim.x) qmax = fmaxf(qmax, fabsf(q[e]));
@@ -546,6 +550,10 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_project_umma_p(const __grid_con
         __syncwarp();
         tmem_alloc(&S.taddr);
     }
+    // launched as a programmatic dependent: everything above overlapped the
+    // previous kernel; rl and partial are touched only after this wait
+    grid_dep_wait();
+    grid_dep_release();
     // one scale for all of this CTA's rows (its accumulator sums them all)
     float vmax = 0.f;
     for (int k = 0; k < mine; ++k) {
@@ -666,6 +674,8 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_project_umma_p(const __grid_con
 }
 
 __global__ void k_umma_reduce(int r, int ld, int nblocks, const float *__restrict__ partial, double *__restrict__ g) {
+    grid_dep_wait();
+    grid_dep_release();
     int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= r * 3) return;
     double s = 0.0;
@@ -738,12 +748,16 @@ void umma_setup(UmmaMaps &M, const void *U, const void *Ut, bool f16, int n, int
 int umma_project_blocks(int n) { return (n + TILE - 1) / TILE; }
 
 void launch_project_umma(cudaStream_t s, const UmmaMaps &M, int r, const float4 *rl, float *partial, double *g,
-                         int *err) {
+                         int *err, bool overlap) {
     int nb;
     if (M.persistent) {
         nb = std::max(1, std::min(M.sms, umma_project_blocks(M.n)));
-        if (M.f16) k_project_umma_p<true><<<nb, PTHREADS, proj_p_smem(), s>>>(M.mapUt, M.n, M.ld, r, rl, partial, err);
-        else k_project_umma_p<false><<<nb, PTHREADS, proj_p_smem(), s>>>(M.mapUt, M.n, M.ld, r, rl, partial, err);
+        if (M.f16)
+            launch_dependent(overlap, k_project_umma_p<true>, nb, PTHREADS, proj_p_smem(), s, M.mapUt, M.n, M.ld, r,
+                             rl, partial, err);
+        else
+            launch_dependent(overlap, k_project_umma_p<false>, nb, PTHREADS, proj_p_smem(), s, M.mapUt, M.n, M.ld, r,
+                             rl, partial, err);
     } else {
         nb = umma_project_blocks(M.n);
         if (M.f16) k_project_umma<true><<<nb, 128, proj_smem(), s>>>(M.mapUt, M.n, M.ld, r, rl, partial, err);
@@ -751,17 +765,22 @@ void launch_project_umma(cudaStream_t s, const UmmaMaps &M, int r, const float4 
     }
     PDC_LAUNCH_CK();
     int thr = r * 3 * 32;
-    k_umma_reduce<<<(thr + 255) / 256, 256, 0, s>>>(r, M.ld, nb, partial, g);
+    launch_dependent(overlap && M.persistent, k_umma_reduce, (thr + 255) / 256, 256, 0, s, r, M.ld, nb,
+                     (const float *)partial, g);
     PDC_LAUNCH_CK();
 }
 
 void launch_lift_umma(cudaStream_t s, const UmmaMaps &M, int r, const float *q, const float4 *din, float4 *dout,
-                      int *err) {
+                      int *err, bool overlap) {
     int nt = (M.n + TILE - 1) / TILE;
     if (M.persistent) {
         int nb = std::max(1, std::min(M.sms, nt));
-        if (M.f16) k_lift_umma_p<true><<<nb, PTHREADS, lift_p_smem(), s>>>(M.mapU, M.n, M.ld, r, q, din, dout, err);
-        else k_lift_umma_p<false><<<nb, PTHREADS, lift_p_smem(), s>>>(M.mapU, M.n, M.ld, r, q, din, dout, err);
+        if (M.f16)
+            launch_dependent(overlap, k_lift_umma_p<true>, nb, PTHREADS, lift_p_smem(), s, M.mapU, M.n, M.ld, r, q,
+                             din, dout, err);
+        else
+            launch_dependent(overlap, k_lift_umma_p<false>, nb, PTHREADS, lift_p_smem(), s, M.mapU, M.n, M.ld, r, q,
+                             din, dout, err);
     } else {
         if (M.f16) k_lift_umma<true><<<nt, 128, lift_smem(), s>>>(M.mapU, M.n, M.ld, r, q, din, dout, err);
         else k_lift_umma<false><<<nt, 128, lift_smem(), s>>>(M.mapU, M.n, M.ld, r, q, din, dout, err);

@@ -99,12 +99,12 @@ __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.w
 __device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
-inline void launch_dependent(bool overlap, void (*kernel)(KArgs...), int grid, int block, cudaStream_t s,
-                             Args &&...args) {
+inline void launch_dependent(bool overlap, void (*kernel)(KArgs...), int grid, int block, size_t smem,
+                             cudaStream_t s, Args &&...args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -136,6 +136,7 @@ struct ClothView {
     int ell_w;
     const int *ell_col;    // [ell_w][n]
     const short *ell_dcol; // [ell_w][n] column minus row when every offset fits 16 bits (else NULL)
+    int overlap;           // launch the step kernels as programmatic dependents
     const float *ell_val;  // [ell_w][n]
     // the same off-diagonals in blocks of ELL_TILE_ROWS rows, one contiguous
     // tile per block: [ell_tw][ELL_TILE_ROWS] float values, then
@@ -194,9 +195,11 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
                       float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs,
                       bool overlap = false, int *err = nullptr);
 // Anderson mixing step on the iterate u (= u_k + delta_k on entry, u_{k+1} on exit).
+// Gb must have been zeroed (aa_clear) after the previous mixing step.
 void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x, float4 *fprev,
                float4 *gprev, float4 *dF, float4 *dG, int slot, int have_prev, int ncol, double *Gb, float *theta,
-               const float4 *xs, float4 *xabs);
+               const float4 *xs, float4 *xabs, bool overlap);
+void aa_clear(cudaStream_t s, double *Gb);
 void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out);
 void launch_set_pins(cudaStream_t s, const int *pins, int npins, const float4 *tgt, const float4 *xs, float4 *u,
                      float4 *xabs);

@@ -30,6 +30,7 @@ struct SubspaceView {
     const UmmaMaps *umma;
     float *umma_partial;       // [tiles][ld][3]
     int *dev_err;              // status word receiving PDC_DEVERR_UMMA
+    int overlap;               // tensor-core path: launch as programmatic dependents
 };
 
 struct SubspaceWork {

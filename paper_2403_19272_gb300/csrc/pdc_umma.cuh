@@ -30,10 +30,12 @@ bool umma_supported(int ld, int n);
 void umma_setup(UmmaMaps &M, const void *U, const void *Ut, bool f16, int n, int n_pad, int ld);
 int umma_project_blocks(int n);
 // g = U[:, :r]^T rl via per-tile partial sums [blocks][ld][3] and an FP64 reduction.
+// With overlap, the kernels are launched as programmatic dependents of the
+// kernel before them (barrier setup and TMEM allocation overlap its tail).
 void launch_project_umma(cudaStream_t s, const UmmaMaps &M, int r, const float4 *rl, float *partial, double *g,
-                         int *err);
+                         int *err, bool overlap = false);
 // dout = din + U[:, :r] q (din may be NULL).
 void launch_lift_umma(cudaStream_t s, const UmmaMaps &M, int r, const float *q, const float4 *din, float4 *dout,
-                      int *err);
+                      int *err, bool overlap = false);
 
 }  // namespace pdc
