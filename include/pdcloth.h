@@ -137,6 +137,16 @@ typedef struct {
                                 kernel's tail (a kernel waits for its
                                 predecessor's results before touching them); 0:
                                 plain stream order.  Results are identical.    */
+    double rf_toi;           /* residual forwarding (Sec. 6, end of Alg. 1): when
+                                the exit time of impact is below rf_toi, up to
+                                rf_iters more LG iterations of the step's problem
+                                run from the filtered positions with every active
+                                constraint at weight k (a = 0) and no CCD; the
+                                change dx shifts the next step's z by 2 dx
+                                (Eq. z_rf).  0 (default): off                   */
+    int32_t rf_iters;        /* cap on those iterations (exact count when
+                                fixed_iters = 1); they stop once the largest
+                                change is below tol_inner * bbox diagonal       */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
@@ -157,6 +167,8 @@ typedef struct {
     int32_t overflow_retries;    /* buffer regrowths during this step            */
     int32_t bp_reused;           /* full CCDs whose candidates were filtered from
                                     the step's first broad phase (bp_reuse)      */
+    int32_t rf_iters;            /* residual-forwarding LG iterations run at the
+                                    end of this step (0: not triggered)          */
 } pdc_stats;
 
 /* Defaults: dt 1/200, g = (0,0,-9.8), K = 2, a_max 20, alpha 0.8, automatic
@@ -203,7 +215,8 @@ pdc_status pdc_set_pin_targets(pdc_handle h, const float *xyz, int32_t on_device
 
 /* Overwrite / read the state x*, v* ([nv][3] each; v may be NULL on set to
  * zero it).  The current positions must be free of intersections (Sec. 3:
- * the barrier method starts from a feasible state). */
+ * the barrier method starts from a feasible state).  Setting the state
+ * discards a pending residual-forwarding displacement (rf_toi). */
 pdc_status pdc_set_state(pdc_handle h, const float *x, const float *v, int32_t on_device);
 pdc_status pdc_get_state(pdc_handle h, float *x, float *v, int32_t on_device);
 

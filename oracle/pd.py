@@ -64,6 +64,8 @@ class Params:
     samples_ee: int = 4
     collisions: bool = True
     fixed_iters: bool = False      # parity mode: run exactly warm/max_outer/max_inner
+    rf_toi: float = 0.0            # residual forwarding (Sec. 6) when the exit TOI is below this (0: off)
+    rf_iters: int = 8              # cap on its LG iterations (exact count in parity mode)
 
 
 # ----------------------------------------------------------------------------
@@ -404,6 +406,9 @@ class StepStats:
     s: float = 1.0
     n_candidates: int = 0
     n_active: int = 0
+    rf_iters: int = 0              # residual-forwarding LG iterations run after this step
+    rf_res0: float = 0.0           # |residual| of the forwarding problem at the filtered x
+    rf_res1: float = 0.0           # ... and after its iterations
     rel_residual: float = 0.0
     log: list = field(default_factory=list)
 
@@ -423,6 +428,7 @@ class Oracle:
         self.obs = [o.positions(0.0).astype(np.float64) for o in scene.obstacles]
         f = self.model.free
         self.k = params.k_ndb_scale * float(np.mean(self.model.diagH[f])) if np.any(f) else 1.0
+        self.rf = None  # residual-forwarding displacement dx for the next step (Sec. 6)
 
     # --- helpers
     def _all(self, x_cloth, obs):
@@ -457,8 +463,12 @@ class Oracle:
         L = M.L
         st = StepStats()
 
-        # Eq. (z): z = x* + h v* + h^2 M^-1 f_ext with f_ext = m g
+        # Eq. (z): z = x* + h v* + h^2 M^-1 f_ext with f_ext = m g; with residual
+        # forwarding (Eq. z_rf) h^2 M^-1 df = 2 dx of the previous step's RF
         z = x_star + h * v_star + h * h * np.asarray(p.gravity)[None, :]
+        if self.rf is not None:
+            z = z + 2.0 * self.rf
+            self.rf = None
         z[~M.free] = pin_next
         x = z.copy()
         rho0 = self.rel_residual(x, z)
@@ -585,6 +595,30 @@ class Oracle:
         st.t_toi, st.s = t_toi, s
         st.n_candidates = len(keys)
         st.n_active = sum(1 for v in state.values() if v[0])
+
+        # residual forwarding (Sec. 6, end of Alg. 1): after a small exit TOI,
+        # more LG iterations of this step's problem from the filtered x, with
+        # every active constraint at weight k (a = 0) and no CCD; the change
+        # dx is carried to the next step's z (Eq. z_rf, h^2 M^-1 df = 2 dx).
+        # Pinned rows stay where the filter left them.
+        if p.rf_toi > 0 and t_toi < p.rf_toi:
+            act = np.array([state.get(kk, (False, 0))[0] for kk in keys], dtype=bool)
+            w = np.full(len(keys), self.k)
+            pin_f = x_new[~M.free].copy()
+            xr = x_new.copy()
+            rf_contact = lambda xx: contact_terms(cm, xm_all, self._all(xx, self.obs), act, quads, kinds, w, p.dhat)
+            st.rf_res0 = self.rel_residual(xr, z, rf_contact(xr))
+            for it in range(p.rf_iters):
+                contact = rf_contact(xr)
+                xn = self._lg(xr, z, pin_f, contact)
+                st.rf_iters += 1
+                dx = np.max(np.abs(xn - xr)) if len(xr) else 0.0
+                xr = xn
+                if not p.fixed_iters and dx <= p.tol_inner * L:
+                    break
+            st.rf_res1 = self.rel_residual(xr, z, rf_contact(xr))
+            self.rf = xr - x_new
+            self.rf[~M.free] = 0.0
         v_new = (x_new - x_star) / h
         self.x, self.v, self.t = x_new, v_new, self.t + h
         return x_new, v_new, st

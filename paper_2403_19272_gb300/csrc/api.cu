@@ -281,6 +281,8 @@ struct pdc_ctx {
     DevBuf<float4> corner;  // per-element corner forces of the residual [3m + 4nh]
     DevBuf<float4> aa_dF, aa_dG, aa_f, aa_g;  // Anderson history
     DevBuf<double> aa_Gb;
+    DevBuf<float4> RFd;        // residual-forwarding dx carried to the next step
+    bool rf_pending = false;
     DevBuf<float> aa_theta;
     double gersh = 1.0;       // Gershgorin bound of D^-1 H
     long long nnz_off = 0;  // off-diagonal entries of H over free rows
@@ -404,7 +406,8 @@ struct pdc_ctx {
     }
     double bytes_basis(int r) const { return (double)n * r * (P.precision != 0 ? 2 : 4) + (double)n * 12; }
     void lg_iteration(bool contacts, bool check_rel, double rho0, bool &converged, int r_nc, int r_c, int cycles,
-                      int sweeps);
+                      int sweeps, bool pccd = true);
+    void residual_forwarding();
     void full_ccd(const float4 *x0, const float4 *x1, bool merge);
     void broad_phase_pass(const float4 *x0, const float4 *x1, bool super);
     void step();
@@ -920,7 +923,7 @@ void pdc_ctx::ensure_topology() {
 // then `cycles` x {subspace correction, `sweeps` Jacobi sweeps}, Xp += delta,
 // then (with contacts) partial CCD on (Xm, Xp).
 void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &converged, int r_nc, int r_c, int cycles,
-                           int sweeps) {
+                           int sweeps, bool pccd) {
     ClothView c = cloth();
     converged = false;
     PDC_CK(cudaMemsetAsync(&sc.p->rsq, 0, sizeof(double), s));
@@ -1061,7 +1064,7 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
                        accel.aa_count, aa_Gb, aa_theta, Xs, Xp, P.launch_overlap != 0));
         accel.aa_have_prev = true;
     }
-    if (contacts && P.collisions) {
+    if (contacts && P.collisions && pccd) {
         bp.prof = prof.on ? &prof : nullptr;
         PROF("partial_ccd", 0,
              launch_partial_ccd(s, coll(), bp, Xm, Xp, cparams(), act, cap_act, n_act_d, &sc.p->overflow, disp));
@@ -1148,7 +1151,7 @@ void pdc_ctx::step() {
 
     // Eq. (z) and x <- z (Alg. 1); obstacles move to their targets in x^+
     float3 g = make_float3((float)P.gravity[0], (float)P.gravity[1], (float)P.gravity[2]);
-    launch_prologue(s, n, Xs, Vs, pins_d, pin_tgt, npins, h, g, Z, Ucur, Xp);
+    launch_prologue(s, n, Xs, Vs, pins_d, pin_tgt, npins, h, g, Z, Ucur, Xp, rf_pending ? RFd.p : nullptr);
     if (nv_all > n)
         PDC_CK(cudaMemcpyAsync(Xp.p + n, obs_tgt.p, sizeof(float4) * (nv_all - n), cudaMemcpyDeviceToDevice, s));
     // rho0 = residual at z (no collision springs)
@@ -1287,7 +1290,6 @@ void pdc_ctx::step() {
         st.t_toi = tt <= 1.0 ? tt : 2.0;
         st.s_line_search = sf;
     }
-    st.ms_step = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (hsc->overflow) {
         // roll back; the caller (pdc_step) grows the buffers and retries
         PDC_CK(cudaMemcpyAsync(Xs.p, Xbak.p, sizeof(float4) * nv_all, cudaMemcpyDeviceToDevice, s));
@@ -1308,8 +1310,52 @@ void pdc_ctx::step() {
         throw Error(PDC_ERR_STATE, "collision list index outside the topology (guard 0x" + std::to_string(guard) +
                                        "); state rolled back");
     }
+    rf_pending = false;  // the previous step's forwarded displacement is used up
+    if (P.collisions && P.rf_toi > 0 && st.t_toi < P.rf_toi) residual_forwarding();
+    st.ms_step = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (prof.on) prof.flush();
     stepped = true;
+}
+
+// Residual forwarding (Sec. 6, end of Alg. 1).  The step has ended at x_new
+// (in Xs); more LG iterations of the same problem (same z) run from x_new
+// with every active constraint at weight k (a = 0) and no partial or full
+// CCD, and their total change dx (pinned rows 0) is kept for the next
+// step's z.  The step's statistics other than rf_iters are left as they
+// were; a non-finite dx is dropped.
+void pdc_ctx::residual_forwarding() {
+    const bool fixed = P.fixed_iters != 0;
+    const int cycles = std::max(P.solve_cycles, 1), sweeps = std::max(P.jacobi_sweeps, 0);
+    const double tolx_in = P.tol_inner * L;
+    launch_rf_rebase(s, n, Xs, Xbak, Z, Ucur, Xp);
+    if (nv_all > n)
+        PDC_CK(cudaMemcpyAsync(Xp.p + n, Xs.p + n, sizeof(float4) * (nv_all - n), cudaMemcpyDeviceToDevice, s));
+    launch_rf_weights(s, act, n_act_d, cap_act, (float)k_ndb);
+    const bool acc_on = accel.on;
+    const double rel = st.rel_residual;
+    const int citers = st.contact_iters;
+    accel.on = false;
+    for (int it = 0; it < std::max(P.rf_iters, 0); ++it) {
+        bool conv = false;
+        lg_iteration(true, false, st.rho0, conv, r_warm, r_reuse, cycles, sweeps, false);
+        st.rf_iters++;
+        if (!fixed) {
+            read_scalars();
+            if (bits_to_float(hsc->dxmax) <= tolx_in) break;
+        }
+    }
+    accel.on = acc_on;
+    st.rel_residual = rel;
+    st.contact_iters = citers;
+    RFd.alloc(n);
+    PDC_CK(cudaMemcpyAsync(RFd.p, Ucur.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+    bad_d.zero(s);
+    k_finite<<<nb(n), 256, 0, s>>>(n, RFd, bad_d);
+    PDC_LAUNCH_CK();
+    int bad = 0;
+    bad_d.download(&bad, 1, s);
+    PDC_CK(cudaStreamSynchronize(s));
+    rf_pending = bad == 0;
 }
 
 // ============================================================================ C ABI
@@ -1369,6 +1415,8 @@ void pdc_default_params(pdc_params *p) {
     p->tensor_cores = 1;
     p->bp_reuse = 0.0;
     p->launch_overlap = 1;
+    p->rf_toi = 0.0;
+    p->rf_iters = 8;
 }
 
 static bool params_valid(const pdc_params *params) {
@@ -1565,6 +1613,7 @@ pdc_status pdc_set_state(pdc_handle h, const float *x, const float *v, int32_t o
     } else {
         h->Vs.zero(h->s);
     }
+    h->rf_pending = false;  // a forwarded residual belongs to the replaced state
     PDC_CK(cudaStreamSynchronize(h->s));
     API_END(h)
 }

@@ -781,6 +781,17 @@ void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, cons
     if (bp.prof) bp.prof->end(s);
 }
 
+// Residual forwarding: every active constraint at the base weight k (a = 0).
+__global__ void k_rf_weights(ActivePair *act, const int *n_act, int cap, float k) {
+    const int n = min(*n_act, cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) act[i].n0w.w = k;
+}
+
+void launch_rf_weights(cudaStream_t s, ActivePair *act, const int *n_act, int cap_act, float k) {
+    k_rf_weights<<<152, 256, 0, s>>>(act, n_act, cap_act, k);
+    PDC_LAUNCH_CK();
+}
+
 void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, const int *n_act, int cap_act,
                     const float4 *x, float dhat, float *cw, float4 *cf) {
     k_contact<<<152 * 4, 256, 0, s>>>(cv, act, n_act, cap_act, x, dhat, cw, cf);

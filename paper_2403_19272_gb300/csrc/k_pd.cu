@@ -89,13 +89,17 @@ __device__ inline void polar32(float3 f1, float3 f2, float3 &r1, float3 &r2) {
 // of neighbouring x* entries are exact in FP32, so element quantities keep
 // the precision of u instead of the ulp of the absolute coordinates.
 
-// Eq. (z): z - x* = h v* + h^2 g (f_ext = m g); the iterate starts at u = z - x*.
+// Eq. (z): z - x* = h v* + h^2 g (f_ext = m g), plus 2 dx of the previous
+// step's residual forwarding when given (Eq. z_rf: h^2 M^-1 df = 2 dx); the
+// iterate starts at u = z - x*.
 __global__ void k_prologue(int n, const float4 *__restrict__ xs, const float4 *__restrict__ vs, float h, float3 g,
-                           float4 *__restrict__ zrel, float4 *__restrict__ u, float4 *__restrict__ xabs) {
+                           const float4 *__restrict__ rf, float4 *__restrict__ zrel, float4 *__restrict__ u,
+                           float4 *__restrict__ xabs) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float3 v = f3(vs[i]);
     float3 d = h * v + (h * h) * g;
+    if (rf) d = d + 2.f * f3(rf[i]);
     float4 o = f4(d);
     zrel[i] = o;
     u[i] = o;
@@ -113,6 +117,19 @@ __global__ void k_set_pins(const int *__restrict__ pins, int np, const float4 *_
     if (zrel) zrel[p] = d;
     u[p] = d;
     xabs[p] = tgt[i];
+}
+
+// Residual forwarding starts from the filtered positions: the base becomes
+// x_new (the caller has stored it in xs), z - x* becomes z - x_new (xold is
+// the step's x*), the displacement restarts at 0 and xabs = x_new.
+__global__ void k_rf_rebase(int n, const float4 *__restrict__ xs, const float4 *__restrict__ xold,
+                            float4 *__restrict__ zrel, float4 *__restrict__ u, float4 *__restrict__ xabs) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float3 xn = f3(xs[i]);
+    zrel[i] = f4(f3(zrel[i]) - (xn - f3(xold[i])));
+    u[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    xabs[i] = f4(xn);
 }
 
 // u = um (the displacement of x^-), xabs = x* + um
@@ -603,13 +620,19 @@ inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 }  // namespace
 
 void launch_prologue(cudaStream_t s, int n, const float4 *xs, const float4 *vs, const int *pins, const float4 *pin_tgt,
-                     int npins, float h, float3 g, float4 *zrel, float4 *u, float4 *xabs) {
-    if (n > 0) k_prologue<<<nblk(n, 256), 256, 0, s>>>(n, xs, vs, h, g, zrel, u, xabs);
+                     int npins, float h, float3 g, float4 *zrel, float4 *u, float4 *xabs, const float4 *rf) {
+    if (n > 0) k_prologue<<<nblk(n, 256), 256, 0, s>>>(n, xs, vs, h, g, rf, zrel, u, xabs);
     PDC_LAUNCH_CK();
     if (npins > 0) {
         k_set_pins<<<nblk(npins, 256), 256, 0, s>>>(pins, npins, pin_tgt, xs, zrel, u, xabs);
         PDC_LAUNCH_CK();
     }
+}
+
+void launch_rf_rebase(cudaStream_t s, int n, const float4 *xs, const float4 *xold, float4 *zrel, float4 *u,
+                      float4 *xabs) {
+    if (n > 0) k_rf_rebase<<<nblk(n, 256), 256, 0, s>>>(n, xs, xold, zrel, u, xabs);
+    PDC_LAUNCH_CK();
 }
 
 void launch_set_pins(cudaStream_t s, const int *pins, int npins, const float4 *tgt, const float4 *xs, float4 *u,

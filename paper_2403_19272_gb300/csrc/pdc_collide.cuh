@@ -126,6 +126,8 @@ void launch_collect_active(cudaStream_t s, const CollView &cv, BroadPhase &bp, c
 void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm, const float4 *xp,
                         const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow, float4 *disp);
 // Collision springs of the active list at positions x: cw += w, cf += w (y - x).
+// sets the weight of every listed active pair to k (residual forwarding, a = 0)
+void launch_rf_weights(cudaStream_t s, ActivePair *act, const int *n_act, int cap_act, float k);
 void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, const int *n_act, int cap_act,
                     const float4 *x, float dhat, float *cw, float4 *cf);
 // Reads and clears the index-guard word of the pair kernels (0: no entry of a

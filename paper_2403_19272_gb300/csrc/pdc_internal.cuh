@@ -182,7 +182,10 @@ struct Scalars {
 // displacement); zrel = z - x*; xabs receives absolute positions for the
 // collision kernels.
 void launch_prologue(cudaStream_t s, int n, const float4 *xs, const float4 *vs, const int *pins, const float4 *pin_tgt,
-                     int npins, float h, float3 g, float4 *zrel, float4 *u, float4 *xabs);
+                     int npins, float h, float3 g, float4 *zrel, float4 *u, float4 *xabs, const float4 *rf = nullptr);
+// residual forwarding: rebase the displacement representation on x_new (in xs)
+void launch_rf_rebase(cudaStream_t s, int n, const float4 *xs, const float4 *xold, float4 *zrel, float4 *u,
+                      float4 *xabs);
 void launch_residual(cudaStream_t s, const ClothView &c, const float4 *xs, const float4 *u, const float4 *zrel,
                      const float *cw, const float4 *cf, float4 *r, Scalars *sc, float *r_soa, int soa_ld);
 void launch_sweep(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,

@@ -470,3 +470,31 @@ def test_contact_iterations_are_counted(pc):
             counted += st["contact_iters"]
     assert counted > 0
     cl.close()
+
+
+def test_residual_forwarding_parity(pc):
+    """A drape thrown at the sphere with two inner iterations per step: the
+    exit TOI falls below 1, residual forwarding (Sec. 6) runs 3 iterations
+    with the active constraints at weight k and no CCD, and the next step's z
+    carries 2 dx.  From the same states, GPU and oracle agree within 1e-5 of
+    the bounding-box diagonal, including the steps that use a forwarded dx."""
+    sc = wl.drape_sphere(side=16, sphere_subdiv=2)
+    v0 = sc.v0.copy()
+    v0[:, 2] -= 20.0
+    sc = dataclasses.replace(sc, v0=v0.astype(np.float32))
+    gp = params(pc, fixed_iters=1, warm_iters=2, max_outer=1, max_inner=2, solve_cycles=40, jacobi_sweeps=8,
+                r_warm=64, r_reuse=64, d_hat=1e-3, rf_toi=1.01, rf_iters=3)
+    cl = pc.Cloth(sc, gp)
+    orc = pd.Oracle(sc, pd.Params(fixed_iters=True, warm_iters=2, max_outer=1, max_inner=2, dhat=1e-3, rf_toi=1.01,
+                                  rf_iters=3))
+    rf_g = rf_o = 0
+    for k in range(4):
+        cl.step()
+        xo, vo, st = orc.step()
+        xg, vg = cl.state()
+        rf_g += cl.stats()["rf_iters"]
+        rf_o += st.rf_iters
+        assert np.max(np.abs(xg - xo)) <= 1e-5 * orc.model.L, k
+        orc.x, orc.v = xg.astype(np.float64), vg.astype(np.float64)  # the oracle keeps its own forwarded dx
+    assert rf_g > 0 and rf_g == rf_o
+    cl.close()

@@ -373,6 +373,76 @@ def test_oracle_drape_is_penetration_free():
 
 
 # ----------------------------------------------------------------------------
+# residual forwarding (Sec. 6, Eq. z_rf, end of Alg. 1)
+# ----------------------------------------------------------------------------
+
+def test_residual_forwarding_shifts_the_next_z_by_twice_dx():
+    """Eq. z_rf with h^2 M^-1 df = 2 dx: with no LG iteration the step
+    returns z, which must be x* + h v* + h^2 g + 2 dx on free rows (pins at
+    their targets); the forwarded dx is used once."""
+    sc = wl.tiny_scene(side=6, curved=True, pinned=True)
+    p = pd.Params(collisions=False, fixed_iters=True, warm_iters=0, max_inner=0)
+    o = pd.Oracle(sc, p)
+    rng = np.random.default_rng(3)
+    D = rng.normal(size=(sc.n, 3)) * 1e-3
+    D[~o.model.free] = 0.0
+    o.rf = D.copy()
+    xs, vs = o.x.copy(), o.v.copy()
+    h, g = p.dt, np.array(p.gravity)
+    x, v, _ = o.step()
+    ze = xs + h * vs + h * h * g + 2.0 * D
+    ze[~o.model.free] = sc.pins_at(h)
+    assert np.max(np.abs(x - ze)) < 1e-14
+    assert o.rf is None
+    x2, _, _ = o.step()
+    ze2 = x + h * v + h * h * g
+    ze2[~o.model.free] = sc.pins_at(2 * h)
+    assert np.max(np.abs(x2 - ze2)) < 1e-14
+
+
+def test_residual_forwarding_leaves_an_exact_free_fall_unchanged():
+    """A rigidly translating rest shape ends every step at the minimiser
+    x = z (up to the FP32 rounding of the filtered state on the collision
+    path, ~1e-8 m here), so forwarding (forced after every step: rf_toi above
+    the no-impact value 2) must find dx ~ 0 (a dx measured from x* instead of
+    the filtered x would be ~h|v| = 2 mm) and keep the closed-form trajectory
+    x_n = x_0 + n h v_0 + h^2 g n (n+1) / 2."""
+    sc = wl.tiny_scene(side=6, curved=True, pinned=False)
+    v0 = np.array([0.3, -0.1, 0.2])
+    sc.v0 = np.tile(v0, (sc.n, 1)).astype(np.float32)
+    v0 = sc.v0[0].astype(np.float64)
+    p = _params(collisions=True, rf_toi=3.0, rf_iters=4)
+    o = pd.Oracle(sc, p)
+    x0 = sc.verts.astype(np.float64)
+    g = np.array(p.gravity)
+    h = p.dt
+    for n in range(1, 7):
+        x, v, st = o.step()
+        assert st.rf_iters > 0
+        assert np.max(np.abs(o.rf)) < 1e-7
+        xe = x0 + n * h * v0 + h * h * g * n * (n + 1) / 2
+        assert np.max(np.abs(x - xe)) < 1e-6
+
+
+def test_residual_forwarding_lowers_the_residual_of_its_problem():
+    """After a filtered step with a small exit TOI (a drape thrown at the
+    sphere, two inner iterations), the forwarding iterations decrease the
+    PD residual of their problem (weights k, no CCD) and leave pinned rows
+    unmoved."""
+    sc = wl.drape_sphere(side=10, sphere_subdiv=2)
+    v0 = sc.v0.copy()
+    v0[:, 2] -= 20.0
+    sc.v0 = v0.astype(np.float32)
+    p = pd.Params(max_outer=1, max_inner=2, rf_toi=1.01, rf_iters=20, tol_inner=1e-14)
+    o = pd.Oracle(sc, p)
+    x, v, st = o.step()
+    assert st.t_toi < 1.0 and st.rf_iters == 20
+    assert st.rf_res1 < 0.6 * st.rf_res0
+    assert np.all(o.rf[~o.model.free] == 0.0) and np.all(np.isfinite(o.rf))
+    assert np.max(np.abs(o.rf)) > 0.0
+
+
+# ----------------------------------------------------------------------------
 # subspace reference
 # ----------------------------------------------------------------------------
 
