@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "Obstacle", "Scene", "grid_mesh", "icosphere", "box_mesh", "cylinder_mesh",
     "cone_skirt", "drape_sphere", "fold_on_box", "hanging_swept", "batched_drape",
-    "skirt_on_body", "tiny_scene", "seed_for",
+    "skirt_on_body", "tiny_scene", "beam_strip", "seed_for",
 ]
 
 
@@ -257,6 +257,25 @@ def drape_sphere(side: int = 32, size: float = 1.0, seed: int = seed_for(0), sph
     return Scene("drape_sphere_%d" % side, V.astype(np.float32), tris, pins,
                  np.zeros_like(V, dtype=np.float32), 0.1, 1e3, 1e-2, obs,
                  settings=dict(dt=1 / 200, steps=200, lg_iters=32))
+
+
+def beam_strip(nx: int = 250, ny: int = 40, length: float = 1.0, width: float = 0.16, k_bend: float = 1.0,
+               seed: int = seed_for(5), jitter: float = 1e-5) -> Scene:
+    """Horizontal strip clamped at one end (the paper's bending-strip scene,
+    Fig. beam: about 30 K DOFs, stiff bending, no collisions): an nx-by-ny
+    grid over length x width at z = 0 with the first two columns (x = 0 and
+    the next) pinned, so the clamp resists the bending moment of gravity.
+    density 0.1, stretch 1e3, bend k_bend, dt 1/200; seeded jitter of
+    +-1e-5 m on z only (the rest stays nearly flat)."""
+    rng = np.random.default_rng(seed)
+    uv, tris = grid_mesh(nx, ny, length, width)
+    V = np.zeros((len(uv), 3))
+    V[:, :2] = uv
+    V[:, 2] = _jitter(rng, len(uv), jitter)
+    pins = np.array([j * nx + i for j in range(ny) for i in range(2)], dtype=np.int32)
+    return Scene("beam_strip_%dx%d" % (nx, ny), V.astype(np.float32), tris, pins,
+                 np.zeros_like(V, dtype=np.float32), 0.1, 1e3, k_bend, [],
+                 settings=dict(dt=1 / 200, steps=100, lg_iters=20))
 
 
 def fold_on_box(side: int = 256, size: float = 2.0, seed: int = seed_for(1), box_subdiv: int = 32) -> Scene:
