@@ -52,6 +52,9 @@ def test_struct_layouts_match_header(libpath):
     assert p.gravity[2] == -9.8
     assert p.samples_vt == 3 and p.samples_ee == 4
     assert p.a_max == 20 and p.collisions == 1 and p.seed == 12345
+    # dependent launches on, residual forwarding off (8 iterations when enabled)
+    assert p.launch_overlap == 1 and p.rf_toi == 0.0 and p.rf_iters == 8
+    assert p.tensor_cores == 1 and p.bp_reuse == 0.0
 
 
 def test_binding_structs_have_the_header_layout(tmp_path):
