@@ -25,6 +25,28 @@ Barriers and Subspace Reuse", arXiv 2403.19272):
 
 Readings where the paper is silent (stretch model, bending stencil, contact
 target, thresholds) are documented beside the code that takes them.
+
+Pins (tests/test_oracle_pins.py; each checks the oracle against something
+other than itself):
+  Model (masses, H)        total mass = density * area; H symmetric positive
+                           definite, elastic rows sum to zero
+  stretch_targets          polar factor orthonormal, rotation-equivariant,
+                           minimal against random rotations (brute force)
+  bend_targets             planar null space and a fold identity of the stencil
+  rhs / solve / residual   dense Cholesky; closed-form free fall; rest states
+                           (rotated, pinned) are fixed points; PD energy
+                           decreases per LG iteration
+  contact_terms (R6)       targets land exactly on C = 0, least-norm among
+                           random feasible moves, identity when inactive
+  CollisionMesh.candidates contains every pair that collides (brute force)
+  Oracle.step              the closed forms above through the whole step, no
+                           triangle intersections on a drape, residual
+                           forwarding: exact 2 dx shift of the next z, dx ~ 0
+                           after an exact free fall, residual decrease
+  collide (C)              closest points against dense search; CCD golden
+                           cases and dense time sampling; partial-CCD identity
+The production mode (1e-3 relative residual, mixed precision) is parity
+unpinned: its error against this oracle is reported, not gated.
 """
 from __future__ import annotations
 

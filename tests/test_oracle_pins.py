@@ -373,6 +373,102 @@ def test_oracle_drape_is_penetration_free():
 
 
 # ----------------------------------------------------------------------------
+# closest points and the contact projection (Sec. 4.1, Sec. 5.1 / R6)
+# ----------------------------------------------------------------------------
+
+def _dense_vt(p, a, b, c, m=400):
+    u, v = np.meshgrid(np.linspace(0, 1, m + 1), np.linspace(0, 1, m + 1))
+    keep = (u + v) <= 1.0
+    u, v = u[keep], v[keep]
+    pts = a[None, :] + u[:, None] * (b - a)[None, :] + v[:, None] * (c - a)[None, :]
+    return float(np.min(np.linalg.norm(pts - p[None, :], axis=1)))
+
+
+def _dense_ee(a0, a1, b0, b1, m=600):
+    s_, t_ = np.meshgrid(np.linspace(0, 1, m + 1), np.linspace(0, 1, m + 1))
+    s_, t_ = s_.ravel(), t_.ravel()
+    pa = a0[None, :] + s_[:, None] * (a1 - a0)[None, :]
+    pb = b0[None, :] + t_[:, None] * (b1 - b0)[None, :]
+    return float(np.min(np.linalg.norm(pa - pb, axis=1)))
+
+
+def test_closest_points_match_a_dense_search():
+    """The gap vector sum_j c_j q_j of closest_coef has the length of the
+    minimum distance found by a dense barycentric (VT) or (s, t) (EE) search,
+    its coefficients sum to zero (translation invariance) and the closest
+    points lie on the primitives; cases include projections outside the
+    triangle (clamped to an edge or a corner) and nearly parallel edges."""
+    rng = np.random.default_rng(11)
+    cases_vt = [rng.normal(size=(4, 3)) for _ in range(12)]
+    cases_vt.append(np.array([[2.0, 2.0, 0.3], [0, 0, 0], [1, 0, 0], [0, 1, 0]]))   # beyond the hypotenuse
+    cases_vt.append(np.array([[-1.0, -1.0, 0.2], [0, 0, 0], [1, 0, 0], [0, 1, 0]]))  # beyond a corner
+    for q in cases_vt:
+        c = collide.closest_coef(q, 0)
+        assert abs(c.sum()) < 1e-12 and c[0] == -1.0
+        assert np.all(c[1:] >= -1e-12) and abs(c[1:].sum() - 1.0) < 1e-12
+        d = float(np.linalg.norm(c @ q))
+        dd = _dense_vt(q[0], q[1], q[2], q[3])
+        scale = float(np.max(np.linalg.norm(q[1:] - q[1], axis=1)))
+        assert d <= dd + 1e-12 and dd - d <= 2e-3 * scale
+    cases_ee = [rng.normal(size=(4, 3)) for _ in range(12)]
+    cases_ee.append(np.array([[0, 0, 0], [1, 0, 0], [0.2, 0.5, 1e-9], [1.2, 0.5, 0.0]]))  # nearly parallel
+    for q in cases_ee:
+        c = collide.closest_coef(q, 1)
+        assert abs(c.sum()) < 1e-12
+        s_, t_ = -c[1], c[3]
+        assert -1e-12 <= s_ <= 1 + 1e-12 and -1e-12 <= t_ <= 1 + 1e-12
+        d = float(np.linalg.norm(c @ q))
+        dd = _dense_ee(q[0], q[1], q[2], q[3])
+        scale = float(max(np.linalg.norm(q[1] - q[0]), np.linalg.norm(q[3] - q[2])))
+        assert d <= dd + 1e-12 and dd - d <= 2e-3 * scale
+
+
+def test_contact_projection_is_the_least_norm_move_onto_the_gap_plane():
+    """R6 (Sec. 5.1 with A = B = Id): for an active pair whose gap along the
+    start direction is below dhat, the spring targets put the pair exactly on
+    C = 0, and no other displacement of the movable vertices that does so is
+    shorter (random feasible alternatives); an obstacle vertex gets no
+    spring; on the inactive side (C >= 0) each target is the vertex itself."""
+    from types import SimpleNamespace
+    dhat = 1e-3
+    # vertex 0 above triangle (1, 2, 3); all cloth (movable), or 3 = obstacle
+    X0 = np.array([[0.3, 0.3, 2 * dhat], [0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=np.float64)
+    x = X0.copy()
+    x[0, 2] = 0.3 * dhat            # moved into the gap band
+    x[1:, 2] += 0.1 * dhat           # the triangle rose a little
+    quads = np.array([[0, 1, 2, 3]])
+    kinds = np.array([0])
+    w = np.array([5.0])
+    for fixed in ([False, False, False, False], [False, False, False, True]):
+        cm = SimpleNamespace(nc=4, fixed_v=np.array(fixed))
+        cw, cy = pd.contact_terms(cm, X0, x, np.array([True]), quads, kinds, w, dhat)
+        coef = collide.closest_coef(X0, 0)
+        n0 = pd.contact_normal(X0, 0, coef)
+        mov = [j for j in range(4) if not fixed[j]]
+        assert all(cw[j] == 5.0 for j in mov) and all(cw[j] == 0.0 for j in range(4) if fixed[j])
+        y = x.copy()
+        for j in mov:
+            y[j] = cy[j] / cw[j]
+        assert abs(float(coef @ y @ n0) - dhat) < 1e-15
+        move = y - x
+        base = float(np.sum(move ** 2))
+        rng = np.random.default_rng(5)
+        for _ in range(200):
+            eta = np.zeros_like(x)
+            eta[mov] = rng.normal(size=(len(mov), 3)) * 1e-3
+            # keep the alternative on the plane: remove the component of eta that changes C
+            g = np.zeros_like(x)
+            g[mov] = coef[mov][:, None] * n0[None, :]
+            eta -= (np.sum(g * eta) / np.sum(g * g)) * g
+            assert float(np.sum((move + eta) ** 2)) >= base - 1e-18
+    # inactive side: C >= 0 at x leaves every target at its vertex
+    x2 = X0.copy()
+    cm = SimpleNamespace(nc=4, fixed_v=np.zeros(4, bool))
+    cw, cy = pd.contact_terms(cm, X0, x2, np.array([True]), quads, kinds, w, dhat)
+    assert np.allclose(cy / cw[:, None], x2, rtol=0, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------
 # residual forwarding (Sec. 6, Eq. z_rf, end of Alg. 1)
 # ----------------------------------------------------------------------------
 
