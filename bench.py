@@ -4,8 +4,10 @@
 Workload: the 512x512 hanging cloth (262,144 vertices, 522,242 triangles),
 1 m wide in the x-z plane, top row pinned and swept 0.2 m at 1 Hz, dt 1/200 s,
 self-collision on; every step iterates until the PD residual falls to 1e-3
-of its value at z (mixed form: BF16 basis of 256 modes, FP64 reduced
-solves; plain form: all FP32).  Metric: ms per time step (lower is better).
+of its value at z.  Forms: mixed16 (the headline: FP16 basis of 256 modes
+scaled by a power of two, tcgen05 projections, FP64 reduced solves), mixed
+(the same with a BF16 basis) and fp32 (all FP32).  Metric: ms per time step
+(lower is better).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -439,7 +441,7 @@ def main():
         "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": head, "basis": "r=256 (r_reuse=32 with collision springs)",
-                   "l2": "inputs larger than L2 (basis 134 MB BF16 / 268 MB FP32 plus matrices and state)",
+                   "l2": "inputs larger than L2 (basis 134 MB in 16 bits / 268 MB FP32 plus matrices and state)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "forms": {f: {"ms_per_step": round(d["ms"], 3), "lg_iters_per_step": d["iters"],
                       "vertex_iters_per_s": round(scene.n * d["iters"] / (d["ms"] * 1e-3), 1),
