@@ -263,6 +263,12 @@ typedef struct {
     double algo_bytes;
 } pdc_kernel_time;
 
+/* Diagnostics read from the environment at pdc_create: PDC_LOG (any value)
+ * prints per-iteration residuals, pass decisions and retries to stderr;
+ * PDC_SYNC_CHECK (any value) synchronises the stream after every profiled
+ * region and fails the call with PDC_ERR_CUDA naming the region if a CUDA
+ * error is pending (slow; for locating a fault). */
+
 /* enable = 1 starts profiling and clears the accumulated times; 0 stops. */
 pdc_status pdc_set_profiling(pdc_handle h, int32_t enable);
 /* Copies at most cap entries; *count receives the number of kernel kinds. */
