@@ -45,6 +45,9 @@ other than itself):
                            after an exact free fall, residual decrease
   collide (C)              closest points against dense search; CCD golden
                            cases and dense time sampling; partial-CCD identity
+  pccd_adaptive            rho* scale/translation invariant; lattice covers its
+                           domain to h/sqrt(2); flags every crossing with
+                           t* <= alpha (the argument of Eq. sample_bound)
 The production mode (1e-3 relative residual, mixed precision) is parity
 unpinned: its error against this oracle is reported, not gated.
 """
@@ -58,7 +61,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import collide
+from . import collide, pccd_adaptive
 
 
 # ----------------------------------------------------------------------------
@@ -88,6 +91,8 @@ class Params:
     fixed_iters: bool = False      # parity mode: run exactly warm/max_outer/max_inner
     rf_toi: float = 0.0            # residual forwarding (Sec. 6) when the exit TOI is below this (0: off)
     rf_iters: int = 8              # cap on its LG iterations (exact count in parity mode)
+    pccd_adaptive: bool = False    # partial-CCD samples from Eq. (sample_bound) instead of fixed patterns
+    pccd_max_axis: int = 64        # cap on the per-axis lattice size of the adaptive samples
 
 
 # ----------------------------------------------------------------------------
@@ -588,7 +593,11 @@ class Oracle:
                 inner_done += 1
                 # partial CCD (Sec. 4.1) on the candidates over (x^-, x^+)
                 Xp = self._all(xn, obs_next).astype(np.float32)
-                flags, _ = collide.partial_ccd(Xm32, Xp, quads, kinds, p.samples_vt, p.samples_ee, p.dhat)
+                if p.pccd_adaptive:
+                    flags = pccd_adaptive.partial_ccd_adaptive(Xm32, Xp, quads, kinds, p.dhat, p.alpha,
+                                                               p.pccd_max_axis)[0]
+                else:
+                    flags, _ = collide.partial_ccd(Xm32, Xp, quads, kinds, p.samples_vt, p.samples_ee, p.dhat)
                 new_state = {}
                 for i, kk in enumerate(keys):
                     was, a = state.get(kk, (False, 0))

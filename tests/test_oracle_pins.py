@@ -469,6 +469,88 @@ def test_contact_projection_is_the_least_norm_move_onto_the_gap_plane():
 
 
 # ----------------------------------------------------------------------------
+# adaptive partial-CCD sample density (Eq. sample_bound)
+# ----------------------------------------------------------------------------
+
+def test_sample_bound_is_scale_and_translation_invariant():
+    """rho* is a length ratio in parameter space: scaling or translating the
+    pair (both times) leaves it unchanged."""
+    from oracle import pccd_adaptive as pa
+    rng = np.random.default_rng(4)
+    for kind in (0, 1):
+        for _ in range(5):
+            q0, q1 = rng.normal(size=(4, 3)), rng.normal(size=(4, 3))
+            r = pa.sample_bound(q0, q1, kind, 0.8)
+            sh = rng.normal(size=3)
+            assert pa.sample_bound(3.7 * q0 + sh, 3.7 * q1 + sh, kind, 0.8) == pytest.approx(r, rel=1e-10)
+
+
+def test_sample_lattice_covers_its_domain():
+    """Every point of the parameter domain (VT: b1, b2 >= 0, b1 + b2 <= 1;
+    EE: the unit square) lies within h / sqrt(2) of a lattice sample."""
+    from oracle import pccd_adaptive as pa
+    rng = np.random.default_rng(9)
+    for kind in (0, 1):
+        for m in (1, 3, 7):
+            L = pa.lattice(kind, m)
+            P = rng.uniform(size=(2000, 2))
+            if kind == 0:
+                P = P[P.sum(axis=1) <= 1.0]
+            d = np.min(np.linalg.norm(P[:, None, :] - L[None, :, :], axis=2), axis=1)
+            assert d.max() <= (1.0 / m) / np.sqrt(2.0) + 1e-12
+
+
+def test_adaptive_density_flags_every_crossing_before_alpha():
+    """Sec. 4.1: a pair whose exact time of impact is at most alpha has
+    Q < 0 on a disc of radius rho* around the contact parameters, so the
+    lattice of spacing <= sqrt(2) rho* flags it (random VT and EE crossings
+    whose elements are comparable in size to their distance, so that the
+    lattice stays below its cap)."""
+    from oracle import pccd_adaptive as pa
+    rng = np.random.default_rng(7)
+    alpha, checked = 0.8, 0
+    for trial in range(700):
+        kind = trial % 2
+        if kind == 0:
+            q0 = np.zeros((4, 3))
+            q0[1:] = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]]) + rng.normal(size=(3, 3)) * 0.05
+            q0[0] = [rng.uniform(-0.2, 1.0), rng.uniform(-0.2, 1.0), rng.uniform(0.3, 1.5)]
+            q1 = q0.copy()
+            q1[0] = [rng.uniform(-0.2, 1.0), rng.uniform(-0.2, 1.0), -rng.uniform(0.3, 1.5)]
+            q1[1:] += rng.normal(size=(3, 3)) * 0.05
+        else:
+            q0 = np.array([[0, 0, 0], [1, 0, 0], [0, 0, 0], [0, 1, 0]], dtype=float) + rng.normal(size=(4, 3)) * 0.05
+            q0[2:] += [rng.uniform(0, 0.5), rng.uniform(-0.5, 0), rng.uniform(0.3, 1.2)]
+            q1 = q0.copy()
+            q1[2:, 2] -= rng.uniform(0.6, 2.5)
+            q1 += rng.normal(size=(4, 3)) * 0.05
+        q0, q1 = q0.astype(np.float32), q1.astype(np.float32)
+        toi = collide.ccd(q0, q1, np.arange(4)[None, :], np.array([kind]), 1e-9)[0]
+        if not (0.0 < toi <= alpha):
+            continue
+        act, _, m, cap = pa.partial_ccd_adaptive(q0, q1, np.arange(4)[None, :], [kind], 0.0, alpha, 64)
+        if cap[0]:
+            continue
+        assert act[0], (trial, kind, toi, m[0])
+        checked += 1
+    assert checked >= 100
+
+
+def test_oracle_drape_with_adaptive_samples_is_penetration_free():
+    """The step with adaptive partial-CCD samples (Eq. sample_bound) still
+    keeps every step intersection free (the exit line search guarantees it)
+    and reaches the sphere."""
+    sc = wl.drape_sphere(side=10, sphere_subdiv=2)
+    o = pd.Oracle(sc, pd.Params(max_outer=2, max_inner=4, pccd_adaptive=True, pccd_max_axis=16))
+    allT = o.cm.tris
+    for k in range(22):
+        x, v, st = o.step()
+        X = np.concatenate([x] + o.obs)
+        assert len(collide.intersecting_triangle_pairs(X, allT)) == 0
+    assert x[:, 2].min() < -0.04
+
+
+# ----------------------------------------------------------------------------
 # residual forwarding (Sec. 6, Eq. z_rf, end of Alg. 1)
 # ----------------------------------------------------------------------------
 
