@@ -173,7 +173,10 @@ typedef struct {
 
 /* Defaults: dt 1/200, g = (0,0,-9.8), K = 2, a_max 20, alpha 0.8, automatic
  * d_hat, eta 1e-9, tolerances 1e-3 / 5e-2, 4 outer x 32 inner, 5 warm
- * iterations, 4 sweeps, 1 cycle, no basis, FP32, samples 3/4, collisions on. */
+ * iterations, 4 damped Jacobi sweeps (automatic omega), 1 cycle, no basis,
+ * FP32, samples 3/4, collisions on, no LG acceleration, tensor cores for the
+ * mixed forms, dependent launches on, broad-phase reuse and residual
+ * forwarding off. */
 void pdc_default_params(pdc_params *p);
 
 /* Build the solver for one cloth mesh (Sec. 3; Eq. (global) rest matrix,
