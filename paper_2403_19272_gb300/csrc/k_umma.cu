@@ -17,11 +17,13 @@
 //               B = q hi/lo [16][r]                (written by the CTA)
 //   projection: A = U^T tile [128 j][128 i] from Ut [ld][n_pad]  (TMA)
 //               B = r hi/lo [16][128 i]            (written by the CTA)
-// One CTA per 128-row tile, 4 warps: thread 0 issues the TMA loads and the
-// MMAs, warp 0 owns the 32 TMEM columns, all four warps read the
-// accumulator (warp w: TMEM lanes 32w..32w+31).  Every wait on an mbarrier
-// is bounded by the global timer; on expiry the CTA records an error bit,
-// waits (bounded) for its copies, frees its TMEM and returns.
+// Persistent kernels: one CTA per SM loops over its 128-row tiles through a
+// ring of shared-memory stages (6 warps: 0-3 write the split operand and read
+// the accumulator, warp w reading TMEM lanes 32w..32w+31; warp 4 issues the
+// TMA loads; warp 5 owns the 32 TMEM columns and issues the MMAs).  Every
+// wait on an mbarrier is bounded by the global timer; on expiry the CTA
+// records an error bit, waits (bounded) for its copies, frees its TMEM and
+// returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -161,214 +163,12 @@ template <bool F16> __device__ inline float block_scale(float local_max, float *
     }
 }
 
-struct alignas(1024) LiftSmem {
-    unsigned char A[UMMA_MAX_LD / KBOX][ABOX_BYTES];
-    unsigned char B[UMMA_MAX_LD / KBOX][BBOX_BYTES];
-    uint64_t bar_tma, bar_mma;
-    uint32_t taddr;
-    int fail;
-    float red[4];
-};
-
-struct alignas(1024) ProjSmem {
-    unsigned char A[UMMA_MAX_LD / TILE][TILE / KBOX][ABOX_BYTES];
-    unsigned char B[TILE / KBOX][BBOX_BYTES];
-    uint64_t bar_tma, bar_mma;
-    uint32_t taddr;
-    int fail;
-    float red[4];
-};
-
 template <class Smem> __device__ inline Smem &smem_1024() {
     extern __shared__ unsigned char smem_raw[];
     uintptr_t p = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023;
     return *reinterpret_cast<Smem *>(p);
 }
 
-// Wait for the MMAs; on expiry mark the CTA failed (no TMEM reads follow).
-__device__ inline void wait_or_flag(uint64_t *bar, uint32_t parity, int *fail) {
-    if (!mbar_wait(bar, parity)) atomicOr(fail, 1);
-}
-
-// dout_i = din_i + sum_j U[i][j] q_j for the 128 rows of this CTA's tile.
-template <bool F16>
-__global__ void __launch_bounds__(128, 1) k_lift_umma(const __grid_constant__ CUtensorMap mapU, int n, int ld, int r,
-                                                      const float *__restrict__ q, const float4 *__restrict__ din,
-                                                      float4 *__restrict__ dout, int *err) {
-    LiftSmem &S = smem_1024<LiftSmem>();
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nkb = ld / KBOX;
-    const int row0 = blockIdx.x * TILE;
-    if (tid == 0) {
-        S.fail = 0;
-        mbar_init(&S.bar_tma, 1);
-        mbar_init(&S.bar_mma, 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        mbar_expect_tx(&S.bar_tma, (uint32_t)(nkb * ABOX_BYTES));
-        for (int kb = 0; kb < nkb; ++kb) tma_load_2d(S.A[kb], &mapU, &S.bar_tma, kb * KBOX, row0);
-    }
-    if (warp == 0) {
-        __syncwarp();
-        tmem_alloc(&S.taddr);
-    }
-    // B = q split into hi / lo parts: [16][ld] in swizzled 64-column boxes
-    float qmax = 0.f;
-    for (int e = tid; e < 3 * r; e += blockDim.x) qmax = fmaxf(qmax, fabsf(q[e]));
-    const float scale = block_scale<F16>(qmax, S.red);
-    for (int c = tid; c < 16 * (ld / 8); c += blockDim.x) {
-        int nn = c / (ld / 8), k0 = (c % (ld / 8)) * 8;
-        float3 v[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            int k = k0 + t;
-            v[t] = k < r ? make_float3(q[k * 3 + 0], q[k * 3 + 1], q[k * 3 + 2]) : make_float3(0.f, 0.f, 0.f);
-        }
-        uint4 val = split_chunk<F16>(nn, v, scale);
-        *reinterpret_cast<uint4 *>(S.B[k0 / KBOX] + sw128_offset(nn, k0 % KBOX)) = val;
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = S.taddr;
-    if (tid == 0) {
-        if (mbar_wait(&S.bar_tma, 0)) {
-            tc_fence_after();
-            for (int kb = 0; kb < nkb; ++kb)
-#pragma unroll
-                for (int k = 0; k < KBOX / 16; ++k)
-                    umma<F16>(tmem, desc_sw128(smem_u32(S.A[kb]) + k * 32), desc_sw128(smem_u32(S.B[kb]) + k * 32),
-                              (kb | k) != 0);
-            umma_commit(&S.bar_mma);
-        } else {
-            S.fail = 1;
-            mbar_arrive(&S.bar_mma);
-        }
-    }
-    __syncwarp();
-    wait_or_flag(&S.bar_mma, 0, &S.fail);
-    tc_fence_after();
-    __syncthreads();  // S.fail is uniform from here on
-    if (S.fail) {
-        if (tid == 0) {
-            atomicOr(err, PDC_DEVERR_UMMA);
-            mbar_wait(&S.bar_tma, 0);  // let the copies land before the CTA exits
-        }
-    } else {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), v);
-        int i = row0 + warp * 32 + lane;
-        if (i < n) {
-            const float inv = 1.f / scale;  // exact: a power of two
-            float4 d = din ? din[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-            dout[i] = make_float4(d.x + inv * (v[0] + v[3]), d.y + inv * (v[1] + v[4]), d.z + inv * (v[2] + v[5]),
-                                  0.f);
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        __syncwarp();
-        tmem_dealloc(tmem);
-    }
-}
-
-// partial[b][j][c] = sum over the 128 rows i of tile b of U[i][j] rl_i[c].
-template <bool F16>
-__global__ void __launch_bounds__(128, 1) k_project_umma(const __grid_constant__ CUtensorMap mapUt, int n, int ld,
-                                                         int r, const float4 *__restrict__ rl,
-                                                         float *__restrict__ partial, int *err) {
-    ProjSmem &S = smem_1024<ProjSmem>();
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nh = ld / TILE;
-    const int i0 = blockIdx.x * TILE;
-    if (tid == 0) {
-        S.fail = 0;
-        mbar_init(&S.bar_tma, 1);
-        mbar_init(&S.bar_mma, 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        mbar_expect_tx(&S.bar_tma, (uint32_t)(nh * (TILE / KBOX) * ABOX_BYTES));
-        for (int h = 0; h < nh; ++h)
-            for (int kb = 0; kb < TILE / KBOX; ++kb) tma_load_2d(S.A[h][kb], &mapUt, &S.bar_tma, i0 + kb * KBOX, h * TILE);
-    }
-    if (warp == 0) {
-        __syncwarp();
-        tmem_alloc(&S.taddr);
-    }
-    // B = r split into hi / lo parts: [16][128] for rows i0 .. i0+127
-    float vmax = 0.f;
-    if (i0 + tid < n) {
-        float3 a = f3(rl[i0 + tid]);
-        vmax = fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z)));
-    }
-    const float scale = block_scale<F16>(vmax, S.red);
-    for (int c = tid; c < 16 * (TILE / 8); c += blockDim.x) {
-        int nn = c / (TILE / 8), k0 = (c % (TILE / 8)) * 8;
-        float3 v[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            int i = i0 + k0 + t;
-            v[t] = i < n ? f3(rl[i]) : make_float3(0.f, 0.f, 0.f);
-        }
-        uint4 val = split_chunk<F16>(nn, v, scale);
-        *reinterpret_cast<uint4 *>(S.B[k0 / KBOX] + sw128_offset(nn, k0 % KBOX)) = val;
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = S.taddr;
-    if (tid == 0) {
-        if (mbar_wait(&S.bar_tma, 0)) {
-            tc_fence_after();
-            for (int h = 0; h < nh; ++h)
-                for (int kb = 0; kb < TILE / KBOX; ++kb)
-#pragma unroll
-                    for (int k = 0; k < KBOX / 16; ++k)
-                        umma<F16>(tmem + 16 * h, desc_sw128(smem_u32(S.A[h][kb]) + k * 32),
-                                  desc_sw128(smem_u32(S.B[kb]) + k * 32), (kb | k) != 0);
-            umma_commit(&S.bar_mma);
-        } else {
-            S.fail = 1;
-            mbar_arrive(&S.bar_mma);
-        }
-    }
-    __syncwarp();
-    wait_or_flag(&S.bar_mma, 0, &S.fail);
-    tc_fence_after();
-    __syncthreads();  // S.fail is uniform from here on
-    if (S.fail) {
-        if (tid == 0) {
-            atomicOr(err, PDC_DEVERR_UMMA);
-            mbar_wait(&S.bar_tma, 0);
-        }
-    } else {
-        for (int h = 0; h < nh; ++h) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * h, v);
-            int j = h * TILE + warp * 32 + lane;
-            if (j < r) {
-                const float inv = 1.f / scale;  // exact: a power of two
-                float *p = partial + ((long long)blockIdx.x * ld + j) * 3;
-                p[0] = inv * (v[0] + v[3]);
-                p[1] = inv * (v[1] + v[4]);
-                p[2] = inv * (v[2] + v[5]);
-            }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        __syncwarp();
-        tmem_dealloc(tmem);
-    }
-}
 
 // ------------------------------------------------------------------ persistent, pipelined versions
 // One CTA per SM loops over its tiles with a ring of LSTAGES shared-memory
@@ -684,8 +484,6 @@ __global__ void k_umma_reduce(int r, int ld, int nblocks, const float *__restric
     if (lane == 0) g[e] = s;
 }
 
-size_t lift_smem() { return sizeof(LiftSmem) + 1024; }
-size_t proj_smem() { return sizeof(ProjSmem) + 1024; }
 size_t lift_p_smem() { return sizeof(LiftPSmem) + 1024; }
 size_t proj_p_smem() { return sizeof(ProjPSmem) + 1024; }
 
@@ -726,10 +524,6 @@ void umma_setup(UmmaMaps &M, const void *U, const void *Ut, bool f16, int n, int
     if (!umma_supported(ld, n) || !U || !Ut) return;
     encode_map(&M.mapU, U, (uint64_t)ld, (uint64_t)n, (uint64_t)ld, f16);
     encode_map(&M.mapUt, Ut, (uint64_t)n, (uint64_t)ld, (uint64_t)n_pad, f16);
-    PDC_CK(cudaFuncSetAttribute(k_lift_umma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lift_smem()));
-    PDC_CK(cudaFuncSetAttribute(k_lift_umma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lift_smem()));
-    PDC_CK(cudaFuncSetAttribute(k_project_umma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem()));
-    PDC_CK(cudaFuncSetAttribute(k_project_umma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem()));
     PDC_CK(cudaFuncSetAttribute(k_lift_umma_p<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lift_p_smem()));
     PDC_CK(cudaFuncSetAttribute(k_lift_umma_p<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lift_p_smem()));
     PDC_CK(cudaFuncSetAttribute(k_project_umma_p<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -749,42 +543,29 @@ int umma_project_blocks(int n) { return (n + TILE - 1) / TILE; }
 
 void launch_project_umma(cudaStream_t s, const UmmaMaps &M, int r, const float4 *rl, float *partial, double *g,
                          int *err, bool overlap) {
-    int nb;
-    if (M.persistent) {
-        nb = std::max(1, std::min(M.sms, umma_project_blocks(M.n)));
-        if (M.f16)
-            launch_dependent(overlap, k_project_umma_p<true>, nb, PTHREADS, proj_p_smem(), s, M.mapUt, M.n, M.ld, r,
-                             rl, partial, err);
-        else
-            launch_dependent(overlap, k_project_umma_p<false>, nb, PTHREADS, proj_p_smem(), s, M.mapUt, M.n, M.ld, r,
-                             rl, partial, err);
-    } else {
-        nb = umma_project_blocks(M.n);
-        if (M.f16) k_project_umma<true><<<nb, 128, proj_smem(), s>>>(M.mapUt, M.n, M.ld, r, rl, partial, err);
-        else k_project_umma<false><<<nb, 128, proj_smem(), s>>>(M.mapUt, M.n, M.ld, r, rl, partial, err);
-    }
+    const int nb = std::max(1, std::min(M.sms, umma_project_blocks(M.n)));
+    if (M.f16)
+        launch_dependent(overlap, k_project_umma_p<true>, nb, PTHREADS, proj_p_smem(), s, M.mapUt, M.n, M.ld, r, rl,
+                         partial, err);
+    else
+        launch_dependent(overlap, k_project_umma_p<false>, nb, PTHREADS, proj_p_smem(), s, M.mapUt, M.n, M.ld, r, rl,
+                         partial, err);
     PDC_LAUNCH_CK();
     int thr = r * 3 * 32;
-    launch_dependent(overlap && M.persistent, k_umma_reduce, (thr + 255) / 256, 256, 0, s, r, M.ld, nb,
-                     (const float *)partial, g);
+    launch_dependent(overlap, k_umma_reduce, (thr + 255) / 256, 256, 0, s, r, M.ld, nb, (const float *)partial, g);
     PDC_LAUNCH_CK();
 }
 
 void launch_lift_umma(cudaStream_t s, const UmmaMaps &M, int r, const float *q, const float4 *din, float4 *dout,
                       int *err, bool overlap) {
-    int nt = (M.n + TILE - 1) / TILE;
-    if (M.persistent) {
-        int nb = std::max(1, std::min(M.sms, nt));
-        if (M.f16)
-            launch_dependent(overlap, k_lift_umma_p<true>, nb, PTHREADS, lift_p_smem(), s, M.mapU, M.n, M.ld, r, q,
-                             din, dout, err);
-        else
-            launch_dependent(overlap, k_lift_umma_p<false>, nb, PTHREADS, lift_p_smem(), s, M.mapU, M.n, M.ld, r, q,
-                             din, dout, err);
-    } else {
-        if (M.f16) k_lift_umma<true><<<nt, 128, lift_smem(), s>>>(M.mapU, M.n, M.ld, r, q, din, dout, err);
-        else k_lift_umma<false><<<nt, 128, lift_smem(), s>>>(M.mapU, M.n, M.ld, r, q, din, dout, err);
-    }
+    const int nt = (M.n + TILE - 1) / TILE;
+    const int nb = std::max(1, std::min(M.sms, nt));
+    if (M.f16)
+        launch_dependent(overlap, k_lift_umma_p<true>, nb, PTHREADS, lift_p_smem(), s, M.mapU, M.n, M.ld, r, q, din,
+                         dout, err);
+    else
+        launch_dependent(overlap, k_lift_umma_p<false>, nb, PTHREADS, lift_p_smem(), s, M.mapU, M.n, M.ld, r, q, din,
+                         dout, err);
     PDC_LAUNCH_CK();
 }
 

@@ -21,7 +21,6 @@ struct UmmaMaps {
     CUtensorMap mapUt;
     int n = 0, ld = 0;
     bool f16 = false;  // FP16 (scaled) basis instead of BF16
-    bool persistent = true;  // one pipelined CTA per SM (else one CTA per tile)
     int sms = 1;
     bool ok = false;
 };
