@@ -608,12 +608,6 @@ __global__ void k_lerp(int nv, const float4 *__restrict__ a, const float4 *__res
     out[i] = f4(p + s * (q - p));
 }
 
-__global__ void k_velocity(int n, const float4 *__restrict__ xn, const float4 *__restrict__ xs, float inv_h,
-                           float4 *__restrict__ v) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    v[i] = f4(inv_h * (f3(xn[i]) - f3(xs[i])));
-}
 
 inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
@@ -759,9 +753,5 @@ void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const
     PDC_LAUNCH_CK();
 }
 
-void launch_velocity(cudaStream_t s, int n, const float4 *xnew, const float4 *xs, float inv_h, float4 *v) {
-    if (n > 0) k_velocity<<<nblk(n, 256), 256, 0, s>>>(n, xnew, xs, inv_h, v);
-    PDC_LAUNCH_CK();
-}
 
 }  // namespace pdc

@@ -209,13 +209,5 @@ void launch_set_pins(cudaStream_t s, const int *pins, int npins, const float4 *t
 void launch_restart(cudaStream_t s, int n, const float4 *xs, const float4 *um, float4 *u, float4 *xabs);
 void launch_scale_disp(cudaStream_t s, int n, const float4 *xs, const float4 *u, const double *s_frac, float4 *um,
                        float4 *xm);
-void launch_velocity(cudaStream_t s, int n, const float4 *xnew, const float4 *xs, float inv_h, float4 *v);
-
-// ---------------------------------------------------------------- kernels (k_collide.cu)
-struct BroadPhase;
-void bp_run(cudaStream_t s, BroadPhase &bp, const CollView &cv, const float4 *x0, const float4 *x1, float dhat,
-            Scalars *sc);
-void launch_ccd(cudaStream_t s, const CollView &cv, const int2 *vt, long long nvt, const int2 *ee, long long nee,
-                const float4 *x0, const float4 *x1, double eta, unsigned long long *toi_min, float *toi_out);
 
 }  // namespace pdc
