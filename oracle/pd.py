@@ -38,6 +38,11 @@ other than itself):
                            decreases per LG iteration
   contact_terms (R6)       targets land exactly on C = 0, least-norm among
                            random feasible moves, identity when inactive
+  ndb_* (Eq. exp)          life-span counters and weights of a scripted
+                           active/inactive sequence written out by hand
+                           (consecutive count, reset, cap, w = k K^a), driven
+                           by the partial CCD of a vertex moved across the
+                           activity threshold; the step's own trace obeys them
   CollisionMesh.candidates contains every pair that collides (brute force)
   Oracle.step              the closed forms above through the whole step, no
                            triangle intersections on a drape, residual
@@ -421,6 +426,49 @@ def contact_terms(cm: CollisionMesh, Xall0, xall, active, quads, kinds, weights,
 
 
 # ----------------------------------------------------------------------------
+# non-distance barrier bookkeeping (Sec. 4, Eq. exp)
+# ----------------------------------------------------------------------------
+
+def ndb_weight(k, K, a):
+    """Eq. (exp): the weight of a constraint whose life-span counter is a,
+    w = k * K^a (a may be an array)."""
+    return k * np.power(float(K), np.asarray(a, dtype=np.float64))
+
+
+def ndb_after_partial_ccd(state, keys, flags, a_max):
+    """Constraint set after one partial CCD (Sec. 4.1) of one LG iteration.
+
+    state maps a pair key to (active, a).  a counts the consecutive LG
+    iterations in which the pair has been active (Sec. 4, text of Eq. exp):
+    a pair flagged now that was active before keeps counting, a <- a + 1
+    (capped at a_max); a pair flagged now that was not active starts at 0;
+    a pair not flagged is inactive and leaves the set, so its counter starts
+    again from 0 when it is next flagged."""
+    new_state = {}
+    for i, kk in enumerate(keys):
+        if flags[i]:
+            was, a = state.get(kk, (False, 0))
+            new_state[kk] = (True, min(a + 1, a_max) if was else 0)
+    return new_state
+
+
+def ndb_after_full_ccd(state, keys, toi):
+    """Constraint set after a full CCD over the fresh candidate list keys
+    (Alg. 1, FullCCD): a pair with an impact in [0, 1] becomes active and
+    keeps the counter it had (0 when it was not active); an active pair
+    without an impact stays active with its counter; pairs that are no
+    longer candidates leave the set."""
+    new_state = {}
+    for i, kk in enumerate(keys):
+        act, a = state.get(kk, (False, 0))
+        if toi[i] <= 1.0:
+            act = True
+        if act:
+            new_state[kk] = (act, a)
+    return new_state
+
+
+# ----------------------------------------------------------------------------
 # the step (Alg. 1, Sec. 7)
 # ----------------------------------------------------------------------------
 
@@ -476,7 +524,12 @@ class Oracle:
         return float(np.linalg.norm(self.model.residual(x, z, cw, cy)))
 
     def step(self, x_star=None, v_star=None, pin_next=None, obs_next=None, trace=None):
-        """Advance one time step; returns (x_new, v_new, stats)."""
+        """Advance one time step; returns (x_new, v_new, stats).
+
+        trace (a list, optional) receives one record per inner LG iteration:
+        the constraint set it started from, the NDB weights and activity each
+        candidate pair had in its contact springs, the partial-CCD flags after
+        its global solve and the constraint set those flags produced."""
         p, M = self.p, self.model
         h = p.dt
         if x_star is None:
@@ -547,10 +600,7 @@ class Oracle:
         xm = xm_all[: cm.nc].copy()
         obs_m = [xm_all[a:b] for a, b in cm.obs_slices]
         pin_m = xm[~M.free].copy()
-        state: Dict = {}
-        for i, kk in enumerate(keys):
-            if toi[i] <= 1.0:
-                state[kk] = (True, 0)
+        state: Dict = ndb_after_full_ccd({}, keys, toi)
         # the iterate starts at x^- with pinned rows at their targets
         x = xm.copy()
         x[~M.free] = pin_next
@@ -560,15 +610,8 @@ class Oracle:
             Xp = self._all(xp, obs_next).astype(np.float32)
             qd, kd, ky = cm.candidates(Xm32, Xp, p.dhat)
             tt = collide.ccd(Xm32, Xp, qd, kd, p.eta)
-            new_state = {}
-            for i, kk in enumerate(ky):
-                act, a = state.get(kk, (False, 0))
-                if tt[i] <= 1.0:
-                    act = True
-                if act:
-                    new_state[kk] = (act, a)
             tmin = float(tt.min()) if len(tt) else 2.0
-            return qd, kd, ky, new_state, tmin
+            return qd, kd, ky, ndb_after_full_ccd(state, ky, tt), tmin
 
         # the first inner loop uses the candidates of the initial full CCD; the
         # first outer pass always ends with a full CCD (pinned rows of x^+ sit
@@ -582,7 +625,7 @@ class Oracle:
             for it in range(p.max_inner):
                 act = np.array([state.get(kk, (False, 0))[0] for kk in keys], dtype=bool)
                 aa = np.array([state.get(kk, (False, 0))[1] for kk in keys], dtype=np.int64)
-                w = self.k * np.power(p.K_ndb, aa.astype(np.float64))
+                w = ndb_weight(self.k, p.K_ndb, aa)
                 xall = self._all(x, obs_next)
                 contact = contact_terms(cm, xm_all, xall, act, quads, kinds, w, p.dhat)
                 if p.tol_rel_residual > 0 and not p.fixed_iters:
@@ -598,14 +641,12 @@ class Oracle:
                                                                p.pccd_max_axis)[0]
                 else:
                     flags, _ = collide.partial_ccd(Xm32, Xp, quads, kinds, p.samples_vt, p.samples_ee, p.dhat)
-                new_state = {}
-                for i, kk in enumerate(keys):
-                    was, a = state.get(kk, (False, 0))
-                    if flags[i]:
-                        new_state[kk] = (True, min(a + 1, p.a_max) if was else 0)
-                state = new_state
                 if trace is not None:
-                    trace.append(dict(state))
+                    trace.append(dict(state_in=dict(state), weights=dict(zip(keys, w)), active=dict(zip(keys, act)),
+                                      flags=dict(zip(keys, np.asarray(flags, dtype=bool)))))
+                state = ndb_after_partial_ccd(state, keys, flags, p.a_max)
+                if trace is not None:
+                    trace[-1]["state"] = dict(state)
                 dx = np.max(np.abs(xn - x))
                 x = xn
                 if not p.fixed_iters and p.tol_rel_residual <= 0 and dx <= p.tol_inner * L:

@@ -691,3 +691,132 @@ def test_jacobi_reference_converges_to_exact_solve():
     ex = np.zeros_like(r)
     ex[f] = np.linalg.solve(A[np.ix_(f, f)], r[f])
     assert np.max(np.abs(d - ex)) < 1e-8 * np.max(np.abs(ex))
+
+
+# ----------------------------------------------------------------------------
+# non-distance barrier life span (Sec. 4, Eq. exp)
+# ----------------------------------------------------------------------------
+
+def test_ndb_counter_and_weight_follow_a_scripted_flag_sequence():
+    """Eq. (exp): w = k K^a with a the number of consecutive LG iterations a
+    constraint has been active.  Seven partial-CCD results for three pairs,
+    with the counters and weights written out by hand (k = 5, K = 2,
+    a_max = 3): A stays flagged (0, 1, 2, 3, then held at the cap), drops
+    out once and restarts at 0; B comes and goes; C is never flagged."""
+    flags = [  # A, B, C
+        (1, 0, 0),
+        (1, 1, 0),
+        (1, 0, 0),
+        (1, 1, 0),
+        (1, 1, 0),
+        (0, 1, 0),
+        (1, 1, 0),
+    ]
+    expect_a = [
+        {"A": 0},
+        {"A": 1, "B": 0},
+        {"A": 2},
+        {"A": 3, "B": 0},
+        {"A": 3, "B": 1},
+        {"B": 2},
+        {"A": 0, "B": 3},
+    ]
+    expect_w = [
+        {"A": 5.0},
+        {"A": 10.0, "B": 5.0},
+        {"A": 20.0},
+        {"A": 40.0, "B": 5.0},
+        {"A": 40.0, "B": 10.0},
+        {"B": 20.0},
+        {"A": 5.0, "B": 40.0},
+    ]
+    keys = ["A", "B", "C"]
+    state = {}
+    for f, ea, ew in zip(flags, expect_a, expect_w):
+        state = pd.ndb_after_partial_ccd(state, keys, f, 3)
+        assert {k: a for k, (act, a) in state.items() if act} == ea
+        assert set(state) == set(ea)  # inactive pairs leave the set
+        got_w = {k: float(pd.ndb_weight(5.0, 2.0, a)) for k, (act, a) in state.items()}
+        assert got_w == ew
+
+
+def test_ndb_full_ccd_keeps_counters_and_activates_impacts_at_zero():
+    """Alg. 1 FullCCD: a pair with an impact in [0, 1] joins the set at a = 0,
+    an active pair keeps its counter whether or not it has an impact, a pair
+    that is no longer a candidate leaves, and a candidate without an impact
+    that was not active stays out."""
+    state = {"A": (True, 2), "B": (True, 1), "F": (True, 4)}
+    keys = ["A", "C", "D", "E", "F"]
+    toi = [2.0, 0.5, 1.5, 1.0, 0.25]
+    got = pd.ndb_after_full_ccd(state, keys, toi)
+    assert got == {"A": (True, 2), "C": (True, 0), "E": (True, 0), "F": (True, 4)}
+    # the next partial CCD flags A, C and D
+    got = pd.ndb_after_partial_ccd(got, keys, [1, 1, 1, 0, 0], 20)
+    assert got == {"A": (True, 3), "C": (True, 1), "D": (True, 0)}
+
+
+def test_ndb_schedule_of_a_vertex_moved_across_the_activity_threshold():
+    """One VT pair: a vertex 5 mm above a static triangle (x^-), its end
+    position x^+ scripted per LG iteration.  With p2 - p1 vertical the
+    closest-point sample gives Q = 5 mm * z1, so the pair is active exactly
+    when the end height z1 <= d_hat (Eq. collision_judge with the gap of
+    R7); the other samples of the pattern lie > 8 cm away sideways and never
+    fire.  The partial CCD of collide.c decides, the NDB rule counts: heights
+    3, 0.5, 0.8, -1, 2, 0.2, 0.1 mm give flags 0 1 1 1 0 1 1, counters
+    -, 0, 1, 2, -, 0, 1 and weights -, k, 2k, 4k, -, k, 2k."""
+    dhat = 1e-3
+    X0 = np.array([[0.25, 0.25, 0.005], [0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    quads = np.array([[0, 1, 2, 3]])
+    kinds = np.array([0])
+    heights = [3e-3, 5e-4, 8e-4, -1e-3, 2e-3, 2e-4, 1e-4]
+    expect_flag = [False, True, True, True, False, True, True]
+    expect_a = [None, 0, 1, 2, None, 0, 1]
+    k = 7.5
+    expect_w = [None, 7.5, 15.0, 30.0, None, 7.5, 15.0]
+    state = {}
+    for z1, ef, ea, ew in zip(heights, expect_flag, expect_a, expect_w):
+        X1 = X0.copy()
+        X1[0, 2] = z1
+        flags, margin = collide.partial_ccd(X0, X1, quads, kinds, 3, 4, dhat)
+        assert bool(flags[0]) == ef, (z1, margin)
+        state = pd.ndb_after_partial_ccd(state, [("vt", 0, 0)], flags, 20)
+        if ea is None:
+            assert state == {}
+        else:
+            assert state == {("vt", 0, 0): (True, ea)}
+            assert float(pd.ndb_weight(k, 2.0, state[("vt", 0, 0)][1])) == ew
+
+
+def test_oracle_step_applies_the_ndb_schedule_in_every_inner_iteration():
+    """A drape thrown at the sphere with 8 inner iterations: in every inner
+    LG iteration of Oracle.step the springs carry w = k K^a of the set the
+    iteration started from (and no spring on a pair outside it), the set
+    after the partial CCD is the consecutive count of the flags, and some
+    counters pass 2, so the growth of Eq. (exp) is exercised."""
+    import dataclasses
+    sc = wl.drape_sphere(side=10, sphere_subdiv=2)
+    v0 = sc.v0.copy()
+    v0[:, 2] -= 20.0
+    sc = dataclasses.replace(sc, v0=v0.astype(np.float32))
+    p = pd.Params(fixed_iters=True, warm_iters=1, max_outer=1, max_inner=8, a_max=6)
+    o = pd.Oracle(sc, p)
+    amax_seen = 0
+    for step in range(3):
+        tr = []
+        o.step(trace=tr)
+        assert len(tr) == 8
+        for rec in tr:
+            s_in, w, act, fl, s_out = rec["state_in"], rec["weights"], rec["active"], rec["flags"], rec["state"]
+            for kk in w:
+                if kk in s_in:
+                    assert act[kk] and w[kk] == o.k * 2.0 ** s_in[kk][1]
+                else:
+                    assert not act[kk]
+            for kk in w:
+                if fl[kk]:
+                    a_prev = s_in[kk][1] if kk in s_in else None
+                    assert s_out[kk] == (True, 0 if a_prev is None else min(a_prev + 1, 6))
+                else:
+                    assert kk not in s_out
+            amax_seen = max([amax_seen] + [a for _, a in s_out.values()])
+    assert amax_seen >= 3
