@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--forms", default="mixed16,mixed,fp32",
                     help="comma list of mixed16 (FP16 basis), mixed (BF16 basis), fp32; the first is the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-side", type=int, default=64)
+    ap.add_argument("--cpu-sample-side", type=int, default=32,
+                    help="grid side of the oracle's sample (CPU baseline, reference arm, error report)")
+    ap.add_argument("--error-steps", type=int, default=2,
+                    help="steps of the per-form error report against the oracle (0: skip)")
     ap.add_argument("--sweeps", type=int, default=28, help="Chebyshev steps per LG iteration")
     ap.add_argument("--cheb-ratio", type=float, default=300.0, help="Chebyshev interval ratio b/a")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form comparison")
@@ -190,24 +193,25 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
     clocks = ClockSampler(dev_index)
     clocks.start()
     time.sleep(0.3)
-    st_list = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(steps):
         one_step()
-        st_list.append(pc.pdc_get_stats(h))
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    # ---- profiled replay of the same steps (per-kernel event timing)
+    # ---- profiled replay of the same steps (per-kernel event timing and the
+    # step statistics, kept out of the timed region)
     restore()
     pc.pdc_set_profiling(h, True)
+    st_list = []
     for _ in range(steps):
         one_step()
+        st_list.append(pc.pdc_get_stats(h))
     torch.cuda.synchronize()
     kt = pc.pdc_get_kernel_times(h)
     pc.pdc_set_profiling(h, False)
@@ -339,27 +343,176 @@ PARENTS = {"broad_phase", "partial_ccd"}
 TRAFFIC = {"cheb_sweep": 33799680.0}
 
 
-def roofline(kernels, pk, ms_step):
+def l2_copy_peak(torch, dev_index, mbytes=40):
+    """Copy bandwidth of a working set that stays in L2 (mbytes of read plus
+    written bytes, 129 MB of L2): torch copies back to back, best of 5 runs
+    of 200, CUDA events; counted like the HBM copy peak (read + write)."""
+    n = mbytes * (1 << 20) // 8
+    a = torch.ones(n, dtype=torch.float32, device=f"cuda:{dev_index}")
+    b = torch.empty_like(a)
+    for _ in range(20):
+        b.copy_(a)
+    best = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(5):
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(200):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * n * 4 * 200 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    del a, b
+    return best
+
+
+# working set of the dominant kernel per launch at the benchmark size (bytes):
+# H tiles (18.9 MB) and the residual, three Chebyshev iterates, diagonal and
+# iterate streams (float4, 4.2 MB each)
+WORKING_SET = {"cheb_sweep": 18.9e6 + 6 * 4.19e6}
+L2_BYTES = 129e6
+
+
+def roofline(kernels, pk, ms_step, l2_gbs=None):
     """Dominant kernel (largest total time among the profiled leaf regions),
     achieved algorithmic bytes per launch / event time against the measured
-    HBM copy peak."""
+    copy peak of the memory level its working set lives in: the L2 copy peak
+    measured in this run when the working set fits in L2, else the HBM copy
+    peak of MEASURED_PEAKS.json (both given)."""
     leaves = {k: v for k, v in kernels.items() if k not in PARENTS}
     best = max(leaves.items(), key=lambda kv: kv[1]["total_ms"])
     name, d = best
     per_launch_ms = d["total_ms"] / max(d["launches"], 1)
     bytes_per_launch = d["algo_bytes"] / max(d["launches"], 1)
     achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
-    peak = float(pk.get("hbm_gbs", 6800.0))
-    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get(name), "launches": d["launches"],
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    ws = WORKING_SET.get(name)
+    in_l2 = ws is not None and ws < 0.5 * L2_BYTES and l2_gbs
+    peak = l2_gbs if in_l2 else hbm
+    return {"kernel": name, "bound": "l2" if in_l2 else "hbm", "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get(name), "launches": d["launches"],
             "ms_per_launch": round(per_launch_ms, 5), "bytes_per_launch": bytes_per_launch,
-            "peak_source": "measured" if not pk.get("_fallback") else "fallback"}
+            "working_set_bytes": ws, "hbm_peak": hbm, "hbm_frac": round(achieved / hbm, 4),
+            "peak_source": ("L2 copy measured in this run (40 MB working set), of measured" if in_l2 else
+                            ("HBM copy of MEASURED_PEAKS.json, of measured" if not pk.get("_fallback") else "fallback"))}
 
 
-def cpu_baseline(side, steps=2, warmup=0):
-    """The FP64 oracle on a bounded sample: `warmup` untimed then `steps`
-    timed steps of the same scene at side x side in one process, one thread;
-    ms/step scaled linearly by vertex count to the full workload."""
+ORACLE_PARAMS = "pd.Params(tol_rel_residual=1e-3, max_outer=2, max_inner=400, warm_iters=5)"
+
+
+def oracle_from_states(side, states_path, out_path):
+    """Runs, in a separate one-thread process, one FP64 oracle step of the
+    swept cloth at side x side from each stored state (x*, v*, t) with the
+    benchmark's stopping rule; stores the results and per-step times."""
+    code = r'''
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+import workloads as wl
+from oracle import pd, build
+build.build()
+sc = wl.hanging_swept(side=%d)
+d = np.load(%r)
+o = pd.Oracle(sc, %s)
+xs, ts, its, res = [], [], [], []
+m = o.model
+for k in range(len(d["t"])):
+    o.x, o.v, o.t = d["x"][k].astype(np.float64), d["v"][k].astype(np.float64), float(d["t"][k])
+    z = o.x + o.p.dt * o.v + o.p.dt ** 2 * np.asarray(o.p.gravity)[None, :]
+    z[~m.free] = sc.pins_at(o.t + o.p.dt)
+    t0 = time.time()
+    x, v, st = o.step()
+    ts.append(time.time() - t0)
+    xs.append(x)
+    its.append(st.warm_iters + st.inner_iters)
+    rho0 = np.linalg.norm(m.residual(z, z))
+    res.append(float(np.linalg.norm(m.residual(x, z)) / rho0) if st.n_active == 0 else -1.0)
+np.savez(%r, x=np.array(xs), s=np.array(ts), iters=np.array(its), res=np.array(res))
+''' % (ROOT, side, states_path, ORACLE_PARAMS, out_path)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    return subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+
+
+def error_vs_oracle(pc, torch, forms, side, warm, steps, dev_index):
+    """Per-step error of each form against the FP64 oracle, on the same swept
+    cloth at side x side (the oracle's brute-force broad phase and exact
+    sparse solves make the full 512 x 512 size impractical).  Start states:
+    the first form's trajectory after `warm` steps.  From each state every
+    form takes one production step (x* + u exactly, from the step's
+    displacement), the oracle one step with the same stopping rule; reported
+    per step: max and RMS vertex distance / bounding-box diagonal, the
+    residual the form reports, the oracle's residual (R11, FP64) at the
+    form's x* + u, and the oracle's own exit residual (these two only for
+    steps without active collision springs)."""
+    import numpy as np
+    import workloads as wl
+    from oracle import pd
+    scene = wl.hanging_swept(side=side)
+    dt = 1.0 / 200
+    first = list(forms)[0]
+    h = pc.pdc_create(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend,
+                      solver_params(pc, FORMS[first]))
+    states = []
+    for k in range(warm + steps):
+        if k >= warm:
+            x, v = pc.pdc_get_state(h, scene.n)
+            states.append((x, v, k * dt))
+        pc.pdc_set_pin_targets(h, scene.pins_at((k + 1) * dt))
+        pc.pdc_step(h, dt)
+    pc.pdc_destroy(h)
+    fd, spath = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    opath = spath.replace(".npz", "_out.npz")
+    np.savez(spath, x=np.array([s[0] for s in states]), v=np.array([s[1] for s in states]),
+             t=np.array([s[2] for s in states]))
+    r = oracle_from_states(side, spath, opath)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    od = np.load(opath)
+    os.unlink(spath)
+    os.unlink(opath)
+    m = pd.Model(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend, dt)
+    g = np.array([0.0, 0.0, -9.8])
+    out = {"grid": "%dx%d (%d vertices), the benchmark's scene and settings" % (side, side, scene.n),
+           "start_states": "%s trajectory after %d steps" % (first, warm), "steps": steps,
+           "oracle": {"rel_residual": [round(float(v), 6) for v in od["res"]],
+                      "lg_iters": [int(v) for v in od["iters"]], "s_per_step": [round(float(v), 2) for v in od["s"]]},
+           "forms": {}}
+    for f in forms:
+        h = pc.pdc_create(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend,
+                          solver_params(pc, FORMS[f]))
+        rec = {"err_max": [], "err_rms": [], "rel_residual_reported": [], "rel_residual_oracle_at_form": [],
+               "n_active": []}
+        for k, (x, v, t) in enumerate(states):
+            pc.pdc_set_state(h, x, v)
+            pc.pdc_set_pin_targets(h, scene.pins_at(t + dt))
+            pc.pdc_step(h, dt)
+            st = pc.pdc_get_stats(h)
+            xg = x.astype(np.float64) + pc.pdc_get_displacement(h, scene.n).astype(np.float64)
+            d = np.linalg.norm(xg - od["x"][k], axis=1)
+            rec["err_max"].append(float(d.max() / m.L))
+            rec["err_rms"].append(float(np.sqrt(np.mean(d * d)) / m.L))
+            rec["rel_residual_reported"].append(st["rel_residual"])
+            rec["n_active"].append(st["n_active"])
+            z = x.astype(np.float64) + dt * v.astype(np.float64) + dt * dt * g[None, :]
+            z[scene.pins] = scene.pins_at(t + dt)
+            ok = st["n_active"] == 0 and st["t_toi"] >= 2.0
+            rec["rel_residual_oracle_at_form"].append(
+                float(np.linalg.norm(m.residual(xg, z)) / np.linalg.norm(m.residual(z, z))) if ok else None)
+        pc.pdc_destroy(h)
+        out["forms"][f] = rec
+    out["_oracle_ms"] = [float(v) * 1e3 for v in od["s"]]
+    out["_oracle_side"] = side
+    return out
+
+
+def cpu_baseline(side, steps, warmup, budget_s=150.0):
+    """The FP64 oracle as it stands on a bounded sample: its own trajectory
+    of the same scene at side x side, `warmup` untimed then up to `steps`
+    timed steps, in a separate one-thread process, stopping once budget_s
+    of timed work is spent.  ms/step is scaled linearly by vertex count to
+    512 x 512: a lower bound of the oracle at full size, whose brute-force
+    broad phase and sparse factorisations grow faster than linearly."""
     code = r'''
 import os, sys, time, json
 sys.path.insert(0, %r)
@@ -367,8 +520,7 @@ import workloads as wl
 from oracle import pd, build
 build.build()
 sc = wl.hanging_swept(side=%d)
-p = pd.Params(tol_rel_residual=1e-3, max_outer=3, max_inner=64, warm_iters=5)
-o = pd.Oracle(sc, p)
+o = pd.Oracle(sc, %s)
 for k in range(%d):
     o.step()
 ts = []
@@ -376,10 +528,12 @@ for k in range(%d):
     t0 = time.time()
     o.step()
     ts.append(time.time() - t0)
-print(json.dumps({"s": ts, "n": sc.n}))
-''' % (ROOT, side, warmup, steps)
+    if sum(ts) > %r:
+        break
+print(json.dumps({"s": ts, "n": sc.n, "cores": os.cpu_count()}))
+''' % (ROOT, side, ORACLE_PARAMS, warmup, max(steps, 1), budget_s)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
     if out.returncode != 0:
         return {"value": None, "error": out.stderr[-300:]}
     d = json.loads(out.stdout.strip().splitlines()[-1])
@@ -387,8 +541,10 @@ print(json.dumps({"s": ts, "n": sc.n}))
     per = [t * 1e3 * scale for t in d["s"]]
     return {"value": round(statistics.mean(per), 1), "unit": "ms/step", "cores": 1, "kind": "oracle",
             "per_step": per,
-            "sample": "%d oracle steps (after %d untimed) of the same swept-cloth scene at %dx%d (%d vertices), "
-                      "ms/step scaled linearly by vertex count to 512x512" % (steps, warmup, side, side, d["n"])}
+            "sample": "%d oracle steps (after %d untimed, of %d asked) of the same swept-cloth scene at %dx%d "
+                      "(%d vertices), one thread on a %d-core host, ms/step scaled linearly by vertex count to "
+                      "512x512 (a lower bound at full size)" % (len(d["s"]), warmup, max(steps, 1), side, side,
+                                                               d["n"], d["cores"])}
 
 
 def main():
@@ -435,7 +591,8 @@ def main():
     if rank != 0:
         return
     pk = peaks()
-    rl = roofline(forms[head]["kernels"], pk, ms)
+    l2 = l2_copy_peak(torch, local)
+    rl = roofline(forms[head]["kernels"], pk, ms, l2)
     line = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms/step", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
@@ -463,8 +620,27 @@ def main():
             line["batched"] = run_batched(pc, torch, dev_index=local)
         except Exception as e:  # reported, not fatal for the headline
             line["batched"] = {"error": str(e)[:200]}
-    if not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(a.cpu_sample_side)
+    if a.error_steps > 0 and world == 1:
+        try:
+            ev = error_vs_oracle(pc, torch, list(forms), a.cpu_sample_side, 5, a.error_steps, local)
+        except Exception as e:  # reported, not fatal for the headline
+            ev = {"error": str(e)[:300]}
+        oms = ev.pop("_oracle_ms", None)
+        oside = ev.pop("_oracle_side", None)
+        line["error_vs_oracle"] = ev
+        if oms and not a.no_cpu_baseline:
+            # the oracle steps of the error report are the CPU baseline's sample
+            scale = (SIDE * SIDE) / float(oside * oside)
+            per = [t * scale for t in oms]
+            line["cpu_baseline"] = {
+                "value": round(statistics.mean(per), 1), "unit": "ms/step", "cores": 1, "kind": "oracle",
+                "per_step": [round(v, 1) for v in per],
+                "sample": "%d oracle steps of the same swept-cloth scene at %dx%d (%d vertices) from the states of the "
+                          "error report, one thread on a %d-core host, ms/step scaled linearly by vertex count to "
+                          "512x512 (a lower bound at full size)" % (len(oms), oside, oside, oside * oside,
+                                                                    os.cpu_count())}
+    if "cpu_baseline" not in line and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a.cpu_sample_side, 2, 3, budget_s=30.0)
     print(json.dumps(line))
 
 

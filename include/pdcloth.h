@@ -241,6 +241,15 @@ pdc_status pdc_step(pdc_handle h, double dt);
 /* Current cloth positions [nv][3]. */
 pdc_status pdc_get_positions(pdc_handle h, float *out, int32_t on_device);
 
+/* Displacement u [nv][3] of the last step: inside a step the iterate is
+ * carried as x = x* + u (x* the state the step started from), and the step
+ * ends at x_new = x* + u, stored as the float32 positions fl32(x* + u).
+ * With x* (the positions before the step) and u both float32, x* + u is the
+ * step's final iterate exactly (in FP64), free of the rounding of the
+ * stored positions, which for a stiff cloth can exceed the residual
+ * tolerance.  Zero before the first step and after pdc_set_state. */
+pdc_status pdc_get_displacement(pdc_handle h, float *u, int32_t on_device);
+
 /* Statistics of the last step. */
 pdc_status pdc_get_stats(pdc_handle h, pdc_stats *out);
 
@@ -270,7 +279,10 @@ typedef struct {
  * prints per-iteration residuals, pass decisions and retries to stderr;
  * PDC_SYNC_CHECK (any value) synchronises the stream after every profiled
  * region and fails the call with PDC_ERR_CUDA naming the region if a CUDA
- * error is pending (slow; for locating a fault). */
+ * error is pending (slow; for locating a fault); PDC_BP_CAPACITY (a positive
+ * integer) sets the initial capacity of the broad-phase candidate lists, in
+ * pairs of each kind, instead of the size-based default (small values make
+ * the first steps regrow the lists, for testing that path). */
 
 /* enable = 1 starts profiling and clears the accumulated times; 0 stops. */
 pdc_status pdc_set_profiling(pdc_handle h, int32_t enable);

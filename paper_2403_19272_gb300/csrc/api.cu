@@ -49,10 +49,12 @@ __global__ void k_step_fraction(const unsigned long long *toi_bits, double alpha
     *s_out = (t <= 1.0) ? alpha * t : 1.0;
 }
 // final state (exit line search of Alg. 1): cloth u = um + s (up - um) (or up),
-// x = x* + u, v = u / h; obstacle vertices lerp between their absolute x^- and x^+.
+// x = x* + u, v = u / h, and u itself in ulast; obstacle vertices lerp
+// between their absolute x^- and x^+.
 __global__ void k_finish(int nv, int n, const float4 *__restrict__ um, const float4 *__restrict__ up,
                          const float4 *__restrict__ xm, const float4 *__restrict__ xp, const double *s_frac,
-                         int use_lerp, float inv_h, float4 *__restrict__ xs, float4 *__restrict__ vs) {
+                         int use_lerp, float inv_h, float4 *__restrict__ xs, float4 *__restrict__ vs,
+                         float4 *__restrict__ ulast) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
     float s = use_lerp ? (float)*s_frac : 1.f;
@@ -63,6 +65,7 @@ __global__ void k_finish(int nv, int n, const float4 *__restrict__ um, const flo
             d = a + s * (d - a);
         }
         vs[i] = f4(inv_h * d);
+        ulast[i] = f4(d);
         xs[i] = f4(f3(xs[i]) + d);
     } else {
         float3 b = f3(xp[i]);
@@ -234,6 +237,7 @@ struct pdc_ctx {
     DevBuf<float4> Xs, Vs, Z, Xp, Xm, Xbak, Vbak, Xprev;
     DevBuf<float4> R, RL, D0, D1, CF;
     DevBuf<float4> Ucur, Um;  // iterate and x^- as displacements from x* (cloth vertices)
+    DevBuf<float4> Ulast;     // displacement x_new - x* of the last step, before rounding x_new
     DevBuf<float> CW;
     DevBuf<float> stage3;  // staging for float[3] transfers
     // obstacles
@@ -245,6 +249,7 @@ struct pdc_ctx {
     DevBuf<int4> ctri;
     DevBuf<int2> cedge;
     DevBuf<unsigned char> vfixed;
+    DevBuf<unsigned int> guard_d;  // index-guard word of this handle's pair kernels
     BroadPhase bp;
     DevBuf<ActivePair> act;
     int cap_act = 0;
@@ -287,6 +292,9 @@ struct pdc_ctx {
     double gersh = 1.0;       // Gershgorin bound of D^-1 H
     long long nnz_off = 0;  // off-diagonal entries of H over free rows
     bool log = std::getenv("PDC_LOG") != nullptr;  // per-iteration residuals to stderr
+    // initial candidate-list capacity (pairs of each kind) when set: small
+    // values exercise the regrowth of the broad-phase buffers
+    long long bp_cap0 = std::getenv("PDC_BP_CAPACITY") ? std::atoll(std::getenv("PDC_BP_CAPACITY")) : 0;
     // diagnostics: synchronise after every profiled region and name the
     // region in the error of a failed kernel
     bool sync_check = std::getenv("PDC_SYNC_CHECK") != nullptr;
@@ -341,6 +349,7 @@ struct pdc_ctx {
         v.tri = ctri;
         v.edge = cedge;
         v.vfixed = vfixed;
+        v.guard = guard_d;
         return v;
     }
     SubspaceView sub(int r_nc, int r_c) const {
@@ -699,6 +708,8 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
     Xacc.alloc(n);
     Ucur.alloc(n);
     Um.alloc(n);
+    Ulast.alloc(n);
+    Ulast.zero(s);
     if (P.sweep_kind == 1) {
         CD0.alloc(n);
 
@@ -910,7 +921,12 @@ void pdc_ctx::ensure_topology() {
     vfixed.upload(vf, s);
     long long cvt = std::max<long long>(1024, 16LL * nv_all), cee = std::max<long long>(1024, 24LL * ne_all);
     long long cent = std::max<long long>(4096, 8LL * (nt_all + ne_all));
-    bp.reserve(coll(), cvt, cee, cent);
+    if (bp_cap0 > 0) cvt = cee = bp_cap0;
+    if (!guard_d.p) {
+        guard_d.alloc(1);
+        guard_d.zero(s);
+    }
+    bp.reserve(coll(), cvt, cee, cent, s);
     cap_act = (int)std::max<long long>(1024, 4LL * nv_all);
     disp.alloc(nv_all);
     act.alloc(cap_act);
@@ -1253,7 +1269,7 @@ void pdc_ctx::step() {
         }
     }
     // exit line search and velocities (Alg. 1; v = (x - x*)/h)
-    k_finish<<<nb(nv_all), 256, 0, s>>>(nv_all, n, Um, Ucur, Xm, Xp, sfrac, use_lerp ? 1 : 0, 1.f / h, Xs, Vs);
+    k_finish<<<nb(nv_all), 256, 0, s>>>(nv_all, n, Um, Ucur, Xm, Xp, sfrac, use_lerp ? 1 : 0, 1.f / h, Xs, Vs, Ulast);
     PDC_LAUNCH_CK();
     bad_d.zero(s);
     k_finite<<<nb(n), 256, 0, s>>>(n, Xs, bad_d);
@@ -1303,7 +1319,7 @@ void pdc_ctx::step() {
         PDC_CK(cudaStreamSynchronize(s));
         throw Error(PDC_ERR_NUMERIC, "non-finite positions; state rolled back");
     }
-    if (unsigned int guard = P.collisions ? pair_guard_take(s) : 0u) {
+    if (unsigned int guard = P.collisions ? pair_guard_take(s, guard_d) : 0u) {
         PDC_CK(cudaMemcpyAsync(Xs.p, Xbak.p, sizeof(float4) * nv_all, cudaMemcpyDeviceToDevice, s));
         PDC_CK(cudaMemcpyAsync(Vs.p, Vbak.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
         PDC_CK(cudaStreamSynchronize(s));
@@ -1614,6 +1630,7 @@ pdc_status pdc_set_state(pdc_handle h, const float *x, const float *v, int32_t o
         h->Vs.zero(h->s);
     }
     h->rf_pending = false;  // a forwarded residual belongs to the replaced state
+    h->Ulast.zero(h->s);
     PDC_CK(cudaStreamSynchronize(h->s));
     API_END(h)
 }
@@ -1638,6 +1655,13 @@ pdc_status pdc_get_positions(pdc_handle h, float *out, int32_t on_device) {
     API_BEGIN(h)
     if (!out) throw Error(PDC_ERR_ARG, "pdc_get_positions: NULL");
     get_f4(h, h->Xs, out, on_device);
+    API_END(h)
+}
+
+pdc_status pdc_get_displacement(pdc_handle h, float *u, int32_t on_device) {
+    API_BEGIN(h)
+    if (!u) throw Error(PDC_ERR_ARG, "pdc_get_displacement: NULL");
+    get_f4(h, h->Ulast, u, on_device);
     API_END(h)
 }
 
@@ -1685,7 +1709,7 @@ pdc_status pdc_step(pdc_handle h, double dt) {
             if (ovf & OVF_HASH) cent *= 2;
             if (ovf & OVF_CELLS) bp.cell_scale *= 4.f;
             if (ovf & OVF_SLOTS) bp.grow_slots(cv, true, true);
-            if (ovf & (OVF_VT | OVF_EE | OVF_HASH)) bp.reserve(cv, cvt, cee, cent);
+            if (ovf & (OVF_VT | OVF_EE | OVF_HASH)) bp.reserve(cv, cvt, cee, cent, h->s);
             if (ovf & OVF_ACTIVE) {
                 h->cap_act *= 2;
                 h->act.alloc(h->cap_act);
@@ -1694,7 +1718,7 @@ pdc_status pdc_step(pdc_handle h, double dt) {
             if (h->log) std::fprintf(stderr, "[pdc] step retried after overflow 0x%x\n", ovf);
         }
     }
-    h->st.overflow_retries = retries;
+    h->st.overflow_retries += retries;  // regrowths inside the step plus whole-step retries
     API_END(h)
 }
 
@@ -1751,7 +1775,7 @@ pdc_status pdc_op_broadphase(pdc_handle h, const float *x0, const float *x1, int
                   cent = bp.cap_ent * ((ovf & OVF_HASH) ? 2 : 1);
         if (ovf & OVF_CELLS) bp.cell_scale *= 4.f;
         if (ovf & OVF_SLOTS) bp.grow_slots(h->coll(), true, true);
-        bp.reserve(h->coll(), cvt, cee, cent);
+        bp.reserve(h->coll(), cvt, cee, cent, h->s);
     }
     BroadPhase &bp = h->bp;
     long long nv_ = 0, ne_ = 0;

@@ -396,7 +396,8 @@ __global__ void k_pair_scatter(int n, const int2 *__restrict__ list, const int *
 }
 }  // namespace
 
-void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee_, long long cap_ent_) {
+void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee_, long long cap_ent_,
+                         cudaStream_t s) {
     nt = cv.nt;
     ne = cv.ne;
     nv = cv.nv;
@@ -448,24 +449,23 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
     cur = 0;
     sup_ok = false;
     for (int k = 0; k < 2; ++k) {
-        cnt_vt_d[k].zero(0);
-        cnt_ee_d[k].zero(0);
+        cnt_vt_d[k].zero(s);
+        cnt_ee_d[k].zero(s);
     }
-    reserve_pccd(cv);
+    reserve_pccd(cv, s);
 }
 
-void BroadPhase::reserve_pccd(const CollView &cv) {
+void BroadPhase::reserve_pccd(const CollView &cv, cudaStream_t s) {
     cap_pairs = cap_vt + cap_ee;
     near.alloc(cap_pairs);
     watch[0].alloc(cap_pairs);
     watch[1].alloc(cap_pairs);
     disp0.alloc(std::max(cv.nv, 1));
-    disp0.zero(0);
+    disp0.zero(s);
     pccd.alloc(1);
-    PccdState p0;
-    memset(&p0, 0, sizeof(p0));
-    p0.force_full = 1;
-    PDC_CK(cudaMemcpy(pccd.p, &p0, sizeof(p0), cudaMemcpyHostToDevice));
+    pccd.zero(s);  // no watch list yet: the first pass scans every pair
+    k_pccd_force<<<1, 1, 0, s>>>(pccd);
+    PDC_LAUNCH_CK();
 }
 
 template <class T> static void grow_keep(DevBuf<T> &b, long long cap, cudaStream_t s) {
@@ -516,7 +516,7 @@ void BroadPhase::grow(const CollView &cv, long long cvt, long long cee, long lon
     }
     if (cap_vt + cap_ee > cap_pairs) {
         PDC_CK(cudaStreamSynchronize(s));
-        reserve_pccd(cv);
+        reserve_pccd(cv, s);
     }
 }
 

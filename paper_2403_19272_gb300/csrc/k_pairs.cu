@@ -291,10 +291,13 @@ __device__ float3 start_dir(int kind, const float4 a0[4], const float c[4]) {
 }
 
 // Index guard: an entry of a device-built list that lies outside the current
-// topology sets a bit here and is skipped (no access through it); the host
-// reads the word after each step and fails the step.
-__device__ unsigned int g_pair_guard;
+// topology sets a bit in the handle's guard word (CollView::guard) and is
+// skipped (no access through it); the host reads the word after each step
+// and fails the step.
 enum GuardBits { GUARD_PAIR = 1, GUARD_WATCH = 2, GUARD_NEAR = 4, GUARD_ACTIVE = 8 };
+__device__ inline void guard_raise(const CollView &cv, unsigned int bit) {
+    if (cv.guard) atomicOr(cv.guard, bit);
+}
 
 __device__ inline bool pair_ids(const CollView &cv, const int2 *vt, const int2 *ee, long long nvt, long long idx,
                                 int ids[4], int &kind) {
@@ -303,7 +306,7 @@ __device__ inline bool pair_ids(const CollView &cv, const int2 *vt, const int2 *
         int2 p = vt[idx];
         kind = 0;
         if (p.x < 0 || p.x >= cv.nv || p.y < 0 || p.y >= cv.nt) {
-            atomicOr(&g_pair_guard, GUARD_PAIR);
+            guard_raise(cv, GUARD_PAIR);
             return false;
         }
         int4 T = cv.tri[p.y];
@@ -312,7 +315,7 @@ __device__ inline bool pair_ids(const CollView &cv, const int2 *vt, const int2 *
         int2 p = ee[idx - nvt];
         kind = 1;
         if (p.x < 0 || p.x >= cv.ne || p.y < 0 || p.y >= cv.ne) {
-            atomicOr(&g_pair_guard, GUARD_PAIR);
+            guard_raise(cv, GUARD_PAIR);
             return false;
         }
         int2 E = cv.edge[p.x], F = cv.edge[p.y];
@@ -537,7 +540,7 @@ __global__ void __launch_bounds__(256) k_pccd_filter(CollView cv, const int2 *__
         int ids[4], kind;
         if (t < n) idx = full ? (int)t : watch[t];
         bool valid = t < n && idx >= 0 && idx < nvt + *nee_p;
-        if (t < n && !valid) atomicOr(&g_pair_guard, GUARD_WATCH);
+        if (t < n && !valid) guard_raise(cv, GUARD_WATCH);
         if (valid && pair_ids(cv, vt, ee, nvt, idx, ids, kind)) {
             float d0 = kind == 0 ? d0_vt[idx] : d0_ee[idx - nvt];
             // |d1 - d0| at any sample is at most the largest relative
@@ -585,7 +588,7 @@ __global__ void __launch_bounds__(256) k_pccd_test(CollView cv, const int2 *__re
         int ids[4], kind;
         int idx = t < n ? near[t] : -1;
         bool valid = idx >= 0 && idx < nvt + *nee_p;
-        if (t < n && !valid) atomicOr(&g_pair_guard, GUARD_NEAR);
+        if (t < n && !valid) guard_raise(cv, GUARD_NEAR);
         if (valid && pair_ids(cv, vt, ee, nvt, idx, ids, kind)) {
             unsigned char *stp = kind == 0 ? st_vt + idx : st_ee + (idx - nvt);
             unsigned char st = *stp;
@@ -626,7 +629,7 @@ __global__ void k_contact(CollView cv, const ActivePair *__restrict__ act, const
         ActivePair ap = act[i];
         int ids[4] = {ap.ids.x, ap.ids.y, ap.ids.z, ap.ids.w};
         if (min(min(ids[0], ids[1]), min(ids[2], ids[3])) < 0 || max(max(ids[0], ids[1]), max(ids[2], ids[3])) >= cv.nv) {
-            atomicOr(&g_pair_guard, GUARD_ACTIVE);
+            guard_raise(cv, GUARD_ACTIVE);
             continue;
         }
         float c[4] = {ap.c.x, ap.c.y, ap.c.z, ap.c.w};
@@ -727,11 +730,11 @@ inline int nblk(long long n, int b) { return (int)std::min<long long>((n + b - 1
 
 }  // namespace
 
-unsigned int pair_guard_take(cudaStream_t s) {
-    unsigned int v = 0, zero = 0;
-    PDC_CK(cudaMemcpyFromSymbolAsync(&v, g_pair_guard, sizeof(v), 0, cudaMemcpyDeviceToHost, s));
+unsigned int pair_guard_take(cudaStream_t s, unsigned int *guard) {
+    unsigned int v = 0;
+    PDC_CK(cudaMemcpyAsync(&v, guard, sizeof(v), cudaMemcpyDeviceToHost, s));
     PDC_CK(cudaStreamSynchronize(s));
-    if (v) PDC_CK(cudaMemcpyToSymbol(g_pair_guard, &zero, sizeof(zero)));
+    if (v) PDC_CK(cudaMemsetAsync(guard, 0, sizeof(v), s));
     return v;
 }
 

@@ -83,7 +83,7 @@ struct BroadPhase {
     DevBuf<int> near, watch[2];
     DevBuf<float4> disp0;
     DevBuf<PccdState> pccd;
-    void reserve_pccd(const CollView &cv);
+    void reserve_pccd(const CollView &cv, cudaStream_t s);
 
     // superset lists of a hash pass with gap d_hat + 2 mu at positions (ref0,
     // ref1); while every vertex stays within mu' = 0.9 mu of that swept box,
@@ -96,7 +96,9 @@ struct BroadPhase {
     float sup_mu = 0.f;
     bool sup_ok = false;
 
-    void reserve(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent);
+    // (re)allocates every buffer for the topology cv; the counts and the
+    // partial-CCD state are reset on stream s
+    void reserve(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent, cudaStream_t s);
     // larger capacities keeping the current candidate lists, states and counts
     void grow(const CollView &cv, long long cap_vt, long long cap_ee, long long cap_ent, cudaStream_t s);
     void grow_slots(const CollView &cv, bool vt, bool ee);
@@ -130,9 +132,10 @@ void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, cons
 void launch_rf_weights(cudaStream_t s, ActivePair *act, const int *n_act, int cap_act, float k);
 void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, const int *n_act, int cap_act,
                     const float4 *x, float dhat, float *cw, float4 *cf);
-// Reads and clears the index-guard word of the pair kernels (0: no entry of a
-// pair, watch, near or active list pointed outside the topology).
-unsigned int pair_guard_take(cudaStream_t s);
+// Reads and clears (stream-ordered on s) the handle's index-guard word of the
+// pair kernels (0: no entry of a pair, watch, near or active list pointed
+// outside the topology).
+unsigned int pair_guard_take(cudaStream_t s, unsigned int *guard);
 // Compact the cloth vertices with cw > 0.
 void launch_contact_list(cudaStream_t s, int n, const float *cw, int *list, int *count);
 

@@ -161,6 +161,7 @@ struct CollView {
     const int4 *tri;       // [nt]
     const int2 *edge;      // [ne] (a < b)
     const unsigned char *vfixed; // [nv] 1: infinite mass (obstacle or pinned)
+    unsigned int *guard;   // the handle's index-guard word (GuardBits), or NULL
 };
 
 // Scalars written by reductions (device).

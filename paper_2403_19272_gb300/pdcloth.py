@@ -74,6 +74,7 @@ SIGNATURES = {
     "pdc_get_basis": (c_i32, [P, P, P]),
     "pdc_step": (c_i32, [P, c_dbl]),
     "pdc_get_positions": (c_i32, [P, P, c_i32]),
+    "pdc_get_displacement": (c_i32, [P, P, c_i32]),
     "pdc_get_stats": (c_i32, [P, P]),
     "pdc_destroy": (None, [P]),
     "pdc_last_error": (ctypes.c_char_p, [P]),
@@ -236,6 +237,12 @@ def pdc_step(h, dt):
 def pdc_get_positions(h, n):
     out = np.empty((n, 3), np.float32)
     _check(h, lib().pdc_get_positions(h, _ptr(out), 0))
+    return out
+
+
+def pdc_get_displacement(h, n):
+    out = np.empty((n, 3), np.float32)
+    _check(h, lib().pdc_get_displacement(h, _ptr(out), 0))
     return out
 
 

@@ -38,10 +38,20 @@ def test_roofline_of_the_dominant_leaf_region():
         "cheb_sweep": {"launches": 100, "total_ms": 0.8, "algo_bytes": 100 * 30e6},
         "local_residual": {"launches": 10, "total_ms": 0.6, "algo_bytes": 10 * 80e6},
     }
+    # without an L2 measurement: against the HBM copy peak
     rl = bench.roofline(kernels, {"hbm_gbs": 6000.0}, 15.0)
     assert rl["kernel"] == "cheb_sweep" and rl["bound"] == "hbm" and rl["unit"] == "GB/s"
     assert rl["ms_per_launch"] == pytest.approx(0.008)
     assert rl["achieved"] == pytest.approx(30e6 / 8e-6 / 1e9, rel=1e-3)
     assert rl["frac"] == pytest.approx(rl["achieved"] / 6000.0, rel=1e-3)
-    assert rl["traffic"] == bench.TRAFFIC["cheb_sweep"] and rl["peak_source"] == "measured"
+    assert rl["traffic"] == bench.TRAFFIC["cheb_sweep"] and rl["peak_source"].startswith("HBM")
     assert bench.roofline(kernels, {"hbm_gbs": 6800.0, "_fallback": True}, 15.0)["peak_source"] == "fallback"
+    # the Chebyshev step's working set fits in L2: against the L2 copy peak
+    rl = bench.roofline(kernels, {"hbm_gbs": 6000.0}, 15.0, l2_gbs=12000.0)
+    assert rl["bound"] == "l2" and rl["peak"] == 12000.0
+    assert rl["frac"] == pytest.approx(rl["achieved"] / 12000.0, rel=1e-3)
+    assert rl["hbm_frac"] == pytest.approx(rl["achieved"] / 6000.0, rel=1e-3)
+    # a kernel with no working-set model stays on the HBM roof
+    k2 = dict(kernels, local_residual={"launches": 10, "total_ms": 9.6, "algo_bytes": 10 * 80e6})
+    rl = bench.roofline(k2, {"hbm_gbs": 6000.0}, 15.0, l2_gbs=12000.0)
+    assert rl["kernel"] == "local_residual" and rl["bound"] == "hbm" and rl["peak"] == 6000.0
