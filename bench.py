@@ -47,6 +47,8 @@ def parse():
                     help="grid side of the oracle's sample (CPU baseline, reference arm, error report)")
     ap.add_argument("--error-steps", type=int, default=2,
                     help="steps of the per-form error report against the oracle (0: skip)")
+    ap.add_argument("--error-side", type=int, default=64,
+                    help="grid side of the per-form error report against the oracle")
     ap.add_argument("--sweeps", type=int, default=28, help="Chebyshev steps per LG iteration")
     ap.add_argument("--cheb-ratio", type=float, default=300.0, help="Chebyshev interval ratio b/a")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form comparison")
@@ -343,27 +345,12 @@ PARENTS = {"broad_phase", "partial_ccd"}
 TRAFFIC = {"cheb_sweep": 33799680.0}
 
 
-def l2_copy_peak(torch, dev_index, mbytes=40):
+def l2_copy_peak(pc, stream, mbytes=40):
     """Copy bandwidth of a working set that stays in L2 (mbytes of read plus
-    written bytes, 129 MB of L2): torch copies back to back, best of 5 runs
-    of 200, CUDA events; counted like the HBM copy peak (read + write)."""
-    n = mbytes * (1 << 20) // 8
-    a = torch.ones(n, dtype=torch.float32, device=f"cuda:{dev_index}")
-    b = torch.empty_like(a)
-    for _ in range(20):
-        b.copy_(a)
-    best = 0.0
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(5):
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(200):
-            b.copy_(a)
-        e1.record()
-        torch.cuda.synchronize()
-        best = max(best, 2 * n * 4 * 200 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
-    del a, b
-    return best
+    written bytes per pass, 129 MB of L2): the library's persistent copy
+    kernel, 400 passes per launch, best of 5, CUDA events; counted like the
+    HBM copy peak (read + written bytes)."""
+    return max(pc.pdc_measure_copy_bandwidth(mbytes << 20, 400, stream) for _ in range(5))
 
 
 # working set of the dominant kernel per launch at the benchmark size (bytes):
@@ -393,7 +380,8 @@ def roofline(kernels, pk, ms_step, l2_gbs=None):
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get(name), "launches": d["launches"],
             "ms_per_launch": round(per_launch_ms, 5), "bytes_per_launch": bytes_per_launch,
             "working_set_bytes": ws, "hbm_peak": hbm, "hbm_frac": round(achieved / hbm, 4),
-            "peak_source": ("L2 copy measured in this run (40 MB working set), of measured" if in_l2 else
+            "peak_source": ("L2 copy measured in this run (persistent copy kernel, 40 MB working set), of measured"
+                            if in_l2 else
                             ("HBM copy of MEASURED_PEAKS.json, of measured" if not pk.get("_fallback") else "fallback"))}
 
 
@@ -425,8 +413,7 @@ for k in range(len(d["t"])):
     ts.append(time.time() - t0)
     xs.append(x)
     its.append(st.warm_iters + st.inner_iters)
-    rho0 = np.linalg.norm(m.residual(z, z))
-    res.append(float(np.linalg.norm(m.residual(x, z)) / rho0) if st.n_active == 0 else -1.0)
+    res.append(float(st.rel_residual))
 np.savez(%r, x=np.array(xs), s=np.array(ts), iters=np.array(its), res=np.array(res))
 ''' % (ROOT, side, states_path, ORACLE_PARAMS, out_path)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
@@ -442,8 +429,9 @@ def error_vs_oracle(pc, torch, forms, side, warm, steps, dev_index):
     displacement), the oracle one step with the same stopping rule; reported
     per step: max and RMS vertex distance / bounding-box diagonal, the
     residual the form reports, the oracle's residual (R11, FP64) at the
-    form's x* + u, and the oracle's own exit residual (these two only for
-    steps without active collision springs)."""
+    form's x* + u (only for steps without active collision springs and
+    without an impact), and the residual at which the oracle's own stopping
+    test ended (before its exit positions are rounded to float32)."""
     import numpy as np
     import workloads as wl
     from oracle import pd
@@ -591,7 +579,7 @@ def main():
     if rank != 0:
         return
     pk = peaks()
-    l2 = l2_copy_peak(torch, local)
+    l2 = l2_copy_peak(pc, torch.cuda.current_stream().cuda_stream)
     rl = roofline(forms[head]["kernels"], pk, ms, l2)
     line = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms/step", "n_gpus": world, "steps": a.steps,
@@ -622,7 +610,7 @@ def main():
             line["batched"] = {"error": str(e)[:200]}
     if a.error_steps > 0 and world == 1:
         try:
-            ev = error_vs_oracle(pc, torch, list(forms), a.cpu_sample_side, 5, a.error_steps, local)
+            ev = error_vs_oracle(pc, torch, list(forms), a.error_side, 5, a.error_steps, local)
         except Exception as e:  # reported, not fatal for the headline
             ev = {"error": str(e)[:300]}
         oms = ev.pop("_oracle_ms", None)

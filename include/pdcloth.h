@@ -253,6 +253,18 @@ pdc_status pdc_get_displacement(pdc_handle h, float *u, int32_t on_device);
 /* Statistics of the last step. */
 pdc_status pdc_get_stats(pdc_handle h, pdc_stats *out);
 
+/* Copy bandwidth (GB/s, read plus written bytes) of a working set of
+ * `bytes`, half of it read and half written per pass, measured by one
+ * persistent kernel that makes `passes` passes over it on `stream` (a
+ * cudaStream_t or NULL), timed with CUDA events, after two untimed passes.
+ * A working set well below the L2 size (129 MB on GB300) gives the L2 copy
+ * bandwidth that bounds the kernels whose data stays in L2.  The paper has
+ * no counterpart: this supplies the roofline of those kernels.  Allocates
+ * and frees its buffers (on the current device); needs no handle (errors:
+ * pdc_last_error(NULL)).  PDC_ERR_ARG unless 1 KiB <= bytes <= 64 GiB and
+ * passes >= 1. */
+pdc_status pdc_measure_copy_bandwidth(int64_t bytes, int32_t passes, void *stream, double *gbs);
+
 /* Free everything owned by the handle (NULL is ignored). */
 void pdc_destroy(pdc_handle h);
 

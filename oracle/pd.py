@@ -484,7 +484,8 @@ class StepStats:
     rf_iters: int = 0              # residual-forwarding LG iterations run after this step
     rf_res0: float = 0.0           # |residual| of the forwarding problem at the filtered x
     rf_res1: float = 0.0           # ... and after its iterations
-    rel_residual: float = 0.0
+    rel_residual: float = 0.0     # relative PD residual (R11); with collisions on, the last one the
+                                  # stopping test of the relative-residual mode measured
     log: list = field(default_factory=list)
 
 
@@ -629,7 +630,9 @@ class Oracle:
                 xall = self._all(x, obs_next)
                 contact = contact_terms(cm, xm_all, xall, act, quads, kinds, w, p.dhat)
                 if p.tol_rel_residual > 0 and not p.fixed_iters:
-                    if self.rel_residual(x, z, contact) <= p.tol_rel_residual * rho0:
+                    rho = self.rel_residual(x, z, contact)
+                    st.rel_residual = rho / max(rho0, 1e-300)  # the last value the stopping test saw
+                    if rho <= p.tol_rel_residual * rho0:
                         break
                 xn = self._lg(x, z, pin_next, contact)
                 st.inner_iters += 1

@@ -94,6 +94,36 @@ __global__ void k_finite(int n, const float4 *__restrict__ a, int *bad) {
     }
 }
 
+// `passes` copies between the halves a and b of a working set (a -> b on
+// even passes, b -> a on odd ones) in one launch, 4 float4 per thread in
+// flight, loads and stores that bypass L1 (cache-global), and the element
+// each thread handles shifted every pass, so that no thread reads back what
+// it has just written.  Timing it gives the copy bandwidth of the level of
+// the memory hierarchy the working set lives in.
+__global__ void __launch_bounds__(512) k_copy_passes(float4 *a, float4 *b, long long n, int passes) {
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int p = 0; p < passes; ++p) {
+        const float4 *src = (p & 1) ? b : a;
+        float4 *dst = (p & 1) ? a : b;
+        const long long shift = ((long long)p * 4099) % nthr;
+        const long long me = (t + shift) % nthr;
+        for (long long i0 = me; i0 < n; i0 += 4 * nthr) {
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                long long i = i0 + k * nthr;
+                if (i < n) v[k] = __ldcg(src + i);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                long long i = i0 + k * nthr;
+                if (i < n) __stcg(dst + i, v[k]);
+            }
+        }
+    }
+}
+
 inline int nb(long long n) { return (int)((n + 255) / 256); }
 inline float bits_to_float(unsigned int u) {
     float f;
@@ -1545,6 +1575,50 @@ pdc_status pdc_create_batch(int32_t count, const pdc_mesh_desc *meshes, const pd
     u.pins = Pn.empty() ? nullptr : Pn.data();
     u.npins = (int32_t)Pn.size();
     return create_ctx(c, &u, params, stream, out);
+}
+
+pdc_status pdc_measure_copy_bandwidth(int64_t bytes, int32_t passes, void *stream, double *gbs) {
+    if (!gbs || bytes < 1024 || passes < 1 || bytes > ((int64_t)1 << 36)) {
+        g_create_error = "pdc_measure_copy_bandwidth: bytes must be in [1 KiB, 64 GiB], passes >= 1, gbs not NULL";
+        return PDC_ERR_ARG;
+    }
+    try {
+        cudaStream_t s = (cudaStream_t)stream;
+        const long long n = bytes / 2 / (long long)sizeof(float4);
+        DevBuf<float4> a, b;
+        a.alloc(n);
+        b.alloc(n);
+        a.zero(s);
+        b.zero(s);
+        int dev = 0, sms = 1;
+        PDC_CK(cudaGetDevice(&dev));
+        PDC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int grid = sms * 4;
+        k_copy_passes<<<grid, 512, 0, s>>>(a, b, n, 2);  // warm the working set into the cache
+        PDC_LAUNCH_CK();
+        cudaEvent_t e0, e1;
+        PDC_CK(cudaEventCreate(&e0));
+        PDC_CK(cudaEventCreate(&e1));
+        PDC_CK(cudaEventRecord(e0, s));
+        k_copy_passes<<<grid, 512, 0, s>>>(a, b, n, passes);
+        PDC_CK(cudaEventRecord(e1, s));
+        cudaError_t le = cudaGetLastError();
+        cudaError_t se = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (le == cudaSuccess && se == cudaSuccess) PDC_CK(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        PDC_CK(le);
+        PDC_CK(se);
+        *gbs = ms > 0.f ? 2.0 * (double)n * sizeof(float4) * passes / (ms * 1e-3) / 1e9 : 0.0;
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.code;
+    } catch (const std::exception &e) {
+        g_create_error = e.what();
+        return PDC_ERR_CUDA;
+    }
+    return PDC_OK;
 }
 
 void pdc_destroy(pdc_handle h) {

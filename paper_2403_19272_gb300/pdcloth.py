@@ -77,6 +77,7 @@ SIGNATURES = {
     "pdc_get_displacement": (c_i32, [P, P, c_i32]),
     "pdc_get_stats": (c_i32, [P, P]),
     "pdc_destroy": (None, [P]),
+    "pdc_measure_copy_bandwidth": (c_i32, [c_i64, c_i32, P, P]),
     "pdc_last_error": (ctypes.c_char_p, [P]),
     "pdc_set_profiling": (c_i32, [P, c_i32]),
     "pdc_get_kernel_times": (c_i32, [P, P, c_i32, P]),
@@ -178,6 +179,14 @@ def pdc_create_batch(instances, params: pdc_params, stream=None):
 
 def pdc_destroy(h):
     lib().pdc_destroy(h)
+
+
+def pdc_measure_copy_bandwidth(nbytes, passes, stream=None) -> float:
+    out = c_dbl()
+    st = lib().pdc_measure_copy_bandwidth(int(nbytes), int(passes), stream, ctypes.byref(out))
+    if st != PDC_OK:
+        raise PdcError(st, lib().pdc_last_error(None).decode())
+    return out.value
 
 
 def pdc_add_obstacle(h, verts, tris) -> int:
