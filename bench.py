@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form comparison")
     ap.add_argument("--launch-overlap", type=int, default=1, choices=[0, 1],
                     help="1: Chebyshev steps launched as programmatic dependents (default)")
+    ap.add_argument("--graph-loops", type=int, default=1, choices=[0, 1],
+                    help="1: LG loops as CUDA graphs with device-side stopping tests (default); 0: host-driven")
     ap.add_argument("--no-launch-count", action="store_true",
                     help="skip the CUDA activity trace (e.g. when running under ncu)")
     return ap.parse_args()
@@ -64,8 +66,9 @@ FORMS = {"mixed16": 2, "mixed": 1, "fp32": 0}
 DTYPES = {"mixed16": "f16+f32+f64", "mixed": "bf16+f32+f64", "fp32": "f32"}
 
 
-def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1):
+def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1, graph_loops=1):
     p = pc.pdc_default_params()
+    p.graph_loops = graph_loops  # LG loops as CUDA graphs (stopping tests on the device)
     p.launch_overlap = overlap  # Chebyshev steps as programmatic dependent launches
     p.tol_rel_residual = 1e-3
     p.max_outer = 2
@@ -155,11 +158,11 @@ class ClockSampler:
 
 
 def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True, sweeps=28, cheb_ratio=300.0,
-             overlap=1):
+             overlap=1, graph_loops=1):
     """Warm-up, timed region (device), profiled replay, e2e through host buffers."""
     import numpy as np
     stream = torch.cuda.Stream()
-    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap)
+    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap, graph_loops)
     t_setup = time.time()
     h = pc.pdc_create(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend, p,
                       stream.cuda_stream)
@@ -206,26 +209,25 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    # ---- profiled replay of the same steps (per-kernel event timing and the
-    # step statistics, kept out of the timed region)
+    # ---- profiled replay of the same steps (per-kernel event timing; the
+    # profiler drives the LG loops from the host, same kernels)
     restore()
     pc.pdc_set_profiling(h, True)
-    st_list = []
     for _ in range(steps):
         one_step()
-        st_list.append(pc.pdc_get_stats(h))
     torch.cuda.synchronize()
     kt = pc.pdc_get_kernel_times(h)
     pc.pdc_set_profiling(h, False)
     # ---- kernel launches of the library per step, counted by the CUDA
     # activity profiler over a replay of the same number of steps
     restore()
-    launches = count_launches(torch, one_step, steps) if launch_count else None
+    launches, busy = count_launches(torch, one_step, steps) if launch_count else (None, None)
     restore()
     # ---- e2e through the public API with host buffers: pin targets h2d, positions d2h
     pin_host = torch.empty(pins.shape[1:], dtype=torch.float32).pin_memory()
     pos_host = torch.empty((scene.n, 3), dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
+    st_list = []
     t0 = time.perf_counter()
     for j in range(steps):
         pin_host.numpy()[:] = scene.pins_at((k + 1) * dt)
@@ -234,6 +236,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
         pc.pdc_step(h, dt)
         k += 1
         pc._check(h, lib.pdc_get_positions(h, pos_host.data_ptr(), 0))
+        st_list.append(pc.pdc_get_stats(h))  # a host-side struct copy
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
     x = pos_host.numpy().copy()
@@ -244,6 +247,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
                 rel_res=statistics.mean(s["rel_residual"] for s in st_list),
                 cand=statistics.mean(s["n_candidates"] for s in st_list),
                 toi=min(s["t_toi"] for s in st_list), finite=bool(np.isfinite(x).all()),
+                graph_loops=statistics.mean(s["graph_loops"] for s in st_list), device_busy=busy,
                 launches=launches)
 
 
@@ -316,8 +320,9 @@ def run_batched(pc, torch, steps=5, warmup=2, dev_index=0):
 
 def count_launches(torch, one_step, steps):
     """Kernels launched by the library (names beginning with k_) during
-    `steps` steps, from torch.profiler's CUDA activity trace; None if the
-    trace is unavailable."""
+    `steps` steps, from torch.profiler's CUDA activity trace, and the share of
+    the traced interval (first kernel start to last kernel end) in which some
+    kernel ran; (None, None) if the trace is unavailable."""
     try:
         from torch.profiler import ProfilerActivity, profile
         with profile(activities=[ProfilerActivity.CUDA]):  # first session initialises the trace
@@ -329,12 +334,29 @@ def count_launches(torch, one_step, steps):
         import re
         pat = re.compile(r"(?:^|[\s:])k_\w+")
         n = 0
+        spans = []
         for ev in prof.events():
-            if str(getattr(ev, "device_type", "")).endswith("CUDA") and pat.search(ev.name or ""):
-                n += 1
-        return n
+            if str(getattr(ev, "device_type", "")).endswith("CUDA"):
+                if pat.search(ev.name or ""):
+                    n += 1
+                tr = getattr(ev, "time_range", None)
+                if tr is not None and tr.end > tr.start:
+                    spans.append((tr.start, tr.end))
+        busy = None
+        if spans:
+            spans.sort()
+            tot, cs, ce = 0.0, spans[0][0], spans[0][1]
+            for a, b in spans[1:]:
+                if a > ce:
+                    tot += ce - cs
+                    cs, ce = a, b
+                else:
+                    ce = max(ce, b)
+            tot += ce - cs
+            busy = round(tot / max(spans[-1][1] - spans[0][0], 1e-9), 4)
+        return n, busy
     except Exception:
-        return None
+        return None, None
 
 
 # profiled regions that enclose other profiled regions (not kernels themselves)
@@ -572,7 +594,7 @@ def main():
     forms = {}
     for f in a.forms.split(","):
         forms[f] = run_form(pc, torch, scene, FORMS[f], a.steps, a.warmup, local,
-                            not a.no_launch_count, a.sweeps, a.cheb_ratio, a.launch_overlap)
+                            not a.no_launch_count, a.sweeps, a.cheb_ratio, a.launch_overlap, a.graph_loops)
     head = list(forms)[0]
     ms = forms[head]["ms"]
     ms = max_over_ranks(ms, f"cuda:{local}")
@@ -592,6 +614,7 @@ def main():
                       "vertex_iters_per_s": round(scene.n * d["iters"] / (d["ms"] * 1e-3), 1),
                       "gpu_launches": d["launches"],
                       "rel_residual": d["rel_res"], "candidates": d["cand"], "min_toi": d["toi"],
+                      "graph_loops_per_step": d["graph_loops"], "device_busy": d["device_busy"],
                       "setup_s": round(d["setup_s"], 2), "e2e_ms_per_step": round(d["e2e_ms"], 3)}
                   for f, d in forms.items()},
         "roofline": rl,

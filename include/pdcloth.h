@@ -147,6 +147,18 @@ typedef struct {
     int32_t rf_iters;        /* cap on those iterations (exact count when
                                 fixed_iters = 1); they stop once the largest
                                 change is below tol_inner * bbox diagonal       */
+    int32_t graph_loops;     /* 1 (default): each LG loop of a step (warm start,
+                                inner loops) runs as one CUDA graph launch whose
+                                conditional while node repeats the iteration
+                                until a one-thread kernel on the device ends it
+                                with the host loop's tests (relative residual,
+                                stagnation, step change, iteration cap): no
+                                host synchronisation per iteration.  0, or
+                                while profiling (pdc_set_profiling), PDC_LOG or
+                                PDC_SYNC_CHECK, or with accel = 1: the host
+                                reads each iteration's residual back and
+                                decides.  Same kernels in the same order either
+                                way.                                              */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
@@ -169,6 +181,8 @@ typedef struct {
                                     the step's first broad phase (bp_reuse)      */
     int32_t rf_iters;            /* residual-forwarding LG iterations run at the
                                     end of this step (0: not triggered)          */
+    int32_t graph_loops;         /* LG loops of this step that ran as one graph
+                                    launch (graph_loops parameter)               */
 } pdc_stats;
 
 /* Defaults: dt 1/200, g = (0,0,-9.8), K = 2, a_max 20, alpha 0.8, automatic
@@ -176,7 +190,7 @@ typedef struct {
  * iterations, 4 damped Jacobi sweeps (automatic omega), 1 cycle, no basis,
  * FP32, samples 3/4, collisions on, no LG acceleration, tensor cores for the
  * mixed forms, dependent launches on, broad-phase reuse and residual
- * forwarding off. */
+ * forwarding off, LG loops as CUDA graphs. */
 void pdc_default_params(pdc_params *p);
 
 /* Build the solver for one cloth mesh (Sec. 3; Eq. (global) rest matrix,

@@ -124,6 +124,109 @@ __global__ void __launch_bounds__(512) k_copy_passes(float4 *a, float4 *b, long 
     }
 }
 
+// ---- device-side control of an LG loop (loops run as CUDA graphs)
+// Settings of one loop for its stopping tests (same tests, in the same order,
+// as the host-driven loop of pdc_ctx::step).
+struct LoopCfg {
+    int kind;                // 0: warm start (counts into warm_iters), 1: inner loop
+    int max_iters;           // iteration cap of the loop
+    int check_rel;           // relative-residual test and stagnation stop before each solve
+    int dx_inner;            // after each solve: stop when max |dx| <= tolx_in
+    int dx_springs;          // after a solve with collision springs: stop when max |dx| <= tolx_out
+    int aa_m;                // Anderson history depth (0: no mixing)
+    int stag_n;              // iterations without 1 % progress that stop the loop
+    int use_cond;            // set the graph's while condition
+    double tol_rel;
+    double tolx_in, tolx_out;
+    cudaGraphConditionalHandle cond;
+};
+
+// At the start of a step: the reference residual (its squared norm is in
+// sc->rsq) and the step's counters.
+__global__ void k_loop_step_init(LoopCtl *c, const Scalars *sc) {
+    c->rho0 = sqrt(sc->rsq);
+    c->rel = 0.0;
+    c->warm_iters = c->inner_iters = c->contact_iters = 0;
+    c->graph_loops = 0;
+}
+
+// At the start of a loop (the host-driven loop resets its Accel state here).
+__global__ void k_loop_begin(LoopCtl *c, int graph) {
+    c->iters = 0;
+    c->go = 1;
+    c->springs = 0;
+    c->stag_best = 0.0;
+    c->stag_count = 0;
+    c->aa_hist_min = 0.0;
+    c->aa_hist_n = 0;
+    c->aa_count = c->aa_widx = c->aa_have_prev = 0;
+    c->aa_slot = c->aa_prev = c->aa_ncol = 0;
+    if (graph) c->graph_loops++;
+}
+
+// The loop's decision after the residual of the current iterate (and, with
+// after_solve, after the solve that produced it): the step-change tests of
+// that solve, the iteration cap, then the relative-residual and stagnation
+// tests; when the loop goes on, the iteration is counted and its
+// Anderson-mixing slot assigned.  One thread.  Every path sets go (and the
+// graph's condition), and go = 1 only while iters < max_iters, so a graph
+// loop ends after at most max_iters iterations; a device error bit (a
+// bounded wait that ran out) ends it at once.
+__global__ void k_loop_decide(LoopCtl *c, LoopCfg f, const Scalars *sc, const int *n_cv, const int *dev_err,
+                              int after_solve) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int go = (*dev_err & (PDC_DEVERR_UMMA | PDC_DEVERR_COPY)) ? 0 : 1;
+    const double dx = (double)__uint_as_float(sc->dxmax);
+    if (go && after_solve) {
+        if (f.dx_inner && dx <= f.tolx_in) go = 0;
+        else if (f.dx_springs && c->springs && dx <= f.tolx_out) go = 0;
+    }
+    if (go && c->iters >= f.max_iters) go = 0;
+    if (go) {
+        const int springs = (n_cv && *n_cv > 0) ? 1 : 0;
+        const double rho = sqrt(sc->rsq);
+        if (f.check_rel) {
+            c->rel = rho / fmax(c->rho0, 1e-300);
+            if (rho <= f.tol_rel * c->rho0) {
+                go = 0;
+            } else if (springs || c->stag_best == 0.0 || rho < 0.99 * c->stag_best) {
+                c->stag_best = (springs || c->stag_best == 0.0) ? rho : fmin(c->stag_best, rho);
+                c->stag_count = 0;
+            } else if (++c->stag_count >= f.stag_n) {
+                go = 0;
+            }
+        }
+        if (go) {
+            if (springs) c->contact_iters++;
+            if (f.aa_m > 0) {
+                // restart the history when the residual jumps above twice its
+                // smallest value since the last restart
+                if (c->aa_hist_n > 0 && rho > 2.0 * c->aa_hist_min) {
+                    c->aa_hist_n = 0;
+                    c->aa_count = c->aa_widx = c->aa_have_prev = 0;
+                }
+                c->aa_hist_min = c->aa_hist_n > 0 ? fmin(c->aa_hist_min, rho) : rho;
+                c->aa_hist_n++;
+                c->aa_prev = c->aa_have_prev;
+                c->aa_slot = 0;
+                if (c->aa_have_prev) {
+                    c->aa_slot = c->aa_widx % f.aa_m;
+                    c->aa_widx++;
+                    c->aa_count = min(c->aa_count + 1, f.aa_m);
+                }
+                c->aa_ncol = c->aa_count;
+                c->aa_have_prev = 1;
+            }
+            c->springs = springs;
+            c->iters++;
+            if (f.kind == 0) c->warm_iters++;
+            else c->inner_iters++;
+        }
+    }
+    c->go = go;
+    if (f.use_cond) cudaGraphSetConditional(f.cond, go ? 1u : 0u);
+}
+
 inline int nb(long long n) { return (int)((n + 255) / 256); }
 inline float bits_to_float(unsigned int u) {
     float f;
@@ -338,6 +441,8 @@ struct pdc_ctx {
 
     ~pdc_ctx() {
         if (hsc) cudaFreeHost(hsc);
+        for (auto &G : gl) free_graph(G);
+        if (gs) cudaStreamDestroy(gs);
     }
 
     ClothView cloth() const {
@@ -446,6 +551,28 @@ struct pdc_ctx {
     double bytes_basis(int r) const { return (double)n * r * (P.precision != 0 ? 2 : 4) + (double)n * 12; }
     void lg_iteration(bool contacts, bool check_rel, double rho0, bool &converged, int r_nc, int r_c, int cycles,
                       int sweeps, bool pccd = true);
+    void enqueue_residual(bool contacts);
+    void enqueue_solve(bool contacts, bool springs, bool device, float w_acc, int r_nc, int r_c, int cycles,
+                       int sweeps, bool pccd);
+    // device-driven LG loops (CUDA graphs with a conditional while node)
+    struct GraphLoop {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t e = nullptr;
+        unsigned gen = 0;
+    };
+    GraphLoop gl[4];             // warm start, inner loop without collisions, inner loop with bp.cur = 0 / 1
+    cudaStream_t gs = nullptr;   // capture stream
+    unsigned graph_gen = 1;      // bumped when a buffer a graph captures is reallocated
+    bool graphs_failed = false;  // a graph could not be built: host-driven loops from then on
+    bool graph_overlap = true;   // programmatic dependent launches inside the graphs
+    DevBuf<LoopCtl> ctl;
+    LoopCtl hctl;
+    bool device_loops_ok() const;
+    void free_graph(GraphLoop &G);
+    LoopCfg loop_cfg(int kind, int max_iters, bool relmode, bool contacts) const;
+    bool build_loop(GraphLoop &G, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
+                    bool pccd);
+    bool run_loop(int gi, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps, bool pccd);
     void residual_forwarding();
     void full_ccd(const float4 *x0, const float4 *x1, bool merge);
     void broad_phase_pass(const float4 *x0, const float4 *x1, bool super);
@@ -773,6 +900,8 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
     umax_d.alloc(1);
     sflag.alloc(1);
     sflag.zero(s);
+    ctl.alloc(1);
+    ctl.zero(s);
     n_cv_d.zero(s);
     n_act_d.zero(s);
     contact_list.alloc(std::max(n, 1));
@@ -785,6 +914,7 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
 }
 
 void pdc_ctx::install_basis(const std::vector<float> &U, int r) {
+    ++graph_gen;  // new basis buffers
     r_warm = r;
     r_reuse = std::min(std::max(P.r_reuse, 0), r);
     if (r_reuse > 128) throw Error(PDC_ERR_ARG, "r_reuse must be <= 128");
@@ -894,6 +1024,7 @@ void pdc_ctx::setup_basis() {
 
 void pdc_ctx::ensure_topology() {
     if (!topo_dirty) return;
+    ++graph_gen;  // collision-set buffers reallocated
     int nvo = 0, nto = 0;
     for (auto &o : obs) {
         nvo += (int)o.V.size() / 3;
@@ -965,16 +1096,16 @@ void pdc_ctx::ensure_topology() {
 }
 
 // ============================================================================ the step (Alg. 1)
-// One LG iteration: local projections + residual at the iterate Xp[0:n],
-// then `cycles` x {subspace correction, `sweeps` Jacobi sweeps}, Xp += delta,
-// then (with contacts) partial CCD on (Xm, Xp).
-void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &converged, int r_nc, int r_c, int cycles,
-                           int sweeps, bool pccd) {
+// An LG iteration in two parts, enqueued on s: the residual part (contact
+// springs of the active pairs and the local projections + residual at the
+// iterate, Eq. local / Eq. global), and the solve part (`cycles` x {subspace
+// correction, `sweeps` Jacobi or Chebyshev steps}, the iterate += delta, LG
+// acceleration, then with contacts the partial CCD of Sec. 4.1 on (Xm, Xp)).
+// The host-driven loop (lg_iteration) takes its stopping tests between the
+// two on the host; the device-driven loop (run_loop) in k_loop_decide.
+void pdc_ctx::enqueue_residual(bool contacts) {
     ClothView c = cloth();
-    converged = false;
     PDC_CK(cudaMemsetAsync(&sc.p->rsq, 0, sizeof(double), s));
-    PDC_CK(cudaMemsetAsync(&sc.p->dxmax, 0, sizeof(unsigned int), s));
-    if (accel.on && P.accel == 2 && P.fixed_iters == 0) aa_clear(s, aa_Gb);  // normal equations of this iteration
     const float *cw = nullptr;
     const float4 *cf = nullptr;
     if (contacts) {
@@ -988,41 +1119,22 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
         n_cv_d.zero(s);
     }
     PROF("local_residual", bytes_residual(contacts), launch_residual(s, c, Xs, Ucur, Z, cw, cf, R, sc, nullptr, 0));
-    bool acc = accel.on && !(P.fixed_iters != 0);
-    bool aa = acc && P.accel == 2;
-    // whether collision springs exist this iteration (device count); known on
-    // the host when the residual is read back anyway
-    bool springs = contacts;
-    last_springs = contacts;
-    if (check_rel || log || acc) {
-        if (contacts) PDC_CK(cudaMemcpyAsync(&sc.p->n_contact_v, n_cv_d.p, sizeof(int), cudaMemcpyDeviceToDevice, s));
-        read_scalars();
-        if (contacts) springs = hsc->n_contact_v > 0;
-        last_springs = springs;
-        double rho = std::sqrt(hsc->rsq);
-        if (log) {
-            int na = 0, ncv = 0;
-            n_act_d.download(&na, 1, s);
-            n_cv_d.download(&ncv, 1, s);
-            PDC_CK(cudaStreamSynchronize(s));
-            std::fprintf(stderr, "[pdc] lg contacts=%d rho=%.6g rel=%.6g active=%d contact_v=%d\n", (int)contacts, rho,
-                         rho / std::max(rho0, 1e-300), na, ncv);
-        }
-    }
-    if (check_rel) {
-        double rho = std::sqrt(hsc->rsq);
-        st.rel_residual = rho / std::max(rho0, 1e-300);
-        if (rho <= P.tol_rel_residual * rho0 || accel.stagnated(rho, springs)) {
-            converged = true;
-            return;
-        }
-    }
-    if (springs) st.contact_iters++;
-    float w_acc = 1.f;
-    if (aa) accel.aa_observe(std::sqrt(hsc->rsq));
-    else if (acc) w_acc = (float)accel.next(std::sqrt(hsc->rsq));
-    if (log && acc && !aa) std::fprintf(stderr, "[pdc]    accel k=%d w=%.4f rho=%.4f\n", accel.k, w_acc, accel.rho);
-    float4 *xprev = (acc && !aa) ? Xacc.p : nullptr;
+}
+
+// springs: whether the iteration has collision springs when the host knows
+// it (host-driven loop); device: the device decides (the tensor-core /
+// compact path, the Anderson bookkeeping) and the host knows only whether
+// springs are possible (contacts).
+void pdc_ctx::enqueue_solve(bool contacts, bool springs, bool device, float w_acc, int r_nc, int r_c, int cycles,
+                            int sweeps, bool pccd) {
+    ClothView c = cloth();
+    const float *cw = contacts ? CW.p : nullptr;
+    PDC_CK(cudaMemsetAsync(&sc.p->dxmax, 0, sizeof(unsigned int), s));
+    const bool acc = accel.on && P.fixed_iters == 0;
+    const bool aa = acc && P.accel == 2;
+    if (aa) aa_clear(s, aa_Gb);  // normal equations of this iteration
+    float4 *xprev = (acc && !aa && !device) ? Xacc.p : nullptr;
+    const bool sp = device ? contacts : springs;  // springs possible on this path
     SubspaceView S = sub(r_nc, r_c);
     SubspaceWork W = work();
     float4 *din = D0, *dout = D1;
@@ -1035,11 +1147,11 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
         }
         if (r_warm > 0 && (r_nc > 0 || r_c > 0)) {
             PROF("subspace_project", bytes_basis(springs ? r_c : r_nc),
-                 launch_project(s, S, rl, n_cv_d, W, springs));
-            if (springs && r_c > 0) PROF("subspace_syrk", 0, launch_syrk(s, S, contact_list, n_cv_d, cw, W));
+                 launch_project(s, S, rl, n_cv_d, W, sp, device));
+            if (sp && r_c > 0) PROF("subspace_syrk", 0, launch_syrk(s, S, contact_list, n_cv_d, cw, W));
             PROF("reduced_solve", 0, launch_reduced_solve(s, S, n_cv_d, W));
             PROF("subspace_lift", bytes_basis(springs ? r_c : r_nc) + 12.0 * n,
-                 launch_lift(s, S, n_cv_d, W, have_delta ? din : nullptr, dout, springs));
+                 launch_lift(s, S, n_cv_d, W, have_delta ? din : nullptr, dout, sp, device));
             std::swap(din, dout);
             have_delta = true;
         }
@@ -1098,17 +1210,23 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
         }
     }
     if (aa) {
-        int m = std::min(std::max(P.aa_depth, 1), 8);
-        int slot = 0;
-        if (accel.aa_have_prev) {
-            slot = accel.aa_widx % m;
-            accel.aa_widx++;
-            accel.aa_count = std::min(accel.aa_count + 1, m);
+        const int m = std::min(std::max(P.aa_depth, 1), 8);
+        if (device) {
+            PROF("anderson_mix", 0,
+                 launch_aa_device(s, n, is_free, din, Ucur, aa_f, aa_g, aa_dF, aa_dG, m, ctl.p, aa_Gb, aa_theta, Xs,
+                                  Xp, P.launch_overlap != 0));
+        } else {
+            int slot = 0;
+            if (accel.aa_have_prev) {
+                slot = accel.aa_widx % m;
+                accel.aa_widx++;
+                accel.aa_count = std::min(accel.aa_count + 1, m);
+            }
+            PROF("anderson_mix", 0,
+                 launch_aa(s, n, is_free, din, Ucur, aa_f, aa_g, aa_dF, aa_dG, slot, accel.aa_have_prev ? 1 : 0,
+                           accel.aa_count, aa_Gb, aa_theta, Xs, Xp, P.launch_overlap != 0));
+            accel.aa_have_prev = true;
         }
-        PROF("anderson_mix", 0,
-             launch_aa(s, n, is_free, din, Ucur, aa_f, aa_g, aa_dF, aa_dG, slot, accel.aa_have_prev ? 1 : 0,
-                       accel.aa_count, aa_Gb, aa_theta, Xs, Xp, P.launch_overlap != 0));
-        accel.aa_have_prev = true;
     }
     if (contacts && P.collisions && pccd) {
         bp.prof = prof.on ? &prof : nullptr;
@@ -1125,6 +1243,188 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
                          cnt[1], ps.pass_full ? "full" : "watch-list", ps.n_watch, ps.n_near);
         }
     }
+}
+
+// One LG iteration driven by the host: the residual part, the stopping tests
+// on the host (residual read back), then the solve part.
+void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &converged, int r_nc, int r_c, int cycles,
+                           int sweeps, bool pccd) {
+    converged = false;
+    enqueue_residual(contacts);
+    bool acc = accel.on && !(P.fixed_iters != 0);
+    bool aa = acc && P.accel == 2;
+    // whether collision springs exist this iteration (device count); known on
+    // the host when the residual is read back anyway
+    bool springs = contacts;
+    last_springs = contacts;
+    if (check_rel || log || acc) {
+        if (contacts) PDC_CK(cudaMemcpyAsync(&sc.p->n_contact_v, n_cv_d.p, sizeof(int), cudaMemcpyDeviceToDevice, s));
+        read_scalars();
+        if (contacts) springs = hsc->n_contact_v > 0;
+        last_springs = springs;
+        double rho = std::sqrt(hsc->rsq);
+        if (log) {
+            int na = 0, ncv = 0;
+            n_act_d.download(&na, 1, s);
+            n_cv_d.download(&ncv, 1, s);
+            PDC_CK(cudaStreamSynchronize(s));
+            std::fprintf(stderr, "[pdc] lg contacts=%d rho=%.6g rel=%.6g active=%d contact_v=%d\n", (int)contacts, rho,
+                         rho / std::max(rho0, 1e-300), na, ncv);
+        }
+    }
+    if (check_rel) {
+        double rho = std::sqrt(hsc->rsq);
+        st.rel_residual = rho / std::max(rho0, 1e-300);
+        if (rho <= P.tol_rel_residual * rho0 || accel.stagnated(rho, springs)) {
+            converged = true;
+            return;
+        }
+    }
+    if (springs) st.contact_iters++;
+    float w_acc = 1.f;
+    if (aa) accel.aa_observe(std::sqrt(hsc->rsq));
+    else if (acc) w_acc = (float)accel.next(std::sqrt(hsc->rsq));
+    if (log && acc && !aa) std::fprintf(stderr, "[pdc]    accel k=%d w=%.4f rho=%.4f\n", accel.k, w_acc, accel.rho);
+    enqueue_solve(contacts, springs, false, w_acc, r_nc, r_c, cycles, sweeps, pccd);
+}
+
+// ---------------------------------------------------------------------------- LG loops as CUDA graphs
+// A loop as one graph: k_loop_begin, the residual part and k_loop_decide,
+// then a conditional while node whose body is {solve part, residual part,
+// k_loop_decide}; k_loop_decide sets the while condition, so the loop runs
+// on the device with no host round trip per iteration.  The graph captures
+// buffer addresses and the list index bp.cur, so it is rebuilt when either
+// changes (graph_gen counts reallocations).
+bool pdc_ctx::device_loops_ok() const {
+    if (P.graph_loops == 0 || graphs_failed || prof.on || log || sync_check) return false;
+    if (P.accel == 1 && P.fixed_iters == 0) return false;  // Chebyshev acceleration: host-side weights
+    // a spring iteration of the mixed form chooses between the tensor-core and
+    // the compact path on the device only when the compact copy covers r_reuse
+    SubspaceView S = sub(r_warm, r_reuse);
+    if (P.collisions && S.umma && r_warm > 0 && !device_path_choice(S)) return false;
+    return true;
+}
+
+void pdc_ctx::free_graph(GraphLoop &G) {
+    if (G.e) cudaGraphExecDestroy(G.e);
+    if (G.g) cudaGraphDestroy(G.g);
+    G.e = nullptr;
+    G.g = nullptr;
+}
+
+LoopCfg pdc_ctx::loop_cfg(int kind, int max_iters, bool relmode, bool contacts) const {
+    LoopCfg f;
+    std::memset(&f, 0, sizeof(f));
+    const bool fixed = P.fixed_iters != 0;
+    f.kind = kind;
+    f.max_iters = max_iters;
+    f.check_rel = relmode ? 1 : 0;
+    f.dx_inner = (!fixed && !relmode) ? 1 : 0;
+    f.dx_springs = (contacts && relmode) ? 1 : 0;
+    f.aa_m = (P.accel == 2 && !fixed) ? std::min(std::max(P.aa_depth, 1), 8) : 0;
+    f.stag_n = Accel::STAG_N;
+    f.tol_rel = P.tol_rel_residual;
+    f.tolx_in = P.tol_inner * L;
+    f.tolx_out = P.tol_outer * L;
+    return f;
+}
+
+bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
+                         bool pccd) {
+    free_graph(G);
+    if (!gs) PDC_CK(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+    cudaStream_t saved = s;
+    s = gs;  // everything below is captured from the capture stream
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t e = nullptr;
+    bool capturing = false;
+    try {
+        PDC_CK(cudaStreamBeginCapture(gs, cudaStreamCaptureModeRelaxed));
+        capturing = true;
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cg = nullptr;
+        PDC_CK(cudaStreamGetCaptureInfo(gs, &cst, nullptr, &cg, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h;
+        PDC_CK(cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault));
+        LoopCfg cfg = cfg0;
+        cfg.cond = h;
+        cfg.use_cond = 1;
+        k_loop_begin<<<1, 1, 0, s>>>(ctl, 1);
+        PDC_LAUNCH_CK();
+        enqueue_residual(contacts);
+        k_loop_decide<<<1, 1, 0, s>>>(ctl, cfg, sc, n_cv_d, sflag, 0);
+        PDC_LAUNCH_CK();
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        PDC_CK(cudaStreamGetCaptureInfo(gs, &cst, nullptr, nullptr, &deps, nullptr, &nd));
+        // (the parameter union has no default constructor: zeroed storage)
+        alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+        std::memset(cp_raw, 0, sizeof(cp_raw));
+        cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_raw);
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn;
+        PDC_CK(cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        PDC_CK(cudaStreamUpdateCaptureDependencies(gs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+        capturing = false;
+        PDC_CK(cudaStreamEndCapture(gs, &g));
+        PDC_CK(cudaStreamBeginCaptureToGraph(gs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        capturing = true;
+        enqueue_solve(contacts, contacts, true, 1.f, r_nc, r_c, cycles, sweeps, pccd);
+        enqueue_residual(contacts);
+        k_loop_decide<<<1, 1, 0, s>>>(ctl, cfg, sc, n_cv_d, sflag, 1);
+        PDC_LAUNCH_CK();
+        cudaGraph_t b2 = nullptr;
+        capturing = false;
+        PDC_CK(cudaStreamEndCapture(gs, &b2));
+        PDC_CK(cudaGraphInstantiate(&e, g, 0));
+    } catch (const std::exception &ex) {
+        if (capturing) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(gs, &junk);
+            if (junk && junk != g) cudaGraphDestroy(junk);
+        }
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();  // clear the failed capture's error
+        s = saved;
+        if (log) std::fprintf(stderr, "[pdc] LG loop graph not built (%s): host-driven loops\n", ex.what());
+        return false;
+    }
+    s = saved;
+    G.g = g;
+    G.e = e;
+    G.gen = graph_gen + bp.gen;
+    return true;
+}
+
+// Runs one LG loop as a graph launch on s (builds or rebuilds the graph when
+// needed).  False when the graph cannot be built: the caller then runs the
+// host-driven loop.
+bool pdc_ctx::run_loop(int gi, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
+                       bool pccd) {
+    GraphLoop &G = gl[gi];
+    if (!G.e || G.gen != graph_gen + bp.gen) {
+        // programmatic dependent launches inside the graph when the driver
+        // takes them, else plain kernel nodes
+        const int ov = P.launch_overlap;
+        if (!graph_overlap) P.launch_overlap = 0;
+        bool ok = build_loop(G, cfg, contacts, r_nc, r_c, cycles, sweeps, pccd);
+        if (!ok && P.launch_overlap) {
+            graph_overlap = false;
+            P.launch_overlap = 0;
+            ok = build_loop(G, cfg, contacts, r_nc, r_c, cycles, sweeps, pccd);
+        }
+        P.launch_overlap = ov;
+        if (!ok) {
+            graphs_failed = true;
+            return false;
+        }
+    }
+    PDC_CK(cudaGraphLaunch(G.e, s));
+    return true;
 }
 
 void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {
@@ -1203,24 +1503,46 @@ void pdc_ctx::step() {
     // rho0 = residual at z (no collision springs)
     PDC_CK(cudaMemsetAsync(&sc.p->rsq, 0, sizeof(double), s));
     launch_residual(s, c, Xs, Ucur, Z, nullptr, nullptr, R, sc, nullptr, 0);
-    read_scalars();
-    double rho0 = std::sqrt(hsc->rsq);
-    st.rho0 = rho0;
+    k_loop_step_init<<<1, 1, 0, s>>>(ctl, sc);
+    PDC_LAUNCH_CK();
+    std::memset(&hctl, 0, sizeof(hctl));
+    // device-driven loops need no residual on the host; the host-driven ones read it here
+    const bool dev = device_loops_ok();
+    double rho0 = 0.0;
+    bool have_rho0 = false;
+    auto host_rho0 = [&]() {
+        if (!have_rho0) {
+            read_scalars();
+            rho0 = std::sqrt(hsc->rsq);
+            st.rho0 = rho0;
+            have_rho0 = true;
+        }
+        return rho0;
+    };
+    if (!dev) host_rho0();
     if (log) std::fprintf(stderr, "[pdc] step n=%d omega=%.4f rho0=%.6g dhat=%.3g k=%.4g\n", n, omega, rho0, dhat, k_ndb);
     const double tolx_in = P.tol_inner * L, tolx_out = P.tol_outer * L;
+    bool dev_used = false;  // some loop ran on the device: its counters are in ctl
+    bool last_dev = false;  // the last loop ran on the device: the last residual is in ctl
 
     // ---- warm start: LG iterations of I + Psi in span(U) + sweeps
     accel.on = P.accel != 0 && !fixed;
     accel.rho_fixed = P.accel_rho;
     accel.reset();
-    for (int it = 0; it < P.warm_iters; ++it) {
-        bool conv = false;
-        lg_iteration(false, relmode, rho0, conv, r_warm, 0, cycles, sweeps);
-        if (conv) break;
-        st.warm_iters++;
-        if (!fixed && !relmode) {
-            read_scalars();
-            if (bits_to_float(hsc->dxmax) <= tolx_in) break;
+    if (dev && run_loop(0, loop_cfg(0, P.warm_iters, relmode, false), false, r_warm, 0, cycles, sweeps, true)) {
+        dev_used = last_dev = true;
+    } else {
+        last_dev = false;
+        host_rho0();
+        for (int it = 0; it < P.warm_iters; ++it) {
+            bool conv = false;
+            lg_iteration(false, relmode, rho0, conv, r_warm, 0, cycles, sweeps);
+            if (conv) break;
+            st.warm_iters++;
+            if (!fixed && !relmode) {
+                read_scalars();
+                if (bits_to_float(hsc->dxmax) <= tolx_in) break;
+            }
         }
     }
 
@@ -1228,14 +1550,21 @@ void pdc_ctx::step() {
     if (!P.collisions) {
         // no collision handling: the inner LG loop without springs or CCD
         accel.reset();
-        for (int it = 0; it < P.max_inner; ++it) {
-            bool conv = false;
-            lg_iteration(false, relmode, rho0, conv, r_warm, 0, cycles, sweeps);
-            if (conv) break;
-            st.inner_iters++;
-            if (!fixed && !relmode) {
-                read_scalars();
-                if (bits_to_float(hsc->dxmax) <= tolx_in) break;
+        if (dev && !graphs_failed &&
+            run_loop(1, loop_cfg(1, P.max_inner, relmode, false), false, r_warm, 0, cycles, sweeps, true)) {
+            dev_used = last_dev = true;
+        } else {
+            last_dev = false;
+            host_rho0();
+            for (int it = 0; it < P.max_inner; ++it) {
+                bool conv = false;
+                lg_iteration(false, relmode, rho0, conv, r_warm, 0, cycles, sweeps);
+                if (conv) break;
+                st.inner_iters++;
+                if (!fixed && !relmode) {
+                    read_scalars();
+                    if (bits_to_float(hsc->dxmax) <= tolx_in) break;
+                }
             }
         }
     } else {
@@ -1264,35 +1593,56 @@ void pdc_ctx::step() {
             st.outer_iters++;
             accel.reset();  // the constraint set changed (full CCD)
             int inner = 0;
-            for (int it = 0; it < P.max_inner; ++it) {
-                bool conv = false;
-                lg_iteration(true, relmode, rho0, conv, r_warm, r_reuse, cycles, sweeps);
-                if (conv) break;
-                ++inner;
-                st.inner_iters++;
-                if (!fixed && !relmode) {
-                    read_scalars();
-                    if (bits_to_float(hsc->dxmax) <= tolx_in) break;
-                } else if (relmode && last_springs) {
-                    // with collision springs the residual carries barrier
-                    // terms whose weights change every iteration: the inner
-                    // loop also ends once the iterate has settled to the
-                    // outer tolerance
-                    read_scalars();
-                    if (bits_to_float(hsc->dxmax) <= tolx_out) break;
+            const int inner0 = hctl.inner_iters;
+            bool ran_dev = dev && !graphs_failed &&
+                           run_loop(2 + bp.cur, loop_cfg(1, P.max_inner, relmode, true), true, r_warm, r_reuse, cycles,
+                                    sweeps, true);
+            if (ran_dev) {
+                dev_used = last_dev = true;
+            } else {
+                last_dev = false;
+                host_rho0();
+                for (int it = 0; it < P.max_inner; ++it) {
+                    bool conv = false;
+                    lg_iteration(true, relmode, rho0, conv, r_warm, r_reuse, cycles, sweeps);
+                    if (conv) break;
+                    ++inner;
+                    st.inner_iters++;
+                    if (!fixed && !relmode) {
+                        read_scalars();
+                        if (bits_to_float(hsc->dxmax) <= tolx_in) break;
+                    } else if (relmode && last_springs) {
+                        // with collision springs the residual carries barrier
+                        // terms whose weights change every iteration: the inner
+                        // loop also ends once the iterate has settled to the
+                        // outer tolerance
+                        read_scalars();
+                        if (bits_to_float(hsc->dxmax) <= tolx_out) break;
+                    }
                 }
+            }
+            // change of the iterate over this pass (the full CCD below leaves it alone)
+            if (!fixed) {
+                umax_d.zero(s);
+                k_maxdiff<<<nb(n), 256, 0, s>>>(n, Ucur, Xprev, umax_d);
+                PDC_LAUNCH_CK();
+            }
+            unsigned int um = 0;
+            if (ran_dev) {  // one read-back for the pass: its iteration count and change
+                ctl.download(&hctl, 1, s);
+                if (!fixed) umax_d.download(&um, 1, s);
+                PDC_CK(cudaStreamSynchronize(s));
+                inner = hctl.inner_iters - inner0;
             }
             if (inner > 0 || o == 0) {
                 full_ccd(Xm, Xp, true);
                 launch_collect_active(s, coll(), bp, Xm, cparams(), act, cap_act, n_act_d, &sc.p->overflow);
             }
             if (!fixed) {
-                umax_d.zero(s);
-                k_maxdiff<<<nb(n), 256, 0, s>>>(n, Ucur, Xprev, umax_d);
-                PDC_LAUNCH_CK();
-                unsigned int um = 0;
-                umax_d.download(&um, 1, s);
-                PDC_CK(cudaStreamSynchronize(s));
+                if (!ran_dev) {
+                    umax_d.download(&um, 1, s);
+                    PDC_CK(cudaStreamSynchronize(s));
+                }
                 PDC_CK(cudaMemcpyAsync(Xprev.p, Ucur.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
                 if (bits_to_float(um) <= tolx_out) break;
             }
@@ -1328,7 +1678,16 @@ void pdc_ctx::step() {
     n_cv_d.download(&ncv, 1, s);
     ttoi.download(&tt, 1, s);
     sfrac.download(&sf, 1, s);
+    if (dev_used) ctl.download(&hctl, 1, s);
     read_scalars();
+    if (dev_used) {  // counters of the loops that ran on the device
+        st.warm_iters += hctl.warm_iters;
+        st.inner_iters += hctl.inner_iters;
+        st.contact_iters += hctl.contact_iters;
+        st.graph_loops = hctl.graph_loops;
+        if (relmode && last_dev) st.rel_residual = hctl.rel;
+        if (!have_rho0) st.rho0 = hctl.rho0;
+    }
     st.n_candidates = counts[0] + counts[1];
     st.n_active = nact;
     st.n_contact_vertices = ncv;
@@ -1463,6 +1822,7 @@ void pdc_default_params(pdc_params *p) {
     p->launch_overlap = 1;
     p->rf_toi = 0.0;
     p->rf_iters = 8;
+    p->graph_loops = 1;
 }
 
 static bool params_valid(const pdc_params *params) {
@@ -1787,6 +2147,7 @@ pdc_status pdc_step(pdc_handle h, double dt) {
             if (ovf & OVF_ACTIVE) {
                 h->cap_act *= 2;
                 h->act.alloc(h->cap_act);
+                ++h->graph_gen;
             }
             h->accel.rho_carry = 0.0;
             if (h->log) std::fprintf(stderr, "[pdc] step retried after overflow 0x%x\n", ovf);

@@ -398,6 +398,7 @@ __global__ void k_pair_scatter(int n, const int2 *__restrict__ list, const int *
 
 void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee_, long long cap_ent_,
                          cudaStream_t s) {
+    ++gen;
     nt = cv.nt;
     ne = cv.ne;
     nv = cv.nv;
@@ -456,6 +457,7 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
 }
 
 void BroadPhase::reserve_pccd(const CollView &cv, cudaStream_t s) {
+    ++gen;
     cap_pairs = cap_vt + cap_ee;
     near.alloc(cap_pairs);
     watch[0].alloc(cap_pairs);
@@ -490,7 +492,7 @@ void BroadPhase::grow_slots(const CollView &cv, bool vt_, bool ee_) {
 }
 
 void BroadPhase::grow(const CollView &cv, long long cvt, long long cee, long long cent, cudaStream_t s) {
-    
+    ++gen;
     if (cent > cap_ent) {
         cap_ent = cent;
         for (int k = 0; k < 2; ++k) {

@@ -468,10 +468,16 @@ __global__ void __launch_bounds__(256) k_aa_gram(int n, const unsigned char *__r
                                                  const float4 *__restrict__ delta, const float4 *__restrict__ xhat,
                                                  float4 *__restrict__ fprev, float4 *__restrict__ gprev,
                                                  float4 *__restrict__ dF, float4 *__restrict__ dG, int slot,
-                                                 int have_prev, int ncol, double *__restrict__ Gb) {
+                                                 int have_prev, int ncol, double *__restrict__ Gb,
+                                                 const LoopCtl *ctl) {
     __shared__ float red[AA_MAX * (AA_MAX + 3) / 2 + AA_MAX][8];
     grid_dep_wait();
     grid_dep_release();
+    if (ctl) {  // bookkeeping taken on the device
+        slot = ctl->aa_slot;
+        have_prev = ctl->aa_prev;
+        ncol = ctl->aa_ncol;
+    }
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float3 col[AA_MAX];
     float3 fk = make_float3(0.f, 0.f, 0.f);
@@ -579,6 +585,90 @@ template <int M> __global__ void k_aa_solve(const double *__restrict__ Gb, float
     grid_dep_wait();
     grid_dep_release();
     if (threadIdx.x == 0 && blockIdx.x == 0) aa_solve<M>(Gb, theta);
+}
+
+// The same solve for a column count ncol <= M read on the device: the
+// ncol x ncol system in the leading block of an M x M one whose other rows
+// and columns are the identity (theta = 0 there).  The leading block's
+// arithmetic is that of aa_solve<ncol> step for step, so theta is the same.
+template <int M> __device__ inline void aa_solve_rt(const double *__restrict__ Gb, float *__restrict__ theta, int ncol) {
+    double A[M][M], b[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        b[j] = 0.0;
+#pragma unroll
+        for (int l = 0; l < M; ++l) A[j][l] = j == l ? 1.0 : 0.0;
+    }
+    int e = 0;
+    double tr = 0.0;
+    for (int j = 0; j < ncol; ++j) {
+        for (int l = j; l < ncol; ++l) A[j][l] = A[l][j] = Gb[e + l - j];
+        e += ncol - j;
+        b[j] = Gb[e++];
+        tr += A[j][j];
+    }
+    for (int j = 0; j < ncol; ++j) A[j][j] += 1e-10 * tr + 1e-300;
+    bool ok = tr > 0.0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        double d = A[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+        ok = ok && d > 0.0;
+        d = sqrt(fmax(d, 1e-300));
+        A[j][j] = d;
+        double inv = 1.0 / d;
+#pragma unroll
+        for (int q = j + 1; q < M; ++q) {
+            double v = A[q][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v -= A[q][k] * A[j][k];
+            A[q][j] = v * inv;
+        }
+    }
+    double y[M], x[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        double v = b[j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) v -= A[j][k] * y[k];
+        y[j] = v / A[j][j];
+    }
+#pragma unroll
+    for (int j = M - 1; j >= 0; --j) {
+        double v = y[j];
+#pragma unroll
+        for (int k = j + 1; k < M; ++k) v -= A[k][j] * x[k];
+        x[j] = v / A[j][j];
+    }
+#pragma unroll
+    for (int j = 0; j < AA_MAX; ++j)
+        theta[j] = (j < ncol && j < M && ok && isfinite(x[j < M ? j : 0])) ? (float)x[j < M ? j : 0] : 0.f;
+}
+
+template <int M> __global__ void k_aa_solve_dev(const double *__restrict__ Gb, float *__restrict__ theta,
+                                                const LoopCtl *ctl) {
+    grid_dep_wait();
+    grid_dep_release();
+    if (threadIdx.x == 0 && blockIdx.x == 0) aa_solve_rt<M>(Gb, theta, min(ctl->aa_ncol, M));
+}
+
+// x_{k+1} = g_k - sum_j theta_j dG_j over the ncol columns of the device state.
+__global__ void __launch_bounds__(256) k_aa_mix_dev(int n, const unsigned char *__restrict__ is_free,
+                                                    const float4 *__restrict__ xhat, const float4 *__restrict__ dG,
+                                                    const float *__restrict__ theta, float4 *__restrict__ xout,
+                                                    const float4 *__restrict__ xs, float4 *__restrict__ xabs,
+                                                    const LoopCtl *ctl, int m) {
+    grid_dep_wait();
+    grid_dep_release();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int ncol = min(ctl->aa_ncol, m);
+    float3 x = f3(xhat[i]);
+    if (is_free[i])
+        for (int j = 0; j < ncol; ++j) x = x - theta[j] * f3(dG[(size_t)j * n + i]);
+    xout[i] = f4(x);
+    if (xabs) xabs[i] = f4(f3(xs[i]) + x);
 }
 
 // x_{k+1} = g_k - sum_j theta_j dG_j on free vertices.
@@ -723,7 +813,7 @@ void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4
     // iteration, so that the gram kernel can follow the last sweep directly
     const int b = nblk(n, 256);
     launch_dependent(overlap, k_aa_gram, b, 256, 0, s, n, is_free, delta, (const float4 *)x, fprev, gprev, dF, dG,
-                     slot, have_prev, ncol, Gb);
+                     slot, have_prev, ncol, Gb, (const LoopCtl *)nullptr);
     if (ncol > 0) {
 #define PDC_AA(M)                                                                                             \
     launch_dependent(overlap, k_aa_solve<M>, 1, 32, 0, s, (const double *)Gb, theta);                          \
@@ -741,6 +831,30 @@ void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4
         }
 #undef PDC_AA
     }
+    PDC_LAUNCH_CK();
+}
+
+void launch_aa_device(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x,
+                      float4 *fprev, float4 *gprev, float4 *dF, float4 *dG, int m, const LoopCtl *ctl, double *Gb,
+                      float *theta, const float4 *xs, float4 *xabs, bool overlap) {
+    if (n <= 0) return;
+    const int b = nblk(n, 256);
+    launch_dependent(overlap, k_aa_gram, b, 256, 0, s, n, is_free, delta, (const float4 *)x, fprev, gprev, dF, dG, 0,
+                     0, 0, Gb, ctl);
+#define PDC_AAD(M) launch_dependent(overlap, k_aa_solve_dev<M>, 1, 32, 0, s, (const double *)Gb, theta, ctl)
+    switch (std::min(std::max(m, 1), AA_MAX)) {
+        case 1: PDC_AAD(1); break;
+        case 2: PDC_AAD(2); break;
+        case 3: PDC_AAD(3); break;
+        case 4: PDC_AAD(4); break;
+        case 5: PDC_AAD(5); break;
+        case 6: PDC_AAD(6); break;
+        case 7: PDC_AAD(7); break;
+        default: PDC_AAD(8); break;
+    }
+#undef PDC_AAD
+    launch_dependent(overlap, k_aa_mix_dev, b, 256, 0, s, n, is_free, (const float4 *)x, (const float4 *)dG,
+                     (const float *)theta, x, xs, xabs, ctl, m);
     PDC_LAUNCH_CK();
 }
 

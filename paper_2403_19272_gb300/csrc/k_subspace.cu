@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(256) k_lift_compact(SubspaceView S, const TU *
 // g[e] = sum over blocks of partial[b][e] (e = 3 j + c): one warp per output,
 // lanes stride over the blocks, shuffle reduction in double.
 __global__ void k_project_reduce(SubspaceView S, const int *n_cv, int nblocks, const float *__restrict__ partial,
-                                 double *__restrict__ g) {
+                                 double *__restrict__ g, int only_with_contacts) {
+    if (only_with_contacts && !(n_cv && *n_cv > 0)) return;  // the tensor-core reduction wrote g
     int r = active_r(S, n_cv);
     int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= r * 3) return;
@@ -521,17 +522,31 @@ template <class F> static void with_basis(const SubspaceView &S, bool compact, F
     else f(compact ? S.Uc32 : S.U32);
 }
 
+bool device_path_choice(const SubspaceView &S) {
+    return S.umma && S.r_nc > 0 && S.r_nc <= S.ld && compact_covers(S);
+}
+
 void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W,
-                    bool maybe_contacts) {
+                    bool maybe_contacts, bool device_choice) {
     if (!maybe_contacts && S.umma && S.r_nc > 0 && S.r_nc <= S.ld) {
         launch_project_umma(s, *S.umma, S.r_nc, rl, S.umma_partial, W.g, S.dev_err, S.overlap != 0);
+        return;
+    }
+    int mx = S.ld * 3 * 32;
+    if (maybe_contacts && device_choice && device_path_choice(S)) {
+        // the iteration's contact-vertex count (device) picks the path: the
+        // full basis on the tensor cores without springs, the compact basis
+        // on the CUDA cores with them; each kernel of the other path returns
+        launch_project_umma(s, *S.umma, S.r_nc, rl, S.umma_partial, W.g, S.dev_err, S.overlap != 0, n_cv);
+        with_basis(S, true, [&](auto *U) { project_compact_t(s, S, U, rl, n_cv, W.partial); });
+        k_project_reduce<<<(mx + 255) / 256, 256, 0, s>>>(S, n_cv, PROJ_BLOCKS, W.partial, W.g, 1);
+        PDC_LAUNCH_CK();
         return;
     }
     with_basis(S, false, [&](auto *U) { project_t(s, S, U, rl, n_cv, W.partial); });
     if (maybe_contacts && compact_covers(S))
         with_basis(S, true, [&](auto *U) { project_compact_t(s, S, U, rl, n_cv, W.partial); });
-    int mx = S.ld * 3 * 32;
-    k_project_reduce<<<(mx + 255) / 256, 256, 0, s>>>(S, n_cv, PROJ_BLOCKS, W.partial, W.g);
+    k_project_reduce<<<(mx + 255) / 256, 256, 0, s>>>(S, n_cv, PROJ_BLOCKS, W.partial, W.g, 0);
     PDC_LAUNCH_CK();
 }
 
@@ -577,9 +592,15 @@ template <class TU> static void lift_t(cudaStream_t s, const SubspaceView &S, co
 }
 
 void launch_lift(cudaStream_t s, const SubspaceView &S, const int *n_cv, const SubspaceWork &W, const float4 *din,
-                 float4 *dout, bool maybe_contacts) {
+                 float4 *dout, bool maybe_contacts, bool device_choice) {
     if (!maybe_contacts && S.umma && S.r_nc > 0 && S.r_nc <= S.ld) {
         launch_lift_umma(s, *S.umma, S.r_nc, W.q, din, dout, S.dev_err, S.overlap != 0);
+        return;
+    }
+    if (maybe_contacts && device_choice && device_path_choice(S)) {  // as in launch_project
+        launch_lift_umma(s, *S.umma, S.r_nc, W.q, din, dout, S.dev_err, S.overlap != 0, n_cv);
+        if (S.n > 0) with_basis(S, true, [&](auto *U) { lift_compact_t(s, S, U, n_cv, W.q, din, dout); });
+        PDC_LAUNCH_CK();
         return;
     }
     if (maybe_contacts && compact_covers(S) && S.n > 0)

@@ -75,6 +75,7 @@ struct BroadPhase {
     DevBuf<float> d0_vt[2], d0_ee[2];  // per pair: closest distance on x^- (partial-CCD prefilter)
     DevBuf<long long> cnt_vt_d[2], cnt_ee_d[2];
     int cur = 0;
+    unsigned gen = 0;          // counts reallocations of the buffers below (captured graphs go stale)
     Profiler *prof = nullptr;  // optional sub-kernel timing
     long long h_pairs = 0;     // host copy of the current list size (kept while profiling)
     // partial-CCD filter: near list, double-buffered watch list, reference

@@ -178,6 +178,27 @@ struct Scalars {
     long long n_hash;      // hash insertions
 };
 
+// ---------------------------------------------------------------- device-side loop control
+// State of the LG loop that is running when its stopping tests are taken on
+// the device (loops run as CUDA graphs): the tests of the host-driven loop
+// (relative residual, stagnation, step change, iteration cap) and the
+// Anderson-mixing bookkeeping, in one struct that one thread updates.
+struct LoopCtl {
+    double rho0;          // PD residual at z (set at the start of the step)
+    double rel;           // last relative residual the stopping test saw
+    double stag_best;     // best residual of the loop (stagnation test)
+    double aa_hist_min;   // smallest residual since the last history restart
+    int aa_hist_n;        // residuals seen since that restart
+    int iters;            // iterations of this loop that ran their solve
+    int go;               // 1 while the loop continues
+    int springs;          // the current iteration has collision springs
+    int stag_count;       // iterations without 1 % progress
+    int aa_count, aa_widx, aa_have_prev;
+    int aa_slot, aa_prev, aa_ncol;  // the mixing step of the current iteration
+    int warm_iters, inner_iters, contact_iters;  // totals of the step
+    int graph_loops;      // loops of the step that ran as one graph launch
+};
+
 // ---------------------------------------------------------------- kernels (k_pd.cu)
 // Inside a step positions are x = x* + u (x* = xs fixed, u a small FP32
 // displacement); zrel = z - x*; xabs receives absolute positions for the
@@ -203,6 +224,11 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
 void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x, float4 *fprev,
                float4 *gprev, float4 *dF, float4 *dG, int slot, int have_prev, int ncol, double *Gb, float *theta,
                const float4 *xs, float4 *xabs, bool overlap);
+// The same step with slot, have_prev and the column count read from the
+// loop state on the device (aa_slot, aa_prev, aa_ncol; at most m columns).
+void launch_aa_device(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x,
+                      float4 *fprev, float4 *gprev, float4 *dF, float4 *dG, int m, const LoopCtl *ctl, double *Gb,
+                      float *theta, const float4 *xs, float4 *xabs, bool overlap);
 void aa_clear(cudaStream_t s, double *Gb);
 void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out);
 void launch_set_pins(cudaStream_t s, const int *pins, int npins, const float4 *tgt, const float4 *xs, float4 *u,

@@ -44,9 +44,15 @@ struct SubspaceWork {
 constexpr int PROJ_BLOCKS = 608;
 
 // g = U[:, :r]^T rl  (r = r_c if *n_cv > 0 else r_nc).  maybe_contacts =
-// false promises *n_cv == 0 (only the full-basis kernel is launched).
+// false promises *n_cv == 0 (only the full-basis kernel is launched).  With
+// device_choice (and device_path_choice(S)) an iteration that may have
+// springs launches both the tensor-core full-basis kernels and the compact
+// ones, and *n_cv (read on the device) decides which of them work, so that
+// the host need not read the count back.
 void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W,
-                    bool maybe_contacts = true);
+                    bool maybe_contacts = true, bool device_choice = false);
+// whether the tensor-core / compact choice of a spring iteration can be left to the device
+bool device_path_choice(const SubspaceView &S);
 // dA = sum over listed vertices of cw_v U_v U_v^T (leading r_c columns).
 void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const int *n_cv, const float *cw,
                  SubspaceWork &W);
@@ -54,7 +60,7 @@ void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const i
 void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv, SubspaceWork &W);
 // dout = din + U q (din may be NULL: zero).
 void launch_lift(cudaStream_t s, const SubspaceView &S, const int *n_cv, const SubspaceWork &W, const float4 *din,
-                 float4 *dout, bool maybe_contacts = true);
+                 float4 *dout, bool maybe_contacts = true, bool device_choice = false);
 // rl = r - (H + diag(cw)) delta (linear residual of the global system).
 void launch_linear_residual(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r,
                             const float4 *delta, float4 *rl);

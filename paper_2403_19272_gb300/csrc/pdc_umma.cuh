@@ -31,10 +31,12 @@ int umma_project_blocks(int n);
 // g = U[:, :r]^T rl via per-tile partial sums [blocks][ld][3] and an FP64 reduction.
 // With overlap, the kernels are launched as programmatic dependents of the
 // kernel before them (barrier setup and TMEM allocation overlap its tail).
+// skip_if (device, may be NULL): the kernels do nothing when *skip_if > 0
+// (an iteration whose collision springs use the compact basis instead).
 void launch_project_umma(cudaStream_t s, const UmmaMaps &M, int r, const float4 *rl, float *partial, double *g,
-                         int *err, bool overlap = false);
+                         int *err, bool overlap = false, const int *skip_if = nullptr);
 // dout = din + U[:, :r] q (din may be NULL).
 void launch_lift_umma(cudaStream_t s, const UmmaMaps &M, int r, const float *q, const float4 *din, float4 *dout,
-                      int *err, bool overlap = false);
+                      int *err, bool overlap = false, const int *skip_if = nullptr);
 
 }  // namespace pdc

@@ -153,3 +153,63 @@ def test_reported_relative_residual_is_the_oracles(pc, precision):
     finally:
         cl.close()
     assert checked >= 5
+
+
+def _run(pc, sc, p, steps):
+    cl = pc.Cloth(sc, p)
+    xs, sts = [], []
+    try:
+        for _ in range(steps):
+            cl.step()
+            xs.append(cl.positions())
+            sts.append(cl.stats())
+    finally:
+        cl.close()
+    return xs, sts
+
+
+def test_graph_loops_take_the_host_loops_steps_in_parity_mode(pc):
+    """Fixed iteration counts with contacts (both candidate-list buffers,
+    the partial CCD and the NDB counters inside the graph's while body): the
+    device-driven loops give the host-driven loops' positions up to the order
+    of float atomics.  (In this mode the host-driven loop reads no count back
+    and counts every iteration of a contact loop as one with springs; the
+    device counts those that have contact vertices.)"""
+    sc = thrown_drape(24)
+    kw = dict(fixed_iters=1, warm_iters=2, max_outer=2, max_inner=4, solve_cycles=20, jacobi_sweeps=8, r_warm=128,
+              r_reuse=32, precision=2, d_hat=1e-3)
+    xg, sg = _run(pc, sc, params(pc, graph_loops=1, **kw), 5)
+    xh, sh = _run(pc, sc, params(pc, graph_loops=0, **kw), 5)
+    L = float(np.linalg.norm(sc.verts.max(0) - sc.verts.min(0)))
+    assert all(s["graph_loops"] >= 3 for s in sg), [s["graph_loops"] for s in sg]
+    assert all(s["graph_loops"] == 0 for s in sh)
+    assert max(s["n_active"] for s in sg) > 0
+    for k in range(5):
+        for key in ("warm_iters", "inner_iters", "outer_iters", "n_active", "n_contact_vertices"):
+            assert sg[k][key] == sh[k][key], (k, key, sg[k][key], sh[k][key])
+        assert sg[k]["contact_iters"] <= sh[k]["contact_iters"] == sh[k]["inner_iters"], k
+        assert np.max(np.abs(xg[k] - xh[k])) <= 1e-6 * L, k
+
+
+@pytest.mark.parametrize("precision", [2, 0])
+def test_graph_loops_take_the_host_loops_steps_in_production_mode(pc, precision):
+    """The benchmark's settings (relative residual 1e-3, stagnation stop,
+    Anderson mixing) on the 64 x 64 swept cloth: the stopping tests taken on
+    the device end the loops where the host's do (iteration counts equal,
+    except where float-atomic noise moves a residual across a threshold) and
+    the steps agree to 1e-5 of the bounding-box diagonal."""
+    import bench
+    sc = wl.hanging_swept(side=64)
+    pg = bench.solver_params(pc, precision)
+    ph = bench.solver_params(pc, precision)
+    ph.graph_loops = 0
+    xg, sg = _run(pc, sc, pg, 8)
+    xh, sh = _run(pc, sc, ph, 8)
+    L = float(np.linalg.norm(sc.verts.max(0) - sc.verts.min(0)))
+    assert all(s["graph_loops"] >= 2 for s in sg) and all(s["graph_loops"] == 0 for s in sh)
+    same = sum(sg[k]["warm_iters"] + sg[k]["inner_iters"] == sh[k]["warm_iters"] + sh[k]["inner_iters"]
+               for k in range(8))
+    assert same >= 7, [(a["inner_iters"], b["inner_iters"]) for a, b in zip(sg, sh)]
+    for k in range(8):
+        assert abs(sg[k]["rel_residual"] - sh[k]["rel_residual"]) <= 0.05 * sh[k]["rel_residual"] + 1e-9, k
+        assert np.max(np.abs(xg[k] - xh[k])) <= 1e-5 * L, k
