@@ -159,6 +159,16 @@ typedef struct {
                                 reads each iteration's residual back and
                                 decides.  Same kernels in the same order either
                                 way.                                              */
+    int32_t pccd_adaptive;   /* 1: the partial CCD tests, instead of the fixed
+                                samples_vt / samples_ee patterns, the t = 0
+                                closest point and a lattice of spacing 1/m over
+                                the pair's parameters, m = ceil(1 / (sqrt(2)
+                                rho*)) from the bound rho* of Eq. (sample_bound)
+                                (Sec. 4.1; with alpha_ls as alpha): every pair
+                                colliding before alpha of the step is flagged
+                                unless m was capped.  0 (default): fixed
+                                patterns                                          */
+    int32_t pccd_max_axis;   /* cap on m (1..256, default 64)                    */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */

@@ -528,6 +528,9 @@ struct pdc_ctx {
         C.a_max = P.a_max;
         C.samples_vt = P.samples_vt;
         C.samples_ee = P.samples_ee;
+        C.adaptive = P.pccd_adaptive;
+        C.max_axis = P.pccd_max_axis;
+        C.alpha = P.alpha_ls;
         return C;
     }
 
@@ -1823,6 +1826,8 @@ void pdc_default_params(pdc_params *p) {
     p->rf_toi = 0.0;
     p->rf_iters = 8;
     p->graph_loops = 1;
+    p->pccd_adaptive = 0;
+    p->pccd_max_axis = 64;
 }
 
 static bool params_valid(const pdc_params *params) {
@@ -1832,7 +1837,9 @@ static bool params_valid(const pdc_params *params) {
            (params->samples_vt == 0 || params->samples_vt == 1 || params->samples_vt == 3) &&
            (params->samples_ee == 0 || params->samples_ee == 1 || params->samples_ee == 4) &&
            params->sweep_kind >= 0 && params->sweep_kind <= 1 && (params->sweep_kind != 1 || params->cheb_ratio > 1.0) &&
-           params->accel >= 0 && params->accel <= 2 && (params->accel != 2 || (params->aa_depth >= 1 && params->aa_depth <= 8));
+           params->accel >= 0 && params->accel <= 2 && (params->accel != 2 || (params->aa_depth >= 1 && params->aa_depth <= 8)) &&
+           (params->pccd_adaptive == 0 || (params->pccd_adaptive == 1 && params->pccd_max_axis >= 1 &&
+                                           params->pccd_max_axis <= 256 && params->alpha_ls > 0 && params->alpha_ls < 1));
 }
 
 static bool mesh_valid(const pdc_mesh_desc *mesh) {

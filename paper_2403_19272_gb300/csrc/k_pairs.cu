@@ -277,6 +277,89 @@ __device__ bool partial_pair(int kind, const float4 a0[4], const float4 a1[4], f
     return false;
 }
 
+// Partial CCD with the sample density of Eq. (sample_bound) (Sec. 4.1): for
+// a pair that collides before alpha of the step, Q < 0 on the disc of radius
+//   rho* = (1/alpha - 1) (H^0)^2 / (2 sqrt(2) L (H^1 + 2L))
+// around the contact parameters (H^0: closest distance at t = 0; H^1: the
+// largest distance between a point of one primitive and one of the other at
+// t = 0 or 1, which bounds their distance over the step; L: the longest edge
+// of either primitive at t = 0 or 1).  A square lattice of spacing 1/m with
+// 1/m <= sqrt(2) rho* puts a sample inside that disc: m = ceil(1 / (sqrt(2)
+// rho*)), at least 1, capped at max_axis (H^0 = 0: max_axis).  The bound and
+// m are taken in FP64 (so that the lattice is the same as an FP64 reference
+// computes from these positions); the samples, the t = 0 closest point and
+// the lattice {(i/m, j/m)} (VT: i + j <= m, barycentric weights of the
+// triangle's second and third vertex; EE: the two edge parameters), are
+// tested in FP32 as the fixed patterns are.
+__device__ int adaptive_axis(int kind, const float4 a0[4], const float4 a1[4], double alpha, int max_axis) {
+    V<double> p[4], e[4];
+    for (int i = 0; i < 4; ++i) { p[i] = ld<double>(a0[i]); e[i] = ld<double>(a1[i]); }
+    const double h0 = gap_dist<double>(kind, p);
+    double h1 = 0.0, L = 0.0;
+    const int n1 = kind == 0 ? 1 : 2;
+    for (int t = 0; t < 2; ++t) {
+        const V<double> *q = t == 0 ? p : e;
+        for (int i = 0; i < n1; ++i)
+            for (int j = n1; j < 4; ++j) { V<double> d = q[j] - q[i]; h1 = fmax(h1, sqrt(dotv(d, d))); }
+        if (kind == 0) {
+            const int ed[3][2] = {{1, 2}, {2, 3}, {3, 1}};
+            for (int k = 0; k < 3; ++k) { V<double> d = q[ed[k][1]] - q[ed[k][0]]; L = fmax(L, sqrt(dotv(d, d))); }
+        } else {
+            V<double> d = q[1] - q[0];
+            L = fmax(L, sqrt(dotv(d, d)));
+            d = q[3] - q[2];
+            L = fmax(L, sqrt(dotv(d, d)));
+        }
+    }
+    if (!(L > 0.0)) return 1;  // rho* infinite
+    const double rho = (1.0 / alpha - 1.0) * h0 * h0 / (2.0 * sqrt(2.0) * L * (h1 + 2.0 * L));
+    if (!(rho > 0.0)) return max_axis;
+    const double need = 1.0 / (sqrt(2.0) * rho);
+    if (!(need < (double)max_axis)) return max_axis;
+    return max(1, (int)ceil(need));
+}
+
+__device__ bool partial_pair_adaptive(int kind, const float4 a0[4], const float4 a1[4], float dhat, double alpha,
+                                      int max_axis, float c[4]) {
+    V<float> p[4], e[4];
+    for (int i = 0; i < 4; ++i) { p[i] = ld<float>(a0[i]); e[i] = ld<float>(a1[i]); }
+    closest_coef<float>(kind, p, c);
+    auto test = [&](float l1, float l2) {
+        V<float> p10, p20, p11, p21;
+        if (kind == 0) {
+            p10 = p[0]; p11 = e[0];
+            p20 = p[1] + (l1 * (p[2] - p[1]) + l2 * (p[3] - p[1]));
+            p21 = e[1] + (l1 * (e[2] - e[1]) + l2 * (e[3] - e[1]));
+        } else {
+            p10 = p[0] + l1 * (p[1] - p[0]); p11 = e[0] + l1 * (e[1] - e[0]);
+            p20 = p[2] + l2 * (p[3] - p[2]); p21 = e[2] + l2 * (e[3] - e[2]);
+        }
+        V<float> d0 = p20 - p10, d1 = p21 - p11;
+        return dotv(d1, d0) - dhat * sqrtf(dotv(d0, d0)) <= 0.f;
+    };
+    // the t = 0 closest point first (FP64 coefficients, as the bound's)
+    {
+        V<double> q[4];
+        for (int i = 0; i < 4; ++i) q[i] = ld<double>(a0[i]);
+        double cd[4];
+        closest_coef<double>(kind, q, cd);
+        if (kind == 0 ? test((float)cd[2], (float)cd[3]) : test((float)-cd[1], (float)cd[3])) return true;
+    }
+    const int m = adaptive_axis(kind, a0, a1, alpha, max_axis);
+    const float inv = 1.f / (float)m;
+    for (int i = 0; i <= m; ++i) {
+        const int jm = kind == 0 ? m - i : m;
+        for (int j = 0; j <= jm; ++j)
+            if (test((float)i * inv, (float)j * inv)) return true;
+    }
+    return false;
+}
+
+__device__ inline bool partial_test(int kind, const float4 a0[4], const float4 a1[4], const CollParams &P, float c[4]) {
+    if (P.adaptive) return partial_pair_adaptive(kind, a0, a1, P.dhat, P.alpha, P.max_axis, c);
+    return partial_pair(kind, a0, a1, P.dhat, kind == 0 ? P.samples_vt : P.samples_ee, c);
+}
+
 // Unit start direction of the gap vector; falls back to the triangle normal
 // (VT) or the edge cross product (EE) when the gap vanishes.
 __device__ float3 start_dir(int kind, const float4 a0[4], const float c[4]) {
@@ -598,7 +681,7 @@ __global__ void __launch_bounds__(256) k_pccd_test(CollView cv, const int2 *__re
                 a1[i] = xp[ids[i]];
             }
             float c[4];
-            bool flag = partial_pair(kind, a0, a1, P.dhat, kind == 0 ? P.samples_vt : P.samples_ee, c);
+            bool flag = partial_test(kind, a0, a1, P, c);
             if (flag) {
                 int a = (st & ST_ACTIVE) ? min((int)(st & 0x7f) + 1, P.a_max) : 0;
                 st = ST_ACTIVE | (unsigned char)a;
@@ -693,7 +776,7 @@ __global__ void k_partial_quads(const int4 *q, const int *kinds, long long np, c
         for (int k = 0; k < 4; ++k) { a0[k] = x0[ids[k]]; a1[k] = x1[ids[k]]; }
         float c[4];
         int kind = kinds[i];
-        active[i] = partial_pair(kind, a0, a1, P.dhat, kind == 0 ? P.samples_vt : P.samples_ee, c) ? 1 : 0;
+        active[i] = partial_test(kind, a0, a1, P, c) ? 1 : 0;
     }
 }
 

@@ -23,6 +23,9 @@ struct CollParams {
     int a_max;        // cap of the life-span counter
     int samples_vt;   // 0, 1, 3
     int samples_ee;   // 0, 1, 4
+    int adaptive;     // 1: sample lattice per pair from the bound of Eq. (sample_bound)
+    int max_axis;     // cap on that lattice's samples per parameter axis
+    double alpha;     // line-search factor alpha of the bound
 };
 
 // An active collision constraint: 4 collision-vertex ids, the gap-vector

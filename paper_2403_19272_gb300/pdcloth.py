@@ -42,7 +42,8 @@ class pdc_params(ctypes.Structure):
                 ("seed", c_u64), ("accel", c_i32), ("accel_rho", c_dbl), ("sweep_kind", c_i32),
                 ("cheb_ratio", c_dbl), ("aa_depth", c_i32),
                 ("tensor_cores", c_i32), ("bp_reuse", c_dbl), ("launch_overlap", c_i32),
-                ("rf_toi", c_dbl), ("rf_iters", c_i32), ("graph_loops", c_i32)]
+                ("rf_toi", c_dbl), ("rf_iters", c_i32), ("graph_loops", c_i32), ("pccd_adaptive", c_i32),
+                ("pccd_max_axis", c_i32)]
 
 
 class pdc_stats(ctypes.Structure):
