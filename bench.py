@@ -251,11 +251,25 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
                 launches=launches)
 
 
+def solver_like(pc, p):
+    """A copy of a pdc_params structure."""
+    q = pc.pdc_default_params()
+    for name, _ in p._fields_:
+        v = getattr(p, name)
+        if name == "gravity":
+            for i in range(3):
+                q.gravity[i] = v[i]
+        else:
+            setattr(q, name, v)
+    return q
+
+
 def run_batched(pc, torch, steps=5, warmup=2, dev_index=0):
     """Batched form (64 drapes of sides 16..192 over their own spheres, about
     0.9 M vertices, FP32, 32 LG iterations per step): one batched handle
     against the same 64 cloths stepped one after another on 64 handles.
-    Instances are placed 2 m apart so that none touches another."""
+    Instances are placed 2 m apart so that none touches another; each takes
+    its own line-search fraction on the batched handle."""
     import numpy as np
     import workloads as wl
     scenes = wl.batched_drape()
@@ -270,12 +284,15 @@ def run_batched(pc, torch, steps=5, warmup=2, dev_index=0):
         shifted.append(((sc.verts + d).astype(np.float32), sc.tris, sc.pins, sc.density, sc.k_stretch, sc.k_bend,
                         obs, [o.tris for o in sc.obstacles]))
     stream = torch.cuda.Stream()
-    # one batched handle
+    # one batched handle, every instance with its own line-search fraction
+    # (its sphere attached to it)
     t0 = time.time()
-    h, off = pc.pdc_create_batch([s[:6] for s in shifted], p, stream.cuda_stream)
-    for s in shifted:
+    pb = solver_like(pc, p)
+    pb.instance_line_search = 1
+    h, off = pc.pdc_create_batch([s[:6] for s in shifted], pb, stream.cuda_stream)
+    for k, s in enumerate(shifted):
         for ov, ot in zip(s[6], s[7]):
-            pc.pdc_add_obstacle(h, ov, ot)
+            pc.pdc_set_obstacle_instance(h, pc.pdc_add_obstacle(h, ov, ot), k)
     setup_b = time.time() - t0
     for _ in range(warmup):
         pc.pdc_step(h, p.dt)

@@ -169,6 +169,21 @@ typedef struct {
                                 unless m was capped.  0 (default): fixed
                                 patterns                                          */
     int32_t pccd_max_axis;   /* cap on m (1..256, default 64)                    */
+    int32_t instance_line_search; /* batched form: 1 gives every instance its own
+                                step fraction s_k = alpha * t_k (1 without an
+                                impact), t_k the smallest time of impact of the
+                                pairs with a vertex in instance k (a pair that
+                                spans two instances counts for both); its
+                                attached obstacles (pdc_set_obstacle_instance)
+                                move with it.  Needs every obstacle attached,
+                                else the union's single fraction is used.  0
+                                (default): one fraction for the union          */
+    int32_t autotune;        /* 1: the first step picks the launch shapes of the
+                                hot kernels by timing every candidate on the
+                                handle's own data (CUDA events; see
+                                pdc_tuning); results do not depend on the
+                                choice beyond the order of float atomics.  0
+                                (default): fixed shapes                          */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
@@ -194,6 +209,22 @@ typedef struct {
     int32_t graph_loops;         /* LG loops of this step that ran as one graph
                                     launch (graph_loops parameter)               */
 } pdc_stats;
+
+/* Launch shapes in use and, after an autotuned first step, the measured
+ * time (ms) of every candidate. */
+typedef struct {
+    int32_t tuned;           /* 1 once the first step has tuned (autotune = 1)   */
+    int32_t residual_block;  /* threads per block of the element-force and
+                                residual kernels (candidates 64, 128, 256)      */
+    int32_t cheb_tile;       /* 1: Chebyshev steps read the TMA-staged matrix
+                                tiles; 0: the ELL arrays (candidates 1, 0)      */
+    int32_t pair_blocks;     /* blocks of the per-pair kernels (152 x 2, 4, 8, 16) */
+    int32_t vt_lanes;        /* lanes per vertex of the VT broad-phase query (4, 8, 16) */
+    float residual_ms[3];
+    float cheb_ms[2];
+    float pair_ms[4];
+    float vt_ms[3];
+} pdc_tuning;
 
 /* Defaults: dt 1/200, g = (0,0,-9.8), K = 2, a_max 20, alpha 0.8, automatic
  * d_hat, eta 1e-9, tolerances 1e-3 / 5e-2, 4 outer x 32 inner, 5 warm
@@ -231,6 +262,13 @@ pdc_status pdc_create_batch(int32_t count, const pdc_mesh_desc *meshes, const pd
  * positions start at verts. */
 pdc_status pdc_add_obstacle(pdc_handle h, const float *verts, int32_t nv, const int32_t *tris, int32_t nt,
                             int32_t *out_id);
+
+/* Batched form: attach obstacle id to instance (0..count-1; -1 detaches):
+ * with instance_line_search its motion within a step is scaled by that
+ * instance's step fraction, so that every pair between the instance's cloth
+ * and the obstacle stays on the linear motion its CCD checked.
+ * PDC_ERR_ARG for a bad id or instance or a handle that is not batched. */
+pdc_status pdc_set_obstacle_instance(pdc_handle h, int32_t id, int32_t instance);
 
 /* Target position of obstacle id at the end of the next step: m4x4 (row
  * major, host) applied to the obstacle's verts as given at pdc_add_obstacle.
@@ -276,6 +314,9 @@ pdc_status pdc_get_displacement(pdc_handle h, float *u, int32_t on_device);
 
 /* Statistics of the last step. */
 pdc_status pdc_get_stats(pdc_handle h, pdc_stats *out);
+
+/* Launch shapes (autotune) of the handle. */
+pdc_status pdc_get_tuning(pdc_handle h, pdc_tuning *out);
 
 /* Copy bandwidth (GB/s, read plus written bytes) of a working set of
  * `bytes`, half of it read and half written per pass, measured by one

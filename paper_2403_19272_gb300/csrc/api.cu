@@ -48,16 +48,28 @@ __global__ void k_step_fraction(const unsigned long long *toi_bits, double alpha
     *t_out = t;
     *s_out = (t <= 1.0) ? alpha * t : 1.0;
 }
+// the same per instance (per-instance line search)
+__global__ void k_instance_fractions(int count, const unsigned long long *toi_bits, double alpha, double *s_out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    double t = __longlong_as_double((long long)toi_bits[k]);
+    s_out[k] = (t <= 1.0) ? alpha * t : 1.0;
+}
+__global__ void k_fill_u64(unsigned long long *p, int count, unsigned long long v) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) p[k] = v;
+}
 // final state (exit line search of Alg. 1): cloth u = um + s (up - um) (or up),
 // x = x* + u, v = u / h, and u itself in ulast; obstacle vertices lerp
-// between their absolute x^- and x^+.
+// between their absolute x^- and x^+.  s: the union's fraction, or with
+// vinst the fraction of the vertex's instance.
 __global__ void k_finish(int nv, int n, const float4 *__restrict__ um, const float4 *__restrict__ up,
                          const float4 *__restrict__ xm, const float4 *__restrict__ xp, const double *s_frac,
                          int use_lerp, float inv_h, float4 *__restrict__ xs, float4 *__restrict__ vs,
-                         float4 *__restrict__ ulast) {
+                         float4 *__restrict__ ulast, const int *__restrict__ vinst, const double *__restrict__ s_inst) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
-    float s = use_lerp ? (float)*s_frac : 1.f;
+    float s = use_lerp ? (float)((vinst && vinst[i] >= 0) ? s_inst[vinst[i]] : *s_frac) : 1.f;
     if (i < n) {
         float3 d = f3(up[i]);
         if (use_lerp) {
@@ -383,6 +395,24 @@ struct pdc_ctx {
     DevBuf<int2> cedge;
     DevBuf<unsigned char> vfixed;
     DevBuf<unsigned int> guard_d;  // index-guard word of this handle's pair kernels
+    // batched form: first vertex of each instance (count + 1 entries), the
+    // instance each obstacle is attached to (-1: none), and for the
+    // per-instance line search the instance of every collision vertex and
+    // each instance's time of impact and step fraction
+    std::vector<int> inst_off;
+    std::vector<int> obs_inst;
+    DevBuf<int> vinst;
+    DevBuf<unsigned long long> toi_inst;
+    DevBuf<double> sfrac_inst;
+    int ninst() const { return inst_off.empty() ? 1 : (int)inst_off.size() - 1; }
+    // one step fraction per instance: asked for, batched, every obstacle attached
+    bool per_instance() const {
+        if (!P.instance_line_search || ninst() < 2) return false;
+        for (int k : obs_inst)
+            if (k < 0) return false;
+        return vinst.p != nullptr;
+    }
+    void upload_vinst();
     BroadPhase bp;
     DevBuf<ActivePair> act;
     int cap_act = 0;
@@ -473,6 +503,8 @@ struct pdc_ctx {
         c.ell_tile = ell_tile.p;
         c.ell_tw = ell_tw;
         c.corner = corner;
+        c.res_block = tune.residual_block;
+        c.cheb_plain = tune.cheb_tile ? 0 : 1;
         return c;
     }
     CollView coll() const {
@@ -485,6 +517,9 @@ struct pdc_ctx {
         v.edge = cedge;
         v.vfixed = vfixed;
         v.guard = guard_d;
+        const bool pi = per_instance();
+        v.vinst = pi ? vinst.p : nullptr;
+        v.toi_inst = pi ? toi_inst.p : nullptr;
         return v;
     }
     SubspaceView sub(int r_nc, int r_c) const {
@@ -570,6 +605,8 @@ struct pdc_ctx {
     bool graph_overlap = true;   // programmatic dependent launches inside the graphs
     DevBuf<LoopCtl> ctl;
     LoopCtl hctl;
+    pdc_tuning tune = {0, 256, 1, 152 * 8, 8, {0, 0, 0}, {0, 0}, {0, 0, 0, 0}, {0, 0, 0}};
+    void autotune_vertex_kernels();
     bool device_loops_ok() const;
     void free_graph(GraphLoop &G);
     LoopCfg loop_cfg(int kind, int max_iters, bool relmode, bool contacts) const;
@@ -1094,8 +1131,77 @@ void pdc_ctx::ensure_topology() {
     cap_act = (int)std::max<long long>(1024, 4LL * nv_all);
     disp.alloc(nv_all);
     act.alloc(cap_act);
+    obs_inst.resize(obs.size(), -1);
+    upload_vinst();
     PDC_CK(cudaStreamSynchronize(s));
     topo_dirty = false;
+}
+
+void pdc_ctx::upload_vinst() {
+    if (ninst() < 2) return;
+    std::vector<int> vi(std::max(nv_all, 1), -1);
+    for (int k = 0; k < ninst(); ++k)
+        for (int v = inst_off[k]; v < inst_off[k + 1]; ++v) vi[v] = k;
+    for (size_t j = 0; j < obs.size(); ++j) {
+        const int nvo = (int)obs[j].V.size() / 3;
+        for (int v = 0; v < nvo; ++v) vi[obs[j].off + v] = obs_inst[j];
+    }
+    vinst.upload(vi, s);
+    toi_inst.alloc(ninst());
+    sfrac_inst.alloc(ninst());
+    PDC_CK(cudaStreamSynchronize(s));
+}
+
+// ============================================================================ autotuning
+// Launch shapes of the hot kernels picked at the first step (autotune = 1):
+// each candidate runs on this handle's own data and its time is taken with
+// CUDA events; the fastest is kept.  Every candidate computes the same
+// values (up to the order of float atomics), so the choice changes speed
+// only.  Here: the block size of the element-force and residual kernels and
+// the Chebyshev step's matrix source; the pair kernels' grid and the VT
+// query's lanes per vertex are tuned at the first full CCD / broad phase.
+void pdc_ctx::autotune_vertex_kernels() {
+    cudaEvent_t e0, e1;
+    PDC_CK(cudaEventCreate(&e0));
+    PDC_CK(cudaEventCreate(&e1));
+    auto timed = [&](auto &&f) {
+        f();  // warm-up
+        PDC_CK(cudaEventRecord(e0, s));
+        for (int k = 0; k < 3; ++k) f();
+        PDC_CK(cudaEventRecord(e1, s));
+        PDC_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PDC_CK(cudaEventElapsedTime(&ms, e0, e1));
+        return ms / 3.f;
+    };
+    const int bsz[3] = {64, 128, 256};
+    int best = 2;
+    for (int k = 0; k < 3; ++k) {
+        tune.residual_block = bsz[k];
+        ClothView c = cloth();
+        tune.residual_ms[k] = timed([&] { launch_residual(s, c, Xs, Ucur, Z, nullptr, nullptr, R, nullptr, nullptr, 0); });
+        if (tune.residual_ms[k] < tune.residual_ms[best]) best = k;
+    }
+    tune.residual_block = bsz[best];
+    if (P.sweep_kind == 1 && ell_tile.p) {
+        // one Chebyshev step from delta = 0 on the residual just formed (scratch outputs)
+        PDC_CK(cudaMemsetAsync(D0.p, 0, sizeof(float4) * n, s));
+        double b = std::max(gersh, 1.0) * 1.02, a = b / std::max(P.cheb_ratio, 1.0001);
+        const float beta = (float)(2.0 / (b + a));
+        for (int k = 0; k < 2; ++k) {
+            tune.cheb_tile = k == 0 ? 1 : 0;
+            ClothView c = cloth();
+            tune.cheb_ms[k] = timed([&] {
+                launch_cheb_step(s, c, nullptr, R, D0, CD0, D1, 0.f, beta, nullptr, nullptr, nullptr, nullptr, 1.f, Xs,
+                                 nullptr, false, sflag.p);
+            });
+        }
+        tune.cheb_tile = tune.cheb_ms[0] <= tune.cheb_ms[1] ? 1 : 0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bp.tune_pairs = bp.tune_query = P.collisions != 0;
+    ++graph_gen;  // graphs capture launch shapes
 }
 
 // ============================================================================ the step (Alg. 1)
@@ -1447,11 +1553,16 @@ void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {
     }
     unsigned long long inf = 0x7ff0000000000000ULL;  // +inf
     PDC_CK(cudaMemcpyAsync(toi_bits.p, &inf, sizeof(inf), cudaMemcpyHostToDevice, s));
+    if (per_instance()) {
+        k_fill_u64<<<(ninst() + 255) / 256, 256, 0, s>>>(toi_inst, ninst(), inf);
+        PDC_LAUNCH_CK();
+    }
     // algorithmic bytes: both position sets once, per pair its key and state
     // (plus the previous list's key and state read by the merge)
     PROF("full_ccd", 32.0 * nv_all + (merge ? 18.0 : 9.0) * (double)bp.h_pairs,
          launch_full_ccd(s, coll(), bp, x0, x1, cparams(), merge, toi_bits));
     k_step_fraction<<<1, 1, 0, s>>>(toi_bits, P.alpha_ls, sfrac, ttoi);
+    if (per_instance()) k_instance_fractions<<<(ninst() + 255) / 256, 256, 0, s>>>(ninst(), toi_inst, P.alpha_ls, sfrac_inst);
     PDC_LAUNCH_CK();
 }
 
@@ -1503,6 +1614,11 @@ void pdc_ctx::step() {
     launch_prologue(s, n, Xs, Vs, pins_d, pin_tgt, npins, h, g, Z, Ucur, Xp, rf_pending ? RFd.p : nullptr);
     if (nv_all > n)
         PDC_CK(cudaMemcpyAsync(Xp.p + n, obs_tgt.p, sizeof(float4) * (nv_all - n), cudaMemcpyDeviceToDevice, s));
+    if (P.autotune && !tune.tuned) {
+        autotune_vertex_kernels();
+        tune.tuned = 1;
+        c = cloth();
+    }
     // rho0 = residual at z (no collision springs)
     PDC_CK(cudaMemsetAsync(&sc.p->rsq, 0, sizeof(double), s));
     launch_residual(s, c, Xs, Ucur, Z, nullptr, nullptr, R, sc, nullptr, 0);
@@ -1581,8 +1697,9 @@ void pdc_ctx::step() {
             PDC_CK(cudaStreamSynchronize(s));
             std::fprintf(stderr, "[pdc] initial full CCD: t_toi=%.6g s=%.6g\n", t0v, s0v);
         }
-        launch_lerp(s, nv_all, Xs, Xp, sfrac, Xm);                // obstacles (and cloth, overwritten next)
-        launch_scale_disp(s, n, Xs, Ucur, sfrac, Um, Xm);         // cloth x^- = x* + s u
+        const int *vi = per_instance() ? vinst.p : nullptr;      // per-instance fractions
+        launch_lerp(s, nv_all, Xs, Xp, sfrac, Xm, vi, sfrac_inst);        // obstacles (and cloth, overwritten next)
+        launch_scale_disp(s, n, Xs, Ucur, sfrac, Um, Xm, vi, sfrac_inst); // cloth x^- = x* + s u
         // the iterate restarts at x^- with pins at their targets
         launch_restart(s, n, Xs, Um, Ucur, Xp);
         launch_set_pins(s, pins_d, npins, pin_tgt, Xs, Ucur, Xp);
@@ -1591,6 +1708,10 @@ void pdc_ctx::step() {
         unsigned long long none = 0x4000000000000000ULL;  // 2.0: no impact yet
         PDC_CK(cudaMemcpyAsync(toi_bits.p, &none, sizeof(none), cudaMemcpyHostToDevice, s));
         k_step_fraction<<<1, 1, 0, s>>>(toi_bits, P.alpha_ls, sfrac, ttoi);
+        if (vi) {
+            k_fill_u64<<<(ninst() + 255) / 256, 256, 0, s>>>(toi_inst, ninst(), none);
+            k_instance_fractions<<<(ninst() + 255) / 256, 256, 0, s>>>(ninst(), toi_inst, P.alpha_ls, sfrac_inst);
+        }
         PDC_LAUNCH_CK();
         for (int o = 0; o < P.max_outer; ++o) {
             st.outer_iters++;
@@ -1652,7 +1773,8 @@ void pdc_ctx::step() {
         }
     }
     // exit line search and velocities (Alg. 1; v = (x - x*)/h)
-    k_finish<<<nb(nv_all), 256, 0, s>>>(nv_all, n, Um, Ucur, Xm, Xp, sfrac, use_lerp ? 1 : 0, 1.f / h, Xs, Vs, Ulast);
+    k_finish<<<nb(nv_all), 256, 0, s>>>(nv_all, n, Um, Ucur, Xm, Xp, sfrac, use_lerp ? 1 : 0, 1.f / h, Xs, Vs, Ulast,
+                                        per_instance() ? vinst.p : nullptr, sfrac_inst.p);
     PDC_LAUNCH_CK();
     bad_d.zero(s);
     k_finite<<<nb(n), 256, 0, s>>>(n, Xs, bad_d);
@@ -1828,6 +1950,8 @@ void pdc_default_params(pdc_params *p) {
     p->graph_loops = 1;
     p->pccd_adaptive = 0;
     p->pccd_max_axis = 64;
+    p->instance_line_search = 0;
+    p->autotune = 0;
 }
 
 static bool params_valid(const pdc_params *params) {
@@ -1934,6 +2058,14 @@ pdc_status pdc_create_batch(int32_t count, const pdc_mesh_desc *meshes, const pd
         nv += m.nv;
     }
     c->M = materials[0];
+    c->inst_off.push_back(0);
+    {
+        long long acc = 0;
+        for (int k = 0; k < count; ++k) {
+            acc += meshes[k].nv;
+            c->inst_off.push_back((int)acc);
+        }
+    }
     pdc_mesh_desc u;
     u.verts = V.data();
     u.nv = (int32_t)nv;
@@ -2015,6 +2147,17 @@ pdc_status pdc_add_obstacle(pdc_handle h, const float *verts, int32_t nv, const 
     h->obs_tgt.release();
     h->ensure_topology();
     if (out_id) *out_id = id;
+    API_END(h)
+}
+
+pdc_status pdc_set_obstacle_instance(pdc_handle h, int32_t id, int32_t instance) {
+    API_BEGIN(h)
+    if (id < 0 || id >= (int)h->obs.size()) throw Error(PDC_ERR_ARG, "pdc_set_obstacle_instance: bad obstacle id");
+    if (instance < -1 || instance >= h->ninst() || h->ninst() < 2)
+        throw Error(PDC_ERR_ARG, "pdc_set_obstacle_instance: instance out of range (or not a batched handle)");
+    h->ensure_topology();
+    h->obs_inst[id] = instance;
+    h->upload_vinst();
     API_END(h)
 }
 
@@ -2177,6 +2320,17 @@ pdc_status pdc_get_kernel_times(pdc_handle h, pdc_kernel_time *out, int32_t cap,
     if (count) *count = k;
     if (out)
         for (int i = 0; i < std::min(k, (int)cap); ++i) out[i] = h->prof.acc[i];
+    API_END(h)
+}
+
+pdc_status pdc_get_tuning(pdc_handle h, pdc_tuning *out) {
+    API_BEGIN(h)
+    if (!out) throw Error(PDC_ERR_ARG, "pdc_get_tuning: NULL");
+    *out = h->tune;
+    out->pair_blocks = h->bp.pair_blocks;
+    out->vt_lanes = h->bp.qg_vt;
+    for (int k = 0; k < 4; ++k) out->pair_ms[k] = h->bp.pair_ms[k];
+    for (int k = 0; k < 3; ++k) out->vt_ms[k] = h->bp.query_ms[k];
     API_END(h)
 }
 

@@ -176,12 +176,12 @@ __global__ void k_hash_insert(int np, const float4 *__restrict__ blo, const floa
 // Queries.  Each primary collects its candidates, sorted by secondary id,
 // in a fixed-width row of a slot buffer; the count is always exact, and a
 // primary with more candidates than the row width flags OVF_SLOTS (the pass
-// is then rerun with wider rows).  In the VT query QG_VT lanes share one
+// is then rerun with wider rows).  In the VT query QG lanes share one
 // vertex and stride over the entries of each bucket of its cell range
 // together (the lanes of a group run the same trip count), append through a
 // group ballot and sort the row once at the end.
 constexpr int QUERY_T = 128;
-constexpr int QG_VT = 8;  // lanes per vertex in the VT query
+// lanes per vertex in the VT query: 4, 8 (default) or 16 (BroadPhase::qg_vt)
 
 __device__ inline void slot_insert(int *row, int width, int c, int q) {
     if (c >= width) return;
@@ -571,10 +571,40 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
     // ---- VT candidates
     if (prof) prof->begin(s, "bp_query_vt", 0.0);
     if (cv.nv) {
-        k_query_vt<QG_VT><<<nblk((long long)cv.nv * QG_VT, QUERY_T), QUERY_T, 0, s>>>(
-            cv, x0, x1, tlo, thi, gp, dhat, (unsigned)(T_vt - 1), bcnt[0], bstart[0], ekey[0], eprim[0], cnt_v,
-            slots_vt, w_vt, tot + 0, cap_ent, overflow);
-        PDC_LAUNCH_CK();
+        auto query = [&](int qg) {
+#define PDC_QVT(Q)                                                                                                   \
+    k_query_vt<Q><<<nblk((long long)cv.nv * Q, QUERY_T), QUERY_T, 0, s>>>(cv, x0, x1, tlo, thi, gp, dhat,             \
+                                                                          (unsigned)(T_vt - 1), bcnt[0], bstart[0],  \
+                                                                          ekey[0], eprim[0], cnt_v, slots_vt, w_vt,  \
+                                                                          tot + 0, cap_ent, overflow)
+            if (qg == 4) PDC_QVT(4);
+            else if (qg == 16) PDC_QVT(16);
+            else PDC_QVT(8);
+#undef PDC_QVT
+            PDC_LAUNCH_CK();
+        };
+        if (tune_query) {
+            // each candidate writes the same counts and rows: time each, keep the fastest
+            tune_query = false;
+            const int cand[3] = {4, 8, 16};
+            cudaEvent_t e[4];
+            for (auto &ev : e) PDC_CK(cudaEventCreate(&ev));
+            query(8);  // warm-up
+            PDC_CK(cudaEventRecord(e[0], s));
+            for (int k = 0; k < 3; ++k) {
+                query(cand[k]);
+                PDC_CK(cudaEventRecord(e[k + 1], s));
+            }
+            PDC_CK(cudaEventSynchronize(e[3]));
+            int best = 1;
+            for (int k = 0; k < 3; ++k) {
+                PDC_CK(cudaEventElapsedTime(&query_ms[k], e[k], e[k + 1]));
+                if (query_ms[k] < query_ms[best]) best = k;
+            }
+            for (auto &ev : e) cudaEventDestroy(ev);
+            qg_vt = cand[best];
+        }
+        query(qg_vt);
     }
     exclusive_scan(s, cnt_v, off_v, cv.nv, scratch, tot + 2);
     k_check_cap<<<1, 1, 0, s>>>(tot + 2, cap_vt, OVF_VT, overflow, out_nvt);

@@ -444,7 +444,6 @@ __device__ inline long long find_pair(const int2 *list, long long n, int2 key) {
     return -1;
 }
 
-constexpr int PAIR_BLOCKS = 152 * 8;
 constexpr int PAIR_THREADS = 256;
 
 __global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const int2 *__restrict__ vt,
@@ -480,7 +479,13 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const in
         double t = ccd_pair(kind, a0, a1, eta);
         if (t <= 1.0) {
             st |= ST_ACTIVE;
-            atomicMin(toi_min, (unsigned long long)__double_as_longlong(t));
+            const unsigned long long tb = (unsigned long long)__double_as_longlong(t);
+            atomicMin(toi_min, tb);
+            if (cv.toi_inst)  // every instance the pair touches
+                for (int j = 0; j < 4; ++j) {
+                    const int k = cv.vinst[ids[j]];
+                    if (k >= 0) atomicMin(&cv.toi_inst[k], tb);
+                }
         }
         if (kind == 0) st_vt[idx] = st; else st_ee[idx - nvt] = st;
     }
@@ -824,17 +829,43 @@ unsigned int pair_guard_take(cudaStream_t s, unsigned int *guard) {
 void launch_full_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *x0, const float4 *x1,
                      const CollParams &P, bool merge, unsigned long long *toi_min) {
     int c = bp.cur, o = c ^ 1;
-    k_full_ccd<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(
-        cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c], bp.st_vt[c], bp.st_ee[c], merge ? bp.vt[o].p : nullptr,
-        merge ? bp.ee[o].p : nullptr, bp.cnt_vt_d[o], bp.cnt_ee_d[o], bp.st_vt[o], bp.st_ee[o], x0, x1, P.eta, toi_min);
-    PDC_LAUNCH_CK();
+    auto launch = [&](int blocks) {
+        k_full_ccd<<<blocks, PAIR_THREADS, 0, s>>>(
+            cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c], bp.st_vt[c], bp.st_ee[c],
+            merge ? bp.vt[o].p : nullptr, merge ? bp.ee[o].p : nullptr, bp.cnt_vt_d[o], bp.cnt_ee_d[o], bp.st_vt[o],
+            bp.st_ee[o], x0, x1, P.eta, toi_min);
+        PDC_LAUNCH_CK();
+    };
+    if (bp.tune_pairs) {
+        // every candidate computes the same states and minimum (the kernel is
+        // idempotent): time each on this list and keep the fastest grid
+        bp.tune_pairs = false;
+        const int cand[4] = {152 * 2, 152 * 4, 152 * 8, 152 * 16};
+        cudaEvent_t e[5];
+        for (auto &ev : e) PDC_CK(cudaEventCreate(&ev));
+        launch(cand[2]);  // warm-up
+        PDC_CK(cudaEventRecord(e[0], s));
+        for (int k = 0; k < 4; ++k) {
+            launch(cand[k]);
+            PDC_CK(cudaEventRecord(e[k + 1], s));
+        }
+        PDC_CK(cudaEventSynchronize(e[4]));
+        int best = 2;
+        for (int k = 0; k < 4; ++k) {
+            PDC_CK(cudaEventElapsedTime(&bp.pair_ms[k], e[k], e[k + 1]));
+            if (bp.pair_ms[k] < bp.pair_ms[best]) best = k;
+        }
+        for (auto &ev : e) cudaEventDestroy(ev);
+        bp.pair_blocks = cand[best];
+    }
+    launch(bp.pair_blocks);
 }
 
 void launch_collect_active(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *xm,
                            const CollParams &P, ActivePair *act, int cap_act, int *n_act, int *overflow) {
     int c = bp.cur;
     PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
-    k_pairs_collect<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
+    k_pairs_collect<<<bp.pair_blocks, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
                                                          bp.st_vt[c], bp.st_ee[c], bp.d0_vt[c], bp.d0_ee[c], xm, P,
                                                          act, cap_act, n_act, overflow);
     PDC_LAUNCH_CK();
@@ -853,14 +884,14 @@ void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, cons
     if (bp.prof) bp.prof->end(s);
     // (full or watch-list pass is decided on the device: no byte model here)
     if (bp.prof) bp.prof->begin(s, "pccd_filter", 0.0);
-    k_pccd_filter<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
+    k_pccd_filter<<<bp.pair_blocks, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c],
                                                        bp.st_vt[c], bp.st_ee[c], bp.d0_vt[c], bp.d0_ee[c], disp,
                                                        P.dhat, tau, bp.pccd, bp.watch[0], bp.watch[1], bp.near,
                                                        bp.cap_pairs);
     PDC_LAUNCH_CK();
     if (bp.prof) bp.prof->end(s);
     if (bp.prof) bp.prof->begin(s, "pccd_test", 0.0);
-    k_pccd_test<<<PAIR_BLOCKS, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c], bp.st_vt[c],
+    k_pccd_test<<<bp.pair_blocks, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c], bp.st_vt[c],
                                                      bp.st_ee[c], xm, xp, P, bp.near, bp.pccd, bp.cap_pairs, act,
                                                      cap_act, n_act, overflow);
     PDC_LAUNCH_CK();

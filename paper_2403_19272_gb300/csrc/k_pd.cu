@@ -142,12 +142,14 @@ __global__ void k_restart(int n, const float4 *__restrict__ xs, const float4 *__
     xabs[i] = f4(f3(xs[i]) + f3(d));
 }
 
-// um = s u (cloth part of the filtered x^-), xm = x* + um
+// um = s u (cloth part of the filtered x^-), xm = x* + um; s is the vertex's
+// instance's fraction when vinst is given (per-instance line search)
 __global__ void k_scale_disp(int n, const float4 *__restrict__ xs, const float4 *__restrict__ u, const double *s_frac,
-                             float4 *__restrict__ um, float4 *__restrict__ xm) {
+                             float4 *__restrict__ um, float4 *__restrict__ xm, const int *__restrict__ vinst,
+                             const double *__restrict__ s_inst) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float s = (float)*s_frac;
+    float s = (float)((vinst && vinst[i] >= 0) ? s_inst[vinst[i]] : *s_frac);
     float3 d = s * f3(u[i]);
     um[i] = f4(d);
     xm[i] = f4(f3(xs[i]) + d);
@@ -690,10 +692,10 @@ __global__ void __launch_bounds__(256) k_aa_mix(int n, const unsigned char *__re
 }
 
 __global__ void k_lerp(int nv, const float4 *__restrict__ a, const float4 *__restrict__ b, const double *s_frac,
-                       float4 *__restrict__ out) {
+                       float4 *__restrict__ out, const int *__restrict__ vinst, const double *__restrict__ s_inst) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
-    float s = (float)(*s_frac);
+    float s = (float)((vinst && vinst[i] >= 0) ? s_inst[vinst[i]] : *s_frac);
     float3 p = f3(a[i]), q = f3(b[i]);
     out[i] = f4(p + s * (q - p));
 }
@@ -731,18 +733,19 @@ void launch_restart(cudaStream_t s, int n, const float4 *xs, const float4 *um, f
 }
 
 void launch_scale_disp(cudaStream_t s, int n, const float4 *xs, const float4 *u, const double *s_frac, float4 *um,
-                       float4 *xm) {
-    if (n > 0) k_scale_disp<<<nblk(n, 256), 256, 0, s>>>(n, xs, u, s_frac, um, xm);
+                       float4 *xm, const int *vinst, const double *s_inst) {
+    if (n > 0) k_scale_disp<<<nblk(n, 256), 256, 0, s>>>(n, xs, u, s_frac, um, xm, vinst, s_inst);
     PDC_LAUNCH_CK();
 }
 
 void launch_residual(cudaStream_t s, const ClothView &c, const float4 *xs, const float4 *u, const float4 *zrel,
                      const float *cw, const float4 *cf, float4 *r, Scalars *sc, float *r_soa, int soa_ld) {
     float4 *ct = c.corner, *ch = c.corner + 3 * (size_t)c.m;
-    const int tb = nblk(c.m, 256), hb = nblk(c.nh, 256);
-    if (tb + hb > 0) launch_dependent(c.overlap != 0, k_elem_corner, tb + hb, 256, 0, s, c, tb, xs, u, ct, ch);
+    const int bs = (c.res_block == 64 || c.res_block == 128) ? c.res_block : 256;
+    const int tb = nblk(c.m, bs), hb = nblk(c.nh, bs);
+    if (tb + hb > 0) launch_dependent(c.overlap != 0, k_elem_corner, tb + hb, bs, 0, s, c, tb, xs, u, ct, ch);
     if (c.n > 0)
-        launch_dependent(c.overlap != 0, k_residual, nblk(c.n, 256), 256, 0, s, c, u, zrel, cw, cf, ct, ch, r, sc,
+        launch_dependent(c.overlap != 0, k_residual, nblk(c.n, bs), bs, 0, s, c, u, zrel, cw, cf, ct, ch, r, sc,
                          r_soa, soa_ld);
     PDC_LAUNCH_CK();
 }
@@ -766,7 +769,7 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
                       const float4 *dprev, float4 *dout, float alpha, float beta, const float4 *x,
                       float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs,
                       bool overlap, int *err) {
-    if (c.n > 0 && c.ell_tile && err) {
+    if (c.n > 0 && c.ell_tile && err && !c.cheb_plain) {
         int b = nblk(c.n, ELL_TILE_ROWS);
         // shared-memory carveout for 8 resident blocks (the register limit)
         static unsigned long long carve[3] = {0, 0, 0};  // per-device bits
@@ -862,8 +865,9 @@ void aa_clear(cudaStream_t s, double *Gb) {
     PDC_CK(cudaMemsetAsync(Gb, 0, sizeof(double) * (AA_MAX * (AA_MAX + 3) / 2 + AA_MAX), s));
 }
 
-void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out) {
-    if (nv > 0) k_lerp<<<nblk(nv, 256), 256, 0, s>>>(nv, a, b, s_frac, out);
+void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out,
+                 const int *vinst, const double *s_inst) {
+    if (nv > 0) k_lerp<<<nblk(nv, 256), 256, 0, s>>>(nv, a, b, s_frac, out, vinst, s_inst);
     PDC_LAUNCH_CK();
 }
 

@@ -79,6 +79,13 @@ struct BroadPhase {
     DevBuf<long long> cnt_vt_d[2], cnt_ee_d[2];
     int cur = 0;
     unsigned gen = 0;          // counts reallocations of the buffers below (captured graphs go stale)
+    // launch shapes (autotuned at the first step when asked): blocks of the
+    // pair kernels and lanes per vertex of the VT query; with tune_* set, the
+    // next launch times every candidate on its own data and keeps the fastest
+    int pair_blocks = 152 * 8;
+    int qg_vt = 8;
+    bool tune_pairs = false, tune_query = false;
+    float pair_ms[4] = {0, 0, 0, 0}, query_ms[3] = {0, 0, 0};
     Profiler *prof = nullptr;  // optional sub-kernel timing
     long long h_pairs = 0;     // host copy of the current list size (kept while profiling)
     // partial-CCD filter: near list, double-buffered watch list, reference

@@ -145,6 +145,8 @@ struct ClothView {
     const unsigned char *ell_tile;
     int ell_tw;            // tile width: 8, 12 or 16 (>= ell_w)
     float4 *corner;        // scratch [3m + 4nh]: per-element corner forces of the residual
+    int res_block;         // threads per block of the residual kernels (64, 128 or 256)
+    int cheb_plain;        // 1: Chebyshev steps read the ELL arrays directly, not the tiles
 };
 
 constexpr int ELL_TILE_ROWS = 256;
@@ -162,6 +164,11 @@ struct CollView {
     const int2 *edge;      // [ne] (a < b)
     const unsigned char *vfixed; // [nv] 1: infinite mass (obstacle or pinned)
     unsigned int *guard;   // the handle's index-guard word (GuardBits), or NULL
+    // per-instance line search (batched form): instance of each collision
+    // vertex (-1: none) and per-instance minimum time of impact (double bits);
+    // NULL when the union takes one step fraction
+    const int *vinst;
+    unsigned long long *toi_inst;
 };
 
 // Scalars written by reductions (device).
@@ -230,11 +237,14 @@ void launch_aa_device(cudaStream_t s, int n, const unsigned char *is_free, const
                       float4 *fprev, float4 *gprev, float4 *dF, float4 *dG, int m, const LoopCtl *ctl, double *Gb,
                       float *theta, const float4 *xs, float4 *xabs, bool overlap);
 void aa_clear(cudaStream_t s, double *Gb);
-void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out);
+// out = a + s (b - a) with s = *s_frac, or with vinst (per-instance line
+// search) s_inst[vinst[i]] for vertices of an instance (vinst[i] >= 0)
+void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out,
+                 const int *vinst = nullptr, const double *s_inst = nullptr);
 void launch_set_pins(cudaStream_t s, const int *pins, int npins, const float4 *tgt, const float4 *xs, float4 *u,
                      float4 *xabs);
 void launch_restart(cudaStream_t s, int n, const float4 *xs, const float4 *um, float4 *u, float4 *xabs);
 void launch_scale_disp(cudaStream_t s, int n, const float4 *xs, const float4 *u, const double *s_frac, float4 *um,
-                       float4 *xm);
+                       float4 *xm, const int *vinst = nullptr, const double *s_inst = nullptr);
 
 }  // namespace pdc

@@ -43,7 +43,7 @@ class pdc_params(ctypes.Structure):
                 ("cheb_ratio", c_dbl), ("aa_depth", c_i32),
                 ("tensor_cores", c_i32), ("bp_reuse", c_dbl), ("launch_overlap", c_i32),
                 ("rf_toi", c_dbl), ("rf_iters", c_i32), ("graph_loops", c_i32), ("pccd_adaptive", c_i32),
-                ("pccd_max_axis", c_i32)]
+                ("pccd_max_axis", c_i32), ("instance_line_search", c_i32), ("autotune", c_i32)]
 
 
 class pdc_stats(ctypes.Structure):
@@ -57,6 +57,15 @@ class pdc_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pdc_tuning(ctypes.Structure):
+    _fields_ = [("tuned", c_i32), ("residual_block", c_i32), ("cheb_tile", c_i32), ("pair_blocks", c_i32),
+                ("vt_lanes", c_i32), ("residual_ms", c_flt * 3), ("cheb_ms", c_flt * 2), ("pair_ms", c_flt * 4),
+                ("vt_ms", c_flt * 3)]
+
+    def as_dict(self):
+        return {k: (list(getattr(self, k)) if k.endswith("_ms") else getattr(self, k)) for k, _ in self._fields_}
+
+
 class pdc_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", c_i64), ("total_ms", c_dbl), ("algo_bytes", c_dbl)]
 
@@ -68,6 +77,7 @@ SIGNATURES = {
     "pdc_create_batch": (c_i32, [c_i32, P, P, P, P, P]),
     "pdc_add_obstacle": (c_i32, [P, P, c_i32, P, c_i32, P]),
     "pdc_set_obstacle_transform": (c_i32, [P, c_i32, P]),
+    "pdc_set_obstacle_instance": (c_i32, [P, c_i32, c_i32]),
     "pdc_set_pin_targets": (c_i32, [P, P, c_i32]),
     "pdc_set_state": (c_i32, [P, P, P, c_i32]),
     "pdc_get_state": (c_i32, [P, P, P, c_i32]),
@@ -77,6 +87,7 @@ SIGNATURES = {
     "pdc_get_positions": (c_i32, [P, P, c_i32]),
     "pdc_get_displacement": (c_i32, [P, P, c_i32]),
     "pdc_get_stats": (c_i32, [P, P]),
+    "pdc_get_tuning": (c_i32, [P, P]),
     "pdc_destroy": (None, [P]),
     "pdc_measure_copy_bandwidth": (c_i32, [c_i64, c_i32, P, P]),
     "pdc_last_error": (ctypes.c_char_p, [P]),
@@ -197,6 +208,10 @@ def pdc_add_obstacle(h, verts, tris) -> int:
     return oid.value
 
 
+def pdc_set_obstacle_instance(h, oid, instance):
+    _check(h, lib().pdc_set_obstacle_instance(h, int(oid), int(instance)))
+
+
 def pdc_set_obstacle_transform(h, oid, m4x4):
     m = _f32(m4x4, (16,))
     _check(h, lib().pdc_set_obstacle_transform(h, int(oid), _ptr(m)))
@@ -264,6 +279,12 @@ def pdc_get_stats(h) -> dict:
     s = pdc_stats()
     _check(h, lib().pdc_get_stats(h, ctypes.byref(s)))
     return s.as_dict()
+
+
+def pdc_get_tuning(h) -> dict:
+    t = pdc_tuning()
+    _check(h, lib().pdc_get_tuning(h, ctypes.byref(t)))
+    return t.as_dict()
 
 
 def pdc_set_profiling(h, enable: bool):

@@ -127,3 +127,101 @@ def test_batch_rejects_bad_instances(pc):
     bad = (sc.verts, sc.tris + 100, sc.pins, sc.density, sc.k_stretch, sc.k_bend)
     with pytest.raises(pc.PdcError):
         pc.pdc_create_batch([(sc.verts, sc.tris, sc.pins, sc.density, sc.k_stretch, sc.k_bend), bad], p)
+
+
+def _thrown(sc, vz):
+    v0 = sc.v0.copy()
+    v0[:, 2] += vz
+    return dataclasses.replace(sc, v0=v0.astype(np.float32))
+
+
+def test_batch_with_instance_line_search_matches_each_instance_alone(pc):
+    """instance_line_search = 1: each instance takes its own step fraction
+    alpha * t_k from the pairs that touch it (its sphere attached to it), so
+    the batch equals every instance stepped by itself; here one drape is
+    thrown fast at its sphere and meets it within the test, the other falls
+    slowly, and each is compared with its own FP64 oracle (the oracle's
+    NDB base weight k set to the union's).  With one fraction for the union
+    the slow drape's steps would be cut short by the fast drape's impacts."""
+    scenes = [_shift(_thrown(wl.drape_sphere(side=12, sphere_subdiv=2), -20.0), 0.0),
+              _shift(_thrown(wl.drape_sphere(side=14, sphere_subdiv=2, seed=77), -0.5), 2.5)]
+    p = _params(pc, collisions=True)
+    p.instance_line_search = 1
+    b = _Batch(pc, scenes, p)
+    for j in range(len(scenes)):
+        pc.pdc_set_obstacle_instance(b.h, j, j)
+    pu = _params(pc, collisions=True)  # the same batch with one fraction for the union
+    bu = _Batch(pc, scenes, pu)
+    # the union's k = mean of diag H over all free vertices
+    models = [pd.Model(s.verts, s.tris, s.pins, s.density, s.k_stretch, s.k_bend, p.dt) for s in scenes]
+    dg = np.concatenate([m.diagH[m.free] for m in models])
+    orcs = [pd.Oracle(s, pd.Params(fixed_iters=True, warm_iters=2, max_outer=1, max_inner=3, dhat=1e-3,
+                                   collisions=True, k_ndb_scale=float(dg.mean() / m.diagH[m.free].mean())))
+            for s, m in zip(scenes, models)]
+    impacts = 0
+    cut_short = 0.0
+    for k in range(5):
+        b.step()
+        bu.step()
+        xg, vg = b.state()
+        xu, vu = bu.state()
+        impacts += b.pc.pdc_get_stats(b.h)["t_toi"] <= 1.0
+        for i, (o, s) in enumerate(zip(orcs, scenes)):
+            xo, vo, _ = o.step()
+            part = slice(b.off[i], b.off[i + 1])
+            assert np.max(np.abs(xg[part] - xo)) <= 1e-5 * o.model.L, (k, i)
+            o.x, o.v = xg[part].astype(np.float64), vg[part].astype(np.float64)
+        cut_short = max(cut_short, float(np.max(np.abs(xu[b.off[1]:] - xg[b.off[1]:]))))
+        pc.pdc_set_state(bu.h, xg, vg)
+    assert impacts > 0
+    assert cut_short > 1e-4  # the union's single fraction would have moved the slow drape less
+    b.close()
+    bu.close()
+
+
+def test_instance_line_search_attachment_is_checked(pc):
+    scenes = [_shift(wl.drape_sphere(side=8, sphere_subdiv=1), 0.0), _shift(wl.drape_sphere(side=8, sphere_subdiv=1), 2.0)]
+    p = _params(pc, collisions=True)
+    p.instance_line_search = 1
+    b = _Batch(pc, scenes, p)
+    with pytest.raises(pc.PdcError):
+        pc.pdc_set_obstacle_instance(b.h, 0, 2)
+    with pytest.raises(pc.PdcError):
+        pc.pdc_set_obstacle_instance(b.h, 5, 0)
+    pc.pdc_set_obstacle_instance(b.h, 0, 0)
+    b.step()  # one obstacle unattached: the union's fraction, still a valid step
+    b.close()
+    sc = wl.drape_sphere(side=8, sphere_subdiv=1)
+    cl = pc.Cloth(sc, _params(pc, collisions=True))
+    with pytest.raises(pc.PdcError):
+        pc.pdc_set_obstacle_instance(cl.h, 0, 0)  # not a batched handle
+    cl.close()
+
+
+def test_autotuned_batch_takes_the_same_steps(pc):
+    """autotune = 1: the first step times every candidate launch shape on the
+    batch's own data and keeps the fastest of each; the steps are those of
+    the fixed shapes (up to the order of float atomics)."""
+    scenes = [_shift(_thrown(wl.drape_sphere(side=12, sphere_subdiv=2), -15.0), 0.0),
+              _shift(wl.drape_sphere(side=20, sphere_subdiv=2, seed=5), 2.5)]
+    pt = _params(pc, collisions=True)
+    pt.autotune = 1
+    bt = _Batch(pc, scenes, pt)
+    bf = _Batch(pc, scenes, _params(pc, collisions=True))
+    L = max(float(np.linalg.norm(s.verts.max(0) - s.verts.min(0))) for s in scenes)
+    for k in range(4):
+        bt.step()
+        bf.step()
+        xt, _ = bt.state()
+        xf, _ = bf.state()
+        assert np.max(np.abs(xt - xf)) <= 1e-6 * L, k
+    t = pc.pdc_get_tuning(bt.h)
+    assert t["tuned"] == 1
+    assert t["residual_block"] in (64, 128, 256) and t["cheb_tile"] in (0, 1)
+    assert t["pair_blocks"] in (152 * 2, 152 * 4, 152 * 8, 152 * 16) and t["vt_lanes"] in (4, 8, 16)
+    assert all(v > 0 for v in t["residual_ms"] + t["pair_ms"] + t["vt_ms"])
+    assert t["residual_ms"][(64, 128, 256).index(t["residual_block"])] == min(t["residual_ms"])
+    assert t["vt_ms"][(4, 8, 16).index(t["vt_lanes"])] == min(t["vt_ms"])
+    assert pc.pdc_get_tuning(bf.h)["tuned"] == 0
+    bt.close()
+    bf.close()

@@ -55,6 +55,9 @@ def test_struct_layouts_match_header(libpath):
     # dependent launches on, residual forwarding off (8 iterations when enabled)
     assert p.launch_overlap == 1 and p.rf_toi == 0.0 and p.rf_iters == 8
     assert p.tensor_cores == 1 and p.bp_reuse == 0.0
+    # LG loops as graphs; fixed partial-CCD patterns, one line-search fraction, no autotuning
+    assert p.graph_loops == 1 and p.pccd_adaptive == 0 and p.pccd_max_axis == 64
+    assert p.instance_line_search == 0 and p.autotune == 0
 
 
 def test_binding_structs_have_the_header_layout(tmp_path):
@@ -63,7 +66,7 @@ def test_binding_structs_have_the_header_layout(tmp_path):
     import ctypes
     from paper_2403_19272_gb300 import pdcloth
     structs = [pdcloth.pdc_mesh_desc, pdcloth.pdc_material, pdcloth.pdc_params, pdcloth.pdc_stats,
-               pdcloth.pdc_kernel_time]
+               pdcloth.pdc_kernel_time, pdcloth.pdc_tuning]
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pdcloth.h"', "int main(void) {"]
     for S in structs:
         t = S.__name__
