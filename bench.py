@@ -289,6 +289,7 @@ def run_batched(pc, torch, steps=5, warmup=2, dev_index=0):
     t0 = time.time()
     pb = solver_like(pc, p)
     pb.instance_line_search = 1
+    pb.autotune = 1  # launch shapes timed on the batch's own data at the first step
     h, off = pc.pdc_create_batch([s[:6] for s in shifted], pb, stream.cuda_stream)
     for k, s in enumerate(shifted):
         for ov, ot in zip(s[6], s[7]):
@@ -304,6 +305,8 @@ def run_batched(pc, torch, steps=5, warmup=2, dev_index=0):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_b = e0.elapsed_time(e1) / steps
+    tuning = pc.pdc_get_tuning(h)
+    gl = pc.pdc_get_stats(h)["graph_loops"]
     pc.pdc_destroy(h)
     # the same cloths on separate handles, stepped in turn on one stream
     t0 = time.time()
@@ -332,7 +335,8 @@ def run_batched(pc, torch, steps=5, warmup=2, dev_index=0):
             "instances": len(shifted), "vertices": int(off[-1]), "steps": steps,
             "ms_per_step_batched": round(ms_b, 3), "ms_per_step_separate_handles": round(ms_s, 3),
             "speedup": round(ms_s / ms_b, 2), "setup_s_batched": round(setup_b, 1),
-            "setup_s_separate": round(setup_s, 1)}
+            "setup_s_separate": round(setup_s, 1), "graph_loops_per_step": gl,
+            "line_search": "per instance", "tuning": tuning}
 
 
 def count_launches(torch, one_step, steps):

@@ -482,13 +482,39 @@ int64_t oc_broadphase_ee_one(const float *X0, const float *X1, const int32_t *e2
 
 static double orient(v3 a, v3 b, v3 c, v3 d) { return det3(sub(b, a), sub(c, a), sub(d, a)); }
 
-/* does segment pq cross triangle abc (proper or touching)? */
+/* does segment pq cross triangle abc (proper or touching)?  An endpoint
+ * whose orientation is below 1e-12 of the triple product of the lengths
+ * involved lies in the triangle's plane up to rounding; a segment with both
+ * endpoints there lies in the plane (coplanar: not counted), whatever
+ * signs rounding gave the two tiny orientations. */
 static int seg_tri(v3 p, v3 q, v3 a, v3 b, v3 c) {
     double sp = orient(a, b, c, p), sq = orient(a, b, c, q);
+    const double lab = nrm(sub(b, a)), lac = nrm(sub(c, a));
+    const double tp = 1e-12 * lab * lac * nrm(sub(p, a)), tq = 1e-12 * lab * lac * nrm(sub(q, a));
+    if (fabs(sp) <= tp) sp = 0.0;
+    if (fabs(sq) <= tq) sq = 0.0;
     if ((sp > 0 && sq > 0) || (sp < 0 && sq < 0)) return 0;
     if (sp == 0 && sq == 0) return 0; /* coplanar: not counted as crossing */
     double s1 = orient(p, q, a, b), s2 = orient(p, q, b, c), s3 = orient(p, q, c, a);
     return ((s1 >= 0 && s2 >= 0 && s3 >= 0) || (s1 <= 0 && s2 <= 0 && s3 <= 0));
+}
+
+/* exact test of one pair (boxes already overlap or not checked) */
+static int tri_pair_hits(const double *X, const int32_t *A, const int32_t *B) {
+    int shared = 0, sa = -1, sb = -1;
+    for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y)
+            if (A[x] == B[y]) { shared++; sa = x; sb = y; }
+    if (shared >= 2) return 0;
+    v3 a[3] = {ld(X + 3 * A[0]), ld(X + 3 * A[1]), ld(X + 3 * A[2])};
+    v3 b[3] = {ld(X + 3 * B[0]), ld(X + 3 * B[1]), ld(X + 3 * B[2])};
+    int hit = 0;
+    for (int e = 0; e < 3 && !hit; ++e) {
+        int e0 = e, e1 = (e + 1) % 3;
+        if (!(shared == 1 && (e0 == sa || e1 == sa))) hit |= seg_tri(a[e0], a[e1], b[0], b[1], b[2]);
+        if (!(shared == 1 && (e0 == sb || e1 == sb))) hit |= seg_tri(b[e0], b[e1], a[0], a[1], a[2]);
+    }
+    return hit;
 }
 
 int64_t oc_count_tri_tri(const double *X, const int32_t *tris, int32_t nt, int64_t cap, int32_t *out) {
@@ -503,11 +529,6 @@ int64_t oc_count_tri_tri(const double *X, const int32_t *tris, int32_t nt, int64
         }
         for (int j = i + 1; j < nt; ++j) {
             const int32_t *B = tris + 3 * j;
-            int shared = 0, sa = -1, sb = -1;
-            for (int x = 0; x < 3; ++x)
-                for (int y = 0; y < 3; ++y)
-                    if (A[x] == B[y]) { shared++; sa = x; sb = y; }
-            if (shared >= 2) continue;
             v3 b[3] = {ld(X + 3 * B[0]), ld(X + 3 * B[1]), ld(X + 3 * B[2])};
             int skip = 0;
             for (int d = 0; d < 3 && !skip; ++d) {
@@ -515,17 +536,93 @@ int64_t oc_count_tri_tri(const double *X, const int32_t *tris, int32_t nt, int64
                 if (fmax(u, fmax(v, w)) < lo[d] || fmin(u, fmin(v, w)) > hi[d]) skip = 1;
             }
             if (skip) continue;
-            int hit = 0;
-            for (int e = 0; e < 3 && !hit; ++e) {
-                int e0 = e, e1 = (e + 1) % 3;
-                if (!(shared == 1 && (e0 == sa || e1 == sa))) hit |= seg_tri(a[e0], a[e1], b[0], b[1], b[2]);
-                if (!(shared == 1 && (e0 == sb || e1 == sb))) hit |= seg_tri(b[e0], b[e1], a[0], a[1], a[2]);
-            }
-            if (hit) {
+            if (tri_pair_hits(X, A, B)) {
                 if (n < cap) { out[2 * n] = i; out[2 * n + 1] = j; }
                 ++n;
             }
         }
     }
+    return n;
+}
+
+/* The same list of intersecting pairs, culled by a uniform grid instead of
+ * the all-pairs sweep: every triangle is entered in each cell its box
+ * touches (cell side `cell`), entries are sorted by cell, and a pair is
+ * tested (with the same exact test) only in the lowest cell its two boxes
+ * share, so each pair is seen once.  Pairs come out sorted (i < j, by i then
+ * j).  Returns the count (-1 when an allocation fails or a box spans more
+ * than 2^21 cells per axis). */
+typedef struct { int64_t key; int32_t tri; } oc_ent;
+static int oc_ent_cmp(const void *p, const void *q) {
+    const oc_ent *a = (const oc_ent *)p, *b = (const oc_ent *)q;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->tri - b->tri;
+}
+static int oc_pair_cmp(const void *p, const void *q) {
+    const int32_t *a = (const int32_t *)p, *b = (const int32_t *)q;
+    if (a[0] != b[0]) return a[0] < b[0] ? -1 : 1;
+    return a[1] < b[1] ? -1 : (a[1] > b[1]);
+}
+
+int64_t oc_count_tri_tri_grid(const double *X, const int32_t *tris, int32_t nt, double cell, int64_t cap,
+                              int32_t *out) {
+    if (nt <= 1) return 0;
+    const double inv = 1.0 / cell;
+    int64_t *clo = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)nt);
+    int64_t *chi = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)nt);
+    if (!clo || !chi) { free(clo); free(chi); return -1; }
+    int64_t total = 0;
+    for (int i = 0; i < nt; ++i) {
+        const int32_t *A = tris + 3 * i;
+        int64_t cnt = 1;
+        for (int d = 0; d < 3; ++d) {
+            double u = X[3 * A[0] + d], v = X[3 * A[1] + d], w = X[3 * A[2] + d];
+            clo[3 * i + d] = (int64_t)floor(fmin(u, fmin(v, w)) * inv);
+            chi[3 * i + d] = (int64_t)floor(fmax(u, fmax(v, w)) * inv);
+            int64_t span = chi[3 * i + d] - clo[3 * i + d] + 1;
+            if (span > (1 << 20) || clo[3 * i + d] < -(1 << 20) || chi[3 * i + d] >= (1 << 20)) {
+                free(clo); free(chi); return -1;
+            }
+            cnt *= span;
+        }
+        total += cnt;
+    }
+    oc_ent *E = (oc_ent *)malloc(sizeof(oc_ent) * (size_t)total);
+    if (!E) { free(clo); free(chi); return -1; }
+    int64_t k = 0;
+    for (int i = 0; i < nt; ++i)
+        for (int64_t z = clo[3 * i + 2]; z <= chi[3 * i + 2]; ++z)
+            for (int64_t y = clo[3 * i + 1]; y <= chi[3 * i + 1]; ++y)
+                for (int64_t x = clo[3 * i]; x <= chi[3 * i]; ++x) {
+                    E[k].key = ((x + (1 << 20)) << 42) | ((y + (1 << 20)) << 21) | (z + (1 << 20));
+                    E[k].tri = i;
+                    ++k;
+                }
+    qsort(E, (size_t)total, sizeof(oc_ent), oc_ent_cmp);
+    int64_t n = 0;
+    for (int64_t a0 = 0; a0 < total;) {
+        int64_t a1 = a0;
+        while (a1 < total && E[a1].key == E[a0].key) ++a1;
+        const int64_t key = E[a0].key;
+        const int64_t cx = (key >> 42) - (1 << 20), cy = ((key >> 21) & ((1 << 21) - 1)) - (1 << 20),
+                      cz = (key & ((1 << 21) - 1)) - (1 << 20);
+        for (int64_t p = a0; p < a1; ++p)
+            for (int64_t q = p + 1; q < a1; ++q) {
+                const int i = E[p].tri, j = E[q].tri;  /* i < j: sorted within the cell */
+                /* the lowest cell both boxes touch (their ranges overlap here) */
+                int64_t lx = clo[3 * i] > clo[3 * j] ? clo[3 * i] : clo[3 * j];
+                int64_t ly = clo[3 * i + 1] > clo[3 * j + 1] ? clo[3 * i + 1] : clo[3 * j + 1];
+                int64_t lz = clo[3 * i + 2] > clo[3 * j + 2] ? clo[3 * i + 2] : clo[3 * j + 2];
+                if (lx != cx || ly != cy || lz != cz) continue;
+                if (!tri_pair_hits(X, tris + 3 * i, tris + 3 * j)) continue;
+                if (n < cap) { out[2 * n] = i; out[2 * n + 1] = j; }
+                ++n;
+            }
+        a0 = a1;
+    }
+    free(E);
+    free(clo);
+    free(chi);
+    if (n <= cap) qsort(out, (size_t)n, 2 * sizeof(int32_t), oc_pair_cmp);
     return n;
 }

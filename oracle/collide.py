@@ -30,6 +30,8 @@ def lib():
         L.oc_broadphase_ee_one.restype = i64
         L.oc_count_tri_tri.argtypes = [P, P, i32, i64, P]
         L.oc_count_tri_tri.restype = i64
+        L.oc_count_tri_tri_grid.argtypes = [P, P, i32, dbl, i64, P]
+        L.oc_count_tri_tri_grid.restype = i64
         L.oc_ccd_vt.argtypes = [P, P, dbl]
         L.oc_ccd_vt.restype = dbl
         L.oc_ccd_ee.argtypes = [P, P, dbl]
@@ -136,6 +138,27 @@ def intersecting_triangle_pairs(X, tris):
     while True:
         out = np.empty((cap, 2), dtype=np.int32)
         n = lib().oc_count_tri_tri(_p(X), _p(tris), len(tris), cap, _p(out))
+        if n <= cap:
+            return out[:n].copy()
+        cap = int(n)
+
+
+def intersecting_triangle_pairs_grid(X, tris, cell=None):
+    """The pairs of intersecting_triangle_pairs (same exact test), culled by
+    a uniform grid of side `cell` (default: the mean largest box extent of
+    the triangles): for the invariant check of large meshes.  Sorted pairs."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    tris = _i32(tris)
+    if cell is None:
+        P3 = X[tris]
+        cell = float(np.mean(np.max(P3.max(1) - P3.min(1), axis=1))) if len(tris) else 1.0
+        cell = max(cell, 1e-9)
+    cap = 1024
+    while True:
+        out = np.empty((cap, 2), dtype=np.int32)
+        n = lib().oc_count_tri_tri_grid(_p(X), _p(tris), len(tris), float(cell), cap, _p(out))
+        if n < 0:
+            raise MemoryError("intersecting_triangle_pairs_grid: grid too large")
         if n <= cap:
             return out[:n].copy()
         cap = int(n)

@@ -820,3 +820,64 @@ def test_oracle_step_applies_the_ndb_schedule_in_every_inner_iteration():
                     assert kk not in s_out
             amax_seen = max([amax_seen] + [a for _, a in s_out.values()])
     assert amax_seen >= 3
+
+
+# ----------------------------------------------------------------------------
+# the non-penetration checker (Sec. 7 invariant)
+# ----------------------------------------------------------------------------
+
+def test_intersection_checker_on_hand_built_pairs():
+    """Two triangles crossing in an X, a triangle pierced by another that
+    shares one vertex with it, a pair sharing an edge (never counted), two
+    disjoint parallel triangles and two coplanar overlapping ones (the
+    coplanar case is not counted)."""
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0],            # 0-2: in z = 0
+                  [0.2, 0.2, -0.5], [0.3, 0.2, 0.5], [0.2, 0.3, 0.5],  # 3-5: pierces 0-2
+                  [2, 0, 0], [3, 0, 0], [2, 1, 0],             # 6-8
+                  [2, 0, 0.1], [3, 0, 0.1], [2, 1, 0.1],       # 9-11: parallel above 6-8
+                  [0.1, 0.1, 0], [0.9, 0.05, 0], [0.1, 0.8, 0]], float)  # 12-14: coplanar with 0-2
+    T = np.array([[0, 1, 2], [3, 4, 5], [6, 7, 8], [9, 10, 11], [12, 13, 14]])
+    got = collide.intersecting_triangle_pairs(X, T)
+    assert sorted(map(tuple, got.tolist())) == [(0, 1), (1, 4)]
+    assert np.array_equal(collide.intersecting_triangle_pairs_grid(X, T), np.array([[0, 1], [1, 4]]))
+    # sharing vertex 0 and folded through: the far edge of one crosses the other
+    X2 = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0.8, 0.3, -0.4], [0.3, 0.8, 0.4]], float)
+    T2 = np.array([[0, 1, 2], [0, 3, 4]])
+    assert len(collide.intersecting_triangle_pairs(X2, T2)) == 1
+    # sharing an edge: skipped even when folded onto each other
+    X3 = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0.5, 0.5, 0.0]], float)
+    assert len(collide.intersecting_triangle_pairs(X3, np.array([[0, 1, 2], [1, 0, 3]]))) == 0
+
+
+def test_intersection_checker_ignores_exactly_aligned_smooth_sheets():
+    """A sheet bent only along x (z a function of x, exactly aligned grid)
+    has quadruples of coplanar points whose orientations round to tiny
+    values of either sign; it does not intersect itself."""
+    uv, tris = wl.grid_mesh(40, 40, 2.0, 2.0)
+    for f in (lambda u: 0.01 * np.sin(7 * u[:, 0]), lambda u: 0.2 * u[:, 0] ** 2, lambda u: 0.0 * u[:, 0]):
+        V = np.zeros((len(uv), 3))
+        V[:, :2] = uv
+        V[:, 2] = f(uv)
+        assert len(collide.intersecting_triangle_pairs(V, tris)) == 0
+        assert len(collide.intersecting_triangle_pairs_grid(V, tris)) == 0
+
+
+def test_grid_culled_checker_lists_the_brute_force_pairs():
+    """The grid-culled checker returns exactly the brute-force list on
+    crumpled sheets (hundreds of intersections) with an obstacle through
+    them, for several cell sizes."""
+    rng = np.random.default_rng(11)
+    for seed in range(3):
+        rng = np.random.default_rng(seed)
+        uv, tris = wl.grid_mesh(28, 28, 1.0, 1.0)
+        V = np.zeros((len(uv), 3))
+        V[:, :2] = uv + rng.normal(size=(len(uv), 2)) * 0.02
+        V[:, 2] = rng.normal(size=len(uv)) * 0.05
+        sv, st = wl.icosphere(2, 0.3, (0.5, 0.5, 0.0))
+        X = np.concatenate([V, sv])
+        T = np.concatenate([tris, np.asarray(st) + len(V)])
+        ref = collide.intersecting_triangle_pairs(X, T)
+        ref = ref[np.lexsort((ref[:, 1], ref[:, 0]))]
+        assert len(ref) > 100
+        for cell in (None, 0.01, 0.05, 0.3):
+            assert np.array_equal(collide.intersecting_triangle_pairs_grid(X, T, cell), ref), (seed, cell)
