@@ -480,19 +480,133 @@ int64_t oc_broadphase_ee_one(const float *X0, const float *X1, const int32_t *e2
  * do not contain the shared vertex; pairs sharing an edge are skipped.
  * ------------------------------------------------------------------------ */
 
-static double orient(v3 a, v3 b, v3 c, v3 d) { return det3(sub(b, a), sub(c, a), sub(d, a)); }
+/* Exact sign of the orientation determinant det[b - a, c - a, d - a]
+ * (Shewchuk, "Adaptive precision floating-point arithmetic and fast robust
+ * geometric predicates", 1997): the double evaluation is kept when it
+ * exceeds a bound on its rounding error; otherwise the determinant is
+ * evaluated exactly in floating-point expansions (sums of nonoverlapping
+ * doubles, increasing magnitude) built with Two-Sum, the FMA two-product
+ * and Grow-/Scale-Expansion, whose largest component has the sign of the
+ * exact value.  Returns a value with the exact sign (0 exactly when the
+ * four points are coplanar). */
+#define OC_EXP_MAX 1024
+static void two_sum(double a, double b, double *x, double *y) {
+    *x = a + b;
+    double bv = *x - a, av = *x - bv;
+    *y = (a - av) + (b - bv);
+}
+/* h = e + b (e nonoverlapping, increasing); returns the length, zeros dropped */
+static int grow_exp(const double *e, int n, double b, double *h) {
+    double q = b;
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        double x, y;
+        two_sum(q, e[i], &x, &y);
+        if (y != 0.0) h[m++] = y;
+        q = x;
+    }
+    if (q != 0.0 || m == 0) h[m++] = q;
+    return m;
+}
+static int sum_exp(const double *e, int n, const double *f, int m, double *h) {
+    double t[OC_EXP_MAX];
+    int k = n;
+    memcpy(t, e, sizeof(double) * (size_t)n);
+    for (int j = 0; j < m; ++j) {
+        double u[OC_EXP_MAX];
+        k = grow_exp(t, k, f[j], u);
+        memcpy(t, u, sizeof(double) * (size_t)k);
+    }
+    memcpy(h, t, sizeof(double) * (size_t)k);
+    return k;
+}
+/* h = e * b exactly */
+static int scale_exp(const double *e, int n, double b, double *h) {
+    double t[OC_EXP_MAX];
+    int k = 1;
+    t[0] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double p = e[i] * b, q = fma(e[i], b, -p);  /* e_i b = p + q exactly */
+        double u[OC_EXP_MAX];
+        k = grow_exp(t, k, q, u);
+        k = grow_exp(u, k, p, t);
+    }
+    memcpy(h, t, sizeof(double) * (size_t)k);
+    return k;
+}
+static int mul_exp(const double *e, int n, const double *f, int m, double *h) {
+    double acc[OC_EXP_MAX], t[OC_EXP_MAX], u[OC_EXP_MAX];
+    int k = 1;
+    acc[0] = 0.0;
+    for (int j = 0; j < m; ++j) {
+        int kt = scale_exp(e, n, f[j], t);
+        k = sum_exp(acc, k, t, kt, u);
+        memcpy(acc, u, sizeof(double) * (size_t)k);
+    }
+    memcpy(h, acc, sizeof(double) * (size_t)k);
+    return k;
+}
+static double exp_sign_value(const double *e, int n) {
+    for (int i = n - 1; i >= 0; --i)
+        if (e[i] != 0.0) return e[i];
+    return 0.0;
+}
+/* b - a as an expansion of one or two components */
+static int diff_exp(double b, double a, double *e) {
+    double x, y;
+    two_sum(b, -a, &x, &y);
+    if (y == 0.0) {
+        e[0] = x;
+        return 1;
+    }
+    e[0] = y;
+    e[1] = x;
+    return 2;
+}
+static double orient_exact(v3 a, v3 b, v3 c, v3 d) {
+    double U[3][2], V[3][2], W[3][2];
+    int nu[3], nv[3], nw[3];
+    const double A[3] = {a.x, a.y, a.z}, B[3] = {b.x, b.y, b.z}, C[3] = {c.x, c.y, c.z}, D[3] = {d.x, d.y, d.z};
+    for (int k = 0; k < 3; ++k) {
+        nu[k] = diff_exp(B[k], A[k], U[k]);
+        nv[k] = diff_exp(C[k], A[k], V[k]);
+        nw[k] = diff_exp(D[k], A[k], W[k]);
+    }
+    /* det = sum over (i, j, k) cyclic of U_i (V_j W_k - V_k W_j) */
+    double det[OC_EXP_MAX];
+    int nd = 1;
+    det[0] = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3, k = (i + 2) % 3;
+        double p1[OC_EXP_MAX], p2[OC_EXP_MAX], c1[OC_EXP_MAX], term[OC_EXP_MAX], nxt[OC_EXP_MAX];
+        int n1 = mul_exp(V[j], nv[j], W[k], nw[k], p1);
+        int n2 = mul_exp(V[k], nv[k], W[j], nw[j], p2);
+        for (int q = 0; q < n2; ++q) p2[q] = -p2[q];
+        int nc = sum_exp(p1, n1, p2, n2, c1);
+        int nt = mul_exp(c1, nc, U[i], nu[i], term);
+        nd = sum_exp(det, nd, term, nt, nxt);
+        memcpy(det, nxt, sizeof(double) * (size_t)nd);
+    }
+    return exp_sign_value(det, nd);
+}
+static double orient(v3 a, v3 b, v3 c, v3 d) {
+    v3 u = sub(b, a), v = sub(c, a), w = sub(d, a);
+    double det = det3(u, v, w);
+    /* the rounding error of the double evaluation (differences included) is
+     * below (7 + 56 eps) eps of the permanent, eps = 2^-53 (Shewchuk's bound);
+     * 2e-15 keeps a margin over it */
+    double perm = fabs(u.x) * (fabs(v.y * w.z) + fabs(v.z * w.y)) + fabs(u.y) * (fabs(v.z * w.x) + fabs(v.x * w.z)) +
+                  fabs(u.z) * (fabs(v.x * w.y) + fabs(v.y * w.x));
+    if (fabs(det) > 2e-15 * perm) return det;
+    return orient_exact(a, b, c, d);
+}
 
-/* does segment pq cross triangle abc (proper or touching)?  An endpoint
- * whose orientation is below 1e-12 of the triple product of the lengths
- * involved lies in the triangle's plane up to rounding; a segment with both
- * endpoints there lies in the plane (coplanar: not counted), whatever
- * signs rounding gave the two tiny orientations. */
+/* does segment pq cross triangle abc (proper or touching)?  The
+ * orientation signs are exact (orient), so a segment in the triangle's
+ * plane is recognised as coplanar and a segment whose line runs nearly
+ * parallel to the plane gets the signs of the exact geometry. */
 static int seg_tri(v3 p, v3 q, v3 a, v3 b, v3 c) {
     double sp = orient(a, b, c, p), sq = orient(a, b, c, q);
-    const double lab = nrm(sub(b, a)), lac = nrm(sub(c, a));
-    const double tp = 1e-12 * lab * lac * nrm(sub(p, a)), tq = 1e-12 * lab * lac * nrm(sub(q, a));
-    if (fabs(sp) <= tp) sp = 0.0;
-    if (fabs(sq) <= tq) sq = 0.0;
     if ((sp > 0 && sq > 0) || (sp < 0 && sq < 0)) return 0;
     if (sp == 0 && sq == 0) return 0; /* coplanar: not counted as crossing */
     double s1 = orient(p, q, a, b), s2 = orient(p, q, b, c), s3 = orient(p, q, c, a);
@@ -553,6 +667,16 @@ int64_t oc_count_tri_tri(const double *X, const int32_t *tris, int32_t nt, int64
  * j).  Returns the count (-1 when an allocation fails or a box spans more
  * than 2^21 cells per axis). */
 typedef struct { int64_t key; int32_t tri; } oc_ent;
+/* closed boxes of the two triangles meet (no intersection otherwise) */
+static int tri_boxes_meet(const double *X, const int32_t *A, const int32_t *B) {
+    for (int d = 0; d < 3; ++d) {
+        double a0 = X[3 * A[0] + d], a1 = X[3 * A[1] + d], a2 = X[3 * A[2] + d];
+        double b0 = X[3 * B[0] + d], b1 = X[3 * B[1] + d], b2 = X[3 * B[2] + d];
+        if (fmax(b0, fmax(b1, b2)) < fmin(a0, fmin(a1, a2)) || fmin(b0, fmin(b1, b2)) > fmax(a0, fmax(a1, a2)))
+            return 0;
+    }
+    return 1;
+}
 static int oc_ent_cmp(const void *p, const void *q) {
     const oc_ent *a = (const oc_ent *)p, *b = (const oc_ent *)q;
     if (a->key != b->key) return a->key < b->key ? -1 : 1;
@@ -614,6 +738,7 @@ int64_t oc_count_tri_tri_grid(const double *X, const int32_t *tris, int32_t nt, 
                 int64_t ly = clo[3 * i + 1] > clo[3 * j + 1] ? clo[3 * i + 1] : clo[3 * j + 1];
                 int64_t lz = clo[3 * i + 2] > clo[3 * j + 2] ? clo[3 * i + 2] : clo[3 * j + 2];
                 if (lx != cx || ly != cy || lz != cz) continue;
+                if (!tri_boxes_meet(X, tris + 3 * i, tris + 3 * j)) continue;
                 if (!tri_pair_hits(X, tris + 3 * i, tris + 3 * j)) continue;
                 if (n < cap) { out[2 * n] = i; out[2 * n + 1] = j; }
                 ++n;

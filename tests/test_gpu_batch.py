@@ -69,6 +69,9 @@ class _Batch:
                 pc.pdc_add_obstacle(self.h, o.verts, o.tris)
         self.n = int(self.off[-1])
         self.pins = np.concatenate([s.verts[s.pins] for s in scenes]).astype(np.float32)
+        v0 = np.concatenate([s.v0 for s in scenes]).astype(np.float32)
+        if np.any(v0):
+            pc.pdc_set_state(self.h, np.concatenate([s.verts for s in scenes]).astype(np.float32), v0)
 
     def step(self):
         if len(self.pins):
