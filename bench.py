@@ -221,7 +221,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
     # ---- kernel launches of the library per step, counted by the CUDA
     # activity profiler over a replay of the same number of steps
     restore()
-    launches, busy = count_launches(torch, one_step, steps) if launch_count else (None, None)
+    launches, busy, gaps = count_launches(torch, one_step, steps) if launch_count else (None, None, None)
     restore()
     # ---- e2e through the public API with host buffers: pin targets h2d, positions d2h
     pin_host = torch.empty(pins.shape[1:], dtype=torch.float32).pin_memory()
@@ -247,7 +247,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
                 rel_res=statistics.mean(s["rel_residual"] for s in st_list),
                 cand=statistics.mean(s["n_candidates"] for s in st_list),
                 toi=min(s["t_toi"] for s in st_list), finite=bool(np.isfinite(x).all()),
-                graph_loops=statistics.mean(s["graph_loops"] for s in st_list), device_busy=busy,
+                graph_loops=statistics.mean(s["graph_loops"] for s in st_list), device_busy=busy, idle_gaps=gaps,
                 launches=launches)
 
 
@@ -339,45 +339,70 @@ def run_batched(pc, torch, steps=5, warmup=2, dev_index=0):
             "line_search": "per instance", "tuning": tuning}
 
 
-def count_launches(torch, one_step, steps):
-    """Kernels launched by the library (names beginning with k_) during
-    `steps` steps, from torch.profiler's CUDA activity trace, and the share of
-    the traced interval (first kernel start to last kernel end) in which some
-    kernel ran; (None, None) if the trace is unavailable."""
+def init_trace(torch):
+    """Starts and stops one CUDA activity trace session, so that the tracer
+    is set up before any CUDA graph is instantiated (kernels of graphs
+    instantiated earlier would not be recorded)."""
     try:
         from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]):  # first session initialises the trace
+        with profile(activities=[ProfilerActivity.CUDA]):
             torch.cuda.synchronize()
+    except Exception:
+        pass
+
+
+def count_launches(torch, one_step, steps):
+    """Kernels launched by the library (names beginning with k_) during
+    `steps` steps, from torch.profiler's CUDA activity trace; the share of
+    the traced interval (first kernel start to last kernel end) in which some
+    kernel ran; and the largest idle gaps between consecutive kernels,
+    summed by the pair of kernels around them.  (None, None, None) if the
+    trace is unavailable."""
+    try:
+        from torch.profiler import ProfilerActivity, profile
         with profile(activities=[ProfilerActivity.CUDA]) as prof:
             for _ in range(steps):
                 one_step()
             torch.cuda.synchronize()
         import re
         pat = re.compile(r"(?:^|[\s:])k_\w+")
+        short = re.compile(r"(k_\w+)")
         n = 0
         spans = []
         for ev in prof.events():
             if str(getattr(ev, "device_type", "")).endswith("CUDA"):
-                if pat.search(ev.name or ""):
+                nm = ev.name or ""
+                if pat.search(nm):
                     n += 1
                 tr = getattr(ev, "time_range", None)
                 if tr is not None and tr.end > tr.start:
-                    spans.append((tr.start, tr.end))
-        busy = None
+                    m = short.search(nm)
+                    spans.append((tr.start, tr.end, m.group(1) if m else nm[:24]))
+        busy, gaps = None, None
         if spans:
             spans.sort()
-            tot, cs, ce = 0.0, spans[0][0], spans[0][1]
-            for a, b in spans[1:]:
+            tot, cs, ce, last = 0.0, spans[0][0], spans[0][1], spans[0][2]
+            acc = {}
+            for a, b, nm in spans[1:]:
                 if a > ce:
                     tot += ce - cs
+                    key = last + " -> " + nm
+                    g = acc.setdefault(key, [0, 0.0])
+                    g[0] += 1
+                    g[1] += a - ce
                     cs, ce = a, b
                 else:
                     ce = max(ce, b)
+                if b >= ce:
+                    last = nm
             tot += ce - cs
-            busy = round(tot / max(spans[-1][1] - spans[0][0], 1e-9), 4)
-        return n, busy
+            span = max(spans[-1][1] - spans[0][0], 1e-9)
+            busy = round(tot / span, 4)
+            top = sorted(acc.items(), key=lambda kv: -kv[1][1])[:10]
+            gaps = {k: {"count": v[0], "us_per_step": round(v[1] / steps, 1)} for k, v in top}
+        return n, busy, gaps
     except Exception:
-        return None, None
+        return None, None, None
 
 
 # profiled regions that enclose other profiled regions (not kernels themselves)
@@ -612,6 +637,8 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     scene = wl.hanging_swept(side=a.side)
+    if not a.no_launch_count:
+        init_trace(torch)
     forms = {}
     for f in a.forms.split(","):
         forms[f] = run_form(pc, torch, scene, FORMS[f], a.steps, a.warmup, local,
@@ -643,6 +670,7 @@ def main():
         "e2e": {"value": round(forms[head]["e2e_ms"], 3), "unit": "ms/step",
                 "h2d_bytes_per_step": forms[head]["h2d"], "d2h_bytes_per_step": forms[head]["d2h"]},
         "gpu_launches": forms[head]["launches"],
+        "idle_gaps": forms[head]["idle_gaps"],
         "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3),
                         "GBps": round(v["algo_bytes"] / max(v["total_ms"], 1e-9) / 1e6, 1)}
                     for k, v in forms[head]["kernels"].items()},

@@ -184,6 +184,10 @@ typedef struct {
                                 pdc_tuning); results do not depend on the
                                 choice beyond the order of float atomics.  0
                                 (default): fixed shapes                          */
+    int32_t graph_unroll;    /* LG iterations per pass of a graph loop's while
+                                node (1..8, default 4): each pass relaunches its
+                                body on the device; the kernels of iterations
+                                after the loop's end return at once             */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
@@ -314,6 +318,17 @@ pdc_status pdc_get_displacement(pdc_handle h, float *u, int32_t on_device);
 
 /* Statistics of the last step. */
 pdc_status pdc_get_stats(pdc_handle h, pdc_stats *out);
+
+/* Candidate pairs of the last full CCD of the last step with their
+ * non-distance-barrier states (Sec. 4, Eq. exp): prim [cap][2] the pair's
+ * primitives (VT: collision vertex, collision triangle; EE: two edge ids,
+ * first < second, edges numbered in ascending (min vertex, max vertex)
+ * order), kinds [cap] (0 VT, 1 EE), state [cap] (bit 7: active; bits 0-6:
+ * the life-span counter a, the weight being k K^a).  VT pairs come first,
+ * each kind sorted by its primitive ids.  *count receives the number of
+ * pairs; only the first cap are written.  0 pairs before the first step or
+ * without collision handling.  Host buffers. */
+pdc_status pdc_get_pairs(pdc_handle h, int32_t *prim, int32_t *kinds, uint8_t *state, int64_t cap, int64_t *count);
 
 /* Launch shapes (autotune) of the handle. */
 pdc_status pdc_get_tuning(pdc_handle h, pdc_tuning *out);

@@ -486,6 +486,7 @@ class StepStats:
     rf_res1: float = 0.0           # ... and after its iterations
     rel_residual: float = 0.0     # relative PD residual (R11); with collisions on, the last one the
                                   # stopping test of the relative-residual mode measured
+    constraints: dict = field(default_factory=dict)  # the constraint set (key -> (active, a)) at the exit
     log: list = field(default_factory=list)
 
 
@@ -530,7 +531,8 @@ class Oracle:
         trace (a list, optional) receives one record per inner LG iteration:
         the constraint set it started from, the NDB weights and activity each
         candidate pair had in its contact springs, the partial-CCD flags after
-        its global solve and the constraint set those flags produced."""
+        its global solve (and each pair's activity margin, min over samples of
+        Q - dhat |p2^0 - p1^0|) and the constraint set those flags produced."""
         p, M = self.p, self.model
         h = p.dt
         if x_star is None:
@@ -640,13 +642,14 @@ class Oracle:
                 # partial CCD (Sec. 4.1) on the candidates over (x^-, x^+)
                 Xp = self._all(xn, obs_next).astype(np.float32)
                 if p.pccd_adaptive:
-                    flags = pccd_adaptive.partial_ccd_adaptive(Xm32, Xp, quads, kinds, p.dhat, p.alpha,
-                                                               p.pccd_max_axis)[0]
+                    flags, margin = pccd_adaptive.partial_ccd_adaptive(Xm32, Xp, quads, kinds, p.dhat, p.alpha,
+                                                                       p.pccd_max_axis)[:2]
                 else:
-                    flags, _ = collide.partial_ccd(Xm32, Xp, quads, kinds, p.samples_vt, p.samples_ee, p.dhat)
+                    flags, margin = collide.partial_ccd(Xm32, Xp, quads, kinds, p.samples_vt, p.samples_ee, p.dhat)
                 if trace is not None:
                     trace.append(dict(state_in=dict(state), weights=dict(zip(keys, w)), active=dict(zip(keys, act)),
-                                      flags=dict(zip(keys, np.asarray(flags, dtype=bool)))))
+                                      flags=dict(zip(keys, np.asarray(flags, dtype=bool))),
+                                      margins=dict(zip(keys, np.asarray(margin, dtype=np.float64)))))
                 state = ndb_after_partial_ccd(state, keys, flags, p.a_max)
                 if trace is not None:
                     trace[-1]["state"] = dict(state)
@@ -668,6 +671,7 @@ class Oracle:
         x_new = xall_new[: cm.nc]
         self.obs = [xall_new[a:b] for a, b in cm.obs_slices]
         st.t_toi, st.s = t_toi, s
+        st.constraints = dict(state)
         st.n_candidates = len(keys)
         st.n_active = sum(1 for v in state.values() if v[0])
 

@@ -187,6 +187,10 @@ __global__ void k_loop_begin(LoopCtl *c, int graph) {
 __global__ void k_loop_decide(LoopCtl *c, LoopCfg f, const Scalars *sc, const int *n_cv, const int *dev_err,
                               int after_solve) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (after_solve && !c->go) {  // an earlier iteration of this pass ended the loop
+        if (f.use_cond) cudaGraphSetConditional(f.cond, 0u);
+        return;
+    }
     int go = (*dev_err & (PDC_DEVERR_UMMA | PDC_DEVERR_COPY)) ? 0 : 1;
     const double dx = (double)__uint_as_float(sc->dxmax);
     if (go && after_solve) {
@@ -505,6 +509,7 @@ struct pdc_ctx {
         c.corner = corner;
         c.res_block = tune.residual_block;
         c.cheb_plain = tune.cheb_tile ? 0 : 1;
+        c.live = live_ptr;
         return c;
     }
     CollView coll() const {
@@ -517,6 +522,7 @@ struct pdc_ctx {
         v.edge = cedge;
         v.vfixed = vfixed;
         v.guard = guard_d;
+        v.live = live_ptr;
         const bool pi = per_instance();
         v.vinst = pi ? vinst.p : nullptr;
         v.toi_inst = pi ? toi_inst.p : nullptr;
@@ -543,6 +549,7 @@ struct pdc_ctx {
         S.umma_partial = umma_partial;
         S.dev_err = sflag;
         S.overlap = P.launch_overlap != 0;
+        S.live = live_ptr;
         return S;
     }
     SubspaceWork work() {
@@ -603,6 +610,9 @@ struct pdc_ctx {
     unsigned graph_gen = 1;      // bumped when a buffer a graph captures is reallocated
     bool graphs_failed = false;  // a graph could not be built: host-driven loops from then on
     bool graph_overlap = true;   // programmatic dependent launches inside the graphs
+    // while a device-driven loop is captured: the loop's go flag, which every
+    // kernel of its iterations reads (they do nothing once the loop has ended)
+    const int *live_ptr = nullptr;
     DevBuf<LoopCtl> ctl;
     LoopCtl hctl;
     pdc_tuning tune = {0, 256, 1, 152 * 8, 8, {0, 0, 0}, {0, 0}, {0, 0, 0, 0}, {0, 0, 0}};
@@ -1214,18 +1224,18 @@ void pdc_ctx::autotune_vertex_kernels() {
 // two on the host; the device-driven loop (run_loop) in k_loop_decide.
 void pdc_ctx::enqueue_residual(bool contacts) {
     ClothView c = cloth();
-    PDC_CK(cudaMemsetAsync(&sc.p->rsq, 0, sizeof(double), s));
+    launch_live_zero(s, live_ptr, &sc.p->rsq, sizeof(double));
     const float *cw = nullptr;
     const float4 *cf = nullptr;
     if (contacts) {
-        CW.zero(s);
-        CF.zero(s);
+        launch_live_zero(s, live_ptr, CW.p, sizeof(float) * n);
+        launch_live_zero(s, live_ptr, CF.p, sizeof(float4) * n);
         PROF("contact_springs", 0, launch_contact(s, coll(), act, n_act_d, cap_act, Xp, dhat, CW, CF));
-        launch_contact_list(s, n, CW, contact_list, n_cv_d);
+        launch_contact_list(s, n, CW, contact_list, n_cv_d, live_ptr);
         cw = CW;
         cf = CF;
     } else {
-        n_cv_d.zero(s);
+        launch_live_zero(s, live_ptr, n_cv_d.p, sizeof(int));
     }
     PROF("local_residual", bytes_residual(contacts), launch_residual(s, c, Xs, Ucur, Z, cw, cf, R, sc, nullptr, 0));
 }
@@ -1238,10 +1248,10 @@ void pdc_ctx::enqueue_solve(bool contacts, bool springs, bool device, float w_ac
                             int sweeps, bool pccd) {
     ClothView c = cloth();
     const float *cw = contacts ? CW.p : nullptr;
-    PDC_CK(cudaMemsetAsync(&sc.p->dxmax, 0, sizeof(unsigned int), s));
+    launch_live_zero(s, live_ptr, &sc.p->dxmax, sizeof(unsigned int));
     const bool acc = accel.on && P.fixed_iters == 0;
     const bool aa = acc && P.accel == 2;
-    if (aa) aa_clear(s, aa_Gb);  // normal equations of this iteration
+    if (aa) aa_clear(s, aa_Gb, live_ptr);  // normal equations of this iteration
     float4 *xprev = (acc && !aa && !device) ? Xacc.p : nullptr;
     const bool sp = device ? contacts : springs;  // springs possible on this path
     SubspaceView S = sub(r_nc, r_c);
@@ -1265,7 +1275,7 @@ void pdc_ctx::enqueue_solve(bool contacts, bool springs, bool device, float w_ac
             have_delta = true;
         }
         if (!have_delta) {
-            PDC_CK(cudaMemsetAsync(din, 0, sizeof(float4) * n, s));
+            launch_live_zero(s, live_ptr, din, sizeof(float4) * n);
             have_delta = true;
         }
         if (P.sweep_kind == 1) {
@@ -1444,6 +1454,7 @@ bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r
     if (!gs) PDC_CK(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
     cudaStream_t saved = s;
     s = gs;  // everything below is captured from the capture stream
+    live_ptr = &ctl.p->go;  // the captured iterations do nothing once the loop has ended
     cudaGraph_t g = nullptr;
     cudaGraphExec_t e = nullptr;
     bool capturing = false;
@@ -1482,10 +1493,19 @@ bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r
         PDC_CK(cudaStreamEndCapture(gs, &g));
         PDC_CK(cudaStreamBeginCaptureToGraph(gs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         capturing = true;
-        enqueue_solve(contacts, contacts, true, 1.f, r_nc, r_c, cycles, sweeps, pccd);
-        enqueue_residual(contacts);
-        k_loop_decide<<<1, 1, 0, s>>>(ctl, cfg, sc, n_cv_d, sflag, 1);
-        PDC_LAUNCH_CK();
+        // graph_unroll iterations per pass of the while node (each pass costs a
+        // relaunch of the body on the device): the kernels of an iteration that
+        // follows the end of the loop read go = 0 and return at once, and only
+        // the last decision of the pass sets the while condition
+        const int unroll = std::min(std::max(P.graph_unroll, 1), 8);
+        for (int u = 0; u < unroll; ++u) {
+            LoopCfg cu = cfg;
+            cu.use_cond = u == unroll - 1 ? 1 : 0;
+            enqueue_solve(contacts, contacts, true, 1.f, r_nc, r_c, cycles, sweeps, pccd);
+            enqueue_residual(contacts);
+            k_loop_decide<<<1, 1, 0, s>>>(ctl, cu, sc, n_cv_d, sflag, 1);
+            PDC_LAUNCH_CK();
+        }
         cudaGraph_t b2 = nullptr;
         capturing = false;
         PDC_CK(cudaStreamEndCapture(gs, &b2));
@@ -1499,10 +1519,12 @@ bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r
         if (g) cudaGraphDestroy(g);
         (void)cudaGetLastError();  // clear the failed capture's error
         s = saved;
+        live_ptr = nullptr;
         if (log) std::fprintf(stderr, "[pdc] LG loop graph not built (%s): host-driven loops\n", ex.what());
         return false;
     }
     s = saved;
+    live_ptr = nullptr;
     G.g = g;
     G.e = e;
     G.gen = graph_gen + bp.gen;
@@ -1952,6 +1974,7 @@ void pdc_default_params(pdc_params *p) {
     p->pccd_max_axis = 64;
     p->instance_line_search = 0;
     p->autotune = 0;
+    p->graph_unroll = 4;
 }
 
 static bool params_valid(const pdc_params *params) {
@@ -2320,6 +2343,44 @@ pdc_status pdc_get_kernel_times(pdc_handle h, pdc_kernel_time *out, int32_t cap,
     if (count) *count = k;
     if (out)
         for (int i = 0; i < std::min(k, (int)cap); ++i) out[i] = h->prof.acc[i];
+    API_END(h)
+}
+
+pdc_status pdc_get_pairs(pdc_handle h, int32_t *prim, int32_t *kinds, uint8_t *state, int64_t cap, int64_t *count) {
+    API_BEGIN(h)
+    if (!count || cap < 0 || (cap > 0 && (!prim || !kinds || !state))) throw Error(PDC_ERR_ARG, "pdc_get_pairs: NULL");
+    *count = 0;
+    if (!h->P.collisions || !h->stepped) return PDC_OK;
+    BroadPhase &bp = h->bp;
+    long long nvt = 0, nee = 0;
+    bp.cnt_vt_d[bp.cur].download(&nvt, 1, h->s);
+    bp.cnt_ee_d[bp.cur].download(&nee, 1, h->s);
+    PDC_CK(cudaStreamSynchronize(h->s));
+    *count = nvt + nee;
+    const long long kv = std::min<long long>(nvt, cap), ke = std::min<long long>(nee, cap - kv);
+    std::vector<int2> pv(std::max<long long>(kv, 1)), pe(std::max<long long>(ke, 1));
+    std::vector<unsigned char> sv(std::max<long long>(kv, 1)), se(std::max<long long>(ke, 1));
+    if (kv > 0) {
+        bp.vt[bp.cur].download(pv.data(), kv, h->s);
+        bp.st_vt[bp.cur].download(sv.data(), kv, h->s);
+    }
+    if (ke > 0) {
+        bp.ee[bp.cur].download(pe.data(), ke, h->s);
+        bp.st_ee[bp.cur].download(se.data(), ke, h->s);
+    }
+    PDC_CK(cudaStreamSynchronize(h->s));
+    for (long long i = 0; i < kv; ++i) {
+        prim[2 * i] = pv[i].x;
+        prim[2 * i + 1] = pv[i].y;
+        kinds[i] = 0;
+        state[i] = sv[i];
+    }
+    for (long long i = 0; i < ke; ++i) {
+        prim[2 * (kv + i)] = pe[i].x;
+        prim[2 * (kv + i) + 1] = pe[i].y;
+        kinds[kv + i] = 1;
+        state[kv + i] = se[i];
+    }
     API_END(h)
 }
 

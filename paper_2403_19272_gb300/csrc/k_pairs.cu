@@ -550,7 +550,8 @@ __device__ inline void warp_max_atomic(float v, unsigned int *dst) {
 // disp = xp - xm; amax = max |disp - disp0| (disp0 := the previous disp when
 // the previous pass was full, i.e. the reference moves to that pass).
 __global__ void k_pccd_disp(int nv, const float4 *__restrict__ xm, const float4 *__restrict__ xp,
-                            float4 *__restrict__ disp, float4 *__restrict__ disp0, PccdState *ps) {
+                            float4 *__restrict__ disp, float4 *__restrict__ disp0, PccdState *ps, const int *live) {
+    if (loop_dead(live)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool moved_ref = ps->pass_full != 0;
     float m = 0.f;
@@ -573,7 +574,9 @@ __global__ void k_pccd_disp(int nv, const float4 *__restrict__ xm, const float4 
 
 // Finishes the previous pass (a full pass installs its watch list) and
 // decides this one; resets the per-pass counters.
-__global__ void k_pccd_decide(PccdState *ps, float tau, long long cap) {
+__global__ void k_pccd_decide(PccdState *ps, float tau, long long cap, const int *live, int *n_act) {
+    if (loop_dead(live)) return;
+    if (n_act) *n_act = 0;  // the active list is rebuilt by this pass
     PccdState p = *ps;
     if (p.pass_full) {
         p.cur ^= 1;
@@ -613,6 +616,7 @@ __global__ void __launch_bounds__(256) k_pccd_filter(CollView cv, const int2 *__
                                                      const float4 *__restrict__ disp4, float dhat, float tau,
                                                      PccdState *ps, int *watch0, int *watch1, int *near,
                                                      long long cap) {
+    if (loop_dead(cv.live)) return;
     const bool full = ps->pass_full != 0;
     const int cur = ps->cur;
     const int *watch = cur ? watch1 : watch0;
@@ -665,6 +669,7 @@ __global__ void __launch_bounds__(256) k_pccd_test(CollView cv, const int2 *__re
                                                    CollParams P, const int *__restrict__ near,
                                                    const PccdState *ps, long long cap, ActivePair *act,
                                                    int cap_act, int *n_act, int *overflow) {
+    if (loop_dead(cv.live)) return;
     long long nvt = *nvt_p;
     long long n = min((long long)ps->n_near, cap);
     long long stride = (long long)gridDim.x * blockDim.x;
@@ -712,6 +717,7 @@ __global__ void __launch_bounds__(256) k_pccd_test(CollView cv, const int2 *__re
 // of the pair gets weight w toward its target (held in place when c_j = 0).
 __global__ void k_contact(CollView cv, const ActivePair *__restrict__ act, const int *n_act_p, int cap,
                           const float4 *__restrict__ x, float dhat, float *__restrict__ cw, float4 *__restrict__ cf) {
+    if (loop_dead(cv.live)) return;
     int n = min(*n_act_p, cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         ActivePair ap = act[i];
@@ -748,7 +754,9 @@ __global__ void k_contact(CollView cv, const ActivePair *__restrict__ act, const
     }
 }
 
-__global__ void k_contact_list(int n, const float *__restrict__ cw, int *__restrict__ list, int *count) {
+__global__ void k_contact_list(int n, const float *__restrict__ cw, int *__restrict__ list, int *count,
+                               const int *live) {
+    if (loop_dead(live)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool want = i < n && cw[i] > 0.f;
     unsigned m = __ballot_sync(0xffffffffu, want);
@@ -877,9 +885,8 @@ void launch_partial_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, cons
     // watch gap: pairs within 2 d_hat of the near bound are re-tested every pass
     const float tau = 2.f * P.dhat;
     if (bp.prof) bp.prof->begin(s, "pccd_prep", 40.0 * cv.nv);
-    PDC_CK(cudaMemsetAsync(n_act, 0, sizeof(int), s));
-    if (cv.nv > 0) k_pccd_disp<<<(cv.nv + 255) / 256, 256, 0, s>>>(cv.nv, xm, xp, disp, bp.disp0, bp.pccd);
-    k_pccd_decide<<<1, 1, 0, s>>>(bp.pccd, tau, bp.cap_pairs);
+    if (cv.nv > 0) k_pccd_disp<<<(cv.nv + 255) / 256, 256, 0, s>>>(cv.nv, xm, xp, disp, bp.disp0, bp.pccd, cv.live);
+    k_pccd_decide<<<1, 1, 0, s>>>(bp.pccd, tau, bp.cap_pairs, cv.live, n_act);
     PDC_LAUNCH_CK();
     if (bp.prof) bp.prof->end(s);
     // (full or watch-list pass is decided on the device: no byte model here)
@@ -915,9 +922,9 @@ void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, c
     PDC_LAUNCH_CK();
 }
 
-void launch_contact_list(cudaStream_t s, int n, const float *cw, int *list, int *count) {
-    PDC_CK(cudaMemsetAsync(count, 0, sizeof(int), s));
-    if (n > 0) k_contact_list<<<(n + 255) / 256, 256, 0, s>>>(n, cw, list, count);
+void launch_contact_list(cudaStream_t s, int n, const float *cw, int *list, int *count, const int *live) {
+    launch_live_zero(s, live, count, sizeof(int));
+    if (n > 0) k_contact_list<<<(n + 255) / 256, 256, 0, s>>>(n, cw, list, count, live);
     PDC_LAUNCH_CK();
 }
 

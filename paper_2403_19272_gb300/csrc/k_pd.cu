@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(256) k_elem_corner(const ClothView c, int tri_
                                                      float4 *__restrict__ ch) {
     grid_dep_wait();
     grid_dep_release();
+    if (loop_dead(c.live)) return;
     if ((int)blockIdx.x < tri_blocks) {
         int t = blockIdx.x * blockDim.x + threadIdx.x;
         if (t < c.m) tri_corner(c, t, xs, u, ct);
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(256) k_residual(const ClothView c, const float
                                                   float *__restrict__ r_soa, int soa_ld) {
     grid_dep_wait();
     grid_dep_release();
+    if (loop_dead(c.live)) return;  // block-uniform: no thread reaches the block reduction
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float sq = 0.f;
     if (i < c.n) {
@@ -293,6 +295,7 @@ __global__ void __launch_bounds__(256) k_sweep(const ClothView c, const float *_
                                                const float4 *x, float4 *xout, float4 *xprev, float w_acc,
                                                const float4 *__restrict__ xs, float4 *__restrict__ xabs,
                                                Scalars *sc) {
+    if (loop_dead(c.live)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float mx = 0.f;
     if (i < c.n) {
@@ -345,6 +348,7 @@ __global__ void __launch_bounds__(256) k_cheb_step(const ClothView c, const floa
                                                    Scalars *sc) {
     grid_dep_wait();
     grid_dep_release();
+    if (loop_dead(c.live)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float mx = 0.f;
     if (i < c.n) {
@@ -406,7 +410,8 @@ __global__ void __launch_bounds__(ELL_TILE_ROWS, 8) k_cheb_step_tile(
     grid_dep_release();
     const int i = blockIdx.x * ELL_TILE_ROWS + t;
     float mx = 0.f;
-    const bool live = i < c.n;
+    // an ended device loop: no load or store, but the tile copy is still awaited
+    const bool live = i < c.n && !loop_dead(c.live);
     const bool fr = live && c.is_free[i];
     float3 di = make_float3(0.f, 0.f, 0.f), ri = di, pi = di;
     float D = 1.f;
@@ -475,6 +480,7 @@ __global__ void __launch_bounds__(256) k_aa_gram(int n, const unsigned char *__r
     __shared__ float red[AA_MAX * (AA_MAX + 3) / 2 + AA_MAX][8];
     grid_dep_wait();
     grid_dep_release();
+    if (ctl && !ctl->go) return;  // the device loop has ended
     if (ctl) {  // bookkeeping taken on the device
         slot = ctl->aa_slot;
         have_prev = ctl->aa_prev;
@@ -652,6 +658,7 @@ template <int M> __global__ void k_aa_solve_dev(const double *__restrict__ Gb, f
                                                 const LoopCtl *ctl) {
     grid_dep_wait();
     grid_dep_release();
+    if (!ctl->go) return;
     if (threadIdx.x == 0 && blockIdx.x == 0) aa_solve_rt<M>(Gb, theta, min(ctl->aa_ncol, M));
 }
 
@@ -663,6 +670,7 @@ __global__ void __launch_bounds__(256) k_aa_mix_dev(int n, const unsigned char *
                                                     const LoopCtl *ctl, int m) {
     grid_dep_wait();
     grid_dep_release();
+    if (!ctl->go) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int ncol = min(ctl->aa_ncol, m);
@@ -861,8 +869,26 @@ void launch_aa_device(cudaStream_t s, int n, const unsigned char *is_free, const
     PDC_LAUNCH_CK();
 }
 
-void aa_clear(cudaStream_t s, double *Gb) {
-    PDC_CK(cudaMemsetAsync(Gb, 0, sizeof(double) * (AA_MAX * (AA_MAX + 3) / 2 + AA_MAX), s));
+__global__ void k_live_zero(const int *live, unsigned int *p, size_t words) {
+    if (loop_dead(live)) return;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < words; k += (size_t)gridDim.x * blockDim.x)
+        p[k] = 0u;
+}
+
+void launch_live_zero(cudaStream_t s, const int *live, void *p, size_t bytes) {
+    if (!bytes) return;
+    if (!live) {
+        PDC_CK(cudaMemsetAsync(p, 0, bytes, s));
+        return;
+    }
+    const size_t words = bytes / 4;
+    const int blocks = (int)std::min<size_t>((words + 255) / 256, 152 * 8);
+    k_live_zero<<<blocks, 256, 0, s>>>(live, (unsigned int *)p, words);
+    PDC_LAUNCH_CK();
+}
+
+void aa_clear(cudaStream_t s, double *Gb, const int *live) {
+    launch_live_zero(s, live, Gb, sizeof(double) * (AA_MAX * (AA_MAX + 3) / 2 + AA_MAX));
 }
 
 void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out,

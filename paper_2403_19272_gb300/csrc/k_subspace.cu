@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(PROJ_T) k_project(SubspaceView S, const TU *__
                                                     const float4 *__restrict__ rl, const int *n_cv,
                                                     float *__restrict__ partial) {
     __shared__ float s_acc[PROJ_W][256 * 3];
+    if (loop_dead(S.live)) return;
     if (compact_active(S, n_cv)) return;
     int r = active_r(S, n_cv);
     if (r == 0) return;
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(PROJ_T) k_project_compact(SubspaceView S, cons
                                                             const float4 *__restrict__ rl, const int *n_cv,
                                                             float *__restrict__ partial) {
     __shared__ float s_acc[PROJ_W][128 * 3];
+    if (loop_dead(S.live)) return;
     if (!compact_active(S, n_cv)) return;
     constexpr int RPW = 32 / LPR;  // rows per warp and pass
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -203,6 +205,7 @@ template <class TU, int LPR>
 __global__ void __launch_bounds__(256) k_lift_compact(SubspaceView S, const TU *__restrict__ U, const int *n_cv,
                                                       const float *__restrict__ q, const float4 *__restrict__ din,
                                                       float4 *__restrict__ dout) {
+    if (loop_dead(S.live)) return;
     if (!compact_active(S, n_cv)) return;
     constexpr int RPW = 32 / LPR;
     int lane = threadIdx.x & 31;
@@ -256,6 +259,7 @@ __global__ void __launch_bounds__(256) k_lift_compact(SubspaceView S, const TU *
 // lanes stride over the blocks, shuffle reduction in double.
 __global__ void k_project_reduce(SubspaceView S, const int *n_cv, int nblocks, const float *__restrict__ partial,
                                  double *__restrict__ g, int only_with_contacts) {
+    if (loop_dead(S.live)) return;
     if (only_with_contacts && !(n_cv && *n_cv > 0)) return;  // the tensor-core reduction wrote g
     int r = active_r(S, n_cv);
     int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -272,6 +276,7 @@ __global__ void k_apply_inverse(SubspaceView S, const int *n_cv, const T *__rest
                                 float *__restrict__ q) {
     grid_dep_wait();
     grid_dep_release();
+    if (loop_dead(S.live)) return;
     if (n_cv && *n_cv > 0) return;
     int r = S.r_nc;
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -304,6 +309,7 @@ __global__ void __launch_bounds__(SYRK_T) k_syrk(SubspaceView S, const TU *__res
                                                  const int *n_cv, const float *__restrict__ cw, double *__restrict__ dA) {
     __shared__ double s_u[128];
     __shared__ double s_w;
+    if (loop_dead(S.live)) return;
     int nc = n_cv ? *n_cv : 0;
     int r = S.r_c;
     if (nc == 0 || r == 0) return;
@@ -341,6 +347,7 @@ __global__ void __launch_bounds__(256) k_chol_solve(SubspaceView S, const int *n
                                                     const double *__restrict__ g, float *__restrict__ q, int *flag) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_bad;
+    if (loop_dead(S.live)) return;
     if (!(n_cv && *n_cv > 0)) return;
     int r = S.r_c;
     if (r == 0) return;
@@ -404,6 +411,7 @@ __global__ void __launch_bounds__(256) k_lift(SubspaceView S, const TU *__restri
                                               const float *__restrict__ q, const float4 *__restrict__ din,
                                               float4 *__restrict__ dout) {
     __shared__ float s_q[256 * NCH * 3];
+    if (loop_dead(S.live)) return;
     if (compact_active(S, n_cv)) return;
     int r = active_r(S, n_cv);
     for (int e = threadIdx.x; e < 256 * NCH * 3; e += blockDim.x) s_q[e] = e < r * 3 ? q[e] : 0.f;
@@ -464,6 +472,7 @@ __global__ void __launch_bounds__(256) k_lift(SubspaceView S, const TU *__restri
 __global__ void __launch_bounds__(256) k_linear_residual(ClothView c, const float *__restrict__ cw,
                                                          const float4 *__restrict__ r, const float4 *__restrict__ d,
                                                          float4 *__restrict__ rl) {
+    if (loop_dead(c.live)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.n) return;
     float3 acc = make_float3(0.f, 0.f, 0.f);
@@ -529,7 +538,7 @@ bool device_path_choice(const SubspaceView &S) {
 void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, const int *n_cv, SubspaceWork &W,
                     bool maybe_contacts, bool device_choice) {
     if (!maybe_contacts && S.umma && S.r_nc > 0 && S.r_nc <= S.ld) {
-        launch_project_umma(s, *S.umma, S.r_nc, rl, S.umma_partial, W.g, S.dev_err, S.overlap != 0);
+        launch_project_umma(s, *S.umma, S.r_nc, rl, S.umma_partial, W.g, S.dev_err, S.overlap != 0, nullptr, S.live);
         return;
     }
     int mx = S.ld * 3 * 32;
@@ -537,7 +546,7 @@ void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, con
         // the iteration's contact-vertex count (device) picks the path: the
         // full basis on the tensor cores without springs, the compact basis
         // on the CUDA cores with them; each kernel of the other path returns
-        launch_project_umma(s, *S.umma, S.r_nc, rl, S.umma_partial, W.g, S.dev_err, S.overlap != 0, n_cv);
+        launch_project_umma(s, *S.umma, S.r_nc, rl, S.umma_partial, W.g, S.dev_err, S.overlap != 0, n_cv, S.live);
         with_basis(S, true, [&](auto *U) { project_compact_t(s, S, U, rl, n_cv, W.partial); });
         k_project_reduce<<<(mx + 255) / 256, 256, 0, s>>>(S, n_cv, PROJ_BLOCKS, W.partial, W.g, 1);
         PDC_LAUNCH_CK();
@@ -553,7 +562,7 @@ void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, con
 void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const int *n_cv, const float *cw,
                  SubspaceWork &W) {
     if (S.r_c == 0) return;
-    PDC_CK(cudaMemsetAsync(W.dA, 0, sizeof(double) * S.r_c * S.r_c, s));
+    launch_live_zero(s, S.live, W.dA, sizeof(double) * S.r_c * S.r_c);
     with_basis(S, false, [&](auto *U) {
         using TU = std::remove_const_t<std::remove_pointer_t<decltype(U)>>;
         int ne = S.r_c * S.r_c;
@@ -594,11 +603,11 @@ template <class TU> static void lift_t(cudaStream_t s, const SubspaceView &S, co
 void launch_lift(cudaStream_t s, const SubspaceView &S, const int *n_cv, const SubspaceWork &W, const float4 *din,
                  float4 *dout, bool maybe_contacts, bool device_choice) {
     if (!maybe_contacts && S.umma && S.r_nc > 0 && S.r_nc <= S.ld) {
-        launch_lift_umma(s, *S.umma, S.r_nc, W.q, din, dout, S.dev_err, S.overlap != 0);
+        launch_lift_umma(s, *S.umma, S.r_nc, W.q, din, dout, S.dev_err, S.overlap != 0, nullptr, S.live);
         return;
     }
     if (maybe_contacts && device_choice && device_path_choice(S)) {  // as in launch_project
-        launch_lift_umma(s, *S.umma, S.r_nc, W.q, din, dout, S.dev_err, S.overlap != 0, n_cv);
+        launch_lift_umma(s, *S.umma, S.r_nc, W.q, din, dout, S.dev_err, S.overlap != 0, n_cv, S.live);
         if (S.n > 0) with_basis(S, true, [&](auto *U) { lift_compact_t(s, S, U, n_cv, W.q, din, dout); });
         PDC_LAUNCH_CK();
         return;

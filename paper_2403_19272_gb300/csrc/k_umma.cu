@@ -210,7 +210,7 @@ template <bool F16>
 __global__ void __launch_bounds__(PTHREADS, 1) k_lift_umma_p(const __grid_constant__ CUtensorMap mapU, int n, int ld,
                                                             int r, const float *__restrict__ q,
                                                             const float4 *__restrict__ din, float4 *__restrict__ dout,
-                                                            int *err, const int *skip_if) {
+                                                            int *err, const int *skip_if, const int *live) {
     LiftPSmem &S = smem_1024<LiftPSmem>();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nkb = ld / KBOX;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_lift_umma_p(const __grid_consta
     grid_dep_release();
     // the lift of an iteration with collision springs runs on the compact
     // basis instead (skip_if: that iteration's contact-vertex count)
-    if (skip_if && *skip_if > 0) mine = 0;
+    if ((skip_if && *skip_if > 0) || loop_dead(live)) mine = 0;
     // B = q split into hi / lo parts, [16][ld], fixed for all tiles
     float qmax = 0.f;
     for (int e = tid; e < 3 * r; e += blockDim.x) qmax = fmaxf(qmax, fabsf(q[e]));
@@ -334,7 +334,7 @@ template <bool F16>
 __global__ void __launch_bounds__(PTHREADS, 1) k_project_umma_p(const __grid_constant__ CUtensorMap mapUt, int n,
                                                                int ld, int r, const float4 *__restrict__ rl,
                                                                float *__restrict__ partial, int *err,
-                                                               const int *skip_if) {
+                                                               const int *skip_if, const int *live) {
     ProjPSmem &S = smem_1024<ProjPSmem>();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nh = ld / TILE;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_project_umma_p(const __grid_con
     grid_dep_wait();
     grid_dep_release();
     // an iteration with collision springs projects on the compact basis instead
-    if (skip_if && *skip_if > 0) mine = 0;
+    if ((skip_if && *skip_if > 0) || loop_dead(live)) mine = 0;
     // one scale for all of this CTA's rows (its accumulator sums them all)
     float vmax = 0.f;
     for (int k = 0; k < mine; ++k) {
@@ -480,10 +480,10 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_project_umma_p(const __grid_con
 }
 
 __global__ void k_umma_reduce(int r, int ld, int nblocks, const float *__restrict__ partial, double *__restrict__ g,
-                              const int *skip_if) {
+                              const int *skip_if, const int *live) {
     grid_dep_wait();
     grid_dep_release();
-    if (skip_if && *skip_if > 0) return;
+    if ((skip_if && *skip_if > 0) || loop_dead(live)) return;
     int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= r * 3) return;
     double s = 0.0;
@@ -550,31 +550,31 @@ void umma_setup(UmmaMaps &M, const void *U, const void *Ut, bool f16, int n, int
 int umma_project_blocks(int n) { return (n + TILE - 1) / TILE; }
 
 void launch_project_umma(cudaStream_t s, const UmmaMaps &M, int r, const float4 *rl, float *partial, double *g,
-                         int *err, bool overlap, const int *skip_if) {
+                         int *err, bool overlap, const int *skip_if, const int *live) {
     const int nb = std::max(1, std::min(M.sms, umma_project_blocks(M.n)));
     if (M.f16)
         launch_dependent(overlap, k_project_umma_p<true>, nb, PTHREADS, proj_p_smem(), s, M.mapUt, M.n, M.ld, r, rl,
-                         partial, err, skip_if);
+                         partial, err, skip_if, live);
     else
         launch_dependent(overlap, k_project_umma_p<false>, nb, PTHREADS, proj_p_smem(), s, M.mapUt, M.n, M.ld, r, rl,
-                         partial, err, skip_if);
+                         partial, err, skip_if, live);
     PDC_LAUNCH_CK();
     int thr = r * 3 * 32;
     launch_dependent(overlap, k_umma_reduce, (thr + 255) / 256, 256, 0, s, r, M.ld, nb, (const float *)partial, g,
-                     skip_if);
+                     skip_if, live);
     PDC_LAUNCH_CK();
 }
 
 void launch_lift_umma(cudaStream_t s, const UmmaMaps &M, int r, const float *q, const float4 *din, float4 *dout,
-                      int *err, bool overlap, const int *skip_if) {
+                      int *err, bool overlap, const int *skip_if, const int *live) {
     const int nt = (M.n + TILE - 1) / TILE;
     const int nb = std::max(1, std::min(M.sms, nt));
     if (M.f16)
         launch_dependent(overlap, k_lift_umma_p<true>, nb, PTHREADS, lift_p_smem(), s, M.mapU, M.n, M.ld, r, q, din,
-                         dout, err, skip_if);
+                         dout, err, skip_if, live);
     else
         launch_dependent(overlap, k_lift_umma_p<false>, nb, PTHREADS, lift_p_smem(), s, M.mapU, M.n, M.ld, r, q, din,
-                         dout, err, skip_if);
+                         dout, err, skip_if, live);
     PDC_LAUNCH_CK();
 }
 

@@ -147,7 +147,12 @@ struct ClothView {
     float4 *corner;        // scratch [3m + 4nh]: per-element corner forces of the residual
     int res_block;         // threads per block of the residual kernels (64, 128 or 256)
     int cheb_plain;        // 1: Chebyshev steps read the ELL arrays directly, not the tiles
+    const int *live;       // device loop flag: the kernels do nothing when *live == 0 (NULL: always run)
 };
+
+// A kernel of an LG iteration of a device-driven loop does nothing once the
+// loop has ended (*live == 0); read after grid_dep_wait().
+__device__ __forceinline__ bool loop_dead(const int *live) { return live && *(const volatile int *)live == 0; }
 
 constexpr int ELL_TILE_ROWS = 256;
 inline size_t ell_tile_bytes(int tw) { return (size_t)tw * ELL_TILE_ROWS * 6; }
@@ -164,6 +169,7 @@ struct CollView {
     const int2 *edge;      // [ne] (a < b)
     const unsigned char *vfixed; // [nv] 1: infinite mass (obstacle or pinned)
     unsigned int *guard;   // the handle's index-guard word (GuardBits), or NULL
+    const int *live;       // device loop flag (see loop_dead), or NULL
     // per-instance line search (batched form): instance of each collision
     // vertex (-1: none) and per-instance minimum time of impact (double bits);
     // NULL when the union takes one step fraction
@@ -236,7 +242,10 @@ void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4
 void launch_aa_device(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x,
                       float4 *fprev, float4 *gprev, float4 *dF, float4 *dG, int m, const LoopCtl *ctl, double *Gb,
                       float *theta, const float4 *xs, float4 *xabs, bool overlap);
-void aa_clear(cudaStream_t s, double *Gb);
+void aa_clear(cudaStream_t s, double *Gb, const int *live = nullptr);
+// Zeroes `bytes` (a multiple of 4) at p unless *live == 0; with live NULL a
+// plain stream memset.
+void launch_live_zero(cudaStream_t s, const int *live, void *p, size_t bytes);
 // out = a + s (b - a) with s = *s_frac, or with vinst (per-instance line
 // search) s_inst[vinst[i]] for vertices of an instance (vinst[i] >= 0)
 void launch_lerp(cudaStream_t s, int nv, const float4 *a, const float4 *b, const double *s_frac, float4 *out,

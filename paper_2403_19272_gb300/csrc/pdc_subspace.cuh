@@ -31,6 +31,7 @@ struct SubspaceView {
     float *umma_partial;       // [tiles][ld][3]
     int *dev_err;              // status word receiving PDC_DEVERR_UMMA
     int overlap;               // tensor-core path: launch as programmatic dependents
+    const int *live;           // device loop flag (see loop_dead), or NULL
 };
 
 struct SubspaceWork {

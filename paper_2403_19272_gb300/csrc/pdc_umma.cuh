@@ -32,11 +32,12 @@ int umma_project_blocks(int n);
 // With overlap, the kernels are launched as programmatic dependents of the
 // kernel before them (barrier setup and TMEM allocation overlap its tail).
 // skip_if (device, may be NULL): the kernels do nothing when *skip_if > 0
-// (an iteration whose collision springs use the compact basis instead).
+// (an iteration whose collision springs use the compact basis instead);
+// live (may be NULL): nor once a device-driven loop has ended (*live == 0).
 void launch_project_umma(cudaStream_t s, const UmmaMaps &M, int r, const float4 *rl, float *partial, double *g,
-                         int *err, bool overlap = false, const int *skip_if = nullptr);
+                         int *err, bool overlap = false, const int *skip_if = nullptr, const int *live = nullptr);
 // dout = din + U[:, :r] q (din may be NULL).
 void launch_lift_umma(cudaStream_t s, const UmmaMaps &M, int r, const float *q, const float4 *din, float4 *dout,
-                      int *err, bool overlap = false, const int *skip_if = nullptr);
+                      int *err, bool overlap = false, const int *skip_if = nullptr, const int *live = nullptr);
 
 }  // namespace pdc

@@ -43,7 +43,8 @@ class pdc_params(ctypes.Structure):
                 ("cheb_ratio", c_dbl), ("aa_depth", c_i32),
                 ("tensor_cores", c_i32), ("bp_reuse", c_dbl), ("launch_overlap", c_i32),
                 ("rf_toi", c_dbl), ("rf_iters", c_i32), ("graph_loops", c_i32), ("pccd_adaptive", c_i32),
-                ("pccd_max_axis", c_i32), ("instance_line_search", c_i32), ("autotune", c_i32)]
+                ("pccd_max_axis", c_i32), ("instance_line_search", c_i32), ("autotune", c_i32),
+                ("graph_unroll", c_i32)]
 
 
 class pdc_stats(ctypes.Structure):
@@ -88,6 +89,7 @@ SIGNATURES = {
     "pdc_get_displacement": (c_i32, [P, P, c_i32]),
     "pdc_get_stats": (c_i32, [P, P]),
     "pdc_get_tuning": (c_i32, [P, P]),
+    "pdc_get_pairs": (c_i32, [P, P, P, P, c_i64, P]),
     "pdc_destroy": (None, [P]),
     "pdc_measure_copy_bandwidth": (c_i32, [c_i64, c_i32, P, P]),
     "pdc_last_error": (ctypes.c_char_p, [P]),
@@ -279,6 +281,18 @@ def pdc_get_stats(h) -> dict:
     s = pdc_stats()
     _check(h, lib().pdc_get_stats(h, ctypes.byref(s)))
     return s.as_dict()
+
+
+def pdc_get_pairs(h):
+    """(prim [k,2] int32, kinds [k] int32, state [k] uint8) of the last step's candidate pairs."""
+    cnt = c_i64()
+    _check(h, lib().pdc_get_pairs(h, None, None, None, 0, ctypes.byref(cnt)))
+    k = cnt.value
+    prim = np.empty((max(k, 1), 2), np.int32)
+    kinds = np.empty(max(k, 1), np.int32)
+    state = np.empty(max(k, 1), np.uint8)
+    _check(h, lib().pdc_get_pairs(h, _ptr(prim), _ptr(kinds), _ptr(state), k, ctypes.byref(cnt)))
+    return prim[:k].copy(), kinds[:k].copy(), state[:k].copy()
 
 
 def pdc_get_tuning(h) -> dict:

@@ -55,8 +55,37 @@ def thrown_drape(side, vz=-20.0, subdiv=2):
     return dataclasses.replace(sc, v0=v0.astype(np.float32))
 
 
-def run_parity(pc, sc, gp, op, steps, check_active=True):
-    """Steps GPU and oracle from identical states; returns per-step records."""
+# A partial-CCD decision whose activity margin lies within rounding of zero
+# may go either way between the FP32 GPU and the FP64 oracle (the positions
+# it is taken on differ by ~1e-7 of their size, and resting contacts sit on
+# the threshold: their springs drive the pair onto the gap).  After each step
+# the GPU's constraint set (pdc_get_pairs: every candidate's activity and
+# life-span counter a) is compared with the oracle's pair by pair; a step
+# where they differ only on pairs the oracle saw within AMBIGUOUS_MARGIN of
+# the threshold is excluded from the position check (both restart from the
+# GPU's state), and any other difference fails.
+AMBIGUOUS_MARGIN = 1e-6
+
+
+def gpu_constraints(pc, cl, cm):
+    prim, kinds, st = pc.pdc_get_pairs(cl.h)
+    out = {}
+    for (p, q), k, s in zip(prim.tolist(), kinds.tolist(), st.tolist()):
+        if not (s & 0x80):
+            continue
+        if k == 0:
+            key = ("vt", p, q)
+        else:
+            a, b = cm.edges[p]
+            c, d = cm.edges[q]
+            key = ("ee", int(a), int(b), int(c), int(d))
+        out[key] = (True, s & 0x7F)
+    return out
+
+
+def run_parity(pc, sc, gp, op, steps, max_flipped=1):
+    """Steps GPU and oracle from identical states; per step, the constraint
+    sets (with their counters) and positions agree; returns records."""
     cl = pc.Cloth(sc, gp)
     orc = pd.Oracle(sc, op)
     recs = []
@@ -67,16 +96,22 @@ def run_parity(pc, sc, gp, op, steps, check_active=True):
             xo, vo, st = orc.step(trace=tr)
             xg, vg = cl.state()
             sg = cl.stats()
+            cg = gpu_constraints(pc, cl, orc.cm)
+            co = st.constraints
+            diff = {q for q in set(cg) | set(co) if cg.get(q) != co.get(q)}
+            amb = {q for rec in tr for q, m in rec["margins"].items() if abs(m) <= AMBIGUOUS_MARGIN}
             err = float(np.max(np.abs(xg - xo)))
-            amax = max([0] + [a for rec in tr for _, a in rec["state"].values()])
-            recs.append(dict(err=err, L=orc.model.L, n_act_g=sg["n_active"], n_act_o=st.n_active, amax=amax,
-                             contact_iters=sg["contact_iters"], t_toi=sg["t_toi"]))
-            assert err <= 1e-5 * orc.model.L, (k, recs[-1])
-            if check_active:
+            amax = max([0] + [a for _, a in co.values()])
+            recs.append(dict(err=err, L=orc.model.L, n_act_g=len(cg), n_act_o=len(co), amax=amax,
+                             contact_iters=sg["contact_iters"], t_toi=sg["t_toi"], flipped=len(diff)))
+            assert diff <= amb, (k, sorted(diff - amb)[:5], recs[-1])
+            if not diff:
+                assert err <= 1e-5 * orc.model.L, (k, recs[-1])
                 assert sg["n_active"] == st.n_active, (k, recs[-1])
             orc.x, orc.v = xg.astype(np.float64), vg.astype(np.float64)
     finally:
         cl.close()
+    assert sum(1 for r in recs if r["flipped"]) <= max_flipped, recs
     return recs
 
 
@@ -108,9 +143,10 @@ def test_ndb_life_span_over_eight_inner_iterations(pc):
     gp = params(pc, fixed_iters=1, warm_iters=2, max_outer=1, max_inner=8, solve_cycles=40, jacobi_sweeps=8,
                 r_warm=64, r_reuse=64, d_hat=1e-3)
     op = pd.Params(fixed_iters=True, warm_iters=2, max_outer=1, max_inner=8, dhat=1e-3)
-    recs = run_parity(pc, sc, gp, op, 4)
-    assert max(r["amax"] for r in recs) >= 5, recs
-    assert max(r["n_act_g"] for r in recs) > 0
+    recs = run_parity(pc, sc, gp, op, 6, max_flipped=2)
+    exact = [r for r in recs if not r["flipped"]]
+    assert len(exact) >= 4 and max(r["amax"] for r in exact) >= 5, recs
+    assert max(r["n_act_g"] for r in exact) > 0
 
 
 @pytest.mark.parametrize("precision", [2, 1, 0])
