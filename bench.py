@@ -56,6 +56,7 @@ def parse():
                     help="1: Chebyshev steps launched as programmatic dependents (default)")
     ap.add_argument("--graph-loops", type=int, default=1, choices=[0, 1],
                     help="1: LG loops as CUDA graphs with device-side stopping tests (default); 0: host-driven")
+    ap.add_argument("--graph-unroll", type=int, default=4, help="LG iterations per pass of a graph loop (1..8)")
     ap.add_argument("--no-launch-count", action="store_true",
                     help="skip the CUDA activity trace (e.g. when running under ncu)")
     return ap.parse_args()
@@ -66,9 +67,10 @@ FORMS = {"mixed16": 2, "mixed": 1, "fp32": 0}
 DTYPES = {"mixed16": "f16+f32+f64", "mixed": "bf16+f32+f64", "fp32": "f32"}
 
 
-def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1, graph_loops=1):
+def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1, graph_loops=1, graph_unroll=4):
     p = pc.pdc_default_params()
     p.graph_loops = graph_loops  # LG loops as CUDA graphs (stopping tests on the device)
+    p.graph_unroll = graph_unroll
     p.launch_overlap = overlap  # Chebyshev steps as programmatic dependent launches
     p.tol_rel_residual = 1e-3
     p.max_outer = 2
@@ -158,11 +160,11 @@ class ClockSampler:
 
 
 def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True, sweeps=28, cheb_ratio=300.0,
-             overlap=1, graph_loops=1):
+             overlap=1, graph_loops=1, graph_unroll=4):
     """Warm-up, timed region (device), profiled replay, e2e through host buffers."""
     import numpy as np
     stream = torch.cuda.Stream()
-    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap, graph_loops)
+    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap, graph_loops, graph_unroll)
     t_setup = time.time()
     h = pc.pdc_create(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend, p,
                       stream.cuda_stream)
@@ -642,7 +644,8 @@ def main():
     forms = {}
     for f in a.forms.split(","):
         forms[f] = run_form(pc, torch, scene, FORMS[f], a.steps, a.warmup, local,
-                            not a.no_launch_count, a.sweeps, a.cheb_ratio, a.launch_overlap, a.graph_loops)
+                            not a.no_launch_count, a.sweeps, a.cheb_ratio, a.launch_overlap, a.graph_loops,
+                            a.graph_unroll)
     head = list(forms)[0]
     ms = forms[head]["ms"]
     ms = max_over_ranks(ms, f"cuda:{local}")
