@@ -54,9 +54,10 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form comparison")
     ap.add_argument("--launch-overlap", type=int, default=1, choices=[0, 1],
                     help="1: Chebyshev steps launched as programmatic dependents (default)")
-    ap.add_argument("--graph-loops", type=int, default=1, choices=[0, 1],
-                    help="1: LG loops as CUDA graphs with device-side stopping tests (default); 0: host-driven")
-    ap.add_argument("--graph-unroll", type=int, default=4, help="LG iterations per pass of a graph loop (1..8)")
+    ap.add_argument("--loop-control", type=int, default=2, choices=[0, 1, 2],
+                    help="stopping tests of the LG loops: 2 on the device, host enqueues ahead (default); "
+                         "1 on the device in a CUDA graph while loop; 0 on the host")
+    ap.add_argument("--graph-unroll", type=int, default=1, help="LG iterations per pass of a graph loop (1..8)")
     ap.add_argument("--no-launch-count", action="store_true",
                     help="skip the CUDA activity trace (e.g. when running under ncu)")
     return ap.parse_args()
@@ -67,9 +68,9 @@ FORMS = {"mixed16": 2, "mixed": 1, "fp32": 0}
 DTYPES = {"mixed16": "f16+f32+f64", "mixed": "bf16+f32+f64", "fp32": "f32"}
 
 
-def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1, graph_loops=1, graph_unroll=4):
+def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1, loop_control=2, graph_unroll=1):
     p = pc.pdc_default_params()
-    p.graph_loops = graph_loops  # LG loops as CUDA graphs (stopping tests on the device)
+    p.loop_control = loop_control  # stopping tests of the LG loops on the device
     p.graph_unroll = graph_unroll
     p.launch_overlap = overlap  # Chebyshev steps as programmatic dependent launches
     p.tol_rel_residual = 1e-3
@@ -160,11 +161,11 @@ class ClockSampler:
 
 
 def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True, sweeps=28, cheb_ratio=300.0,
-             overlap=1, graph_loops=1, graph_unroll=4):
+             overlap=1, loop_control=2, graph_unroll=1):
     """Warm-up, timed region (device), profiled replay, e2e through host buffers."""
     import numpy as np
     stream = torch.cuda.Stream()
-    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap, graph_loops, graph_unroll)
+    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap, loop_control, graph_unroll)
     t_setup = time.time()
     h = pc.pdc_create(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend, p,
                       stream.cuda_stream)
@@ -249,7 +250,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
                 rel_res=statistics.mean(s["rel_residual"] for s in st_list),
                 cand=statistics.mean(s["n_candidates"] for s in st_list),
                 toi=min(s["t_toi"] for s in st_list), finite=bool(np.isfinite(x).all()),
-                graph_loops=statistics.mean(s["graph_loops"] for s in st_list), device_busy=busy, idle_gaps=gaps,
+                device_loops=statistics.mean(s["device_loops"] for s in st_list), device_busy=busy, idle_gaps=gaps,
                 launches=launches)
 
 
@@ -308,7 +309,7 @@ def run_batched(pc, torch, steps=5, warmup=2, dev_index=0):
     torch.cuda.synchronize()
     ms_b = e0.elapsed_time(e1) / steps
     tuning = pc.pdc_get_tuning(h)
-    gl = pc.pdc_get_stats(h)["graph_loops"]
+    gl = pc.pdc_get_stats(h)["device_loops"]
     pc.pdc_destroy(h)
     # the same cloths on separate handles, stepped in turn on one stream
     t0 = time.time()
@@ -337,7 +338,7 @@ def run_batched(pc, torch, steps=5, warmup=2, dev_index=0):
             "instances": len(shifted), "vertices": int(off[-1]), "steps": steps,
             "ms_per_step_batched": round(ms_b, 3), "ms_per_step_separate_handles": round(ms_s, 3),
             "speedup": round(ms_s / ms_b, 2), "setup_s_batched": round(setup_b, 1),
-            "setup_s_separate": round(setup_s, 1), "graph_loops_per_step": gl,
+            "setup_s_separate": round(setup_s, 1), "device_loops_per_step": gl,
             "line_search": "per instance", "tuning": tuning}
 
 
@@ -644,7 +645,7 @@ def main():
     forms = {}
     for f in a.forms.split(","):
         forms[f] = run_form(pc, torch, scene, FORMS[f], a.steps, a.warmup, local,
-                            not a.no_launch_count, a.sweeps, a.cheb_ratio, a.launch_overlap, a.graph_loops,
+                            not a.no_launch_count, a.sweeps, a.cheb_ratio, a.launch_overlap, a.loop_control,
                             a.graph_unroll)
     head = list(forms)[0]
     ms = forms[head]["ms"]
@@ -665,7 +666,7 @@ def main():
                       "vertex_iters_per_s": round(scene.n * d["iters"] / (d["ms"] * 1e-3), 1),
                       "gpu_launches": d["launches"],
                       "rel_residual": d["rel_res"], "candidates": d["cand"], "min_toi": d["toi"],
-                      "graph_loops_per_step": d["graph_loops"], "device_busy": d["device_busy"],
+                      "device_loops_per_step": d["device_loops"], "device_busy": d["device_busy"],
                       "setup_s": round(d["setup_s"], 2), "e2e_ms_per_step": round(d["e2e_ms"], 3)}
                   for f, d in forms.items()},
         "roofline": rl,

@@ -147,18 +147,22 @@ typedef struct {
     int32_t rf_iters;        /* cap on those iterations (exact count when
                                 fixed_iters = 1); they stop once the largest
                                 change is below tol_inner * bbox diagonal       */
-    int32_t graph_loops;     /* 1 (default): each LG loop of a step (warm start,
-                                inner loops) runs as one CUDA graph launch whose
-                                conditional while node repeats the iteration
-                                until a one-thread kernel on the device ends it
-                                with the host loop's tests (relative residual,
-                                stagnation, step change, iteration cap): no
-                                host synchronisation per iteration.  0, or
-                                while profiling (pdc_set_profiling), PDC_LOG or
-                                PDC_SYNC_CHECK, or with accel = 1: the host
-                                reads each iteration's residual back and
-                                decides.  Same kernels in the same order either
-                                way.                                              */
+    int32_t loop_control;    /* who takes the stopping tests of the LG loops
+                                (warm start, inner loops): the relative
+                                residual, stagnation, step-change and cap tests.
+                                2 (default): a one-thread kernel on the device
+                                after each residual; the host enqueues the
+                                iterations ahead (at most 2 in flight) and reads
+                                the decisions from host-mapped memory, with no
+                                stream synchronisation per iteration; kernels
+                                enqueued past the loop's end return at once.
+                                1: the same device tests, the loop run as one
+                                CUDA graph whose conditional while node repeats
+                                the iteration (graph_unroll per pass).  0: the
+                                host reads each iteration's residual back and
+                                decides (also while profiling, with PDC_LOG or
+                                PDC_SYNC_CHECK, or with accel = 1).  Same
+                                kernels in the same order in every mode.        */
     int32_t pccd_adaptive;   /* 1: the partial CCD tests, instead of the fixed
                                 samples_vt / samples_ee patterns, the t = 0
                                 closest point and a lattice of spacing 1/m over
@@ -184,10 +188,12 @@ typedef struct {
                                 pdc_tuning); results do not depend on the
                                 choice beyond the order of float atomics.  0
                                 (default): fixed shapes                          */
-    int32_t graph_unroll;    /* LG iterations per pass of a graph loop's while
-                                node (1..8, default 4): each pass relaunches its
-                                body on the device; the kernels of iterations
-                                after the loop's end return at once             */
+    int32_t graph_unroll;    /* loop_control = 1: LG iterations per pass of the
+                                while node (1..8, default 1): each pass
+                                relaunches its body on the device, at a cost
+                                that grows with the body's node count; the
+                                kernels of iterations after the loop's end
+                                return at once                                   */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
@@ -210,8 +216,8 @@ typedef struct {
                                     the step's first broad phase (bp_reuse)      */
     int32_t rf_iters;            /* residual-forwarding LG iterations run at the
                                     end of this step (0: not triggered)          */
-    int32_t graph_loops;         /* LG loops of this step that ran as one graph
-                                    launch (graph_loops parameter)               */
+    int32_t device_loops;        /* LG loops of this step whose stopping tests
+                                    ran on the device (loop_control 1 or 2)      */
 } pdc_stats;
 
 /* Launch shapes in use and, after an autotuned first step, the measured
@@ -235,7 +241,7 @@ typedef struct {
  * iterations, 4 damped Jacobi sweeps (automatic omega), 1 cycle, no basis,
  * FP32, samples 3/4, collisions on, no LG acceleration, tensor cores for the
  * mixed forms, dependent launches on, broad-phase reuse and residual
- * forwarding off, LG loops as CUDA graphs. */
+ * forwarding off, LG-loop tests on the device (loop_control 2). */
 void pdc_default_params(pdc_params *p);
 
 /* Build the solver for one cloth mesh (Sec. 3; Eq. (global) rest matrix,

@@ -159,7 +159,7 @@ __global__ void k_loop_step_init(LoopCtl *c, const Scalars *sc) {
     c->rho0 = sqrt(sc->rsq);
     c->rel = 0.0;
     c->warm_iters = c->inner_iters = c->contact_iters = 0;
-    c->graph_loops = 0;
+    c->device_loops = 0;
 }
 
 // At the start of a loop (the host-driven loop resets its Accel state here).
@@ -173,7 +173,7 @@ __global__ void k_loop_begin(LoopCtl *c, int graph) {
     c->aa_hist_n = 0;
     c->aa_count = c->aa_widx = c->aa_have_prev = 0;
     c->aa_slot = c->aa_prev = c->aa_ncol = 0;
-    if (graph) c->graph_loops++;
+    if (graph) c->device_loops++;
 }
 
 // The loop's decision after the residual of the current iterate (and, with
@@ -184,13 +184,9 @@ __global__ void k_loop_begin(LoopCtl *c, int graph) {
 // graph's condition), and go = 1 only while iters < max_iters, so a graph
 // loop ends after at most max_iters iterations; a device error bit (a
 // bounded wait that ran out) ends it at once.
-__global__ void k_loop_decide(LoopCtl *c, LoopCfg f, const Scalars *sc, const int *n_cv, const int *dev_err,
-                              int after_solve) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (after_solve && !c->go) {  // an earlier iteration of this pass ended the loop
-        if (f.use_cond) cudaGraphSetConditional(f.cond, 0u);
-        return;
-    }
+__device__ int loop_decide(LoopCtl *c, const LoopCfg &f, const Scalars *sc, const int *n_cv, const int *dev_err,
+                           int after_solve) {
+    if (after_solve && !c->go) return 0;  // an earlier iteration of this pass ended the loop
     int go = (*dev_err & (PDC_DEVERR_UMMA | PDC_DEVERR_COPY)) ? 0 : 1;
     const double dx = (double)__uint_as_float(sc->dxmax);
     if (go && after_solve) {
@@ -240,8 +236,36 @@ __global__ void k_loop_decide(LoopCtl *c, LoopCfg f, const Scalars *sc, const in
         }
     }
     c->go = go;
-    if (f.use_cond) cudaGraphSetConditional(f.cond, go ? 1u : 0u);
+    return go;
 }
+
+// Two kernels: only the decision that ends a pass of the while node sets its
+// condition (a kernel that calls into the device runtime costs more to
+// complete, so the other decisions of an unrolled pass do without).
+__global__ void k_loop_decide(LoopCtl *c, LoopCfg f, const Scalars *sc, const int *n_cv, const int *dev_err,
+                              int after_solve) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) loop_decide(c, f, sc, n_cv, dev_err, after_solve);
+}
+// The decision of a loop whose iterations the host enqueues ahead: go and
+// the number of decisions taken so far go to host-mapped memory (read there
+// without a stream synchronisation).
+__global__ void k_loop_decide_host(LoopCtl *c, LoopCfg f, const Scalars *sc, const int *n_cv, const int *dev_err,
+                                   int after_solve, volatile int *host) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int go = loop_decide(c, f, sc, n_cv, dev_err, after_solve);
+    host[0] = go;
+    __threadfence_system();
+    host[1] = host[1] + 1;
+    __threadfence_system();
+}
+__global__ void k_loop_decide_cond(LoopCtl *c, LoopCfg f, const Scalars *sc, const int *n_cv, const int *dev_err,
+                                   int after_solve) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int go = loop_decide(c, f, sc, n_cv, dev_err, after_solve);
+    cudaGraphSetConditional(f.cond, go ? 1u : 0u);
+}
+
+
 
 inline int nb(long long n) { return (int)((n + 255) / 256); }
 inline float bits_to_float(unsigned int u) {
@@ -475,6 +499,7 @@ struct pdc_ctx {
 
     ~pdc_ctx() {
         if (hsc) cudaFreeHost(hsc);
+        if (hmap) cudaFreeHost((void *)hmap);
         for (auto &G : gl) free_graph(G);
         if (gs) cudaStreamDestroy(gs);
     }
@@ -623,6 +648,10 @@ struct pdc_ctx {
     bool build_loop(GraphLoop &G, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
                     bool pccd);
     bool run_loop(int gi, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps, bool pccd);
+    // loop_control = 2: host-mapped {go, decisions} of the loop being run
+    volatile int *hmap = nullptr;
+    int *hmap_dev = nullptr;
+    void run_loop_ahead(const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps, bool pccd);
     void residual_forwarding();
     void full_ccd(const float4 *x0, const float4 *x1, bool merge);
     void broad_phase_pass(const float4 *x0, const float4 *x1, bool super);
@@ -1415,7 +1444,8 @@ void pdc_ctx::lg_iteration(bool contacts, bool check_rel, double rho0, bool &con
 // buffer addresses and the list index bp.cur, so it is rebuilt when either
 // changes (graph_gen counts reallocations).
 bool pdc_ctx::device_loops_ok() const {
-    if (P.graph_loops == 0 || graphs_failed || prof.on || log || sync_check) return false;
+    if (P.loop_control == 0 || prof.on || log || sync_check) return false;
+    if (P.loop_control == 1 && graphs_failed) return false;
     if (P.accel == 1 && P.fixed_iters == 0) return false;  // Chebyshev acceleration: host-side weights
     // a spring iteration of the mixed form chooses between the tensor-core and
     // the compact path on the device only when the compact copy covers r_reuse
@@ -1454,7 +1484,10 @@ bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r
     if (!gs) PDC_CK(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
     cudaStream_t saved = s;
     s = gs;  // everything below is captured from the capture stream
-    live_ptr = &ctl.p->go;  // the captured iterations do nothing once the loop has ended
+    // unrolled: the captured iterations do nothing once the loop has ended (a
+    // single iteration per pass always runs: the while node checked go)
+    const int unroll = std::min(std::max(P.graph_unroll, 1), 8);
+    live_ptr = unroll > 1 ? &ctl.p->go : nullptr;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t e = nullptr;
     bool capturing = false;
@@ -1472,7 +1505,7 @@ bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r
         k_loop_begin<<<1, 1, 0, s>>>(ctl, 1);
         PDC_LAUNCH_CK();
         enqueue_residual(contacts);
-        k_loop_decide<<<1, 1, 0, s>>>(ctl, cfg, sc, n_cv_d, sflag, 0);
+        k_loop_decide_cond<<<1, 1, 0, s>>>(ctl, cfg, sc, n_cv_d, sflag, 0);
         PDC_LAUNCH_CK();
         const cudaGraphNode_t *deps = nullptr;
         size_t nd = 0;
@@ -1497,13 +1530,13 @@ bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r
         // relaunch of the body on the device): the kernels of an iteration that
         // follows the end of the loop read go = 0 and return at once, and only
         // the last decision of the pass sets the while condition
-        const int unroll = std::min(std::max(P.graph_unroll, 1), 8);
         for (int u = 0; u < unroll; ++u) {
             LoopCfg cu = cfg;
             cu.use_cond = u == unroll - 1 ? 1 : 0;
             enqueue_solve(contacts, contacts, true, 1.f, r_nc, r_c, cycles, sweeps, pccd);
             enqueue_residual(contacts);
-            k_loop_decide<<<1, 1, 0, s>>>(ctl, cu, sc, n_cv_d, sflag, 1);
+            if (cu.use_cond) k_loop_decide_cond<<<1, 1, 0, s>>>(ctl, cu, sc, n_cv_d, sflag, 1);
+            else k_loop_decide<<<1, 1, 0, s>>>(ctl, cu, sc, n_cv_d, sflag, 1);
             PDC_LAUNCH_CK();
         }
         cudaGraph_t b2 = nullptr;
@@ -1531,11 +1564,16 @@ bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r
     return true;
 }
 
-// Runs one LG loop as a graph launch on s (builds or rebuilds the graph when
-// needed).  False when the graph cannot be built: the caller then runs the
-// host-driven loop.
+// Runs one LG loop with its tests on the device: enqueued ahead of the
+// device's decisions (loop_control 2), or as a graph launch on s (1; the
+// graph is built or rebuilt when needed).  False when the graph cannot be
+// built: the caller then runs the host-driven loop.
 bool pdc_ctx::run_loop(int gi, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
                        bool pccd) {
+    if (P.loop_control == 2) {
+        run_loop_ahead(cfg, contacts, r_nc, r_c, cycles, sweeps, pccd);
+        return true;
+    }
     GraphLoop &G = gl[gi];
     if (!G.e || G.gen != graph_gen + bp.gen) {
         // programmatic dependent launches inside the graph when the driver
@@ -1556,6 +1594,58 @@ bool pdc_ctx::run_loop(int gi, const LoopCfg &cfg, bool contacts, int r_nc, int 
     }
     PDC_CK(cudaGraphLaunch(G.e, s));
     return true;
+}
+
+// loop_control = 2: the host enqueues the loop's iterations (residual part,
+// device decision, solve part) on s, each kernel returning at once after the
+// loop's end, and runs at most AHEAD iterations ahead of the device's
+// decisions, which it reads from host-mapped memory: the device never waits
+// for the host between iterations, and no stream synchronisation is needed.
+// The wait for the device is bounded (a stream synchronisation after
+// AHEAD_TIMEOUT, then the decisions are read from device memory).
+void pdc_ctx::run_loop_ahead(const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
+                             bool pccd) {
+    constexpr int AHEAD = 2;
+    constexpr double AHEAD_TIMEOUT_S = 30.0;
+    if (!hmap) {
+        void *p = nullptr;
+        PDC_CK(cudaHostAlloc(&p, 2 * sizeof(int), cudaHostAllocMapped));
+        hmap = (volatile int *)p;
+        PDC_CK(cudaHostGetDevicePointer((void **)&hmap_dev, p, 0));
+    }
+    // the previous loop's kernels must be done before the flags are reset
+    PDC_CK(cudaStreamSynchronize(s));
+    hmap[0] = 1;
+    hmap[1] = 0;
+    live_ptr = &ctl.p->go;
+    k_loop_begin<<<1, 1, 0, s>>>(ctl, 1);
+    PDC_LAUNCH_CK();
+    enqueue_residual(contacts);
+    k_loop_decide_host<<<1, 1, 0, s>>>(ctl, cfg, sc, n_cv_d, sflag, 0, hmap_dev);
+    PDC_LAUNCH_CK();
+    int enq = 0;  // iterations enqueued after the first decision
+    auto t0 = std::chrono::steady_clock::now();
+    while (enq < cfg.max_iters) {
+        // wait until the device has taken all but AHEAD of the decisions enqueued
+        bool timed_out = false;
+        while (hmap[0] && (enq + 1) - hmap[1] > AHEAD) {
+            if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > AHEAD_TIMEOUT_S) {
+                timed_out = true;
+                break;
+            }
+        }
+        if (timed_out) {
+            PDC_CK(cudaStreamSynchronize(s));
+            if (!hmap[0]) break;
+        }
+        if (!hmap[0]) break;  // the loop has ended; anything enqueued after its end does nothing
+        enqueue_solve(contacts, contacts, true, 1.f, r_nc, r_c, cycles, sweeps, pccd);
+        enqueue_residual(contacts);
+        k_loop_decide_host<<<1, 1, 0, s>>>(ctl, cfg, sc, n_cv_d, sflag, 1, hmap_dev);
+        PDC_LAUNCH_CK();
+        ++enq;
+    }
+    live_ptr = nullptr;
 }
 
 void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {
@@ -1831,7 +1921,7 @@ void pdc_ctx::step() {
         st.warm_iters += hctl.warm_iters;
         st.inner_iters += hctl.inner_iters;
         st.contact_iters += hctl.contact_iters;
-        st.graph_loops = hctl.graph_loops;
+        st.device_loops = hctl.device_loops;
         if (relmode && last_dev) st.rel_residual = hctl.rel;
         if (!have_rho0) st.rho0 = hctl.rho0;
     }
@@ -1969,12 +2059,12 @@ void pdc_default_params(pdc_params *p) {
     p->launch_overlap = 1;
     p->rf_toi = 0.0;
     p->rf_iters = 8;
-    p->graph_loops = 1;
+    p->loop_control = 2;
     p->pccd_adaptive = 0;
     p->pccd_max_axis = 64;
     p->instance_line_search = 0;
     p->autotune = 0;
-    p->graph_unroll = 4;
+    p->graph_unroll = 1;
 }
 
 static bool params_valid(const pdc_params *params) {
@@ -1985,6 +2075,7 @@ static bool params_valid(const pdc_params *params) {
            (params->samples_ee == 0 || params->samples_ee == 1 || params->samples_ee == 4) &&
            params->sweep_kind >= 0 && params->sweep_kind <= 1 && (params->sweep_kind != 1 || params->cheb_ratio > 1.0) &&
            params->accel >= 0 && params->accel <= 2 && (params->accel != 2 || (params->aa_depth >= 1 && params->aa_depth <= 8)) &&
+           params->loop_control >= 0 && params->loop_control <= 2 &&
            (params->pccd_adaptive == 0 || (params->pccd_adaptive == 1 && params->pccd_max_axis >= 1 &&
                                            params->pccd_max_axis <= 256 && params->alpha_ls > 0 && params->alpha_ls < 1));
 }

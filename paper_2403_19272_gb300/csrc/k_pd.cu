@@ -396,18 +396,25 @@ __global__ void __launch_bounds__(ELL_TILE_ROWS, 8) k_cheb_step_tile(
     constexpr uint32_t BYTES = (uint32_t)W * ELL_TILE_ROWS * 6;
     __shared__ __align__(128) unsigned char tile[BYTES];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_dead;
     const int t = threadIdx.x;
     if (t == 0) {
         mbar_init(&bar, 1);
         mbar_fence_init();
+        // a device loop's flag only ever goes from 1 to 0 within the loop, so
+        // an early read of 0 is final: the step of an iteration enqueued past
+        // the loop's end issues no tile copy
+        s_dead = loop_dead(c.live) ? 1 : 0;
     }
     __syncthreads();
-    if (t == 0) {
+    const bool dead_early = s_dead != 0;
+    if (t == 0 && !dead_early) {
         mbar_expect_tx(&bar, BYTES);
         bulk_load(tile, c.ell_tile + (size_t)blockIdx.x * BYTES, BYTES, &bar);
     }
     grid_dep_wait();
     grid_dep_release();
+    if (dead_early) return;  // no copy in flight
     const int i = blockIdx.x * ELL_TILE_ROWS + t;
     float mx = 0.f;
     // an ended device loop: no load or store, but the tile copy is still awaited

@@ -209,7 +209,7 @@ struct LoopCtl {
     int aa_count, aa_widx, aa_have_prev;
     int aa_slot, aa_prev, aa_ncol;  // the mixing step of the current iteration
     int warm_iters, inner_iters, contact_iters;  // totals of the step
-    int graph_loops;      // loops of the step that ran as one graph launch
+    int device_loops;     // loops of the step whose tests ran on the device
 };
 
 // ---------------------------------------------------------------- kernels (k_pd.cu)

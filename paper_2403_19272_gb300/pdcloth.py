@@ -42,7 +42,7 @@ class pdc_params(ctypes.Structure):
                 ("seed", c_u64), ("accel", c_i32), ("accel_rho", c_dbl), ("sweep_kind", c_i32),
                 ("cheb_ratio", c_dbl), ("aa_depth", c_i32),
                 ("tensor_cores", c_i32), ("bp_reuse", c_dbl), ("launch_overlap", c_i32),
-                ("rf_toi", c_dbl), ("rf_iters", c_i32), ("graph_loops", c_i32), ("pccd_adaptive", c_i32),
+                ("rf_toi", c_dbl), ("rf_iters", c_i32), ("loop_control", c_i32), ("pccd_adaptive", c_i32),
                 ("pccd_max_axis", c_i32), ("instance_line_search", c_i32), ("autotune", c_i32),
                 ("graph_unroll", c_i32)]
 
@@ -52,7 +52,7 @@ class pdc_stats(ctypes.Structure):
                 ("n_candidates", c_i64), ("n_active", c_i64), ("n_contact_vertices", c_i64), ("t_toi", c_dbl),
                 ("s_line_search", c_dbl), ("rho0", c_dbl), ("rel_residual", c_dbl), ("ms_step", c_dbl),
                 ("ms_broad", c_dbl), ("ms_narrow", c_dbl), ("ms_lg", c_dbl), ("overflow_retries", c_i32),
-                ("bp_reused", c_i32), ("rf_iters", c_i32), ("graph_loops", c_i32)]
+                ("bp_reused", c_i32), ("rf_iters", c_i32), ("device_loops", c_i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

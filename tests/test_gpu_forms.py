@@ -204,23 +204,25 @@ def _run(pc, sc, p, steps):
     return xs, sts
 
 
-def test_graph_loops_take_the_host_loops_steps_in_parity_mode(pc):
+@pytest.mark.parametrize("mode", [2, 1])
+def test_device_loops_take_the_host_loops_steps_in_parity_mode(pc, mode):
     """Fixed iteration counts with contacts (both candidate-list buffers,
-    the partial CCD and the NDB counters inside the graph's while body): the
-    device-driven loops give the host-driven loops' positions up to the order
-    of float atomics.  (In this mode the host-driven loop reads no count back
-    and counts every iteration of a contact loop as one with springs; the
-    device counts those that have contact vertices.  The graph's loop also
-    evaluates the springs at the final iterate, so the contact-vertex count
-    of the last evaluation may differ.)"""
+    the partial CCD and the NDB counters in the device-decided iterations):
+    loops whose tests run on the device (mode 2: iterations enqueued ahead of
+    the decisions; mode 1: a graph while loop) give the host-driven loops'
+    positions up to the order of float atomics.  (The host-driven loop reads
+    no count back in this mode and counts every iteration of a contact loop
+    as one with springs; the device counts those that have contact vertices.
+    A device loop also evaluates the springs at the final iterate, so the
+    contact-vertex count of the last evaluation may differ.)"""
     sc = thrown_drape(24)
     kw = dict(fixed_iters=1, warm_iters=2, max_outer=2, max_inner=4, solve_cycles=20, jacobi_sweeps=8, r_warm=128,
               r_reuse=32, precision=2, d_hat=1e-3)
-    xg, sg = _run(pc, sc, params(pc, graph_loops=1, **kw), 5)
-    xh, sh = _run(pc, sc, params(pc, graph_loops=0, **kw), 5)
+    xg, sg = _run(pc, sc, params(pc, loop_control=mode, **kw), 5)
+    xh, sh = _run(pc, sc, params(pc, loop_control=0, **kw), 5)
     L = float(np.linalg.norm(sc.verts.max(0) - sc.verts.min(0)))
-    assert all(s["graph_loops"] >= 3 for s in sg), [s["graph_loops"] for s in sg]
-    assert all(s["graph_loops"] == 0 for s in sh)
+    assert all(s["device_loops"] >= 3 for s in sg), [s["device_loops"] for s in sg]
+    assert all(s["device_loops"] == 0 for s in sh)
     assert max(s["n_active"] for s in sg) > 0
     for k in range(5):
         for key in ("warm_iters", "inner_iters", "outer_iters", "n_active"):
@@ -229,8 +231,8 @@ def test_graph_loops_take_the_host_loops_steps_in_parity_mode(pc):
         assert np.max(np.abs(xg[k] - xh[k])) <= 1e-6 * L, k
 
 
-@pytest.mark.parametrize("precision", [2, 0])
-def test_graph_loops_take_the_host_loops_steps_in_production_mode(pc, precision):
+@pytest.mark.parametrize("precision,mode", [(2, 2), (0, 2), (2, 1)])
+def test_device_loops_take_the_host_loops_steps_in_production_mode(pc, precision, mode):
     """The benchmark's settings (relative residual 1e-3, stagnation stop,
     Anderson mixing) on the 64 x 64 swept cloth: the stopping tests taken on
     the device end the loops where the host's do (iteration counts equal,
@@ -239,12 +241,13 @@ def test_graph_loops_take_the_host_loops_steps_in_production_mode(pc, precision)
     import bench
     sc = wl.hanging_swept(side=64)
     pg = bench.solver_params(pc, precision)
+    pg.loop_control = mode
     ph = bench.solver_params(pc, precision)
-    ph.graph_loops = 0
+    ph.loop_control = 0
     xg, sg = _run(pc, sc, pg, 8)
     xh, sh = _run(pc, sc, ph, 8)
     L = float(np.linalg.norm(sc.verts.max(0) - sc.verts.min(0)))
-    assert all(s["graph_loops"] >= 2 for s in sg) and all(s["graph_loops"] == 0 for s in sh)
+    assert all(s["device_loops"] >= 2 for s in sg) and all(s["device_loops"] == 0 for s in sh)
     same = sum(sg[k]["warm_iters"] + sg[k]["inner_iters"] == sh[k]["warm_iters"] + sh[k]["inner_iters"]
                for k in range(8))
     assert same >= 7, [(a["inner_iters"], b["inner_iters"]) for a, b in zip(sg, sh)]
