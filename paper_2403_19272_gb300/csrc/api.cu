@@ -153,6 +153,41 @@ struct LoopCfg {
     cudaGraphConditionalHandle cond;
 };
 
+// Everything an LG iteration accumulates into, zeroed in one launch at the
+// start of its residual part: the residual norm, the contact-vertex count,
+// the collision springs (cw, cf), the Anderson normal equations, the
+// collision update of the reduced matrix and (host-driven loops; device
+// decisions zero it after reading it) the step-change maximum.
+struct IterZero {
+    double *rsq;
+    unsigned int *dxmax;  // NULL: left to the decision kernel
+    int *ncv;
+    float *cw;
+    float4 *cf;
+    int n;                // entries of cw / cf (0: no collision springs this loop)
+    double *gb;
+    int ngb;
+    double *da;
+    int nda;
+};
+__global__ void k_iter_begin(IterZero z, const int *live) {
+    grid_dep_wait();
+    grid_dep_release();
+    if (loop_dead(live)) return;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+    if (t == 0) {
+        *z.rsq = 0.0;
+        if (z.dxmax) *z.dxmax = 0u;
+        *z.ncv = 0;
+    }
+    for (long long k = t; k < z.ngb; k += nt) z.gb[k] = 0.0;
+    for (long long k = t; k < z.nda; k += nt) z.da[k] = 0.0;
+    for (long long i = t; i < z.n; i += nt) {
+        z.cw[i] = 0.f;
+        z.cf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 // At the start of a step: the reference residual (its squared norm is in
 // sc->rsq) and the step's counters.
 __global__ void k_loop_step_init(LoopCtl *c, const Scalars *sc) {
@@ -163,7 +198,8 @@ __global__ void k_loop_step_init(LoopCtl *c, const Scalars *sc) {
 }
 
 // At the start of a loop (the host-driven loop resets its Accel state here).
-__global__ void k_loop_begin(LoopCtl *c, int graph) {
+__global__ void k_loop_begin(LoopCtl *c, int graph, Scalars *sc) {
+    sc->dxmax = 0u;  // the loop's first solve reduces into zero
     c->iters = 0;
     c->go = 1;
     c->springs = 0;
@@ -189,6 +225,7 @@ __device__ int loop_decide(LoopCtl *c, const LoopCfg &f, const Scalars *sc, cons
     if (after_solve && !c->go) return 0;  // an earlier iteration of this pass ended the loop
     int go = (*dev_err & (PDC_DEVERR_UMMA | PDC_DEVERR_COPY)) ? 0 : 1;
     const double dx = (double)__uint_as_float(sc->dxmax);
+    const_cast<Scalars *>(sc)->dxmax = 0u;  // consumed: the next solve reduces into zero
     if (go && after_solve) {
         if (f.dx_inner && dx <= f.tolx_in) go = 0;
         else if (f.dx_springs && c->springs && dx <= f.tolx_out) go = 0;
@@ -640,6 +677,7 @@ struct pdc_ctx {
     const int *live_ptr = nullptr;
     DevBuf<LoopCtl> ctl;
     LoopCtl hctl;
+    bool device_decides = false;  // the loop being enqueued takes its tests on the device
     pdc_tuning tune = {0, 256, 1, 152 * 8, 8, {0, 0, 0}, {0, 0}, {0, 0, 0, 0}, {0, 0, 0}};
     void autotune_vertex_kernels();
     bool device_loops_ok() const;
@@ -1253,18 +1291,29 @@ void pdc_ctx::autotune_vertex_kernels() {
 // two on the host; the device-driven loop (run_loop) in k_loop_decide.
 void pdc_ctx::enqueue_residual(bool contacts) {
     ClothView c = cloth();
-    launch_live_zero(s, live_ptr, &sc.p->rsq, sizeof(double));
+    {
+        IterZero z;
+        z.rsq = &sc.p->rsq;
+        z.dxmax = device_decides ? nullptr : &sc.p->dxmax;
+        z.ncv = n_cv_d.p;
+        z.cw = CW.p;
+        z.cf = CF.p;
+        z.n = contacts ? n : 0;
+        const bool aa = accel.on && P.fixed_iters == 0 && P.accel == 2;
+        z.gb = aa_Gb.p;
+        z.ngb = aa ? aa_gram_doubles() : 0;
+        z.da = dA.p;
+        z.nda = contacts ? r_reuse * r_reuse : 0;
+        const int blocks = contacts ? std::min(nb(n), 152 * 4) : 1;
+        launch_dependent(P.launch_overlap != 0, k_iter_begin, blocks, 256, 0, s, z, live_ptr);
+    }
     const float *cw = nullptr;
     const float4 *cf = nullptr;
     if (contacts) {
-        launch_live_zero(s, live_ptr, CW.p, sizeof(float) * n);
-        launch_live_zero(s, live_ptr, CF.p, sizeof(float4) * n);
         PROF("contact_springs", 0, launch_contact(s, coll(), act, n_act_d, cap_act, Xp, dhat, CW, CF));
-        launch_contact_list(s, n, CW, contact_list, n_cv_d, live_ptr);
+        launch_contact_list(s, n, CW, contact_list, n_cv_d, live_ptr, false);
         cw = CW;
         cf = CF;
-    } else {
-        launch_live_zero(s, live_ptr, n_cv_d.p, sizeof(int));
     }
     PROF("local_residual", bytes_residual(contacts), launch_residual(s, c, Xs, Ucur, Z, cw, cf, R, sc, nullptr, 0));
 }
@@ -1277,10 +1326,10 @@ void pdc_ctx::enqueue_solve(bool contacts, bool springs, bool device, float w_ac
                             int sweeps, bool pccd) {
     ClothView c = cloth();
     const float *cw = contacts ? CW.p : nullptr;
-    launch_live_zero(s, live_ptr, &sc.p->dxmax, sizeof(unsigned int));
+    // the accumulators of this solve (step-change maximum, Anderson normal
+    // equations, reduced-matrix update) were zeroed by the residual part
     const bool acc = accel.on && P.fixed_iters == 0;
     const bool aa = acc && P.accel == 2;
-    if (aa) aa_clear(s, aa_Gb, live_ptr);  // normal equations of this iteration
     float4 *xprev = (acc && !aa && !device) ? Xacc.p : nullptr;
     const bool sp = device ? contacts : springs;  // springs possible on this path
     SubspaceView S = sub(r_nc, r_c);
@@ -1296,7 +1345,7 @@ void pdc_ctx::enqueue_solve(bool contacts, bool springs, bool device, float w_ac
         if (r_warm > 0 && (r_nc > 0 || r_c > 0)) {
             PROF("subspace_project", bytes_basis(springs ? r_c : r_nc),
                  launch_project(s, S, rl, n_cv_d, W, sp, device));
-            if (sp && r_c > 0) PROF("subspace_syrk", 0, launch_syrk(s, S, contact_list, n_cv_d, cw, W));
+            if (sp && r_c > 0) PROF("subspace_syrk", 0, launch_syrk(s, S, contact_list, n_cv_d, cw, W, false));
             PROF("reduced_solve", 0, launch_reduced_solve(s, S, n_cv_d, W));
             PROF("subspace_lift", bytes_basis(springs ? r_c : r_nc) + 12.0 * n,
                  launch_lift(s, S, n_cv_d, W, have_delta ? din : nullptr, dout, sp, device));
@@ -1488,6 +1537,7 @@ bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r
     // single iteration per pass always runs: the while node checked go)
     const int unroll = std::min(std::max(P.graph_unroll, 1), 8);
     live_ptr = unroll > 1 ? &ctl.p->go : nullptr;
+    device_decides = true;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t e = nullptr;
     bool capturing = false;
@@ -1502,7 +1552,7 @@ bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r
         LoopCfg cfg = cfg0;
         cfg.cond = h;
         cfg.use_cond = 1;
-        k_loop_begin<<<1, 1, 0, s>>>(ctl, 1);
+        k_loop_begin<<<1, 1, 0, s>>>(ctl, 1, sc);
         PDC_LAUNCH_CK();
         enqueue_residual(contacts);
         k_loop_decide_cond<<<1, 1, 0, s>>>(ctl, cfg, sc, n_cv_d, sflag, 0);
@@ -1553,11 +1603,13 @@ bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r
         (void)cudaGetLastError();  // clear the failed capture's error
         s = saved;
         live_ptr = nullptr;
+        device_decides = false;
         if (log) std::fprintf(stderr, "[pdc] LG loop graph not built (%s): host-driven loops\n", ex.what());
         return false;
     }
     s = saved;
     live_ptr = nullptr;
+    device_decides = false;
     G.g = g;
     G.e = e;
     G.gen = graph_gen + bp.gen;
@@ -1618,7 +1670,15 @@ void pdc_ctx::run_loop_ahead(const LoopCfg &cfg, bool contacts, int r_nc, int r_
     hmap[0] = 1;
     hmap[1] = 0;
     live_ptr = &ctl.p->go;
-    k_loop_begin<<<1, 1, 0, s>>>(ctl, 1);
+    device_decides = true;
+    struct Reset {  // the flags belong to this loop only, whatever happens
+        pdc_ctx *c;
+        ~Reset() {
+            c->live_ptr = nullptr;
+            c->device_decides = false;
+        }
+    } reset{this};
+    k_loop_begin<<<1, 1, 0, s>>>(ctl, 1, sc);
     PDC_LAUNCH_CK();
     enqueue_residual(contacts);
     k_loop_decide_host<<<1, 1, 0, s>>>(ctl, cfg, sc, n_cv_d, sflag, 0, hmap_dev);
@@ -1645,7 +1705,6 @@ void pdc_ctx::run_loop_ahead(const LoopCfg &cfg, bool contacts, int r_nc, int r_
         PDC_LAUNCH_CK();
         ++enq;
     }
-    live_ptr = nullptr;
 }
 
 void pdc_ctx::full_ccd(const float4 *x0, const float4 *x1, bool merge) {

@@ -922,8 +922,9 @@ void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, c
     PDC_LAUNCH_CK();
 }
 
-void launch_contact_list(cudaStream_t s, int n, const float *cw, int *list, int *count, const int *live) {
-    launch_live_zero(s, live, count, sizeof(int));
+void launch_contact_list(cudaStream_t s, int n, const float *cw, int *list, int *count, const int *live,
+                         bool zero) {
+    if (zero) launch_live_zero(s, live, count, sizeof(int));
     if (n > 0) k_contact_list<<<(n + 255) / 256, 256, 0, s>>>(n, cw, list, count, live);
     PDC_LAUNCH_CK();
 }

@@ -894,6 +894,8 @@ void launch_live_zero(cudaStream_t s, const int *live, void *p, size_t bytes) {
     PDC_LAUNCH_CK();
 }
 
+int aa_gram_doubles() { return AA_MAX * (AA_MAX + 3) / 2 + AA_MAX; }
+
 void aa_clear(cudaStream_t s, double *Gb, const int *live) {
     launch_live_zero(s, live, Gb, sizeof(double) * (AA_MAX * (AA_MAX + 3) / 2 + AA_MAX));
 }

@@ -560,9 +560,9 @@ void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, con
 }
 
 void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const int *n_cv, const float *cw,
-                 SubspaceWork &W) {
+                 SubspaceWork &W, bool zero) {
     if (S.r_c == 0) return;
-    launch_live_zero(s, S.live, W.dA, sizeof(double) * S.r_c * S.r_c);
+    if (zero) launch_live_zero(s, S.live, W.dA, sizeof(double) * S.r_c * S.r_c);
     with_basis(S, false, [&](auto *U) {
         using TU = std::remove_const_t<std::remove_pointer_t<decltype(U)>>;
         int ne = S.r_c * S.r_c;

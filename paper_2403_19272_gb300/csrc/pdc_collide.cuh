@@ -148,7 +148,9 @@ void launch_contact(cudaStream_t s, const CollView &cv, const ActivePair *act, c
 // outside the topology).
 unsigned int pair_guard_take(cudaStream_t s, unsigned int *guard);
 // Compact the cloth vertices with cw > 0.
-void launch_contact_list(cudaStream_t s, int n, const float *cw, int *list, int *count, const int *live = nullptr);
+// (zero = false: *count has been zeroed already)
+void launch_contact_list(cudaStream_t s, int n, const float *cw, int *list, int *count, const int *live = nullptr,
+                         bool zero = true);
 
 // Stage helpers on explicit quads (kinds: 0 VT, 1 EE).
 void launch_ccd_quads(cudaStream_t s, const int4 *quads, const int *kinds, long long np, const float4 *x0,

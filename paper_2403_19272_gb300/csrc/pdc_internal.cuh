@@ -243,6 +243,7 @@ void launch_aa_device(cudaStream_t s, int n, const unsigned char *is_free, const
                       float4 *fprev, float4 *gprev, float4 *dF, float4 *dG, int m, const LoopCtl *ctl, double *Gb,
                       float *theta, const float4 *xs, float4 *xabs, bool overlap);
 void aa_clear(cudaStream_t s, double *Gb, const int *live = nullptr);
+int aa_gram_doubles();  // entries of the Anderson normal-equation buffer
 // Zeroes `bytes` (a multiple of 4) at p unless *live == 0; with live NULL a
 // plain stream memset.
 void launch_live_zero(cudaStream_t s, const int *live, void *p, size_t bytes);

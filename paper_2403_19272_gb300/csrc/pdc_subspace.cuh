@@ -54,9 +54,10 @@ void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, con
                     bool maybe_contacts = true, bool device_choice = false);
 // whether the tensor-core / compact choice of a spring iteration can be left to the device
 bool device_path_choice(const SubspaceView &S);
-// dA = sum over listed vertices of cw_v U_v U_v^T (leading r_c columns).
+// dA = sum over listed vertices of cw_v U_v U_v^T (leading r_c columns);
+// zero = false: dA has been zeroed already.
 void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const int *n_cv, const float *cw,
-                 SubspaceWork &W);
+                 SubspaceWork &W, bool zero = true);
 // q = (reduced matrix)^-1 g.
 void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv, SubspaceWork &W);
 // dout = din + U q (din may be NULL: zero).
