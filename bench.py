@@ -54,10 +54,13 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form comparison")
     ap.add_argument("--launch-overlap", type=int, default=1, choices=[0, 1],
                     help="1: Chebyshev steps launched as programmatic dependents (default)")
-    ap.add_argument("--loop-control", type=int, default=2, choices=[0, 1, 2],
-                    help="stopping tests of the LG loops: 2 on the device, host enqueues ahead (default); "
-                         "1 on the device in a CUDA graph while loop; 0 on the host")
+    ap.add_argument("--loop-control", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="stopping tests of the LG loops: 1 on the device in a CUDA graph while loop (default); "
+                         "3 on the device, the host enqueueing each iteration ahead as one graph launch; 2 the "
+                         "same with kernel launches; 0 on the host")
     ap.add_argument("--graph-unroll", type=int, default=1, help="LG iterations per pass of a graph loop (1..8)")
+    ap.add_argument("--loop-ahead", type=int, default=1, choices=[0, 1, 2],
+                    help="LG iterations enqueued beyond the last decision read (loop control 2, 3)")
     ap.add_argument("--no-launch-count", action="store_true",
                     help="skip the CUDA activity trace (e.g. when running under ncu)")
     return ap.parse_args()
@@ -68,10 +71,12 @@ FORMS = {"mixed16": 2, "mixed": 1, "fp32": 0}
 DTYPES = {"mixed16": "f16+f32+f64", "mixed": "bf16+f32+f64", "fp32": "f32"}
 
 
-def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1, loop_control=2, graph_unroll=1):
+def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1, loop_control=1, graph_unroll=1,
+                  loop_ahead=1):
     p = pc.pdc_default_params()
     p.loop_control = loop_control  # stopping tests of the LG loops on the device
     p.graph_unroll = graph_unroll
+    p.loop_ahead = loop_ahead
     p.launch_overlap = overlap  # Chebyshev steps as programmatic dependent launches
     p.tol_rel_residual = 1e-3
     p.max_outer = 2
@@ -161,11 +166,11 @@ class ClockSampler:
 
 
 def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True, sweeps=28, cheb_ratio=300.0,
-             overlap=1, loop_control=2, graph_unroll=1):
+             overlap=1, loop_control=1, graph_unroll=1, loop_ahead=1):
     """Warm-up, timed region (device), profiled replay, e2e through host buffers."""
     import numpy as np
     stream = torch.cuda.Stream()
-    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap, loop_control, graph_unroll)
+    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap, loop_control, graph_unroll, loop_ahead)
     t_setup = time.time()
     h = pc.pdc_create(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend, p,
                       stream.cuda_stream)
@@ -646,7 +651,7 @@ def main():
     for f in a.forms.split(","):
         forms[f] = run_form(pc, torch, scene, FORMS[f], a.steps, a.warmup, local,
                             not a.no_launch_count, a.sweeps, a.cheb_ratio, a.launch_overlap, a.loop_control,
-                            a.graph_unroll)
+                            a.graph_unroll, a.loop_ahead)
     head = list(forms)[0]
     ms = forms[head]["ms"]
     ms = max_over_ranks(ms, f"cuda:{local}")
@@ -661,7 +666,8 @@ def main():
         "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": head, "basis": "r=256 (r_reuse=32 with collision springs)",
                    "l2": "inputs larger than L2 (basis 134 MB in 16 bits / 268 MB FP32 plus matrices and state)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "loop_control": a.loop_control, "loop_ahead": a.loop_ahead},
         "forms": {f: {"ms_per_step": round(d["ms"], 3), "lg_iters_per_step": d["iters"],
                       "vertex_iters_per_s": round(scene.n * d["iters"] / (d["ms"] * 1e-3), 1),
                       "gpu_launches": d["launches"],

@@ -150,15 +150,18 @@ typedef struct {
     int32_t loop_control;    /* who takes the stopping tests of the LG loops
                                 (warm start, inner loops): the relative
                                 residual, stagnation, step-change and cap tests.
-                                2 (default): a one-thread kernel on the device
-                                after each residual; the host enqueues the
-                                iterations ahead (at most 2 in flight) and reads
-                                the decisions from host-mapped memory, with no
+                                1 (default): a one-thread kernel on the device
+                                after each residual, the loop run as one CUDA
+                                graph whose conditional while node repeats the
+                                iteration (graph_unroll per pass); the fastest
+                                of the four on the 512 x 512 sheet.  2: the
+                                same device tests; the host enqueues the
+                                iterations ahead (loop_ahead) and reads the
+                                decisions from host-mapped memory, with no
                                 stream synchronisation per iteration; kernels
                                 enqueued past the loop's end return at once.
-                                1: the same device tests, the loop run as one
-                                CUDA graph whose conditional while node repeats
-                                the iteration (graph_unroll per pass).  0: the
+                                3: as 2, each iteration launched as one CUDA
+                                graph (captured once per loop kind).  0: the
                                 host reads each iteration's residual back and
                                 decides (also while profiling, with PDC_LOG or
                                 PDC_SYNC_CHECK, or with accel = 1).  Same
@@ -194,6 +197,12 @@ typedef struct {
                                 that grows with the body's node count; the
                                 kernels of iterations after the loop's end
                                 return at once                                   */
+    int32_t loop_ahead;      /* loop_control = 2, 3: LG iterations the host
+                                enqueues beyond the last one whose decision it
+                                has read (0..2, default 1).  Each one the loop
+                                ends before costs a pass of kernels that return
+                                at once; 0 leaves the device waiting for the
+                                host between iterations                         */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
@@ -217,7 +226,7 @@ typedef struct {
     int32_t rf_iters;            /* residual-forwarding LG iterations run at the
                                     end of this step (0: not triggered)          */
     int32_t device_loops;        /* LG loops of this step whose stopping tests
-                                    ran on the device (loop_control 1 or 2)      */
+                                    ran on the device (loop_control 1, 2 or 3) */
 } pdc_stats;
 
 /* Launch shapes in use and, after an autotuned first step, the measured
@@ -241,7 +250,7 @@ typedef struct {
  * iterations, 4 damped Jacobi sweeps (automatic omega), 1 cycle, no basis,
  * FP32, samples 3/4, collisions on, no LG acceleration, tensor cores for the
  * mixed forms, dependent launches on, broad-phase reuse and residual
- * forwarding off, LG-loop tests on the device (loop_control 2). */
+ * forwarding off, LG-loop tests on the device (loop_control 1). */
 void pdc_default_params(pdc_params *p);
 
 /* Build the solver for one cloth mesh (Sec. 3; Eq. (global) rest matrix,

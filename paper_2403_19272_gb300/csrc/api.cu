@@ -538,6 +538,7 @@ struct pdc_ctx {
         if (hsc) cudaFreeHost(hsc);
         if (hmap) cudaFreeHost((void *)hmap);
         for (auto &G : gl) free_graph(G);
+        for (auto &G : gb) free_body(G);
         if (gs) cudaStreamDestroy(gs);
     }
 
@@ -668,6 +669,18 @@ struct pdc_ctx {
         unsigned gen = 0;
     };
     GraphLoop gl[4];             // warm start, inner loop without collisions, inner loop with bp.cur = 0 / 1
+    // loop_control = 3: one iteration of the same four loops, instantiated
+    // MAX_AHEAD + 1 times and launched in turn, so that no instance is
+    // launched again while its previous launch is in flight (such a launch
+    // starts late, by about the time the device takes to relaunch it)
+    static constexpr int MAX_AHEAD = 2;  // largest loop_ahead
+    struct BodyGraph {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t e[MAX_AHEAD + 1] = {};
+        unsigned gen = 0;
+    };
+    BodyGraph gb[4];
+    bool bodies_failed = false;  // an iteration graph could not be built: stream launches
     cudaStream_t gs = nullptr;   // capture stream
     unsigned graph_gen = 1;      // bumped when a buffer a graph captures is reallocated
     bool graphs_failed = false;  // a graph could not be built: host-driven loops from then on
@@ -686,10 +699,15 @@ struct pdc_ctx {
     bool build_loop(GraphLoop &G, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
                     bool pccd);
     bool run_loop(int gi, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps, bool pccd);
-    // loop_control = 2: host-mapped {go, decisions} of the loop being run
+    // loop_control = 2, 3: host-mapped {go, decisions} of the loop being run
     volatile int *hmap = nullptr;
     int *hmap_dev = nullptr;
-    void run_loop_ahead(const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps, bool pccd);
+    void enqueue_iteration(const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps, bool pccd);
+    void free_body(BodyGraph &G);
+    bool build_body(BodyGraph &G, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
+                    bool pccd);
+    void run_loop_ahead(int gi, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
+                        bool pccd);
     void residual_forwarding();
     void full_ccd(const float4 *x0, const float4 *x1, bool merge);
     void broad_phase_pass(const float4 *x0, const float4 *x1, bool super);
@@ -1622,8 +1640,8 @@ bool pdc_ctx::build_loop(GraphLoop &G, const LoopCfg &cfg0, bool contacts, int r
 // built: the caller then runs the host-driven loop.
 bool pdc_ctx::run_loop(int gi, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
                        bool pccd) {
-    if (P.loop_control == 2) {
-        run_loop_ahead(cfg, contacts, r_nc, r_c, cycles, sweeps, pccd);
+    if (P.loop_control >= 2) {
+        run_loop_ahead(gi, cfg, contacts, r_nc, r_c, cycles, sweeps, pccd);
         return true;
     }
     GraphLoop &G = gl[gi];
@@ -1648,16 +1666,78 @@ bool pdc_ctx::run_loop(int gi, const LoopCfg &cfg, bool contacts, int r_nc, int 
     return true;
 }
 
-// loop_control = 2: the host enqueues the loop's iterations (residual part,
-// device decision, solve part) on s, each kernel returning at once after the
-// loop's end, and runs at most AHEAD iterations ahead of the device's
-// decisions, which it reads from host-mapped memory: the device never waits
-// for the host between iterations, and no stream synchronisation is needed.
-// The wait for the device is bounded (a stream synchronisation after
-// AHEAD_TIMEOUT, then the decisions are read from device memory).
-void pdc_ctx::run_loop_ahead(const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
+// One iteration of a device-decided loop after its first decision: the solve
+// part, the residual part and the decision, which it writes to host memory.
+void pdc_ctx::enqueue_iteration(const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
+                                bool pccd) {
+    enqueue_solve(contacts, contacts, true, 1.f, r_nc, r_c, cycles, sweeps, pccd);
+    enqueue_residual(contacts);
+    k_loop_decide_host<<<1, 1, 0, s>>>(ctl, cfg, sc, n_cv_d, sflag, 1, hmap_dev);
+    PDC_LAUNCH_CK();
+}
+
+// enqueue_iteration captured as a graph (loop_control = 3), with programmatic
+// dependent launches inside when the driver takes them; false if it cannot be
+// built.  Called with the loop's go flag set (live_ptr, device_decides).
+void pdc_ctx::free_body(BodyGraph &G) {
+    for (auto &e : G.e) {
+        if (e) cudaGraphExecDestroy(e);
+        e = nullptr;
+    }
+    if (G.g) cudaGraphDestroy(G.g);
+    G.g = nullptr;
+}
+
+bool pdc_ctx::build_body(BodyGraph &G, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
+                         bool pccd) {
+    free_body(G);
+    if (!gs) PDC_CK(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+    const int ov = P.launch_overlap;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (!graph_overlap) P.launch_overlap = 0;
+        cudaStream_t saved = s;
+        s = gs;
+        bool capturing = false;
+        try {
+            PDC_CK(cudaStreamBeginCapture(gs, cudaStreamCaptureModeRelaxed));
+            capturing = true;
+            enqueue_iteration(cfg, contacts, r_nc, r_c, cycles, sweeps, pccd);
+            capturing = false;
+            PDC_CK(cudaStreamEndCapture(gs, &G.g));
+            for (auto &e : G.e) PDC_CK(cudaGraphInstantiate(&e, G.g, 0));
+            s = saved;
+            P.launch_overlap = ov;
+            G.gen = graph_gen + bp.gen;
+            return true;
+        } catch (const std::exception &ex) {
+            if (capturing) {
+                cudaGraph_t junk = nullptr;
+                cudaStreamEndCapture(gs, &junk);
+                if (junk) cudaGraphDestroy(junk);
+            }
+            free_body(G);
+            (void)cudaGetLastError();
+            s = saved;
+            P.launch_overlap = ov;
+            if (log) std::fprintf(stderr, "[pdc] iteration graph not built (%s)\n", ex.what());
+            if (!graph_overlap || !ov) return false;
+            graph_overlap = false;  // once more without programmatic launches
+        }
+    }
+    return false;
+}
+
+// loop_control = 2, 3: the host enqueues the loop's iterations (residual
+// part, device decision, solve part) on s, each kernel returning at once
+// after the loop's end, and keeps loop_ahead iterations enqueued beyond the
+// last one whose decision it has read from host-mapped memory: with
+// loop_ahead >= 1 the device does not wait for the host between iterations,
+// and no stream synchronisation is needed.  With 3 an iteration is one launch
+// of its graph gb[gi] (stream launches if the graph cannot be built).  The
+// wait for the device is bounded (a stream synchronisation after
+// AHEAD_TIMEOUT_S, then the decisions are read from device memory).
+void pdc_ctx::run_loop_ahead(int gi, const LoopCfg &cfg, bool contacts, int r_nc, int r_c, int cycles, int sweeps,
                              bool pccd) {
-    constexpr int AHEAD = 2;
     constexpr double AHEAD_TIMEOUT_S = 30.0;
     if (!hmap) {
         void *p = nullptr;
@@ -1678,6 +1758,14 @@ void pdc_ctx::run_loop_ahead(const LoopCfg &cfg, bool contacts, int r_nc, int r_
             c->device_decides = false;
         }
     } reset{this};
+    BodyGraph &G = gb[gi];
+    bool graph = P.loop_control == 3 && !bodies_failed;
+    if (graph && (!G.e[0] || G.gen != graph_gen + bp.gen)) {
+        if (!build_body(G, cfg, contacts, r_nc, r_c, cycles, sweeps, pccd)) {
+            bodies_failed = true;
+            graph = false;
+        }
+    }
     k_loop_begin<<<1, 1, 0, s>>>(ctl, 1, sc);
     PDC_LAUNCH_CK();
     enqueue_residual(contacts);
@@ -1686,9 +1774,10 @@ void pdc_ctx::run_loop_ahead(const LoopCfg &cfg, bool contacts, int r_nc, int r_
     int enq = 0;  // iterations enqueued after the first decision
     auto t0 = std::chrono::steady_clock::now();
     while (enq < cfg.max_iters) {
-        // wait until the device has taken all but AHEAD of the decisions enqueued
+        // wait until at most loop_ahead iterations are enqueued beyond the
+        // last one decided (enq + 1 decisions enqueued, hmap[1] taken)
         bool timed_out = false;
-        while (hmap[0] && (enq + 1) - hmap[1] > AHEAD) {
+        while (hmap[0] && enq - hmap[1] >= P.loop_ahead) {
             if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > AHEAD_TIMEOUT_S) {
                 timed_out = true;
                 break;
@@ -1699,10 +1788,8 @@ void pdc_ctx::run_loop_ahead(const LoopCfg &cfg, bool contacts, int r_nc, int r_
             if (!hmap[0]) break;
         }
         if (!hmap[0]) break;  // the loop has ended; anything enqueued after its end does nothing
-        enqueue_solve(contacts, contacts, true, 1.f, r_nc, r_c, cycles, sweeps, pccd);
-        enqueue_residual(contacts);
-        k_loop_decide_host<<<1, 1, 0, s>>>(ctl, cfg, sc, n_cv_d, sflag, 1, hmap_dev);
-        PDC_LAUNCH_CK();
+        if (graph) PDC_CK(cudaGraphLaunch(G.e[enq % (MAX_AHEAD + 1)], s));
+        else enqueue_iteration(cfg, contacts, r_nc, r_c, cycles, sweeps, pccd);
         ++enq;
     }
 }
@@ -2118,12 +2205,13 @@ void pdc_default_params(pdc_params *p) {
     p->launch_overlap = 1;
     p->rf_toi = 0.0;
     p->rf_iters = 8;
-    p->loop_control = 2;
+    p->loop_control = 1;
     p->pccd_adaptive = 0;
     p->pccd_max_axis = 64;
     p->instance_line_search = 0;
     p->autotune = 0;
     p->graph_unroll = 1;
+    p->loop_ahead = 1;
 }
 
 static bool params_valid(const pdc_params *params) {
@@ -2134,7 +2222,8 @@ static bool params_valid(const pdc_params *params) {
            (params->samples_ee == 0 || params->samples_ee == 1 || params->samples_ee == 4) &&
            params->sweep_kind >= 0 && params->sweep_kind <= 1 && (params->sweep_kind != 1 || params->cheb_ratio > 1.0) &&
            params->accel >= 0 && params->accel <= 2 && (params->accel != 2 || (params->aa_depth >= 1 && params->aa_depth <= 8)) &&
-           params->loop_control >= 0 && params->loop_control <= 2 &&
+           params->loop_control >= 0 && params->loop_control <= 3 && params->loop_ahead >= 0 &&
+           params->loop_ahead <= 2 &&
            (params->pccd_adaptive == 0 || (params->pccd_adaptive == 1 && params->pccd_max_axis >= 1 &&
                                            params->pccd_max_axis <= 256 && params->alpha_ls > 0 && params->alpha_ls < 1));
 }

@@ -204,12 +204,13 @@ def _run(pc, sc, p, steps):
     return xs, sts
 
 
-@pytest.mark.parametrize("mode", [2, 1])
+@pytest.mark.parametrize("mode", [3, 2, 1])
 def test_device_loops_take_the_host_loops_steps_in_parity_mode(pc, mode):
     """Fixed iteration counts with contacts (both candidate-list buffers,
     the partial CCD and the NDB counters in the device-decided iterations):
-    loops whose tests run on the device (mode 2: iterations enqueued ahead of
-    the decisions; mode 1: a graph while loop) give the host-driven loops'
+    loops whose tests run on the device (modes 3 and 2: iterations enqueued
+    ahead of the decisions, as one graph launch each or kernel by kernel;
+    mode 1: a graph while loop) give the host-driven loops'
     positions up to the order of float atomics.  (The host-driven loop reads
     no count back in this mode and counts every iteration of a contact loop
     as one with springs; the device counts those that have contact vertices.
@@ -231,7 +232,7 @@ def test_device_loops_take_the_host_loops_steps_in_parity_mode(pc, mode):
         assert np.max(np.abs(xg[k] - xh[k])) <= 1e-6 * L, k
 
 
-@pytest.mark.parametrize("precision,mode", [(2, 2), (0, 2), (2, 1)])
+@pytest.mark.parametrize("precision,mode", [(2, 3), (0, 3), (2, 2), (2, 1)])
 def test_device_loops_take_the_host_loops_steps_in_production_mode(pc, precision, mode):
     """The benchmark's settings (relative residual 1e-3, stagnation stop,
     Anderson mixing) on the 64 x 64 swept cloth: the stopping tests taken on
