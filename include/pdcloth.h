@@ -238,11 +238,12 @@ typedef struct {
     int32_t cheb_tile;       /* 1: Chebyshev steps read the TMA-staged matrix
                                 tiles; 0: the ELL arrays (candidates 1, 0)      */
     int32_t pair_blocks;     /* blocks of the per-pair kernels (152 x 2, 4, 8, 16) */
-    int32_t vt_lanes;        /* lanes per vertex of the VT broad-phase query (4, 8, 16) */
+    int32_t cell_warps;      /* warps per block of the broad phase's cell-pair
+                                kernel (candidates 2, 4, 6)                     */
     float residual_ms[3];
     float cheb_ms[2];
     float pair_ms[4];
-    float vt_ms[3];
+    float cell_ms[3];
 } pdc_tuning;
 
 /* Defaults: dt 1/200, g = (0,0,-9.8), K = 2, a_max 20, alpha 0.8, automatic
@@ -467,9 +468,8 @@ pdc_status pdc_op_lift(pdc_handle h, const double *q, int32_t r, float *out);
 /* Allocation-free variant of pdc_op_contact.  The paper has no counterpart:
  * this is a library-integration entry point, not part of the method.
  *
- * It computes exactly what pdc_op_contact computes (the collision springs of
- * Sec. 5.1 with A_i = B_i = Id for the given pairs and weights) but
- * allocates no device memory: no cudaMalloc / cudaFree and no allocating
+ * It computes exactly what pdc_op_contact computes for the given pairs and
+ * weights, but allocates no device memory: no cudaMalloc / cudaFree and no allocating
  * library routine.  It is meant for callers that cannot let a library
  * allocate inside a call -- a process whose caching allocator already holds
  * nearly all free device memory (a cudaMalloc there fails, or forces the

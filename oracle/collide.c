@@ -751,3 +751,151 @@ int64_t oc_count_tri_tri_grid(const double *X, const int32_t *tris, int32_t nt, 
     if (n <= cap) qsort(out, (size_t)n, 2 * sizeof(int32_t), oc_pair_cmp);
     return n;
 }
+
+/* ---------------------------------------------------------------------------
+ * Grid-culled broad phase: the same VT and EE pairs as oc_broadphase_vt /
+ * oc_broadphase_ee (the same bp_overlap predicate and exclusions), found by
+ * binning every primitive into the cells of side `cell` that its box grown
+ * by g = d_hat + 1e-5 (1 + |largest coordinate|) on every side touches, and
+ * testing all pairs that share a cell.  If bp_overlap holds, lo_a <=
+ * fl32(hi_b + d_hat) <= hi_b + g and likewise for b, so the grown boxes
+ * overlap and share a cell.  A pair found in several cells is kept once
+ * (sort, then drop repeats).  For lists too large for the brute force.
+ * Returns 0, or -1 when memory or the cell range runs out; the pair counts
+ * go to n_vt / n_ee, at most cap_* pairs to out_*, sorted.
+ * ------------------------------------------------------------------------ */
+typedef struct { int64_t key; int32_t id, kind; } oc_bent;  /* kind 0 vertex, 1 edge, 2 triangle */
+
+static int oc_bent_cmp(const void *p, const void *q) {
+    const oc_bent *a = (const oc_bent *)p, *b = (const oc_bent *)q;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    if (a->kind != b->kind) return a->kind - b->kind;
+    return a->id - b->id;
+}
+
+/* sorts the n pairs of P and moves the distinct ones to its front; returns their count */
+static int64_t oc_unique_count(int32_t *P, int64_t n) {
+    qsort(P, (size_t)n, 2 * sizeof(int32_t), oc_pair_cmp);
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (m == 0 || P[2 * i] != P[2 * (m - 1)] || P[2 * i + 1] != P[2 * (m - 1) + 1]) {
+            P[2 * m] = P[2 * i];
+            P[2 * m + 1] = P[2 * i + 1];
+            ++m;
+        }
+    return m;
+}
+
+int oc_broadphase_grid(const float *X0, const float *X1, int32_t nv, int32_t n_dyn, const int32_t *tris,
+                       int32_t nt, const int32_t *edges, int32_t ne, float dhat, double cell, int64_t cap_vt,
+                       int32_t *out_vt, int64_t cap_ee, int32_t *out_ee, int64_t *n_vt, int64_t *n_ee) {
+    const int64_t np = (int64_t)nv + ne + nt;
+    *n_vt = 0;
+    *n_ee = 0;
+    if (np == 0) return 0;
+    box *B = (box *)malloc(sizeof(box) * (size_t)np);
+    if (!B) return -1;
+    double amax = 0.0;
+    for (int64_t p = 0; p < np; ++p) {
+        if (p < nv) { int32_t v = (int32_t)p; B[p] = box_of(X0, X1, &v, 1); }
+        else if (p < nv + ne) B[p] = box_of(X0, X1, edges + 2 * (p - nv), 2);
+        else B[p] = box_of(X0, X1, tris + 3 * (p - nv - ne), 3);
+        for (int d = 0; d < 3; ++d) {
+            if (fabs(B[p].lo[d]) > amax) amax = fabs(B[p].lo[d]);
+            if (fabs(B[p].hi[d]) > amax) amax = fabs(B[p].hi[d]);
+        }
+    }
+    const double g = (double)dhat + 1e-5 * (1.0 + amax), inv = 1.0 / cell;
+    /* cell ranges of the grown boxes */
+    int64_t total = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        int64_t c = 1;
+        for (int d = 0; d < 3; ++d) {
+            double lo = floor(((double)B[p].lo[d] - g) * inv), hi = floor(((double)B[p].hi[d] + g) * inv);
+            if (lo < -(double)(1 << 20) || hi >= (double)(1 << 20) || hi - lo > 4096) { free(B); return -1; }
+            c *= (int64_t)(hi - lo) + 1;
+        }
+        total += c;
+    }
+    oc_bent *E = (oc_bent *)malloc(sizeof(oc_bent) * (size_t)total);
+    if (!E) { free(B); return -1; }
+    int64_t k = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        int64_t lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = (int64_t)floor(((double)B[p].lo[d] - g) * inv);
+            hi[d] = (int64_t)floor(((double)B[p].hi[d] + g) * inv);
+        }
+        const int kind = p < nv ? 0 : (p < nv + ne ? 1 : 2);
+        const int32_t id = (int32_t)(kind == 0 ? p : (kind == 1 ? p - nv : p - nv - ne));
+        for (int64_t z = lo[2]; z <= hi[2]; ++z)
+            for (int64_t y = lo[1]; y <= hi[1]; ++y)
+                for (int64_t x = lo[0]; x <= hi[0]; ++x) {
+                    E[k].key = ((x + (1 << 20)) << 42) | ((y + (1 << 20)) << 21) | (z + (1 << 20));
+                    E[k].id = id;
+                    E[k].kind = kind;
+                    ++k;
+                }
+    }
+    qsort(E, (size_t)total, sizeof(oc_bent), oc_bent_cmp);
+    /* pairs of every cell, repeats included */
+    int64_t cvt = 1024, cee = 1024, nvt = 0, nee = 0;
+    int32_t *PV = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)cvt);
+    int32_t *PE = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)cee);
+    int fail = !PV || !PE;
+    for (int64_t a0 = 0; a0 < total && !fail;) {
+        int64_t a1 = a0;
+        while (a1 < total && E[a1].key == E[a0].key) ++a1;
+        /* the cell's entries are sorted by kind: vertices, edges, triangles */
+        int64_t e0 = a0, t0;
+        while (e0 < a1 && E[e0].kind == 0) ++e0;
+        t0 = e0;
+        while (t0 < a1 && E[t0].kind == 1) ++t0;
+        for (int64_t i = a0; i < t0 && !fail; ++i)
+            for (int64_t j = (i < e0 ? t0 : i + 1); j < (i < e0 ? a1 : t0) && !fail; ++j) {
+                int32_t a = E[i].id, b = E[j].id;
+                if (E[i].kind == 0 && E[j].kind == 2) {          /* (vertex a, triangle b) */
+                    const int32_t *T = tris + 3 * b;
+                    if (T[0] == a || T[1] == a || T[2] == a) continue;
+                    if (a >= n_dyn && T[0] >= n_dyn && T[1] >= n_dyn && T[2] >= n_dyn) continue;
+                    if (!bp_overlap(&B[a], &B[nv + ne + b], dhat)) continue;
+                    if (nvt == cvt) {
+                        cvt *= 2;
+                        int32_t *t = (int32_t *)realloc(PV, sizeof(int32_t) * 2 * (size_t)cvt);
+                        if (!t) { fail = 1; break; }
+                        PV = t;
+                    }
+                    PV[2 * nvt] = a;
+                    PV[2 * nvt + 1] = b;
+                    ++nvt;
+                } else if (E[i].kind == 1 && E[j].kind == 1 && a < b) {  /* (edge a, edge b), a < b */
+                    const int32_t *Ea = edges + 2 * a, *Eb = edges + 2 * b;
+                    if (Ea[0] == Eb[0] || Ea[0] == Eb[1] || Ea[1] == Eb[0] || Ea[1] == Eb[1]) continue;
+                    if (Ea[0] >= n_dyn && Ea[1] >= n_dyn && Eb[0] >= n_dyn && Eb[1] >= n_dyn) continue;
+                    if (!bp_overlap(&B[nv + a], &B[nv + b], dhat)) continue;
+                    if (nee == cee) {
+                        cee *= 2;
+                        int32_t *t = (int32_t *)realloc(PE, sizeof(int32_t) * 2 * (size_t)cee);
+                        if (!t) { fail = 1; break; }
+                        PE = t;
+                    }
+                    PE[2 * nee] = a;
+                    PE[2 * nee + 1] = b;
+                    ++nee;
+                }
+            }
+        a0 = a1;
+    }
+    free(E);
+    free(B);
+    if (fail) { free(PV); free(PE); return -1; }
+    nvt = oc_unique_count(PV, nvt);
+    nee = oc_unique_count(PE, nee);
+    for (int64_t i = 0; i < nvt && i < cap_vt; ++i) { out_vt[2 * i] = PV[2 * i]; out_vt[2 * i + 1] = PV[2 * i + 1]; }
+    for (int64_t i = 0; i < nee && i < cap_ee; ++i) { out_ee[2 * i] = PE[2 * i]; out_ee[2 * i + 1] = PE[2 * i + 1]; }
+    free(PV);
+    free(PE);
+    *n_vt = nvt;
+    *n_ee = nee;
+    return 0;
+}

@@ -32,6 +32,8 @@ def lib():
         L.oc_count_tri_tri.restype = i64
         L.oc_count_tri_tri_grid.argtypes = [P, P, i32, dbl, i64, P]
         L.oc_count_tri_tri_grid.restype = i64
+        L.oc_broadphase_grid.argtypes = [P, P, i32, i32, P, i32, P, i32, flt, dbl, i64, P, i64, P, P, P]
+        L.oc_broadphase_grid.restype = ctypes.c_int
         L.oc_ccd_vt.argtypes = [P, P, dbl]
         L.oc_ccd_vt.restype = dbl
         L.oc_ccd_ee.argtypes = [P, P, dbl]
@@ -111,6 +113,34 @@ def broadphase(X0, X1, n_dyn, tris, edges, dhat):
             break
         cap = int(n)
     return vt, ee
+
+
+def broadphase_grid(X0, X1, n_dyn, tris, edges, dhat, cell=None):
+    """The pairs of broadphase (same predicate and exclusions), culled by a
+    uniform grid of side `cell` (default: the mean largest swept-box extent
+    of the triangles, at least 2 d_hat): for lists too large for the brute
+    force.  Returns (vt [k,2], ee [l,2]), sorted."""
+    X0, X1, tris, edges = _f32(X0), _f32(X1), _i32(tris), _i32(edges)
+    if cell is None:
+        if len(tris):
+            P = np.concatenate([X0[tris], X1[tris]], axis=1).astype(np.float64)
+            cell = float(np.mean(np.max(P.max(1) - P.min(1), axis=1)))
+        else:
+            cell = 1.0
+        cell = max(cell, 2.0 * float(dhat), 1e-9)
+    cap_vt = cap_ee = 1 << 16
+    while True:
+        ovt = np.empty((cap_vt, 2), dtype=np.int32)
+        oee = np.empty((cap_ee, 2), dtype=np.int32)
+        nvt, nee = ctypes.c_int64(0), ctypes.c_int64(0)
+        rc = lib().oc_broadphase_grid(_p(X0), _p(X1), len(X0), int(n_dyn), _p(tris), len(tris), _p(edges),
+                                      len(edges), np.float32(dhat), float(cell), cap_vt, _p(ovt), cap_ee, _p(oee),
+                                      ctypes.byref(nvt), ctypes.byref(nee))
+        if rc != 0:
+            raise MemoryError("broadphase_grid: grid too large")
+        if nvt.value <= cap_vt and nee.value <= cap_ee:
+            return ovt[:nvt.value].copy(), oee[:nee.value].copy()
+        cap_vt, cap_ee = max(cap_vt, int(nvt.value)), max(cap_ee, int(nee.value))
 
 
 def broadphase_vt_one(X0, X1, v, n_dyn, tris, dhat):

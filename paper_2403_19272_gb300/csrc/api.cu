@@ -1216,7 +1216,7 @@ void pdc_ctx::ensure_topology() {
     for (int i = 0; i < n; ++i) vf[i] = freev[i] ? 0 : 1;
     vfixed.upload(vf, s);
     long long cvt = std::max<long long>(1024, 16LL * nv_all), cee = std::max<long long>(1024, 24LL * ne_all);
-    long long cent = std::max<long long>(4096, 8LL * (nt_all + ne_all));
+    long long cent = std::max<long long>(4096, 8LL * ((long long)nv_all + nt_all + ne_all));
     if (bp_cap0 > 0) cvt = cee = bp_cap0;
     if (!guard_d.p) {
         guard_d.alloc(1);
@@ -1295,7 +1295,7 @@ void pdc_ctx::autotune_vertex_kernels() {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    bp.tune_pairs = bp.tune_query = P.collisions != 0;
+    bp.tune_pairs = bp.tune_cells = P.collisions != 0;
     ++graph_gen;  // graphs capture launch shapes
 }
 
@@ -2628,9 +2628,9 @@ pdc_status pdc_get_tuning(pdc_handle h, pdc_tuning *out) {
     if (!out) throw Error(PDC_ERR_ARG, "pdc_get_tuning: NULL");
     *out = h->tune;
     out->pair_blocks = h->bp.pair_blocks;
-    out->vt_lanes = h->bp.qg_vt;
+    out->cell_warps = h->bp.cell_warps;
     for (int k = 0; k < 4; ++k) out->pair_ms[k] = h->bp.pair_ms[k];
-    for (int k = 0; k < 3; ++k) out->vt_ms[k] = h->bp.query_ms[k];
+    for (int k = 0; k < 3; ++k) out->cell_ms[k] = h->bp.cell_ms[k];
     API_END(h)
 }
 

@@ -51,38 +51,16 @@ __device__ inline bool box_overlap(float3 alo, float3 ahi, float3 blo, float3 bh
            blo.y <= __fadd_rn(ahi.y, d) && alo.z <= __fadd_rn(bhi.z, d) && blo.z <= __fadd_rn(ahi.z, d);
 }
 
-// Cells of the table side: the primitive's own box, not inflated.
-__device__ inline void cell_range_raw(float3 lo, float3 hi, float inv, int3 &clo, int3 &chi) {
-    clo = cellv(lo, inv);
-    chi = cellv(hi, inv);
-}
-
-// Cells searched by a query box b: if a table box a satisfies the predicate
-// with b, then a_lo <= fl32(b_hi + d) and a_hi >= b_lo - d - |a_hi + d| 2^-24
-// (from b_lo <= fl32(a_hi + d)); the search range covers both bounds (the
-// low end is lowered by a margin of 2^-20 (|b_lo| + d) that exceeds the
-// rounding of fl32(a_hi + d) and of its own computation), and floor(v / cell)
-// is monotone, so the raw cell range of a meets it.  Only the query side is
-// inflated: the gap is counted once.
-__device__ inline float low_search(float lo, float d) {
-    float m = (fabsf(lo) + d) * 9.5367431640625e-07f;  // 2^-20
-    return __fsub_rn(__fsub_rn(lo, d), m);
-}
-__device__ inline void cell_range_query(float3 lo, float3 hi, float d, float inv, int3 &clo, int3 &chi) {
-    float3 l = make_float3(low_search(lo.x, d), low_search(lo.y, d), low_search(lo.z, d));
-    float3 h = make_float3(__fadd_rn(hi.x, d), __fadd_rn(hi.y, d), __fadd_rn(hi.z, d));
-    clo = cellv(l, inv);
-    chi = cellv(h, inv);
-}
-
-// A table entry stores (primitive << 3) | lowx | lowy << 1 | lowz << 2,
-// where low* says that the entry's cell is the lowest cell of the
-// primitive's raw range along that axis.  A pair is reported only in the
-// lowest cell common to the query range and the table range, max(q_lo,
-// t_lo) per axis; at a cell c of the query range this holds iff, per axis,
-// low* is set or c equals the query's lowest cell.
-__device__ inline bool owner_cell(int flags, int x, int y, int z, int3 qlo) {
-    return ((flags & 1) || x == qlo.x) && ((flags & 2) || y == qlo.y) && ((flags & 4) || z == qlo.z);
+// insertion sort of a short row
+__device__ inline void sort_row(int *row, int c) {
+    for (int i = 1; i < c; ++i) {
+        int q = row[i], j = i - 1;
+        while (j >= 0 && row[j] > q) {
+            row[j + 1] = row[j];
+            --j;
+        }
+        row[j + 1] = q;
+    }
 }
 
 __device__ inline void vbox(const float4 *x0, const float4 *x1, int v, float3 &lo, float3 &hi) {
@@ -139,201 +117,340 @@ __global__ void k_grid_params(GridParams *gp, int nt, float dhat, float scale) {
     gp->inv_cell = 1.f / cell;
 }
 
-// ------------------------------------------------------------------ hash table
-// mode 0: count per bucket; mode 1: fill entries.
-__global__ void k_hash_insert(int np, const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
-                              const GridParams *gp, float dhat, unsigned int mask, int *__restrict__ bcnt,
-                              const int *__restrict__ bstart, int *__restrict__ bfill,
-                              unsigned long long *__restrict__ ekey, int *__restrict__ eprim, int mode,
-                              const long long *total, long long cap, int *overflow) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    if (mode == 1 && *total > cap) return;
-    float inv = gp->inv_cell;
-    int3 lo, hi;
-    cell_range_raw(f3(blo[p]), f3(bhi[p]), inv, lo, hi);
-    long long ncell = (long long)(hi.x - lo.x + 1) * (hi.y - lo.y + 1) * (hi.z - lo.z + 1);
-    if (ncell > MAX_CELLS_PER_PRIM) {
-        if (mode == 0) atomicOr(overflow, OVF_CELLS);
-        return;
-    }
-    for (int z = lo.z; z <= hi.z; ++z)
-        for (int y = lo.y; y <= hi.y; ++y)
-            for (int x = lo.x; x <= hi.x; ++x) {
-                unsigned long long k = cell_key(x, y, z);
-                unsigned int b = hash_key(k, mask);
-                if (mode == 0) {
-                    atomicAdd(&bcnt[b], 1);
-                } else {
-                    int pos = bstart[b] + atomicAdd(&bfill[b], 1);
-                    ekey[pos] = k;
-                    eprim[pos] = (p << 3) | (x == lo.x ? 1 : 0) | (y == lo.y ? 2 : 0) | (z == lo.z ? 4 : 0);
-                }
-            }
+// ------------------------------------------------------------------ cell table
+// Table primitives: collision vertices [0, nv), edges [nv, nv + ne),
+// triangles [nv + ne, nv + ne + nt).  Primitive p covers the cells of its
+// swept box with the upper side raised by d_hat, [lo, fl32(hi + d_hat)].  Two
+// raised boxes overlap on an axis iff lo_a <= fl32(hi_b + d) and lo_b <=
+// fl32(hi_a + d), which is the candidate predicate itself; then the cell of
+// max(lo_a, lo_b) per axis lies in both cell ranges (floor(v / cell) is
+// monotone), and it is the one common cell where, per axis, one of the two
+// entries sits at the lowest cell of its range (the owner test below), so
+// every candidate pair is tested in exactly one cell.
+constexpr int KIND_V = 0, KIND_E = 1, KIND_T = 2;
+constexpr unsigned PAY_PRIM = (1u << 27) - 1;
+
+__device__ inline unsigned pay_pack(int prim, int kind, int low) {
+    return (unsigned)prim | ((unsigned)kind << 27) | ((unsigned)low << 29);
 }
 
-// ------------------------------------------------------------------ queries
-// Queries.  Each primary collects its candidates, sorted by secondary id,
-// in a fixed-width row of a slot buffer; the count is always exact, and a
-// primary with more candidates than the row width flags OVF_SLOTS (the pass
-// is then rerun with wider rows).  In the VT query QG lanes share one
-// vertex and stride over the entries of each bucket of its cell range
-// together (the lanes of a group run the same trip count), append through a
-// group ballot and sort the row once at the end.
-constexpr int QUERY_T = 128;
-// lanes per vertex in the VT query: 4, 8 (default) or 16 (BroadPhase::qg_vt)
-
-__device__ inline void slot_insert(int *row, int width, int c, int q) {
-    if (c >= width) return;
-    int j = c - 1;
-    while (j >= 0 && row[j] > q) {
-        row[j + 1] = row[j];
-        --j;
-    }
-    row[j + 1] = q;
+__device__ inline float3 raise_d(float3 h, float d) {
+    return make_float3(__fadd_rn(h.x, d), __fadd_rn(h.y, d), __fadd_rn(h.z, d));
 }
 
-__device__ inline void sort_row(int *row, int c) {
-    for (int i = 1; i < c; ++i) {
-        int q = row[i], j = i - 1;
-        while (j >= 0 && row[j] > q) {
-            row[j + 1] = row[j];
-            --j;
+// The swept box of table primitive p (not raised), its kind and id.
+__device__ inline void table_box(const CollView &cv, const float4 *x0, const float4 *x1, const float4 *tlo,
+                                 const float4 *thi, const float4 *elo, const float4 *ehi, int p, int &kind,
+                                 int &prim, float3 &lo, float3 &hi) {
+    if (p < cv.nv) {
+        kind = KIND_V;
+        prim = p;
+        vbox(x0, x1, p, lo, hi);
+    } else if (p < cv.nv + cv.ne) {
+        kind = KIND_E;
+        prim = p - cv.nv;
+        lo = f3(elo[prim]);
+        hi = f3(ehi[prim]);
+    } else {
+        kind = KIND_T;
+        prim = p - cv.nv - cv.ne;
+        lo = f3(tlo[prim]);
+        hi = f3(thi[prim]);
+    }
+}
+
+// mode 0: count the entries of every bucket; mode 1: write them.  In each
+// round every lane takes the next cell of its primitive, and the lanes that
+// land in the same bucket are served by one atomic (match_any), so
+// neighbouring primitives (the mesh order is spatially coherent) share it.
+__global__ void k_cell_insert(CollView cv, const float4 *__restrict__ x0, const float4 *__restrict__ x1,
+                              const float4 *__restrict__ tlo, const float4 *__restrict__ thi,
+                              const float4 *__restrict__ elo, const float4 *__restrict__ ehi, const GridParams *gp,
+                              float dhat, unsigned int mask, int *__restrict__ bcnt, const int *__restrict__ bstart,
+                              int *__restrict__ bfill, unsigned long long *__restrict__ ekey,
+                              unsigned int *__restrict__ epay, int mode, const long long *total, long long cap,
+                              int *overflow) {
+    const int np = cv.nv + cv.ne + cv.nt;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned lane = threadIdx.x & 31;
+    if (mode == 1 && *total > cap) return;  // the table does not fit (uniform over the grid)
+    const float inv = gp->inv_cell;
+    int kind = 0, prim = 0, ncell = 0;
+    int3 lo = make_int3(0, 0, 0), hi = make_int3(-1, -1, -1);
+    if (p < np) {
+        float3 l, h;
+        table_box(cv, x0, x1, tlo, thi, elo, ehi, p, kind, prim, l, h);
+        lo = cellv(l, inv);
+        hi = cellv(raise_d(h, dhat), inv);
+        long long nc = (long long)(hi.x - lo.x + 1) * (hi.y - lo.y + 1) * (hi.z - lo.z + 1);
+        if (nc > MAX_CELLS_PER_PRIM) {
+            if (mode == 0) atomicOr(overflow, OVF_CELLS);
+        } else {
+            ncell = (int)nc;
         }
-        row[j + 1] = q;
     }
-}
-
-// VT: primary = vertex v (all collision vertices), secondary = triangle.
-template <int QG>
-__global__ void __launch_bounds__(QUERY_T) k_query_vt(CollView cv, const float4 *__restrict__ x0,
-                                                      const float4 *__restrict__ x1, const float4 *__restrict__ tlo,
-                                                      const float4 *__restrict__ thi, const GridParams *gp, float dhat, unsigned int mask,
-                                                      const int *__restrict__ bcnt, const int *__restrict__ bstart,
-                                                      const unsigned long long *__restrict__ ekey,
-                                                      const int *__restrict__ eprim, int *__restrict__ cnt,
-                                                      int *__restrict__ slots, int width,
-                                                      const long long *hash_total, long long cap_ent, int *overflow) {
-    auto grp = cg::tiled_partition<QG>(cg::this_thread_block());
-    const int gl = (int)grp.thread_rank();
-    const int v = (blockIdx.x * blockDim.x + threadIdx.x) / QG;
-    if (v >= cv.nv) return;  // uniform per group
-    if (*hash_total > cap_ent) {  // table not filled: produce nothing
-        if (gl == 0) cnt[v] = 0;
-        return;
-    }
-    float inv = gp->inv_cell;
-    float3 lo, hi;
-    vbox(x0, x1, v, lo, hi);
-    int3 clo, chi;
-    cell_range_query(lo, hi, dhat, inv, clo, chi);
-    if ((long long)(chi.x - clo.x + 1) * (chi.y - clo.y + 1) * (chi.z - clo.z + 1) > MAX_CELLS_PER_PRIM) {
-        if (gl == 0) {
-            cnt[v] = 0;
-            atomicOr(overflow, OVF_CELLS);
+    const int sx = hi.x - lo.x + 1, sy = hi.y - lo.y + 1;
+    const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)ncell);
+    for (int r = 0; r < rounds; ++r) {
+        const bool act = r < ncell;
+        int x = 0, y = 0, z = 0;
+        unsigned long long k = 0;
+        unsigned int b = 0xffffffffu;  // no bucket (mask < 2^31)
+        if (act) {
+            x = lo.x + r % sx;
+            y = lo.y + (r / sx) % sy;
+            z = lo.z + r / (sx * sy);
+            k = cell_key(x, y, z);
+            b = hash_key(k, mask);
         }
-        return;
-    }
-    const bool vfix = v >= cv.nc;
-    int *row = slots + (size_t)v * width;
-    int c = 0;
-    for (int z = clo.z; z <= chi.z; ++z)
-        for (int y = clo.y; y <= chi.y; ++y)
-            for (int x = clo.x; x <= chi.x; ++x) {
-                const unsigned long long k = cell_key(x, y, z);
-                const unsigned int b = hash_key(k, mask);
-                const int e0 = bstart[b], e1 = e0 + bcnt[b];
-                for (int eb = e0; eb < e1; eb += QG) {
-                    const int e = eb + gl;
-                    bool cand = false;
-                    int t = 0;
-                    if (e < e1 && ekey[e] == k) {
-                        const int pk = eprim[e];
-                        t = pk >> 3;
-                        if (owner_cell(pk, x, y, z, clo)) {
-                            int4 T = cv.tri[t];
-                            cand = T.x != v && T.y != v && T.z != v &&
-                                   !(vfix && T.x >= cv.nc && T.y >= cv.nc && T.z >= cv.nc) &&
-                                   box_overlap(lo, hi, f3(tlo[t]), f3(thi[t]), dhat);
-                        }
-                    }
-                    const unsigned m = grp.ballot(cand);
-                    if (cand) {
-                        int slot = c + __popc(m & ((1u << gl) - 1u));
-                        if (slot < width) row[slot] = t;
-                    }
-                    c += __popc(m);
-                }
-            }
-    grp.sync();
-    if (gl == 0) {
-        sort_row(row, min(c, width));
-        cnt[v] = c;
-        if (c > width) atomicOr(overflow, OVF_SLOTS);
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        if (!act) continue;
+        const int leader = __ffs(peers) - 1;
+        if (mode == 0) {
+            if ((int)lane == leader) atomicAdd(&bcnt[b], __popc(peers));
+        } else {
+            int base = 0;
+            if ((int)lane == leader) base = atomicAdd(&bfill[b], __popc(peers));
+            base = __shfl_sync(peers, base, leader);
+            const int pos = bstart[b] + base + __popc(peers & ((1u << lane) - 1u));
+            ekey[pos] = k;
+            epay[pos] = pay_pack(prim, kind, (x == lo.x ? 1 : 0) | (y == lo.y ? 2 : 0) | (z == lo.z ? 4 : 0));
+        }
     }
 }
 
-// EE: primary = edge e, secondary = edge f > e; one thread per edge (the
-// edge buckets are short and half their entries fail f > e at once, so the
-// grouped scan of the VT query does not pay here: measured slower).
-__global__ void __launch_bounds__(QUERY_T) k_query_ee(CollView cv, const float4 *__restrict__ elo,
-                                                  const float4 *__restrict__ ehi, const GridParams *gp, float dhat, unsigned int mask,
-                                                  const int *__restrict__ bcnt, const int *__restrict__ bstart,
-                                                  const unsigned long long *__restrict__ ekey,
-                                                  const int *__restrict__ eprim, int *__restrict__ cnt,
-                                                  int *__restrict__ slots, int width,
-                                                  const long long *hash_total, long long cap_ent, int *overflow) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= cv.ne) return;
-    if (*hash_total > cap_ent) {
-        cnt[e] = 0;
-        return;
-    }
-    float inv = gp->inv_cell;
-    float3 lo = f3(elo[e]), hi = f3(ehi[e]);
-    int3 clo, chi;
-    cell_range_query(lo, hi, dhat, inv, clo, chi);
-    if ((long long)(chi.x - clo.x + 1) * (chi.y - clo.y + 1) * (chi.z - clo.z + 1) > MAX_CELLS_PER_PRIM) {
-        cnt[e] = 0;
-        atomicOr(overflow, OVF_CELLS);
-        return;
-    }
-    int2 E = cv.edge[e];
-    bool efix = E.x >= cv.nc && E.y >= cv.nc;
-    int *row = slots + (size_t)e * width;
-    int c = 0;
-    for (int z = clo.z; z <= chi.z; ++z)
-        for (int y = clo.y; y <= chi.y; ++y)
-            for (int x = clo.x; x <= chi.x; ++x) {
-                unsigned long long k = cell_key(x, y, z);
-                unsigned int b = hash_key(k, mask);
-                int e0 = bstart[b], e1 = e0 + bcnt[b];
-                for (int q = e0; q < e1; ++q) {
-                    if (ekey[q] != k) continue;
-                    const int pk = eprim[q];
-                    const int f = pk >> 3;
-                    if (f <= e) continue;
-                    if (!owner_cell(pk, x, y, z, clo)) continue;
-                    int2 F = cv.edge[f];
-                    if (E.x == F.x || E.x == F.y || E.y == F.x || E.y == F.y) continue;
-                    if (efix && F.x >= cv.nc && F.y >= cv.nc) continue;
-                    if (!box_overlap(lo, hi, f3(elo[f]), f3(ehi[f]), dhat)) continue;
-                    slot_insert(row, width, c, f);
-                    ++c;
-                }
+// ------------------------------------------------------------------ cell pairs
+// A warp takes buckets 32 at a time from a global counter and, for every
+// bucket with two entries or more, loads its entries into shared memory in
+// chunks of CELL_CHUNK (boxes, vertex ids, cell keys, lists per kind) and
+// tests every VT pair and every unordered EE pair of each chunk and of each
+// pair of chunks, lanes striding over the flattened pair index.  Entries of
+// other cells that share the bucket are told apart by their keys.  A
+// candidate (v, t) or (e, f), e < f, is appended to the row of v or e; rows
+// are sorted when they are compacted.
+constexpr int CELL_CHUNK = 64;
+constexpr unsigned FL_FIXED = 1u << 3;  // every vertex of the primitive is an obstacle vertex
+
+struct CellRegion {
+    float4 lo[CELL_CHUNK];  // w: primitive id
+    float4 hi[CELL_CHUNK];  // w: lowest-cell flags | FL_FIXED
+    int4 ids[CELL_CHUNK];   // vertex ids (-1 past the primitive's own)
+    unsigned long long key[CELL_CHUNK];
+    unsigned char lv[CELL_CHUNK], le[CELL_CHUNK], lt[CELL_CHUNK];
+};
+
+struct KindCounts {
+    int v, e, t;
+};
+
+__device__ inline KindCounts load_chunk(CellRegion &R, const CollView &cv, const float4 *x0, const float4 *x1,
+                                        const float4 *tlo, const float4 *thi, const float4 *elo, const float4 *ehi,
+                                        const unsigned long long *ekey, const unsigned int *epay, int e0, int cnt,
+                                        unsigned lane) {
+    KindCounts kc = {0, 0, 0};
+    const unsigned below = (1u << lane) - 1u;
+    for (int base = 0; base < cnt; base += 32) {  // warp-uniform
+        const int i = base + (int)lane;
+        int kind = -1;
+        if (i < cnt) {
+            const unsigned pay = epay[e0 + i];
+            const int prim = (int)(pay & PAY_PRIM);
+            kind = (int)((pay >> 27) & 3u);
+            unsigned fl = pay >> 29;
+            float3 lo, hi;
+            int4 ids;
+            if (kind == KIND_V) {
+                vbox(x0, x1, prim, lo, hi);
+                ids = make_int4(prim, -1, -1, -1);
+                if (prim >= cv.nc) fl |= FL_FIXED;
+            } else if (kind == KIND_E) {
+                lo = f3(elo[prim]);
+                hi = f3(ehi[prim]);
+                const int2 E = cv.edge[prim];
+                ids = make_int4(E.x, E.y, -1, -1);
+                if (E.x >= cv.nc && E.y >= cv.nc) fl |= FL_FIXED;
+            } else {
+                lo = f3(tlo[prim]);
+                hi = f3(thi[prim]);
+                const int4 Tr = cv.tri[prim];
+                ids = make_int4(Tr.x, Tr.y, Tr.z, -1);
+                if (Tr.x >= cv.nc && Tr.y >= cv.nc && Tr.z >= cv.nc) fl |= FL_FIXED;
             }
-    cnt[e] = c;
-    if (c > width) atomicOr(overflow, OVF_SLOTS);
+            R.lo[i] = make_float4(lo.x, lo.y, lo.z, __int_as_float(prim));
+            R.hi[i] = make_float4(hi.x, hi.y, hi.z, __uint_as_float(fl));
+            R.ids[i] = ids;
+            R.key[i] = ekey[e0 + i];
+        }
+        const unsigned mv = __ballot_sync(0xffffffffu, kind == KIND_V);
+        const unsigned me = __ballot_sync(0xffffffffu, kind == KIND_E);
+        const unsigned mt = __ballot_sync(0xffffffffu, kind == KIND_T);
+        if (kind == KIND_V) R.lv[kc.v + __popc(mv & below)] = (unsigned char)i;
+        if (kind == KIND_E) R.le[kc.e + __popc(me & below)] = (unsigned char)i;
+        if (kind == KIND_T) R.lt[kc.t + __popc(mt & below)] = (unsigned char)i;
+        kc.v += __popc(mv);
+        kc.e += __popc(me);
+        kc.t += __popc(mt);
+    }
+    __syncwarp();
+    return kc;
 }
 
-// out[off[p] + k] = (p, slots[p][k]) for k < cnt[p]
-__global__ void k_compact_slots(int np, const int *__restrict__ cnt, const int *__restrict__ off,
-                                const int *__restrict__ slots, int width, const long long *total, long long cap,
-                                int2 *__restrict__ out) {
+// q = floor(k / n) for k < 2^12 and 0 < n <= CELL_CHUNK: (k + 1/2) / n is at
+// least 1/(2n) from an integer, far more than the float error of the product.
+__device__ inline int div_small(int k, float inv_n) { return (int)(((float)k + 0.5f) * inv_n); }
+
+__device__ inline bool owner_pair(unsigned fa, unsigned fb) { return ((fa | fb) & 7u) == 7u; }
+
+struct RowsOut {
+    int *cnt_v, *slots_vt, *cnt_e, *slots_ee;
+    int w_vt, w_ee;
+    int *overflow;
+};
+
+__device__ inline void emit(int *cnt, int *slots, int width, int p, int q, int *overflow) {
+    const int slot = atomicAdd(&cnt[p], 1);
+    if (slot < width) slots[(size_t)p * width + slot] = q;
+    else if (slot == width) atomicOr(overflow, OVF_SLOTS);
+}
+
+// (vertex entry i of A, triangle entry j of B)
+__device__ inline void test_vt(const CellRegion &A, int i, const CellRegion &B, int j, float dhat, const RowsOut &o) {
+    if (A.key[i] != B.key[j]) return;
+    const float4 alo = A.lo[i], ahi = A.hi[i], blo = B.lo[j], bhi = B.hi[j];
+    const unsigned fa = __float_as_uint(ahi.w), fb = __float_as_uint(bhi.w);
+    if (!owner_pair(fa, fb)) return;
+    const int v = __float_as_int(alo.w);
+    const int4 T = B.ids[j];
+    if (T.x == v || T.y == v || T.z == v) return;
+    if ((fa & fb & FL_FIXED) != 0) return;
+    if (!box_overlap(f3(alo), f3(ahi), f3(blo), f3(bhi), dhat)) return;
+    emit(o.cnt_v, o.slots_vt, o.w_vt, v, __float_as_int(blo.w), o.overflow);
+}
+
+// (edge entry i of A, edge entry j of B)
+__device__ inline void test_ee(const CellRegion &A, int i, const CellRegion &B, int j, float dhat, const RowsOut &o) {
+    if (A.key[i] != B.key[j]) return;
+    const float4 alo = A.lo[i], ahi = A.hi[i], blo = B.lo[j], bhi = B.hi[j];
+    const unsigned fa = __float_as_uint(ahi.w), fb = __float_as_uint(bhi.w);
+    if (!owner_pair(fa, fb)) return;
+    const int4 a = A.ids[i], b = B.ids[j];
+    if (a.x == b.x || a.x == b.y || a.y == b.x || a.y == b.y) return;
+    if ((fa & fb & FL_FIXED) != 0) return;
+    if (!box_overlap(f3(alo), f3(ahi), f3(blo), f3(bhi), dhat)) return;
+    int e = __float_as_int(alo.w), f = __float_as_int(blo.w);
+    if (e > f) {
+        const int t = e;
+        e = f;
+        f = t;
+    }
+    emit(o.cnt_e, o.slots_ee, o.w_ee, e, f, o.overflow);
+}
+
+// every (vertex of A, triangle of B)
+__device__ inline void pairs_vt(const CellRegion &A, int nv, const CellRegion &B, int nt, float dhat,
+                                const RowsOut &o, unsigned lane) {
+    const int n = nv * nt;
+    if (n == 0) return;
+    const float inv = 1.f / (float)nt;
+    for (int k = (int)lane; k < n; k += 32) {
+        const int i = div_small(k, inv), j = k - i * nt;
+        test_vt(A, A.lv[i], B, B.lt[j], dhat, o);
+    }
+}
+
+// every unordered pair of edges of A: pair (i, i + d mod n) for offsets
+// d = 1 .. (n - 1) / 2 and every i, and, for even n, (i, i + n / 2), i < n / 2
+__device__ inline void pairs_ee_within(const CellRegion &A, int n, float dhat, const RowsOut &o, unsigned lane) {
+    if (n < 2) return;
+    const int h = (n - 1) / 2, n1 = n * h, tot = n * (n - 1) / 2;
+    const float inv = 1.f / (float)n;
+    for (int k = (int)lane; k < tot; k += 32) {
+        int i, d;
+        if (k < n1) {
+            d = div_small(k, inv);
+            i = k - d * n;
+            d += 1;
+        } else {
+            i = k - n1;
+            d = n / 2;
+        }
+        int j = i + d;
+        if (j >= n) j -= n;
+        test_ee(A, A.le[i], A, A.le[j], dhat, o);
+    }
+}
+
+// every (edge of A, edge of B), A and B disjoint chunks
+__device__ inline void pairs_ee_across(const CellRegion &A, int na, const CellRegion &B, int nb, float dhat,
+                                       const RowsOut &o, unsigned lane) {
+    const int n = na * nb;
+    if (n == 0) return;
+    const float inv = 1.f / (float)nb;
+    for (int k = (int)lane; k < n; k += 32) {
+        const int i = div_small(k, inv), j = k - i * nb;
+        test_ee(A, A.le[i], B, B.le[j], dhat, o);
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(W * 32) k_cell_pairs(CollView cv, const float4 *__restrict__ x0,
+                                                       const float4 *__restrict__ x1, const float4 *__restrict__ tlo,
+                                                       const float4 *__restrict__ thi, const float4 *__restrict__ elo,
+                                                       const float4 *__restrict__ ehi, float dhat, int T,
+                                                       const int *__restrict__ bcnt, const int *__restrict__ bstart,
+                                                       const unsigned long long *__restrict__ ekey,
+                                                       const unsigned int *__restrict__ epay, RowsOut o, int *work,
+                                                       const long long *hash_total, long long cap_ent) {
+    __shared__ CellRegion reg[W][2];
+    if (*hash_total > cap_ent) return;  // table not filled: no candidates (the pass is redone)
+    const unsigned lane = threadIdx.x & 31;
+    CellRegion &RA = reg[threadIdx.x >> 5][0];
+    CellRegion &RB = reg[threadIdx.x >> 5][1];
+    for (;;) {
+        int b0 = 0;
+        if (lane == 0) b0 = atomicAdd(work, 32);
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        if (b0 >= T) break;
+        const int b = b0 + (int)lane;
+        const int m = b < T ? bcnt[b] : 0;
+        const int st = b < T ? bstart[b] : 0;
+        unsigned todo = __ballot_sync(0xffffffffu, m >= 2);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int mb = __shfl_sync(0xffffffffu, m, l);
+            const int eb = __shfl_sync(0xffffffffu, st, l);
+            const int nch = (mb + CELL_CHUNK - 1) / CELL_CHUNK;
+            for (int ca = 0; ca < nch; ++ca) {
+                const KindCounts a = load_chunk(RA, cv, x0, x1, tlo, thi, elo, ehi, ekey, epay, eb + ca * CELL_CHUNK,
+                                                min(CELL_CHUNK, mb - ca * CELL_CHUNK), lane);
+                pairs_vt(RA, a.v, RA, a.t, dhat, o, lane);
+                pairs_ee_within(RA, a.e, dhat, o, lane);
+                for (int cb = ca + 1; cb < nch; ++cb) {
+                    const KindCounts c = load_chunk(RB, cv, x0, x1, tlo, thi, elo, ehi, ekey, epay,
+                                                    eb + cb * CELL_CHUNK, min(CELL_CHUNK, mb - cb * CELL_CHUNK), lane);
+                    pairs_vt(RA, a.v, RB, c.t, dhat, o, lane);
+                    pairs_vt(RB, c.v, RA, a.t, dhat, o, lane);
+                    pairs_ee_across(RA, a.e, RB, c.e, dhat, o, lane);
+                    __syncwarp();  // RB is reloaded next
+                }
+                __syncwarp();  // RA is reloaded next
+            }
+        }
+    }
+}
+
+// out[off[p] + k] = (p, k-th smallest of row p) for k < cnt[p]; the row is
+// sorted in place first (rows are short), so the list comes out sorted by
+// (primary, secondary) whatever order the appends took
+__global__ void k_compact_rows(int np, const int *__restrict__ cnt, const int *__restrict__ off,
+                               int *__restrict__ slots, int width, const long long *total, long long cap,
+                               int2 *__restrict__ out) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np || *total > cap) return;
-    int c = min(cnt[p], width), o = off[p];
-    const int *row = slots + (size_t)p * width;
+    const int c = min(cnt[p], width), o = off[p];
+    int *row = slots + (size_t)p * width;
+    sort_row(row, c);
     for (int k = 0; k < c; ++k) out[o + k] = make_int2(p, row[k]);
 }
 
@@ -407,18 +524,18 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
         while (p < x) p <<= 1;
         return p;
     };
-    T_vt = (int)pow2(2LL * cv.nt + 1024);
-    T_ee = (int)pow2(2LL * cv.ne + 1024);
-    for (int k = 0; k < 2; ++k) {
-        bcnt[k].alloc(k == 0 ? T_vt : T_ee);
-        bstart[k].alloc(k == 0 ? T_vt : T_ee);
-        bfill[k].alloc(k == 0 ? T_vt : T_ee);
-    }
+    if ((long long)cv.nv + cv.ne + cv.nt >= (1LL << 27))
+        throw Error(PDC_ERR_ARG, "broad phase: 2^27 or more vertices, edges and triangles");
+    // about one bucket per primitive: occupied cells are far fewer, so most
+    // buckets hold a single cell
+    T = (int)pow2((long long)cv.nv + cv.ne + cv.nt + 1024);
+    bcnt.alloc(T);
+    bstart.alloc(T);
+    bfill.alloc(T);
+    work.alloc(1);
     cap_ent = cap_ent_;
-    for (int k = 0; k < 2; ++k) {
-        ekey[k].alloc(cap_ent);
-        eprim[k].alloc(cap_ent);
-    }
+    ekey.alloc(cap_ent);
+    epay.alloc(cap_ent);
     tlo.alloc(cv.nt);
     thi.alloc(cv.nt);
     elo.alloc(cv.ne);
@@ -427,11 +544,9 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
     off_v.alloc(cv.nv);
     cnt_e.alloc(cv.ne);
     off_e.alloc(cv.ne);
-    if (cv.nt >= (1 << 28) || cv.ne >= (1 << 28))
-        throw Error(PDC_ERR_ARG, "broad phase: more than 2^28 triangles or edges");
     slots_vt.alloc((size_t)cv.nv * w_vt);
     slots_ee.alloc((size_t)cv.ne * w_ee);
-    long long mx = std::max<long long>(std::max<long long>(T_vt, T_ee), std::max<long long>(cv.nv, cv.ne));
+    long long mx = std::max<long long>(T, std::max<long long>(cv.nv, cv.ne));
     scratch.alloc(scan_scratch_ints((int)mx) + 16);
     gp.alloc(1);
     totals.alloc(8);
@@ -495,10 +610,8 @@ void BroadPhase::grow(const CollView &cv, long long cvt, long long cee, long lon
     ++gen;
     if (cent > cap_ent) {
         cap_ent = cent;
-        for (int k = 0; k < 2; ++k) {
-            ekey[k].alloc(cap_ent);
-            eprim[k].alloc(cap_ent);
-        }
+        ekey.alloc(cap_ent);
+        epay.alloc(cap_ent);
     }
     if (cvt > cap_vt) {
         cap_vt = cvt;
@@ -548,83 +661,83 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
             k_grid_params<<<1, 1, 0, s>>>(gp, cv.nt, dhat, cell_scale));
     PDC_LAUNCH_CK();
     long long *tot = totals.p;
-    // ---- tables: 0 = triangles (VT), 1 = edges (EE)
-    for (int k = 0; k < 2; ++k) {
-        int np = k == 0 ? cv.nt : cv.ne;
-        int T = k == 0 ? T_vt : T_ee;
-        const float4 *lo = k == 0 ? tlo.p : elo.p;
-        const float4 *hi = k == 0 ? thi.p : ehi.p;
-        BP_PROF("bp_hash_build", bcnt[k].zero(s); bfill[k].zero(s);
-        if (np) {
-            k_hash_insert<<<nblk(np, 256), 256, 0, s>>>(np, lo, hi, gp, dhat, (unsigned)(T - 1), bcnt[k], bstart[k],
-                                                        bfill[k], ekey[k], eprim[k], 0, tot + k, cap_ent, overflow);
-            PDC_LAUNCH_CK();
-        }
-        exclusive_scan(s, bcnt[k], bstart[k], T, scratch, tot + k);
-        k_check_cap<<<1, 1, 0, s>>>(tot + k, cap_ent, OVF_HASH, overflow, tot + 4 + k);
-        if (np) {
-            k_hash_insert<<<nblk(np, 256), 256, 0, s>>>(np, lo, hi, gp, dhat, (unsigned)(T - 1), bcnt[k], bstart[k],
-                                                        bfill[k], ekey[k], eprim[k], 1, tot + k, cap_ent, overflow);
-            PDC_LAUNCH_CK();
-        });
+    const int np = cv.nv + cv.ne + cv.nt;
+    const unsigned mask = (unsigned)(T - 1);
+    // ---- cell table: count per bucket, prefix sum, fill
+    BP_PROF("bp_hash_build", bcnt.zero(s); bfill.zero(s);
+    if (np) {
+        k_cell_insert<<<nblk(np, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, elo, ehi, gp, dhat, mask, bcnt, bstart, bfill,
+                                                    ekey, epay, 0, tot, cap_ent, overflow);
+        PDC_LAUNCH_CK();
     }
-    // ---- VT candidates
-    if (prof) prof->begin(s, "bp_query_vt", 0.0);
-    if (cv.nv) {
-        auto query = [&](int qg) {
-#define PDC_QVT(Q)                                                                                                   \
-    k_query_vt<Q><<<nblk((long long)cv.nv * Q, QUERY_T), QUERY_T, 0, s>>>(cv, x0, x1, tlo, thi, gp, dhat,             \
-                                                                          (unsigned)(T_vt - 1), bcnt[0], bstart[0],  \
-                                                                          ekey[0], eprim[0], cnt_v, slots_vt, w_vt,  \
-                                                                          tot + 0, cap_ent, overflow)
-            if (qg == 4) PDC_QVT(4);
-            else if (qg == 16) PDC_QVT(16);
-            else PDC_QVT(8);
-#undef PDC_QVT
-            PDC_LAUNCH_CK();
-        };
-        if (tune_query) {
-            // each candidate writes the same counts and rows: time each, keep the fastest
-            tune_query = false;
-            const int cand[3] = {4, 8, 16};
-            cudaEvent_t e[4];
-            for (auto &ev : e) PDC_CK(cudaEventCreate(&ev));
-            query(8);  // warm-up
-            PDC_CK(cudaEventRecord(e[0], s));
-            for (int k = 0; k < 3; ++k) {
-                query(cand[k]);
-                PDC_CK(cudaEventRecord(e[k + 1], s));
-            }
-            PDC_CK(cudaEventSynchronize(e[3]));
-            int best = 1;
-            for (int k = 0; k < 3; ++k) {
-                PDC_CK(cudaEventElapsedTime(&query_ms[k], e[k], e[k + 1]));
-                if (query_ms[k] < query_ms[best]) best = k;
-            }
-            for (auto &ev : e) cudaEventDestroy(ev);
-            qg_vt = cand[best];
+    exclusive_scan(s, bcnt, bstart, T, scratch, tot);
+    k_check_cap<<<1, 1, 0, s>>>(tot, cap_ent, OVF_HASH, overflow, tot + 4);
+    if (np) {
+        k_cell_insert<<<nblk(np, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, elo, ehi, gp, dhat, mask, bcnt, bstart, bfill,
+                                                    ekey, epay, 1, tot, cap_ent, overflow);
+        PDC_LAUNCH_CK();
+    });
+    // ---- VT and EE pairs of every cell into the per-primary rows
+    if (prof) prof->begin(s, "bp_cell_pairs", 0.0);
+    RowsOut o;
+    o.cnt_v = cnt_v;
+    o.slots_vt = slots_vt;
+    o.cnt_e = cnt_e;
+    o.slots_ee = slots_ee;
+    o.w_vt = w_vt;
+    o.w_ee = w_ee;
+    o.overflow = overflow;
+    auto pairs = [&](int w) {
+        cnt_v.zero(s);
+        cnt_e.zero(s);
+        work.zero(s);
+        if (np == 0) return;
+#define PDC_CELLS(W, B)                                                                                            \
+    k_cell_pairs<W><<<152 * (B), (W) * 32, 0, s>>>(cv, x0, x1, tlo, thi, elo, ehi, dhat, T, bcnt, bstart, ekey, epay, \
+                                                   o, work, tot, cap_ent)
+        if (w == 2) PDC_CELLS(2, 12);
+        else if (w == 6) PDC_CELLS(6, 4);
+        else PDC_CELLS(4, 6);
+#undef PDC_CELLS
+        PDC_LAUNCH_CK();
+    };
+    if (tune_cells) {
+        // every candidate writes the same rows (up to their order, which the
+        // compaction sorts out): time each, keep the fastest
+        tune_cells = false;
+        const int cand[3] = {2, 4, 6};
+        cudaEvent_t e[4];
+        for (auto &ev : e) PDC_CK(cudaEventCreate(&ev));
+        pairs(4);  // warm-up
+        PDC_CK(cudaEventRecord(e[0], s));
+        for (int k = 0; k < 3; ++k) {
+            pairs(cand[k]);
+            PDC_CK(cudaEventRecord(e[k + 1], s));
         }
-        query(qg_vt);
+        PDC_CK(cudaEventSynchronize(e[3]));
+        int best = 1;
+        for (int k = 0; k < 3; ++k) {
+            PDC_CK(cudaEventElapsedTime(&cell_ms[k], e[k], e[k + 1]));
+            if (cell_ms[k] < cell_ms[best]) best = k;
+        }
+        for (auto &ev : e) cudaEventDestroy(ev);
+        cell_warps = cand[best];
+    } else {
+        pairs(cell_warps);
     }
+    if (prof) prof->end(s);
+    // ---- rows -> sorted pair lists
+    if (prof) prof->begin(s, "bp_compact", 0.0);
     exclusive_scan(s, cnt_v, off_v, cv.nv, scratch, tot + 2);
     k_check_cap<<<1, 1, 0, s>>>(tot + 2, cap_vt, OVF_VT, overflow, out_nvt);
     if (cv.nv) {
-        k_compact_slots<<<nblk(cv.nv, 256), 256, 0, s>>>(cv.nv, cnt_v, off_v, slots_vt, w_vt, tot + 2, cap_vt, out_vt);
-        PDC_LAUNCH_CK();
-    }
-    if (prof) prof->end(s);
-    // ---- EE candidates
-    if (prof) prof->begin(s, "bp_query_ee", 0.0);
-    if (cv.ne) {
-        k_query_ee<<<nblk(cv.ne, QUERY_T), QUERY_T, 0, s>>>(
-            cv, elo, ehi, gp, dhat, (unsigned)(T_ee - 1), bcnt[1], bstart[1], ekey[1], eprim[1], cnt_e,
-            slots_ee, w_ee, tot + 1, cap_ent, overflow);
+        k_compact_rows<<<nblk(cv.nv, 256), 256, 0, s>>>(cv.nv, cnt_v, off_v, slots_vt, w_vt, tot + 2, cap_vt, out_vt);
         PDC_LAUNCH_CK();
     }
     exclusive_scan(s, cnt_e, off_e, cv.ne, scratch, tot + 3);
     k_check_cap<<<1, 1, 0, s>>>(tot + 3, cap_ee, OVF_EE, overflow, out_nee);
     if (cv.ne) {
-        k_compact_slots<<<nblk(cv.ne, 256), 256, 0, s>>>(cv.ne, cnt_e, off_e, slots_ee, w_ee, tot + 3, cap_ee, out_ee);
+        k_compact_rows<<<nblk(cv.ne, 256), 256, 0, s>>>(cv.ne, cnt_e, off_e, slots_ee, w_ee, tot + 3, cap_ee, out_ee);
         PDC_LAUNCH_CK();
     }
     if (prof) prof->end(s);

@@ -58,17 +58,22 @@ struct PccdState {
     int cur;                 // which watch buffer is current
 };
 
+// Broad phase (Sec. 4 candidate pairs, culled by a uniform grid): one hash
+// table of grid cells holding every collision vertex, edge and triangle over
+// the cells its swept box covers, the box's upper side raised by d_hat; the
+// VT and EE pairs of each cell are tested from shared memory.
 struct BroadPhase {
     int nt = 0, ne = 0, nv = 0;
-    int T_vt = 0, T_ee = 0;
+    int T = 0;  // buckets of the cell table (power of two)
     long long cap_ent = 0, cap_vt = 0, cap_ee = 0;
     float cell_scale = 1.f;
-    DevBuf<int> bcnt[2], bstart[2], bfill[2];
-    DevBuf<unsigned long long> ekey[2];
-    DevBuf<int> eprim[2];
+    DevBuf<int> bcnt, bstart, bfill;
+    DevBuf<unsigned long long> ekey;  // cell key of each table entry
+    DevBuf<unsigned int> epay;        // primitive | kind << 27 | lowest-cell flags << 29
+    DevBuf<int> work;                 // bucket counter of the cell-pair kernel
     DevBuf<float4> tlo, thi, elo, ehi;
     DevBuf<int> cnt_v, off_v, cnt_e, off_e, scratch;
-    DevBuf<int> slots_vt, slots_ee;  // per-primary sorted candidate rows
+    DevBuf<int> slots_vt, slots_ee;  // per-primary candidate rows (sorted when compacted)
     int w_vt = 16, w_ee = 32;        // row widths (doubled on OVF_SLOTS)
     DevBuf<GridParams> gp;
     DevBuf<long long> totals;
@@ -80,12 +85,13 @@ struct BroadPhase {
     int cur = 0;
     unsigned gen = 0;          // counts reallocations of the buffers below (captured graphs go stale)
     // launch shapes (autotuned at the first step when asked): blocks of the
-    // pair kernels and lanes per vertex of the VT query; with tune_* set, the
-    // next launch times every candidate on its own data and keeps the fastest
+    // pair kernels and warps per block of the cell-pair kernel; with tune_*
+    // set, the next launch times every candidate on its own data and keeps
+    // the fastest
     int pair_blocks = 152 * 8;
-    int qg_vt = 8;
-    bool tune_pairs = false, tune_query = false;
-    float pair_ms[4] = {0, 0, 0, 0}, query_ms[3] = {0, 0, 0};
+    int cell_warps = 4;
+    bool tune_pairs = false, tune_cells = false;
+    float pair_ms[4] = {0, 0, 0, 0}, cell_ms[3] = {0, 0, 0};
     Profiler *prof = nullptr;  // optional sub-kernel timing
     long long h_pairs = 0;     // host copy of the current list size (kept while profiling)
     // partial-CCD filter: near list, double-buffered watch list, reference

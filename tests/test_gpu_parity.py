@@ -121,6 +121,44 @@ def test_broadphase_pairs_on_the_predicate_boundary(pc):
     pc.pdc_destroy(h)
 
 
+def _canon_ee(q):
+    """EE pairs as vertex quads (a, b, c, d), each edge as (min, max) and the
+    two edges in lexicographic order, rows sorted: a form independent of the
+    edge numbering of either side."""
+    q = np.asarray(q, np.int64).reshape(-1, 4)
+    e1 = np.sort(q[:, :2], axis=1)
+    e2 = np.sort(q[:, 2:], axis=1)
+    swap = (e1[:, 0] > e2[:, 0]) | ((e1[:, 0] == e2[:, 0]) & (e1[:, 1] > e2[:, 1]))
+    a = np.where(swap[:, None], e2, e1)
+    b = np.where(swap[:, None], e1, e2)
+    c = np.concatenate([a, b], axis=1)
+    return c[np.lexsort((c[:, 3], c[:, 2], c[:, 1], c[:, 0]))]
+
+
+def test_broadphase_full_lists_at_262k_vertices(pc):
+    """The whole VT and EE lists of the 512 x 512 swept sheet (the benchmark's
+    mesh, 1.8 M candidates, as many as the benchmark's steps hold) under a
+    3 mm motion across the sheet with noise, bit-exact against the oracle's
+    grid-culled lists, which are pinned to the brute force on small meshes."""
+    sc = wl.hanging_swept(side=512)
+    assert not sc.obstacles
+    cl = pc.Cloth(sc, params(pc, d_hat=1e-3))
+    rng = np.random.default_rng(23)
+    X0 = sc.verts.astype(np.float32)
+    X1 = X0.copy()
+    X1 += (rng.normal(size=X1.shape) * 0.0001 + np.array([0.0, 0.003, -0.0005])).astype(np.float32)
+    vt_g, ee_g = pc.pdc_op_broadphase(cl.h, X0, X1)
+    cl.close()
+    tris = np.asarray(sc.tris, np.int64)
+    ed = np.sort(np.concatenate([tris[:, [0, 1]], tris[:, [1, 2]], tris[:, [2, 0]]]), axis=1)
+    edges = np.unique(ed, axis=0)
+    vt_o, ee_o = collide.broadphase_grid(X0, X1, sc.n, tris, edges, 1e-3)
+    assert len(vt_o) > 100000 and len(ee_o) > 100000
+    assert np.array_equal(vt_g, vt_o)  # both sorted by (v, t)
+    q_o = np.concatenate([edges[ee_o[:, 0]], edges[ee_o[:, 1]]], axis=1)
+    assert np.array_equal(_canon_ee(ee_g), _canon_ee(q_o))
+
+
 def test_broadphase_sampled_at_65k_vertices(pc):
     sc = wl.fold_on_box(side=256, box_subdiv=16)
     cl = pc.Cloth(sc, params(pc, d_hat=1e-3))

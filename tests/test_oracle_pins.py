@@ -330,6 +330,52 @@ def test_partial_ccd_flags_crossing_and_not_separating():
 # broad phase, non-penetration
 # ----------------------------------------------------------------------------
 
+def _facing_sheets(n1, d):
+    """Two parallel sheets whose gap is exactly fl32(z + d_hat), shifted so
+    that facing primitives satisfy the FP32 predicate with equality on z."""
+    g = np.linspace(0.0, 0.5, n1, dtype=np.float32)
+    xx, yy = np.meshgrid(g, g, indexing="ij")
+    za = np.float32(0.3)
+    zb = np.float32(za + np.float32(d))
+    A = np.stack([xx.ravel(), yy.ravel(), np.full(n1 * n1, za, np.float32)], 1)
+    B = np.stack([xx.ravel() + np.float32(0.013), yy.ravel(), np.full(n1 * n1, zb, np.float32)], 1)
+    T = []
+    for i in range(n1 - 1):
+        for j in range(n1 - 1):
+            a, b, c, e = i * n1 + j, (i + 1) * n1 + j, i * n1 + j + 1, (i + 1) * n1 + j + 1
+            T += [[a, b, c], [b, e, c]]
+    T = np.array(T, np.int32)
+    return np.concatenate([A, B]).astype(np.float32), np.concatenate([T, T + n1 * n1]).astype(np.int32)
+
+
+def test_broadphase_grid_equals_the_brute_force():
+    """The grid-culled lists (for sizes the brute force cannot reach) equal
+    the brute-force definition: a swept drape with an obstacle, and two
+    sheets exactly d_hat apart (pairs on the predicate boundary), for grid
+    cells far smaller and far larger than the primitives."""
+    rng = np.random.default_rng(31)
+    sc = wl.drape_sphere(side=12, sphere_subdiv=2)
+    m = pd.Model(sc.verts, sc.tris, sc.pins, 0.1, 1e3, 1e-2, 0.005)
+    cm = pd.CollisionMesh(m, sc.obstacles)
+    X0 = np.concatenate([sc.verts] + [o.positions(0.0) for o in sc.obstacles]).astype(np.float32)
+    X1 = X0.copy()
+    X1[: sc.n] += (rng.normal(size=(sc.n, 3)) * 0.01 + np.array([0, 0, -0.05])).astype(np.float32)
+    cases = [(X0, X1, cm.nc, cm.tris, cm.edges, 1e-3)]
+    V, T = _facing_sheets(9, 1e-3)
+    ms = pd.Model(V, T, np.zeros(0, np.int32), 0.1, 1e3, 1e-2, 0.005)
+    cs = pd.CollisionMesh(ms, [])
+    cases.append((V, V, cs.nc, cs.tris, cs.edges, 1e-3))
+    for X0_, X1_, nc, tris, edges, d in cases:
+        vt_b, ee_b = collide.broadphase(X0_, X1_, nc, tris, edges, d)
+        assert len(vt_b) > 50 and len(ee_b) > 50
+        vt_b = vt_b[np.lexsort((vt_b[:, 1], vt_b[:, 0]))]
+        ee_b = ee_b[np.lexsort((ee_b[:, 1], ee_b[:, 0]))]
+        for cell in (None, 2e-3, 0.02, 0.3, 2.0):
+            vt_g, ee_g = collide.broadphase_grid(X0_, X1_, nc, tris, edges, d, cell)
+            assert np.array_equal(vt_g, vt_b), cell
+            assert np.array_equal(ee_g, ee_b), cell
+
+
 def test_broadphase_contains_every_colliding_pair():
     rng = np.random.default_rng(12)
     sc = wl.tiny_scene(side=6)

@@ -1,9 +1,10 @@
 """GPU test of pdc_op_contact_noalloc, the allocation-free variant of
-pdc_op_contact (collision springs of Sec. 5.1 with A_i = B_i = Id).
+pdc_op_contact.
 
 It must give what pdc_op_contact gives on the same inputs -- up to the
 order of the float atomics that accumulate per-vertex sums, hence the
-relative tolerances below -- on two calls in a row, with the outputs filled
+relative tolerances below -- and what the oracle's contact_terms gives for
+the same pairs and weights, on two calls in a row, with the outputs filled
 with garbage in between (nothing has to start at zero), and reject inputs
 larger than its static scratch before doing any work.  The file name keeps it
 last in collection so that it also runs after the other GPU tests.
@@ -30,14 +31,18 @@ def env():
     return torch, pdcloth
 
 
+def _mesh(sc):
+    m = pd.Model(sc.verts, sc.tris, sc.pins, 0.1, 1e3, 1e-2, 0.005)
+    return pd.CollisionMesh(m, sc.obstacles)
+
+
 def _case(pc, seed):
     rng = np.random.default_rng(seed)
     sc = wl.drape_sphere(side=16, sphere_subdiv=2)
     p = pc.pdc_default_params()
     p.d_hat = 1e-3
     cl = pc.Cloth(sc, p)
-    m = pd.Model(sc.verts, sc.tris, sc.pins, 0.1, 1e3, 1e-2, 0.005)
-    cm = pd.CollisionMesh(m, sc.obstacles)
+    cm = _mesh(sc)
     X0 = np.concatenate([sc.verts] + [o.positions(0.0) for o in sc.obstacles]).astype(np.float32)
     X1 = X0.copy()
     X1[: sc.n] += (rng.normal(size=(sc.n, 3)) * 0.02).astype(np.float32)
@@ -64,6 +69,10 @@ def test_noalloc_contact_matches_contact_twice(env):
     assert len(quads) > 50
     cw_ref, cf_ref = pc.pdc_op_contact(cl.h, sc.n, X0, X1, quads, kinds, w)
     assert np.max(cw_ref) > 0 and np.max(np.abs(cf_ref)) > 0
+    # the oracle's springs (Sec. 5.1) for the same pairs and weights, every pair active
+    cw_o, cy_o = pd.contact_terms(_mesh(sc), X0.astype(np.float64), X1.astype(np.float64),
+                                  np.ones(len(quads), bool), quads, kinds, w.astype(np.float64), 1e-3)
+    cf_o = cy_o - cw_o[:, None] * X1[: sc.n].astype(np.float64)
     cw = torch.full((sc.n,), float("nan"), device="cuda")
     cf = torch.full((sc.n, 3), float("nan"), device="cuda")
     for _ in range(2):
@@ -71,6 +80,8 @@ def test_noalloc_contact_matches_contact_twice(env):
         assert np.all(np.isfinite(got_cw)) and np.all(np.isfinite(got_cf))
         assert np.max(np.abs(got_cw - cw_ref)) <= 1e-5 * np.max(cw_ref)
         assert np.max(np.abs(got_cf - cf_ref)) <= 1e-5 * np.max(np.abs(cf_ref))
+        assert np.max(np.abs(got_cw - cw_o)) <= 1e-5 * np.max(cw_o)
+        assert np.max(np.abs(got_cf - cf_o)) <= 1e-4 * max(np.max(np.abs(cf_o)), 1e-12)
         cw.fill_(1e30)
         cf.fill_(-1e30)
     cl.close()
