@@ -239,7 +239,7 @@ typedef struct {
                                 tiles; 0: the ELL arrays (candidates 1, 0)      */
     int32_t pair_blocks;     /* blocks of the per-pair kernels (152 x 2, 4, 8, 16) */
     int32_t cell_warps;      /* warps per block of the broad phase's cell-pair
-                                kernel (candidates 2, 4, 6)                     */
+                                kernel (candidates 2, 4, 8)                     */
     float residual_ms[3];
     float cheb_ms[2];
     float pair_ms[4];

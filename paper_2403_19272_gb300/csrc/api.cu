@@ -1270,13 +1270,14 @@ void pdc_ctx::autotune_vertex_kernels() {
         return ms / 3.f;
     };
     const int bsz[3] = {64, 128, 256};
-    int best = 2;
     for (int k = 0; k < 3; ++k) {
         tune.residual_block = bsz[k];
         ClothView c = cloth();
         tune.residual_ms[k] = timed([&] { launch_residual(s, c, Xs, Ucur, Z, nullptr, nullptr, R, nullptr, nullptr, 0); });
-        if (tune.residual_ms[k] < tune.residual_ms[best]) best = k;
     }
+    int best = 0;  // the fastest, once all are timed
+    for (int k = 1; k < 3; ++k)
+        if (tune.residual_ms[k] < tune.residual_ms[best]) best = k;
     tune.residual_block = bsz[best];
     if (P.sweep_kind == 1 && ell_tile.p) {
         // one Chebyshev step from delta = 0 on the residual just formed (scratch outputs)

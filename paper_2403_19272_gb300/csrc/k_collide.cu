@@ -51,18 +51,6 @@ __device__ inline bool box_overlap(float3 alo, float3 ahi, float3 blo, float3 bh
            blo.y <= __fadd_rn(ahi.y, d) && alo.z <= __fadd_rn(bhi.z, d) && blo.z <= __fadd_rn(ahi.z, d);
 }
 
-// insertion sort of a short row
-__device__ inline void sort_row(int *row, int c) {
-    for (int i = 1; i < c; ++i) {
-        int q = row[i], j = i - 1;
-        while (j >= 0 && row[j] > q) {
-            row[j + 1] = row[j];
-            --j;
-        }
-        row[j + 1] = q;
-    }
-}
-
 __device__ inline void vbox(const float4 *x0, const float4 *x1, int v, float3 &lo, float3 &hi) {
     float3 a = f3(x0[v]), b = f3(x1[v]);
     lo = fmin3(a, b);
@@ -228,34 +216,85 @@ __global__ void k_cell_insert(CollView cv, const float4 *__restrict__ x0, const 
 // other cells that share the bucket are told apart by their keys.  A
 // candidate (v, t) or (e, f), e < f, is appended to the row of v or e; rows
 // are sorted when they are compacted.
+//
+// Most pairs that share a cell fail either the owner test or the predicate,
+// so each entry also carries its raised box quantized to 8 bits per axis
+// within the cell, q = clamp(floor or ceil((v - cell origin) * 256 / cell),
+// 0, 255): a map that is monotone in v, so quantized boxes of a pair that
+// meets the predicate in this cell meet too.  The three fields sit at bits
+// 0, 9 and 18 of a word, the high corner's word with the guard bits 8, 17
+// and 26 set, so that one subtraction compares all three (a field's guard
+// bit survives hi - lo iff lo <= hi); the low corner's word carries the
+// owner flags (bits 27..29) and FL_FIXED (bit 30).  Pairs that pass this
+// prefilter go through a per-warp queue to the full test, so that the rare
+// survivors do not stall the lanes that keep scanning.
 constexpr int CELL_CHUNK = 64;
-constexpr unsigned FL_FIXED = 1u << 3;  // every vertex of the primitive is an obstacle vertex
+constexpr unsigned FL_FIXED = 1u << 3;       // every vertex of the primitive is an obstacle vertex
+constexpr unsigned Q_GUARD = (1u << 8) | (1u << 17) | (1u << 26);
+constexpr unsigned Q_OWNER = 7u << 27;       // lowest-cell flags in the low corner's word
+constexpr unsigned Q_FIXED = FL_FIXED << 27;
+constexpr int QUEUE = 64;                    // survivor queue per warp
 
+// One chunk of a bucket in shared memory, in kind order: vertices [0, nv),
+// edges [nv, nv + ne), triangles [nv + ne, nv + ne + nt).
 struct CellRegion {
-    float4 lo[CELL_CHUNK];  // w: primitive id
-    float4 hi[CELL_CHUNK];  // w: lowest-cell flags | FL_FIXED
-    int4 ids[CELL_CHUNK];   // vertex ids (-1 past the primitive's own)
+    float4 lo[CELL_CHUNK];   // w: primitive id
+    float4 hi[CELL_CHUNK];
+    int4 ids[CELL_CHUNK];    // vertex ids (-1 past the primitive's own)
     unsigned long long key[CELL_CHUNK];
-    unsigned char lv[CELL_CHUNK], le[CELL_CHUNK], lt[CELL_CHUNK];
+    unsigned int qlo[CELL_CHUNK];  // quantized low corner | (lowest-cell flags | FL_FIXED) << 27
+    unsigned int qhi[CELL_CHUNK];  // quantized raised high corner | Q_GUARD
 };
+
+// per warp: two chunk regions and the survivor queue
+struct CellWarp {
+    CellRegion r[2];
+    unsigned int queue[QUEUE];
+};
+
+__device__ inline unsigned quant_lo(float v, float c0, float s) {
+    return (unsigned)fminf(fmaxf(floorf(__fmul_rn(__fsub_rn(v, c0), s)), 0.f), 255.f);
+}
+__device__ inline unsigned quant_hi(float v, float c0, float s) {
+    return (unsigned)fminf(fmaxf(ceilf(__fmul_rn(__fsub_rn(v, c0), s)), 0.f), 255.f);
+}
 
 struct KindCounts {
     int v, e, t;
 };
 
-__device__ inline KindCounts load_chunk(CellRegion &R, const CollView &cv, const float4 *x0, const float4 *x1,
+// Loads entries [e0, e0 + cnt) of the table into R in kind order (a count
+// pass over the payloads, then the write pass).
+__device__ __forceinline__ KindCounts load_chunk(CellRegion &R, const CollView &cv, const float4 *x0, const float4 *x1,
                                         const float4 *tlo, const float4 *thi, const float4 *elo, const float4 *ehi,
                                         const unsigned long long *ekey, const unsigned int *epay, int e0, int cnt,
-                                        unsigned lane) {
-    KindCounts kc = {0, 0, 0};
+                                        float cell, float dhat, unsigned lane) {
+    const float qs = 256.f / cell;
     const unsigned below = (1u << lane) - 1u;
+    KindCounts kc = {0, 0, 0};
     for (int base = 0; base < cnt; base += 32) {  // warp-uniform
         const int i = base + (int)lane;
+        const int kind = i < cnt ? (int)((epay[e0 + i] >> 27) & 3u) : -1;
+        kc.v += __popc(__ballot_sync(0xffffffffu, kind == KIND_V));
+        kc.e += __popc(__ballot_sync(0xffffffffu, kind == KIND_E));
+        kc.t += __popc(__ballot_sync(0xffffffffu, kind == KIND_T));
+    }
+    int cv_ = 0, ce = kc.v, ct = kc.v + kc.e;  // next slot of each kind
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + (int)lane;
+        unsigned pay = 0;
         int kind = -1;
         if (i < cnt) {
-            const unsigned pay = epay[e0 + i];
-            const int prim = (int)(pay & PAY_PRIM);
+            pay = epay[e0 + i];
             kind = (int)((pay >> 27) & 3u);
+        }
+        const unsigned mv = __ballot_sync(0xffffffffu, kind == KIND_V);
+        const unsigned me = __ballot_sync(0xffffffffu, kind == KIND_E);
+        const unsigned mt = __ballot_sync(0xffffffffu, kind == KIND_T);
+        if (kind >= 0) {
+            const int d = kind == KIND_V ? cv_ + __popc(mv & below)
+                                         : (kind == KIND_E ? ce + __popc(me & below) : ct + __popc(mt & below));
+            const int prim = (int)(pay & PAY_PRIM);
             unsigned fl = pay >> 29;
             float3 lo, hi;
             int4 ids;
@@ -276,30 +315,35 @@ __device__ inline KindCounts load_chunk(CellRegion &R, const CollView &cv, const
                 ids = make_int4(Tr.x, Tr.y, Tr.z, -1);
                 if (Tr.x >= cv.nc && Tr.y >= cv.nc && Tr.z >= cv.nc) fl |= FL_FIXED;
             }
-            R.lo[i] = make_float4(lo.x, lo.y, lo.z, __int_as_float(prim));
-            R.hi[i] = make_float4(hi.x, hi.y, hi.z, __uint_as_float(fl));
-            R.ids[i] = ids;
-            R.key[i] = ekey[e0 + i];
+            const unsigned long long key = ekey[e0 + i];
+            R.lo[d] = make_float4(lo.x, lo.y, lo.z, __int_as_float(prim));
+            R.hi[d] = make_float4(hi.x, hi.y, hi.z, 0.f);
+            R.ids[d] = ids;
+            R.key[d] = key;
+            // cell origin from the key (the same for every entry of the cell)
+            const float cx = __fmul_rn((float)((int)((key >> 42) & 0x1fffffu) - CELL_BIAS), cell);
+            const float cy = __fmul_rn((float)((int)((key >> 21) & 0x1fffffu) - CELL_BIAS), cell);
+            const float cz = __fmul_rn((float)((int)(key & 0x1fffffu) - CELL_BIAS), cell);
+            const float3 hr = raise_d(hi, dhat);
+            R.qlo[d] = quant_lo(lo.x, cx, qs) | (quant_lo(lo.y, cy, qs) << 9) | (quant_lo(lo.z, cz, qs) << 18) |
+                       (fl << 27);
+            R.qhi[d] = quant_hi(hr.x, cx, qs) | (quant_hi(hr.y, cy, qs) << 9) | (quant_hi(hr.z, cz, qs) << 18) |
+                       Q_GUARD;
         }
-        const unsigned mv = __ballot_sync(0xffffffffu, kind == KIND_V);
-        const unsigned me = __ballot_sync(0xffffffffu, kind == KIND_E);
-        const unsigned mt = __ballot_sync(0xffffffffu, kind == KIND_T);
-        if (kind == KIND_V) R.lv[kc.v + __popc(mv & below)] = (unsigned char)i;
-        if (kind == KIND_E) R.le[kc.e + __popc(me & below)] = (unsigned char)i;
-        if (kind == KIND_T) R.lt[kc.t + __popc(mt & below)] = (unsigned char)i;
-        kc.v += __popc(mv);
-        kc.e += __popc(me);
-        kc.t += __popc(mt);
+        cv_ += __popc(mv);
+        ce += __popc(me);
+        ct += __popc(mt);
     }
     __syncwarp();
     return kc;
 }
 
-// q = floor(k / n) for k < 2^12 and 0 < n <= CELL_CHUNK: (k + 1/2) / n is at
-// least 1/(2n) from an integer, far more than the float error of the product.
-__device__ inline int div_small(int k, float inv_n) { return (int)(((float)k + 0.5f) * inv_n); }
-
-__device__ inline bool owner_pair(unsigned fa, unsigned fb) { return ((fa | fb) & 7u) == 7u; }
+// owner test, both-kinematic test and quantized boxes (of one cell when the
+// keys agree, which the full tests check)
+__device__ __forceinline__ bool prefilter(unsigned la, unsigned ha, unsigned lb, unsigned hb) {
+    const unsigned meet = (hb - la) & (ha - lb) & Q_GUARD;
+    return ((la | lb) & Q_OWNER) == Q_OWNER && (la & lb & Q_FIXED) == 0 && meet == Q_GUARD;
+}
 
 struct RowsOut {
     int *cnt_v, *slots_vt, *cnt_e, *slots_ee;
@@ -307,36 +351,32 @@ struct RowsOut {
     int *overflow;
 };
 
-__device__ inline void emit(int *cnt, int *slots, int width, int p, int q, int *overflow) {
+__device__ __forceinline__ void emit(int *cnt, int *slots, int width, int p, int q, int *overflow) {
     const int slot = atomicAdd(&cnt[p], 1);
     if (slot < width) slots[(size_t)p * width + slot] = q;
     else if (slot == width) atomicOr(overflow, OVF_SLOTS);
 }
 
-// (vertex entry i of A, triangle entry j of B)
-__device__ inline void test_vt(const CellRegion &A, int i, const CellRegion &B, int j, float dhat, const RowsOut &o) {
+// (vertex entry i of A, triangle entry j of B) past the prefilter
+__device__ __forceinline__ void full_vt(const CellRegion &A, int i, const CellRegion &B, int j, float dhat,
+                                        const RowsOut &o) {
     if (A.key[i] != B.key[j]) return;
-    const float4 alo = A.lo[i], ahi = A.hi[i], blo = B.lo[j], bhi = B.hi[j];
-    const unsigned fa = __float_as_uint(ahi.w), fb = __float_as_uint(bhi.w);
-    if (!owner_pair(fa, fb)) return;
+    const float4 alo = A.lo[i], blo = B.lo[j];
     const int v = __float_as_int(alo.w);
     const int4 T = B.ids[j];
     if (T.x == v || T.y == v || T.z == v) return;
-    if ((fa & fb & FL_FIXED) != 0) return;
-    if (!box_overlap(f3(alo), f3(ahi), f3(blo), f3(bhi), dhat)) return;
+    if (!box_overlap(f3(alo), f3(A.hi[i]), f3(blo), f3(B.hi[j]), dhat)) return;
     emit(o.cnt_v, o.slots_vt, o.w_vt, v, __float_as_int(blo.w), o.overflow);
 }
 
-// (edge entry i of A, edge entry j of B)
-__device__ inline void test_ee(const CellRegion &A, int i, const CellRegion &B, int j, float dhat, const RowsOut &o) {
+// (edge entry i of A, edge entry j of B) past the prefilter
+__device__ __forceinline__ void full_ee(const CellRegion &A, int i, const CellRegion &B, int j, float dhat,
+                                        const RowsOut &o) {
     if (A.key[i] != B.key[j]) return;
-    const float4 alo = A.lo[i], ahi = A.hi[i], blo = B.lo[j], bhi = B.hi[j];
-    const unsigned fa = __float_as_uint(ahi.w), fb = __float_as_uint(bhi.w);
-    if (!owner_pair(fa, fb)) return;
     const int4 a = A.ids[i], b = B.ids[j];
     if (a.x == b.x || a.x == b.y || a.y == b.x || a.y == b.y) return;
-    if ((fa & fb & FL_FIXED) != 0) return;
-    if (!box_overlap(f3(alo), f3(ahi), f3(blo), f3(bhi), dhat)) return;
+    const float4 alo = A.lo[i], blo = B.lo[j];
+    if (!box_overlap(f3(alo), f3(A.hi[i]), f3(blo), f3(B.hi[j]), dhat)) return;
     int e = __float_as_int(alo.w), f = __float_as_int(blo.w);
     if (e > f) {
         const int t = e;
@@ -346,49 +386,92 @@ __device__ inline void test_ee(const CellRegion &A, int i, const CellRegion &B, 
     emit(o.cnt_e, o.slots_ee, o.w_ee, e, f, o.overflow);
 }
 
-// every (vertex of A, triangle of B)
-__device__ inline void pairs_vt(const CellRegion &A, int nv, const CellRegion &B, int nt, float dhat,
-                                const RowsOut &o, unsigned lane) {
-    const int n = nv * nt;
-    if (n == 0) return;
-    const float inv = 1.f / (float)nt;
-    for (int k = (int)lane; k < n; k += 32) {
-        const int i = div_small(k, inv), j = k - i * nt;
-        test_vt(A, A.lv[i], B, B.lt[j], dhat, o);
+// Survivor queue of one warp: code = i | region_i << 6 | j << 7 | region_j << 13 | ee << 14.
+struct PairQueue {
+    CellWarp &w;
+    const float dhat;
+    const RowsOut &o;
+    const unsigned lane;
+    int n = 0;  // warp-uniform
+    __device__ __forceinline__ void run(unsigned c) const {
+        const int i = (int)(c & 63u), j = (int)((c >> 7) & 63u);
+        const CellRegion &A = w.r[(c >> 6) & 1u], &B = w.r[(c >> 13) & 1u];
+        if (c & (1u << 14)) full_ee(A, i, B, j, dhat, o);
+        else full_vt(A, i, B, j, dhat, o);
     }
-}
-
-// every unordered pair of edges of A: pair (i, i + d mod n) for offsets
-// d = 1 .. (n - 1) / 2 and every i, and, for even n, (i, i + n / 2), i < n / 2
-__device__ inline void pairs_ee_within(const CellRegion &A, int n, float dhat, const RowsOut &o, unsigned lane) {
-    if (n < 2) return;
-    const int h = (n - 1) / 2, n1 = n * h, tot = n * (n - 1) / 2;
-    const float inv = 1.f / (float)n;
-    for (int k = (int)lane; k < tot; k += 32) {
-        int i, d;
-        if (k < n1) {
-            d = div_small(k, inv);
-            i = k - d * n;
-            d += 1;
-        } else {
-            i = k - n1;
-            d = n / 2;
+    // every lane calls it (pass: its pair survived the prefilter)
+    __device__ __forceinline__ void push(bool pass, unsigned code) {
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (pass) w.queue[n + __popc(m & ((1u << lane) - 1u))] = code;
+        n += __popc(m);
+        if (n >= 32) {  // one survivor per lane
+            __syncwarp();
+            n -= 32;
+            run(w.queue[n + lane]);
+            __syncwarp();
         }
-        int j = i + d;
-        if (j >= n) j -= n;
-        test_ee(A, A.le[i], A, A.le[j], dhat, o);
+    }
+    __device__ __forceinline__ void flush() {
+        __syncwarp();
+        if ((int)lane < n) run(w.queue[lane]);
+        n = 0;
+        __syncwarp();
+    }
+};
+
+// every (vertex of region a, triangle of region b): lanes own the triangles
+// (their quantized boxes in registers) and run through the vertices
+__device__ __forceinline__ void pairs_vt(PairQueue &q, int ra, KindCounts ka, int rb, KindCounts kb) {
+    if (ka.v == 0 || kb.t == 0) return;
+    const CellRegion &A = q.w.r[ra], &B = q.w.r[rb];
+    const int t0 = kb.v + kb.e;
+    for (int tb = 0; tb < kb.t; tb += 32) {  // warp-uniform
+        const bool own = tb + (int)q.lane < kb.t;
+        const int j = t0 + (own ? tb + (int)q.lane : 0);
+        const unsigned lb = B.qlo[j], hb = B.qhi[j];
+        for (int i = 0; i < ka.v; ++i) {
+            const bool pass = own && prefilter(A.qlo[i], A.qhi[i], lb, hb);
+            q.push(pass, (unsigned)i | ((unsigned)ra << 6) | ((unsigned)j << 7) | ((unsigned)rb << 13));
+        }
     }
 }
 
-// every (edge of A, edge of B), A and B disjoint chunks
-__device__ inline void pairs_ee_across(const CellRegion &A, int na, const CellRegion &B, int nb, float dhat,
-                                       const RowsOut &o, unsigned lane) {
-    const int n = na * nb;
-    if (n == 0) return;
-    const float inv = 1.f / (float)nb;
-    for (int k = (int)lane; k < n; k += 32) {
-        const int i = div_small(k, inv), j = k - i * nb;
-        test_ee(A, A.le[i], B, B.le[j], dhat, o);
+// every unordered pair of edges of region a: lane entry ii meets ii + d
+// (mod n) for d = 1 .. (n - 1) / 2, and, for even n, ii + n / 2 when ii < n / 2
+__device__ __forceinline__ void pairs_ee_within(PairQueue &q, int ra, KindCounts ka) {
+    const int n = ka.e;
+    if (n < 2) return;
+    const CellRegion &A = q.w.r[ra];
+    const int e0 = ka.v, h = (n - 1) / 2, dlim = h + ((n & 1) == 0 ? 1 : 0);
+    for (int ib = 0; ib < n; ib += 32) {  // warp-uniform
+        const int ii = ib + (int)q.lane;
+        const bool own = ii < n;
+        const int i = e0 + (own ? ii : 0);
+        const unsigned la = A.qlo[i], ha = A.qhi[i];
+        const int dmax = own ? h + (((n & 1) == 0 && ii < n / 2) ? 1 : 0) : 0;
+        int jj = own ? ii : 0;
+        for (int d = 1; d <= dlim; ++d) {
+            if (++jj >= n) jj -= n;
+            const int j = e0 + jj;
+            const bool pass = d <= dmax && prefilter(la, ha, A.qlo[j], A.qhi[j]);
+            q.push(pass, (unsigned)i | ((unsigned)ra << 6) | ((unsigned)j << 7) | ((unsigned)ra << 13) | (1u << 14));
+        }
+    }
+}
+
+// every (edge of region a, edge of region b), two chunks of one bucket
+__device__ __forceinline__ void pairs_ee_across(PairQueue &q, int ra, KindCounts ka, int rb, KindCounts kb) {
+    if (ka.e == 0 || kb.e == 0) return;
+    const CellRegion &A = q.w.r[ra], &B = q.w.r[rb];
+    for (int ib = 0; ib < ka.e; ib += 32) {  // warp-uniform
+        const bool own = ib + (int)q.lane < ka.e;
+        const int i = ka.v + (own ? ib + (int)q.lane : 0);
+        const unsigned la = A.qlo[i], ha = A.qhi[i];
+        for (int jj = 0; jj < kb.e; ++jj) {
+            const int j = kb.v + jj;
+            const bool pass = own && prefilter(la, ha, B.qlo[j], B.qhi[j]);
+            q.push(pass, (unsigned)i | ((unsigned)ra << 6) | ((unsigned)j << 7) | ((unsigned)rb << 13) | (1u << 14));
+        }
     }
 }
 
@@ -400,12 +483,14 @@ __global__ void __launch_bounds__(W * 32) k_cell_pairs(CollView cv, const float4
                                                        const int *__restrict__ bcnt, const int *__restrict__ bstart,
                                                        const unsigned long long *__restrict__ ekey,
                                                        const unsigned int *__restrict__ epay, RowsOut o, int *work,
-                                                       const long long *hash_total, long long cap_ent) {
-    __shared__ CellRegion reg[W][2];
+                                                       const GridParams *gp, const long long *hash_total,
+                                                       long long cap_ent) {
+    extern __shared__ __align__(16) unsigned char cell_smem[];  // W CellWarp
     if (*hash_total > cap_ent) return;  // table not filled: no candidates (the pass is redone)
     const unsigned lane = threadIdx.x & 31;
-    CellRegion &RA = reg[threadIdx.x >> 5][0];
-    CellRegion &RB = reg[threadIdx.x >> 5][1];
+    CellWarp &cw = reinterpret_cast<CellWarp *>(cell_smem)[threadIdx.x >> 5];
+    PairQueue q{cw, dhat, o, lane};
+    const float cell = gp->cell;
     for (;;) {
         int b0 = 0;
         if (lane == 0) b0 = atomicAdd(work, 32);
@@ -422,36 +507,58 @@ __global__ void __launch_bounds__(W * 32) k_cell_pairs(CollView cv, const float4
             const int eb = __shfl_sync(0xffffffffu, st, l);
             const int nch = (mb + CELL_CHUNK - 1) / CELL_CHUNK;
             for (int ca = 0; ca < nch; ++ca) {
-                const KindCounts a = load_chunk(RA, cv, x0, x1, tlo, thi, elo, ehi, ekey, epay, eb + ca * CELL_CHUNK,
-                                                min(CELL_CHUNK, mb - ca * CELL_CHUNK), lane);
-                pairs_vt(RA, a.v, RA, a.t, dhat, o, lane);
-                pairs_ee_within(RA, a.e, dhat, o, lane);
+                const KindCounts a = load_chunk(cw.r[0], cv, x0, x1, tlo, thi, elo, ehi, ekey, epay,
+                                                eb + ca * CELL_CHUNK, min(CELL_CHUNK, mb - ca * CELL_CHUNK), cell,
+                                                dhat, lane);
+                pairs_vt(q, 0, a, 0, a);
+                pairs_ee_within(q, 0, a);
                 for (int cb = ca + 1; cb < nch; ++cb) {
-                    const KindCounts c = load_chunk(RB, cv, x0, x1, tlo, thi, elo, ehi, ekey, epay,
-                                                    eb + cb * CELL_CHUNK, min(CELL_CHUNK, mb - cb * CELL_CHUNK), lane);
-                    pairs_vt(RA, a.v, RB, c.t, dhat, o, lane);
-                    pairs_vt(RB, c.v, RA, a.t, dhat, o, lane);
-                    pairs_ee_across(RA, a.e, RB, c.e, dhat, o, lane);
-                    __syncwarp();  // RB is reloaded next
+                    const KindCounts c = load_chunk(cw.r[1], cv, x0, x1, tlo, thi, elo, ehi, ekey, epay,
+                                                    eb + cb * CELL_CHUNK, min(CELL_CHUNK, mb - cb * CELL_CHUNK), cell,
+                                                    dhat, lane);
+                    pairs_vt(q, 0, a, 1, c);
+                    pairs_vt(q, 1, c, 0, a);
+                    pairs_ee_across(q, 0, a, 1, c);
+                    q.flush();  // region 1 is reloaded next
                 }
-                __syncwarp();  // RA is reloaded next
+                q.flush();  // region 0 is reloaded next
             }
         }
     }
 }
 
-// out[off[p] + k] = (p, k-th smallest of row p) for k < cnt[p]; the row is
-// sorted in place first (rows are short), so the list comes out sorted by
-// (primary, secondary) whatever order the appends took
+// out[off[p] + k] = (p, k-th smallest of row p) for k < cnt[p]: the list
+// comes out sorted by (primary, secondary) whatever order the appends took.
+// A warp takes 32 rows; for each non-empty one its lanes hold the row's
+// entries and place each at its rank (entries of a row are distinct).
 __global__ void k_compact_rows(int np, const int *__restrict__ cnt, const int *__restrict__ off,
-                               int *__restrict__ slots, int width, const long long *total, long long cap,
+                               const int *__restrict__ slots, int width, const long long *total, long long cap,
                                int2 *__restrict__ out) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np || *total > cap) return;
-    const int c = min(cnt[p], width), o = off[p];
-    int *row = slots + (size_t)p * width;
-    sort_row(row, c);
-    for (int k = 0; k < c; ++k) out[o + k] = make_int2(p, row[k]);
+    const unsigned lane = threadIdx.x & 31;
+    const int p0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31;
+    if (p0 >= np || *total > cap) return;  // uniform per warp
+    const int p = p0 + (int)lane;
+    const int c = p < np ? min(cnt[p], width) : 0;
+    const int o = p < np ? off[p] : 0;
+    unsigned todo = __ballot_sync(0xffffffffu, c > 0);
+    while (todo) {
+        const int l = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const int q = p0 + l;
+        const int cq = __shfl_sync(0xffffffffu, c, l), oq = __shfl_sync(0xffffffffu, o, l);
+        const int *row = slots + (size_t)q * width;
+        for (int k0 = 0; k0 < cq; k0 += 32) {  // entries k0 + lane ranked against the whole row
+            const int k = k0 + (int)lane;
+            const int v = k < cq ? row[k] : 0x7fffffff;
+            int rank = 0;
+            for (int j0 = 0; j0 < cq; j0 += 32) {
+                const int w = j0 + (int)lane < cq ? row[j0 + lane] : 0x7fffffff;
+                const int nj = min(32, cq - j0);
+                for (int j = 0; j < nj; ++j) rank += __shfl_sync(0xffffffffu, w, j) < v ? 1 : 0;
+            }
+            if (k < cq) out[oq + rank] = make_int2(q, v);
+        }
+    }
 }
 
 __global__ void k_check_cap(const long long *total, long long cap, int flag, int *overflow, long long *count_out) {
@@ -692,11 +799,20 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
         cnt_e.zero(s);
         work.zero(s);
         if (np == 0) return;
-#define PDC_CELLS(W, B)                                                                                            \
-    k_cell_pairs<W><<<152 * (B), (W) * 32, 0, s>>>(cv, x0, x1, tlo, thi, elo, ehi, dhat, T, bcnt, bstart, ekey, epay, \
-                                                   o, work, tot, cap_ent)
+        // about 24 resident warps per SM for each shape (two regions per warp)
+#define PDC_CELLS(W, B)                                                                                              \
+    do {                                                                                                             \
+        const int smem = (W) * (int)sizeof(CellWarp);                                                               \
+        static bool attr = false;                                                                                    \
+        if (!attr) {                                                                                                 \
+            PDC_CK(cudaFuncSetAttribute(k_cell_pairs<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));        \
+            attr = true;                                                                                             \
+        }                                                                                                            \
+        k_cell_pairs<W><<<152 * (B), (W) * 32, smem, s>>>(cv, x0, x1, tlo, thi, elo, ehi, dhat, T, bcnt, bstart, ekey, \
+                                                          epay, o, work, gp, tot, cap_ent);                          \
+    } while (0)
         if (w == 2) PDC_CELLS(2, 12);
-        else if (w == 6) PDC_CELLS(6, 4);
+        else if (w == 8) PDC_CELLS(8, 3);
         else PDC_CELLS(4, 6);
 #undef PDC_CELLS
         PDC_LAUNCH_CK();
@@ -705,7 +821,7 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
         // every candidate writes the same rows (up to their order, which the
         // compaction sorts out): time each, keep the fastest
         tune_cells = false;
-        const int cand[3] = {2, 4, 6};
+        const int cand[3] = {2, 4, 8};
         cudaEvent_t e[4];
         for (auto &ev : e) PDC_CK(cudaEventCreate(&ev));
         pairs(4);  // warm-up
@@ -715,11 +831,10 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
             PDC_CK(cudaEventRecord(e[k + 1], s));
         }
         PDC_CK(cudaEventSynchronize(e[3]));
-        int best = 1;
-        for (int k = 0; k < 3; ++k) {
-            PDC_CK(cudaEventElapsedTime(&cell_ms[k], e[k], e[k + 1]));
+        for (int k = 0; k < 3; ++k) PDC_CK(cudaEventElapsedTime(&cell_ms[k], e[k], e[k + 1]));
+        int best = 0;  // the fastest, once all are timed
+        for (int k = 1; k < 3; ++k)
             if (cell_ms[k] < cell_ms[best]) best = k;
-        }
         for (auto &ev : e) cudaEventDestroy(ev);
         cell_warps = cand[best];
     } else {

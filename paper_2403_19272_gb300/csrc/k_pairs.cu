@@ -858,11 +858,10 @@ void launch_full_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const f
             PDC_CK(cudaEventRecord(e[k + 1], s));
         }
         PDC_CK(cudaEventSynchronize(e[4]));
-        int best = 2;
-        for (int k = 0; k < 4; ++k) {
-            PDC_CK(cudaEventElapsedTime(&bp.pair_ms[k], e[k], e[k + 1]));
+        for (int k = 0; k < 4; ++k) PDC_CK(cudaEventElapsedTime(&bp.pair_ms[k], e[k], e[k + 1]));
+        int best = 0;  // the fastest, once all are timed
+        for (int k = 1; k < 4; ++k)
             if (bp.pair_ms[k] < bp.pair_ms[best]) best = k;
-        }
         for (auto &ev : e) cudaEventDestroy(ev);
         bp.pair_blocks = cand[best];
     }
