@@ -59,6 +59,8 @@ def parse():
                          "3 on the device, the host enqueueing each iteration ahead as one graph launch; 2 the "
                          "same with kernel launches; 0 on the host")
     ap.add_argument("--graph-unroll", type=int, default=1, help="LG iterations per pass of a graph loop (1..8)")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="1: launch shapes and the broad-phase grid timed on the handle's data in the warm-up")
     ap.add_argument("--loop-ahead", type=int, default=1, choices=[0, 1, 2],
                     help="LG iterations enqueued beyond the last decision read (loop control 2, 3)")
     ap.add_argument("--no-launch-count", action="store_true",
@@ -72,7 +74,7 @@ DTYPES = {"mixed16": "f16+f32+f64", "mixed": "bf16+f32+f64", "fp32": "f32"}
 
 
 def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1, loop_control=1, graph_unroll=1,
-                  loop_ahead=1):
+                  loop_ahead=1, autotune=1):
     p = pc.pdc_default_params()
     p.loop_control = loop_control  # stopping tests of the LG loops on the device
     p.graph_unroll = graph_unroll
@@ -91,6 +93,7 @@ def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1, loop_co
     p.accel = 2             # Anderson mixing of the LG iterates
     p.aa_depth = 6
     p.solve_cycles = 1
+    p.autotune = autotune   # launch shapes (first step) and broad-phase grid (8th pass) timed in the warm-up
     p.eig_iters = 12
     return p
 
@@ -166,11 +169,11 @@ class ClockSampler:
 
 
 def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True, sweeps=28, cheb_ratio=300.0,
-             overlap=1, loop_control=1, graph_unroll=1, loop_ahead=1):
+             overlap=1, loop_control=1, graph_unroll=1, loop_ahead=1, autotune=1):
     """Warm-up, timed region (device), profiled replay, e2e through host buffers."""
     import numpy as np
     stream = torch.cuda.Stream()
-    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap, loop_control, graph_unroll, loop_ahead)
+    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap, loop_control, graph_unroll, loop_ahead, autotune)
     t_setup = time.time()
     h = pc.pdc_create(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend, p,
                       stream.cuda_stream)
@@ -248,6 +251,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
     x = pos_host.numpy().copy()
+    tuning = pc.pdc_get_tuning(h)
     pc.pdc_destroy(h)
     iters = [s["warm_iters"] + s["inner_iters"] for s in st_list]
     return dict(ms=ms / steps, setup_s=setup_s, clocks=clk, kernels=kt, e2e_ms=e2e_ms,
@@ -256,7 +260,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
                 cand=statistics.mean(s["n_candidates"] for s in st_list),
                 toi=min(s["t_toi"] for s in st_list), finite=bool(np.isfinite(x).all()),
                 device_loops=statistics.mean(s["device_loops"] for s in st_list), device_busy=busy, idle_gaps=gaps,
-                launches=launches)
+                launches=launches, tuning=tuning)
 
 
 def solver_like(pc, p):
@@ -651,7 +655,7 @@ def main():
     for f in a.forms.split(","):
         forms[f] = run_form(pc, torch, scene, FORMS[f], a.steps, a.warmup, local,
                             not a.no_launch_count, a.sweeps, a.cheb_ratio, a.launch_overlap, a.loop_control,
-                            a.graph_unroll, a.loop_ahead)
+                            a.graph_unroll, a.loop_ahead, a.autotune)
     head = list(forms)[0]
     ms = forms[head]["ms"]
     ms = max_over_ranks(ms, f"cuda:{local}")
@@ -667,13 +671,14 @@ def main():
         "config": {"workload": WORKLOAD, "form": head, "basis": "r=256 (r_reuse=32 with collision springs)",
                    "l2": "inputs larger than L2 (basis 134 MB in 16 bits / 268 MB FP32 plus matrices and state)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "loop_control": a.loop_control, "loop_ahead": a.loop_ahead},
+                   "loop_control": a.loop_control, "loop_ahead": a.loop_ahead, "autotune": a.autotune},
         "forms": {f: {"ms_per_step": round(d["ms"], 3), "lg_iters_per_step": d["iters"],
                       "vertex_iters_per_s": round(scene.n * d["iters"] / (d["ms"] * 1e-3), 1),
                       "gpu_launches": d["launches"],
                       "rel_residual": d["rel_res"], "candidates": d["cand"], "min_toi": d["toi"],
                       "device_loops_per_step": d["device_loops"], "device_busy": d["device_busy"],
-                      "setup_s": round(d["setup_s"], 2), "e2e_ms_per_step": round(d["e2e_ms"], 3)}
+                      "setup_s": round(d["setup_s"], 2), "e2e_ms_per_step": round(d["e2e_ms"], 3),
+                      "tuning": d["tuning"]}
                   for f, d in forms.items()},
         "roofline": rl,
         "clocks": forms[head]["clocks"],

@@ -188,9 +188,11 @@ typedef struct {
     int32_t autotune;        /* 1: the first step picks the launch shapes of the
                                 hot kernels by timing every candidate on the
                                 handle's own data (CUDA events; see
-                                pdc_tuning); results do not depend on the
-                                choice beyond the order of float atomics.  0
-                                (default): fixed shapes                          */
+                                pdc_tuning), the broad phase its grid and
+                                block shape on its 8th pass (the first steps
+                                see the cloth nearly at rest); results do not
+                                depend on the choice beyond the order of float
+                                atomics.  0 (default): fixed shapes            */
     int32_t graph_unroll;    /* loop_control = 1: LG iterations per pass of the
                                 while node (1..8, default 1): each pass
                                 relaunches its body on the device, at a cost
@@ -244,6 +246,10 @@ typedef struct {
     float cheb_ms[2];
     float pair_ms[4];
     float cell_ms[3];
+    float cell_grid;         /* factor of the broad phase's cell side over the
+                                mean triangle extent (candidates 1, 1.5, 2);
+                                the pair lists do not depend on it             */
+    float grid_ms[3];
 } pdc_tuning;
 
 /* Defaults: dt 1/200, g = (0,0,-9.8), K = 2, a_max 20, alpha 0.8, automatic

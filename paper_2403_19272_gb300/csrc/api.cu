@@ -691,7 +691,7 @@ struct pdc_ctx {
     DevBuf<LoopCtl> ctl;
     LoopCtl hctl;
     bool device_decides = false;  // the loop being enqueued takes its tests on the device
-    pdc_tuning tune = {0, 256, 1, 152 * 8, 8, {0, 0, 0}, {0, 0}, {0, 0, 0, 0}, {0, 0, 0}};
+    pdc_tuning tune = {0, 256, 1, 152 * 8, 4, {0, 0, 0}, {0, 0}, {0, 0, 0, 0}, {0, 0, 0}, 1.f, {0, 0, 0}};
     void autotune_vertex_kernels();
     bool device_loops_ok() const;
     void free_graph(GraphLoop &G);
@@ -2632,6 +2632,8 @@ pdc_status pdc_get_tuning(pdc_handle h, pdc_tuning *out) {
     out->cell_warps = h->bp.cell_warps;
     for (int k = 0; k < 4; ++k) out->pair_ms[k] = h->bp.pair_ms[k];
     for (int k = 0; k < 3; ++k) out->cell_ms[k] = h->bp.cell_ms[k];
+    out->cell_grid = h->bp.cell_grid;
+    for (int k = 0; k < 3; ++k) out->grid_ms[k] = h->bp.grid_ms[k];
     API_END(h)
 }
 

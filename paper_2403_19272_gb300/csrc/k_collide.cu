@@ -762,30 +762,9 @@ void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const
 
 void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat,
                            int *overflow, int2 *out_vt, int2 *out_ee, long long *out_nvt, long long *out_nee) {
-    PDC_CK(cudaMemsetAsync(gp.p, 0, sizeof(GridParams), s));
-    BP_PROF("bp_boxes", if (cv.nt) k_tri_boxes<<<nblk(cv.nt, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, gp);
-            if (cv.ne) k_edge_boxes<<<nblk(cv.ne, 256), 256, 0, s>>>(cv, x0, x1, elo, ehi);
-            k_grid_params<<<1, 1, 0, s>>>(gp, cv.nt, dhat, cell_scale));
-    PDC_LAUNCH_CK();
     long long *tot = totals.p;
     const int np = cv.nv + cv.ne + cv.nt;
     const unsigned mask = (unsigned)(T - 1);
-    // ---- cell table: count per bucket, prefix sum, fill
-    BP_PROF("bp_hash_build", bcnt.zero(s); bfill.zero(s);
-    if (np) {
-        k_cell_insert<<<nblk(np, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, elo, ehi, gp, dhat, mask, bcnt, bstart, bfill,
-                                                    ekey, epay, 0, tot, cap_ent, overflow);
-        PDC_LAUNCH_CK();
-    }
-    exclusive_scan(s, bcnt, bstart, T, scratch, tot);
-    k_check_cap<<<1, 1, 0, s>>>(tot, cap_ent, OVF_HASH, overflow, tot + 4);
-    if (np) {
-        k_cell_insert<<<nblk(np, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, elo, ehi, gp, dhat, mask, bcnt, bstart, bfill,
-                                                    ekey, epay, 1, tot, cap_ent, overflow);
-        PDC_LAUNCH_CK();
-    });
-    // ---- VT and EE pairs of every cell into the per-primary rows
-    if (prof) prof->begin(s, "bp_cell_pairs", 0.0);
     RowsOut o;
     o.cnt_v = cnt_v;
     o.slots_vt = slots_vt;
@@ -794,12 +773,34 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
     o.w_vt = w_vt;
     o.w_ee = w_ee;
     o.overflow = overflow;
-    auto pairs = [&](int w) {
+    // boxes, grid (cell = mean triangle extent x scale), cell table, the VT
+    // and EE pairs of every cell into the per-primary rows (w warps a block)
+    auto build = [&](float scale, int w) {
+        PDC_CK(cudaMemsetAsync(gp.p, 0, sizeof(GridParams), s));
+        BP_PROF("bp_boxes", if (cv.nt) k_tri_boxes<<<nblk(cv.nt, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, gp);
+                if (cv.ne) k_edge_boxes<<<nblk(cv.ne, 256), 256, 0, s>>>(cv, x0, x1, elo, ehi);
+                k_grid_params<<<1, 1, 0, s>>>(gp, cv.nt, dhat, scale));
+        PDC_LAUNCH_CK();
+        // ---- cell table: count per bucket, prefix sum, fill
+        BP_PROF("bp_hash_build", bcnt.zero(s); bfill.zero(s);
+        if (np) {
+            k_cell_insert<<<nblk(np, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, elo, ehi, gp, dhat, mask, bcnt, bstart,
+                                                        bfill, ekey, epay, 0, tot, cap_ent, overflow);
+            PDC_LAUNCH_CK();
+        }
+        exclusive_scan(s, bcnt, bstart, T, scratch, tot);
+        k_check_cap<<<1, 1, 0, s>>>(tot, cap_ent, OVF_HASH, overflow, tot + 4);
+        if (np) {
+            k_cell_insert<<<nblk(np, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, elo, ehi, gp, dhat, mask, bcnt, bstart,
+                                                        bfill, ekey, epay, 1, tot, cap_ent, overflow);
+            PDC_LAUNCH_CK();
+        });
+        if (prof) prof->begin(s, "bp_cell_pairs", 0.0);
         cnt_v.zero(s);
         cnt_e.zero(s);
         work.zero(s);
-        if (np == 0) return;
-        // about 24 resident warps per SM for each shape (two regions per warp)
+        if (np) {
+            // about 24 resident warps per SM for each shape
 #define PDC_CELLS(W, B)                                                                                              \
     do {                                                                                                             \
         const int smem = (W) * (int)sizeof(CellWarp);                                                               \
@@ -811,36 +812,47 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
         k_cell_pairs<W><<<152 * (B), (W) * 32, smem, s>>>(cv, x0, x1, tlo, thi, elo, ehi, dhat, T, bcnt, bstart, ekey, \
                                                           epay, o, work, gp, tot, cap_ent);                          \
     } while (0)
-        if (w == 2) PDC_CELLS(2, 12);
-        else if (w == 8) PDC_CELLS(8, 3);
-        else PDC_CELLS(4, 6);
+            if (w == 2) PDC_CELLS(2, 12);
+            else if (w == 8) PDC_CELLS(8, 3);
+            else PDC_CELLS(4, 6);
 #undef PDC_CELLS
-        PDC_LAUNCH_CK();
+            PDC_LAUNCH_CK();
+        }
+        if (prof) prof->end(s);
     };
-    if (tune_cells) {
-        // every candidate writes the same rows (up to their order, which the
-        // compaction sorts out): time each, keep the fastest
+    // tuned on the TUNE_PASS-th pass after the request: the first passes of a
+    // run see the cloth nearly at rest, smaller boxes than later on
+    constexpr int TUNE_PASS = 8;
+    if (tune_cells && ++tune_wait >= TUNE_PASS) {
+        // every candidate finds the same pairs (the rows differ only in order,
+        // which the compaction sorts out): time each whole build, keep the
+        // fastest grid, then the fastest block shape on it
         tune_cells = false;
-        const int cand[3] = {2, 4, 8};
+        tune_wait = 0;
+        const float grids[3] = {1.f, 1.5f, 2.f};
+        const int warps[3] = {2, 4, 8};
         cudaEvent_t e[4];
         for (auto &ev : e) PDC_CK(cudaEventCreate(&ev));
-        pairs(4);  // warm-up
-        PDC_CK(cudaEventRecord(e[0], s));
-        for (int k = 0; k < 3; ++k) {
-            pairs(cand[k]);
-            PDC_CK(cudaEventRecord(e[k + 1], s));
-        }
-        PDC_CK(cudaEventSynchronize(e[3]));
-        for (int k = 0; k < 3; ++k) PDC_CK(cudaEventElapsedTime(&cell_ms[k], e[k], e[k + 1]));
-        int best = 0;  // the fastest, once all are timed
-        for (int k = 1; k < 3; ++k)
-            if (cell_ms[k] < cell_ms[best]) best = k;
+        auto sweep = [&](float *ms, auto &&run) {
+            PDC_CK(cudaEventRecord(e[0], s));
+            for (int k = 0; k < 3; ++k) {
+                run(k);
+                PDC_CK(cudaEventRecord(e[k + 1], s));
+            }
+            PDC_CK(cudaEventSynchronize(e[3]));
+            for (int k = 0; k < 3; ++k) PDC_CK(cudaEventElapsedTime(&ms[k], e[k], e[k + 1]));
+            int best = 0;  // the fastest, once all are timed
+            for (int k = 1; k < 3; ++k)
+                if (ms[k] < ms[best]) best = k;
+            return best;
+        };
+        build(cell_scale * cell_grid, cell_warps);  // warm-up
+        cell_grid = grids[sweep(grid_ms, [&](int k) { build(cell_scale * grids[k], cell_warps); })];
+        cell_warps = warps[sweep(cell_ms, [&](int k) { build(cell_scale * cell_grid, warps[k]); })];
         for (auto &ev : e) cudaEventDestroy(ev);
-        cell_warps = cand[best];
     } else {
-        pairs(cell_warps);
+        build(cell_scale * cell_grid, cell_warps);
     }
-    if (prof) prof->end(s);
     // ---- rows -> sorted pair lists
     if (prof) prof->begin(s, "bp_compact", 0.0);
     exclusive_scan(s, cnt_v, off_v, cv.nv, scratch, tot + 2);

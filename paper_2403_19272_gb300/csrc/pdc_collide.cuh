@@ -66,7 +66,8 @@ struct BroadPhase {
     int nt = 0, ne = 0, nv = 0;
     int T = 0;  // buckets of the cell table (power of two)
     long long cap_ent = 0, cap_vt = 0, cap_ee = 0;
-    float cell_scale = 1.f;
+    float cell_scale = 1.f;  // grown x4 when a primitive covers too many cells
+    float cell_grid = 1.f;   // tuned factor of the cell side (1, 1.5 or 2)
     DevBuf<int> bcnt, bstart, bfill;
     DevBuf<unsigned long long> ekey;  // cell key of each table entry
     DevBuf<unsigned int> epay;        // primitive | kind << 27 | lowest-cell flags << 29
@@ -91,7 +92,8 @@ struct BroadPhase {
     int pair_blocks = 152 * 8;
     int cell_warps = 4;
     bool tune_pairs = false, tune_cells = false;
-    float pair_ms[4] = {0, 0, 0, 0}, cell_ms[3] = {0, 0, 0};
+    int tune_wait = 0;  // passes since tune_cells was set
+    float pair_ms[4] = {0, 0, 0, 0}, cell_ms[3] = {0, 0, 0}, grid_ms[3] = {0, 0, 0};
     Profiler *prof = nullptr;  // optional sub-kernel timing
     long long h_pairs = 0;     // host copy of the current list size (kept while profiling)
     // partial-CCD filter: near list, double-buffered watch list, reference

@@ -203,8 +203,9 @@ def test_instance_line_search_attachment_is_checked(pc):
 
 def test_autotuned_batch_takes_the_same_steps(pc):
     """autotune = 1: the first step times every candidate launch shape on the
-    batch's own data and keeps the fastest of each; the steps are those of
-    the fixed shapes (up to the order of float atomics)."""
+    batch's own data and keeps the fastest of each, the broad phase its grid
+    and block shape on its 8th pass; the steps are those of the fixed shapes
+    (up to the order of float atomics)."""
     scenes = [_shift(_thrown(wl.drape_sphere(side=12, sphere_subdiv=2), -15.0), 0.0),
               _shift(wl.drape_sphere(side=20, sphere_subdiv=2, seed=5), 2.5)]
     pt = _params(pc, collisions=True)
@@ -212,7 +213,7 @@ def test_autotuned_batch_takes_the_same_steps(pc):
     bt = _Batch(pc, scenes, pt)
     bf = _Batch(pc, scenes, _params(pc, collisions=True))
     L = max(float(np.linalg.norm(s.verts.max(0) - s.verts.min(0))) for s in scenes)
-    for k in range(4):
+    for k in range(6):
         bt.step()
         bf.step()
         xt, _ = bt.state()
@@ -225,6 +226,8 @@ def test_autotuned_batch_takes_the_same_steps(pc):
     assert all(v > 0 for v in t["residual_ms"] + t["pair_ms"] + t["cell_ms"])
     assert t["residual_ms"][(64, 128, 256).index(t["residual_block"])] == min(t["residual_ms"])
     assert t["cell_ms"][(2, 4, 8).index(t["cell_warps"])] == min(t["cell_ms"])
+    assert t["cell_grid"] in (1.0, 1.5, 2.0) and all(v > 0 for v in t["grid_ms"])
+    assert t["grid_ms"][(1.0, 1.5, 2.0).index(t["cell_grid"])] == min(t["grid_ms"])
     assert pc.pdc_get_tuning(bf.h)["tuned"] == 0
     bt.close()
     bf.close()
