@@ -59,6 +59,8 @@ def parse():
                          "3 on the device, the host enqueueing each iteration ahead as one graph launch; 2 the "
                          "same with kernel launches; 0 on the host")
     ap.add_argument("--graph-unroll", type=int, default=1, help="LG iterations per pass of a graph loop (1..8)")
+    ap.add_argument("--cheb-source", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="matrix of the Chebyshev steps: -1 automatic, 0 ELL arrays, 1 row tiles, 2 patch tiles")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="1: launch shapes and the broad-phase grid timed on the handle's data in the warm-up")
     ap.add_argument("--loop-ahead", type=int, default=1, choices=[0, 1, 2],
@@ -74,7 +76,7 @@ DTYPES = {"mixed16": "f16+f32+f64", "mixed": "bf16+f32+f64", "fp32": "f32"}
 
 
 def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1, loop_control=1, graph_unroll=1,
-                  loop_ahead=1, autotune=1):
+                  loop_ahead=1, autotune=1, cheb_source=-1):
     p = pc.pdc_default_params()
     p.loop_control = loop_control  # stopping tests of the LG loops on the device
     p.graph_unroll = graph_unroll
@@ -94,6 +96,7 @@ def solver_params(pc, precision, sweeps=28, cheb_ratio=300.0, overlap=1, loop_co
     p.aa_depth = 6
     p.solve_cycles = 1
     p.autotune = autotune   # launch shapes (first step) and broad-phase grid (8th pass) timed in the warm-up
+    p.cheb_source = cheb_source
     p.eig_iters = 12
     return p
 
@@ -169,11 +172,12 @@ class ClockSampler:
 
 
 def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count=True, sweeps=28, cheb_ratio=300.0,
-             overlap=1, loop_control=1, graph_unroll=1, loop_ahead=1, autotune=1):
+             overlap=1, loop_control=1, graph_unroll=1, loop_ahead=1, autotune=1, cheb_source=-1):
     """Warm-up, timed region (device), profiled replay, e2e through host buffers."""
     import numpy as np
     stream = torch.cuda.Stream()
-    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap, loop_control, graph_unroll, loop_ahead, autotune)
+    p = solver_params(pc, precision, sweeps, cheb_ratio, overlap, loop_control, graph_unroll, loop_ahead, autotune,
+                      cheb_source)
     t_setup = time.time()
     h = pc.pdc_create(scene.verts, scene.tris, scene.pins, scene.density, scene.k_stretch, scene.k_bend, p,
                       stream.cuda_stream)
@@ -655,7 +659,7 @@ def main():
     for f in a.forms.split(","):
         forms[f] = run_form(pc, torch, scene, FORMS[f], a.steps, a.warmup, local,
                             not a.no_launch_count, a.sweeps, a.cheb_ratio, a.launch_overlap, a.loop_control,
-                            a.graph_unroll, a.loop_ahead, a.autotune)
+                            a.graph_unroll, a.loop_ahead, a.autotune, a.cheb_source)
     head = list(forms)[0]
     ms = forms[head]["ms"]
     ms = max_over_ranks(ms, f"cuda:{local}")

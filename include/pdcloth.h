@@ -205,6 +205,13 @@ typedef struct {
                                 ends before costs a pass of kernels that return
                                 at once; 0 leaves the device waiting for the
                                 host between iterations                         */
+    int32_t cheb_source;     /* matrix the Chebyshev steps read: -1 (default)
+                                the patch tiles when they exist, else the row
+                                tiles (autotune: the fastest of those built);
+                                0 the ELL arrays; 1 the row tiles; 2 the patch
+                                tiles (a source that is not built falls back
+                                to the next simpler one).  Same arithmetic in
+                                the same order in every source                  */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */
@@ -237,13 +244,17 @@ typedef struct {
     int32_t tuned;           /* 1 once the first step has tuned (autotune = 1)   */
     int32_t residual_block;  /* threads per block of the element-force and
                                 residual kernels (candidates 64, 128, 256)      */
-    int32_t cheb_tile;       /* 1: Chebyshev steps read the TMA-staged matrix
-                                tiles; 0: the ELL arrays (candidates 1, 0)      */
+    int32_t cheb_tile;       /* Chebyshev steps read 2 (default when built): the
+                                matrix tiles of compact patches of the rest
+                                mesh, delta staged with the patch's halo in
+                                shared memory; 1: the TMA-staged tiles of
+                                consecutive rows; 0: the ELL arrays
+                                (candidates 1, 0, 2)                            */
     int32_t pair_blocks;     /* blocks of the per-pair kernels (152 x 2, 4, 8, 16) */
     int32_t cell_warps;      /* warps per block of the broad phase's cell-pair
                                 kernel (candidates 2, 4, 8)                     */
     float residual_ms[3];
-    float cheb_ms[2];
+    float cheb_ms[3];
     float pair_ms[4];
     float cell_ms[3];
     float cell_grid;         /* factor of the broad phase's cell side over the

@@ -439,6 +439,8 @@ struct pdc_ctx {
     DevBuf<short> ell_dcol;
     DevBuf<unsigned char> ell_tile;
     int ell_tw = 0;
+    DevBuf<unsigned char> ell_halo;  // patch tiles (ClothView::ell_halo)
+    void build_patch_tiles(const std::vector<int> &ecol, const std::vector<float> &evalv);
     DevBuf<unsigned char> is_free;
     int ell_w = 0;
     // pins
@@ -569,9 +571,13 @@ struct pdc_ctx {
         c.overlap = P.launch_overlap != 0;
         c.ell_tile = ell_tile.p;
         c.ell_tw = ell_tw;
+        c.ell_halo = ell_halo.p;
         c.corner = corner;
         c.res_block = tune.residual_block;
-        c.cheb_plain = tune.cheb_tile ? 0 : 1;
+        {
+            const int want = P.cheb_source >= 0 ? P.cheb_source : tune.cheb_tile;
+            c.cheb_mode = want == 2 && !ell_halo.p ? 1 : want;
+        }
         c.live = live_ptr;
         return c;
     }
@@ -691,7 +697,7 @@ struct pdc_ctx {
     DevBuf<LoopCtl> ctl;
     LoopCtl hctl;
     bool device_decides = false;  // the loop being enqueued takes its tests on the device
-    pdc_tuning tune = {0, 256, 1, 152 * 8, 4, {0, 0, 0}, {0, 0}, {0, 0, 0, 0}, {0, 0, 0}, 1.f, {0, 0, 0}};
+    pdc_tuning tune = {0, 256, 2, 152 * 8, 4, {0, 0, 0}, {0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0}, 1.f, {0, 0, 0}};
     void autotune_vertex_kernels();
     bool device_loops_ok() const;
     void free_graph(GraphLoop &G);
@@ -984,8 +990,10 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
                     }
             }
             ell_tile.upload(tiles, s);
+            build_patch_tiles(ecol, evalv);
         } else {
             ell_tile.release();
+            ell_halo.release();
         }
     }
     ell_val.upload(evalv, s);
@@ -1255,6 +1263,77 @@ void pdc_ctx::upload_vinst() {
 // only.  Here: the block size of the element-force and residual kernels and
 // the Chebyshev step's matrix source; the pair kernels' grid and the VT
 // query's lanes per vertex are tuned at the first full CCD / broad phase.
+// Patch tiles for the Chebyshev step: the rows are cut into patches of
+// ELL_TILE_ROWS vertices consecutive in the Morton order of the rest
+// positions (one scale for all three axes, so a flat sheet's jitter does not
+// decide the order), ids ascending within a patch; each patch lists the other
+// vertices its rows reference (its halo) and stores its rows' off-diagonals,
+// in the order of the ELL arrays, with columns local to rows + halo.  Not
+// built (the row tiles serve) when some patch's halo exceeds HALO_MAX.
+void pdc_ctx::build_patch_tiles(const std::vector<int> &ecol, const std::vector<float> &evalv) {
+    ell_halo.release();
+    if (n == 0 || ell_w == 0) return;
+    float lo[3] = {X[0], X[1], X[2]}, hi[3] = {X[0], X[1], X[2]};
+    for (int i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], X[3 * (size_t)i + d]);
+            hi[d] = std::max(hi[d], X[3 * (size_t)i + d]);
+        }
+    double ext = std::max({(double)hi[0] - lo[0], (double)hi[1] - lo[1], (double)hi[2] - lo[2], 1e-30});
+    std::vector<std::pair<unsigned long long, int>> key(n);
+    for (int i = 0; i < n; ++i) {
+        unsigned long long code = 0;
+        unsigned q[3];
+        for (int d = 0; d < 3; ++d)
+            q[d] = (unsigned)std::min(1023.0, std::max(0.0, ((double)X[3 * (size_t)i + d] - lo[d]) / ext * 1023.0));
+        for (int b = 0; b < 10; ++b)
+            for (int d = 0; d < 3; ++d) code |= (unsigned long long)((q[d] >> b) & 1u) << (3 * b + d);
+        key[i] = {code, i};
+    }
+    std::sort(key.begin(), key.end());
+    const int R = ELL_TILE_ROWS, tw = ell_tw;
+    const size_t nb = ((size_t)n + R - 1) / R, rb = halo_tile_bytes(tw);
+    std::vector<unsigned char> rec(nb * rb, 0);
+    std::vector<int> loc(n, -1), own, halo;
+    for (size_t b = 0; b < nb; ++b) {
+        own.clear();
+        halo.clear();
+        for (size_t j = b * R; j < std::min((size_t)n, (b + 1) * R); ++j) own.push_back(key[j].second);
+        std::sort(own.begin(), own.end());
+        for (int t = 0; t < (int)own.size(); ++t) loc[own[t]] = t;
+        bool ok = true;
+        for (int t = 0; t < (int)own.size() && ok; ++t)
+            for (int k = 0; k < ell_w && ok; ++k) {
+                const int col = ecol[(size_t)k * n + own[t]];
+                if (loc[col] >= 0) continue;
+                if ((int)halo.size() == HALO_MAX) ok = false;
+                else {
+                    loc[col] = R + (int)halo.size();
+                    halo.push_back(col);
+                }
+            }
+        if (ok) {
+            unsigned char *p = rec.data() + b * rb;
+            float *tv = reinterpret_cast<float *>(p);
+            short *tc = reinterpret_cast<short *>(p + (size_t)tw * R * 4);
+            int *gid = reinterpret_cast<int *>(p + (size_t)tw * R * 6);
+            int *hid = gid + R;
+            for (int t = 0; t < R; ++t) gid[t] = t < (int)own.size() ? own[t] : -1;
+            for (int t = 0; t < (int)own.size(); ++t)
+                for (int k = 0; k < ell_w; ++k) {
+                    tv[k * R + t] = evalv[(size_t)k * n + own[t]];
+                    tc[k * R + t] = (short)loc[ecol[(size_t)k * n + own[t]]];
+                }
+            for (int h = 0; h < (int)halo.size(); ++h) hid[h] = halo[h];
+            hid[HALO_MAX] = (int)halo.size();
+        }
+        for (int v : own) loc[v] = -1;
+        for (int v : halo) loc[v] = -1;
+        if (!ok) return;
+    }
+    ell_halo.upload(rec, s);
+}
+
 void pdc_ctx::autotune_vertex_kernels() {
     cudaEvent_t e0, e1;
     PDC_CK(cudaEventCreate(&e0));
@@ -1279,20 +1358,27 @@ void pdc_ctx::autotune_vertex_kernels() {
     for (int k = 1; k < 3; ++k)
         if (tune.residual_ms[k] < tune.residual_ms[best]) best = k;
     tune.residual_block = bsz[best];
-    if (P.sweep_kind == 1 && ell_tile.p) {
-        // one Chebyshev step from delta = 0 on the residual just formed (scratch outputs)
+    if (P.sweep_kind == 1 && ell_tile.p && P.cheb_source < 0) {
+        // Chebyshev steps from delta = 0 on the residual just formed (scratch outputs)
         PDC_CK(cudaMemsetAsync(D0.p, 0, sizeof(float4) * n, s));
         double b = std::max(gersh, 1.0) * 1.02, a = b / std::max(P.cheb_ratio, 1.0001);
         const float beta = (float)(2.0 / (b + a));
-        for (int k = 0; k < 2; ++k) {
-            tune.cheb_tile = k == 0 ? 1 : 0;
+        const int modes[3] = {1, 0, 2};  // row tiles, ELL arrays, patch tiles
+        const int nm = ell_halo.p ? 3 : 2;
+        for (int k = 0; k < nm; ++k) {
+            tune.cheb_tile = modes[k];
             ClothView c = cloth();
+            // eight steps back to back, launched as in the LG iteration
             tune.cheb_ms[k] = timed([&] {
-                launch_cheb_step(s, c, nullptr, R, D0, CD0, D1, 0.f, beta, nullptr, nullptr, nullptr, nullptr, 1.f, Xs,
-                                 nullptr, false, sflag.p);
-            });
+                for (int rep = 0; rep < 8; ++rep)
+                    launch_cheb_step(s, c, nullptr, R, D0, CD0, D1, 0.f, beta, nullptr, nullptr, nullptr, nullptr,
+                                     1.f, Xs, nullptr, P.launch_overlap != 0, sflag.p);
+            }) / 8.f;
         }
-        tune.cheb_tile = tune.cheb_ms[0] <= tune.cheb_ms[1] ? 1 : 0;
+        int best = 0;  // the fastest, once all are timed
+        for (int k = 1; k < nm; ++k)
+            if (tune.cheb_ms[k] < tune.cheb_ms[best]) best = k;
+        tune.cheb_tile = modes[best];
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2213,6 +2299,7 @@ void pdc_default_params(pdc_params *p) {
     p->autotune = 0;
     p->graph_unroll = 1;
     p->loop_ahead = 1;
+    p->cheb_source = -1;
 }
 
 static bool params_valid(const pdc_params *params) {
@@ -2224,7 +2311,7 @@ static bool params_valid(const pdc_params *params) {
            params->sweep_kind >= 0 && params->sweep_kind <= 1 && (params->sweep_kind != 1 || params->cheb_ratio > 1.0) &&
            params->accel >= 0 && params->accel <= 2 && (params->accel != 2 || (params->aa_depth >= 1 && params->aa_depth <= 8)) &&
            params->loop_control >= 0 && params->loop_control <= 3 && params->loop_ahead >= 0 &&
-           params->loop_ahead <= 2 &&
+           params->loop_ahead <= 2 && params->cheb_source >= -1 && params->cheb_source <= 2 &&
            (params->pccd_adaptive == 0 || (params->pccd_adaptive == 1 && params->pccd_max_axis >= 1 &&
                                            params->pccd_max_axis <= 256 && params->alpha_ls > 0 && params->alpha_ls < 1));
 }
@@ -2630,6 +2717,7 @@ pdc_status pdc_get_tuning(pdc_handle h, pdc_tuning *out) {
     *out = h->tune;
     out->pair_blocks = h->bp.pair_blocks;
     out->cell_warps = h->bp.cell_warps;
+    out->cheb_tile = h->cloth().cheb_mode;  // the source in use
     for (int k = 0; k < 4; ++k) out->pair_ms[k] = h->bp.pair_ms[k];
     for (int k = 0; k < 3; ++k) out->cell_ms[k] = h->bp.cell_ms[k];
     out->cell_grid = h->bp.cell_grid;

@@ -469,6 +469,113 @@ __global__ void __launch_bounds__(ELL_TILE_ROWS, 8) k_cheb_step_tile(
     if (xout && sc) block_max(mx, &sc->dxmax);
 }
 
+// The Chebyshev step over patch tiles (ClothView::ell_halo): a block takes
+// one patch of ELL_TILE_ROWS rows that are close on the rest mesh, so the
+// vertices its rows reference are its own rows plus a thin halo.  One thread
+// bulk-copies the patch's tile (values, local columns, vertex ids of rows and
+// halo) before the dependency wait; after it the block stages delta of its
+// rows and halo in shared memory once, and every neighbour term reads it from
+// there instead of gathering from global memory.  Same arithmetic, in the
+// same order, as k_cheb_step.
+template <int W>
+__global__ void __launch_bounds__(ELL_TILE_ROWS, 4) k_cheb_step_halo(
+    const ClothView c, const float *__restrict__ cw, const float4 *__restrict__ r, const float4 *__restrict__ din,
+    const float4 *__restrict__ dprev, float4 *__restrict__ dout, float alpha, float beta, const float4 *x,
+    float4 *xout, float4 *xprev, float w_acc, const float4 *__restrict__ xs, float4 *__restrict__ xabs, Scalars *sc,
+    int *err) {
+    // the copy takes values, columns and row ids; the halo ids are read from
+    // global memory by the threads that stage them
+    constexpr uint32_t BYTES = (uint32_t)((size_t)W * ELL_TILE_ROWS * 6 + (size_t)ELL_TILE_ROWS * 4);
+    constexpr int R = ELL_TILE_ROWS;
+    __shared__ __align__(128) unsigned char tile[BYTES];
+    __shared__ float dsh[3 * (R + HALO_MAX)];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_dead;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        s_dead = loop_dead(c.live) ? 1 : 0;  // final once read as 0 (see k_cheb_step_tile)
+    }
+    __syncthreads();
+    const bool dead_early = s_dead != 0;
+    if (t == 0 && !dead_early) {
+        mbar_expect_tx(&bar, BYTES);
+        bulk_load(tile, c.ell_halo + (size_t)blockIdx.x * halo_tile_bytes(W), BYTES, &bar);
+    }
+    grid_dep_wait();
+    grid_dep_release();
+    if (dead_early) return;  // no copy in flight
+    const bool alive = !loop_dead(c.live);
+    if (!__syncthreads_and(mbar_wait(&bar, 0))) {  // block-uniform
+        if (t == 0) {
+            atomicOr(err, PDC_DEVERR_COPY);
+            mbar_wait(&bar, 0);  // let the copy land before the block's shared memory is released
+        }
+        return;
+    }
+    const int *gid = reinterpret_cast<const int *>(tile + (size_t)W * R * 6);
+    const int *hid = reinterpret_cast<const int *>(c.ell_halo + (size_t)blockIdx.x * halo_tile_bytes(W) +
+                                                   (size_t)W * R * 6) + R;
+    const int nh = min(__ldg(hid + HALO_MAX), HALO_MAX);
+    const int i = gid[t];
+    // delta of the rows and the halo, once per block
+    for (int j = t; j < R + nh; j += R) {
+        const int g = j < R ? gid[j] : __ldg(hid + (j - R));
+        const float4 v = (alive && g >= 0 && g < c.n) ? din[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+        dsh[3 * j] = v.x;
+        dsh[3 * j + 1] = v.y;
+        dsh[3 * j + 2] = v.z;
+    }
+    const bool live = alive && i >= 0 && i < c.n;
+    const bool fr = live && c.is_free[i];
+    float3 ri = make_float3(0.f, 0.f, 0.f), pi = ri;
+    float D = 1.f;
+    if (fr) {
+        ri = f3(r[i]);
+        if (alpha != 0.f) pi = f3(dprev[i]);
+        D = c.hdiag[i] + (cw ? cw[i] : 0.f);
+    }
+    __syncthreads();
+    float mx = 0.f;
+    if (live) {
+        float3 dn = make_float3(0.f, 0.f, 0.f);
+        if (fr) {
+            const float *sv = reinterpret_cast<const float *>(tile);
+            const short *sd = reinterpret_cast<const short *>(tile + (size_t)W * R * 4);
+            const float3 di = make_float3(dsh[3 * t], dsh[3 * t + 1], dsh[3 * t + 2]);
+            float3 e = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                if (k < c.ell_w) {
+                    const int j = sd[k * R + t];
+                    e = e + sv[k * R + t] * make_float3(dsh[3 * j], dsh[3 * j + 1], dsh[3 * j + 2]);
+                }
+            float3 acc = ri - D * di - e;
+            float3 dd = (beta / D) * acc;
+            if (alpha != 0.f) dd = dd + alpha * (di - pi);
+            dn = di + dd;
+        }
+        dout[i] = f4(dn);
+        if (xout) {
+            float3 xo = f3(x[i]);
+            float3 xn = xo + dn;
+            if (xprev) {
+                if (fr && w_acc != 1.f) {
+                    float3 xp = f3(xprev[i]);
+                    xn = xp + w_acc * (xn - xp);
+                }
+                xprev[i] = f4(xo);
+            }
+            xout[i] = f4(xn);
+            if (xabs) xabs[i] = f4(f3(xs[i]) + xn);
+            float3 d = xn - xo;
+            mx = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z)));
+        }
+    }
+    if (xout && sc) block_max(mx, &sc->dxmax);
+}
+
 // Anderson mixing of the LG fixed-point map x -> G(x) = x + delta(x)
 // (history of depth m): with f_k = delta_k, g_k = x_k + delta_k and the
 // differences dF_j, dG_j of consecutive f and g, theta minimises
@@ -784,7 +891,31 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
                       const float4 *dprev, float4 *dout, float alpha, float beta, const float4 *x,
                       float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs,
                       bool overlap, int *err) {
-    if (c.n > 0 && c.ell_tile && err && !c.cheb_plain) {
+    if (c.n > 0 && c.ell_halo && err && c.cheb_mode == 2) {
+        int b = nblk(c.n, ELL_TILE_ROWS);
+        // all of the shared memory for the blocks (29 KB each at width 12)
+        static unsigned long long carve_h[3] = {0, 0, 0};  // per-device bits
+        int ci = c.ell_tw == 8 ? 0 : c.ell_tw == 12 ? 1 : 2, dev = 0;
+        PDC_CK(cudaGetDevice(&dev));
+        if (!(carve_h[ci] >> (dev & 63) & 1ull)) {
+            const int pct = 100;
+            cudaError_t e = ci == 0 ? cudaFuncSetAttribute(k_cheb_step_halo<8>, cudaFuncAttributePreferredSharedMemoryCarveout, pct)
+                          : ci == 1 ? cudaFuncSetAttribute(k_cheb_step_halo<12>, cudaFuncAttributePreferredSharedMemoryCarveout, pct)
+                                    : cudaFuncSetAttribute(k_cheb_step_halo<16>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            PDC_CK(e);
+            carve_h[ci] |= 1ull << (dev & 63);
+        }
+#define PDC_CHEB_H(W)                                                                                       \
+    launch_dependent(overlap, k_cheb_step_halo<W>, b, ELL_TILE_ROWS, 0, s, c, cw, r, din, dprev, dout, alpha, beta, x, \
+                     xout, xprev, w_acc, xs, xabs, sc, err)
+        if (c.ell_tw == 8) PDC_CHEB_H(8);
+        else if (c.ell_tw == 12) PDC_CHEB_H(12);
+        else PDC_CHEB_H(16);
+#undef PDC_CHEB_H
+        PDC_LAUNCH_CK();
+        return;
+    }
+    if (c.n > 0 && c.ell_tile && err && c.cheb_mode != 0) {
         int b = nblk(c.n, ELL_TILE_ROWS);
         // shared-memory carveout for 8 resident blocks (the register limit)
         static unsigned long long carve[3] = {0, 0, 0};  // per-device bits

@@ -144,9 +144,14 @@ struct ClothView {
     // offsets do not fit 16 bits or the width exceeds 16)
     const unsigned char *ell_tile;
     int ell_tw;            // tile width: 8, 12 or 16 (>= ell_w)
+    // the same off-diagonals per patch of ELL_TILE_ROWS rows (vertices
+    // consecutive in the Morton order of the rest positions), with columns
+    // local to the patch and its halo (see halo_tile_bytes; NULL when some
+    // patch's halo exceeds HALO_MAX or the tiles above are absent)
+    const unsigned char *ell_halo;
     float4 *corner;        // scratch [3m + 4nh]: per-element corner forces of the residual
     int res_block;         // threads per block of the residual kernels (64, 128 or 256)
-    int cheb_plain;        // 1: Chebyshev steps read the ELL arrays directly, not the tiles
+    int cheb_mode;         // Chebyshev step reads: 0 the ELL arrays, 1 the row tiles, 2 the patch tiles
     const int *live;       // device loop flag: the kernels do nothing when *live == 0 (NULL: always run)
 };
 
@@ -156,6 +161,14 @@ __device__ __forceinline__ bool loop_dead(const int *live) { return live && *(co
 
 constexpr int ELL_TILE_ROWS = 256;
 inline size_t ell_tile_bytes(int tw) { return (size_t)tw * ELL_TILE_ROWS * 6; }
+// Patch tile: [tw][ELL_TILE_ROWS] float values, [tw][ELL_TILE_ROWS] int16
+// columns local to the patch (rows at 0..255, halo vertices from 256 on),
+// [ELL_TILE_ROWS] int32 vertex ids of the rows (-1 past the last), [HALO_MAX]
+// int32 vertex ids of the halo, int32 halo count, 12 bytes of padding.
+constexpr int HALO_MAX = 512;
+__host__ __device__ constexpr size_t halo_tile_bytes(int tw) {
+    return (size_t)tw * ELL_TILE_ROWS * 6 + (size_t)ELL_TILE_ROWS * 4 + (size_t)HALO_MAX * 4 + 16;
+}
 
 // Device error bit set in the status word when a bounded wait for a bulk
 // copy into shared memory ran out.

@@ -44,7 +44,7 @@ class pdc_params(ctypes.Structure):
                 ("tensor_cores", c_i32), ("bp_reuse", c_dbl), ("launch_overlap", c_i32),
                 ("rf_toi", c_dbl), ("rf_iters", c_i32), ("loop_control", c_i32), ("pccd_adaptive", c_i32),
                 ("pccd_max_axis", c_i32), ("instance_line_search", c_i32), ("autotune", c_i32),
-                ("graph_unroll", c_i32), ("loop_ahead", c_i32)]
+                ("graph_unroll", c_i32), ("loop_ahead", c_i32), ("cheb_source", c_i32)]
 
 
 class pdc_stats(ctypes.Structure):
@@ -60,7 +60,7 @@ class pdc_stats(ctypes.Structure):
 
 class pdc_tuning(ctypes.Structure):
     _fields_ = [("tuned", c_i32), ("residual_block", c_i32), ("cheb_tile", c_i32), ("pair_blocks", c_i32),
-                ("cell_warps", c_i32), ("residual_ms", c_flt * 3), ("cheb_ms", c_flt * 2), ("pair_ms", c_flt * 4),
+                ("cell_warps", c_i32), ("residual_ms", c_flt * 3), ("cheb_ms", c_flt * 3), ("pair_ms", c_flt * 4),
                 ("cell_ms", c_flt * 3), ("cell_grid", c_flt), ("grid_ms", c_flt * 3)]
 
     def as_dict(self):
