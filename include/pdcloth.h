@@ -212,6 +212,12 @@ typedef struct {
                                 tiles (a source that is not built falls back
                                 to the next simpler one).  Same arithmetic in
                                 the same order in every source                  */
+    int32_t residual_patch;  /* 1 (default): the element projections and the
+                                residual of an LG iteration in one kernel per
+                                mesh patch (each patch's element forces in
+                                shared memory); 0: two kernels through
+                                per-corner force arrays in device memory.
+                                Same terms summed in the same order             */
 } pdc_params;
 
 /* Per-step statistics (Tab. 1 columns: LG iterations, #Col., B|N|P|F). */

@@ -440,7 +440,21 @@ struct pdc_ctx {
     DevBuf<unsigned char> ell_tile;
     int ell_tw = 0;
     DevBuf<unsigned char> ell_halo;  // patch tiles (ClothView::ell_halo)
+    std::vector<int> morton_order() const;
     void build_patch_tiles(const std::vector<int> &ecol, const std::vector<float> &evalv);
+    // element forces and residual per mesh patch (ClothView::rp_*)
+    DevBuf<unsigned char> rp_rec;
+    DevBuf<long long> rp_off;
+    int rp_loc = 0, rp_tri = 0, rp_hin = 0;  // largest counts over the patches
+    // shared memory of k_residual_patch: positions x*, u of the touched
+    // vertices (6 floats), corner forces of the triangles (9), per hinge its
+    // vector s_hat - s and the four weights w K_j (7)
+    size_t residual_patch_smem() const {
+        return 4 * (6 * (size_t)rp_loc + 9 * (size_t)rp_tri + 7 * (size_t)rp_hin);
+    }
+    void build_residual_patches(const std::vector<int> &vto, const std::vector<int> &vtl, const std::vector<int> &vho,
+                                const std::vector<int> &vhl, const std::vector<int4> &tri_h,
+                                const std::vector<int4> &hin_h);
     DevBuf<unsigned char> is_free;
     int ell_w = 0;
     // pins
@@ -572,6 +586,12 @@ struct pdc_ctx {
         c.ell_tile = ell_tile.p;
         c.ell_tw = ell_tw;
         c.ell_halo = ell_halo.p;
+        const bool rp = P.residual_patch != 0 && rp_rec.p;
+        c.rp_rec = rp ? rp_rec.p : nullptr;
+        c.rp_off = rp ? rp_off.p : nullptr;
+        c.rp_loc = rp_loc;
+        c.rp_tri = rp_tri;
+        c.rp_hin = rp_hin;
         c.corner = corner;
         c.res_block = tune.residual_block;
         {
@@ -945,6 +965,7 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
         int ids[4] = {hin_h[hh].x, hin_h[hh].y, hin_h[hh].z, hin_h[hh].w};
         for (int k = 0; k < 4; ++k) vhl[fh[ids[k]]++] = (hh << 2) | k;
     }
+    build_residual_patches(vto, vtl, vho, vhl, tri_h, hin_h);
 
     // ---- upload
     tri.upload(tri_h, s);
@@ -1263,16 +1284,17 @@ void pdc_ctx::upload_vinst() {
 // only.  Here: the block size of the element-force and residual kernels and
 // the Chebyshev step's matrix source; the pair kernels' grid and the VT
 // query's lanes per vertex are tuned at the first full CCD / broad phase.
-// Patch tiles for the Chebyshev step: the rows are cut into patches of
-// ELL_TILE_ROWS vertices consecutive in the Morton order of the rest
-// positions (one scale for all three axes, so a flat sheet's jitter does not
-// decide the order), ids ascending within a patch; each patch lists the other
+// Patch tiles for the Chebyshev step: the rows are cut into the mesh patches
+// (morton_order), ids ascending within a patch; each patch lists the other
 // vertices its rows reference (its halo) and stores its rows' off-diagonals,
 // in the order of the ELL arrays, with columns local to rows + halo.  Not
 // built (the row tiles serve) when some patch's halo exceeds HALO_MAX.
-void pdc_ctx::build_patch_tiles(const std::vector<int> &ecol, const std::vector<float> &evalv) {
-    ell_halo.release();
-    if (n == 0 || ell_w == 0) return;
+// Vertices in the Morton order of their rest positions (10 bits per axis, one
+// scale for all three axes, so a flat sheet's jitter does not decide the
+// order); consecutive runs of ELL_TILE_ROWS are the mesh patches.
+std::vector<int> pdc_ctx::morton_order() const {
+    std::vector<int> order(n);
+    if (n == 0) return order;
     float lo[3] = {X[0], X[1], X[2]}, hi[3] = {X[0], X[1], X[2]};
     for (int i = 0; i < n; ++i)
         for (int d = 0; d < 3; ++d) {
@@ -1291,6 +1313,122 @@ void pdc_ctx::build_patch_tiles(const std::vector<int> &ecol, const std::vector<
         key[i] = {code, i};
     }
     std::sort(key.begin(), key.end());
+    for (int i = 0; i < n; ++i) order[i] = key[i].second;
+    return order;
+}
+
+// Records for the one-kernel residual: per mesh patch, the vertices it
+// touches (its own rows first, then the other vertices of the elements at
+// them), the triangles and hinges at its rows with their vertices as local
+// indices, and each row's incidences as local element indices in the order
+// of the global incidence lists (so the residual sums the same terms in the
+// same order as the two-kernel form).  Sections 16-byte aligned:
+// int4 {n_loc, n_tri, n_hin, n_own}; int vid[n_loc]; int tri[n_tri];
+// int2 tri_loc[n_tri] (a | b << 16, c); int hin[n_hin]; int2 hin_loc[n_hin]
+// (a | b << 16, c | d << 16); int vt_off[n_own + 1], vt_ent[]; int
+// vh_off[n_own + 1], vh_ent[] (entries: local element << 2 | corner).  Not
+// built when a patch would need more than 96 KB of shared memory.
+void pdc_ctx::build_residual_patches(const std::vector<int> &vto, const std::vector<int> &vtl,
+                                     const std::vector<int> &vho, const std::vector<int> &vhl,
+                                     const std::vector<int4> &tri_h, const std::vector<int4> &hin_h) {
+    rp_rec.release();
+    rp_off.release();
+    rp_loc = rp_tri = rp_hin = 0;
+    if (n == 0) return;
+    const std::vector<int> order = morton_order();
+    const int R = ELL_TILE_ROWS;
+    const size_t nb = ((size_t)n + R - 1) / R;
+    std::vector<unsigned char> rec;
+    std::vector<long long> off(nb + 1, 0);
+    std::vector<int> vloc(n, -1), tloc(m, -1), hloc(nh, -1);
+    std::vector<int> own, verts, tris, hins;
+    auto put = [&](const void *p, size_t bytes) {
+        const unsigned char *q = static_cast<const unsigned char *>(p);
+        rec.insert(rec.end(), q, q + bytes);
+        while (rec.size() % 16) rec.push_back(0);
+    };
+    for (size_t b = 0; b < nb; ++b) {
+        off[b] = (long long)rec.size();
+        own.assign(order.begin() + b * R, order.begin() + std::min((size_t)n, (b + 1) * R));
+        std::sort(own.begin(), own.end());
+        verts = own;
+        for (int k = 0; k < (int)own.size(); ++k) vloc[own[k]] = k;
+        tris.clear();
+        hins.clear();
+        for (int v : own) {
+            for (int e = vto[v]; e < vto[v + 1]; ++e)
+                if (tloc[vtl[e] >> 2] < 0) {
+                    tloc[vtl[e] >> 2] = (int)tris.size();
+                    tris.push_back(vtl[e] >> 2);
+                }
+            for (int e = vho[v]; e < vho[v + 1]; ++e)
+                if (hloc[vhl[e] >> 2] < 0) {
+                    hloc[vhl[e] >> 2] = (int)hins.size();
+                    hins.push_back(vhl[e] >> 2);
+                }
+        }
+        auto local = [&](int g) {
+            if (vloc[g] < 0) {
+                vloc[g] = (int)verts.size();
+                verts.push_back(g);
+            }
+            return vloc[g];
+        };
+        std::vector<int2> tl(tris.size()), hl(hins.size());
+        for (size_t k = 0; k < tris.size(); ++k) {
+            const int4 T = tri_h[tris[k]];
+            const int a = local(T.x), bb = local(T.y), cc = local(T.z);
+            tl[k] = make_int2(a | (bb << 16), cc);
+        }
+        for (size_t k = 0; k < hins.size(); ++k) {
+            const int4 Hh = hin_h[hins[k]];
+            const int a = local(Hh.x), bb = local(Hh.y), cc = local(Hh.z), dd = local(Hh.w);
+            hl[k] = make_int2(a | (bb << 16), cc | (dd << 16));
+        }
+        std::vector<int> vt_o(own.size() + 1, 0), vt_e, vh_o(own.size() + 1, 0), vh_e;
+        for (size_t k = 0; k < own.size(); ++k) {
+            const int v = own[k];
+            for (int e = vto[v]; e < vto[v + 1]; ++e) vt_e.push_back((tloc[vtl[e] >> 2] << 2) | (vtl[e] & 3));
+            for (int e = vho[v]; e < vho[v + 1]; ++e) vh_e.push_back((hloc[vhl[e] >> 2] << 2) | (vhl[e] & 3));
+            vt_o[k + 1] = (int)vt_e.size();
+            vh_o[k + 1] = (int)vh_e.size();
+        }
+        const bool fits = verts.size() < 65536;
+        const int hd[4] = {(int)verts.size(), (int)tris.size(), (int)hins.size(), (int)own.size()};
+        put(hd, sizeof(hd));
+        put(verts.data(), 4 * verts.size());
+        put(tris.data(), 4 * tris.size());
+        put(tl.data(), 8 * tl.size());
+        put(hins.data(), 4 * hins.size());
+        put(hl.data(), 8 * hl.size());
+        put(vt_o.data(), 4 * vt_o.size());
+        put(vt_e.data(), 4 * vt_e.size());
+        put(vh_o.data(), 4 * vh_o.size());
+        put(vh_e.data(), 4 * vh_e.size());
+        rp_loc = std::max(rp_loc, hd[0]);
+        rp_tri = std::max(rp_tri, hd[1]);
+        rp_hin = std::max(rp_hin, hd[2]);
+        for (int v : verts) vloc[v] = -1;
+        for (int t : tris) tloc[t] = -1;
+        for (int h : hins) hloc[h] = -1;
+        if (!fits) {
+            rp_loc = rp_tri = rp_hin = 0;
+            return;
+        }
+    }
+    off[nb] = (long long)rec.size();
+    if (residual_patch_smem() > 96 * 1024) {
+        rp_loc = rp_tri = rp_hin = 0;
+        return;
+    }
+    rp_rec.upload(rec, s);
+    rp_off.upload(off, s);
+}
+
+void pdc_ctx::build_patch_tiles(const std::vector<int> &ecol, const std::vector<float> &evalv) {
+    ell_halo.release();
+    if (n == 0 || ell_w == 0) return;
+    const std::vector<int> order = morton_order();
     const int R = ELL_TILE_ROWS, tw = ell_tw;
     const size_t nb = ((size_t)n + R - 1) / R, rb = halo_tile_bytes(tw);
     std::vector<unsigned char> rec(nb * rb, 0);
@@ -1298,7 +1436,7 @@ void pdc_ctx::build_patch_tiles(const std::vector<int> &ecol, const std::vector<
     for (size_t b = 0; b < nb; ++b) {
         own.clear();
         halo.clear();
-        for (size_t j = b * R; j < std::min((size_t)n, (b + 1) * R); ++j) own.push_back(key[j].second);
+        for (size_t j = b * R; j < std::min((size_t)n, (b + 1) * R); ++j) own.push_back(order[j]);
         std::sort(own.begin(), own.end());
         for (int t = 0; t < (int)own.size(); ++t) loc[own[t]] = t;
         bool ok = true;
@@ -2300,6 +2438,7 @@ void pdc_default_params(pdc_params *p) {
     p->graph_unroll = 1;
     p->loop_ahead = 1;
     p->cheb_source = -1;
+    p->residual_patch = 1;
 }
 
 static bool params_valid(const pdc_params *params) {
@@ -2312,6 +2451,7 @@ static bool params_valid(const pdc_params *params) {
            params->accel >= 0 && params->accel <= 2 && (params->accel != 2 || (params->aa_depth >= 1 && params->aa_depth <= 8)) &&
            params->loop_control >= 0 && params->loop_control <= 3 && params->loop_ahead >= 0 &&
            params->loop_ahead <= 2 && params->cheb_source >= -1 && params->cheb_source <= 2 &&
+           (params->residual_patch == 0 || params->residual_patch == 1) &&
            (params->pccd_adaptive == 0 || (params->pccd_adaptive == 1 && params->pccd_max_axis >= 1 &&
                                            params->pccd_max_axis <= 256 && params->alpha_ls > 0 && params->alpha_ls < 1));
 }

@@ -258,6 +258,142 @@ __global__ void __launch_bounds__(256) k_residual(const ClothView c, const float
     if (sc) block_add(sq, &sc->rsq);
 }
 
+// The same residual in one kernel per mesh patch (ClothView::rp_rec): a
+// block stages x* and u of the vertices its patch touches in shared memory,
+// computes the projections of the triangles and hinges at its rows once into
+// shared memory (a triangle's three corner forces as tri_corner forms them; a
+// hinge's vector s_hat - s and its four weights w K_j, whose products are
+// hinge_corner's corner forces), and each of its rows then sums its corner
+// forces in the order of its incidence lists, as k_residual does; the
+// per-corner arrays never go through device memory.
+// Elements at a patch border are computed by every patch they touch.  512
+// threads a block, four blocks an SM at 54 KB of shared memory (512 x 512
+// sheet): the element phase has about three elements per thread.
+__device__ __forceinline__ const unsigned char *align16(const unsigned char *p, size_t bytes) {
+    return p + ((bytes + 15) & ~(size_t)15);
+}
+
+__global__ void __launch_bounds__(512) k_residual_patch(const ClothView c, const float4 *__restrict__ xs,
+                                                        const float4 *__restrict__ u,
+                                                        const float4 *__restrict__ zrel,
+                                                        const float *__restrict__ cw, const float4 *__restrict__ cf,
+                                                        float4 *__restrict__ r, Scalars *sc,
+                                                        float *__restrict__ r_soa, int soa_ld) {
+    extern __shared__ float rp_sm[];
+    grid_dep_wait();
+    grid_dep_release();
+    if (loop_dead(c.live)) return;  // block-uniform: no thread reaches the block reduction
+    const int t = threadIdx.x;
+    const unsigned char *p = c.rp_rec + c.rp_off[blockIdx.x];
+    const int4 hd = *reinterpret_cast<const int4 *>(p);
+    const int nloc = hd.x, ntri = hd.y, nhin = hd.z, nown = hd.w;
+    const int *vid = reinterpret_cast<const int *>(align16(p, 16));
+    const int *tg = reinterpret_cast<const int *>(align16(reinterpret_cast<const unsigned char *>(vid), 4 * (size_t)nloc));
+    const int2 *tl = reinterpret_cast<const int2 *>(align16(reinterpret_cast<const unsigned char *>(tg), 4 * (size_t)ntri));
+    const int *hg = reinterpret_cast<const int *>(align16(reinterpret_cast<const unsigned char *>(tl), 8 * (size_t)ntri));
+    const int2 *hl = reinterpret_cast<const int2 *>(align16(reinterpret_cast<const unsigned char *>(hg), 4 * (size_t)nhin));
+    const int *vto = reinterpret_cast<const int *>(align16(reinterpret_cast<const unsigned char *>(hl), 8 * (size_t)nhin));
+    const int *vte = reinterpret_cast<const int *>(align16(reinterpret_cast<const unsigned char *>(vto), 4 * (size_t)(nown + 1)));
+    const int *vho = reinterpret_cast<const int *>(align16(reinterpret_cast<const unsigned char *>(vte), 4 * (size_t)__ldg(vto + nown)));
+    const int *vhe = reinterpret_cast<const int *>(align16(reinterpret_cast<const unsigned char *>(vho), 4 * (size_t)(nown + 1)));
+    float *px = rp_sm;                     // [3 * rp_loc] x*
+    float *pu = px + 3 * c.rp_loc;         // [3 * rp_loc] u
+    float *td = pu + 3 * c.rp_loc;         // [9 * rp_tri] triangle corner forces
+    float *hv = td + 9 * c.rp_tri;         // [7 * rp_hin] hinge: s_hat - s, then w K_j (j = 0..3)
+    for (int j = t; j < nloc; j += blockDim.x) {
+        const int g = __ldg(vid + j);
+        const float4 a = xs[g], b = u[g];
+        px[3 * j] = a.x;
+        px[3 * j + 1] = a.y;
+        px[3 * j + 2] = a.z;
+        pu[3 * j] = b.x;
+        pu[3 * j + 1] = b.y;
+        pu[3 * j + 2] = b.z;
+    }
+    __syncthreads();
+    auto P3 = [&](const float *q, int j) { return make_float3(q[3 * j], q[3 * j + 1], q[3 * j + 2]); };
+    auto put3 = [&](float *o, float3 v) {
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+    };
+    for (int e = t; e < ntri; e += blockDim.x) {  // as tri_corner
+        const float w = c.tri_w[__ldg(tg + e)];
+        const int gt = __ldg(tg + e);
+        const int2 L = __ldg(tl + e);
+        const int a = L.x & 0xffff, b = L.x >> 16, cc = L.y;
+        const float4 g = c.tri_g[gt];
+        const float3 p0 = P3(px, a), p1 = P3(px, b), p2 = P3(px, cc);
+        const float3 q0 = P3(pu, a), q1 = P3(pu, b), q2 = P3(pu, cc);
+        float3 e1 = (p1 - p0) + (q1 - q0), e2 = (p2 - p0) + (q2 - q0);
+        float3 F1 = g.x * e1 + g.z * e2;
+        float3 F2 = g.y * e1 + g.w * e2;
+        float3 R1, R2;
+        polar32(F1, F2, R1, R2);
+        const float3 d1 = R1 - F1, d2 = R2 - F2;
+        float *o = td + 9 * e;
+        put3(o, w * (-(g.x + g.z) * d1 + -(g.y + g.w) * d2));
+        put3(o + 3, w * (g.x * d1 + g.y * d2));
+        put3(o + 6, w * (g.z * d1 + g.w * d2));
+    }
+    for (int e = t; e < nhin; e += blockDim.x) {  // as hinge_corner
+        const int gh = __ldg(hg + e);
+        const int2 L = __ldg(hl + e);
+        const int a = L.x & 0xffff, b = L.x >> 16, cc = L.y & 0xffff, dd = L.y >> 16;
+        const float4 K = c.hin_K[gh];
+        const float sl = c.hin_slen[gh];
+        const float3 p0 = P3(px, a), q0 = P3(pu, a);
+        const float3 d1 = (P3(px, b) - p0) + (P3(pu, b) - q0);
+        const float3 d2 = (P3(px, cc) - p0) + (P3(pu, cc) - q0);
+        const float3 d3 = (P3(px, dd) - p0) + (P3(pu, dd) - q0);
+        const float3 sv = K.y * d1 + K.z * d2 + K.w * d3;
+        float3 sh;
+        const float ns = sqrtf(dot3(sv, sv));
+        if (sl == 0.f) sh = make_float3(0.f, 0.f, 0.f);
+        else if (ns > 1e-30f) sh = (sl / ns) * sv;
+        else sh = f3(c.hin_srest[gh]);
+        const float3 d = sh - sv;
+        const float hw = c.hin_w[gh];
+        float *o = hv + 7 * e;  // corner j = (w K_j) d, formed in the gather
+        put3(o, d);
+        o[3] = hw * K.x;
+        o[4] = hw * K.y;
+        o[5] = hw * K.z;
+        o[6] = hw * K.w;
+    }
+    __syncthreads();
+    float sq = 0.f;
+    if (t < nown) {
+        const int i = __ldg(vid + t);
+        float3 f = make_float3(0.f, 0.f, 0.f);
+        if (c.is_free[i]) {
+            f = c.mh2[i] * (f3(zrel[i]) - P3(pu, t));
+            const int tb = __ldg(vto + t), te = __ldg(vto + t + 1);
+#pragma unroll 4
+            for (int k = tb; k < te; ++k) {
+                const int ent = __ldg(vte + k);
+                f = f + P3(td, 3 * (ent >> 2) + (ent & 3));
+            }
+            const int hb = __ldg(vho + t), he = __ldg(vho + t + 1);
+#pragma unroll 4
+            for (int k = hb; k < he; ++k) {
+                const int ent = __ldg(vhe + k);
+                const float *o = hv + 7 * (ent >> 2);
+                f = f + o[3 + (ent & 3)] * make_float3(o[0], o[1], o[2]);
+            }
+            if (cf) f = f + f3(cf[i]);
+            sq = dot3(f, f);
+        }
+        r[i] = f4(f);
+        if (r_soa) {
+            r_soa[i] = f.x;
+            r_soa[soa_ld + i] = f.y;
+            r_soa[2 * soa_ld + i] = f.z;
+        }
+    }
+    if (sc) block_add(sq, &sc->rsq);
+}
+
 // sum_k H_ik delta_k over the ELL off-diagonals of row i; with WMAX > 0 (a
 // compile-time bound on the row width) the loop is unrolled so that the
 // loads of all entries are in flight together.
@@ -862,6 +998,20 @@ void launch_scale_disp(cudaStream_t s, int n, const float4 *xs, const float4 *u,
 
 void launch_residual(cudaStream_t s, const ClothView &c, const float4 *xs, const float4 *u, const float4 *zrel,
                      const float *cw, const float4 *cf, float4 *r, Scalars *sc, float *r_soa, int soa_ld) {
+    if (c.rp_rec && c.n > 0) {
+        const size_t smem = 4 * (6 * (size_t)c.rp_loc + 9 * (size_t)c.rp_tri + 7 * (size_t)c.rp_hin);
+        static unsigned long long attr = 0;  // per-device bits: the shared-memory limit raised
+        int dev = 0;
+        PDC_CK(cudaGetDevice(&dev));
+        if (!(attr >> (dev & 63) & 1ull)) {
+            PDC_CK(cudaFuncSetAttribute(k_residual_patch, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            attr |= 1ull << (dev & 63);
+        }
+        launch_dependent(c.overlap != 0, k_residual_patch, nblk(c.n, ELL_TILE_ROWS), 512, smem, s, c, xs, u, zrel, cw,
+                         cf, r, sc, r_soa, soa_ld);
+        PDC_LAUNCH_CK();
+        return;
+    }
     float4 *ct = c.corner, *ch = c.corner + 3 * (size_t)c.m;
     const int bs = (c.res_block == 64 || c.res_block == 128) ? c.res_block : 256;
     const int tb = nblk(c.m, bs), hb = nblk(c.nh, bs);

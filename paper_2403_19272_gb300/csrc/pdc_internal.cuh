@@ -150,6 +150,11 @@ struct ClothView {
     // patch's halo exceeds HALO_MAX or the tiles above are absent)
     const unsigned char *ell_halo;
     float4 *corner;        // scratch [3m + 4nh]: per-element corner forces of the residual
+    // one-kernel residual per mesh patch (NULL when not built or not used):
+    // records and their byte offsets, the largest counts over the patches
+    const unsigned char *rp_rec;
+    const long long *rp_off;
+    int rp_loc, rp_tri, rp_hin;
     int res_block;         // threads per block of the residual kernels (64, 128 or 256)
     int cheb_mode;         // Chebyshev step reads: 0 the ELL arrays, 1 the row tiles, 2 the patch tiles
     const int *live;       // device loop flag: the kernels do nothing when *live == 0 (NULL: always run)

@@ -44,7 +44,8 @@ class pdc_params(ctypes.Structure):
                 ("tensor_cores", c_i32), ("bp_reuse", c_dbl), ("launch_overlap", c_i32),
                 ("rf_toi", c_dbl), ("rf_iters", c_i32), ("loop_control", c_i32), ("pccd_adaptive", c_i32),
                 ("pccd_max_axis", c_i32), ("instance_line_search", c_i32), ("autotune", c_i32),
-                ("graph_unroll", c_i32), ("loop_ahead", c_i32), ("cheb_source", c_i32)]
+                ("graph_unroll", c_i32), ("loop_ahead", c_i32), ("cheb_source", c_i32),
+                ("residual_patch", c_i32)]
 
 
 class pdc_stats(ctypes.Structure):

@@ -251,10 +251,13 @@ def test_partial_ccd_parity_random_pairs(pc):
 
 
 # ----------------------------------------------------------------------------- local step / springs
-def test_residual_parity_force_form(pc):
+@pytest.mark.parametrize("patch", [1, 0])
+def test_residual_parity_force_form(pc, patch):
+    # patch 1: element forces and residual in one kernel per mesh patch;
+    # 0: two kernels through the per-corner force arrays
     rng = np.random.default_rng(25)
     sc = wl.drape_sphere(side=24, with_sphere=False)
-    cl = pc.Cloth(sc, params(pc))
+    cl = pc.Cloth(sc, params(pc, residual_patch=patch))
     m = pd.Model(sc.verts, sc.tris, sc.pins, sc.density, sc.k_stretch, sc.k_bend, 0.005)
     x = (m.X + rng.normal(size=m.X.shape) * 0.003).astype(np.float32)
     z = (m.X + rng.normal(size=m.X.shape) * 0.001).astype(np.float32)
@@ -274,20 +277,25 @@ def test_residual_parity_force_form(pc):
 
 def test_residual_parity_full_size_512(pc):
     # the benchmark's cloth (262,144 vertices, 522,242 triangles, 782,341
-    # hinges) in the launch configuration of the step; every entry compared
+    # hinges) in the launch configuration of the step; every entry compared,
+    # for the one-kernel patch form (the default) and the two-kernel form,
+    # which sum the same terms in the same order
     rng = np.random.default_rng(28)
     sc = wl.hanging_swept(side=512)
-    cl = pc.Cloth(sc, params(pc, r_warm=0))
     m = pd.Model(sc.verts, sc.tris, sc.pins, sc.density, sc.k_stretch, sc.k_bend, 0.005)
     x = (m.X + rng.normal(size=m.X.shape) * 5e-4).astype(np.float32)
     z = (m.X + rng.normal(size=m.X.shape) * 2e-4).astype(np.float32)
-    rg = pc.pdc_op_residual(cl.h, x, z)
     ro = -m.residual(x.astype(np.float64), z.astype(np.float64))
     full = np.zeros((m.n, 3))
     full[m.free] = ro
     scale = np.max(np.abs(full))
-    assert np.max(np.abs(rg - full)) <= 1e-4 * scale
-    cl.close()
+    rgs = []
+    for patch in (1, 0):
+        cl = pc.Cloth(sc, params(pc, r_warm=0, residual_patch=patch))
+        rgs.append(pc.pdc_op_residual(cl.h, x, z))
+        cl.close()
+        assert np.max(np.abs(rgs[-1] - full)) <= 1e-4 * scale, patch
+    assert np.max(np.abs(rgs[0] - rgs[1])) <= 1e-6 * scale
 
 
 def test_contact_springs_parity(pc):

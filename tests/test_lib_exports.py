@@ -57,7 +57,7 @@ def test_struct_layouts_match_header(libpath):
     assert p.tensor_cores == 1 and p.bp_reuse == 0.0
     # LG loops as graphs; fixed partial-CCD patterns, one line-search fraction, no autotuning
     assert p.loop_control == 1 and p.pccd_adaptive == 0 and p.pccd_max_axis == 64
-    assert p.instance_line_search == 0 and p.autotune == 0 and p.graph_unroll == 1 and p.loop_ahead == 1 and p.cheb_source == -1
+    assert p.instance_line_search == 0 and p.autotune == 0 and p.graph_unroll == 1 and p.loop_ahead == 1 and p.cheb_source == -1 and p.residual_patch == 1
 
 
 def test_binding_structs_have_the_header_layout(tmp_path):
