@@ -28,7 +28,9 @@ __device__ inline int cell1(float v, float inv) {
     c = fminf(fmaxf(c, (float)(-CELL_BIAS)), (float)(CELL_BIAS - 1));
     return (int)c;
 }
-__device__ inline int3 cellv(float3 p, float inv) { return make_int3(cell1(p.x, inv), cell1(p.y, inv), cell1(p.z, inv)); }
+__device__ inline int3 cellv(float3 p, float3 inv) {
+    return make_int3(cell1(p.x, inv.x), cell1(p.y, inv.y), cell1(p.z, inv.z));
+}
 __device__ inline unsigned long long cell_key(int x, int y, int z) {
     return ((unsigned long long)(x + CELL_BIAS) << 42) | ((unsigned long long)(y + CELL_BIAS) << 21) |
            (unsigned long long)(z + CELL_BIAS);
@@ -71,7 +73,7 @@ template <int K> __device__ inline void prim_box(const float4 *x0, const float4 
 __global__ void k_tri_boxes(CollView cv, const float4 *__restrict__ x0, const float4 *__restrict__ x1,
                             float4 *__restrict__ blo, float4 *__restrict__ bhi, GridParams *gp) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    float ext = 0.f;
+    float3 ext = make_float3(0.f, 0.f, 0.f);
     if (t < cv.nt) {
         int4 T = cv.tri[t];
         int ids[3] = {T.x, T.y, T.z};
@@ -79,10 +81,27 @@ __global__ void k_tri_boxes(CollView cv, const float4 *__restrict__ x0, const fl
         prim_box<3>(x0, x1, ids, lo, hi);
         blo[t] = f4(lo);
         bhi[t] = f4(hi);
-        ext = fmaxf(hi.x - lo.x, fmaxf(hi.y - lo.y, hi.z - lo.z));
+        ext = hi - lo;
     }
-    for (int o = 16; o > 0; o >>= 1) ext += __shfl_xor_sync(0xffffffffu, ext, o);
-    if ((threadIdx.x & 31) == 0 && ext > 0.f) atomicAdd(&gp->ext_sum, (double)ext);
+    // per-axis sums: warp, then block (one atomic per axis and block)
+    __shared__ float part[3][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        ext.x += __shfl_xor_sync(0xffffffffu, ext.x, o);
+        ext.y += __shfl_xor_sync(0xffffffffu, ext.y, o);
+        ext.z += __shfl_xor_sync(0xffffffffu, ext.z, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        part[0][w] = ext.x;
+        part[1][w] = ext.y;
+        part[2][w] = ext.z;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double sum = 0.0;
+        for (int k = 0; k < nw; ++k) sum += part[threadIdx.x][k];
+        if (sum > 0.0) atomicAdd(&gp->ext_sum[threadIdx.x], sum);
+    }
 }
 
 __global__ void k_edge_boxes(CollView cv, const float4 *__restrict__ x0, const float4 *__restrict__ x1,
@@ -98,11 +117,13 @@ __global__ void k_edge_boxes(CollView cv, const float4 *__restrict__ x0, const f
 }
 
 __global__ void k_grid_params(GridParams *gp, int nt, float dhat, float scale) {
-    double mean = nt > 0 ? gp->ext_sum / nt : 0.0;
-    float cell = fmaxf((float)mean, 2.f * dhat);
-    cell = fmaxf(cell, 1e-6f) * scale;
-    gp->cell = cell;
-    gp->inv_cell = 1.f / cell;
+    for (int d = 0; d < 3; ++d) {
+        double mean = nt > 0 ? gp->ext_sum[d] / nt : 0.0;
+        float cell = fmaxf((float)mean, 2.f * dhat);
+        cell = fmaxf(cell, 1e-6f) * scale;
+        gp->cell[d] = cell;
+        gp->inv_cell[d] = 1.f / cell;
+    }
 }
 
 // ------------------------------------------------------------------ cell table
@@ -162,7 +183,7 @@ __global__ void k_cell_insert(CollView cv, const float4 *__restrict__ x0, const 
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned lane = threadIdx.x & 31;
     if (mode == 1 && *total > cap) return;  // the table does not fit (uniform over the grid)
-    const float inv = gp->inv_cell;
+    const float3 inv = make_float3(gp->inv_cell[0], gp->inv_cell[1], gp->inv_cell[2]);
     int kind = 0, prim = 0, ncell = 0;
     int3 lo = make_int3(0, 0, 0), hi = make_int3(-1, -1, -1);
     if (p < np) {
@@ -268,8 +289,8 @@ struct KindCounts {
 __device__ __forceinline__ KindCounts load_chunk(CellRegion &R, const CollView &cv, const float4 *x0, const float4 *x1,
                                         const float4 *tlo, const float4 *thi, const float4 *elo, const float4 *ehi,
                                         const unsigned long long *ekey, const unsigned int *epay, int e0, int cnt,
-                                        float cell, float dhat, unsigned lane) {
-    const float qs = 256.f / cell;
+                                        float3 cell, float dhat, unsigned lane) {
+    const float3 qs = make_float3(256.f / cell.x, 256.f / cell.y, 256.f / cell.z);
     const unsigned below = (1u << lane) - 1u;
     KindCounts kc = {0, 0, 0};
     for (int base = 0; base < cnt; base += 32) {  // warp-uniform
@@ -321,13 +342,13 @@ __device__ __forceinline__ KindCounts load_chunk(CellRegion &R, const CollView &
             R.ids[d] = ids;
             R.key[d] = key;
             // cell origin from the key (the same for every entry of the cell)
-            const float cx = __fmul_rn((float)((int)((key >> 42) & 0x1fffffu) - CELL_BIAS), cell);
-            const float cy = __fmul_rn((float)((int)((key >> 21) & 0x1fffffu) - CELL_BIAS), cell);
-            const float cz = __fmul_rn((float)((int)(key & 0x1fffffu) - CELL_BIAS), cell);
+            const float cx = __fmul_rn((float)((int)((key >> 42) & 0x1fffffu) - CELL_BIAS), cell.x);
+            const float cy = __fmul_rn((float)((int)((key >> 21) & 0x1fffffu) - CELL_BIAS), cell.y);
+            const float cz = __fmul_rn((float)((int)(key & 0x1fffffu) - CELL_BIAS), cell.z);
             const float3 hr = raise_d(hi, dhat);
-            R.qlo[d] = quant_lo(lo.x, cx, qs) | (quant_lo(lo.y, cy, qs) << 9) | (quant_lo(lo.z, cz, qs) << 18) |
+            R.qlo[d] = quant_lo(lo.x, cx, qs.x) | (quant_lo(lo.y, cy, qs.y) << 9) | (quant_lo(lo.z, cz, qs.z) << 18) |
                        (fl << 27);
-            R.qhi[d] = quant_hi(hr.x, cx, qs) | (quant_hi(hr.y, cy, qs) << 9) | (quant_hi(hr.z, cz, qs) << 18) |
+            R.qhi[d] = quant_hi(hr.x, cx, qs.x) | (quant_hi(hr.y, cy, qs.y) << 9) | (quant_hi(hr.z, cz, qs.z) << 18) |
                        Q_GUARD;
         }
         cv_ += __popc(mv);
@@ -490,7 +511,7 @@ __global__ void __launch_bounds__(W * 32) k_cell_pairs(CollView cv, const float4
     const unsigned lane = threadIdx.x & 31;
     CellWarp &cw = reinterpret_cast<CellWarp *>(cell_smem)[threadIdx.x >> 5];
     PairQueue q{cw, dhat, o, lane};
-    const float cell = gp->cell;
+    const float3 cell = make_float3(gp->cell[0], gp->cell[1], gp->cell[2]);
     for (;;) {
         int b0 = 0;
         if (lane == 0) b0 = atomicAdd(work, 32);

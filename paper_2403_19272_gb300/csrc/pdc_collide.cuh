@@ -9,9 +9,12 @@ namespace pdc {
 
 enum OverflowBits { OVF_HASH = 1, OVF_VT = 2, OVF_EE = 4, OVF_ACTIVE = 8, OVF_CELLS = 16, OVF_SLOTS = 32 };
 
+// Cells are boxes whose side along each axis follows the mean swept-box
+// extent of the triangles along that axis (boxes stretched by the motion
+// get cells stretched the same way).
 struct GridParams {
-    double ext_sum;  // sum over triangles of the largest swept-box extent
-    float cell, inv_cell;
+    double ext_sum[3];  // per axis: sum over triangles of the swept-box extent
+    float cell[3], inv_cell[3];
 };
 
 // Collision settings shared by the pair kernels.
