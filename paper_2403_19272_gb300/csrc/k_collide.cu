@@ -669,9 +669,12 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
     elo.alloc(cv.ne);
     ehi.alloc(cv.ne);
     cnt_v.alloc(cv.nv);
-    off_v.alloc(cv.nv);
+    for (int k = 0; k < 2; ++k) {
+        off_v[k].alloc(std::max(cv.nv, 1));
+        off_e[k].alloc(std::max(cv.ne, 1));
+        off_ok[k] = false;
+    }
     cnt_e.alloc(cv.ne);
-    off_e.alloc(cv.ne);
     slots_vt.alloc((size_t)cv.nv * w_vt);
     slots_ee.alloc((size_t)cv.ne * w_ee);
     long long mx = std::max<long long>(T, std::max<long long>(cv.nv, cv.ne));
@@ -774,7 +777,8 @@ void BroadPhase::grow(const CollView &cv, long long cvt, long long cee, long lon
 void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat,
                      int *overflow) {
     int nw = cur ^ 1;
-    hash_pass(s, cv, x0, x1, dhat, overflow, vt[nw], ee[nw], cnt_vt_d[nw], cnt_ee_d[nw]);
+    hash_pass(s, cv, x0, x1, dhat, overflow, vt[nw], ee[nw], cnt_vt_d[nw], cnt_ee_d[nw], nw);
+    off_ok[nw] = true;
     cur = nw;
     sup_ok = false;
     k_pccd_force<<<1, 1, 0, s>>>(pccd);  // new lists: the next partial-CCD pass scans them all
@@ -782,7 +786,8 @@ void BroadPhase::run(cudaStream_t s, const CollView &cv, const float4 *x0, const
 }
 
 void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat,
-                           int *overflow, int2 *out_vt, int2 *out_ee, long long *out_nvt, long long *out_nee) {
+                           int *overflow, int2 *out_vt, int2 *out_ee, long long *out_nvt, long long *out_nee,
+                           int slot) {
     long long *tot = totals.p;
     const int np = cv.nv + cv.ne + cv.nt;
     const unsigned mask = (unsigned)(T - 1);
@@ -876,16 +881,17 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
     }
     // ---- rows -> sorted pair lists
     if (prof) prof->begin(s, "bp_compact", 0.0);
-    exclusive_scan(s, cnt_v, off_v, cv.nv, scratch, tot + 2);
+    int *ov = off_v[slot], *oe = off_e[slot];
+    exclusive_scan(s, cnt_v, ov, cv.nv, scratch, tot + 2);
     k_check_cap<<<1, 1, 0, s>>>(tot + 2, cap_vt, OVF_VT, overflow, out_nvt);
     if (cv.nv) {
-        k_compact_rows<<<nblk(cv.nv, 256), 256, 0, s>>>(cv.nv, cnt_v, off_v, slots_vt, w_vt, tot + 2, cap_vt, out_vt);
+        k_compact_rows<<<nblk(cv.nv, 256), 256, 0, s>>>(cv.nv, cnt_v, ov, slots_vt, w_vt, tot + 2, cap_vt, out_vt);
         PDC_LAUNCH_CK();
     }
-    exclusive_scan(s, cnt_e, off_e, cv.ne, scratch, tot + 3);
+    exclusive_scan(s, cnt_e, oe, cv.ne, scratch, tot + 3);
     k_check_cap<<<1, 1, 0, s>>>(tot + 3, cap_ee, OVF_EE, overflow, out_nee);
     if (cv.ne) {
-        k_compact_rows<<<nblk(cv.ne, 256), 256, 0, s>>>(cv.ne, cnt_e, off_e, slots_ee, w_ee, tot + 3, cap_ee, out_ee);
+        k_compact_rows<<<nblk(cv.ne, 256), 256, 0, s>>>(cv.ne, cnt_e, oe, slots_ee, w_ee, tot + 3, cap_ee, out_ee);
         PDC_LAUNCH_CK();
     }
     if (prof) prof->end(s);
@@ -899,7 +905,8 @@ void BroadPhase::run_super(cudaStream_t s, const CollView &cv, const float4 *x0,
     // gap of the superset: every pair within d_hat of each other on a swept
     // box grown by mu' per side is within d_hat + 2 mu on the reference boxes
     float gap = dhat + 2.f * mu;
-    hash_pass(s, cv, x0, x1, gap, overflow, sup_vt, sup_ee, sup_cnt.p, sup_cnt.p + 1);
+    hash_pass(s, cv, x0, x1, gap, overflow, sup_vt, sup_ee, sup_cnt.p, sup_cnt.p + 1, cur ^ 1);
+    off_ok[cur ^ 1] = false;  // those offsets are the superset's
     long long cnt[2] = {0, 0};
     sup_cnt.download(cnt, 2, s);
     PDC_CK(cudaStreamSynchronize(s));
@@ -965,6 +972,7 @@ void BroadPhase::filter(cudaStream_t s, const CollView &cv, const float4 *x0, co
         PDC_CK(cudaMemcpyAsync(nout, tot + 6 + k, sizeof(long long), cudaMemcpyDeviceToDevice, s));
     }
     if (prof) prof->end(s);
+    off_ok[nw] = false;  // a filtered list has no segment offsets
     cur = nw;
     k_pccd_force<<<1, 1, 0, s>>>(pccd);  // new lists: the next partial-CCD pass scans them all
     PDC_LAUNCH_CK();

@@ -444,6 +444,21 @@ __device__ inline long long find_pair(const int2 *list, long long n, int2 key) {
     return -1;
 }
 
+// The same search within the segment of key.x when the list's per-primary
+// offsets are known (off: np primaries, the last segment ends at n).
+__device__ inline long long find_pair_seg(const int2 *list, long long n, const int *off, int np, int2 key) {
+    if (key.x < 0 || key.x >= np) return -1;
+    long long b = off[key.x], e = key.x + 1 < np ? (long long)off[key.x + 1] : n;
+    b = max(b, 0ll);
+    e = min(e, n);
+    for (long long j = b; j < e; ++j) {
+        const int2 v = list[j];
+        if (v.x == key.x && v.y == key.y) return j;
+        if (v.x != key.x || v.y > key.y) break;
+    }
+    return -1;
+}
+
 constexpr int PAIR_THREADS = 256;
 
 __global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const int2 *__restrict__ vt,
@@ -454,6 +469,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const in
                                                            const long long *onvt_p, const long long *onee_p,
                                                            const unsigned char *__restrict__ ost_vt,
                                                            const unsigned char *__restrict__ ost_ee,
+                                                           const int *__restrict__ ooff_v, const int *__restrict__ ooff_e,
                                                            const float4 *__restrict__ x0, const float4 *__restrict__ x1,
                                                            double eta, unsigned long long *toi_min) {
     long long nvt = *nvt_p, n = nvt + *nee_p;
@@ -466,10 +482,11 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const in
         if (ovt) {
             long long j;
             if (kind == 0) {
-                j = find_pair(ovt, onvt, vt[idx]);
+                j = ooff_v ? find_pair_seg(ovt, onvt, ooff_v, cv.nv, vt[idx]) : find_pair(ovt, onvt, vt[idx]);
                 if (j >= 0) st = ost_vt[j];
             } else {
-                j = find_pair(oee, onee, ee[idx - nvt]);
+                j = ooff_e ? find_pair_seg(oee, onee, ooff_e, cv.ne, ee[idx - nvt])
+                           : find_pair(oee, onee, ee[idx - nvt]);
                 if (j >= 0) st = ost_ee[j];
             }
             if (!(st & ST_ACTIVE)) st = 0;
@@ -841,7 +858,8 @@ void launch_full_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const f
         k_full_ccd<<<blocks, PAIR_THREADS, 0, s>>>(
             cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c], bp.st_vt[c], bp.st_ee[c],
             merge ? bp.vt[o].p : nullptr, merge ? bp.ee[o].p : nullptr, bp.cnt_vt_d[o], bp.cnt_ee_d[o], bp.st_vt[o],
-            bp.st_ee[o], x0, x1, P.eta, toi_min);
+            bp.st_ee[o], merge && bp.off_ok[o] ? bp.off_v[o].p : nullptr, merge && bp.off_ok[o] ? bp.off_e[o].p : nullptr,
+            x0, x1, P.eta, toi_min);
         PDC_LAUNCH_CK();
     };
     if (bp.tune_pairs) {

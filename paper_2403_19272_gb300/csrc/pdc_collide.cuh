@@ -76,7 +76,13 @@ struct BroadPhase {
     DevBuf<unsigned int> epay;        // primitive | kind << 27 | lowest-cell flags << 29
     DevBuf<int> work;                 // bucket counter of the cell-pair kernel
     DevBuf<float4> tlo, thi, elo, ehi;
-    DevBuf<int> cnt_v, off_v, cnt_e, off_e, scratch;
+    DevBuf<int> cnt_v, cnt_e, scratch;
+    // per list buffer: offset of each primary's segment in that list (the
+    // prefix sum of the counts), valid when the list came from a hash pass
+    // (off_ok), so that the next full CCD finds a pair's old state in its
+    // primary's segment instead of by binary search over the whole list
+    DevBuf<int> off_v[2], off_e[2];
+    bool off_ok[2] = {false, false};
     DevBuf<int> slots_vt, slots_ee;  // per-primary candidate rows (sorted when compacted)
     int w_vt = 16, w_ee = 32;        // row widths (doubled on OVF_SLOTS)
     DevBuf<GridParams> gp;
@@ -134,7 +140,7 @@ struct BroadPhase {
     void filter(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat);
     // the hash pipeline writing into the given lists
     void hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0, const float4 *x1, float dhat, int *overflow,
-                   int2 *out_vt, int2 *out_ee, long long *out_nvt, long long *out_nee);
+                   int2 *out_vt, int2 *out_ee, long long *out_nvt, long long *out_nee, int slot);
 };
 
 // Exact CCD over the current lists; if merge, NDB states are carried over
