@@ -125,14 +125,14 @@ __device__ inline double det3(V<double> a, V<double> b, V<double> c) { return do
 __device__ inline double cubic(const double c[4], double t) { return ((c[3] * t + c[2]) * t + c[1]) * t + c[0]; }
 
 // Exact CCD (Sec. 4, Eq. intersect) of one pair moving linearly q0 -> q1.
-// FP32 filter: the distance at t = 0 minus the largest relative displacement
-// bounds the distance over the whole interval from below; pairs that stay
-// apart are rejected.  Survivors: the four points must become coplanar for
+// FP32 filter (ccd_may_hit): a Lipschitz bound of the distance over [0, 1]
+// rejects pairs that stay apart.  Survivors (ccd_exact, FP64): the four points must become coplanar for
 // contact, f(t) = det[q1-q0, q2-q0, q3-q0] = 0 (cubic); candidate times are
 // 0, the critical points of f and its roots (bisection on monotone pieces),
 // in increasing order; the first one at which the primitives are within eta
 // is the time of impact.  Coplanar motion (f == 0): 1025 uniform samples.
-__device__ double ccd_pair(int kind, const float4 a0[4], const float4 a1[4], double eta) {
+// The FP32 part: false when no impact is possible (the pair is then done).
+__device__ inline bool ccd_may_hit(int kind, const float4 a0[4], const float4 a1[4], double eta) {
     {
         V<float> q[4];
         float cmax = 0.f;
@@ -152,8 +152,31 @@ __device__ double ccd_pair(int kind, const float4 a0[4], const float4 a1[4], dou
                 for (int k = 2; k < 4; ++k) { V<float> r = dv[k] - dv[j]; maxrel = fmaxf(maxrel, sqrtf(dotv(r, r))); }
         }
         float d0 = gap_dist<float>(kind, q);
-        if (d0 > 1.001f * maxrel + (float)eta + 4e-6f * cmax) return 2.0;
+        // The gap d(t) of linearly moving primitives changes by at most the
+        // largest relative displacement L per unit t (for fixed closest-point
+        // parameters the gap vector moves by a convex combination of relative
+        // displacements), so on [t_a, t_b] it stays above
+        // (d(t_a) + d(t_b) - L (t_b - t_a)) / 2.  No impact if that bound
+        // clears eta (with the FP32 margin) on all of [0, 1]: first from d0
+        // alone, then on eight sub-intervals.
+        const float L = 1.001f * maxrel, mg = (float)eta + 4e-6f * cmax;
+        if (d0 > L + mg) return false;
+        bool clear = true;
+        float dprev = d0;
+        for (int k = 1; k <= 8 && clear; ++k) {
+            const float t = 0.125f * (float)k;
+            V<float> qt[4];
+            for (int i = 0; i < 4; ++i) qt[i] = q[i] + t * dv[i];
+            const float dk = gap_dist<float>(kind, qt);
+            if (0.5f * (dprev + dk - 0.125f * L) <= mg) clear = false;
+            dprev = dk;
+        }
+        return !clear;
     }
+}
+
+// The FP64 part for pairs that passed ccd_may_hit.
+__device__ double ccd_exact(int kind, const float4 a0[4], const float4 a1[4], double eta) {
     V<double> q0[4], q1[4];
     for (int i = 0; i < 4; ++i) { q0[i] = ld<double>(a0[i]); q1[i] = ld<double>(a1[i]); }
     V<double> u0 = q0[1] - q0[0], v0 = q0[2] - q0[0], w0 = q0[3] - q0[0];
@@ -232,6 +255,10 @@ __device__ double ccd_pair(int kind, const float4 a0[4], const float4 a1[4], dou
     for (int i = 0; i < nc; ++i)
         if (at(cand[i]) <= eta) return cand[i];
     return 2.0;
+}
+
+__device__ double ccd_pair(int kind, const float4 a0[4], const float4 a1[4], double eta) {
+    return ccd_may_hit(kind, a0, a1, eta) ? ccd_exact(kind, a0, a1, eta) : 2.0;
 }
 
 // Partial CCD (Sec. 4.1): Q(lambda) = (p2^1 - p1^1).(p2^0 - p1^0) at the t=0
@@ -461,50 +488,93 @@ __device__ inline long long find_pair_seg(const int2 *list, long long n, const i
 
 constexpr int PAIR_THREADS = 256;
 
-__global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd(CollView cv, const int2 *__restrict__ vt,
-                                                           const int2 *__restrict__ ee, const long long *nvt_p,
-                                                           const long long *nee_p, unsigned char *__restrict__ st_vt,
-                                                           unsigned char *__restrict__ st_ee,
-                                                           const int2 *__restrict__ ovt, const int2 *__restrict__ oee,
-                                                           const long long *onvt_p, const long long *onee_p,
-                                                           const unsigned char *__restrict__ ost_vt,
-                                                           const unsigned char *__restrict__ ost_ee,
-                                                           const int *__restrict__ ooff_v, const int *__restrict__ ooff_e,
-                                                           const float4 *__restrict__ x0, const float4 *__restrict__ x1,
-                                                           double eta, unsigned long long *toi_min) {
-    long long nvt = *nvt_p, n = nvt + *nee_p;
-    long long onvt = ovt ? *onvt_p : 0, onee = oee ? *onee_p : 0;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (long long)gridDim.x * blockDim.x) {
+// Full CCD in two kernels.  k_full_ccd_filter takes every pair: its NDB
+// state carried from the previous list (merge), then the FP32 filter; a pair
+// that cannot hit is done, the others are appended (warp-aggregated) to a
+// survivor list.  k_full_ccd_exact runs the FP64 part on the survivors only,
+// so the filter runs at full occupancy and the FP64 registers are paid only
+// where needed.  An impact in [0, 1] makes the pair active.
+__global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd_filter(
+    CollView cv, const int2 *__restrict__ vt, const int2 *__restrict__ ee, const long long *nvt_p,
+    const long long *nee_p, unsigned char *__restrict__ st_vt, unsigned char *__restrict__ st_ee,
+    const int2 *__restrict__ ovt, const int2 *__restrict__ oee, const long long *onvt_p, const long long *onee_p,
+    const unsigned char *__restrict__ ost_vt, const unsigned char *__restrict__ ost_ee,
+    const int *__restrict__ ooff_v, const int *__restrict__ ooff_e, const float4 *__restrict__ x0,
+    const float4 *__restrict__ x1, double eta, int *__restrict__ surv, int *nsurv, long long cap) {
+    const long long nvt = *nvt_p, n = nvt + *nee_p;
+    const long long onvt = ovt ? *onvt_p : 0, onee = oee ? *onee_p : 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const unsigned lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {  // warp-uniform trip count
+        const long long idx = base + lane;
+        bool hit = false;
+        int ids[4], kind;
+        if (idx < n && pair_ids(cv, vt, ee, nvt, idx, ids, kind)) {
+            unsigned char st = 0;
+            if (ovt) {
+                long long j;
+                if (kind == 0) {
+                    j = ooff_v ? find_pair_seg(ovt, onvt, ooff_v, cv.nv, vt[idx]) : find_pair(ovt, onvt, vt[idx]);
+                    if (j >= 0) st = ost_vt[j];
+                } else {
+                    j = ooff_e ? find_pair_seg(oee, onee, ooff_e, cv.ne, ee[idx - nvt])
+                               : find_pair(oee, onee, ee[idx - nvt]);
+                    if (j >= 0) st = ost_ee[j];
+                }
+                if (!(st & ST_ACTIVE)) st = 0;
+            }
+            if (kind == 0) st_vt[idx] = st;
+            else st_ee[idx - nvt] = st;
+            float4 a0[4], a1[4];
+            for (int i = 0; i < 4; ++i) {
+                a0[i] = x0[ids[i]];
+                a1[i] = x1[ids[i]];
+            }
+            hit = ccd_may_hit(kind, a0, a1, eta);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m) {
+            int b0 = 0;
+            if (lane == 0) b0 = atomicAdd(nsurv, __popc(m));
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            const long long pos = (long long)b0 + __popc(m & ((1u << lane) - 1u));
+            if (hit && pos < cap) surv[pos] = (int)idx;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(PAIR_THREADS) k_full_ccd_exact(CollView cv, const int2 *__restrict__ vt,
+                                                                 const int2 *__restrict__ ee, const long long *nvt_p,
+                                                                 unsigned char *__restrict__ st_vt,
+                                                                 unsigned char *__restrict__ st_ee,
+                                                                 const int *__restrict__ surv, const int *nsurv,
+                                                                 long long cap, const float4 *__restrict__ x0,
+                                                                 const float4 *__restrict__ x1, double eta,
+                                                                 unsigned long long *toi_min) {
+    const long long nvt = *nvt_p, ns = min((long long)*nsurv, cap);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < ns;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long idx = surv[k];
         int ids[4], kind;
         if (!pair_ids(cv, vt, ee, nvt, idx, ids, kind)) continue;
-        unsigned char st = 0;
-        if (ovt) {
-            long long j;
-            if (kind == 0) {
-                j = ooff_v ? find_pair_seg(ovt, onvt, ooff_v, cv.nv, vt[idx]) : find_pair(ovt, onvt, vt[idx]);
-                if (j >= 0) st = ost_vt[j];
-            } else {
-                j = ooff_e ? find_pair_seg(oee, onee, ooff_e, cv.ne, ee[idx - nvt])
-                           : find_pair(oee, onee, ee[idx - nvt]);
-                if (j >= 0) st = ost_ee[j];
-            }
-            if (!(st & ST_ACTIVE)) st = 0;
-        }
         float4 a0[4], a1[4];
-        for (int i = 0; i < 4; ++i) { a0[i] = x0[ids[i]]; a1[i] = x1[ids[i]]; }
-        double t = ccd_pair(kind, a0, a1, eta);
+        for (int i = 0; i < 4; ++i) {
+            a0[i] = x0[ids[i]];
+            a1[i] = x1[ids[i]];
+        }
+        const double t = ccd_exact(kind, a0, a1, eta);
         if (t <= 1.0) {
-            st |= ST_ACTIVE;
+            if (kind == 0) st_vt[idx] |= ST_ACTIVE;
+            else st_ee[idx - nvt] |= ST_ACTIVE;
             const unsigned long long tb = (unsigned long long)__double_as_longlong(t);
             atomicMin(toi_min, tb);
             if (cv.toi_inst)  // every instance the pair touches
                 for (int j = 0; j < 4; ++j) {
-                    const int k = cv.vinst[ids[j]];
-                    if (k >= 0) atomicMin(&cv.toi_inst[k], tb);
+                    const int kk = cv.vinst[ids[j]];
+                    if (kk >= 0) atomicMin(&cv.toi_inst[kk], tb);
                 }
         }
-        if (kind == 0) st_vt[idx] = st; else st_ee[idx - nvt] = st;
     }
 }
 
@@ -854,12 +924,18 @@ unsigned int pair_guard_take(cudaStream_t s, unsigned int *guard) {
 void launch_full_ccd(cudaStream_t s, const CollView &cv, BroadPhase &bp, const float4 *x0, const float4 *x1,
                      const CollParams &P, bool merge, unsigned long long *toi_min) {
     int c = bp.cur, o = c ^ 1;
+    // survivors of the filter go to the near list (free until the next partial CCD)
+    bp.ccd_count.alloc(1);
     auto launch = [&](int blocks) {
-        k_full_ccd<<<blocks, PAIR_THREADS, 0, s>>>(
+        bp.ccd_count.zero(s);
+        k_full_ccd_filter<<<blocks, PAIR_THREADS, 0, s>>>(
             cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.cnt_ee_d[c], bp.st_vt[c], bp.st_ee[c],
             merge ? bp.vt[o].p : nullptr, merge ? bp.ee[o].p : nullptr, bp.cnt_vt_d[o], bp.cnt_ee_d[o], bp.st_vt[o],
             bp.st_ee[o], merge && bp.off_ok[o] ? bp.off_v[o].p : nullptr, merge && bp.off_ok[o] ? bp.off_e[o].p : nullptr,
-            x0, x1, P.eta, toi_min);
+            x0, x1, P.eta, bp.near, bp.ccd_count, bp.cap_pairs);
+        k_full_ccd_exact<<<blocks, PAIR_THREADS, 0, s>>>(cv, bp.vt[c], bp.ee[c], bp.cnt_vt_d[c], bp.st_vt[c],
+                                                         bp.st_ee[c], bp.near, bp.ccd_count, bp.cap_pairs, x0, x1,
+                                                         P.eta, toi_min);
         PDC_LAUNCH_CK();
     };
     if (bp.tune_pairs) {

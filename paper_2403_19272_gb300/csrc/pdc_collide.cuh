@@ -109,6 +109,7 @@ struct BroadPhase {
     // displacement of the last full pass, bookkeeping
     long long cap_pairs = 0;
     DevBuf<int> near, watch[2];
+    DevBuf<int> ccd_count;  // survivors of the full CCD's FP32 filter (listed in near)
     DevBuf<float4> disp0;
     DevBuf<PccdState> pccd;
     void reserve_pccd(const CollView &cv, cudaStream_t s);
