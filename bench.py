@@ -426,7 +426,7 @@ PARENTS = {"broad_phase", "partial_ccd"}
 # DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, one
 # capture at 512x512) of the kernels that can be the dominant one; the file
 # under profiles/ gives the command
-TRAFFIC = {"cheb_sweep": 33799680.0}
+TRAFFIC = {"cheb_sweep": 35386880.0}
 
 
 def l2_copy_peak(pc, stream, mbytes=40):
@@ -438,9 +438,9 @@ def l2_copy_peak(pc, stream, mbytes=40):
 
 
 # working set of the dominant kernel per launch at the benchmark size (bytes):
-# H tiles (18.9 MB) and the residual, three Chebyshev iterates, diagonal and
-# iterate streams (float4, 4.2 MB each)
-WORKING_SET = {"cheb_sweep": 18.9e6 + 6 * 4.19e6}
+# the patch tiles of H (1,024 x 21.5 KB) and the residual, three Chebyshev
+# iterates, diagonal and iterate streams (float4, 4.2 MB each)
+WORKING_SET = {"cheb_sweep": 22.0e6 + 6 * 4.19e6}
 L2_BYTES = 129e6
 
 
