@@ -280,7 +280,7 @@ def solver_like(pc, p):
     return q
 
 
-def run_batched(pc, torch, steps=5, warmup=2, dev_index=0):
+def run_batched(pc, torch, steps=5, warmup=5, dev_index=0):
     """Batched form (64 drapes of sides 16..192 over their own spheres, about
     0.9 M vertices, FP32, 32 LG iterations per step): one batched handle
     against the same 64 cloths stepped one after another on 64 handles.
