@@ -59,8 +59,8 @@ def parse():
                          "3 on the device, the host enqueueing each iteration ahead as one graph launch; 2 the "
                          "same with kernel launches; 0 on the host")
     ap.add_argument("--graph-unroll", type=int, default=1, help="LG iterations per pass of a graph loop (1..8)")
-    ap.add_argument("--cheb-source", type=int, default=-1, choices=[-1, 0, 1, 2],
-                    help="matrix of the Chebyshev steps: -1 automatic, 0 ELL arrays, 1 row tiles, 2 patch tiles")
+    ap.add_argument("--cheb-source", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                    help="matrix of the Chebyshev steps: -1 automatic, 0 ELL arrays, 1 row tiles, 2 patch tiles, 3 two steps a launch")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="1: launch shapes and the broad-phase grid timed on the handle's data in the warm-up")
     ap.add_argument("--loop-ahead", type=int, default=1, choices=[0, 1, 2],

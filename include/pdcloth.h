@@ -209,9 +209,11 @@ typedef struct {
                                 the patch tiles when they exist, else the row
                                 tiles (autotune: the fastest of those built);
                                 0 the ELL arrays; 1 the row tiles; 2 the patch
-                                tiles (a source that is not built falls back
-                                to the next simpler one).  Same arithmetic in
-                                the same order in every source                  */
+                                tiles; 3 two steps a launch over patches
+                                widened by a second ring (a source that is not
+                                built falls back to the next simpler one).
+                                Same arithmetic in the same order in every
+                                source                                          */
     int32_t residual_patch;  /* 1 (default): the element projections and the
                                 residual of an LG iteration in one kernel per
                                 mesh patch (each patch's element forces in
@@ -253,14 +255,15 @@ typedef struct {
     int32_t cheb_tile;       /* Chebyshev steps read 2 (default when built): the
                                 matrix tiles of compact patches of the rest
                                 mesh, delta staged with the patch's halo in
-                                shared memory; 1: the TMA-staged tiles of
-                                consecutive rows; 0: the ELL arrays
-                                (candidates 1, 0, 2)                            */
+                                shared memory; 3: two steps a launch over
+                                patches widened by a second ring; 1: the
+                                TMA-staged tiles of consecutive rows; 0: the
+                                ELL arrays (candidates 1, 0, 2, 3)              */
     int32_t pair_blocks;     /* blocks of the per-pair kernels (152 x 2, 4, 8, 16) */
     int32_t cell_warps;      /* warps per block of the broad phase's cell-pair
                                 kernel (candidates 2, 4, 8)                     */
     float residual_ms[3];
-    float cheb_ms[3];
+    float cheb_ms[4];
     float pair_ms[4];
     float cell_ms[3];
     float cell_grid;         /* factor of the broad phase's cell side over the

@@ -440,6 +440,9 @@ struct pdc_ctx {
     DevBuf<unsigned char> ell_tile;
     int ell_tw = 0;
     DevBuf<unsigned char> ell_halo;  // patch tiles (ClothView::ell_halo)
+    DevBuf<unsigned char> ell_halo2; // two-step patch tiles (ClothView::ell_halo2)
+    int h2_rows = 0, h2_verts = 0;
+    void build_patch_tiles2(const std::vector<int> &ecol, const std::vector<float> &evalv);
     std::vector<int> morton_order() const;
     void build_patch_tiles(const std::vector<int> &ecol, const std::vector<float> &evalv);
     // element forces and residual per mesh patch (ClothView::rp_*)
@@ -527,6 +530,7 @@ struct pdc_ctx {
     DevBuf<float4> Xacc;  // previous iterate for the accelerated update
     DevBuf<float4> disp;  // x^+ - x^- per collision vertex
     DevBuf<float4> CD0;  // third Chebyshev iterate (delta_{k-1})
+    DevBuf<float4> CD1;  // fourth, for two steps a launch
     DevBuf<float4> corner;  // per-element corner forces of the residual [3m + 4nh]
     DevBuf<float4> aa_dF, aa_dG, aa_f, aa_g;  // Anderson history
     DevBuf<double> aa_Gb;
@@ -586,6 +590,9 @@ struct pdc_ctx {
         c.ell_tile = ell_tile.p;
         c.ell_tw = ell_tw;
         c.ell_halo = ell_halo.p;
+        c.ell_halo2 = ell_halo2.p;
+        c.h2_rows = h2_rows;
+        c.h2_verts = h2_verts;
         const bool rp = P.residual_patch != 0 && rp_rec.p;
         c.rp_rec = rp ? rp_rec.p : nullptr;
         c.rp_off = rp ? rp_off.p : nullptr;
@@ -595,8 +602,10 @@ struct pdc_ctx {
         c.corner = corner;
         c.res_block = tune.residual_block;
         {
-            const int want = P.cheb_source >= 0 ? P.cheb_source : tune.cheb_tile;
-            c.cheb_mode = want == 2 && !ell_halo.p ? 1 : want;
+            int want = P.cheb_source >= 0 ? P.cheb_source : tune.cheb_tile;
+            if (want == 3 && !ell_halo2.p) want = 2;
+            if (want == 2 && !ell_halo.p) want = 1;
+            c.cheb_mode = want;
         }
         c.live = live_ptr;
         return c;
@@ -717,7 +726,7 @@ struct pdc_ctx {
     DevBuf<LoopCtl> ctl;
     LoopCtl hctl;
     bool device_decides = false;  // the loop being enqueued takes its tests on the device
-    pdc_tuning tune = {0, 256, 2, 152 * 8, 4, {0, 0, 0}, {0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0}, 1.f, {0, 0, 0}};
+    pdc_tuning tune = {0, 256, 2, 152 * 8, 4, {0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0}, 1.f, {0, 0, 0}};
     void autotune_vertex_kernels();
     bool device_loops_ok() const;
     void free_graph(GraphLoop &G);
@@ -1012,9 +1021,11 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
             }
             ell_tile.upload(tiles, s);
             build_patch_tiles(ecol, evalv);
+            build_patch_tiles2(ecol, evalv);
         } else {
             ell_tile.release();
             ell_halo.release();
+            ell_halo2.release();
         }
     }
     ell_val.upload(evalv, s);
@@ -1033,6 +1044,7 @@ void pdc_ctx::setup(const pdc_mesh_desc *mesh) {
     Ulast.zero(s);
     if (P.sweep_kind == 1) {
         CD0.alloc(n);
+        CD1.alloc(n);
 
     }
     if (P.accel == 2) {
@@ -1425,6 +1437,74 @@ void pdc_ctx::build_residual_patches(const std::vector<int> &vto, const std::vec
     rp_off.upload(off, s);
 }
 
+// Records for the two-step Chebyshev kernel: per mesh patch, its rows are the
+// patch's own vertices and their ELL neighbours (first ring), its vertices
+// those rows and their neighbours (second ring); columns local to the
+// vertices, entries in the order of the ELL arrays.  Not built when a patch
+// exceeds 512 rows or 1024 vertices.
+void pdc_ctx::build_patch_tiles2(const std::vector<int> &ecol, const std::vector<float> &evalv) {
+    ell_halo2.release();
+    h2_rows = h2_verts = 0;
+    if (n == 0 || ell_w == 0) return;
+    const std::vector<int> order = morton_order();
+    const int R = ELL_TILE_ROWS, tw = ell_tw;
+    const size_t nb = ((size_t)n + R - 1) / R;
+    std::vector<int> loc(n, -1);
+    std::vector<std::vector<int>> verts(nb);
+    std::vector<int> nown(nb), nrows(nb);
+    for (size_t b = 0; b < nb; ++b) {
+        std::vector<int> &V = verts[b];
+        V.assign(order.begin() + b * R, order.begin() + std::min((size_t)n, (b + 1) * R));
+        std::sort(V.begin(), V.end());
+        nown[b] = (int)V.size();
+        for (int k = 0; k < (int)V.size(); ++k) loc[V[k]] = k;
+        auto ring = [&](int from, int to) {  // neighbours of V[from, to) not yet listed
+            for (int r = from; r < to; ++r)
+                for (int k = 0; k < ell_w; ++k) {
+                    const int col = ecol[(size_t)k * n + V[r]];
+                    if (loc[col] < 0) {
+                        loc[col] = (int)V.size();
+                        V.push_back(col);
+                    }
+                }
+        };
+        ring(0, nown[b]);
+        nrows[b] = (int)V.size();
+        ring(nown[b], nrows[b]);
+        for (int v : V) loc[v] = -1;
+        h2_rows = std::max(h2_rows, nrows[b]);
+        h2_verts = std::max(h2_verts, (int)V.size());
+    }
+    h2_rows = (h2_rows + 31) & ~31;
+    h2_verts = (h2_verts + 31) & ~31;
+    if (h2_rows > 512 || h2_verts > 1024) {
+        h2_rows = h2_verts = 0;
+        return;
+    }
+    const size_t rb = halo2_tile_bytes(tw, h2_rows, h2_verts);
+    std::vector<unsigned char> rec(nb * rb, 0);
+    for (size_t b = 0; b < nb; ++b) {
+        const std::vector<int> &V = verts[b];
+        for (int k = 0; k < (int)V.size(); ++k) loc[V[k]] = k;
+        unsigned char *p = rec.data() + b * rb;
+        int *hd = reinterpret_cast<int *>(p);
+        hd[0] = nown[b];
+        hd[1] = nrows[b];
+        hd[2] = (int)V.size();
+        float *tv = reinterpret_cast<float *>(p + 16);
+        short *tc = reinterpret_cast<short *>(p + 16 + (size_t)tw * h2_rows * 4);
+        int *gid = reinterpret_cast<int *>(p + 16 + (size_t)tw * h2_rows * 6);
+        for (int r = 0; r < nrows[b]; ++r)
+            for (int k = 0; k < ell_w; ++k) {
+                tv[k * h2_rows + r] = evalv[(size_t)k * n + V[r]];
+                tc[k * h2_rows + r] = (short)loc[ecol[(size_t)k * n + V[r]]];
+            }
+        for (int k = 0; k < h2_verts; ++k) gid[k] = k < (int)V.size() ? V[k] : -1;
+        for (int v : V) loc[v] = -1;
+    }
+    ell_halo2.upload(rec, s);
+}
+
 void pdc_ctx::build_patch_tiles(const std::vector<int> &ecol, const std::vector<float> &evalv) {
     ell_halo.release();
     if (n == 0 || ell_w == 0) return;
@@ -1501,16 +1581,21 @@ void pdc_ctx::autotune_vertex_kernels() {
         PDC_CK(cudaMemsetAsync(D0.p, 0, sizeof(float4) * n, s));
         double b = std::max(gersh, 1.0) * 1.02, a = b / std::max(P.cheb_ratio, 1.0001);
         const float beta = (float)(2.0 / (b + a));
-        const int modes[3] = {1, 0, 2};  // row tiles, ELL arrays, patch tiles
-        const int nm = ell_halo.p ? 3 : 2;
+        const int modes[4] = {1, 0, 2, 3};  // row tiles, ELL arrays, patch tiles, two-step patch tiles
+        const int nm = ell_halo2.p ? 4 : ell_halo.p ? 3 : 2;
         for (int k = 0; k < nm; ++k) {
             tune.cheb_tile = modes[k];
             ClothView c = cloth();
             // eight steps back to back, launched as in the LG iteration
             tune.cheb_ms[k] = timed([&] {
-                for (int rep = 0; rep < 8; ++rep)
-                    launch_cheb_step(s, c, nullptr, R, D0, CD0, D1, 0.f, beta, nullptr, nullptr, nullptr, nullptr,
-                                     1.f, Xs, nullptr, P.launch_overlap != 0, sflag.p);
+                if (modes[k] == 3)
+                    for (int rep = 0; rep < 4; ++rep)
+                        launch_cheb_step2(s, c, nullptr, R, D0, CD0, D1, CD1, 0.f, beta, 0.f, beta, nullptr, nullptr,
+                                          nullptr, nullptr, 1.f, Xs, nullptr, P.launch_overlap != 0, sflag.p);
+                else
+                    for (int rep = 0; rep < 8; ++rep)
+                        launch_cheb_step(s, c, nullptr, R, D0, CD0, D1, 0.f, beta, nullptr, nullptr, nullptr, nullptr,
+                                         1.f, Xs, nullptr, P.launch_overlap != 0, sflag.p);
             }) / 8.f;
         }
         int best = 0;  // the fastest, once all are timed
@@ -1606,16 +1691,7 @@ void pdc_ctx::enqueue_solve(bool contacts, bool springs, bool device, float w_ac
             double rho_prev = 1.0 / sig;
             // delta_{k-1}: the one of the three buffers that is neither din nor dout
             float4 *dp = (CD0.p != din && CD0.p != dout) ? CD0.p : (D0.p != din && D0.p != dout) ? D0.p : D1.p;
-            // the steps run back to back (each a programmatic dependent of the
-            // one before) and are timed as one run between two events
-            if (prof.on && sweeps > 0)
-                prof.begin(s, "cheb_sweep",
-                           (sweeps - 1) * bytes_sweep(contacts, false) + bytes_sweep(contacts, cyc == cycles - 1) +
-                               12.0 * n * sweeps,
-                           sweeps);
-            for (int k = 0; k < sweeps; ++k) {
-                bool last = (cyc == cycles - 1) && (k == sweeps - 1);
-                double alpha, beta;
+            auto coef = [&](int k, double &alpha, double &beta) {  // in step order
                 if (k == 0) {
                     alpha = 0.0;
                     beta = 1.0 / theta;
@@ -1625,6 +1701,41 @@ void pdc_ctx::enqueue_solve(bool contacts, bool springs, bool device, float w_ac
                     beta = 2.0 * rk / dl;
                     rho_prev = rk;
                 }
+            };
+            // the steps run back to back (each a programmatic dependent of the
+            // one before) and are timed as one run between two events
+            if (prof.on && sweeps > 0)
+                prof.begin(s, "cheb_sweep",
+                           (sweeps - 1) * bytes_sweep(contacts, false) + bytes_sweep(contacts, cyc == cycles - 1) +
+                               12.0 * n * sweeps,
+                           sweeps);
+            int k0 = 0;
+            if (cheb_two_steps(c) && sweeps >= 2) {
+                // pairs of steps: delta_k, delta_{k-1} in, delta_{k+1}, delta_{k+2}
+                // out (a fourth buffer, since other blocks still read the
+                // inputs while the outputs are written)
+                float4 *q = nullptr;  // the buffer that is none of din, dp, dout
+                for (float4 *cand : {D0.p, D1.p, CD0.p, CD1.p})
+                    if (cand != din && cand != dp && cand != dout) q = cand;
+                for (; k0 + 1 < sweeps; k0 += 2) {
+                    const bool last = (cyc == cycles - 1) && (k0 + 1 == sweeps - 1);
+                    double a1, b1, a2, b2;
+                    coef(k0, a1, b1);
+                    coef(k0 + 1, a2, b2);
+                    launch_cheb_step2(s, c, cw, R, din, dp, dout, q, (float)a1, (float)b1, (float)a2, (float)b2, Ucur,
+                                      last ? Ucur.p : nullptr, last ? sc.p : nullptr, last ? xprev : nullptr, w_acc,
+                                      Xs, last ? Xp.p : nullptr, P.launch_overlap != 0, sflag.p);
+                    float4 *a = din, *b = dp;  // delta_{k+2}, delta_{k+1} become the inputs
+                    din = q;
+                    dp = dout;
+                    dout = a;
+                    q = b;
+                }
+            }
+            for (int k = k0; k < sweeps; ++k) {
+                bool last = (cyc == cycles - 1) && (k == sweeps - 1);
+                double alpha, beta;
+                coef(k, alpha, beta);
                 launch_cheb_step(s, c, cw, R, din, dp, dout, (float)alpha, (float)beta, Ucur, last ? Ucur.p : nullptr,
                                  last ? sc.p : nullptr, last ? xprev : nullptr, w_acc, Xs, last ? Xp.p : nullptr,
                                  P.launch_overlap != 0, sflag.p);
@@ -2450,7 +2561,7 @@ static bool params_valid(const pdc_params *params) {
            params->sweep_kind >= 0 && params->sweep_kind <= 1 && (params->sweep_kind != 1 || params->cheb_ratio > 1.0) &&
            params->accel >= 0 && params->accel <= 2 && (params->accel != 2 || (params->aa_depth >= 1 && params->aa_depth <= 8)) &&
            params->loop_control >= 0 && params->loop_control <= 3 && params->loop_ahead >= 0 &&
-           params->loop_ahead <= 2 && params->cheb_source >= -1 && params->cheb_source <= 2 &&
+           params->loop_ahead <= 2 && params->cheb_source >= -1 && params->cheb_source <= 3 &&
            (params->residual_patch == 0 || params->residual_patch == 1) &&
            (params->pccd_adaptive == 0 || (params->pccd_adaptive == 1 && params->pccd_max_axis >= 1 &&
                                            params->pccd_max_axis <= 256 && params->alpha_ls > 0 && params->alpha_ls < 1));

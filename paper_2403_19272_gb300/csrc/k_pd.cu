@@ -258,6 +258,144 @@ __global__ void __launch_bounds__(256) k_residual(const ClothView c, const float
     if (sc) block_add(sq, &sc->rsq);
 }
 
+// Two Chebyshev steps in one launch over two-step patch tiles
+// (ClothView::ell_halo2).  A block takes one patch; its rows are the patch's
+// own vertices and their neighbours (the first ring), its vertices those rows
+// and their neighbours.  After staging delta_k of all its vertices it forms
+// delta_{k+1} of all its rows (the first-ring rows as their own patches form
+// them), then delta_{k+2} of its own rows from those, and writes both for its
+// own rows: the next launch reads delta_{k+2} and delta_{k+1}.  Each step is
+// k_cheb_step's arithmetic in the same order, so the results are bitwise
+// those of two single steps.
+template <int W>
+__global__ void __launch_bounds__(256) k_cheb_step2_halo(
+    const ClothView c, const float *__restrict__ cw, const float4 *__restrict__ r, const float4 *__restrict__ din,
+    const float4 *__restrict__ dprev, float4 *__restrict__ dmid, float4 *__restrict__ dout, float a1, float b1,
+    float a2, float b2, const float4 *x, float4 *xout, float4 *xprev, float w_acc, const float4 *__restrict__ xs,
+    float4 *__restrict__ xabs, Scalars *sc, int *err) {
+    extern __shared__ __align__(128) unsigned char h2sm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_dead;
+    const int RW = c.h2_rows, VW = c.h2_verts;
+    const uint32_t BYTES = (uint32_t)halo2_tile_bytes(W, RW, VW);
+    unsigned char *tile = h2sm;
+    float *dk = reinterpret_cast<float *>(h2sm + BYTES);  // [3 * VW] delta_k of the vertices
+    float *d1 = dk + 3 * VW;                              // [3 * RW] delta_{k+1} of the rows
+    const int t = threadIdx.x;
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        s_dead = loop_dead(c.live) ? 1 : 0;  // final once read as 0 (see k_cheb_step_tile)
+    }
+    __syncthreads();
+    const bool dead_early = s_dead != 0;
+    if (t == 0 && !dead_early) {
+        mbar_expect_tx(&bar, BYTES);
+        bulk_load(tile, c.ell_halo2 + (size_t)blockIdx.x * BYTES, BYTES, &bar);
+    }
+    grid_dep_wait();
+    grid_dep_release();
+    if (dead_early) return;  // no copy in flight
+    const bool alive = !loop_dead(c.live);
+    if (!__syncthreads_and(mbar_wait(&bar, 0))) {  // block-uniform
+        if (t == 0) {
+            atomicOr(err, PDC_DEVERR_COPY);
+            mbar_wait(&bar, 0);  // let the copy land before the block's shared memory is released
+        }
+        return;
+    }
+    const int *hd = reinterpret_cast<const int *>(tile);
+    const int nown = min(hd[0], ELL_TILE_ROWS), nrows = min(hd[1], RW), nverts = min(hd[2], VW);
+    const float *sv = reinterpret_cast<const float *>(tile + 16);
+    const short *sd = reinterpret_cast<const short *>(tile + 16 + (size_t)W * RW * 4);
+    const int *gid = reinterpret_cast<const int *>(tile + 16 + (size_t)W * RW * 6);
+    for (int j = t; j < nverts; j += blockDim.x) {
+        const int g = gid[j];
+        const float4 v = (alive && g >= 0 && g < c.n) ? din[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+        dk[3 * j] = v.x;
+        dk[3 * j + 1] = v.y;
+        dk[3 * j + 2] = v.z;
+    }
+    // the block's rows t and t + 256: right-hand side, delta_{k-1}, diagonal
+    float3 rr[2], pp[2];
+    float DD[2];
+    bool fr[2];
+    int gi[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int j = t + q * ELL_TILE_ROWS;
+        gi[q] = j < nrows ? gid[j] : -1;
+        fr[q] = alive && gi[q] >= 0 && gi[q] < c.n && c.is_free[gi[q]];
+        rr[q] = pp[q] = make_float3(0.f, 0.f, 0.f);
+        DD[q] = 1.f;
+        if (fr[q]) {
+            rr[q] = f3(r[gi[q]]);
+            if (a1 != 0.f) pp[q] = f3(dprev[gi[q]]);
+            DD[q] = c.hdiag[gi[q]] + (cw ? cw[gi[q]] : 0.f);
+        }
+    }
+    __syncthreads();
+    auto V3 = [](const float *a, int j) { return make_float3(a[3 * j], a[3 * j + 1], a[3 * j + 2]); };
+    // step k -> k + 1 on every row
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int j = t + q * ELL_TILE_ROWS;
+        if (j >= nrows) continue;
+        float3 dn = make_float3(0.f, 0.f, 0.f);
+        if (fr[q]) {
+            const float3 di = V3(dk, j);
+            float3 e = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                if (k < c.ell_w) e = e + sv[k * RW + j] * V3(dk, sd[k * RW + j]);
+            float3 acc = rr[q] - DD[q] * di - e;
+            float3 dd = (b1 / DD[q]) * acc;
+            if (a1 != 0.f) dd = dd + a1 * (di - pp[q]);
+            dn = di + dd;
+        }
+        d1[3 * j] = dn.x;
+        d1[3 * j + 1] = dn.y;
+        d1[3 * j + 2] = dn.z;
+    }
+    __syncthreads();
+    // step k + 1 -> k + 2 on the own rows (row t, t < nown; their columns are rows)
+    float mx = 0.f;
+    if (alive && t < nown && gi[0] >= 0 && gi[0] < c.n) {
+        const int i = gi[0];
+        const float3 dm = V3(d1, t);
+        float3 dn = make_float3(0.f, 0.f, 0.f);
+        if (fr[0]) {
+            const float3 di = dm, pi = V3(dk, t);
+            float3 e = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                if (k < c.ell_w) e = e + sv[k * RW + t] * V3(d1, sd[k * RW + t]);
+            float3 acc = rr[0] - DD[0] * di - e;
+            float3 dd = (b2 / DD[0]) * acc;
+            if (a2 != 0.f) dd = dd + a2 * (di - pi);
+            dn = di + dd;
+        }
+        dmid[i] = f4(dm);
+        dout[i] = f4(dn);
+        if (xout) {
+            float3 xo = f3(x[i]);
+            float3 xn = xo + dn;
+            if (xprev) {
+                if (fr[0] && w_acc != 1.f) {
+                    float3 xpv = f3(xprev[i]);
+                    xn = xpv + w_acc * (xn - xpv);
+                }
+                xprev[i] = f4(xo);
+            }
+            xout[i] = f4(xn);
+            if (xabs) xabs[i] = f4(f3(xs[i]) + xn);
+            float3 d = xn - xo;
+            mx = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z)));
+        }
+    }
+    if (xout && sc) block_max(mx, &sc->dxmax);
+}
+
 // The same residual in one kernel per mesh patch (ClothView::rp_rec): a
 // block stages x* and u of the vertices its patch touches in shared memory,
 // computes the projections of the triangles and hinges at its rows once into
@@ -1101,6 +1239,36 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
         else PDC_CHEB(0);
 #undef PDC_CHEB
     }
+    PDC_LAUNCH_CK();
+}
+
+bool cheb_two_steps(const ClothView &c) { return c.n > 0 && c.ell_halo2 && c.cheb_mode == 3; }
+
+void launch_cheb_step2(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
+                       const float4 *dprev, float4 *dmid, float4 *dout, float a1, float b1, float a2, float b2,
+                       const float4 *x, float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs,
+                       float4 *xabs, bool overlap, int *err) {
+    if (!cheb_two_steps(c) || !err) throw Error(PDC_ERR_STATE, "two-step Chebyshev tiles not built");
+    const size_t smem = halo2_tile_bytes(c.ell_tw, c.h2_rows, c.h2_verts) + 12 * (size_t)(c.h2_rows + c.h2_verts);
+    static unsigned long long attr[3] = {0, 0, 0};  // per-device bits: the shared-memory limit raised
+    int ci = c.ell_tw == 8 ? 0 : c.ell_tw == 12 ? 1 : 2, dev = 0;
+    PDC_CK(cudaGetDevice(&dev));
+    if (!(attr[ci] >> (dev & 63) & 1ull)) {
+        const int lim = 160 * 1024;
+        cudaError_t e = ci == 0 ? cudaFuncSetAttribute(k_cheb_step2_halo<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+                      : ci == 1 ? cudaFuncSetAttribute(k_cheb_step2_halo<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+                                : cudaFuncSetAttribute(k_cheb_step2_halo<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        PDC_CK(e);
+        attr[ci] |= 1ull << (dev & 63);
+    }
+    const int b = nblk(c.n, ELL_TILE_ROWS);
+#define PDC_CHEB2(W)                                                                                          \
+    launch_dependent(overlap, k_cheb_step2_halo<W>, b, 256, smem, s, c, cw, r, din, dprev, dmid, dout, a1, b1, a2, b2, \
+                     x, xout, xprev, w_acc, xs, xabs, sc, err)
+    if (c.ell_tw == 8) PDC_CHEB2(8);
+    else if (c.ell_tw == 12) PDC_CHEB2(12);
+    else PDC_CHEB2(16);
+#undef PDC_CHEB2
     PDC_LAUNCH_CK();
 }
 

@@ -149,6 +149,10 @@ struct ClothView {
     // local to the patch and its halo (see halo_tile_bytes; NULL when some
     // patch's halo exceeds HALO_MAX or the tiles above are absent)
     const unsigned char *ell_halo;
+    // two-step patch tiles (see k_cheb_step2_halo): rows = the patch and its
+    // first halo ring, columns local to rows + second ring; fixed stride
+    const unsigned char *ell_halo2;
+    int h2_rows, h2_verts;  // largest row and vertex counts over the patches (multiples of 32)
     float4 *corner;        // scratch [3m + 4nh]: per-element corner forces of the residual
     // one-kernel residual per mesh patch (NULL when not built or not used):
     // records and their byte offsets, the largest counts over the patches
@@ -156,7 +160,8 @@ struct ClothView {
     const long long *rp_off;
     int rp_loc, rp_tri, rp_hin;
     int res_block;         // threads per block of the residual kernels (64, 128 or 256)
-    int cheb_mode;         // Chebyshev step reads: 0 the ELL arrays, 1 the row tiles, 2 the patch tiles
+    int cheb_mode;         // Chebyshev step reads: 0 the ELL arrays, 1 the row tiles, 2 the patch tiles,
+                           // 3 the two-step patch tiles (two steps a launch)
     const int *live;       // device loop flag: the kernels do nothing when *live == 0 (NULL: always run)
 };
 
@@ -171,6 +176,13 @@ inline size_t ell_tile_bytes(int tw) { return (size_t)tw * ELL_TILE_ROWS * 6; }
 // [ELL_TILE_ROWS] int32 vertex ids of the rows (-1 past the last), [HALO_MAX]
 // int32 vertex ids of the halo, int32 halo count, 12 bytes of padding.
 constexpr int HALO_MAX = 512;
+// Two-step patch tile, per patch: int4 {n_own, n_rows, n_verts, 0};
+// [tw][rows] float values, [tw][rows] int16 columns local to the vertices,
+// [verts] int32 vertex ids (rows first, own rows first among them; -1 past
+// the counts); rows and verts are the largest counts over the patches.
+__host__ __device__ constexpr size_t halo2_tile_bytes(int tw, int rows, int verts) {
+    return 16 + (size_t)tw * rows * 6 + (size_t)verts * 4;
+}
 __host__ __device__ constexpr size_t halo_tile_bytes(int tw) {
     return (size_t)tw * ELL_TILE_ROWS * 6 + (size_t)ELL_TILE_ROWS * 4 + (size_t)HALO_MAX * 4 + 16;
 }
@@ -250,6 +262,15 @@ void launch_cheb_step(cudaStream_t s, const ClothView &c, const float *cw, const
                       const float4 *dprev, float4 *dout, float alpha, float beta, const float4 *x,
                       float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs, float4 *xabs,
                       bool overlap = false, int *err = nullptr);
+// Two Chebyshev steps in one launch over the two-step patch tiles
+// (cheb_mode 3): dmid = the first step's result, dout = the second's
+// (coefficients a1, b1 then a2, b2); the iterate outputs as the second step
+// of launch_cheb_step.  cheb_two_steps: whether the view selects it.
+bool cheb_two_steps(const ClothView &c);
+void launch_cheb_step2(cudaStream_t s, const ClothView &c, const float *cw, const float4 *r, const float4 *din,
+                       const float4 *dprev, float4 *dmid, float4 *dout, float a1, float b1, float a2, float b2,
+                       const float4 *x, float4 *xout, Scalars *sc, float4 *xprev, float w_acc, const float4 *xs,
+                       float4 *xabs, bool overlap, int *err);
 // Anderson mixing step on the iterate u (= u_k + delta_k on entry, u_{k+1} on exit).
 // Gb must have been zeroed (aa_clear) after the previous mixing step.
 void launch_aa(cudaStream_t s, int n, const unsigned char *is_free, const float4 *delta, float4 *x, float4 *fprev,

@@ -61,7 +61,7 @@ class pdc_stats(ctypes.Structure):
 
 class pdc_tuning(ctypes.Structure):
     _fields_ = [("tuned", c_i32), ("residual_block", c_i32), ("cheb_tile", c_i32), ("pair_blocks", c_i32),
-                ("cell_warps", c_i32), ("residual_ms", c_flt * 3), ("cheb_ms", c_flt * 3), ("pair_ms", c_flt * 4),
+                ("cell_warps", c_i32), ("residual_ms", c_flt * 3), ("cheb_ms", c_flt * 4), ("pair_ms", c_flt * 4),
                 ("cell_ms", c_flt * 3), ("cell_grid", c_flt), ("grid_ms", c_flt * 3)]
 
     def as_dict(self):
