@@ -158,20 +158,42 @@ __device__ inline bool ccd_may_hit(int kind, const float4 a0[4], const float4 a1
         // displacements), so on [t_a, t_b] it stays above
         // (d(t_a) + d(t_b) - L (t_b - t_a)) / 2.  No impact if that bound
         // clears eta (with the FP32 margin) on all of [0, 1]: first from d0
-        // alone, then on eight sub-intervals.
+        // alone, then on [0, 1] and, where it does not, on its halves,
+        // quarters and eighths (distances at t = k / 8, evaluated as needed).
         const float L = 1.001f * maxrel, mg = (float)eta + 4e-6f * cmax;
         if (d0 > L + mg) return false;
-        bool clear = true;
-        float dprev = d0;
-        for (int k = 1; k <= 8 && clear; ++k) {
-            const float t = 0.125f * (float)k;
-            V<float> qt[4];
-            for (int i = 0; i < 4; ++i) qt[i] = q[i] + t * dv[i];
-            const float dk = gap_dist<float>(kind, qt);
-            if (0.5f * (dprev + dk - 0.125f * L) <= mg) clear = false;
-            dprev = dk;
+        float d[9];
+        unsigned have = 1u | (1u << 8);
+        d[0] = d0;
+        auto at = [&](int k) {
+            if (!(have >> k & 1u)) {
+                const float t = 0.125f * (float)k;
+                V<float> qt[4];
+                for (int i = 0; i < 4; ++i) qt[i] = q[i] + t * dv[i];
+                d[k] = gap_dist<float>(kind, qt);
+                have |= 1u << k;
+            }
+            return d[k];
+        };
+        {
+            V<float> q1[4];
+            for (int i = 0; i < 4; ++i) q1[i] = q[i] + dv[i];
+            d[8] = gap_dist<float>(kind, q1);
         }
-        return !clear;
+        unsigned open = 1u;  // intervals of the current level not yet cleared
+        for (int level = 0; level <= 3; ++level) {
+            const int w = 8 >> level;  // interval width in eighths
+            unsigned next = 0u;
+            for (int i = 0; i < (1 << level); ++i) {
+                if (!(open >> i & 1u)) continue;
+                const int a = i * w, b = a + w;
+                if (0.5f * (at(a) + at(b) - 0.125f * (float)w * L) > mg) continue;
+                next |= 3u << (2 * i);  // both halves go on to the next level
+            }
+            if (!next) return false;
+            open = next;
+        }
+        return true;
     }
 }
 
