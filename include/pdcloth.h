@@ -261,7 +261,7 @@ typedef struct {
                                 ELL arrays (candidates 1, 0, 2, 3)              */
     int32_t pair_blocks;     /* blocks of the per-pair kernels (152 x 2, 4, 8, 16) */
     int32_t cell_warps;      /* warps per block of the broad phase's cell-pair
-                                kernel (candidates 2, 4, 8)                     */
+                                kernel (candidates 4, 8, 16)                     */
     float residual_ms[3];
     float cheb_ms[4];
     float pair_ms[4];

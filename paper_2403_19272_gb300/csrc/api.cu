@@ -726,7 +726,7 @@ struct pdc_ctx {
     DevBuf<LoopCtl> ctl;
     LoopCtl hctl;
     bool device_decides = false;  // the loop being enqueued takes its tests on the device
-    pdc_tuning tune = {0, 256, 2, 152 * 8, 4, {0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0}, 1.f, {0, 0, 0}};
+    pdc_tuning tune = {0, 256, 2, 152 * 8, 8, {0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0}, 1.f, {0, 0, 0}};
     void autotune_vertex_kernels();
     bool device_loops_ok() const;
     void free_graph(GraphLoop &G);

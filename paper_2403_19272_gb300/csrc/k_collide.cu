@@ -126,6 +126,20 @@ __global__ void k_grid_params(GridParams *gp, int nt, float dhat, float scale) {
     }
 }
 
+constexpr int CELL_CHUNK = 64;
+constexpr unsigned FL_FIXED = 1u << 3;       // every vertex of the primitive is an obstacle vertex
+constexpr unsigned Q_GUARD = (1u << 8) | (1u << 17) | (1u << 26);
+constexpr unsigned Q_OWNER = 7u << 27;       // lowest-cell flags in the low corner's word
+constexpr unsigned Q_FIXED = FL_FIXED << 27;
+constexpr int QUEUE = 64;                    // survivor queue per warp
+
+__device__ inline unsigned quant_lo(float v, float c0, float s) {
+    return (unsigned)fminf(fmaxf(floorf(__fmul_rn(__fsub_rn(v, c0), s)), 0.f), 255.f);
+}
+__device__ inline unsigned quant_hi(float v, float c0, float s) {
+    return (unsigned)fminf(fmaxf(ceilf(__fmul_rn(__fsub_rn(v, c0), s)), 0.f), 255.f);
+}
+
 // ------------------------------------------------------------------ cell table
 // Table primitives: collision vertices [0, nv), edges [nv, nv + ne),
 // triangles [nv + ne, nv + ne + nt).  Primitive p covers the cells of its
@@ -177,8 +191,8 @@ __global__ void k_cell_insert(CollView cv, const float4 *__restrict__ x0, const 
                               const float4 *__restrict__ elo, const float4 *__restrict__ ehi, const GridParams *gp,
                               float dhat, unsigned int mask, int *__restrict__ bcnt, const int *__restrict__ bstart,
                               int *__restrict__ bfill, unsigned long long *__restrict__ ekey,
-                              unsigned int *__restrict__ epay, int mode, const long long *total, long long cap,
-                              int *overflow) {
+                              unsigned int *__restrict__ epay, unsigned long long *__restrict__ equ, int mode,
+                              const long long *total, long long cap, int *overflow) {
     const int np = cv.nv + cv.ne + cv.nt;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned lane = threadIdx.x & 31;
@@ -186,8 +200,8 @@ __global__ void k_cell_insert(CollView cv, const float4 *__restrict__ x0, const 
     const float3 inv = make_float3(gp->inv_cell[0], gp->inv_cell[1], gp->inv_cell[2]);
     int kind = 0, prim = 0, ncell = 0;
     int3 lo = make_int3(0, 0, 0), hi = make_int3(-1, -1, -1);
+    float3 l = make_float3(0.f, 0.f, 0.f), h = l;
     if (p < np) {
-        float3 l, h;
         table_box(cv, x0, x1, tlo, thi, elo, ehi, p, kind, prim, l, h);
         lo = cellv(l, inv);
         hi = cellv(raise_d(h, dhat), inv);
@@ -200,6 +214,21 @@ __global__ void k_cell_insert(CollView cv, const float4 *__restrict__ x0, const 
     }
     const int sx = hi.x - lo.x + 1, sy = hi.y - lo.y + 1;
     const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)ncell);
+    // fill pass: the raised box, the kinematic flag and the quantization scale
+    unsigned fixed = 0;
+    float3 hr = h, qs = make_float3(0.f, 0.f, 0.f);
+    if (mode == 1 && ncell > 0) {
+        hr = raise_d(h, dhat);
+        qs = make_float3(256.f / gp->cell[0], 256.f / gp->cell[1], 256.f / gp->cell[2]);
+        if (kind == KIND_V) fixed = prim >= cv.nc;
+        else if (kind == KIND_E) {
+            const int2 E = cv.edge[prim];
+            fixed = E.x >= cv.nc && E.y >= cv.nc;
+        } else {
+            const int4 Tr = cv.tri[prim];
+            fixed = Tr.x >= cv.nc && Tr.y >= cv.nc && Tr.z >= cv.nc;
+        }
+    }
     for (int r = 0; r < rounds; ++r) {
         const bool act = r < ncell;
         int x = 0, y = 0, z = 0;
@@ -222,8 +251,17 @@ __global__ void k_cell_insert(CollView cv, const float4 *__restrict__ x0, const 
             if ((int)lane == leader) base = atomicAdd(&bfill[b], __popc(peers));
             base = __shfl_sync(peers, base, leader);
             const int pos = bstart[b] + base + __popc(peers & ((1u << lane) - 1u));
+            const unsigned low = (x == lo.x ? 1u : 0u) | (y == lo.y ? 2u : 0u) | (z == lo.z ? 4u : 0u);
             ekey[pos] = k;
-            epay[pos] = pay_pack(prim, kind, (x == lo.x ? 1 : 0) | (y == lo.y ? 2 : 0) | (z == lo.z ? 4 : 0));
+            epay[pos] = pay_pack(prim, kind, (int)low);
+            // the box quantized within this cell (cell origin from its index)
+            const float cx = __fmul_rn((float)x, gp->cell[0]), cy = __fmul_rn((float)y, gp->cell[1]),
+                        cz = __fmul_rn((float)z, gp->cell[2]);
+            const unsigned ql = quant_lo(l.x, cx, qs.x) | (quant_lo(l.y, cy, qs.y) << 9) |
+                                (quant_lo(l.z, cz, qs.z) << 18) | ((low | (fixed ? FL_FIXED : 0u)) << 27);
+            const unsigned qh = quant_hi(hr.x, cx, qs.x) | (quant_hi(hr.y, cy, qs.y) << 9) |
+                                (quant_hi(hr.z, cz, qs.z) << 18) | Q_GUARD;
+            equ[pos] = (unsigned long long)ql | ((unsigned long long)qh << 32);
         }
     }
 }
@@ -249,22 +287,16 @@ __global__ void k_cell_insert(CollView cv, const float4 *__restrict__ x0, const 
 // owner flags (bits 27..29) and FL_FIXED (bit 30).  Pairs that pass this
 // prefilter go through a per-warp queue to the full test, so that the rare
 // survivors do not stall the lanes that keep scanning.
-constexpr int CELL_CHUNK = 64;
-constexpr unsigned FL_FIXED = 1u << 3;       // every vertex of the primitive is an obstacle vertex
-constexpr unsigned Q_GUARD = (1u << 8) | (1u << 17) | (1u << 26);
-constexpr unsigned Q_OWNER = 7u << 27;       // lowest-cell flags in the low corner's word
-constexpr unsigned Q_FIXED = FL_FIXED << 27;
-constexpr int QUEUE = 64;                    // survivor queue per warp
-
 // One chunk of a bucket in shared memory, in kind order: vertices [0, nv),
-// edges [nv, nv + ne), triangles [nv + ne, nv + ne + nt).
+// edges [nv, nv + ne), triangles [nv + ne, nv + ne + nt): cell key,
+// quantized box words (as the insert pass wrote them) and primitive id.  The
+// exact boxes and vertex ids of a pair are read from device memory only for
+// the pairs that pass the prefilter.
 struct CellRegion {
-    float4 lo[CELL_CHUNK];   // w: primitive id
-    float4 hi[CELL_CHUNK];
-    int4 ids[CELL_CHUNK];    // vertex ids (-1 past the primitive's own)
     unsigned long long key[CELL_CHUNK];
     unsigned int qlo[CELL_CHUNK];  // quantized low corner | (lowest-cell flags | FL_FIXED) << 27
     unsigned int qhi[CELL_CHUNK];  // quantized raised high corner | Q_GUARD
+    int pid[CELL_CHUNK];
 };
 
 // per warp: two chunk regions and the survivor queue
@@ -273,24 +305,15 @@ struct CellWarp {
     unsigned int queue[QUEUE];
 };
 
-__device__ inline unsigned quant_lo(float v, float c0, float s) {
-    return (unsigned)fminf(fmaxf(floorf(__fmul_rn(__fsub_rn(v, c0), s)), 0.f), 255.f);
-}
-__device__ inline unsigned quant_hi(float v, float c0, float s) {
-    return (unsigned)fminf(fmaxf(ceilf(__fmul_rn(__fsub_rn(v, c0), s)), 0.f), 255.f);
-}
-
 struct KindCounts {
     int v, e, t;
 };
 
 // Loads entries [e0, e0 + cnt) of the table into R in kind order (a count
-// pass over the payloads, then the write pass).
-__device__ __forceinline__ KindCounts load_chunk(CellRegion &R, const CollView &cv, const float4 *x0, const float4 *x1,
-                                        const float4 *tlo, const float4 *thi, const float4 *elo, const float4 *ehi,
-                                        const unsigned long long *ekey, const unsigned int *epay, int e0, int cnt,
-                                        float3 cell, float dhat, unsigned lane) {
-    const float3 qs = make_float3(256.f / cell.x, 256.f / cell.y, 256.f / cell.z);
+// pass over the payloads, then the write pass); coalesced, no gathers.
+__device__ __forceinline__ KindCounts load_chunk(CellRegion &R, const unsigned long long *ekey,
+                                                 const unsigned int *epay, const unsigned long long *equ, int e0,
+                                                 int cnt, unsigned lane) {
     const unsigned below = (1u << lane) - 1u;
     KindCounts kc = {0, 0, 0};
     for (int base = 0; base < cnt; base += 32) {  // warp-uniform
@@ -315,41 +338,11 @@ __device__ __forceinline__ KindCounts load_chunk(CellRegion &R, const CollView &
         if (kind >= 0) {
             const int d = kind == KIND_V ? cv_ + __popc(mv & below)
                                          : (kind == KIND_E ? ce + __popc(me & below) : ct + __popc(mt & below));
-            const int prim = (int)(pay & PAY_PRIM);
-            unsigned fl = pay >> 29;
-            float3 lo, hi;
-            int4 ids;
-            if (kind == KIND_V) {
-                vbox(x0, x1, prim, lo, hi);
-                ids = make_int4(prim, -1, -1, -1);
-                if (prim >= cv.nc) fl |= FL_FIXED;
-            } else if (kind == KIND_E) {
-                lo = f3(elo[prim]);
-                hi = f3(ehi[prim]);
-                const int2 E = cv.edge[prim];
-                ids = make_int4(E.x, E.y, -1, -1);
-                if (E.x >= cv.nc && E.y >= cv.nc) fl |= FL_FIXED;
-            } else {
-                lo = f3(tlo[prim]);
-                hi = f3(thi[prim]);
-                const int4 Tr = cv.tri[prim];
-                ids = make_int4(Tr.x, Tr.y, Tr.z, -1);
-                if (Tr.x >= cv.nc && Tr.y >= cv.nc && Tr.z >= cv.nc) fl |= FL_FIXED;
-            }
-            const unsigned long long key = ekey[e0 + i];
-            R.lo[d] = make_float4(lo.x, lo.y, lo.z, __int_as_float(prim));
-            R.hi[d] = make_float4(hi.x, hi.y, hi.z, 0.f);
-            R.ids[d] = ids;
-            R.key[d] = key;
-            // cell origin from the key (the same for every entry of the cell)
-            const float cx = __fmul_rn((float)((int)((key >> 42) & 0x1fffffu) - CELL_BIAS), cell.x);
-            const float cy = __fmul_rn((float)((int)((key >> 21) & 0x1fffffu) - CELL_BIAS), cell.y);
-            const float cz = __fmul_rn((float)((int)(key & 0x1fffffu) - CELL_BIAS), cell.z);
-            const float3 hr = raise_d(hi, dhat);
-            R.qlo[d] = quant_lo(lo.x, cx, qs.x) | (quant_lo(lo.y, cy, qs.y) << 9) | (quant_lo(lo.z, cz, qs.z) << 18) |
-                       (fl << 27);
-            R.qhi[d] = quant_hi(hr.x, cx, qs.x) | (quant_hi(hr.y, cy, qs.y) << 9) | (quant_hi(hr.z, cz, qs.z) << 18) |
-                       Q_GUARD;
+            const unsigned long long q = equ[e0 + i];
+            R.key[d] = ekey[e0 + i];
+            R.qlo[d] = (unsigned)q;
+            R.qhi[d] = (unsigned)(q >> 32);
+            R.pid[d] = (int)(pay & PAY_PRIM);
         }
         cv_ += __popc(mv);
         ce += __popc(me);
@@ -378,27 +371,34 @@ __device__ __forceinline__ void emit(int *cnt, int *slots, int width, int p, int
     else if (slot == width) atomicOr(overflow, OVF_SLOTS);
 }
 
+// What the full tests read from device memory.
+struct CellData {
+    CollView cv;
+    const float4 *x0, *x1, *tlo, *thi, *elo, *ehi;
+    float dhat;
+};
+
 // (vertex entry i of A, triangle entry j of B) past the prefilter
-__device__ __forceinline__ void full_vt(const CellRegion &A, int i, const CellRegion &B, int j, float dhat,
+__device__ __forceinline__ void full_vt(const CellRegion &A, int i, const CellRegion &B, int j, const CellData &g,
                                         const RowsOut &o) {
     if (A.key[i] != B.key[j]) return;
-    const float4 alo = A.lo[i], blo = B.lo[j];
-    const int v = __float_as_int(alo.w);
-    const int4 T = B.ids[j];
+    const int v = A.pid[i], t = B.pid[j];
+    const int4 T = g.cv.tri[t];
     if (T.x == v || T.y == v || T.z == v) return;
-    if (!box_overlap(f3(alo), f3(A.hi[i]), f3(blo), f3(B.hi[j]), dhat)) return;
-    emit(o.cnt_v, o.slots_vt, o.w_vt, v, __float_as_int(blo.w), o.overflow);
+    float3 lo, hi;
+    vbox(g.x0, g.x1, v, lo, hi);
+    if (!box_overlap(lo, hi, f3(g.tlo[t]), f3(g.thi[t]), g.dhat)) return;
+    emit(o.cnt_v, o.slots_vt, o.w_vt, v, t, o.overflow);
 }
 
 // (edge entry i of A, edge entry j of B) past the prefilter
-__device__ __forceinline__ void full_ee(const CellRegion &A, int i, const CellRegion &B, int j, float dhat,
+__device__ __forceinline__ void full_ee(const CellRegion &A, int i, const CellRegion &B, int j, const CellData &g,
                                         const RowsOut &o) {
     if (A.key[i] != B.key[j]) return;
-    const int4 a = A.ids[i], b = B.ids[j];
+    int e = A.pid[i], f = B.pid[j];
+    const int2 a = g.cv.edge[e], b = g.cv.edge[f];
     if (a.x == b.x || a.x == b.y || a.y == b.x || a.y == b.y) return;
-    const float4 alo = A.lo[i], blo = B.lo[j];
-    if (!box_overlap(f3(alo), f3(A.hi[i]), f3(blo), f3(B.hi[j]), dhat)) return;
-    int e = __float_as_int(alo.w), f = __float_as_int(blo.w);
+    if (!box_overlap(f3(g.elo[e]), f3(g.ehi[e]), f3(g.elo[f]), f3(g.ehi[f]), g.dhat)) return;
     if (e > f) {
         const int t = e;
         e = f;
@@ -410,15 +410,15 @@ __device__ __forceinline__ void full_ee(const CellRegion &A, int i, const CellRe
 // Survivor queue of one warp: code = i | region_i << 6 | j << 7 | region_j << 13 | ee << 14.
 struct PairQueue {
     CellWarp &w;
-    const float dhat;
+    const CellData &g;
     const RowsOut &o;
     const unsigned lane;
     int n = 0;  // warp-uniform
     __device__ __forceinline__ void run(unsigned c) const {
         const int i = (int)(c & 63u), j = (int)((c >> 7) & 63u);
         const CellRegion &A = w.r[(c >> 6) & 1u], &B = w.r[(c >> 13) & 1u];
-        if (c & (1u << 14)) full_ee(A, i, B, j, dhat, o);
-        else full_vt(A, i, B, j, dhat, o);
+        if (c & (1u << 14)) full_ee(A, i, B, j, g, o);
+        else full_vt(A, i, B, j, g, o);
     }
     // every lane calls it (pass: its pair survived the prefilter)
     __device__ __forceinline__ void push(bool pass, unsigned code) {
@@ -497,21 +497,17 @@ __device__ __forceinline__ void pairs_ee_across(PairQueue &q, int ra, KindCounts
 }
 
 template <int W>
-__global__ void __launch_bounds__(W * 32) k_cell_pairs(CollView cv, const float4 *__restrict__ x0,
-                                                       const float4 *__restrict__ x1, const float4 *__restrict__ tlo,
-                                                       const float4 *__restrict__ thi, const float4 *__restrict__ elo,
-                                                       const float4 *__restrict__ ehi, float dhat, int T,
-                                                       const int *__restrict__ bcnt, const int *__restrict__ bstart,
+__global__ void __launch_bounds__(W * 32) k_cell_pairs(CellData g, int T, const int *__restrict__ bcnt,
+                                                       const int *__restrict__ bstart,
                                                        const unsigned long long *__restrict__ ekey,
-                                                       const unsigned int *__restrict__ epay, RowsOut o, int *work,
-                                                       const GridParams *gp, const long long *hash_total,
-                                                       long long cap_ent) {
+                                                       const unsigned int *__restrict__ epay,
+                                                       const unsigned long long *__restrict__ equ, RowsOut o,
+                                                       int *work, const long long *hash_total, long long cap_ent) {
     extern __shared__ __align__(16) unsigned char cell_smem[];  // W CellWarp
     if (*hash_total > cap_ent) return;  // table not filled: no candidates (the pass is redone)
     const unsigned lane = threadIdx.x & 31;
     CellWarp &cw = reinterpret_cast<CellWarp *>(cell_smem)[threadIdx.x >> 5];
-    PairQueue q{cw, dhat, o, lane};
-    const float3 cell = make_float3(gp->cell[0], gp->cell[1], gp->cell[2]);
+    PairQueue q{cw, g, o, lane};
     for (;;) {
         int b0 = 0;
         if (lane == 0) b0 = atomicAdd(work, 32);
@@ -528,15 +524,13 @@ __global__ void __launch_bounds__(W * 32) k_cell_pairs(CollView cv, const float4
             const int eb = __shfl_sync(0xffffffffu, st, l);
             const int nch = (mb + CELL_CHUNK - 1) / CELL_CHUNK;
             for (int ca = 0; ca < nch; ++ca) {
-                const KindCounts a = load_chunk(cw.r[0], cv, x0, x1, tlo, thi, elo, ehi, ekey, epay,
-                                                eb + ca * CELL_CHUNK, min(CELL_CHUNK, mb - ca * CELL_CHUNK), cell,
-                                                dhat, lane);
+                const KindCounts a = load_chunk(cw.r[0], ekey, epay, equ, eb + ca * CELL_CHUNK,
+                                                min(CELL_CHUNK, mb - ca * CELL_CHUNK), lane);
                 pairs_vt(q, 0, a, 0, a);
                 pairs_ee_within(q, 0, a);
                 for (int cb = ca + 1; cb < nch; ++cb) {
-                    const KindCounts c = load_chunk(cw.r[1], cv, x0, x1, tlo, thi, elo, ehi, ekey, epay,
-                                                    eb + cb * CELL_CHUNK, min(CELL_CHUNK, mb - cb * CELL_CHUNK), cell,
-                                                    dhat, lane);
+                    const KindCounts c = load_chunk(cw.r[1], ekey, epay, equ, eb + cb * CELL_CHUNK,
+                                                    min(CELL_CHUNK, mb - cb * CELL_CHUNK), lane);
                     pairs_vt(q, 0, a, 1, c);
                     pairs_vt(q, 1, c, 0, a);
                     pairs_ee_across(q, 0, a, 1, c);
@@ -664,6 +658,7 @@ void BroadPhase::reserve(const CollView &cv, long long cap_vt_, long long cap_ee
     cap_ent = cap_ent_;
     ekey.alloc(cap_ent);
     epay.alloc(cap_ent);
+    equ.alloc(cap_ent);
     tlo.alloc(cv.nt);
     thi.alloc(cv.nt);
     elo.alloc(cv.ne);
@@ -743,6 +738,7 @@ void BroadPhase::grow(const CollView &cv, long long cvt, long long cee, long lon
         cap_ent = cent;
         ekey.alloc(cap_ent);
         epay.alloc(cap_ent);
+        equ.alloc(cap_ent);
     }
     if (cvt > cap_vt) {
         cap_vt = cvt;
@@ -791,6 +787,15 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
     long long *tot = totals.p;
     const int np = cv.nv + cv.ne + cv.nt;
     const unsigned mask = (unsigned)(T - 1);
+    CellData g;
+    g.cv = cv;
+    g.x0 = x0;
+    g.x1 = x1;
+    g.tlo = tlo;
+    g.thi = thi;
+    g.elo = elo;
+    g.ehi = ehi;
+    g.dhat = dhat;
     RowsOut o;
     o.cnt_v = cnt_v;
     o.slots_vt = slots_vt;
@@ -811,14 +816,14 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
         BP_PROF("bp_hash_build", bcnt.zero(s); bfill.zero(s);
         if (np) {
             k_cell_insert<<<nblk(np, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, elo, ehi, gp, dhat, mask, bcnt, bstart,
-                                                        bfill, ekey, epay, 0, tot, cap_ent, overflow);
+                                                        bfill, ekey, epay, equ, 0, tot, cap_ent, overflow);
             PDC_LAUNCH_CK();
         }
         exclusive_scan(s, bcnt, bstart, T, scratch, tot);
         k_check_cap<<<1, 1, 0, s>>>(tot, cap_ent, OVF_HASH, overflow, tot + 4);
         if (np) {
             k_cell_insert<<<nblk(np, 256), 256, 0, s>>>(cv, x0, x1, tlo, thi, elo, ehi, gp, dhat, mask, bcnt, bstart,
-                                                        bfill, ekey, epay, 1, tot, cap_ent, overflow);
+                                                        bfill, ekey, epay, equ, 1, tot, cap_ent, overflow);
             PDC_LAUNCH_CK();
         });
         if (prof) prof->begin(s, "bp_cell_pairs", 0.0);
@@ -826,7 +831,7 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
         cnt_e.zero(s);
         work.zero(s);
         if (np) {
-            // about 24 resident warps per SM for each shape
+            // 64 resident warps an SM for each shape (2.8 KB of shared memory a warp)
 #define PDC_CELLS(W, B)                                                                                              \
     do {                                                                                                             \
         const int smem = (W) * (int)sizeof(CellWarp);                                                               \
@@ -835,12 +840,12 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
             PDC_CK(cudaFuncSetAttribute(k_cell_pairs<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));        \
             attr = true;                                                                                             \
         }                                                                                                            \
-        k_cell_pairs<W><<<152 * (B), (W) * 32, smem, s>>>(cv, x0, x1, tlo, thi, elo, ehi, dhat, T, bcnt, bstart, ekey, \
-                                                          epay, o, work, gp, tot, cap_ent);                          \
+        k_cell_pairs<W><<<152 * (B), (W) * 32, smem, s>>>(g, T, bcnt, bstart, ekey, epay, equ, o, work, tot,      \
+                                                          cap_ent);                                                  \
     } while (0)
-            if (w == 2) PDC_CELLS(2, 12);
-            else if (w == 8) PDC_CELLS(8, 3);
-            else PDC_CELLS(4, 6);
+            if (w == 4) PDC_CELLS(4, 16);
+            else if (w == 16) PDC_CELLS(16, 4);
+            else PDC_CELLS(8, 8);
 #undef PDC_CELLS
             PDC_LAUNCH_CK();
         }
@@ -856,7 +861,7 @@ void BroadPhase::hash_pass(cudaStream_t s, const CollView &cv, const float4 *x0,
         tune_cells = false;
         tune_wait = 0;
         const float grids[3] = {1.f, 1.5f, 2.f};
-        const int warps[3] = {2, 4, 8};
+        const int warps[3] = {4, 8, 16};
         cudaEvent_t e[4];
         for (auto &ev : e) PDC_CK(cudaEventCreate(&ev));
         auto sweep = [&](float *ms, auto &&run) {

@@ -74,6 +74,7 @@ struct BroadPhase {
     DevBuf<int> bcnt, bstart, bfill;
     DevBuf<unsigned long long> ekey;  // cell key of each table entry
     DevBuf<unsigned int> epay;        // primitive | kind << 27 | lowest-cell flags << 29
+    DevBuf<unsigned long long> equ;   // the entry's box quantized within its cell (two words)
     DevBuf<int> work;                 // bucket counter of the cell-pair kernel
     DevBuf<float4> tlo, thi, elo, ehi;
     DevBuf<int> cnt_v, cnt_e, scratch;
@@ -99,7 +100,7 @@ struct BroadPhase {
     // set, the next launch times every candidate on its own data and keeps
     // the fastest
     int pair_blocks = 152 * 8;
-    int cell_warps = 4;
+    int cell_warps = 8;
     bool tune_pairs = false, tune_cells = false;
     int tune_wait = 0;  // passes since tune_cells was set
     float pair_ms[4] = {0, 0, 0, 0}, cell_ms[3] = {0, 0, 0}, grid_ms[3] = {0, 0, 0};

@@ -222,10 +222,10 @@ def test_autotuned_batch_takes_the_same_steps(pc):
     t = pc.pdc_get_tuning(bt.h)
     assert t["tuned"] == 1
     assert t["residual_block"] in (64, 128, 256) and t["cheb_tile"] in (0, 1, 2, 3)
-    assert t["pair_blocks"] in (152 * 2, 152 * 4, 152 * 8, 152 * 16) and t["cell_warps"] in (2, 4, 8)
+    assert t["pair_blocks"] in (152 * 2, 152 * 4, 152 * 8, 152 * 16) and t["cell_warps"] in (4, 8, 16)
     assert all(v > 0 for v in t["residual_ms"] + t["pair_ms"] + t["cell_ms"])
     assert t["residual_ms"][(64, 128, 256).index(t["residual_block"])] == min(t["residual_ms"])
-    assert t["cell_ms"][(2, 4, 8).index(t["cell_warps"])] == min(t["cell_ms"])
+    assert t["cell_ms"][(4, 8, 16).index(t["cell_warps"])] == min(t["cell_ms"])
     assert t["cell_grid"] in (1.0, 1.5, 2.0) and all(v > 0 for v in t["grid_ms"])
     assert t["grid_ms"][(1.0, 1.5, 2.0).index(t["cell_grid"])] == min(t["grid_ms"])
     assert pc.pdc_get_tuning(bf.h)["tuned"] == 0
