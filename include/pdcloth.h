@@ -95,7 +95,9 @@ typedef struct {
     double jacobi_omega;     /* Jacobi damping; <= 0: automatic                  */
     int32_t solve_cycles;    /* subspace correction + sweeps per LG iteration    */
     int32_t r_warm;          /* basis size used without collision springs (0: none) */
-    int32_t r_reuse;         /* leading columns used with collision springs      */
+    int32_t r_reuse;         /* leading columns used with collision springs
+                                (<= 512; above 128 the reduced system is
+                                factored by blocks over many CTAs)           */
     int32_t precision;       /* 0: plain FP32; 1: mixed with a BF16 basis; 2:
                                 mixed with an FP16 basis scaled by a power of two
                                 (its rounding noise carries ~2^-6 of the BF16
@@ -470,7 +472,7 @@ pdc_status pdc_op_residual(pdc_handle h, const float *x, const float *z, const f
  * `cycles` times {subspace correction in span(U[:, :r]) with the reduced
  * matrix U^T (H + diag(cw)) U (Eq. subspace_collision / uu), `sweeps`
  * Jacobi sweeps (Eq. high_frequency_residual)}; writes x_out = x + delta.
- * r = 0 skips the correction.  Host arrays. */
+ * r = 0 skips the correction; 0 <= r <= min(r_warm, 512).  Host arrays. */
 pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, const float *cw, const float *cf,
                                int32_t r, int32_t cycles, int32_t sweeps, float *x_out);
 

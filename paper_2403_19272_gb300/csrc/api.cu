@@ -1093,7 +1093,7 @@ void pdc_ctx::install_basis(const std::vector<float> &U, int r) {
     ++graph_gen;  // new basis buffers
     r_warm = r;
     r_reuse = std::min(std::max(P.r_reuse, 0), r);
-    if (r_reuse > 128) throw Error(PDC_ERR_ARG, "r_reuse must be <= 128");
+    if (r_reuse > R_REUSE_MAX) throw Error(PDC_ERR_ARG, "r_reuse must be <= 512");
     if (r > 1024) throw Error(PDC_ERR_ARG, "basis size must be <= 1024");
     // rows padded to a multiple of 8 columns: 16-byte aligned vector loads
     ld = (r + 7) / 8 * 8;
@@ -1151,10 +1151,11 @@ void pdc_ctx::install_basis(const std::vector<float> &U, int r) {
     U32.upload(Uz, s);
     // compact copy of the leading columns for the solves with collision
     // springs: width a power of two in [8, 128] holding r_reuse columns
+    // (wider reuse bases stream the full basis)
     ldc = 0;
     Uc32.release();
     Uc16bits.release();
-    if (r_reuse > 0) {
+    if (r_reuse > 0 && r_reuse <= CHOL_ONE_CTA) {
         ldc = 8;
         while (ldc < r_reuse) ldc *= 2;
         if (P.precision != 0) {
@@ -1182,7 +1183,7 @@ void pdc_ctx::install_basis(const std::vector<float> &U, int r) {
     proj_partial.alloc((size_t)PROJ_BLOCKS * ld * 3);
     gbuf.alloc((size_t)ld * 3);
     qbuf.alloc((size_t)ld * 3);
-    dA.alloc((size_t)std::max(r_reuse * r_reuse, 1));
+    dA.alloc(dA_elems(r_reuse));
     PDC_CK(cudaStreamSynchronize(s));
 }
 
@@ -1631,7 +1632,7 @@ void pdc_ctx::enqueue_residual(bool contacts) {
         z.gb = aa_Gb.p;
         z.ngb = aa ? aa_gram_doubles() : 0;
         z.da = dA.p;
-        z.nda = contacts ? r_reuse * r_reuse : 0;
+        z.nda = contacts ? (int)dA_zero_elems(r_reuse) : 0;
         const int blocks = contacts ? std::min(nb(n), 152 * 4) : 1;
         launch_dependent(P.launch_overlap != 0, k_iter_begin, blocks, 256, 0, s, z, live_ptr);
     }
@@ -1673,8 +1674,11 @@ void pdc_ctx::enqueue_solve(bool contacts, bool springs, bool device, float w_ac
         if (r_warm > 0 && (r_nc > 0 || r_c > 0)) {
             PROF("subspace_project", bytes_basis(springs ? r_c : r_nc),
                  launch_project(s, S, rl, n_cv_d, W, sp, device));
-            if (sp && r_c > 0) PROF("subspace_syrk", 0, launch_syrk(s, S, contact_list, n_cv_d, cw, W, false));
-            PROF("reduced_solve", 0, launch_reduced_solve(s, S, n_cv_d, W));
+            // the spring weights and the basis are fixed within a solve: the
+            // reduced matrix is updated (and factored) in its first cycle
+            if (sp && r_c > 0 && cyc == 0)
+                PROF("subspace_syrk", 0, launch_syrk(s, S, contact_list, n_cv_d, cw, W, false));
+            PROF("reduced_solve", 0, launch_reduced_solve(s, S, n_cv_d, W, cyc == 0));
             PROF("subspace_lift", bytes_basis(springs ? r_c : r_nc) + 12.0 * n,
                  launch_lift(s, S, n_cv_d, W, have_delta ? din : nullptr, dout, sp, device));
             std::swap(din, dout);
@@ -2554,7 +2558,7 @@ void pdc_default_params(pdc_params *p) {
 
 static bool params_valid(const pdc_params *params) {
     return params->dt > 0 && params->precision >= 0 && params->precision <= 2 && params->r_warm >= 0 &&
-           params->r_reuse >= 0 && params->r_reuse <= 128 && params->max_outer >= 0 && params->max_inner >= 0 &&
+           params->r_reuse >= 0 && params->r_reuse <= R_REUSE_MAX && params->max_outer >= 0 && params->max_inner >= 0 &&
            params->warm_iters >= 0 && params->a_max >= 0 && params->a_max <= 127 &&
            (params->samples_vt == 0 || params->samples_vt == 1 || params->samples_vt == 3) &&
            (params->samples_ee == 0 || params->samples_ee == 1 || params->samples_ee == 4) &&
@@ -3159,7 +3163,7 @@ pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, con
     API_BEGIN(h)
     if (!x || !z || !x_out || cycles < 1 || sweeps < 0) throw Error(PDC_ERR_ARG, "pdc_op_global_solve: bad arguments");
     if (r < 0 || r > h->r_warm) throw Error(PDC_ERR_ARG, "pdc_op_global_solve: r exceeds the basis size");
-    if (r > 128) throw Error(PDC_ERR_ARG, "pdc_op_global_solve: r must be <= 128");
+    if (r > R_REUSE_MAX) throw Error(PDC_ERR_ARG, "pdc_op_global_solve: r must be <= 512");
     cudaStream_t s = h->s;
     int n = h->n;
     DevBuf<float4> xa, za, ua, xo;
@@ -3172,7 +3176,7 @@ pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, con
     xo.alloc(n);
     upload_contact(h, cw, cf);
     ClothView c = h->cloth();
-    if (h->dA.n < (size_t)std::max(r * r, 1)) h->dA.alloc((size_t)r * r);
+    if (h->dA.n < dA_elems(r)) h->dA.alloc(dA_elems(r));
     // the factorised path with the leading r columns: reduced matrix U^T (H + diag(cw)) U
     SubspaceView S = h->sub(0, r);
     SubspaceWork W = h->work();
@@ -3192,7 +3196,7 @@ pdc_status pdc_op_global_solve(pdc_handle h, const float *x, const float *z, con
         }
         if (r > 0) {
             launch_project(s, S, rl, one, W);
-            PDC_CK(cudaMemsetAsync(W.dA, 0, sizeof(double) * r * r, s));
+            PDC_CK(cudaMemsetAsync(W.dA, 0, sizeof(double) * dA_zero_elems(r), s));
             launch_syrk(s, S, h->contact_list, ncv, h->CW, W);
             launch_reduced_solve(s, S, one, W);
             launch_lift(s, S, one, W, have ? din : nullptr, dout);

@@ -7,8 +7,9 @@
 // fixed and its inverse is precomputed (the explicit-inverse idea of the
 // paper's implementation section), so the solve is a matrix-vector product;
 // with springs the leading r_c x r_c block plus the SYRK update is factored
-// by Cholesky in one CTA.  Mixed form: FP64 inverse / factorisation; plain
-// form: FP32.
+// by Cholesky in FP64 (in one CTA up to 128 columns, by blocks over many
+// CTAs above).  The inverse is FP64 in the mixed forms and FP32 in the
+// plain form.
 #include <algorithm>
 #include <type_traits>
 
@@ -404,6 +405,300 @@ __global__ void __launch_bounds__(256) k_chol_solve(SubspaceView S, const int *n
     for (int e = tid; e < r * 3; e += nt) q[e] = s_bad ? 0.f : (float)b[e];
 }
 
+// ---------------------------------------------------------------- blocked factorisation (r_c > CHOL_ONE_CTA)
+// The same solve as k_chol_solve for wider reuse bases: r_c is padded to
+// R = nb * CHOL_B (identity on the padding, zero right-hand side there) and
+// the lower Cholesky factor is formed by block columns (a panel launch, then
+// a launch updating the trailing block triangle), followed by forward and
+// backward substitution by blocks.  Every step is FP64.  A CTA that needs a
+// diagonal block's factor or a block of the solution computes it itself from
+// data the previous launches finished, in the same order as the CTA that
+// stores it, so no CTA waits on another.
+
+// Block (bi, bj), bj <= bi, of a lower block triangle numbered row by row.
+__device__ inline void tri_tile(int t, int &bi, int &bj) {
+    int i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    while (i > 0 && i * (i + 1) / 2 > t) --i;
+    bi = i;
+    bj = t - i * (i + 1) / 2;
+}
+
+// Regions of dA on the blocked path (see dA_elems).
+struct BlkLayout {
+    double *A, *Dg, *b, *y, *q, *bad;
+};
+__device__ inline BlkLayout blk_layout(double *dA, int R) {
+    BlkLayout L;
+    L.A = dA;
+    L.Dg = dA + (long long)R * R;
+    L.b = L.Dg + (long long)CHOL_B * R;
+    L.y = L.b + 3LL * R;
+    L.q = L.y + 3LL * R;
+    L.bad = L.q + 3LL * R;
+    return L;
+}
+
+__device__ inline bool blk_skip(const SubspaceView &S, const int *n_cv) {
+    return loop_dead(S.live) || !(n_cv && *n_cv > 0) || S.r_c <= CHOL_ONE_CTA;
+}
+
+constexpr int SYRKB_C = 32;  // contact vertices staged per round
+
+// Lower block tiles of dA = sum_v cw_v U_v U_v^T (leading r_c columns, rows
+// and columns padded to R with zeros); blockIdx.y splits the contact list.
+template <class TU>
+__global__ void __launch_bounds__(256) k_syrk_blocks(SubspaceView S, const TU *__restrict__ U,
+                                                     const int *__restrict__ list, const int *n_cv,
+                                                     const float *__restrict__ cw, double *__restrict__ dA) {
+    __shared__ double s_a[SYRKB_C][CHOL_B + 1], s_b[SYRKB_C][CHOL_B + 1];
+    __shared__ double s_w[SYRKB_C];
+    if (blk_skip(S, n_cv)) return;
+    const int nc = *n_cv, r = S.r_c, R = chol_pad(r);
+    int bi, bj;
+    tri_tile(blockIdx.x, bi, bj);
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    const int nchunk = (nc + SYRKB_C - 1) / SYRKB_C;
+    for (int ch = blockIdx.y; ch < nchunk; ch += gridDim.y) {
+        __syncthreads();
+        for (int e = tid; e < SYRKB_C * CHOL_B; e += blockDim.x) {
+            const int c = e / CHOL_B, k = e % CHOL_B, ci = ch * SYRKB_C + c;
+            double a = 0.0, b = 0.0;
+            if (ci < nc) {
+                const TU *row = U + (long long)list[ci] * S.ld;
+                const int ja = bi * CHOL_B + k, jb = bj * CHOL_B + k;
+                if (ja < r) a = (double)tofloat<TU>(row[ja]);
+                if (jb < r) b = (double)tofloat<TU>(row[jb]);
+            }
+            s_a[c][k] = a;
+            s_b[c][k] = b;
+        }
+        if (tid < SYRKB_C) {
+            const int ci = ch * SYRKB_C + tid;
+            s_w[tid] = ci < nc ? (double)cw[list[ci]] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int c = 0; c < SYRKB_C; ++c) {
+            const double w = s_w[c];
+            const double a0 = w * s_a[c][2 * ty], a1 = w * s_a[c][2 * ty + 1];
+            const double b0 = s_b[c][2 * tx], b1 = s_b[c][2 * tx + 1];
+            acc[0][0] = fma(a0, b0, acc[0][0]);
+            acc[0][1] = fma(a0, b1, acc[0][1]);
+            acc[1][0] = fma(a1, b0, acc[1][0]);
+            acc[1][1] = fma(a1, b1, acc[1][1]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (acc[a][b] != 0.0)
+                atomicAdd(&dA[(long long)(bi * CHOL_B + 2 * ty + a) * R + bj * CHOL_B + 2 * tx + b], acc[a][b]);
+}
+
+// b = g (zero on the padding); with `matrix`, also the lower triangle of
+// A = A0[:r, :r] + dA (identity on the padding) and the failed-pivot marker
+// cleared.
+__global__ void k_chol_blk_init(SubspaceView S, const int *n_cv, double *__restrict__ dA,
+                                const double *__restrict__ g, int matrix) {
+    if (blk_skip(S, n_cv)) return;
+    const int r = S.r_c, R = chol_pad(r);
+    const BlkLayout L = blk_layout(dA, R);
+    const long long nm = (long long)R * R, tot = nm + 3LL * R + (matrix ? 1 : 0);
+    for (long long e = (matrix ? 0 : nm) + (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (e < nm) {
+            const int i = (int)(e / R), j = (int)(e % R);
+            if (j > i) continue;
+            dA[e] = i < r ? S.A0[(long long)i * S.ld + j] + dA[e] : (i == j ? 1.0 : 0.0);
+        } else if (e < nm + 3LL * R) {
+            const int k = (int)(e - nm);
+            L.b[k] = k < 3 * r ? g[k] : 0.0;
+        } else {
+            *L.bad = 0.0;
+        }
+    }
+}
+
+// Cholesky factor of diagonal block k (lower, in place in shared memory),
+// one warp; lane i owns row i.  A non-positive pivot is replaced by 1 and
+// reported.
+__device__ inline bool factor_diag_block(double (*D)[CHOL_B + 1], int lane) {
+    bool bad = false;
+    for (int c = 0; c < CHOL_B; ++c) {
+        double p = D[c][c];
+        if (!(p > 0.0) || !isfinite(p)) {
+            bad = true;
+            p = 1.0;
+        }
+        const double d = sqrt(p);
+        __syncwarp();
+        if (lane == c) D[c][c] = d;
+        if (lane > c) D[lane][c] /= d;
+        __syncwarp();
+        if (lane > c) {
+            const double l = D[lane][c];
+            for (int j = c + 1; j <= lane; ++j) D[lane][j] -= l * D[j][c];
+        }
+        __syncwarp();
+    }
+    return bad;
+}
+
+// Panel k: every CTA factors diagonal block k of A; CTA 0 stores the factor
+// L_kk in the diagonal-factor region, CTA c >= 1 forms block (k + c, k) of
+// the factor in place, L_ik = A_ik L_kk^-T.
+__global__ void __launch_bounds__(32) k_chol_blk_panel(SubspaceView S, const int *n_cv, double *__restrict__ dA,
+                                                       int k, int *flag) {
+    __shared__ double D[CHOL_B][CHOL_B + 1];
+    __shared__ double X[CHOL_B][CHOL_B + 1];
+    if (blk_skip(S, n_cv)) return;
+    const int R = chol_pad(S.r_c), lane = threadIdx.x;
+    const long long k0 = (long long)k * CHOL_B;
+    for (int i = 0; i < CHOL_B; ++i) D[i][lane] = dA[(k0 + i) * R + k0 + lane];
+    __syncwarp();
+    const bool bad = factor_diag_block(D, lane);
+    if (blockIdx.x == 0) {  // to its own region: the other CTAs read block (k, k) of A
+        const BlkLayout L = blk_layout(dA, R);
+        for (int i = 0; i < CHOL_B; ++i) L.Dg[(k0 + i) * CHOL_B + lane] = D[i][lane];
+        if (bad && lane == 0) {
+            *L.bad = 1.0;
+            atomicOr(flag, 1);
+        }
+        return;
+    }
+    const long long i0 = (long long)(k + blockIdx.x) * CHOL_B;
+    for (int i = 0; i < CHOL_B; ++i) X[i][lane] = dA[(i0 + i) * R + k0 + lane];
+    __syncwarp();
+    // row `lane` of X L_kk^T = A_ik, column by column
+    for (int c = 0; c < CHOL_B; ++c) {
+        double x = X[lane][c];
+        for (int m = 0; m < c; ++m) x -= X[lane][m] * D[c][m];
+        X[lane][c] = x / D[c][c];
+    }
+    __syncwarp();
+    for (int i = 0; i < CHOL_B; ++i) dA[(i0 + i) * R + k0 + lane] = X[i][lane];
+}
+
+// Trailing update after panel k: A_ij -= L_ik L_jk^T for the lower block
+// tiles k < j <= i < nb (diagonal tiles in full; their upper half is never read).
+__global__ void __launch_bounds__(256) k_chol_blk_update(SubspaceView S, const int *n_cv, double *__restrict__ dA,
+                                                         int k) {
+    __shared__ double Li[CHOL_B][CHOL_B + 1], Lj[CHOL_B][CHOL_B + 1];
+    if (blk_skip(S, n_cv)) return;
+    const int R = chol_pad(S.r_c);
+    int ti, tj;
+    tri_tile(blockIdx.x, ti, tj);
+    const long long k0 = (long long)k * CHOL_B, i0 = (long long)(k + 1 + ti) * CHOL_B,
+                    j0 = (long long)(k + 1 + tj) * CHOL_B;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < CHOL_B * CHOL_B; e += blockDim.x) {
+        const int row = e / CHOL_B, col = e % CHOL_B;
+        Li[row][col] = dA[(i0 + row) * R + k0 + col];
+        Lj[row][col] = dA[(j0 + row) * R + k0 + col];
+    }
+    __syncthreads();
+    const int ty = tid >> 4, tx = tid & 15;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int row = 2 * ty + a, col = 2 * tx + b;
+            double acc = 0.0;
+#pragma unroll 8
+            for (int m = 0; m < CHOL_B; ++m) acc = fma(Li[row][m], Lj[col][m], acc);
+            dA[(i0 + row) * R + j0 + col] -= acc;
+        }
+}
+
+// Forward substitution, block column k: every CTA forms y_k = L_kk^-1 b_k
+// (lane i owns row i); CTA 0 stores it, CTA c >= 1 updates
+// b_{k+c} -= L_{k+c,k} y_k.
+__global__ void __launch_bounds__(32) k_chol_blk_fwd(SubspaceView S, const int *n_cv, double *__restrict__ dA,
+                                                     int k) {
+    __shared__ double D[CHOL_B][CHOL_B + 1];
+    __shared__ double Y[CHOL_B][3];
+    if (blk_skip(S, n_cv)) return;
+    const int R = chol_pad(S.r_c), lane = threadIdx.x;
+    const long long k0 = (long long)k * CHOL_B;
+    const BlkLayout L = blk_layout(dA, R);
+    double *b = L.b, *y = L.y;
+    for (int i = 0; i < CHOL_B; ++i) D[i][lane] = L.Dg[(k0 + i) * CHOL_B + lane];
+    double v[3];
+    for (int d = 0; d < 3; ++d) v[d] = b[(k0 + lane) * 3 + d];
+    __syncwarp();
+    for (int c = 0; c < CHOL_B; ++c) {
+        const double dcc = D[c][c];
+        for (int d = 0; d < 3; ++d) {
+            if (lane == c) v[d] /= dcc;
+            const double yc = __shfl_sync(0xffffffffu, v[d], c);
+            if (lane > c) v[d] -= D[lane][c] * yc;
+        }
+    }
+    if (blockIdx.x == 0) {
+        for (int d = 0; d < 3; ++d) y[(k0 + lane) * 3 + d] = v[d];
+        return;
+    }
+    for (int d = 0; d < 3; ++d) Y[lane][d] = v[d];
+    const long long i0 = (long long)(k + blockIdx.x) * CHOL_B;
+    __syncwarp();
+    for (int i = 0; i < CHOL_B; ++i) D[i][lane] = dA[(i0 + i) * R + k0 + lane];
+    __syncwarp();
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < CHOL_B; ++c) {
+        const double l = D[lane][c];
+        for (int d = 0; d < 3; ++d) acc[d] = fma(l, Y[c][d], acc[d]);
+    }
+    for (int d = 0; d < 3; ++d) b[(i0 + lane) * 3 + d] -= acc[d];
+}
+
+// Backward substitution L^T q = y, block row k (launched for k = nb-1 .. 0):
+// every CTA forms q_k = L_kk^-T y_k; CTA 0 stores it (and, at k = 0, writes
+// the FP32 solution, zero after a failed pivot), CTA c >= 1 updates
+// y_{k-c} -= L_{k,k-c}^T q_k.
+__global__ void __launch_bounds__(32) k_chol_blk_bwd(SubspaceView S, const int *n_cv, double *__restrict__ dA,
+                                                     int k, float *__restrict__ q_out) {
+    __shared__ double D[CHOL_B][CHOL_B + 1];
+    __shared__ double Q[CHOL_B][3];
+    if (blk_skip(S, n_cv)) return;
+    const int r = S.r_c, R = chol_pad(r), lane = threadIdx.x;
+    const long long k0 = (long long)k * CHOL_B;
+    const BlkLayout L = blk_layout(dA, R);
+    double *y = L.y, *q = L.q;
+    for (int i = 0; i < CHOL_B; ++i) D[i][lane] = L.Dg[(k0 + i) * CHOL_B + lane];
+    double v[3];
+    for (int d = 0; d < 3; ++d) v[d] = y[(k0 + lane) * 3 + d];
+    __syncwarp();
+    for (int c = CHOL_B - 1; c >= 0; --c) {
+        const double dcc = D[c][c];
+        for (int d = 0; d < 3; ++d) {
+            if (lane == c) v[d] /= dcc;
+            const double qc = __shfl_sync(0xffffffffu, v[d], c);
+            if (lane < c) v[d] -= D[c][lane] * qc;
+        }
+    }
+    if (blockIdx.x == 0) {
+        for (int d = 0; d < 3; ++d) q[(k0 + lane) * 3 + d] = v[d];
+        if (k == 0) {
+            __syncwarp();  // this warp's stores of block 0 are visible to its lanes
+            const bool bad = *L.bad != 0.0;
+            for (int e = lane; e < 3 * r; e += 32) q_out[e] = bad ? 0.f : (float)q[e];
+        }
+        return;
+    }
+    for (int d = 0; d < 3; ++d) Q[lane][d] = v[d];
+    __syncwarp();
+    const long long i0 = (long long)(k - blockIdx.x) * CHOL_B;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < CHOL_B; ++c) {
+        const double l = dA[(k0 + c) * R + i0 + lane];  // L[k0 + c][i0 + lane]
+        for (int d = 0; d < 3; ++d) acc[d] = fma(l, Q[c][d], acc[d]);
+    }
+    for (int d = 0; d < 3; ++d) y[(i0 + lane) * 3 + d] -= acc[d];
+}
+
 // dout_i = din_i + sum_j U[i][j] q_j: one warp per row, lane l owns columns
 // 8l..8l+7 of each 256-column chunk, warp-shuffle reduction of the 3 sums.
 template <class TU, int NCH>
@@ -562,7 +857,17 @@ void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, con
 void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const int *n_cv, const float *cw,
                  SubspaceWork &W, bool zero) {
     if (S.r_c == 0) return;
-    if (zero) launch_live_zero(s, S.live, W.dA, sizeof(double) * S.r_c * S.r_c);
+    if (zero) launch_live_zero(s, S.live, W.dA, sizeof(double) * dA_zero_elems(S.r_c));
+    if (S.r_c > CHOL_ONE_CTA) {
+        const int nb = chol_pad(S.r_c) / CHOL_B, ntile = nb * (nb + 1) / 2;
+        const dim3 grid(ntile, std::max(1, 4 * 152 / ntile));
+        with_basis(S, false, [&](auto *U) {
+            using TU = std::remove_const_t<std::remove_pointer_t<decltype(U)>>;
+            k_syrk_blocks<TU><<<grid, 256, 0, s>>>(S, U, list, n_cv, cw, W.dA);
+        });
+        PDC_LAUNCH_CK();
+        return;
+    }
     with_basis(S, false, [&](auto *U) {
         using TU = std::remove_const_t<std::remove_pointer_t<decltype(U)>>;
         int ne = S.r_c * S.r_c;
@@ -573,7 +878,7 @@ void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const i
     PDC_LAUNCH_CK();
 }
 
-void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv, SubspaceWork &W) {
+void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv, SubspaceWork &W, bool factor) {
     const bool mixed = S.precision != 0;  // mixed forms: FP64 reduced solves
     if (S.r_nc > 0) {
         int thr = S.r_nc * 32;
@@ -583,9 +888,21 @@ void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv
         else
             k_apply_inverse<float><<<(thr + 255) / 256, 256, 0, s>>>(S, n_cv, S.A0inv32, W.g, W.q);
     }
-    if (S.r_c > 0) {  // FP64 in both forms (see k_syrk)
+    if (S.r_c > 0 && S.r_c <= CHOL_ONE_CTA) {  // FP64 in both forms (see k_syrk)
         size_t sm = sizeof(double) * (S.r_c * S.r_c + S.r_c * 3);
         k_chol_solve<<<1, 256, sm, s>>>(S, n_cv, W.dA, W.g, W.q, W.flag);
+    } else if (S.r_c > CHOL_ONE_CTA) {
+        const int R = chol_pad(S.r_c), nb = R / CHOL_B;
+        const long long tot = factor ? (long long)R * R + 3LL * R + 1 : 3LL * R;
+        k_chol_blk_init<<<(int)std::min<long long>((tot + 255) / 256, 152 * 8), 256, 0, s>>>(S, n_cv, W.dA, W.g,
+                                                                                          factor ? 1 : 0);
+        for (int k = 0; factor && k < nb; ++k) {
+            k_chol_blk_panel<<<nb - k, 32, 0, s>>>(S, n_cv, W.dA, k, W.flag);
+            const int m = nb - k - 1;
+            if (m > 0) k_chol_blk_update<<<m * (m + 1) / 2, 256, 0, s>>>(S, n_cv, W.dA, k);
+        }
+        for (int k = 0; k < nb; ++k) k_chol_blk_fwd<<<nb - k, 32, 0, s>>>(S, n_cv, W.dA, k);
+        for (int k = nb - 1; k >= 0; --k) k_chol_blk_bwd<<<k + 1, 32, 0, s>>>(S, n_cv, W.dA, k, W.q);
     }
     PDC_LAUNCH_CK();
 }

@@ -1,5 +1,7 @@
 // Subspace-reuse kernels (Sec. 5) and basis construction.
 #pragma once
+#include <algorithm>
+
 #include "pdc_internal.cuh"
 #include "pdc_umma.cuh"
 
@@ -38,9 +40,32 @@ struct SubspaceWork {
     float *partial;    // [blocks][ld][3]
     double *g;         // [ld][3]
     float *q;          // [ld][3]
-    double *dA;        // [r_c][r_c] collision update of the reduced matrix (FP64)
+    double *dA;        // collision update of the reduced matrix (FP64), see dA_elems
     int *flag;         // factorisation status
 };
+
+// Solves with collision springs on up to CHOL_ONE_CTA columns factor the
+// reduced matrix in one CTA's shared memory, dA holding [r_c][r_c].  Wider
+// ones pad r_c to R = a multiple of CHOL_B and factor by blocks over many
+// CTAs: dA then holds the [R][R] matrix (lower triangle used), the factors
+// of its diagonal blocks ([R/CHOL_B][CHOL_B][CHOL_B]), the right-hand side
+// b, the forward solution y and the solution q (each [R][3]) and a
+// failed-pivot marker.
+constexpr int CHOL_ONE_CTA = 128;
+constexpr int CHOL_B = 32;
+constexpr int R_REUSE_MAX = 512;
+__host__ __device__ inline int chol_pad(int r) { return (r + CHOL_B - 1) / CHOL_B * CHOL_B; }
+// doubles of dA a solve on r_c columns uses / that must be zero before the update
+inline size_t dA_elems(int r) {
+    if (r <= CHOL_ONE_CTA) return (size_t)std::max(r * r, 1);
+    size_t R = (size_t)chol_pad(r);
+    return R * R + (size_t)(CHOL_B + 9) * R + 1;
+}
+inline size_t dA_zero_elems(int r) {
+    if (r <= CHOL_ONE_CTA) return (size_t)r * r;
+    size_t R = (size_t)chol_pad(r);
+    return R * R;
+}
 
 constexpr int PROJ_BLOCKS = 608;
 
@@ -54,12 +79,16 @@ void launch_project(cudaStream_t s, const SubspaceView &S, const float4 *rl, con
                     bool maybe_contacts = true, bool device_choice = false);
 // whether the tensor-core / compact choice of a spring iteration can be left to the device
 bool device_path_choice(const SubspaceView &S);
-// dA = sum over listed vertices of cw_v U_v U_v^T (leading r_c columns);
-// zero = false: dA has been zeroed already.
+// dA = sum over listed vertices of cw_v U_v U_v^T (leading r_c columns;
+// above CHOL_ONE_CTA columns only the lower block triangle of the padded
+// matrix); zero = false: dA has been zeroed already.
 void launch_syrk(cudaStream_t s, const SubspaceView &S, const int *list, const int *n_cv, const float *cw,
                  SubspaceWork &W, bool zero = true);
-// q = (reduced matrix)^-1 g.
-void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv, SubspaceWork &W);
+// q = (reduced matrix)^-1 g.  factor = false: the reduced matrix with
+// springs is the one the previous call factored (only the blocked path above
+// CHOL_ONE_CTA columns keeps its factor; the one-CTA path refactors).
+void launch_reduced_solve(cudaStream_t s, const SubspaceView &S, const int *n_cv, SubspaceWork &W,
+                          bool factor = true);
 // dout = din + U q (din may be NULL: zero).
 void launch_lift(cudaStream_t s, const SubspaceView &S, const int *n_cv, const SubspaceWork &W, const float4 *din,
                  float4 *dout, bool maybe_contacts = true, bool device_choice = false);

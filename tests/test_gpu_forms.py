@@ -136,6 +136,20 @@ def test_two_subspace_split_120_30_parity_with_contacts(pc):
     assert max(r["n_act_g"] for r in recs) > 0
 
 
+def test_wide_reuse_basis_parity_with_contacts(pc):
+    """Mixed FP16 form with collision springs on 160 of 256 columns: the
+    solves without springs run on the tensor cores, those with springs
+    factor the reduced system by blocks over many CTAs (FP64) instead of in
+    one CTA."""
+    sc = thrown_drape(24)
+    gp = params(pc, fixed_iters=1, warm_iters=2, max_outer=1, max_inner=3, solve_cycles=40, jacobi_sweeps=8,
+                r_warm=256, r_reuse=160, precision=2, tensor_cores=1, d_hat=1e-3)
+    op = pd.Params(fixed_iters=True, warm_iters=2, max_outer=1, max_inner=3, dhat=1e-3)
+    recs = run_parity(pc, sc, gp, op, 5)
+    assert sum(r["contact_iters"] for r in recs) > 0
+    assert max(r["n_act_g"] for r in recs) > 0
+
+
 def test_ndb_life_span_over_eight_inner_iterations(pc):
     """Eq. (exp) with counters well past 2: the GPU's springs double their
     weight every iteration a pair stays active, exactly as the oracle's."""

@@ -356,6 +356,35 @@ def test_global_solve_one_cycle_matches_dense_reference(pc):
     cl.close()
 
 
+@pytest.mark.parametrize("side,r", [(20, 150), (24, 512)])
+def test_global_solve_one_cycle_wide_reuse_basis(pc, side, r):
+    """Reduced solves with collision springs on more than 128 columns (the
+    blocked FP64 factorisation over many CTAs; r = 150 pads to 160 with a
+    ragged last block, r = 512 is the largest accepted) against the dense
+    FP64 reference, as in the 16-column case."""
+    rng = np.random.default_rng(31)
+    sc = wl.drape_sphere(side=side, with_sphere=False)
+    cl = pc.Cloth(sc, params(pc, r_warm=0, jacobi_omega=0.5))
+    m = pd.Model(sc.verts, sc.tris, sc.pins, sc.density, sc.k_stretch, sc.k_bend, 0.005)
+    U = _seeded_basis(m.n, r, m.free, 32)
+    pc.pdc_set_basis(cl.h, U)
+    x = (m.X + rng.normal(size=m.X.shape) * 0.003).astype(np.float32)
+    z = m.X.astype(np.float32)
+    # spring weights spanning four decades, as life-span doubling produces
+    cw = np.where(rng.random(m.n) < 0.15, 80.0 * 2.0 ** rng.integers(0, 14, m.n), 0.0).astype(np.float32)
+    cw[~m.free] = 0
+    cf = np.zeros((m.n, 3), np.float32)
+    out = pc.pdc_op_global_solve(cl.h, x, z, cw, cf, r, 1, 6)
+    x64 = x.astype(np.float64)
+    rr = np.zeros_like(x64)
+    rr[m.free] = -m.residual(x64, z.astype(np.float64), cw.astype(np.float64), cw[:, None] * x64)
+    d0, _ = subspace.subspace_correction(U.astype(np.float64), m.H, cw.astype(np.float64), rr)
+    d = subspace.jacobi(m.H, cw.astype(np.float64), rr, d0, 6, 0.5, m.free)
+    exp = x64 + d
+    assert np.max(np.abs(out - exp)) <= 1e-4 * np.max(np.abs(d))
+    cl.close()
+
+
 def test_global_solve_converges_to_exact_solution(pc):
     rng = np.random.default_rng(29)
     sc = wl.drape_sphere(side=20, with_sphere=False)

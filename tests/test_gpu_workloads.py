@@ -7,9 +7,10 @@ basis on the tensor cores), checked by properties that hold at any size:
   no cloth vertex ever ends inside the box (obstacles have infinite mass and
   the exit line search keeps every step free of penetration);
 * skirt on a moving body (1024 x 332, 339,968 vertices, basis of 512 columns,
-  which exceeds the tensor-core kernels' row limit and runs on the CUDA-core
-  kernels): the pinned ring follows the body's rigid motion and each step
-  ends with a small relative residual;
+  all of them reused with collision springs; it exceeds the tensor-core
+  kernels' row limit and runs on the CUDA-core kernels): the pinned ring
+  follows the body's rigid motion and each step ends with a small relative
+  residual;
 * the fold on the box as configured (dropped flat from 0.5 m, velocity noise
   N(0, 0.01), 64 LG iterations per step, 500 steps).
 
@@ -94,7 +95,7 @@ def test_fold_on_box_lands_without_entering_the_box(pc):
 
 def test_skirt_on_moving_body_runs_on_the_cuda_core_subspace_path(pc):
     sc = wl.skirt_on_body()
-    p = _production(pc, r_warm=512, r_reuse=32, eig_iters=4, max_inner=200)
+    p = _production(pc, r_warm=512, r_reuse=512, eig_iters=4, max_inner=200)
     cl = pc.Cloth(sc, p)
     chk = _Checker(sc)
     for k in range(3):
