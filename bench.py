@@ -236,7 +236,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
     # ---- kernel launches of the library per step, counted by the CUDA
     # activity profiler over a replay of the same number of steps
     restore()
-    launches, busy, gaps = count_launches(torch, one_step, steps) if launch_count else (None, None, None)
+    launches, busy, gaps, kern_ms = count_launches(torch, one_step, steps) if launch_count else (None,) * 4
     restore()
     # ---- e2e through the public API with host buffers: pin targets h2d, positions d2h
     pin_host = torch.empty(pins.shape[1:], dtype=torch.float32).pin_memory()
@@ -264,7 +264,7 @@ def run_form(pc, torch, scene, precision, steps, warmup, dev_index, launch_count
                 cand=statistics.mean(s["n_candidates"] for s in st_list),
                 toi=min(s["t_toi"] for s in st_list), finite=bool(np.isfinite(x).all()),
                 device_loops=statistics.mean(s["device_loops"] for s in st_list), device_busy=busy, idle_gaps=gaps,
-                launches=launches, tuning=tuning)
+                kernel_ms=kern_ms, launches=launches, tuning=tuning)
 
 
 def solver_like(pc, p):
@@ -371,9 +371,13 @@ def count_launches(torch, one_step, steps):
     """Kernels launched by the library (names beginning with k_) during
     `steps` steps, from torch.profiler's CUDA activity trace; the share of
     the traced interval (first kernel start to last kernel end) in which some
-    kernel ran; and the largest idle gaps between consecutive kernels,
-    summed by the pair of kernels around them.  (None, None, None) if the
-    trace is unavailable."""
+    kernel ran; the largest idle gaps between consecutive kernels, summed by
+    the pair of kernels around them; and the time per step in which some
+    kernel ran (ms).  The trace lengthens the relaunch of a CUDA-graph while
+    node's body (the gaps before each LG iteration's first kernel), so the
+    busy share of the traced interval understates the untraced one; the
+    kernel time per step against the untraced ms/step does not.  (None,) * 4
+    if the trace is unavailable."""
     try:
         from torch.profiler import ProfilerActivity, profile
         with profile(activities=[ProfilerActivity.CUDA]) as prof:
@@ -416,9 +420,10 @@ def count_launches(torch, one_step, steps):
             busy = round(tot / span, 4)
             top = sorted(acc.items(), key=lambda kv: -kv[1][1])[:10]
             gaps = {k: {"count": v[0], "us_per_step": round(v[1] / steps, 1)} for k, v in top}
-        return n, busy, gaps
+        kern_ms = round(tot / 1e3 / steps, 3) if spans else None
+        return n, busy, gaps, kern_ms
     except Exception:
-        return None, None, None
+        return None, None, None, None
 
 
 # profiled regions that enclose other profiled regions (not kernels themselves)
@@ -681,6 +686,7 @@ def main():
                       "gpu_launches": d["launches"],
                       "rel_residual": d["rel_res"], "candidates": d["cand"], "min_toi": d["toi"],
                       "device_loops_per_step": d["device_loops"], "device_busy": d["device_busy"],
+                      "kernel_ms_per_step": d["kernel_ms"],
                       "setup_s": round(d["setup_s"], 2), "e2e_ms_per_step": round(d["e2e_ms"], 3),
                       "tuning": d["tuning"]}
                   for f, d in forms.items()},
